@@ -1,0 +1,69 @@
+"""Pins for the FP64 kick-drift-kick leapfrog ("update step", Sec. 1).
+
+Kepler's two-body orbit in closed form (solved through Kepler's equation)
+gives second-order convergence; the energy error of a Plummer cluster scales
+as dt^2; the scheme is time-reversible and conserves momentum.
+"""
+import math
+
+import numpy as np
+
+import oracle
+import workloads
+
+
+def _kepler_orbit(t, a=1.0, e=0.5, mu=1.0):
+    """Relative position of a bound Kepler orbit at time t (periapsis at t=0)."""
+    n = math.sqrt(mu / a ** 3)
+    M = n * t
+    E = M
+    for _ in range(60):
+        E -= (E - e * math.sin(E) - M) / (1.0 - e * math.cos(E))
+    return np.array([a * (math.cos(E) - e), a * math.sqrt(1 - e * e) * math.sin(E), 0.0])
+
+
+def _kepler_run(dt, T, e=0.5):
+    m1, m2 = 0.7, 0.3
+    a = 1.0
+    rp = a * (1 - e)
+    vp = math.sqrt((m1 + m2) * (1 + e) / (a * (1 - e)))
+    rel_x = np.array([rp, 0.0, 0.0])
+    rel_v = np.array([0.0, vp, 0.0])
+    x = np.array([-m2 / (m1 + m2) * rel_x, m1 / (m1 + m2) * rel_x])
+    v = np.array([-m2 / (m1 + m2) * rel_v, m1 / (m1 + m2) * rel_v])
+    sysm = oracle.GravSystem([m1, m2], G=1.0, eps=0.0)
+    xT, _ = oracle.leapfrog(sysm, x, v, dt, int(round(T / dt)))
+    rel = xT[1] - xT[0]
+    return np.linalg.norm(rel - _kepler_orbit(T, a, e, m1 + m2))
+
+
+def test_kepler_second_order_convergence():
+    period = 2 * math.pi
+    errs = [_kepler_run(period / k, period) for k in (400, 800, 1600)]
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.5 < r1 < 4.5 and 3.5 < r2 < 4.5, errs
+    assert errs[2] < 1e-3
+
+
+def test_energy_error_scales_as_dt_squared():
+    g = workloads.plummer(64, seed=8)
+    sysm = oracle.GravSystem(g.m, eps=0.05)
+    E0 = oracle.diagnostics(sysm, g.x, g.v)["E"]
+    errs = []
+    for dt in (2e-3, 1e-3):
+        xs, vs = oracle.leapfrog(sysm, g.x, g.v, dt, int(round(0.2 / dt)), store=True)
+        errs.append(max(abs(oracle.diagnostics(sysm, x, v)["E"] - E0)
+                        for x, v in zip(xs[::10], vs[::10])))
+    assert 3.0 < errs[0] / errs[1] < 5.0, errs
+
+
+def test_time_reversibility_and_momentum():
+    g = workloads.plummer(32, seed=6)
+    sysm = oracle.GravSystem(g.m, eps=0.05)
+    x1, v1 = oracle.leapfrog(sysm, g.x, g.v, 1e-3, 50)
+    x2, v2 = oracle.leapfrog(sysm, x1, -v1, 1e-3, 50)
+    np.testing.assert_allclose(x2, g.x, atol=1e-12)
+    np.testing.assert_allclose(-v2, g.v, atol=1e-12)
+    P0 = np.sum(g.m[:, None] * g.v, axis=0)
+    P1 = np.sum(g.m[:, None] * v1, axis=0)
+    np.testing.assert_allclose(P1, P0, atol=1e-15)
