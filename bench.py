@@ -1,0 +1,338 @@
+"""Benchmark: all-pairs softened gravity + KDK leapfrog on one GB300.
+
+Workload: Plummer sphere, N = 262144, eps = 0.04 N^(-1/3), dt = 1e-4 (the
+large gravity workload at the size the headline metric is quoted on). One
+"step" is one leapfrog step through the public C ABI (nbody_step with
+NBODY_ACC_VALID): first half-kick + drift, the all-pairs force kernel, and the
+finalize kernel (compensated partial sums, second half-kick).
+
+Prints one JSON line: interactions/s (N^2 ordered pairs per step, the paper's
+count), the force kernel's roofline fraction against the FP32 pipe, the FP64
+oracle timed on the host cores, an end-to-end number through host buffers and
+the sampled SM clocks. ``--impl reference`` times the FP64 oracle instead.
+Under torchrun (N > 1 GPUs) every rank runs an independent replica.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_BENCH = 262144
+DT = 1e-4
+OPS_PER_PAIR = 12          # FP32 lane ops per pair of the plain gravity kernel (no potential)
+FP32_LANES_PER_SM = 128    # FFMA/FADD/FMUL lanes per SM per clock (4 SMSPs x 32)
+SM_MAX_MHZ = 2070.0
+CPU_SAMPLE_TARGETS = 16384  # oracle sample: targets x all N sources per timed "step"
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def metric_name():
+    return "G pair-interactions/s (Plummer N=262144, leapfrog step)"
+
+
+def config(n_gpus):
+    return {"workload": f"plummer-{N_BENCH}-kdk-leapfrog", "n": N_BENCH,
+            "eps": 4.0 / N_BENCH ** (1.0 / 3.0) * 0.01, "dt": DT,
+            "pairs_per_step": N_BENCH * N_BENCH, "law": "gravity (Eq. 1)",
+            "precision": "FP32 pairs, compensated per-tile sums",
+            "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"replicas x{n_gpus}" if n_gpus > 1 else "single GPU"}
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.split(",") for r in self.tmp.read().strip().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            r = [c.strip() for c in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(n_targets: int, seed: int = 1):
+    """Time the FP64 oracle on n_targets sampled targets against all N sources."""
+    import oracle
+    import workloads
+    g = workloads.plummer(N_BENCH, seed=seed, eps=workloads.plummer_softening(N_BENCH))
+    x, _, m = g.f32_as_f64()
+    idx = np.sort(np.random.default_rng(7).choice(N_BENCH, n_targets, replace=False))
+    eps = float(np.float32(g.eps))
+    oracle.grav_accel(x, m, eps=eps, idx=idx[:64])  # load + warm
+    t0 = time.perf_counter()
+    oracle.grav_accel(x, m, eps=eps, idx=idx)
+    dt = time.perf_counter() - t0
+    return n_targets * N_BENCH / dt, dt
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = os.cpu_count()
+    n_t = max(256, CPU_SAMPLE_TARGETS // 8)
+    for _ in range(args.warmup):
+        oracle_rate(n_t // 4)
+    tot_pairs, tot_t = 0.0, 0.0
+    for _ in range(args.steps):
+        r, dt = oracle_rate(n_t)
+        tot_pairs += r * dt
+        tot_t += dt
+    val = tot_pairs / tot_t / 1e9
+    out = {"impl": "reference", "metric": metric_name(), "value": val,
+           "unit": "G pair-interactions/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config(args.gpus),
+           "cpu_baseline": {"value": val, "unit": "G pair-interactions/s", "cores": cores,
+                            "kind": "oracle",
+                            "sample": f"{n_t} seeded targets x all {N_BENCH} sources per step"},
+           "e2e": {"value": val, "unit": "G pair-interactions/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="run only warmup + this many steps (for ncu launch lists)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 0)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_0706_3060_gb300 as nb
+    import workloads
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    nb._lib.load()  # fails loudly if the CUDA library is not built
+
+    g = workloads.plummer(N_BENCH, seed=1, eps=workloads.plummer_softening(N_BENCH))
+    eps = float(np.float32(g.eps))
+    x, v, m = g.f32()
+    host_pos = np.concatenate([x, m[:, None]], 1).astype(np.float32)
+    host_vel = np.concatenate([v, np.zeros((N_BENCH, 1), np.float32)], 1)
+    pos = torch.from_numpy(host_pos).to(dev).contiguous()
+    vel = torch.from_numpy(host_vel).to(dev).contiguous()
+    acc = torch.empty_like(pos)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    # a(x_0) once, then steps reuse the acceleration of the previous step
+    nb.step(pos, vel, acc, dt=DT, nsteps=0, eps=eps)
+    for _ in range(args.warmup):
+        flush.zero_()
+        nb.step(pos, vel, acc, dt=DT, nsteps=1, eps=eps, acc_valid=True)
+    torch.cuda.synchronize()
+    if args.profile_steps:
+        for _ in range(args.profile_steps):
+            nb.step(pos, vel, acc, dt=DT, nsteps=1, eps=eps, acc_valid=True)
+        torch.cuda.synchronize()
+        return
+
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    nb.timing_read(0)
+    nb.timing_enable(True)
+    t_wall = time.perf_counter()
+    for k in range(K):
+        flush.zero_()
+        starts[k].record(stream)
+        nb.step(pos, vel, acc, dt=DT, nsteps=1, eps=eps, acc_valid=True)
+        stops[k].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    nb.timing_enable(False)
+    n_force, force_ms = nb.timing_read(0)
+    clk = clocks.stop()
+    nb.sync_check()
+    step_ms = float(sum(s.elapsed_time(e) for s, e in zip(starts, stops)))
+    t_local = step_ms / 1e3
+    if world > 1:
+        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    pairs = float(N_BENCH) * N_BENCH
+    value = world * pairs * K / t_max / 1e9
+
+    # roofline of the dominant kernel (the all-pairs force kernel)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12          # T lane-op/s
+    avg_force_s = force_ms / max(n_force, 1) / 1e3
+    achieved = OPS_PER_PAIR * pairs / avg_force_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "force_kernel<grav>", "launches_timed": n_force,
+            "avg_launch_ms": avg_force_s * 1e3,
+            "ops_per_pair": OPS_PER_PAIR,
+            "peak_basis": (f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz; "
+                           "one FFMA/FADD/FMUL lane op = 1")}
+    if clk.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = achieved / (sms * FP32_LANES_PER_SM * clk["sm_mhz"] * 1e6
+                                                    / 1e12)
+    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(traffic_file):
+        try:
+            tr = json.load(open(traffic_file))
+            if tr.get("kernel_hash") == kernel_hash():
+                roof["traffic"] = tr.get("bytes_per_launch")
+        except Exception:
+            pass
+
+    out = {"metric": metric_name(), "value": value, "unit": "G pair-interactions/s",
+           "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": step_ms / K,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded Plummer sphere)", "config": config(world),
+           "roofline": roof, "clocks": clk, "gpu_launches": 3 * K,
+           "wall_s_timed_region": t_wall}
+
+    # end to end through the C ABI with pinned host buffers (copies inside)
+    hp = torch.from_numpy(host_pos.copy()).pin_memory()
+    hv = torch.from_numpy(host_vel.copy()).pin_memory()
+    ha = torch.empty_like(hp).pin_memory()
+    nb.step(hp, hv, ha, dt=DT, nsteps=0, eps=eps)
+    Ke = max(3, min(K, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        nb.step(hp, hv, ha, dt=DT, nsteps=1, eps=eps, acc_valid=True)
+    te = time.perf_counter() - t0
+    out["e2e"] = {"value": pairs * Ke / te / 1e9, "unit": "G pair-interactions/s",
+                  "h2d_bytes_per_step": 3 * N_BENCH * 16, "d2h_bytes_per_step": 3 * N_BENCH * 16,
+                  "path": "nbody_step on pinned host buffers (staged H2D, step, D2H, sync)"}
+
+    if rank == 0 and world == 1:
+        r, dt_cpu = oracle_rate(CPU_SAMPLE_TARGETS)
+        out["cpu_baseline"] = {"value": r / 1e9, "unit": "G pair-interactions/s",
+                               "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": (f"{CPU_SAMPLE_TARGETS} seeded targets x all {N_BENCH} "
+                                          f"sources, FP64, {dt_cpu:.1f} s")}
+    if not args.no_extras and rank == 0:
+        out["extras"] = extras(nb, torch, dev, g, eps)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("force_kernel.cuh", "device_common.cuh", "force_grav.cu"):
+        with open(os.path.join(ROOT, "paper_0706_3060_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def extras(nb, torch, dev, g, eps):
+    """Accuracy and the secondary forms, measured on the same GPU (not timed above)."""
+    import oracle
+    ex = {}
+    x, v, m = g.f32()
+    pos = torch.from_numpy(np.concatenate([x, m[:, None]], 1)).to(dev).contiguous()
+    acc = nb.forces(pos, eps=eps).cpu().numpy()
+    idx = np.sort(np.random.default_rng(0).choice(N_BENCH, 1024, replace=False))
+    ref = oracle.grav_accel(x.astype(np.float64), m.astype(np.float64), eps=eps, idx=idx)
+    e = np.linalg.norm(acc[idx, :3] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    ex["force_err_rms"] = float(np.sqrt(np.mean(e * e)))
+    ex["force_err_max"] = float(e.max())
+    ex["force_err_sample"] = "1024 seeded targets vs FP64 oracle"
+    # energy drift over 100 steps at dt = 1e-4 (FP64 diagnostics on the GPU)
+    vel = torch.from_numpy(np.concatenate([v, np.zeros((N_BENCH, 1), np.float32)], 1)).to(dev)
+    a2 = torch.empty_like(pos)
+    d = nb.step(pos, vel, a2, dt=DT, nsteps=100, eps=eps, report_every=100).cpu().numpy()
+    E0, E1 = d[0, 0] + d[0, 1], d[1, 0] + d[1, 1]
+    ex["energy_drift_100_steps"] = float((E1 - E0) / abs(E0))
+    return ex
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * nbody.h -- C ABI of the GB300 (sm_103a) all-pairs N-body library.
+ *
+ * The library evaluates the O(N^2) direct-summation forces of Elsen et al.,
+ * "N-Body Simulations on GPUs" (arXiv 0706.3060) -- softened gravity (Eq. 1,
+ * Table 1 "Gravity (accel)") and Lennard-Jones plus Coulomb in a continuum
+ * solvent of constant dielectric (Table 1 "LJC(constant)") -- and the update
+ * step that consumes them (Sec. 1: "a force evaluation step ... and an update
+ * step"), which it implements as kick-drift-kick leapfrog.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Interactions are ordered pairs (i, j), i != j, as in Sec. 2: the force on
+ *    i sums over all j and Newton's third law is not used to halve the work.
+ *  - Particle data are arrays of float4, 16-byte aligned, one element per
+ *    particle:
+ *      pos_m[i] = (x, y, z, m)                          both laws
+ *      prm[i]   = (q~, s~, e~, type)                    LJC only, made by
+ *                 nbody_pack_ljc: q~ = q sqrt(k_e/eps_r), s~ = sigma/2,
+ *                 e~ = sqrt(24 eps); type is the atom type as a float.
+ *      acc[i]   = (ax, ay, az, phi)  acceleration and per-particle potential
+ *                 (gravity: phi_i = -G sum_j m_j / s_ij, U = 1/2 sum m_i phi_i;
+ *                  LJC: phi_i = sum_j u_ij pair energies, U = 1/2 sum phi_i).
+ *      vel[i]   = (vx, vy, vz, unused)
+ *  - Pointers are device pointers unless an entry point says otherwise. The
+ *    caller owns every array it passes; the library owns only its internal
+ *    workspace (see nbody_release).
+ *  - All work is enqueued on the caller's CUDA stream `stream` (a
+ *    cudaStream_t; NULL is the legacy default stream) and is asynchronous,
+ *    except where a function states that it synchronizes.
+ *  - Every function returns an nbody_status. On failure the reason is
+ *    available from nbody_last_error() (thread-local). No function aborts,
+ *    exits or throws across the ABI. Arguments are validated before any work
+ *    is enqueued; a rejected call leaves every output untouched.
+ *  - A kernel never waits without a bound: a wait that runs out sets a device
+ *    error flag, the kernel returns, and the next synchronizing call reports
+ *    NBODY_ETIMEOUT.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *nbody_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    NBODY_OK = 0,
+    NBODY_EINVAL = 1,       /* bad size, null pointer, bad enum or flag      */
+    NBODY_EALIGN = 2,       /* pointer not 16-byte aligned                   */
+    NBODY_ENOMEM = 3,       /* workspace allocation failed                   */
+    NBODY_ECUDA = 4,        /* a CUDA runtime call failed                    */
+    NBODY_ETIMEOUT = 5,     /* a bounded device wait ran out                 */
+    NBODY_EUNSUPPORTED = 6, /* no GPU, wrong architecture, or unsupported mode */
+} nbody_status;
+
+/* Force laws (Table 1). */
+enum {
+    NBODY_LAW_GRAV = 0, /* "Gravity (accel)", Eq. 1                        */
+    NBODY_LAW_LJC = 1,  /* "LJC(constant)": LJ 12-6 + Coulomb / eps_r       */
+};
+
+/* nbody_params.flags */
+enum {
+    NBODY_COMPUTE_POT = 1u << 0,     /* also compute phi (acc[i].w)            */
+    NBODY_PRECISE_RSQRT = 1u << 1,   /* one Newton step on the hardware rsqrt  */
+    NBODY_NO_COMPENSATION = 1u << 2, /* plain FP32 sums (default: per-tile
+                                        TwoSum compensated sums)               */
+    NBODY_ACC_VALID = 1u << 3,       /* nbody_step: acc already holds a(x) for
+                                        the entry positions                    */
+    NBODY_ACCUMULATE = 1u << 4,      /* nbody_adjoint: add into the outputs    */
+};
+
+typedef struct {
+    int32_t law;     /* NBODY_LAW_*                                          */
+    uint32_t flags;  /* NBODY_* flags above                                  */
+    float G;         /* gravitational constant (gravity)                     */
+    float eps2;      /* squared softening eps^2 (gravity; the Appendix "eps") */
+    int32_t tile;    /* kernel tile configuration, -1 = tuned/default        */
+    int32_t jsplit;  /* j-slices per i-tile ("replication", Sec. 3.4), 0 = auto */
+} nbody_params;
+
+/* Library version (major * 10000 + minor * 100 + patch). Never fails. */
+int nbody_version(void);
+
+/* Thread-local message for the last non-OK status returned on this thread. */
+const char *nbody_last_error(void);
+
+/* Release the library's internal workspaces on the current device.
+ * Synchronizes the device. */
+int nbody_release(void);
+
+/* Synchronize `stream`, then report (and clear) any error a kernel recorded
+ * since the last check: NBODY_ETIMEOUT for a bounded wait that ran out,
+ * NBODY_EINVAL for a work item that failed its bounds check. */
+int nbody_check(nbody_stream_t stream);
+
+/* Kernel timers. While enabled, every all-pairs kernel launch made outside
+ * stream capture is bracketed by two CUDA events recorded on its own stream.
+ * nbody_timing_read synchronizes those events and returns, for `which`
+ * (0 = force kernels, 1 = VJP kernels), the number of timed launches and their
+ * summed device time in milliseconds since the previous read, then resets. */
+int nbody_timing_enable(int32_t on);
+int nbody_timing_read(int32_t which, int64_t *launches, double *total_ms);
+
+/* ---------------------------------------------------------------------------
+ * S0 pack (Sec. 2 "stream coordinates"; Appendix jpos/jmass float4).
+ * Converts caller SoA data in double precision into the float4 streams above.
+ *   x, y, z, m : n doubles each (device).      pos_m : n float4 (device, out)
+ *   nbody_pack_ljc additionally takes q, sigma, eps (per particle, doubles),
+ *   type (int32) and kq = k_e / eps_r, and writes prm (n float4).
+ * --------------------------------------------------------------------------- */
+int nbody_pack_grav(const double *x, const double *y, const double *z, const double *m,
+                    void *pos_m, int64_t n, nbody_stream_t stream);
+int nbody_pack_ljc(const double *q, const double *sigma, const double *eps,
+                   const int32_t *type, double kq, void *prm, int64_t n,
+                   nbody_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * nbody_forces -- one force evaluation (Sec. 2 "forces = kforce(coordinates)",
+ * Eq. 1 / Table 1).
+ *   pos_m  : n float4 (x, y, z, m)                                   in
+ *   prm    : n float4 LJC parameters (NULL for gravity)              in
+ *   acc    : n float4 (ax, ay, az, phi); phi only with COMPUTE_POT   out
+ *   acc_lo : n float4 low parts of the compensated sums, or NULL     out
+ *            (acc + acc_lo is the sum to about twice FP32 precision)
+ * Gravity: a_i = G sum_{j!=i} m_j (x_j - x_i) / (|x_j - x_i|^2 + eps2)^{3/2}.
+ * LJC    : a_i = F_i / m_i with the 12-6 LJ + Coulomb force of Table 1.
+ * Pointers may be device pointers or, all of them together, host pointers; in
+ * the host case the library stages through device memory and the call
+ * synchronizes `stream` before returning. n == 0 is a no-op. n <= 2^31 - 1.
+ * --------------------------------------------------------------------------- */
+int nbody_forces(const void *pos_m, const void *prm, void *acc, void *acc_lo, int64_t n,
+                 const nbody_params *params, nbody_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * nbody_step -- nsteps kick-drift-kick leapfrog steps of size dt (the update
+ * step of Sec. 1), each consuming one all-pairs force evaluation:
+ *   v += dt/2 a(x);  x += dt v;  v += dt/2 a(x)
+ *   pos_m : n float4, in/out; w (mass) is not modified
+ *   vel   : n float4, in/out (synchronized with pos_m on entry and exit)
+ *   acc   : n float4, in/out: on exit a(x) at the exit positions. On entry it
+ *           is read only when params->flags has NBODY_ACC_VALID.
+ *   prm   : LJC parameters or NULL.
+ *   report_every : 0 = no diagnostics; R > 0 = FP64 diagnostics at steps
+ *           0, R, 2R, ... <= nsteps, written as rows of 8 doubles
+ *           (K, U, Px, Py, Pz, Lx, Ly, Lz) into diag (host or device,
+ *           floor(nsteps / R) + 1 rows). The FP64 reductions are the only
+ *           double-precision arithmetic on the GPU.
+ *   trace : NULL, or (nsteps + 1) * n float4 receiving the positions x_0 ..
+ *           x_nsteps (used by reverse-mode recomputation).
+ * Host pointers are accepted as in nbody_forces (all of pos_m, vel, acc, prm
+ * on the host); then the call synchronizes. A host diag also synchronizes.
+ * --------------------------------------------------------------------------- */
+int nbody_step(void *pos_m, void *vel, void *acc, const void *prm, int64_t n, float dt,
+               int32_t nsteps, int32_t report_every, double *diag, void *trace,
+               const nbody_params *params, nbody_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched ensembles (Sec. 3.4 "optimization for small systems"): many
+ * independent systems of uneven size in one persistent launch per step.
+ * System k occupies particles [offset, offset + n) of the shared arrays.
+ * --------------------------------------------------------------------------- */
+typedef struct {
+    int64_t offset; /* first particle; a multiple of 4                        */
+    int32_t n;      /* particles in the system, >= 1                          */
+    int32_t law;    /* NBODY_LAW_*                                            */
+    float G;        /* gravity constant (gravity systems)                     */
+    float eps2;     /* squared softening (gravity systems)                    */
+    float dt;       /* leapfrog step of this system                           */
+    int32_t reserved;
+} nbody_system;
+
+typedef struct nbody_batch_plan nbody_batch_plan;
+
+/* Build the work list (longest items first) for a host table of systems.
+ * flags: NBODY_PRECISE_RSQRT / NBODY_NO_COMPENSATION. tile = -1 picks the
+ * tuned configuration. Allocates device memory; no stream work. */
+int nbody_batch_plan_create(const nbody_system *systems, int32_t nsys, uint32_t flags,
+                            int32_t tile, nbody_batch_plan **plan);
+int nbody_batch_plan_destroy(nbody_batch_plan *plan);
+/* Total particles covered by the plan (max offset + n). */
+int64_t nbody_batch_plan_particles(const nbody_batch_plan *plan);
+
+/* nsteps == 0: forces only (acc = a(x) of every system). nsteps > 0: nsteps
+ * leapfrog steps per system (acc must hold a(x) on entry when ACC_VALID is set
+ * in `flags`; otherwise it is computed first). With use_graph != 0 the whole
+ * nsteps loop is captured once into a CUDA graph per (plan, nsteps, pointers)
+ * and replayed. Device pointers only. */
+int nbody_batch_run(nbody_batch_plan *plan, void *pos_m, void *vel, void *acc,
+                    const void *prm, int32_t nsteps, uint32_t flags, int32_t use_graph,
+                    nbody_stream_t stream);
+
+/* One-shot convenience: plan, run, destroy (synchronizes the stream). The
+ * system table is on the host. */
+int nbody_forces_batched(const nbody_system *systems, int32_t nsys, void *pos_m, void *vel,
+                         void *acc, const void *prm, int32_t nsteps, uint32_t flags,
+                         nbody_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * nbody_adjoint -- one vector-Jacobian product of the force law (derived from
+ * Eq. 1 and Table 1 by differentiation; the paper has no adjoint):
+ *   grad_x[k] (+)= alpha * sum_i (d a_i / d x_k)^T lam_i
+ *   grad_m[k] (+)= alpha * sum_i lam_i . d a_i / d m_k
+ *   grad_types (+)= alpha * (d/d sigma_t, d/d eps_t of sum_i lam_i . a_i),
+ *                  2 * ntypes doubles (LJC only; NULL to skip)
+ *   pos_m, prm : as in nbody_forces; lam : n float4 (w ignored)
+ *   grad_x : n float4 (w ignored on input, 0 on output); grad_m : n floats
+ * With NBODY_ACCUMULATE the outputs are added to, else overwritten.
+ * Device pointers only.
+ * --------------------------------------------------------------------------- */
+int nbody_adjoint(const void *pos_m, const void *prm, const void *lam, void *grad_x,
+                  float *grad_m, double *grad_types, int32_t ntypes, float alpha, int64_t n,
+                  const nbody_params *params, nbody_stream_t stream);
+
+/* nbody_adjoint_leapfrog -- reverse of `k` leapfrog steps n = k-1 .. 0 over
+ * stored positions xs[0..k-1] (k * n float4, as written by nbody_step's
+ * trace), each reverse step being
+ *   lam_v += dt * lam_x;   lam_x += w_n * J(x_n)^T lam_v
+ * with w_n = dt, except w_0 = dt/2 when `first` is nonzero (the chunk starts
+ * at step 0 of the trajectory). Mass and per-type gradients accumulate with
+ * the same weights into grad_m / grad_types (which are NOT cleared).
+ * lam_x, lam_v : n float4, in/out. Device pointers only.
+ * --------------------------------------------------------------------------- */
+int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k, float dt,
+                           int32_t first, void *lam_x, void *lam_v, float *grad_m,
+                           double *grad_types, int32_t ntypes, const nbody_params *params,
+                           nbody_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Tile configurations and tuning.
+ * --------------------------------------------------------------------------- */
+/* Number of compiled tile configurations for `law` (0 gravity, 1 LJC,
+ * 2 the mixed-law batched kernel), or a negative status. */
+int nbody_tile_count(int32_t law);
+/* Describe configuration `tile` of `law`: threads per CTA (consumer warps),
+ * i-particles per thread, j-lanes per warp, j-tile length. */
+int nbody_tile_info(int32_t law, int32_t tile, int32_t *threads, int32_t *i_per_thread,
+                    int32_t *j_lanes, int32_t *j_tile);
+/* Install the tuned (tile, jsplit) for (law, n-bucket); bucket = floor(log2 n).
+ * Used by params->tile == -1. */
+int nbody_set_tuned(int32_t law, int32_t log2n, int32_t tile, int32_t jsplit);
+/* Query the configuration a call with (law, n) and tile == -1 would use. */
+int nbody_get_config(int32_t law, int64_t n, int32_t *tile, int32_t *jsplit);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBODY_H */

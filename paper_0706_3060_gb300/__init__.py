@@ -1,0 +1,21 @@
+"""GB300-native (sm_103a) all-pairs N-body forces and leapfrog, after
+Elsen et al., "N-Body Simulations on GPUs" (arXiv 0706.3060).
+
+The numerical work runs in ``libnbody.so`` (hand-written CUDA kernels behind the
+C ABI of ``include/nbody.h``); this package only marshals torch tensors into
+that ABI. There is no CPU fallback: calls raise if the library is not built.
+"""
+from . import _lib
+from ._lib import (ACC_VALID, ACCUMULATE, COMPUTE_POT, LAW_GRAV, LAW_LJC, NO_COMPENSATION,
+                   PRECISE_RSQRT, NBodyError)
+from .api import (COULOMB_K, BatchPlan, adjoint, adjoint_leapfrog, forces, forces_batched,
+                  get_config, pack_grav, pack_ljc, params, release, set_tuned, step, sync_check,
+                  tile_count, tile_info, timing_enable, timing_read, version)
+
+__all__ = [
+    "ACC_VALID", "ACCUMULATE", "COMPUTE_POT", "LAW_GRAV", "LAW_LJC", "NO_COMPENSATION",
+    "PRECISE_RSQRT", "NBodyError", "COULOMB_K", "BatchPlan", "adjoint", "adjoint_leapfrog",
+    "forces", "forces_batched", "get_config", "pack_grav", "pack_ljc", "params", "release",
+    "set_tuned", "step", "sync_check", "tile_count", "tile_info", "timing_enable",
+    "timing_read", "version",
+]

@@ -1,0 +1,373 @@
+// api.cu -- C-ABI entry points for single systems: pack, forces, leapfrog steps,
+// tile queries and library housekeeping (declared in include/nbody.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "api_common.h"
+#include "aux_kernels.cuh"
+
+using namespace nbody;
+
+namespace nbody {
+
+int launch_finalize(const FinalizeArgs &f, cudaStream_t s, int *nblk_out) {
+  const int nblk = std::max(1, (f.n + kFinThreads - 1) / kFinThreads);
+  finalize_kernel<<<nblk, kFinThreads, 0, s>>>(f);
+  NB_CUDA(cudaGetLastError());
+  if (nblk_out) *nblk_out = nblk;
+  return NBODY_OK;
+}
+
+int launch_diag_reduce(const double *part, int nblk, double *out, cudaStream_t s) {
+  diag_reduce_kernel<<<1, kFinThreads, 0, s>>>(part, nblk, out);
+  NB_CUDA(cudaGetLastError());
+  return NBODY_OK;
+}
+
+int launch_kick_drift(float4 *pos, float4 *vel, const float4 *acc, int n, float dt,
+                      float4 *trace1, const int *sys_of, const void *sys, cudaStream_t s) {
+  if (n <= 0) return NBODY_OK;
+  kick_drift_kernel<<<(n + 255) / 256, 256, 0, s>>>(pos, vel, acc, n, dt, trace1, sys_of,
+                                                    static_cast<const SysInfo *>(sys));
+  NB_CUDA(cudaGetLastError());
+  return NBODY_OK;
+}
+
+}  // namespace nbody
+
+namespace {
+
+constexpr int kMaxN = 0x7fffffff;
+
+int check_params(const nbody_params *p, const void *prm) {
+  if (!p) return set_error_msg(NBODY_EINVAL, "params is NULL");
+  if (p->law != NBODY_LAW_GRAV && p->law != NBODY_LAW_LJC)
+    return set_error_msg(NBODY_EINVAL, "unknown law %d", p->law);
+  const uint32_t known = NBODY_COMPUTE_POT | NBODY_PRECISE_RSQRT | NBODY_NO_COMPENSATION |
+                         NBODY_ACC_VALID | NBODY_ACCUMULATE;
+  if (p->flags & ~known) return set_error_msg(NBODY_EINVAL, "unknown flag bits 0x%x", p->flags);
+  if (p->law == NBODY_LAW_LJC && !prm)
+    return set_error_msg(NBODY_EINVAL, "LJC law needs the prm array");
+  if (p->law == NBODY_LAW_GRAV && !(p->eps2 >= 0.0f))
+    return set_error_msg(NBODY_EINVAL, "eps2 must be >= 0");
+  if (p->law == NBODY_LAW_GRAV && !std::isfinite(p->G))
+    return set_error_msg(NBODY_EINVAL, "G must be finite");
+  int count = 0;
+  tiles_for(p->law, &count);
+  if (p->tile < -1 || p->tile >= count) return set_error_msg(NBODY_EINVAL, "bad tile %d", p->tile);
+  if (p->jsplit < 0) return set_error_msg(NBODY_EINVAL, "bad jsplit %d", p->jsplit);
+  return NBODY_OK;
+}
+
+int check_ptr(const void *p, const char *name, bool required = true) {
+  if (!p) return required ? set_error_msg(NBODY_EINVAL, "%s is NULL", name) : NBODY_OK;
+  if (!aligned16(p)) return set_error_msg(NBODY_EALIGN, "%s is not 16-byte aligned", name);
+  return NBODY_OK;
+}
+
+// Scratch layout for one single-system evaluation.
+struct Scratch {
+  float4 *part_hi;
+  float4 *part_lo;
+  double *diag_part;
+  double *diag_rows;
+};
+
+int get_scratch(cudaStream_t s, int n, int slices, int diag_rows, Scratch *out) {
+  const size_t part = round_up(size_t(slices) * size_t(n) * sizeof(float4), 256);
+  const int nblk = std::max(1, (n + kFinThreads - 1) / kFinThreads);
+  const size_t dpart = round_up(size_t(nblk) * kDiagFields * sizeof(double), 256);
+  const size_t drows = round_up(size_t(std::max(diag_rows, 1)) * kDiagFields * sizeof(double), 256);
+  void *base = nullptr;
+  NB_TRY(workspace(s, 2 * part + dpart + drows, &base));
+  char *b = static_cast<char *>(base);
+  out->part_hi = reinterpret_cast<float4 *>(b);
+  out->part_lo = reinterpret_cast<float4 *>(b + part);
+  out->diag_part = reinterpret_cast<double *>(b + 2 * part);
+  out->diag_rows = reinterpret_cast<double *>(b + 2 * part + dpart);
+  return NBODY_OK;
+}
+
+// One force evaluation into scratch partials, then one finalize launch.
+int eval_and_finalize(const float4 *pos, const float4 *prm, const nbody_params &p, int n,
+                      const Plan1 &plan, const Scratch &sc, int *err, bool pot,
+                      FinalizeArgs f, cudaStream_t s, int *nblk) {
+  NB_TRY(launch_forces(pos, prm, p.law, p.flags, p.eps2, n, plan, sc.part_hi, sc.part_lo, err,
+                       pot, s));
+  f.part_hi = sc.part_hi;
+  f.part_lo = sc.part_lo;
+  f.stride = n;
+  f.slices = plan.slices;
+  f.sys_of = nullptr;
+  f.sys = nullptr;
+  f.n = n;
+  f.law = p.law;
+  f.G = p.G;
+  f.diag_part = sc.diag_part;
+  return launch_finalize(f, s, nblk);
+}
+
+int forces_device(const float4 *pos, const float4 *prm, float4 *acc, float4 *acc_lo, int n,
+                  const nbody_params &p, int sms, cudaStream_t s) {
+  Plan1 plan{};
+  NB_TRY(plan_single(p.law, n, p.tile, p.jsplit, sms, &plan));
+  Scratch sc{};
+  NB_TRY(get_scratch(s, n, plan.slices, 0, &sc));
+  int *err = nullptr;
+  NB_TRY(error_word(&err));
+  FinalizeArgs f{};
+  f.pos = const_cast<float4 *>(pos);
+  f.acc = acc;
+  f.acc_lo = acc_lo;
+  f.mode = kFinWriteAcc;
+  return eval_and_finalize(pos, prm, p, n, plan, sc, err, (p.flags & NBODY_COMPUTE_POT) != 0, f,
+                           s, nullptr);
+}
+
+int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n, float dt,
+                int nsteps, int report_every, double *diag_dev, float4 *trace,
+                const nbody_params &p, int sms, cudaStream_t s) {
+  Plan1 plan{};
+  NB_TRY(plan_single(p.law, n, p.tile, p.jsplit, sms, &plan));
+  const int rows = report_every > 0 ? nsteps / report_every + 1 : 0;
+  Scratch sc{};
+  NB_TRY(get_scratch(s, n, plan.slices, rows, &sc));
+  int *err = nullptr;
+  NB_TRY(error_word(&err));
+  auto report = [&](int step) { return report_every > 0 && step % report_every == 0; };
+  const bool want_pot = (p.flags & NBODY_COMPUTE_POT) != 0;
+  if (trace) NB_CUDA(cudaMemcpyAsync(trace, pos, size_t(n) * sizeof(float4),
+                                     cudaMemcpyDeviceToDevice, s));
+  int row = 0;
+  FinalizeArgs f{};
+  f.pos = pos;
+  f.vel = vel;
+  f.acc = acc;
+  f.acc_lo = nullptr;
+  f.dt = dt;
+  // Step 0: a(x_0) from the caller or from one evaluation; then kick + drift.
+  if (!(p.flags & NBODY_ACC_VALID) || report(0)) {
+    int nblk = 0;
+    f.mode = kFinWriteAcc | (report(0) ? kFinDiag : 0) | (nsteps > 0 ? kFinKickDrift : 0);
+    f.trace_next = (trace && nsteps > 0) ? trace + size_t(n) : nullptr;
+    NB_TRY(eval_and_finalize(pos, prm, p, n, plan, sc, err,
+                             report(0) || (nsteps == 0 && want_pot), f, s, &nblk));
+    if (report(0)) NB_TRY(launch_diag_reduce(sc.diag_part, nblk, sc.diag_rows + kDiagFields * row++, s));
+  } else if (nsteps > 0) {
+    NB_TRY(launch_kick_drift(pos, vel, acc, n, dt, trace ? trace + size_t(n) : nullptr, nullptr,
+                             nullptr, s));
+  }
+  for (int st = 1; st <= nsteps; ++st) {
+    const bool rep = report(st);
+    const bool last = (st == nsteps);
+    int nblk = 0;
+    f.mode = kFinWriteAcc | kFinKickSync | (rep ? kFinDiag : 0) | (last ? 0 : kFinKickDrift);
+    f.trace_next = (trace && !last) ? trace + size_t(st + 1) * size_t(n) : nullptr;
+    NB_TRY(eval_and_finalize(pos, prm, p, n, plan, sc, err, rep || (last && want_pot), f, s,
+                             &nblk));
+    if (rep) NB_TRY(launch_diag_reduce(sc.diag_part, nblk, sc.diag_rows + kDiagFields * row++, s));
+  }
+  if (rows > 0)
+    NB_CUDA(cudaMemcpyAsync(diag_dev, sc.diag_rows, size_t(rows) * kDiagFields * sizeof(double),
+                            cudaMemcpyDefault, s));
+  return NBODY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nbody_version(void) { return 10000; }
+
+const char *nbody_last_error(void) { return last_error_text(); }
+
+int nbody_release(void) {
+  clear_error();
+  release_all();
+  return NBODY_OK;
+}
+
+int nbody_check(nbody_stream_t stream) {
+  clear_error();
+  int dev = 0, sms = 0;
+  NB_TRY(check_device(&dev, &sms));
+  return sync_and_check(reinterpret_cast<cudaStream_t>(stream));
+}
+
+int nbody_pack_grav(const double *x, const double *y, const double *z, const double *m,
+                    void *pos_m, int64_t n, nbody_stream_t stream) {
+  clear_error();
+  if (n < 0 || n > kMaxN) return set_error_msg(NBODY_EINVAL, "n out of range: %lld", (long long)n);
+  if (n == 0) return NBODY_OK;
+  if (!x || !y || !z || !m) return set_error_msg(NBODY_EINVAL, "x, y, z and m must be non-NULL");
+  NB_TRY(check_ptr(pos_m, "pos_m"));
+  NB_TRY(check_device(nullptr, nullptr));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  pack_grav_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(x, y, z, m,
+                                                             static_cast<float4 *>(pos_m), n);
+  NB_CUDA(cudaGetLastError());
+  return NBODY_OK;
+}
+
+int nbody_pack_ljc(const double *q, const double *sigma, const double *eps, const int32_t *type,
+                   double kq, void *prm, int64_t n, nbody_stream_t stream) {
+  clear_error();
+  if (n < 0 || n > kMaxN) return set_error_msg(NBODY_EINVAL, "n out of range: %lld", (long long)n);
+  if (n == 0) return NBODY_OK;
+  if (!q || !sigma || !eps || !type)
+    return set_error_msg(NBODY_EINVAL, "q, sigma, eps and type must be non-NULL");
+  if (!(kq >= 0.0) || !std::isfinite(kq)) return set_error_msg(NBODY_EINVAL, "kq must be >= 0");
+  NB_TRY(check_ptr(prm, "prm"));
+  NB_TRY(check_device(nullptr, nullptr));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  pack_ljc_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(q, sigma, eps, type, std::sqrt(kq),
+                                                            static_cast<float4 *>(prm), n);
+  NB_CUDA(cudaGetLastError());
+  return NBODY_OK;
+}
+
+int nbody_forces(const void *pos_m, const void *prm, void *acc, void *acc_lo, int64_t n,
+                 const nbody_params *params, nbody_stream_t stream) {
+  clear_error();
+  if (n < 0 || n > kMaxN) return set_error_msg(NBODY_EINVAL, "n out of range: %lld", (long long)n);
+  if (!params) return set_error_msg(NBODY_EINVAL, "params is NULL");
+  if (n == 0) return NBODY_OK;
+  NB_TRY(check_params(params, prm));
+  NB_TRY(check_ptr(pos_m, "pos_m"));
+  NB_TRY(check_ptr(acc, "acc"));
+  NB_TRY(check_ptr(prm, "prm", false));
+  NB_TRY(check_ptr(acc_lo, "acc_lo", false));
+  int dev = 0, sms = 0;
+  NB_TRY(check_device(&dev, &sms));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const nbody_params p = *params;
+  const int host = is_host_pointer(pos_m);
+  if (is_host_pointer(acc) != host || (prm && is_host_pointer(prm) != host) ||
+      (acc_lo && is_host_pointer(acc_lo) != host))
+    return set_error_msg(NBODY_EINVAL, "pointers must be all host or all device");
+  const size_t bytes = size_t(n) * sizeof(float4);
+  if (!host)
+    return forces_device(static_cast<const float4 *>(pos_m), static_cast<const float4 *>(prm),
+                         static_cast<float4 *>(acc), static_cast<float4 *>(acc_lo), int(n), p,
+                         sms, s);
+  void *st = nullptr;
+  NB_TRY(staging(s, 4 * bytes, &st));
+  float4 *d_pos = static_cast<float4 *>(st);
+  float4 *d_prm = d_pos + n;
+  float4 *d_acc = d_prm + n;
+  float4 *d_lo = d_acc + n;
+  NB_CUDA(cudaMemcpyAsync(d_pos, pos_m, bytes, cudaMemcpyHostToDevice, s));
+  if (prm) NB_CUDA(cudaMemcpyAsync(d_prm, prm, bytes, cudaMemcpyHostToDevice, s));
+  NB_TRY(forces_device(d_pos, prm ? d_prm : nullptr, d_acc, acc_lo ? d_lo : nullptr, int(n), p,
+                       sms, s));
+  NB_CUDA(cudaMemcpyAsync(acc, d_acc, bytes, cudaMemcpyDeviceToHost, s));
+  if (acc_lo) NB_CUDA(cudaMemcpyAsync(acc_lo, d_lo, bytes, cudaMemcpyDeviceToHost, s));
+  return sync_and_check(s);
+}
+
+int nbody_step(void *pos_m, void *vel, void *acc, const void *prm, int64_t n, float dt,
+               int32_t nsteps, int32_t report_every, double *diag, void *trace,
+               const nbody_params *params, nbody_stream_t stream) {
+  clear_error();
+  if (n < 0 || n > kMaxN) return set_error_msg(NBODY_EINVAL, "n out of range: %lld", (long long)n);
+  if (nsteps < 0) return set_error_msg(NBODY_EINVAL, "nsteps must be >= 0");
+  if (report_every < 0) return set_error_msg(NBODY_EINVAL, "report_every must be >= 0");
+  if (!std::isfinite(dt)) return set_error_msg(NBODY_EINVAL, "dt must be finite");
+  if (report_every > 0 && !diag) return set_error_msg(NBODY_EINVAL, "diag is NULL");
+  if (!params) return set_error_msg(NBODY_EINVAL, "params is NULL");
+  if (n == 0) return NBODY_OK;
+  NB_TRY(check_params(params, prm));
+  NB_TRY(check_ptr(pos_m, "pos_m"));
+  NB_TRY(check_ptr(vel, "vel"));
+  NB_TRY(check_ptr(acc, "acc"));
+  NB_TRY(check_ptr(prm, "prm", false));
+  NB_TRY(check_ptr(trace, "trace", false));
+  int dev = 0, sms = 0;
+  NB_TRY(check_device(&dev, &sms));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const nbody_params p = *params;
+  const int host = is_host_pointer(pos_m);
+  if (is_host_pointer(vel) != host || is_host_pointer(acc) != host ||
+      (prm && is_host_pointer(prm) != host))
+    return set_error_msg(NBODY_EINVAL, "pos_m, vel, acc and prm must be all host or all device");
+  if (trace && is_host_pointer(trace))
+    return set_error_msg(NBODY_EINVAL, "trace must be device memory");
+  const int rows = report_every > 0 ? nsteps / report_every + 1 : 0;
+  const bool host_diag = rows > 0 && is_host_pointer(diag);
+  const size_t bytes = size_t(n) * sizeof(float4);
+  if (!host) {
+    NB_TRY(step_device(static_cast<float4 *>(pos_m), static_cast<float4 *>(vel),
+                       static_cast<float4 *>(acc), static_cast<const float4 *>(prm), int(n), dt,
+                       nsteps, report_every, diag, static_cast<float4 *>(trace), p, sms, s));
+    return host_diag ? sync_and_check(s) : NBODY_OK;
+  }
+  void *st = nullptr;
+  NB_TRY(staging(s, 4 * bytes, &st));
+  float4 *d_pos = static_cast<float4 *>(st);
+  float4 *d_vel = d_pos + n;
+  float4 *d_acc = d_vel + n;
+  float4 *d_prm = d_acc + n;
+  NB_CUDA(cudaMemcpyAsync(d_pos, pos_m, bytes, cudaMemcpyHostToDevice, s));
+  NB_CUDA(cudaMemcpyAsync(d_vel, vel, bytes, cudaMemcpyHostToDevice, s));
+  if (p.flags & NBODY_ACC_VALID) NB_CUDA(cudaMemcpyAsync(d_acc, acc, bytes, cudaMemcpyHostToDevice, s));
+  if (prm) NB_CUDA(cudaMemcpyAsync(d_prm, prm, bytes, cudaMemcpyHostToDevice, s));
+  NB_TRY(step_device(d_pos, d_vel, d_acc, prm ? d_prm : nullptr, int(n), dt, nsteps,
+                     report_every, diag, static_cast<float4 *>(trace), p, sms, s));
+  NB_CUDA(cudaMemcpyAsync(pos_m, d_pos, bytes, cudaMemcpyDeviceToHost, s));
+  NB_CUDA(cudaMemcpyAsync(vel, d_vel, bytes, cudaMemcpyDeviceToHost, s));
+  NB_CUDA(cudaMemcpyAsync(acc, d_acc, bytes, cudaMemcpyDeviceToHost, s));
+  return sync_and_check(s);
+}
+
+int nbody_timing_enable(int32_t on) {
+  clear_error();
+  return timing_enable(on);
+}
+
+int nbody_timing_read(int32_t which, int64_t *launches, double *total_ms) {
+  clear_error();
+  return timing_read(which, launches, total_ms);
+}
+
+int nbody_tile_count(int32_t law) {
+  clear_error();
+  if (law < 0 || law > 2) return set_error_msg(-NBODY_EINVAL, "bad law %d", law);
+  int count = 0;
+  tiles_for(law, &count);
+  return count;
+}
+
+int nbody_tile_info(int32_t law, int32_t tile, int32_t *threads, int32_t *i_per_thread,
+                    int32_t *j_lanes, int32_t *j_tile) {
+  clear_error();
+  if (law < 0 || law > 2) return set_error_msg(NBODY_EINVAL, "bad law %d", law);
+  int count = 0;
+  const TileDesc *t = tiles_for(law, &count);
+  if (tile < 0 || tile >= count) return set_error_msg(NBODY_EINVAL, "bad tile %d", tile);
+  if (threads) *threads = t[tile].nt;
+  if (i_per_thread) *i_per_thread = t[tile].i;
+  if (j_lanes) *j_lanes = t[tile].sw;
+  if (j_tile) *j_tile = t[tile].jt;
+  return NBODY_OK;
+}
+
+int nbody_set_tuned(int32_t law, int32_t log2n, int32_t tile, int32_t jsplit) {
+  clear_error();
+  return set_tuned(law, log2n, tile, jsplit);
+}
+
+int nbody_get_config(int32_t law, int64_t n, int32_t *tile, int32_t *jsplit) {
+  clear_error();
+  if (law < 0 || law > 2) return set_error_msg(NBODY_EINVAL, "bad law %d", law);
+  if (!tile || !jsplit) return set_error_msg(NBODY_EINVAL, "NULL output");
+  int t = 0, j = 0;
+  get_config(law, n, &t, &j);
+  *tile = t;
+  *jsplit = j;
+  return NBODY_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,268 @@
+// api_adjoint.cu -- C-ABI entry points of the reverse-mode path: one force VJP
+// (nbody_adjoint) and the reverse leapfrog sweep over stored positions
+// (nbody_adjoint_leapfrog). Kernels in vjp_kernel.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <initializer_list>
+#include <cmath>
+
+#include "api_common.h"
+#include "vjp_kernel.cuh"
+
+using namespace nbody;
+
+namespace {
+
+struct VjpDesc {
+  int tile_i;
+  int jt;
+  int threads;
+  size_t smem;
+  cudaError_t (*launch)(const VjpArgs &, int, cudaStream_t);
+  int (*occupancy)();
+};
+
+template <int LAW, int NT, int I, int SW, int JT>
+struct VjpImpl {
+  using T = VjpTile<LAW, NT, I, SW, JT>;
+  static cudaError_t launch(const VjpArgs &a, int grid, cudaStream_t s) {
+    auto k = vjp_kernel<LAW, NT, I, SW, JT>;
+    if (T::kSmemBytes > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)T::kSmemBytes);
+      if (e != cudaSuccess) return e;
+    }
+    k<<<grid, T::kThreads, T::kSmemBytes, s>>>(a);
+    return cudaGetLastError();
+  }
+  static int occupancy() {
+    int nb = 0;
+    auto k = vjp_kernel<LAW, NT, I, SW, JT>;
+    if (T::kSmemBytes > 48 * 1024)
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, T::kThreads, T::kSmemBytes) !=
+        cudaSuccess)
+      return 1;
+    return std::max(nb, 1);
+  }
+  static VjpDesc desc() {
+    return VjpDesc{T::kTileI, JT, T::kThreads, T::kSmemBytes, &launch, &occupancy};
+  }
+};
+
+const VjpDesc &vjp_tile(int law, int64_t n) {
+  static const VjpDesc grav_big = VjpImpl<kLawGrav, 256, 2, 1, 256>::desc();
+  static const VjpDesc grav_small = VjpImpl<kLawGrav, 128, 2, 4, 256>::desc();
+  static const VjpDesc ljc_big = VjpImpl<kLawLJC, 256, 2, 1, 256>::desc();
+  static const VjpDesc ljc_small = VjpImpl<kLawLJC, 128, 1, 4, 256>::desc();
+  if (law == NBODY_LAW_GRAV) return n >= 8192 ? grav_big : grav_small;
+  return n >= 8192 ? ljc_big : ljc_small;
+}
+
+struct VjpScratch {
+  float4 *part_hi, *part_lo, *u;
+  double *type_part;
+  int slices, slice_len, grid, nblk;
+  long long bstride;
+  const VjpDesc *d;
+};
+
+int vjp_prepare(int law, int n, int sms, cudaStream_t s, VjpScratch *sc) {
+  const VjpDesc &d = vjp_tile(law, n);
+  const int n_it = (n + d.tile_i - 1) / d.tile_i;
+  const int cap = sms * d.occupancy();
+  const int max_s = (n + d.jt - 1) / d.jt;
+  int S = 1;
+  double best = -1.0;
+  for (int k = 1; k <= 64 && k <= max_s; ++k) {
+    const int len = int(round_up(size_t((n + k - 1) / k), size_t(d.jt)));
+    const int kk = (n + len - 1) / len;
+    const double waves = double(n_it) * kk / cap;
+    const double score = waves / std::ceil(waves) - 0.002 * kk;
+    if (score > best + 1e-12) {
+      best = score;
+      S = kk;
+    }
+  }
+  const int len = int(round_up(size_t((n + S - 1) / S), size_t(d.jt)));
+  S = (n + len - 1) / len;
+  const int blocks = law == NBODY_LAW_LJC ? 2 : 1;
+  const size_t part = round_up(size_t(blocks) * S * size_t(n) * sizeof(float4), 256);
+  const size_t ubytes = round_up(size_t(n) * sizeof(float4), 256);
+  const int nblk = (n + 255) / 256;
+  const size_t tbytes = round_up(size_t(nblk) * 8 * sizeof(double), 256);
+  void *base = nullptr;
+  NB_TRY(workspace(s, 2 * part + ubytes + tbytes, &base));
+  char *b = static_cast<char *>(base);
+  sc->part_hi = reinterpret_cast<float4 *>(b);
+  sc->part_lo = reinterpret_cast<float4 *>(b + part);
+  sc->u = reinterpret_cast<float4 *>(b + 2 * part);
+  sc->type_part = reinterpret_cast<double *>(b + 2 * part + ubytes);
+  sc->slices = S;
+  sc->slice_len = len;
+  sc->grid = n_it * S;
+  sc->nblk = nblk;
+  sc->bstride = (long long)S * n;
+  sc->d = &d;
+  return NBODY_OK;
+}
+
+// One VJP: all-pairs kernel + finalize (+ type reduction).
+int vjp_once(const float4 *pos, const float4 *prm, const float4 *lam, float4 *grad_x,
+             float *grad_m, double *grad_types, int ntypes, float alpha, int accumulate, int n,
+             const nbody_params &p, const VjpScratch &sc, float4 *lam_v, float dt_next,
+             cudaStream_t s) {
+  int *err = nullptr;
+  NB_TRY(error_word(&err));
+  const float4 *src = lam;
+  if (p.law == NBODY_LAW_LJC) {
+    lam_over_m_kernel<<<(n + 255) / 256, 256, 0, s>>>(lam, pos, sc.u, n);
+    NB_CUDA(cudaGetLastError());
+    src = sc.u;
+  }
+  VjpArgs a{};
+  a.pos = pos;
+  a.lam = src;
+  a.prm = prm;
+  a.part_hi = sc.part_hi;
+  a.part_lo = sc.part_lo;
+  a.stride = n;
+  a.bstride = sc.bstride;
+  a.err = err;
+  a.n = n;
+  a.slices = sc.slices;
+  a.slice_len = sc.slice_len;
+  a.eps2 = p.eps2;
+  a.comp = (p.flags & NBODY_NO_COMPENSATION) ? 0 : 1;
+  const TimerMark tm = timer_begin(1, s);
+  cudaError_t e = sc.d->launch(a, sc.grid, s);
+  timer_end(tm, s);
+  if (e != cudaSuccess)
+    return set_error_msg(NBODY_ECUDA, "VJP kernel launch failed: %s", cudaGetErrorString(e));
+  VjpFinalizeArgs f{};
+  f.part_hi = sc.part_hi;
+  f.part_lo = sc.part_lo;
+  f.stride = n;
+  f.bstride = sc.bstride;
+  f.slices = sc.slices;
+  f.n = n;
+  f.law = p.law;
+  f.G = p.G;
+  f.alpha = alpha;
+  f.pos = pos;
+  f.prm = prm;
+  f.lam = src;
+  f.grad_x = grad_x;
+  f.grad_m = grad_m;
+  f.accumulate = accumulate;
+  const bool types = grad_types && p.law == NBODY_LAW_LJC;
+  f.type_part = types ? sc.type_part : nullptr;
+  f.lam_v = lam_v;
+  f.dt_next = dt_next;
+  vjp_finalize_kernel<<<sc.nblk, 256, 0, s>>>(f);
+  NB_CUDA(cudaGetLastError());
+  if (types) {
+    type_reduce_kernel<<<1, 32, 0, s>>>(sc.type_part, sc.nblk, ntypes, grad_types);
+    NB_CUDA(cudaGetLastError());
+  }
+  return NBODY_OK;
+}
+
+int check_common(const nbody_params *p, const void *pos, const void *prm, int64_t n,
+                 int ntypes, const double *grad_types) {
+  if (!p) return set_error_msg(NBODY_EINVAL, "params is NULL");
+  if (p->law != NBODY_LAW_GRAV && p->law != NBODY_LAW_LJC)
+    return set_error_msg(NBODY_EINVAL, "unknown law %d", p->law);
+  if (n < 0 || n > 0x7fffffffLL) return set_error_msg(NBODY_EINVAL, "n out of range");
+  if (!pos) return set_error_msg(NBODY_EINVAL, "pos_m is NULL");
+  if (p->law == NBODY_LAW_LJC && !prm) return set_error_msg(NBODY_EINVAL, "LJC needs prm");
+  if (grad_types && (ntypes < 1 || ntypes > 4))
+    return set_error_msg(NBODY_EUNSUPPORTED, "per-type gradients support 1..4 types");
+  if (!(p->eps2 >= 0.0f)) return set_error_msg(NBODY_EINVAL, "eps2 must be >= 0");
+  return NBODY_OK;
+}
+
+int check_dev(const void *q, const char *name, bool required) {
+  if (!q) return required ? set_error_msg(NBODY_EINVAL, "%s is NULL", name) : NBODY_OK;
+  if (!aligned16(q)) return set_error_msg(NBODY_EALIGN, "%s is not 16-byte aligned", name);
+  return NBODY_OK;
+}
+
+int check_dev_ptrs(std::initializer_list<const void *> ptrs) {
+  for (const void *q : ptrs)
+    if (q && is_host_pointer(q)) return set_error_msg(NBODY_EINVAL, "device pointers only");
+  return NBODY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nbody_adjoint(const void *pos_m, const void *prm, const void *lam, void *grad_x,
+                  float *grad_m, double *grad_types, int32_t ntypes, float alpha, int64_t n,
+                  const nbody_params *params, nbody_stream_t stream) {
+  clear_error();
+  NB_TRY(check_common(params, pos_m, prm, n, ntypes, grad_types));
+  NB_TRY(check_dev(pos_m, "pos_m", true));
+  NB_TRY(check_dev(lam, "lam", true));
+  NB_TRY(check_dev(grad_x, "grad_x", true));
+  NB_TRY(check_dev(prm, "prm", false));
+  if (grad_m && (reinterpret_cast<uintptr_t>(grad_m) & 3u))
+    return set_error_msg(NBODY_EALIGN, "grad_m is not 4-byte aligned");
+  if (!std::isfinite(alpha)) return set_error_msg(NBODY_EINVAL, "alpha must be finite");
+  if (n == 0) return NBODY_OK;
+  int dev = 0, sms = 0;
+  NB_TRY(check_device(&dev, &sms));
+  NB_TRY(check_dev_ptrs({pos_m, prm, lam, grad_x, grad_m, grad_types}));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const nbody_params p = *params;
+  VjpScratch sc{};
+  NB_TRY(vjp_prepare(p.law, int(n), sms, s, &sc));
+  const int acc = (p.flags & NBODY_ACCUMULATE) ? 1 : 0;
+  if (grad_types && !acc && p.law == NBODY_LAW_LJC) {
+    zero_doubles_kernel<<<1, 32, 0, s>>>(grad_types, 2 * ntypes);
+    NB_CUDA(cudaGetLastError());
+  }
+  return vjp_once(static_cast<const float4 *>(pos_m), static_cast<const float4 *>(prm),
+                  static_cast<const float4 *>(lam), static_cast<float4 *>(grad_x), grad_m,
+                  grad_types, ntypes, alpha, acc, int(n), p, sc, nullptr, 0.0f, s);
+}
+
+int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k, float dt,
+                           int32_t first, void *lam_x, void *lam_v, float *grad_m,
+                           double *grad_types, int32_t ntypes, const nbody_params *params,
+                           nbody_stream_t stream) {
+  clear_error();
+  NB_TRY(check_common(params, xs, prm, n, ntypes, grad_types));
+  if (k < 0) return set_error_msg(NBODY_EINVAL, "k must be >= 0");
+  if (!std::isfinite(dt)) return set_error_msg(NBODY_EINVAL, "dt must be finite");
+  NB_TRY(check_dev(xs, "xs", true));
+  NB_TRY(check_dev(lam_x, "lam_x", true));
+  NB_TRY(check_dev(lam_v, "lam_v", true));
+  NB_TRY(check_dev(prm, "prm", false));
+  if (n == 0 || k == 0) return NBODY_OK;
+  int dev = 0, sms = 0;
+  NB_TRY(check_device(&dev, &sms));
+  NB_TRY(check_dev_ptrs({xs, prm, lam_x, lam_v, grad_m, grad_types}));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const nbody_params p = *params;
+  VjpScratch sc{};
+  NB_TRY(vjp_prepare(p.law, int(n), sms, s, &sc));
+  float4 *lx = static_cast<float4 *>(lam_x);
+  float4 *lv = static_cast<float4 *>(lam_v);
+  const float4 *X = static_cast<const float4 *>(xs);
+  const float4 *q = static_cast<const float4 *>(prm);
+  // First reverse drift of the chunk: lam_v += dt lam_x.
+  axpy4_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(dt, lx, lv, int(n));
+  NB_CUDA(cudaGetLastError());
+  for (int st = k - 1; st >= 0; --st) {
+    const float w = (st == 0 && first) ? 0.5f * dt : dt;
+    // lam_x += w J(x_st)^T lam_v, then (except after the last) lam_v += dt lam_x.
+    NB_TRY(vjp_once(X + size_t(st) * size_t(n), q, lv, lx, grad_m, grad_types, ntypes, w, 1,
+                    int(n), p, sc, st > 0 ? lv : nullptr, dt, s));
+  }
+  return NBODY_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,378 @@
+// api_common.cu -- host helpers behind the C ABI (see api_common.h).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <map>
+#include <utility>
+#include <vector>
+
+#include "api_common.h"
+
+namespace nbody {
+
+namespace {
+thread_local std::string t_err;
+
+struct Arena {
+  void *ptr = nullptr;
+  size_t cap = 0;
+};
+
+std::mutex g_mu;
+std::map<std::pair<int, cudaStream_t>, Arena> g_ws;
+std::map<std::pair<int, cudaStream_t>, Arena> g_stage;
+std::map<int, int *> g_err_word;
+std::map<int, int> g_checked;  // device -> sms
+
+struct Tuned {
+  int tile = -1;
+  int jsplit = 0;
+};
+Tuned g_tuned[3][64];
+
+int grow(std::map<std::pair<int, cudaStream_t>, Arena> &tab, cudaStream_t s, size_t bytes,
+         void **out) {
+  int dev = 0;
+  NB_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  Arena &a = tab[{dev, s}];
+  if (a.cap < bytes) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    NB_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return set_error_msg(NBODY_EINVAL,
+                           "workspace of %zu bytes needed during stream capture; run the "
+                           "same call once before capturing",
+                           bytes);
+    // The old buffer may still be in use by work queued on this stream: free it
+    // in stream order, then allocate the larger one.
+    if (a.ptr) NB_CUDA(cudaFreeAsync(a.ptr, s));
+    a.ptr = nullptr;
+    a.cap = 0;
+    size_t want = bytes + bytes / 4 + 4096;
+    cudaError_t e = cudaMallocAsync(&a.ptr, want, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      a.ptr = nullptr;
+      return set_error_msg(NBODY_ENOMEM, "workspace allocation of %zu bytes failed: %s", want,
+                           cudaGetErrorString(e));
+    }
+    a.cap = want;
+  }
+  *out = a.ptr;
+  return NBODY_OK;
+}
+}  // namespace
+
+int set_error_msg(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+void clear_error() { t_err.clear(); }
+
+const char *last_error_text() { return t_err.c_str(); }
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int check_device(int *device, int *sms) {
+  int dev = 0, count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0) {
+    cudaGetLastError();
+    return set_error_msg(NBODY_EUNSUPPORTED, "no CUDA device available (%s)",
+                         cudaGetErrorString(e));
+  }
+  NB_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_checked.find(dev);
+    if (it != g_checked.end()) {
+      if (device) *device = dev;
+      if (sms) *sms = it->second;
+      return NBODY_OK;
+    }
+  }
+  int major = 0, minor = 0, nsm = 0;
+  NB_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+  NB_CUDA(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+  NB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (major != 10 || minor != 3)
+    return set_error_msg(NBODY_EUNSUPPORTED,
+                         "this library is compiled for sm_103a only; device %d is sm_%d%d", dev,
+                         major, minor);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_checked[dev] = nsm;
+  if (device) *device = dev;
+  if (sms) *sms = nsm;
+  return NBODY_OK;
+}
+
+int is_host_pointer(const void *p) {
+  cudaPointerAttributes at{};
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 0 : 1;
+}
+
+int workspace(cudaStream_t s, size_t bytes, void **out) { return grow(g_ws, s, bytes, out); }
+int staging(cudaStream_t s, size_t bytes, void **out) { return grow(g_stage, s, bytes, out); }
+
+int error_word(int **out) {
+  int dev = 0;
+  NB_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_err_word.find(dev);
+  if (it == g_err_word.end()) {
+    int *p = nullptr;
+    NB_CUDA(cudaMalloc(&p, sizeof(int)));
+    NB_CUDA(cudaMemset(p, 0, sizeof(int)));
+    NB_CUDA(cudaDeviceSynchronize());
+    it = g_err_word.emplace(dev, p).first;
+  }
+  *out = it->second;
+  return NBODY_OK;
+}
+
+int sync_and_check(cudaStream_t s) {
+  NB_CUDA(cudaStreamSynchronize(s));
+  int *w = nullptr;
+  NB_TRY(error_word(&w));
+  int h = 0;
+  NB_CUDA(cudaMemcpy(&h, w, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h != 0) {
+    NB_CUDA(cudaMemset(w, 0, sizeof(int)));
+    if (h == kDevTimeout)
+      return set_error_msg(NBODY_ETIMEOUT, "a bounded device wait ran out (pipeline stalled)");
+    return set_error_msg(NBODY_EINVAL, "device reported error code %d (bad work item)", h);
+  }
+  return NBODY_OK;
+}
+
+void release_all() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaDeviceSynchronize();
+  for (auto *tab : {&g_ws, &g_stage}) {
+    for (auto &kv : *tab)
+      if (kv.second.ptr) cudaFree(kv.second.ptr);
+    tab->clear();
+  }
+  for (auto &kv : g_err_word) cudaFree(kv.second);
+  g_err_word.clear();
+}
+
+namespace {
+struct TimerState {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[2];
+};
+TimerState g_timer;
+
+cudaEvent_t take_event() {
+  if (!g_timer.pool.empty()) {
+    cudaEvent_t e = g_timer.pool.back();
+    g_timer.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+}  // namespace
+
+TimerMark timer_begin(int which, cudaStream_t s) {
+  TimerMark m;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_timer.on) return m;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return m;
+  }
+  m.start = take_event();
+  if (m.start && cudaEventRecord(m.start, s) == cudaSuccess) m.which = which;
+  return m;
+}
+
+void timer_end(const TimerMark &m, cudaStream_t s) {
+  if (m.which < 0) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaEvent_t stop = take_event();
+  if (!stop || cudaEventRecord(stop, s) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  g_timer.pending[m.which].push_back({m.start, stop});
+}
+
+int timing_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_timer.on = on != 0;
+  return NBODY_OK;
+}
+
+int timing_read(int which, int64_t *launches, double *total_ms) {
+  if (which < 0 || which > 1) return set_error_msg(NBODY_EINVAL, "bad timer %d", which);
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    evs.swap(g_timer.pending[which]);
+  }
+  double tot = 0.0;
+  int st = NBODY_OK;
+  for (auto &pr : evs) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(pr.second);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+    if (e != cudaSuccess && st == NBODY_OK)
+      st = set_error_msg(NBODY_ECUDA, "timer event: %s", cudaGetErrorString(e));
+    tot += ms;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto &pr : evs) {
+      g_timer.pool.push_back(pr.first);
+      g_timer.pool.push_back(pr.second);
+    }
+  }
+  if (launches) *launches = int64_t(evs.size());
+  if (total_ms) *total_ms = tot;
+  return st;
+}
+
+const TileDesc *tiles_for(int law, int *count) {
+  if (law == NBODY_LAW_GRAV) return grav_tiles(count);
+  if (law == NBODY_LAW_LJC) return ljc_tiles(count);
+  return mixed_tiles(count);
+}
+
+int set_tuned(int law, int log2n, int tile, int jsplit) {
+  if (law < 0 || law > 2 || log2n < 0 || log2n >= 64)
+    return set_error_msg(NBODY_EINVAL, "bad law %d or log2n %d", law, log2n);
+  int count = 0;
+  tiles_for(law, &count);
+  if (tile < -1 || tile >= count) return set_error_msg(NBODY_EINVAL, "bad tile %d", tile);
+  if (jsplit < 0) return set_error_msg(NBODY_EINVAL, "bad jsplit %d", jsplit);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_tuned[law][log2n].tile = tile;
+  g_tuned[law][log2n].jsplit = jsplit;
+  return NBODY_OK;
+}
+
+static int log2_floor(int64_t n) {
+  int b = 0;
+  while ((int64_t(1) << (b + 1)) <= n && b < 62) ++b;
+  return b;
+}
+
+// Default tile when nothing is tuned: big register blocks for large N, j-lanes
+// inside the warp for small N (where there are too few targets to fill the GPU).
+static int default_tile(int law, int64_t n) {
+  if (law == NBODY_LAW_GRAV) {
+    if (n >= 65536) return 0;
+    if (n >= 8192) return 3;
+    if (n >= 1024) return 4;
+    return 5;
+  }
+  if (n >= 65536) return 0;
+  if (n >= 16384) return 1;
+  if (n >= 1024) return 3;
+  return 4;
+}
+
+int get_config(int law, int64_t n, int *tile, int *jsplit) {
+  int t = -1, j = 0;
+  if (n > 0) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    const Tuned &tu = g_tuned[law][log2_floor(n)];
+    t = tu.tile;
+    j = tu.jsplit;
+  }
+  if (t < 0) t = default_tile(law, n);
+  *tile = t;
+  *jsplit = j;
+  return NBODY_OK;
+}
+
+int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out) {
+  int count = 0;
+  const TileDesc *tiles = tiles_for(law, &count);
+  int tj = 0;
+  if (tile < 0) get_config(law, n, &tile, &tj);
+  if (jsplit <= 0) jsplit = tj;
+  if (tile < 0 || tile >= count) return set_error_msg(NBODY_EINVAL, "bad tile %d", tile);
+  const TileDesc &d = tiles[tile];
+  const int n_it = int((n + d.tile_i - 1) / d.tile_i);
+  const int max_slices = int((n + d.jt - 1) / d.jt);
+  int S = jsplit;
+  if (S <= 0) {
+    // Pick the j-split whose item count fills whole waves of resident CTAs
+    // best; prefer fewer slices among equals (less partial-sum traffic).
+    const int cap = sms * d.occupancy();
+    double best = -1.0;
+    S = 1;
+    for (int s = 1; s <= 64 && s <= max_slices; ++s) {
+      const int len = int(round_up(size_t((n + s - 1) / s), size_t(d.jt)));
+      const int ss = int((n + len - 1) / len);
+      const double items = double(n_it) * ss;
+      const double waves = items / cap;
+      const double eff = waves / std::ceil(waves);
+      const double score = eff - 0.002 * ss;
+      if (score > best + 1e-12) {
+        best = score;
+        S = ss;
+      }
+    }
+  }
+  S = std::max(1, std::min(S, max_slices));
+  int len = int(round_up(size_t((n + S - 1) / S), size_t(d.jt)));
+  S = int((n + len - 1) / len);
+  out->tile = &d;
+  out->slices = S;
+  out->slice_len = len;
+  out->n_itiles = n_it;
+  out->grid = n_it * S;
+  return NBODY_OK;
+}
+
+int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
+                  int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, int *err, bool pot,
+                  cudaStream_t s) {
+  ForceArgs a{};
+  a.pos = pos;
+  a.prm = prm;
+  a.part_hi = part_hi;
+  a.part_lo = part_lo;
+  a.stride = n;
+  a.err = err;
+  a.n = n;
+  a.slices = p.slices;
+  a.slice_len = p.slice_len;
+  a.eps2 = eps2;
+  a.items = nullptr;
+  a.n_items = 0;
+  a.counter = nullptr;
+  a.comp = (flags & NBODY_NO_COMPENSATION) ? 0 : 1;
+  (void)law;
+  const TimerMark tm = timer_begin(0, s);
+  cudaError_t e = p.tile->launch(a, p.grid, pot, (flags & NBODY_PRECISE_RSQRT) != 0, s);
+  timer_end(tm, s);
+  if (e != cudaSuccess)
+    return set_error_msg(e == cudaErrorNoKernelImageForDevice ? NBODY_EUNSUPPORTED : NBODY_ECUDA,
+                         "force kernel launch failed: %s", cudaGetErrorString(e));
+  return NBODY_OK;
+}
+
+}  // namespace nbody

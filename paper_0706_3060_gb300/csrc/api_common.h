@@ -1,0 +1,97 @@
+// api_common.h -- host-side helpers shared by the C-ABI translation units:
+// error reporting, argument checks, per-(device, stream) workspaces, device
+// capability checks and tuned tile selection.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+#include <string>
+
+#include "nbody.h"
+#include "tiles.h"
+
+namespace nbody {
+
+int set_error_msg(int code, const char *fmt, ...);
+void clear_error();
+
+#define NB_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return ::nbody::set_error_msg(e_ == cudaErrorMemoryAllocation ? NBODY_ENOMEM      \
+                                                                    : NBODY_ECUDA,      \
+                                    "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                                    __FILE__, __LINE__);                                \
+  } while (0)
+
+#define NB_TRY(expr)             \
+  do {                           \
+    int s_ = (expr);             \
+    if (s_ != NBODY_OK) return s_; \
+  } while (0)
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Device readiness: current device is sm_103 (the only compiled target).
+// Also returns the SM count.
+int check_device(int *device, int *sms);
+
+// 1 if p is host memory (pageable or pinned), 0 if device/managed memory.
+int is_host_pointer(const void *p);
+
+// Scratch owned by the library, one arena per (device, stream). The pointer
+// stays valid until the next call on the same (device, stream) asks for more.
+int workspace(cudaStream_t s, size_t bytes, void **out);
+int staging(cudaStream_t s, size_t bytes, void **out);
+// Device error word of the current device (zeroed at creation).
+int error_word(int **out);
+// Synchronize `s`, then read and clear the error word.
+int sync_and_check(cudaStream_t s);
+
+// Tile tables.
+const TileDesc *tiles_for(int law, int *count);
+// Decide (tile, slices, slice_len) for a single-system evaluation.
+struct Plan1 {
+  const TileDesc *tile;
+  int slices;
+  int slice_len;
+  int n_itiles;
+  int grid;
+};
+int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out);
+
+// Launch: all-pairs partial sums into part_hi/lo (slices x n).
+int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
+                  int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, int *err, bool pot,
+                  cudaStream_t s);
+
+size_t round_up(size_t x, size_t a);
+
+int set_tuned(int law, int log2n, int tile, int jsplit);
+int get_config(int law, int64_t n, int *tile, int *jsplit);
+const char *last_error_text();
+void release_all();
+
+// Kernel timers (nbody_timing_*): bracket a launch with events when enabled.
+struct TimerMark {
+  cudaEvent_t start = nullptr;
+  int which = -1;
+};
+TimerMark timer_begin(int which, cudaStream_t s);
+void timer_end(const TimerMark &m, cudaStream_t s);
+int timing_enable(int on);
+int timing_read(int which, int64_t *launches, double *total_ms);
+
+// O(N) kernel launches (aux_kernels.cuh), used by several entry points.
+struct FinalizeArgs;
+int launch_finalize(const FinalizeArgs &f, cudaStream_t s, int *nblk_out);
+int launch_diag_reduce(const double *part, int nblk, double *out, cudaStream_t s);
+int launch_kick_drift(float4 *pos, float4 *vel, const float4 *acc, int n, float dt,
+                      float4 *trace1, const int *sys_of, const void *sys, cudaStream_t s);
+
+}  // namespace nbody

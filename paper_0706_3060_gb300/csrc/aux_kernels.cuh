@@ -1,0 +1,187 @@
+// aux_kernels.cuh -- O(N) kernels around the all-pairs force kernel:
+//   S0 pack (caller SoA doubles -> float4 streams),
+//   S4/S5 finalize (fixed-order compensated sum of the per-slice partials,
+//         law scaling, leapfrog kick/drift, position trace),
+//   S6 FP64 diagnostics (block partials, then one deterministic final sum).
+#pragma once
+
+#include <cstdint>
+
+#include "aux_types.h"
+#include "device_common.cuh"
+
+namespace nbody {
+
+// Sum of 8 doubles over the block in a fixed order; thread 0 gets the result.
+__device__ __forceinline__ void block_sum8(double v[kDiagFields], double *out) {
+  __shared__ double red[kFinThreads / 32][kDiagFields];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kDiagFields; ++k) {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    if (lane == 0) red[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < kDiagFields) {
+    double s = 0.0;
+    for (int w = 0; w < kFinThreads / 32; ++w) s += red[w][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArgs f) {
+  const int i = blockIdx.x * kFinThreads + threadIdx.x;
+  double dv[kDiagFields] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (i < f.n) {
+    int law = f.law, slices = f.slices;
+    float G = f.G, dt = f.dt;
+    bool live = true;
+    if (f.sys_of) {
+      const int s = f.sys_of[i];
+      if (s < 0) {
+        live = false;
+      } else {
+        const SysInfo si = f.sys[s];
+        law = si.law;
+        slices = si.slices;
+        G = si.G;
+        dt = si.dt;
+      }
+    }
+    if (live) {
+      float4 hi = f.part_hi[i];
+      float4 lo = f.part_lo[i];
+      for (int k = 1; k < slices; ++k) {
+        const float4 h = f.part_hi[(long long)k * f.stride + i];
+        const float4 l = f.part_lo[(long long)k * f.stride + i];
+        comp_add(hi.x, lo.x, h.x);
+        comp_add(hi.y, lo.y, h.y);
+        comp_add(hi.z, lo.z, h.z);
+        comp_add(hi.w, lo.w, h.w);
+        lo.x = __fadd_rn(lo.x, l.x);
+        lo.y = __fadd_rn(lo.y, l.y);
+        lo.z = __fadd_rn(lo.z, l.z);
+        lo.w = __fadd_rn(lo.w, l.w);
+      }
+      // Round hi + lo to FP32 and keep the residual (Fast2Sum, |hi| >= |lo|).
+      float4 t, r;
+      t.x = __fadd_rn(hi.x, lo.x);
+      r.x = __fsub_rn(lo.x, __fsub_rn(t.x, hi.x));
+      t.y = __fadd_rn(hi.y, lo.y);
+      r.y = __fsub_rn(lo.y, __fsub_rn(t.y, hi.y));
+      t.z = __fadd_rn(hi.z, lo.z);
+      r.z = __fsub_rn(lo.z, __fsub_rn(t.z, hi.z));
+      t.w = __fadd_rn(hi.w, lo.w);
+      r.w = __fsub_rn(lo.w, __fsub_rn(t.w, hi.w));
+      float4 x = f.pos[i];
+      float4 a, alo;
+      if (law == 0) {  // gravity: a = G sum m_j y^3 d, phi = -G sum m_j y
+        a = make_float4(G * t.x, G * t.y, G * t.z, -G * t.w);
+        alo = make_float4(G * r.x, G * r.y, G * r.z, -G * r.w);
+      } else {  // LJC: F = -sum f d, a = F / m; phi = sum of pair energies
+        const float inv_m = 1.0f / x.w;
+        a = make_float4(-t.x * inv_m, -t.y * inv_m, -t.z * inv_m, t.w);
+        alo = make_float4(-r.x * inv_m, -r.y * inv_m, -r.z * inv_m, r.w);
+      }
+      if (f.mode & kFinWriteAcc) {
+        f.acc[i] = a;
+        if (f.acc_lo) f.acc_lo[i] = alo;
+      }
+      if (f.mode & (kFinKickSync | kFinDiag | kFinKickDrift)) {
+        float4 v = f.vel[i];
+        const float h = 0.5f * dt;
+        if (f.mode & kFinKickSync) {
+          v.x = fmaf(h, a.x, v.x);
+          v.y = fmaf(h, a.y, v.y);
+          v.z = fmaf(h, a.z, v.z);
+        }
+        if (f.mode & kFinDiag) {
+          const double m = x.w;
+          const double vx = v.x, vy = v.y, vz = v.z;
+          const double px = x.x, py = x.y, pz = x.z;
+          dv[0] = 0.5 * m * (vx * vx + vy * vy + vz * vz);
+          dv[1] = (law == 0) ? 0.5 * m * (double)a.w : 0.5 * (double)a.w;
+          dv[2] = m * vx;
+          dv[3] = m * vy;
+          dv[4] = m * vz;
+          dv[5] = m * (py * vz - pz * vy);
+          dv[6] = m * (pz * vx - px * vz);
+          dv[7] = m * (px * vy - py * vx);
+        }
+        if (f.mode & kFinKickDrift) {
+          v.x = fmaf(h, a.x, v.x);
+          v.y = fmaf(h, a.y, v.y);
+          v.z = fmaf(h, a.z, v.z);
+          x.x = fmaf(dt, v.x, x.x);
+          x.y = fmaf(dt, v.y, x.y);
+          x.z = fmaf(dt, v.z, x.z);
+          f.pos[i] = x;
+          if (f.trace_next) f.trace_next[i] = x;
+        }
+        f.vel[i] = v;
+      }
+    }
+  }
+  if (f.mode & kFinDiag) block_sum8(dv, f.diag_part + (size_t)blockIdx.x * kDiagFields);
+}
+
+// Deterministic final sum of the per-block FP64 diagnostics: one block,
+// thread t adds blocks t, t + 256, ... in order, then a fixed tree.
+__global__ void __launch_bounds__(kFinThreads) diag_reduce_kernel(const double *part, int nblk,
+                                                                  double *out) {
+  double v[kDiagFields] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblk; b += kFinThreads)
+#pragma unroll
+    for (int k = 0; k < kDiagFields; ++k) v[k] += part[(size_t)b * kDiagFields + k];
+  block_sum8(v, out);
+}
+
+// First half-kick and drift from a caller-supplied acceleration (NBODY_ACC_VALID).
+// Batched runs pass sys_of / sys for the per-system step size.
+__global__ void kick_drift_kernel(float4 *pos, float4 *vel, const float4 *acc, int n, float dt,
+                                  float4 *trace1, const int *sys_of, const SysInfo *sys) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (sys_of) {
+    const int s = sys_of[i];
+    if (s < 0) return;
+    dt = sys[s].dt;
+  }
+  float4 x = pos[i], v = vel[i];
+  const float4 a = acc[i];
+  const float h = 0.5f * dt;
+  v.x = fmaf(h, a.x, v.x);
+  v.y = fmaf(h, a.y, v.y);
+  v.z = fmaf(h, a.z, v.z);
+  x.x = fmaf(dt, v.x, x.x);
+  x.y = fmaf(dt, v.y, x.y);
+  x.z = fmaf(dt, v.z, x.z);
+  pos[i] = x;
+  vel[i] = v;
+  if (trace1) trace1[i] = x;
+}
+
+__global__ void copy_float4_kernel(const float4 *src, float4 *dst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i];
+}
+
+// S0: caller SoA doubles -> (x, y, z, m) float4.
+__global__ void pack_grav_kernel(const double *x, const double *y, const double *z,
+                                 const double *m, float4 *out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float4((float)x[i], (float)y[i], (float)z[i], (float)m[i]);
+}
+
+// S0: LJC parameters (q~, s~, e~, type) with q~ = q sqrt(kq), s~ = sigma / 2,
+// e~ = sqrt(24 eps); computed in FP64 and rounded once.
+__global__ void pack_ljc_kernel(const double *q, const double *sig, const double *eps,
+                                const int32_t *type, double sqrt_kq, float4 *out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n)
+    out[i] = make_float4((float)(q[i] * sqrt_kq), (float)(0.5 * sig[i]),
+                         (float)sqrt(24.0 * eps[i]), (float)type[i]);
+}
+
+}  // namespace nbody

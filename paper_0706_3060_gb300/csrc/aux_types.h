@@ -1,0 +1,46 @@
+// aux_types.h -- data shared by the O(N) kernels and their host-side callers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace nbody {
+
+// Per-system data of a batched run (one entry per system).
+struct SysInfo {
+  int law;      // kLawGrav / kLawLJC
+  int slices;   // partial slots written for this system
+  float G;
+  float dt;
+};
+
+enum : int {
+  kFinWriteAcc = 1,   // store acc (and acc_lo)
+  kFinKickSync = 2,   // v += dt/2 a       (completes the previous step)
+  kFinDiag = 4,       // FP64 diagnostics with the synchronized velocity
+  kFinKickDrift = 8,  // v += dt/2 a; x += dt v   (starts the next step)
+};
+
+struct FinalizeArgs {
+  const float4 *part_hi;
+  const float4 *part_lo;
+  long long stride;
+  int slices;
+  const int *sys_of;     // batched: system of each particle (-1: gap), or null
+  const SysInfo *sys;    // batched: per-system info, or null
+  int n;
+  int law;
+  float G;
+  float dt;
+  float4 *pos;
+  float4 *vel;
+  float4 *acc;
+  float4 *acc_lo;        // may be null
+  float4 *trace_next;    // positions after the drift, or null
+  int mode;
+  double *diag_part;     // [gridDim.x][8]
+};
+
+constexpr int kFinThreads = 256;
+constexpr int kDiagFields = 8;  // K, U, Px, Py, Pz, Lx, Ly, Lz
+
+}  // namespace nbody

@@ -1,0 +1,122 @@
+// device_common.cuh -- sm_103a device primitives shared by the all-pairs kernels:
+// mbarriers, 1-D TMA bulk copies, bounded waits, the hardware rsqrt and
+// error-free transformations for compensated sums.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace nbody {
+
+// Device error codes written to the error word (first error wins).
+enum : int {
+  kDevOk = 0,
+  kDevTimeout = 1,   // a bounded mbarrier wait ran out
+  kDevBadItem = 2,   // a work item failed its bounds check
+};
+
+// ~2 s at 2 GHz: no legitimate wait in these kernels comes near it.
+constexpr long long kWaitLimitCycles = 4000000000LL;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void set_error(int *err, int code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+// ---- mbarrier (shared::cta) -------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete, for at most
+// kWaitLimitCycles. Returns false (and records kDevTimeout) if it ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitLimitCycles) {
+      set_error(err, kDevTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+
+// ---- TMA: 1-D bulk copy global -> shared, completing on an mbarrier -----------
+// dst and src 16-byte aligned, bytes a multiple of 16 (checked by callers).
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// ---- arithmetic ---------------------------------------------------------------
+// Hardware reciprocal square root (MUFU.RSQ); s > 0 in every caller.
+__device__ __forceinline__ float rsqrt_hw(float s) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(s));
+  return y;
+}
+
+// One Newton-Raphson step for 1/sqrt(s): y <- y (3 - s y^2) / 2 (textbook).
+__device__ __forceinline__ float rsqrt_newton(float y, float s) {
+  const float hs = -0.5f * s;
+  const float yy = y * y;
+  return y * fmaf(hs, yy, 1.5f);
+}
+
+// Knuth's TwoSum: s + e == a + b exactly, s = fl(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Add b into the compensated pair (hi, lo).
+__device__ __forceinline__ void comp_add(float &hi, float &lo, float b) {
+  float s, e;
+  two_sum(hi, b, s, e);
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
+}  // namespace nbody

@@ -1,0 +1,21 @@
+// force_grav.cu -- instantiations of the all-pairs kernel for softened gravity
+// (Eq. 1, Table 1 "Gravity (accel)").
+#include "tiles.h"
+
+namespace nbody {
+
+const TileDesc *grav_tiles(int *count) {
+  // (threads, targets/thread, j-lanes/warp, j-tile)
+  static const TileDesc tiles[] = {
+      TileImpl<kLawGrav, 256, 4, 1, 256>::desc(),  // 0: 1024 targets per item
+      TileImpl<kLawGrav, 128, 8, 1, 256>::desc(),  // 1: 1024
+      TileImpl<kLawGrav, 256, 2, 1, 256>::desc(),  // 2: 512
+      TileImpl<kLawGrav, 128, 4, 1, 256>::desc(),  // 3: 512
+      TileImpl<kLawGrav, 128, 2, 4, 256>::desc(),  // 4: 64 targets, 4 j-lanes (small N)
+      TileImpl<kLawGrav, 64, 2, 8, 128>::desc(),   // 5: 16 targets, 8 j-lanes (tiny N)
+  };
+  *count = int(sizeof(tiles) / sizeof(tiles[0]));
+  return tiles;
+}
+
+}  // namespace nbody

@@ -1,0 +1,411 @@
+// force_kernel.cuh -- warp-specialized all-pairs force kernel for sm_103a.
+//
+// The computation is the direct sum of Sec. 2 ("for i: for j: force[i] +=
+// force_function(ri, rj)"), parallel over i, with the j-stream shared by every
+// thread of a CTA, as in the paper's kforce kernel. GB300 mapping:
+//   * one producer warp streams j-tiles of JT particles (16 B each, plus 16 B
+//     of LJC parameters) from global memory into a STAGES-deep shared-memory
+//     ring with 1-D TMA bulk copies completing on mbarriers (S1);
+//   * NT consumer threads each hold I target particles in registers -- the
+//     "i unrolled" half of the paper's A x B unrolling (Sec. 3.3) -- and read
+//     every staged j once per I interactions; the j-loop is unrolled (S2);
+//   * each j-tile's contribution is summed plainly in FP32 and then folded into
+//     a (hi, lo) pair with TwoSum, so the compensation costs a few operations
+//     per tile rather than per pair (S3, precision policy of Sec. 3.2);
+//   * SW j-lanes per warp split the j-range inside a warp and are combined
+//     with __shfl_xor in a fixed butterfly; several CTAs may split the
+//     j-range of one i-tile ("replication", Sec. 3.4) and write per-slice
+//     partials that the finalize kernel adds in a fixed order (S4). Results
+//     are therefore bitwise reproducible run to run.
+// The self pair is excluded by index (the Appendix's Ilist != Jlist test)
+// only in tiles whose j-range overlaps the CTA's i-range.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace nbody {
+
+enum : int { kLawGrav = 0, kLawLJC = 1, kLawMixed = 2 };
+
+constexpr int kStages = 4;
+
+// One unit of work: targets [i0, i0+ni) against sources [j0, j0+nj) of the
+// same system; results go to partial slot `slice`.
+struct WorkItem {
+  int i0;
+  int ni;
+  int j0;
+  int nj;
+  int law;
+  int slice;
+  float eps2;
+  int pad;
+};
+
+struct ForceArgs {
+  const float4 *pos;   // (x, y, z, m)
+  const float4 *prm;   // LJC (q~, s~, e~, type) or null
+  float4 *part_hi;     // [slices][stride]
+  float4 *part_lo;     // [slices][stride]
+  long long stride;    // elements per slice
+  int *err;            // device error word
+  // single system: items are (i-tile, j-slice) pairs enumerated by blockIdx.x
+  int n;
+  int slices;
+  int slice_len;       // multiple of JT
+  float eps2;
+  // work list (batched): items[k], k taken from *counter (persistent CTAs)
+  const WorkItem *items;
+  int n_items;
+  int *counter;        // null: single-system mode
+  int comp;            // 1: compensated (hi, lo) sums per j-tile
+};
+
+enum : int { kChunkFirst = 1, kChunkLast = 2, kChunkEnd = 4 };
+
+struct ChunkMeta {
+  WorkItem item;
+  int cj0;
+  int len;
+  int flags;
+  int pad;
+};
+
+// ---- pair interactions ---------------------------------------------------------
+// Gravity (Eq. 1, Appendix listing): d = x_j - x_i, s2 = |d|^2 + eps^2,
+// y = 1/sqrt(s2); acc += m_j y^3 d; pot += m_j y (scaled by G / -G later).
+template <bool POT, bool PRECISE, bool MASK>
+__device__ __forceinline__ void grav_pair(const float4 pj, float xi, float yi, float zi,
+                                          float eps2, float4 &acc, bool self) {
+  const float dx = pj.x - xi;
+  const float dy = pj.y - yi;
+  const float dz = pj.z - zi;
+  const float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+  float y = rsqrt_hw(s2);
+  if (PRECISE) y = rsqrt_newton(y, s2);
+  if (MASK) y = self ? 0.0f : y;
+  const float my = pj.w * y;
+  const float w = my * (y * y);
+  acc.x = fmaf(w, dx, acc.x);
+  acc.y = fmaf(w, dy, acc.y);
+  acc.z = fmaf(w, dz, acc.z);
+  if (POT) acc.w += my;
+}
+
+// LJ 12-6 + Coulomb (Table 1 LJC(constant)) with pre-scaled parameters:
+// q~ = q sqrt(k/eps_r), s~ = sigma/2, e~ = sqrt(24 eps), so that
+// q~i q~j = k qi qj / eps_r, s~i + s~j = sigma_ij, e~i e~j = 24 eps_ij.
+// With d = x_j - x_i, y = 1/r, u = (sigma_ij y)^6:
+//   f = q~q~ y^3 + e~e~ y^2 (2u^2 - u);  acc += f d  (force on i is -acc)
+//   pot += q~q~ y + (e~e~ / 6)(u^2 - u)
+template <bool POT, bool PRECISE, bool MASK>
+__device__ __forceinline__ void ljc_pair(const float4 pj, const float4 qj, float xi, float yi,
+                                         float zi, float qi, float si, float ei, float4 &acc,
+                                         bool self) {
+  const float dx = pj.x - xi;
+  const float dy = pj.y - yi;
+  const float dz = pj.z - zi;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  float y = rsqrt_hw(r2);
+  if (PRECISE) y = rsqrt_newton(y, r2);
+  if (MASK) y = self ? 0.0f : y;
+  const float y2 = y * y;
+  const float qq = qi * qj.x;
+  const float s = si + qj.y;
+  const float t = (s * s) * y2;
+  const float u = (t * t) * t;
+  const float ee = ei * qj.z;
+  const float fc = (qq * y) * y2;
+  const float h = fmaf(u, 2.0f, -1.0f) * u;
+  const float f = fmaf(ee * y2, h, fc);
+  acc.x = fmaf(f, dx, acc.x);
+  acc.y = fmaf(f, dy, acc.y);
+  acc.z = fmaf(f, dz, acc.z);
+  if (POT) {
+    acc.w = fmaf(qq, y, acc.w);
+    acc.w = fmaf(ee * (1.0f / 6.0f), fmaf(u, u, -u), acc.w);
+  }
+}
+
+template <int LAW, int NT, int I, int SW, int JT>
+struct ForceTile {
+  static constexpr int kThreads = NT + 32;  // + producer warp
+  static constexpr int kSlots = NT / SW;    // i-slots per CTA
+  static constexpr int kTileI = kSlots * I; // targets per item
+  static constexpr bool kPrm = (LAW != kLawGrav);
+  static constexpr size_t kSmemBytes = size_t(kStages) * JT * 16 * (kPrm ? 2 : 1);
+};
+
+// ---- the kernel -------------------------------------------------------------------
+template <int LAW, int NT, int I, int SW, int JT, bool POT, bool PRECISE>
+__global__ void __launch_bounds__(NT + 32) force_kernel(const ForceArgs a) {
+  using T = ForceTile<LAW, NT, I, SW, JT>;
+  constexpr int NWARPS = NT / 32;
+  constexpr int SLOTS = T::kSlots;
+  constexpr int TI = T::kTileI;
+  static_assert(NT % 32 == 0 && 32 % SW == 0, "bad tile");
+  static_assert(JT % SW == 0, "bad j tile");
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float4 *sm_pos = reinterpret_cast<float4 *>(smem_raw);
+  float4 *sm_prm = sm_pos + kStages * JT;
+  __shared__ __align__(8) uint64_t full_bar[kStages];
+  __shared__ __align__(8) uint64_t empty_bar[kStages];
+  __shared__ ChunkMeta meta[kStages];
+
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], NWARPS);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  // ===================== producer warp: TMA j-tiles into the ring ================
+  if (tid >= NT) {
+    if (tid != NT) return;
+    int it = 0;
+    bool ok = true;
+    auto push = [&](const WorkItem &w, int cj0, int len, int flags) {
+      const int st = it % kStages;
+      const uint32_t par = ((it / kStages) & 1) ^ 1;
+      if (!mbar_wait(&empty_bar[st], par, a.err)) {
+        ok = false;
+        return;
+      }
+      meta[st].item = w;
+      meta[st].cj0 = cj0;
+      meta[st].len = len;
+      meta[st].flags = flags;
+      if (flags & kChunkEnd) {
+        mbar_arrive(&full_bar[st]);
+      } else {
+        const uint32_t bytes = uint32_t(len) * 16u;
+        const bool with_prm = (LAW == kLawLJC) || (LAW == kLawMixed && w.law == kLawLJC);
+        mbar_arrive_expect_tx(&full_bar[st], with_prm ? 2u * bytes : bytes);
+        tma_load_1d(sm_pos + st * JT, a.pos + cj0, bytes, &full_bar[st]);
+        if (with_prm) tma_load_1d(sm_prm + st * JT, a.prm + cj0, bytes, &full_bar[st]);
+      }
+      ++it;
+    };
+    auto push_item = [&](const WorkItem &w) {
+      const int jend = w.j0 + w.nj;
+      for (int cj = w.j0; cj < jend && ok; cj += JT) {
+        const int len = min(JT, jend - cj);
+        int flags = 0;
+        if (cj == w.j0) flags |= kChunkFirst;
+        if (cj + len >= jend) flags |= kChunkLast;
+        push(w, cj, len, flags);
+      }
+    };
+    if (a.counter == nullptr) {
+      const int b = blockIdx.x;
+      WorkItem w;
+      const int t = b / a.slices, s = b % a.slices;
+      w.i0 = t * TI;
+      w.ni = min(TI, a.n - w.i0);
+      w.j0 = s * a.slice_len;
+      w.nj = min(a.slice_len, a.n - w.j0);
+      w.law = LAW == kLawLJC ? kLawLJC : kLawGrav;
+      w.slice = s;
+      w.eps2 = a.eps2;
+      w.pad = 0;
+      if (w.ni > 0 && w.nj > 0) push_item(w);
+      else set_error(a.err, kDevBadItem);
+    } else {
+      while (ok) {
+        const int k = atomicAdd(a.counter, 1);
+        if (k >= a.n_items) break;
+        const WorkItem w = a.items[k];
+        if (w.ni <= 0 || w.ni > TI || w.nj <= 0 || w.i0 < 0 || w.j0 < 0) {
+          set_error(a.err, kDevBadItem);
+          continue;
+        }
+        push_item(w);
+      }
+    }
+    if (ok) {
+      WorkItem none{};
+      push(none, 0, 0, kChunkEnd);
+    }
+    if (!ok) {
+      // Bounded drain of copies still in flight before leaving.
+      for (int k = max(0, it - kStages); k < it; ++k)
+        mbar_wait(&full_bar[k % kStages], (k / kStages) & 1, a.err);
+    }
+    return;
+  }
+
+  // ===================== consumer warps ===========================================
+  const int warp = tid >> 5, lane = tid & 31;
+  const int jl = (SW > 1) ? (lane % SW) : 0;
+  const int slot = warp * (32 / SW) + lane / SW;
+
+  float xi[I], yi[I], zi[I];
+  float qi[I], si[I], ei[I];
+  int ig[I];
+  float4 p[I], hi[I], lo[I];
+  WorkItem cur{};
+  int cur_law = LAW == kLawLJC ? kLawLJC : kLawGrav;
+
+  for (int it = 0;; ++it) {
+    const int st = it % kStages;
+    if (!mbar_wait(&full_bar[st], (it / kStages) & 1, a.err)) return;
+    const int flags = meta[st].flags;
+    if (flags & kChunkEnd) break;
+    const int cj0 = meta[st].cj0;
+    const int len = meta[st].len;
+    if (flags & kChunkFirst) {
+      cur = meta[st].item;
+      if (LAW == kLawMixed) cur_law = cur.law;
+#pragma unroll
+      for (int r = 0; r < I; ++r) {
+        const int il = r * SLOTS + slot;
+        const int g = cur.i0 + min(il, cur.ni - 1);
+        ig[r] = (il < cur.ni) ? g : -1;
+        const float4 pi4 = __ldg(a.pos + g);
+        xi[r] = pi4.x;
+        yi[r] = pi4.y;
+        zi[r] = pi4.z;
+        if (T::kPrm && cur_law == kLawLJC) {
+          const float4 pr = __ldg(a.prm + g);
+          qi[r] = pr.x;
+          si[r] = pr.y;
+          ei[r] = pr.z;
+        } else {
+          qi[r] = si[r] = ei[r] = 0.0f;
+        }
+        hi[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        lo[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        p[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    const float4 *sp = sm_pos + st * JT;
+    const float4 *sq = sm_prm + st * JT;
+    const bool masked = (cj0 < cur.i0 + cur.ni) && (cur.i0 < cj0 + len);
+    const float eps2 = cur.eps2;
+
+    if (!T::kPrm || cur_law == kLawGrav) {
+      if (!masked && len == JT) {
+#pragma unroll 4
+        for (int jj = jl; jj < JT; jj += SW) {
+          const float4 pj = sp[jj];
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            grav_pair<POT, PRECISE, false>(pj, xi[r], yi[r], zi[r], eps2, p[r], false);
+        }
+      } else if (!masked) {
+#pragma unroll 2
+        for (int jj = jl; jj < len; jj += SW) {
+          const float4 pj = sp[jj];
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            grav_pair<POT, PRECISE, false>(pj, xi[r], yi[r], zi[r], eps2, p[r], false);
+        }
+      } else {
+        for (int jj = jl; jj < len; jj += SW) {
+          const float4 pj = sp[jj];
+          const int jg = cj0 + jj;
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            grav_pair<POT, PRECISE, true>(pj, xi[r], yi[r], zi[r], eps2, p[r], jg == ig[r]);
+        }
+      }
+    } else {
+      if (!masked && len == JT) {
+#pragma unroll 2
+        for (int jj = jl; jj < JT; jj += SW) {
+          const float4 pj = sp[jj];
+          const float4 qj = sq[jj];
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            ljc_pair<POT, PRECISE, false>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r],
+                                          p[r], false);
+        }
+      } else if (!masked) {
+        for (int jj = jl; jj < len; jj += SW) {
+          const float4 pj = sp[jj];
+          const float4 qj = sq[jj];
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            ljc_pair<POT, PRECISE, false>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r],
+                                          p[r], false);
+        }
+      } else {
+        for (int jj = jl; jj < len; jj += SW) {
+          const float4 pj = sp[jj];
+          const float4 qj = sq[jj];
+          const int jg = cj0 + jj;
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            ljc_pair<POT, PRECISE, true>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r],
+                                         p[r], jg == ig[r]);
+        }
+      }
+    }
+
+    // The stage has been read: hand it back to the producer.
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty_bar[st]);
+
+    // Fold this j-tile's plain FP32 partial into the compensated (hi, lo).
+#pragma unroll
+    for (int r = 0; r < I; ++r) {
+      if (a.comp) {
+        comp_add(hi[r].x, lo[r].x, p[r].x);
+        comp_add(hi[r].y, lo[r].y, p[r].y);
+        comp_add(hi[r].z, lo[r].z, p[r].z);
+        if (POT) comp_add(hi[r].w, lo[r].w, p[r].w);
+      } else {
+        hi[r].x += p[r].x;
+        hi[r].y += p[r].y;
+        hi[r].z += p[r].z;
+        if (POT) hi[r].w += p[r].w;
+      }
+      p[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+
+    if (flags & kChunkLast) {
+      // Combine the SW j-lanes of each target: fixed butterfly, identical on
+      // both partners of every exchange.
+#pragma unroll
+      for (int off = SW / 2; off >= 1; off >>= 1) {
+#pragma unroll
+        for (int r = 0; r < I; ++r) {
+          float4 oh, ol;
+          oh.x = __shfl_xor_sync(0xffffffffu, hi[r].x, off);
+          oh.y = __shfl_xor_sync(0xffffffffu, hi[r].y, off);
+          oh.z = __shfl_xor_sync(0xffffffffu, hi[r].z, off);
+          oh.w = __shfl_xor_sync(0xffffffffu, hi[r].w, off);
+          ol.x = __shfl_xor_sync(0xffffffffu, lo[r].x, off);
+          ol.y = __shfl_xor_sync(0xffffffffu, lo[r].y, off);
+          ol.z = __shfl_xor_sync(0xffffffffu, lo[r].z, off);
+          ol.w = __shfl_xor_sync(0xffffffffu, lo[r].w, off);
+          float e;
+          two_sum(hi[r].x, oh.x, hi[r].x, e);
+          lo[r].x = __fadd_rn(__fadd_rn(lo[r].x, ol.x), e);
+          two_sum(hi[r].y, oh.y, hi[r].y, e);
+          lo[r].y = __fadd_rn(__fadd_rn(lo[r].y, ol.y), e);
+          two_sum(hi[r].z, oh.z, hi[r].z, e);
+          lo[r].z = __fadd_rn(__fadd_rn(lo[r].z, ol.z), e);
+          two_sum(hi[r].w, oh.w, hi[r].w, e);
+          lo[r].w = __fadd_rn(__fadd_rn(lo[r].w, ol.w), e);
+        }
+      }
+      if (jl == 0) {
+        const long long base = (long long)cur.slice * a.stride;
+#pragma unroll
+        for (int r = 0; r < I; ++r) {
+          if (ig[r] >= 0) {
+            a.part_hi[base + ig[r]] = hi[r];
+            a.part_lo[base + ig[r]] = lo[r];
+          }
+        }
+      }
+    }
+  }
+}
+
+}  // namespace nbody

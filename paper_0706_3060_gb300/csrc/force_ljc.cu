@@ -1,0 +1,19 @@
+// force_ljc.cu -- instantiations of the all-pairs kernel for Lennard-Jones plus
+// Coulomb with a constant dielectric (Table 1 "LJC(constant)").
+#include "tiles.h"
+
+namespace nbody {
+
+const TileDesc *ljc_tiles(int *count) {
+  static const TileDesc tiles[] = {
+      TileImpl<kLawLJC, 256, 2, 1, 256>::desc(),  // 0: 512 targets per item
+      TileImpl<kLawLJC, 128, 4, 1, 256>::desc(),  // 1: 512
+      TileImpl<kLawLJC, 256, 4, 1, 256>::desc(),  // 2: 1024
+      TileImpl<kLawLJC, 128, 2, 4, 256>::desc(),  // 3: 64 targets, 4 j-lanes
+      TileImpl<kLawLJC, 64, 2, 8, 128>::desc(),   // 4: 16 targets, 8 j-lanes
+  };
+  *count = int(sizeof(tiles) / sizeof(tiles[0]));
+  return tiles;
+}
+
+}  // namespace nbody

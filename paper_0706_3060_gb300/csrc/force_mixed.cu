@@ -1,0 +1,18 @@
+// force_mixed.cu -- persistent work-list instantiations for batched ensembles
+// that mix gravity and LJC systems in one launch (Sec. 3.4, small systems).
+#include "tiles.h"
+
+namespace nbody {
+
+const TileDesc *mixed_tiles(int *count) {
+  static const TileDesc tiles[] = {
+      TileImpl<kLawMixed, 128, 2, 4, 256>::desc(),  // 0: 64 targets, 4 j-lanes
+      TileImpl<kLawMixed, 128, 2, 1, 256>::desc(),  // 1: 256 targets
+      TileImpl<kLawMixed, 128, 2, 2, 256>::desc(),  // 2: 128 targets, 2 j-lanes
+      TileImpl<kLawMixed, 64, 2, 8, 128>::desc(),   // 3: 16 targets, 8 j-lanes
+  };
+  *count = int(sizeof(tiles) / sizeof(tiles[0]));
+  return tiles;
+}
+
+}  // namespace nbody

@@ -1,0 +1,67 @@
+// tiles.h -- host-side table of compiled force-kernel tile configurations.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "force_kernel.cuh"
+
+namespace nbody {
+
+using ForceLauncher = cudaError_t (*)(const ForceArgs &, int grid, bool pot, bool precise,
+                                      cudaStream_t);
+using ForceOccupancy = int (*)();  // resident CTAs per SM of the (pot=0, precise=0) kernel
+
+struct TileDesc {
+  int law;
+  int nt;     // consumer threads
+  int i;      // targets per thread
+  int sw;     // j-lanes per warp
+  int jt;     // j-tile length
+  int tile_i; // targets per item
+  int threads;
+  size_t smem;
+  ForceLauncher launch;
+  ForceOccupancy occupancy;
+};
+
+// Defined in force_grav.cu / force_ljc.cu / force_mixed.cu.
+const TileDesc *grav_tiles(int *count);
+const TileDesc *ljc_tiles(int *count);
+const TileDesc *mixed_tiles(int *count);
+
+template <int LAW, int NT, int I, int SW, int JT>
+struct TileImpl {
+  using T = ForceTile<LAW, NT, I, SW, JT>;
+  template <bool POT, bool PRE>
+  static cudaError_t go(const ForceArgs &a, int grid, cudaStream_t s) {
+    auto k = force_kernel<LAW, NT, I, SW, JT, POT, PRE>;
+    if (T::kSmemBytes > 48 * 1024) {
+      cudaError_t e =
+          cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
+      if (e != cudaSuccess) return e;
+    }
+    k<<<grid, T::kThreads, T::kSmemBytes, s>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t launch(const ForceArgs &a, int grid, bool pot, bool precise,
+                            cudaStream_t s) {
+    if (pot) return precise ? go<true, true>(a, grid, s) : go<true, false>(a, grid, s);
+    return precise ? go<false, true>(a, grid, s) : go<false, false>(a, grid, s);
+  }
+  static int occupancy() {
+    int nb = 0;
+    auto k = force_kernel<LAW, NT, I, SW, JT, false, false>;
+    if (T::kSmemBytes > 48 * 1024)
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, T::kThreads, T::kSmemBytes) !=
+        cudaSuccess)
+      return 1;
+    return nb > 0 ? nb : 1;
+  }
+  static TileDesc desc() {
+    return TileDesc{LAW, NT, I, SW, JT, T::kTileI, T::kThreads, T::kSmemBytes, &launch,
+                    &occupancy};
+  }
+};
+
+}  // namespace nbody

@@ -1,0 +1,491 @@
+// vjp_kernel.cuh -- all-pairs vector-Jacobian product of the force laws for
+// reverse-mode leapfrog. The paper has no adjoint; the pair terms below are the
+// derivatives of Eq. 1 and of the Table 1 LJC(constant) law.
+//
+// Gravity, target k, source j, d = x_j - x_k, s^2 = |d|^2 + eps^2, y = 1/s,
+// w = m_k lam_j - m_j lam_k:
+//   g_k  = G sum_j [ y^3 w - 3 y^5 (d.w) d ]        (T = I/s^3 - 3 d d^T / s^5)
+//   gm_k = -G sum_j (lam_j . d) y^3                   (d/dm_k of sum_i lam_i . a_i)
+// LJC with u = lam / m, w = u_k - u_j, y = 1/r, sigma = s~k + s~j,
+// u6 = (sigma y)^6, phi = q~q~ y^3 + e~e~ y^2 (2 u6^2 - u6) and
+// 2 phi' = y^2 [ -3 q~q~ y^3 + e~e~ y^2 (8 u6 - 28 u6^2) ]:
+//   g_k  = sum_j [ phi w + 2 phi' (d.w) d ]           (H = phi I + 2 phi' d d^T)
+//   F_k  = -sum_j phi d                               (mass derivative -u_k.F_k / m_k)
+//   D_k  = sum_j (d.w) e~e~ y^2 (4 u6^2 - u6) / sigma (sigma derivative, x -3 later)
+//   E_k  = sum_j (d.w) e~e~ y^2 (2 u6^2 - u6)         (epsilon derivative, x -1/(2 eps_k))
+// The pipeline (producer warp, TMA ring, compensated per-tile sums, j-lanes
+// with shuffle reduction, per-slice partials) is the same as force_kernel.cuh.
+#pragma once
+
+#include "device_common.cuh"
+#include "force_kernel.cuh"
+
+namespace nbody {
+
+struct VjpArgs {
+  const float4 *pos;   // (x, y, z, m)
+  const float4 *lam;   // gravity: lam; LJC: u = lam / m
+  const float4 *prm;   // LJC parameters or null
+  float4 *part_hi;     // [2][slices][stride]: block A then block B (LJC)
+  float4 *part_lo;
+  long long stride;
+  long long bstride;   // offset of block B (slices * stride)
+  int *err;
+  int n;
+  int slices;
+  int slice_len;
+  float eps2;
+  int comp;
+};
+
+__device__ __forceinline__ float rcp_hw(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+template <bool MASK>
+__device__ __forceinline__ void grav_vjp_pair(const float4 pj, const float4 lj, float xk,
+                                              float yk, float zk, float mk, float lkx, float lky,
+                                              float lkz, float eps2, float4 &A, bool self) {
+  const float dx = pj.x - xk;
+  const float dy = pj.y - yk;
+  const float dz = pj.z - zk;
+  const float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+  float y = rsqrt_hw(s2);
+  if (MASK) y = self ? 0.0f : y;
+  const float y2 = y * y;
+  const float y3 = y2 * y;
+  const float mj = pj.w;
+  const float wx = fmaf(mk, lj.x, -(mj * lkx));
+  const float wy = fmaf(mk, lj.y, -(mj * lky));
+  const float wz = fmaf(mk, lj.z, -(mj * lkz));
+  const float dw = fmaf(dx, wx, fmaf(dy, wy, dz * wz));
+  const float c = (-3.0f * dw) * (y3 * y2);
+  A.x = fmaf(c, dx, fmaf(y3, wx, A.x));
+  A.y = fmaf(c, dy, fmaf(y3, wy, A.y));
+  A.z = fmaf(c, dz, fmaf(y3, wz, A.z));
+  const float ld = fmaf(lj.x, dx, fmaf(lj.y, dy, lj.z * dz));
+  A.w = fmaf(ld, y3, A.w);
+}
+
+template <bool MASK>
+__device__ __forceinline__ void ljc_vjp_pair(const float4 pj, const float4 uj, const float4 qj,
+                                             float xk, float yk, float zk, float ukx, float uky,
+                                             float ukz, float qk, float sk, float ek, float4 &A,
+                                             float4 &B, bool self) {
+  const float dx = pj.x - xk;
+  const float dy = pj.y - yk;
+  const float dz = pj.z - zk;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  float y = rsqrt_hw(r2);
+  if (MASK) y = self ? 0.0f : y;
+  const float y2 = y * y;
+  const float qq = qk * qj.x;
+  const float s = sk + qj.y;
+  const float ee = ek * qj.z;
+  const float t = (s * s) * y2;
+  const float u = (t * t) * t;
+  const float qy3 = qq * (y * y2);
+  const float eey2 = ee * y2;
+  const float h = fmaf(u, 2.0f, -1.0f) * u;
+  const float phi_lj = eey2 * h;
+  const float phi = phi_lj + qy3;
+  const float k1 = fmaf(u, -28.0f, 8.0f) * u;
+  const float tp = y2 * fmaf(eey2, k1, -3.0f * qy3);
+  const float wx = ukx - uj.x;
+  const float wy = uky - uj.y;
+  const float wz = ukz - uj.z;
+  const float dw = fmaf(dx, wx, fmaf(dy, wy, dz * wz));
+  const float c = tp * dw;
+  A.x = fmaf(c, dx, fmaf(phi, wx, A.x));
+  A.y = fmaf(c, dy, fmaf(phi, wy, A.y));
+  A.z = fmaf(c, dz, fmaf(phi, wz, A.z));
+  B.x = fmaf(phi, dx, B.x);
+  B.y = fmaf(phi, dy, B.y);
+  B.z = fmaf(phi, dz, B.z);
+  const float k2 = fmaf(u, 4.0f, -1.0f) * u;
+  const float rs = MASK ? (self ? 0.0f : rcp_hw(s)) : rcp_hw(s);
+  A.w = fmaf(dw, (eey2 * k2) * rs, A.w);
+  B.w = fmaf(dw, phi_lj, B.w);
+}
+
+template <int LAW, int NT, int I, int SW, int JT>
+struct VjpTile {
+  static constexpr int kThreads = NT + 32;
+  static constexpr int kSlots = NT / SW;
+  static constexpr int kTileI = kSlots * I;
+  static constexpr int kStreams = (LAW == kLawLJC) ? 3 : 2;
+  static constexpr size_t kSmemBytes = size_t(kStages) * JT * 16 * kStreams;
+};
+
+__device__ __forceinline__ void comp_fold(float4 &hi, float4 &lo, float4 &p, int comp) {
+  if (comp) {
+    comp_add(hi.x, lo.x, p.x);
+    comp_add(hi.y, lo.y, p.y);
+    comp_add(hi.z, lo.z, p.z);
+    comp_add(hi.w, lo.w, p.w);
+  } else {
+    hi.x += p.x;
+    hi.y += p.y;
+    hi.z += p.z;
+    hi.w += p.w;
+  }
+  p = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ void shfl_combine(float4 &hi, float4 &lo, int off) {
+  float4 oh, ol;
+  oh.x = __shfl_xor_sync(0xffffffffu, hi.x, off);
+  oh.y = __shfl_xor_sync(0xffffffffu, hi.y, off);
+  oh.z = __shfl_xor_sync(0xffffffffu, hi.z, off);
+  oh.w = __shfl_xor_sync(0xffffffffu, hi.w, off);
+  ol.x = __shfl_xor_sync(0xffffffffu, lo.x, off);
+  ol.y = __shfl_xor_sync(0xffffffffu, lo.y, off);
+  ol.z = __shfl_xor_sync(0xffffffffu, lo.z, off);
+  ol.w = __shfl_xor_sync(0xffffffffu, lo.w, off);
+  float e;
+  two_sum(hi.x, oh.x, hi.x, e);
+  lo.x = __fadd_rn(__fadd_rn(lo.x, ol.x), e);
+  two_sum(hi.y, oh.y, hi.y, e);
+  lo.y = __fadd_rn(__fadd_rn(lo.y, ol.y), e);
+  two_sum(hi.z, oh.z, hi.z, e);
+  lo.z = __fadd_rn(__fadd_rn(lo.z, ol.z), e);
+  two_sum(hi.w, oh.w, hi.w, e);
+  lo.w = __fadd_rn(__fadd_rn(lo.w, ol.w), e);
+}
+
+template <int LAW, int NT, int I, int SW, int JT>
+__global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
+  using T = VjpTile<LAW, NT, I, SW, JT>;
+  constexpr int NWARPS = NT / 32;
+  constexpr int SLOTS = T::kSlots;
+  constexpr int TI = T::kTileI;
+  constexpr bool LJ = (LAW == kLawLJC);
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float4 *sm_pos = reinterpret_cast<float4 *>(smem_raw);
+  float4 *sm_lam = sm_pos + kStages * JT;
+  float4 *sm_prm = sm_lam + kStages * JT;
+  __shared__ __align__(8) uint64_t full_bar[kStages];
+  __shared__ __align__(8) uint64_t empty_bar[kStages];
+  __shared__ int meta_len[kStages];
+  __shared__ int meta_cj0[kStages];
+
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], NWARPS);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  const int b = blockIdx.x;
+  const int tile = b / a.slices, slice = b % a.slices;
+  const int i0 = tile * TI;
+  const int ni = min(TI, a.n - i0);
+  const int j0 = slice * a.slice_len;
+  const int jend = min(a.n, j0 + a.slice_len);
+  const int nchunks = (jend - j0 + JT - 1) / JT;
+  if (ni <= 0 || jend <= j0) {
+    if (tid == 0) set_error(a.err, kDevBadItem);
+    return;
+  }
+
+  if (tid >= NT) {  // producer
+    if (tid != NT) return;
+    int it = 0;
+    for (; it < nchunks; ++it) {
+      const int st = it % kStages;
+      if (!mbar_wait(&empty_bar[st], ((it / kStages) & 1) ^ 1, a.err)) break;
+      const int cj = j0 + it * JT;
+      const int len = min(JT, jend - cj);
+      meta_len[st] = len;
+      meta_cj0[st] = cj;
+      const uint32_t bytes = uint32_t(len) * 16u;
+      mbar_arrive_expect_tx(&full_bar[st], bytes * T::kStreams);
+      tma_load_1d(sm_pos + st * JT, a.pos + cj, bytes, &full_bar[st]);
+      tma_load_1d(sm_lam + st * JT, a.lam + cj, bytes, &full_bar[st]);
+      if (LJ) tma_load_1d(sm_prm + st * JT, a.prm + cj, bytes, &full_bar[st]);
+    }
+    if (it < nchunks)  // timed out: bounded drain of copies in flight
+      for (int k = max(0, it - kStages); k < it; ++k)
+        mbar_wait(&full_bar[k % kStages], (k / kStages) & 1, a.err);
+    return;
+  }
+
+  const int warp = tid >> 5, lane = tid & 31;
+  const int jl = (SW > 1) ? (lane % SW) : 0;
+  const int slot = warp * (32 / SW) + lane / SW;
+  float xk[I], yk[I], zk[I], mk[I], lx[I], ly[I], lz[I], qk[I], sk[I], ek[I];
+  int ig[I];
+  float4 pA[I], hA[I], oA[I], pB[I], hB[I], oB[I];
+#pragma unroll
+  for (int r = 0; r < I; ++r) {
+    const int il = r * SLOTS + slot;
+    const int g = i0 + min(il, ni - 1);
+    ig[r] = (il < ni) ? g : -1;
+    const float4 p4 = __ldg(a.pos + g);
+    const float4 l4 = __ldg(a.lam + g);
+    xk[r] = p4.x;
+    yk[r] = p4.y;
+    zk[r] = p4.z;
+    mk[r] = p4.w;
+    lx[r] = l4.x;
+    ly[r] = l4.y;
+    lz[r] = l4.z;
+    if (LJ) {
+      const float4 q4 = __ldg(a.prm + g);
+      qk[r] = q4.x;
+      sk[r] = q4.y;
+      ek[r] = q4.z;
+    } else {
+      qk[r] = sk[r] = ek[r] = 0.f;
+    }
+    pA[r] = hA[r] = oA[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    pB[r] = hB[r] = oB[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+
+  for (int it = 0; it < nchunks; ++it) {
+    const int st = it % kStages;
+    if (!mbar_wait(&full_bar[st], (it / kStages) & 1, a.err)) return;
+    const int len = meta_len[st];
+    const int cj0 = meta_cj0[st];
+    const float4 *sp = sm_pos + st * JT;
+    const float4 *sl = sm_lam + st * JT;
+    const float4 *sq = sm_prm + st * JT;
+    const bool masked = (cj0 < i0 + ni) && (i0 < cj0 + len);
+    if (!LJ) {
+      if (!masked) {
+#pragma unroll 2
+        for (int jj = jl; jj < len; jj += SW) {
+          const float4 pj = sp[jj];
+          const float4 lj = sl[jj];
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            grav_vjp_pair<false>(pj, lj, xk[r], yk[r], zk[r], mk[r], lx[r], ly[r], lz[r], a.eps2,
+                                 pA[r], false);
+        }
+      } else {
+        for (int jj = jl; jj < len; jj += SW) {
+          const float4 pj = sp[jj];
+          const float4 lj = sl[jj];
+          const int jg = cj0 + jj;
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            grav_vjp_pair<true>(pj, lj, xk[r], yk[r], zk[r], mk[r], lx[r], ly[r], lz[r], a.eps2,
+                                pA[r], jg == ig[r]);
+        }
+      }
+    } else {
+      if (!masked) {
+        for (int jj = jl; jj < len; jj += SW) {
+          const float4 pj = sp[jj];
+          const float4 uj = sl[jj];
+          const float4 qj = sq[jj];
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            ljc_vjp_pair<false>(pj, uj, qj, xk[r], yk[r], zk[r], lx[r], ly[r], lz[r], qk[r],
+                                sk[r], ek[r], pA[r], pB[r], false);
+        }
+      } else {
+        for (int jj = jl; jj < len; jj += SW) {
+          const float4 pj = sp[jj];
+          const float4 uj = sl[jj];
+          const float4 qj = sq[jj];
+          const int jg = cj0 + jj;
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            ljc_vjp_pair<true>(pj, uj, qj, xk[r], yk[r], zk[r], lx[r], ly[r], lz[r], qk[r],
+                               sk[r], ek[r], pA[r], pB[r], jg == ig[r]);
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty_bar[st]);
+#pragma unroll
+    for (int r = 0; r < I; ++r) {
+      comp_fold(hA[r], oA[r], pA[r], a.comp);
+      if (LJ) comp_fold(hB[r], oB[r], pB[r], a.comp);
+    }
+  }
+
+#pragma unroll
+  for (int off = SW / 2; off >= 1; off >>= 1) {
+#pragma unroll
+    for (int r = 0; r < I; ++r) {
+      shfl_combine(hA[r], oA[r], off);
+      if (LJ) shfl_combine(hB[r], oB[r], off);
+    }
+  }
+  if (jl == 0) {
+    const long long base = (long long)slice * a.stride;
+#pragma unroll
+    for (int r = 0; r < I; ++r) {
+      if (ig[r] < 0) continue;
+      a.part_hi[base + ig[r]] = hA[r];
+      a.part_lo[base + ig[r]] = oA[r];
+      if (LJ) {
+        a.part_hi[a.bstride + base + ig[r]] = hB[r];
+        a.part_lo[a.bstride + base + ig[r]] = oB[r];
+      }
+    }
+  }
+}
+
+// ---- O(N) kernels of the reverse sweep -------------------------------------------
+struct VjpFinalizeArgs {
+  const float4 *part_hi;
+  const float4 *part_lo;
+  long long stride;
+  long long bstride;
+  int slices;
+  int n;
+  int law;
+  float G;
+  float alpha;        // weight of this VJP (h or dt in the reverse sweep)
+  const float4 *pos;
+  const float4 *prm;
+  const float4 *lam;  // gravity: lam; LJC: u
+  float4 *grad_x;     // += alpha g (or = when !accumulate)
+  float *grad_m;      // may be null
+  int accumulate;
+  double *type_part;  // [gridDim.x][8] or null
+  float4 *lam_v;      // if non-null: lam_v += dt_next * grad_x afterwards
+  float dt_next;
+};
+
+__global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs f) {
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  double tv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (i < f.n) {
+    float4 hA = f.part_hi[i], oA = f.part_lo[i];
+    float4 hB = make_float4(0.f, 0.f, 0.f, 0.f), oB = hB;
+    const bool lj = (f.law == kLawLJC);
+    if (lj) {
+      hB = f.part_hi[f.bstride + i];
+      oB = f.part_lo[f.bstride + i];
+    }
+    for (int k = 1; k < f.slices; ++k) {
+      const long long o = (long long)k * f.stride + i;
+      float4 h = f.part_hi[o], l = f.part_lo[o];
+      comp_add(hA.x, oA.x, h.x);
+      comp_add(hA.y, oA.y, h.y);
+      comp_add(hA.z, oA.z, h.z);
+      comp_add(hA.w, oA.w, h.w);
+      oA.x += l.x;
+      oA.y += l.y;
+      oA.z += l.z;
+      oA.w += l.w;
+      if (lj) {
+        h = f.part_hi[f.bstride + o];
+        l = f.part_lo[f.bstride + o];
+        comp_add(hB.x, oB.x, h.x);
+        comp_add(hB.y, oB.y, h.y);
+        comp_add(hB.z, oB.z, h.z);
+        comp_add(hB.w, oB.w, h.w);
+        oB.x += l.x;
+        oB.y += l.y;
+        oB.z += l.z;
+        oB.w += l.w;
+      }
+    }
+    const float ax = hA.x + oA.x, ay = hA.y + oA.y, az = hA.z + oA.z, aw = hA.w + oA.w;
+    float gx, gy, gz, gm;
+    if (!lj) {
+      gx = f.G * ax;
+      gy = f.G * ay;
+      gz = f.G * az;
+      gm = -f.G * aw;
+    } else {
+      const float4 x = f.pos[i];
+      const float4 u = f.lam[i];
+      const float bx = hB.x + oB.x, by = hB.y + oB.y, bz = hB.z + oB.z, bw = hB.w + oB.w;
+      gx = ax;
+      gy = ay;
+      gz = az;
+      gm = (u.x * bx + u.y * by + u.z * bz) / x.w;
+      const float4 q = f.prm[i];
+      const int t = int(q.w);
+      if (f.type_part && t >= 0 && t < 4) {
+        const double e2 = double(q.z) * double(q.z);  // 24 eps_k
+        tv[t] = -3.0 * double(aw) * f.alpha;
+        tv[4 + t] = -12.0 / e2 * double(bw) * f.alpha;
+      }
+    }
+    float4 gxo = f.accumulate ? f.grad_x[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    gxo.x = fmaf(f.alpha, gx, gxo.x);
+    gxo.y = fmaf(f.alpha, gy, gxo.y);
+    gxo.z = fmaf(f.alpha, gz, gxo.z);
+    gxo.w = 0.0f;
+    f.grad_x[i] = gxo;
+    if (f.grad_m) {
+      const float gmo = f.accumulate ? f.grad_m[i] : 0.0f;
+      f.grad_m[i] = fmaf(f.alpha, gm, gmo);
+    }
+    if (f.lam_v) {
+      float4 v = f.lam_v[i];
+      v.x = fmaf(f.dt_next, gxo.x, v.x);
+      v.y = fmaf(f.dt_next, gxo.y, v.y);
+      v.z = fmaf(f.dt_next, gxo.z, v.z);
+      f.lam_v[i] = v;
+    }
+  }
+  if (f.type_part) {
+    // fixed-order block sum of the 8 per-type fields
+    __shared__ double red[8][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) tv[k] += __shfl_down_sync(0xffffffffu, tv[k], off);
+      if (lane == 0) red[warp][k] = tv[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+      f.type_part[(size_t)blockIdx.x * 8 + threadIdx.x] = s;
+    }
+  }
+}
+
+// Sum per-block type partials in order and add them into out[0..2*ntypes).
+__global__ void type_reduce_kernel(const double *part, int nblk, int ntypes, double *out) {
+  const int k = threadIdx.x;
+  if (k >= 8) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(size_t)b * 8 + k];
+  const int t = k & 3, which = k >> 2;  // 0: sigma, 1: eps
+  if (t < ntypes) out[which * ntypes + t] += s;
+}
+
+// u = lam / m (LJC sources are weighted by 1 / m_j).
+__global__ void lam_over_m_kernel(const float4 *lam, const float4 *pos, float4 *u, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 l = lam[i];
+  const float inv = 1.0f / pos[i].w;
+  u[i] = make_float4(l.x * inv, l.y * inv, l.z * inv, 0.0f);
+}
+
+// y += alpha * x on float4 xyz.
+__global__ void axpy4_kernel(float alpha, const float4 *x, float4 *y, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 a = x[i];
+  float4 b = y[i];
+  b.x = fmaf(alpha, a.x, b.x);
+  b.y = fmaf(alpha, a.y, b.y);
+  b.z = fmaf(alpha, a.z, b.z);
+  y[i] = b;
+}
+
+__global__ void zero_doubles_kernel(double *p, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = 0.0;
+}
+
+}  // namespace nbody

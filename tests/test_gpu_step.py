@@ -1,0 +1,133 @@
+"""GPU parity: nbody_step (KDK leapfrog over the all-pairs forces) against the
+FP64 oracle's leapfrog, plus the FP64 diagnostics, resume equivalence, the
+position trace and the host-pointer path."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from gpu_util import dev, grav_tensors, lib, ljc_tensors, oracle_ljc_system, traj_errors
+
+pytestmark = pytest.mark.gpu
+
+
+def _grav_ref_traj(g, dt, nsteps):
+    x, v, m = g.f32_as_f64()
+    sysm = oracle.GravSystem(m, G=g.G, eps=float(np.float32(g.eps)))
+    xs, vs = oracle.leapfrog(sysm, x, v, dt, nsteps, store=True)
+    return sysm, xs, vs
+
+
+def test_plummer_1024_ten_steps():
+    """N = 1024 Plummer, eps = 0.01, 10 steps at dt = 1e-3 (the small gravity workload)."""
+    nb = lib()
+    g = workloads.plummer(1024, seed=0, eps=0.01)
+    pos, vel = grav_tensors(g)
+    acc = torch.empty_like(pos)
+    diag = nb.step(pos, vel, acc, dt=1e-3, nsteps=10, eps=float(np.float32(g.eps)),
+                   report_every=5)
+    sysm, xs, vs = _grav_ref_traj(g, 1e-3, 10)
+    ex = traj_errors(pos[:, :3].cpu().numpy(), xs[-1])
+    ev = traj_errors(vel[:, :3].cpu().numpy(), vs[-1])
+    assert ex[0] <= 1e-6 and ex[1] <= 1e-5, ex
+    assert ev[0] <= 1e-5 and ev[1] <= 1e-4, ev
+    # acceleration at the exit positions
+    a_ref = sysm.accel(xs[-1])
+    e = np.linalg.norm(acc[:, :3].cpu().numpy() - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)
+    assert np.sqrt(np.mean(e ** 2)) <= 2e-5
+    # FP64 diagnostics at steps 0, 5, 10
+    d = diag.cpu().numpy()
+    assert d.shape == (3, 8)
+    for row, k in zip(d, (0, 5, 10)):
+        ref = oracle.diagnostics(sysm, xs[k], vs[k])
+        assert abs(row[0] - ref["K"]) <= 1e-5 * abs(ref["K"])
+        assert abs(row[1] - ref["U"]) <= 1e-5 * abs(ref["U"])
+        np.testing.assert_allclose(row[2:5], ref["P"], atol=1e-6)
+        np.testing.assert_allclose(row[5:8], ref["L"], atol=1e-6)
+
+
+def test_resume_and_acc_valid_equivalence():
+    """2 x 5 steps (second call reusing acc) is bitwise equal to 10 steps."""
+    nb = lib()
+    g = workloads.plummer(3000, seed=11, eps=0.01)
+    eps = float(np.float32(g.eps))
+    p1, v1 = grav_tensors(g)
+    a1 = torch.empty_like(p1)
+    nb.step(p1, v1, a1, dt=1e-3, nsteps=10, eps=eps)
+    p2, v2 = grav_tensors(g)
+    a2 = torch.empty_like(p2)
+    nb.step(p2, v2, a2, dt=1e-3, nsteps=5, eps=eps)
+    nb.step(p2, v2, a2, dt=1e-3, nsteps=5, eps=eps, acc_valid=True)
+    assert torch.equal(p1, p2) and torch.equal(v1, v2) and torch.equal(a1, a2)
+
+
+def test_trace_holds_every_position():
+    nb = lib()
+    g = workloads.plummer(700, seed=12, eps=0.02)
+    eps = float(np.float32(g.eps))
+    pos, vel = grav_tensors(g)
+    acc = torch.empty_like(pos)
+    trace = torch.empty((7 * 700, 4), device=dev())
+    p0 = pos.clone()
+    nb.step(pos, vel, acc, dt=1e-3, nsteps=6, eps=eps, trace=trace)
+    tr = trace.view(7, 700, 4)
+    assert torch.equal(tr[0], p0) and torch.equal(tr[6], pos)
+    # each stored state equals an independent run of k steps
+    pk, vk = grav_tensors(g)
+    ak = torch.empty_like(pk)
+    nb.step(pk, vk, ak, dt=1e-3, nsteps=3, eps=eps)
+    assert torch.equal(tr[3], pk)
+
+
+def test_host_pointer_step_matches_device():
+    nb = lib()
+    g = workloads.plummer(1500, seed=13, eps=0.01)
+    eps = float(np.float32(g.eps))
+    pd, vd = grav_tensors(g)
+    ad = torch.empty_like(pd)
+    nb.step(pd, vd, ad, dt=1e-3, nsteps=4, eps=eps)
+    ph, vh = pd.new_empty(0), None
+    ph, vh = grav_tensors(g, device="cpu")
+    ah = torch.empty_like(ph)
+    nb.step(ph, vh, ah, dt=1e-3, nsteps=4, eps=eps)
+    assert torch.equal(pd.cpu(), ph) and torch.equal(vd.cpu(), vh)
+
+
+def test_plummer_16384_hundred_steps_energy():
+    """N = 16384 Plummer with eps = 0.04 N^-1/3, 100 steps at dt = 1e-4."""
+    nb = lib()
+    n = 16384
+    g = workloads.plummer(n, seed=1, eps=workloads.plummer_softening(n))
+    pos, vel = grav_tensors(g)
+    acc = torch.empty_like(pos)
+    diag = nb.step(pos, vel, acc, dt=1e-4, nsteps=100, eps=float(np.float32(g.eps)),
+                   report_every=100).cpu().numpy()
+    sysm, xs, vs = _grav_ref_traj(g, 1e-4, 100)
+    ex = traj_errors(pos[:, :3].cpu().numpy(), xs[-1])
+    ev = traj_errors(vel[:, :3].cpu().numpy(), vs[-1])
+    assert ex[0] <= 1e-5 and ex[1] <= 1e-4, ex
+    assert ev[0] <= 1e-5 and ev[1] <= 1e-4, ev
+    E0 = diag[0, 0] + diag[0, 1]
+    E1 = diag[1, 0] + diag[1, 1]
+    ref0 = oracle.diagnostics(sysm, xs[0], vs[0])["E"]
+    ref1 = oracle.diagnostics(sysm, xs[-1], vs[-1])["E"]
+    assert abs(E0 - ref0) <= 1e-5 * abs(ref0)
+    # GPU drift matches the integrator's own drift to within FP32 effects
+    assert abs((E1 - E0) - (ref1 - ref0)) <= 2e-6 * abs(ref0)
+
+
+def test_ljc_steps():
+    nb = lib()
+    s = workloads.ljc_sphere(2048, seed=21)
+    pos, vel, prm = ljc_tensors(s)
+    acc = torch.empty_like(pos)
+    dt = 1e-4
+    nb.step(pos, vel, acc, prm, dt=dt, nsteps=5)
+    sysm, x, v = oracle_ljc_system(s)
+    xs, vs = oracle.leapfrog(sysm, x, v, dt, 5, store=True)
+    ex = traj_errors(pos[:, :3].cpu().numpy(), xs[-1])
+    assert ex[0] <= 1e-6 and ex[1] <= 1e-5, ex
+    # velocities start at 0: compare against the velocity scale after 5 steps
+    ev = traj_errors(vel[:, :3].cpu().numpy(), vs[-1])
+    assert ev[0] <= 1e-5 and ev[1] <= 1e-4, ev

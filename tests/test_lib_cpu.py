@@ -1,0 +1,91 @@
+"""CPU-only checks of the C ABI: the library builds, loads, exports every symbol
+include/nbody.h declares, and rejects bad arguments before touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0706_3060_gb300 import _lib, build
+    if not os.path.exists(_lib.LIB_PATH):
+        build.build()
+    return _lib.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "nbody.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nbody_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_0706_3060_gb300 import _lib
+    names = _declared()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(_lib.EXPORTS) == names
+
+
+def test_version_and_tiles(lib):
+    import paper_0706_3060_gb300 as nb
+    assert nb.version() >= 10000
+    for law in (0, 1, 2):
+        c = nb.tile_count(law)
+        assert c >= 4
+        for t in range(c):
+            info = nb.tile_info(law, t)
+            assert info["threads"] % 32 == 0 and 32 % info["j_lanes"] == 0
+            assert info["j_tile"] % info["j_lanes"] == 0
+    with pytest.raises(nb.NBodyError):
+        nb.tile_info(0, 99)
+
+
+def test_tuned_table_roundtrip(lib):
+    import paper_0706_3060_gb300 as nb
+    nb.set_tuned(nb.LAW_GRAV, 5000, 3, 2)
+    assert nb.get_config(nb.LAW_GRAV, 5000) == (3, 2)
+    nb.set_tuned(nb.LAW_GRAV, 5000, -1, 0)
+    assert nb.get_config(nb.LAW_GRAV, 5000)[1] == 0
+
+
+def test_bad_arguments_rejected_without_gpu(lib):
+    from paper_0706_3060_gb300._lib import NBodyParams
+    p = NBodyParams(0, 0, 1.0, 0.0, -1, 0)
+    # NULL params
+    assert lib.nbody_forces(None, None, None, None, 8, None, None) == 1
+    # negative n
+    assert lib.nbody_forces(None, None, None, None, -1, ctypes.byref(p), None) == 1
+    # unknown law
+    q = NBodyParams(7, 0, 1.0, 0.0, -1, 0)
+    assert lib.nbody_forces(ctypes.c_void_p(16), None, ctypes.c_void_p(16), None, 8,
+                            ctypes.byref(q), None) == 1
+    # misaligned pointer
+    assert lib.nbody_forces(ctypes.c_void_p(8), None, ctypes.c_void_p(16), None, 8,
+                            ctypes.byref(p), None) == 2
+    assert b"aligned" in lib.nbody_last_error()
+    # LJC without prm
+    q = NBodyParams(1, 0, 1.0, 0.0, -1, 0)
+    assert lib.nbody_forces(ctypes.c_void_p(16), None, ctypes.c_void_p(16), None, 8,
+                            ctypes.byref(q), None) == 1
+    # n == 0 is a no-op even without a device
+    assert lib.nbody_forces(None, None, None, None, 0, ctypes.byref(p), None) == 0
+    # negative steps
+    assert lib.nbody_step(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), None, 8,
+                          ctypes.c_float(1e-3), -1, 0, None, None, ctypes.byref(p), None) == 1
+
+
+def test_no_device_is_reported(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_0706_3060_gb300._lib import NBodyParams
+    p = NBodyParams(0, 0, 1.0, 0.0, -1, 0)
+    st = lib.nbody_forces(ctypes.c_void_p(16), None, ctypes.c_void_p(32), None, 8,
+                          ctypes.byref(p), None)
+    assert st == 6  # NBODY_EUNSUPPORTED
