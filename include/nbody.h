@@ -106,6 +106,14 @@ int nbody_check(nbody_stream_t stream);
 int nbody_timing_enable(int32_t on);
 int nbody_timing_read(int32_t which, int64_t *launches, double *total_ms);
 
+/* Throughput microbenchmark of the units that bound the all-pairs kernels
+ * (no counterpart in the paper; used to check the roofline denominators):
+ * kind 0 = scalar FP32 FFMA, 1 = packed f32x2 FFMA (2 lane ops each),
+ * 2 = MUFU rsqrt. Runs 8 x 256 threads per SM, 16 independent chains per
+ * thread, `iters` iterations; returns lane operations per SM per clock and
+ * per second. Synchronizes the device. */
+int nbody_peak_probe(int32_t kind, int32_t iters, double *ops_per_clk_sm, double *ops_per_s);
+
 /* ---------------------------------------------------------------------------
  * S0 pack (Sec. 2 "stream coordinates"; Appendix jpos/jmass float4).
  * Converts caller SoA data in double precision into the float4 streams above.
@@ -152,11 +160,17 @@ int nbody_forces(const void *pos_m, const void *prm, void *acc, void *acc_lo, in
  *           double-precision arithmetic on the GPU.
  *   trace : NULL, or (nsteps + 1) * n float4 receiving the positions x_0 ..
  *           x_nsteps (used by reverse-mode recomputation).
+ *   state_lo : NULL, or 2 * n float4 holding the low parts of a two-float
+ *           state (first n: x_lo, next n: v_lo; zero them to start). With it,
+ *           every kick and drift is a compensated (TwoSum) update of
+ *           (hi, lo), so FP32 rounding does not drift over many steps
+ *           (Sec. 3.2: higher precision only where it is needed). Forces are
+ *           always evaluated at the FP32 positions pos_m.
  * Host pointers are accepted as in nbody_forces (all of pos_m, vel, acc, prm
  * on the host); then the call synchronizes. A host diag also synchronizes.
  * --------------------------------------------------------------------------- */
 int nbody_step(void *pos_m, void *vel, void *acc, const void *prm, int64_t n, float dt,
-               int32_t nsteps, int32_t report_every, double *diag, void *trace,
+               int32_t nsteps, int32_t report_every, double *diag, void *trace, void *state_lo,
                const nbody_params *params, nbody_stream_t stream);
 
 /* ---------------------------------------------------------------------------

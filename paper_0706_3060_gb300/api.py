@@ -20,6 +20,23 @@ from ._lib import (ACC_VALID, ACCUMULATE, COMPUTE_POT, LAW_GRAV, LAW_LJC, NO_COM
 COULOMB_K = 332.0637  # kcal A / (mol e^2): units A, kcal/mol, e, amu (AKMA time)
 
 
+_tuned_done = False
+
+
+def _lib():
+    """The loaded library, with the stored tuning table of this GPU installed once."""
+    global _tuned_done
+    lib = load()
+    if not _tuned_done:
+        _tuned_done = True
+        try:
+            from . import tune
+            tune.load_cache()
+        except Exception:  # a missing or foreign cache only means default tiles
+            pass
+    return lib
+
+
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
@@ -108,15 +125,18 @@ def forces(pos_m, prm=None, *, law=None, G=1.0, eps=0.0, pot=False, precise=Fals
     acc = torch.empty_like(pos_m) if out is None else out
     lo = (torch.empty_like(pos_m) if out_lo is None else out_lo) if want_lo else None
     p = params(law, G, eps, pot, precise, compensated, tile, jsplit)
-    check(load().nbody_forces(_ptr(pos_m), _ptr(prm), _ptr(acc), _ptr(lo), n, ctypes.byref(p),
+    check(_lib().nbody_forces(_ptr(pos_m), _ptr(prm), _ptr(acc), _ptr(lo), n, ctypes.byref(p),
                               _stream(stream, pos_m.device)), "nbody_forces")
     return (acc, lo) if want_lo else acc
 
 
 def step(pos_m, vel, acc, prm=None, *, dt, nsteps=1, law=None, G=1.0, eps=0.0,
          report_every=0, acc_valid=False, pot=False, precise=False, compensated=True,
-         tile=-1, jsplit=0, trace=None, diag=None, stream=None):
+         tile=-1, jsplit=0, trace=None, diag=None, state_lo=None, stream=None):
     """``nsteps`` KDK leapfrog steps in place on (pos_m, vel); acc receives a(x_T).
+
+    ``state_lo`` (2n, 4) float32, zero-initialised by the caller, turns on the
+    compensated two-float state update (low parts of x, then of v).
 
     Returns the FP64 diagnostics (rows of K, U, Px, Py, Pz, Lx, Ly, Lz) as a
     float64 tensor when ``report_every`` > 0, else None.
@@ -130,9 +150,10 @@ def step(pos_m, vel, acc, prm=None, *, dt, nsteps=1, law=None, G=1.0, eps=0.0,
     if rows and diag is None:
         diag = torch.zeros((rows, 8), dtype=torch.float64, device=pos_m.device)
     p = params(law, G, eps, pot, precise, compensated, tile, jsplit, acc_valid)
-    check(load().nbody_step(_ptr(pos_m), _ptr(vel), _ptr(acc), _ptr(prm), n, float(dt),
+    check(_lib().nbody_step(_ptr(pos_m), _ptr(vel), _ptr(acc), _ptr(prm), n, float(dt),
                             int(nsteps), int(report_every), _ptr(diag) if rows else None,
-                            _ptr(trace), ctypes.byref(p), _stream(stream, pos_m.device)),
+                            _ptr(trace), _ptr(state_lo), ctypes.byref(p),
+                            _stream(stream, pos_m.device)),
           "nbody_step")
     return diag if rows else None
 
@@ -145,7 +166,7 @@ class BatchPlan:
 
     def __init__(self, systems, precise=False, compensated=True, tile=-1):
         """systems: iterable of dicts with offset, n, law, G, eps, dt."""
-        lib = load()
+        lib = _lib()
         systems = list(systems)
         arr = (NBodySystem * len(systems))()
         for k, s in enumerate(systems):
@@ -180,7 +201,7 @@ class BatchPlan:
 
 def forces_batched(systems, pos_m, vel, acc, prm=None, nsteps=0, acc_valid=False, stream=None):
     """One-shot batched run (plan, run, destroy); synchronizes."""
-    lib = load()
+    lib = _lib()
     systems = list(systems)
     arr = (NBodySystem * len(systems))()
     for k, s in enumerate(systems):
@@ -208,7 +229,7 @@ def adjoint(pos_m, lam, prm=None, *, law=None, G=1.0, eps=0.0, alpha=1.0, grad_x
     if gt is None and law == LAW_LJC:
         gt = torch.zeros(2 * ntypes, dtype=torch.float64, device=dev)
     p = params(law, G, eps, accumulate=accumulate)
-    check(load().nbody_adjoint(_ptr(pos_m), _ptr(prm), _ptr(lam), _ptr(gx), _ptr(gm), _ptr(gt),
+    check(_lib().nbody_adjoint(_ptr(pos_m), _ptr(prm), _ptr(lam), _ptr(gx), _ptr(gm), _ptr(gt),
                                int(ntypes), float(alpha), n, ctypes.byref(p),
                                _stream(stream, dev)), "nbody_adjoint")
     return gx, gm, gt
@@ -221,7 +242,7 @@ def adjoint_leapfrog(xs, lam_x, lam_v, prm=None, *, k, dt, first, law=None, G=1.
     n = lam_x.shape[0]
     law = (LAW_LJC if prm is not None else LAW_GRAV) if law is None else law
     p = params(law, G, eps)
-    check(load().nbody_adjoint_leapfrog(_ptr(xs), _ptr(prm), n, int(k), float(dt), int(first),
+    check(_lib().nbody_adjoint_leapfrog(_ptr(xs), _ptr(prm), n, int(k), float(dt), int(first),
                                         _ptr(lam_x), _ptr(lam_v), _ptr(grad_m), _ptr(grad_types),
                                         int(ntypes), ctypes.byref(p),
                                         _stream(stream, lam_x.device)),

@@ -1,0 +1,116 @@
+"""Reverse-mode leapfrog as a torch.autograd.Function with checkpointing.
+
+Forward: ``nsteps`` KDK steps through nbody_step with the compensated two-float
+state, storing (x, v, low parts) every ``k`` steps. Backward: for each chunk, newest first, recompute its positions with
+nbody_step's trace, then run the reverse sweep nbody_adjoint_leapfrog (force
+VJP kernels + fused adjoint updates). With merged half-kicks the sweep is
+
+    lam_x += dt/2 J(x_T)^T lam_v                      (only if dL/dv_T != 0)
+    for n = T-1 .. 0:  lam_v += dt lam_x;  lam_x += w_n J(x_n)^T lam_v
+                       (w_n = dt, w_0 = dt/2)
+
+and returns dL/dx_0 = lam_x, dL/dv_0 = lam_v, dL/dm and, for LJC, dL/dsigma_t
+and dL/deps_t. All arithmetic runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import api
+from ._lib import LAW_GRAV, LAW_LJC
+
+
+class _Cfg:
+    def __init__(self, law, dt, nsteps, k, G, eps, q=None, types=None, kq=None, ntypes=4):
+        self.law, self.dt, self.nsteps, self.k = law, float(dt), int(nsteps), int(k)
+        self.G, self.eps = float(G), float(eps)
+        self.q, self.types, self.kq, self.ntypes = q, types, kq, ntypes
+
+
+def _prm(cfg, sig_t, eps_t):
+    if cfg.law != LAW_LJC:
+        return None
+    t = cfg.types.long()
+    return api.pack_ljc(cfg.q, sig_t.double()[t], eps_t.double()[t], cfg.types, kq=cfg.kq)
+
+
+class NBodyLeapfrog(torch.autograd.Function):
+    """(x0, v0, m, sig_t, eps_t) -> (x_T, v_T) through ``nsteps`` leapfrog steps."""
+
+    @staticmethod
+    def forward(ctx, x0, v0, m, sig_t, eps_t, cfg):
+        dev = x0.device
+        n = x0.shape[0]
+        pos = torch.empty((n, 4), dtype=torch.float32, device=dev)
+        pos[:, :3] = x0.detach()
+        pos[:, 3] = m.detach()
+        vel = torch.zeros((n, 4), dtype=torch.float32, device=dev)
+        vel[:, :3] = v0.detach()
+        acc = torch.empty_like(pos)
+        lo = torch.zeros((2 * n, 4), dtype=torch.float32, device=dev)  # two-float state
+        prm = _prm(cfg, sig_t, eps_t)
+        ckpts = []
+        done = 0
+        while done < cfg.nsteps:
+            steps = min(cfg.k, cfg.nsteps - done)
+            ckpts.append((pos.clone(), vel.clone(), lo.clone()))
+            api.step(pos, vel, acc, prm, dt=cfg.dt, nsteps=steps, law=cfg.law, G=cfg.G,
+                     eps=cfg.eps, acc_valid=done > 0, state_lo=lo)
+            done += steps
+        ctx.cfg = cfg
+        ctx.ckpts = ckpts
+        ctx.prm = prm
+        ctx.save_for_backward(pos)
+        return pos[:, :3].clone(), vel[:, :3].clone()
+
+    @staticmethod
+    def backward(ctx, gx, gv):
+        cfg = ctx.cfg
+        (pos_T,) = ctx.saved_tensors
+        n = pos_T.shape[0]
+        dev = pos_T.device
+        lam_x = torch.zeros((n, 4), dtype=torch.float32, device=dev)
+        lam_v = torch.zeros((n, 4), dtype=torch.float32, device=dev)
+        if gx is not None:
+            lam_x[:, :3] = gx
+        if gv is not None:
+            lam_v[:, :3] = gv
+        grad_m = torch.zeros(n, dtype=torch.float32, device=dev)
+        grad_t = torch.zeros(2 * cfg.ntypes, dtype=torch.float64, device=dev)
+        gt = grad_t if cfg.law == LAW_LJC else None
+        if gv is not None and bool(torch.any(gv != 0)):
+            api.adjoint(pos_T, lam_v, ctx.prm, law=cfg.law, G=cfg.G, eps=cfg.eps,
+                        alpha=0.5 * cfg.dt, grad_x=lam_x, grad_m=grad_m, grad_types=gt,
+                        ntypes=cfg.ntypes, accumulate=True)
+        acc = torch.empty_like(pos_T)
+        starts = [cfg.k * c for c in range(len(ctx.ckpts))]
+        for c in range(len(ctx.ckpts) - 1, -1, -1):
+            p0, v0, l0 = ctx.ckpts[c]
+            steps = min(cfg.k, cfg.nsteps - starts[c])
+            pos, vel, lo = p0.clone(), v0.clone(), l0.clone()
+            trace = torch.empty(((steps + 1) * n, 4), dtype=torch.float32, device=dev)
+            api.step(pos, vel, acc, ctx.prm, dt=cfg.dt, nsteps=steps, law=cfg.law, G=cfg.G,
+                     eps=cfg.eps, trace=trace, state_lo=lo)
+            api.adjoint_leapfrog(trace, lam_x, lam_v, ctx.prm, k=steps, dt=cfg.dt,
+                                 first=starts[c] == 0, law=cfg.law, G=cfg.G, eps=cfg.eps,
+                                 grad_m=grad_m, grad_types=gt, ntypes=cfg.ntypes)
+        g_sig = g_eps = None
+        if cfg.law == LAW_LJC:
+            g_sig = grad_t[:cfg.ntypes].to(torch.float32)
+            g_eps = grad_t[cfg.ntypes:].to(torch.float32)
+        return lam_x[:, :3].clone(), lam_v[:, :3].clone(), grad_m, g_sig, g_eps, None
+
+
+def leapfrog(x0, v0, m, *, dt, nsteps, k=20, G=1.0, eps=0.0, law=LAW_GRAV, q=None,
+             types=None, sig_t=None, eps_t=None, kq=None):
+    """Differentiable leapfrog: returns (x_T, v_T); gradients flow to x0, v0, m
+    and (LJC) sig_t, eps_t. Gravity by default; pass law=LAW_LJC with per-atom
+    charges q (float64), int32 types and per-type sig_t, eps_t for LJ + Coulomb."""
+    if law == LAW_LJC:
+        kq = api.COULOMB_K / 80.0 if kq is None else kq
+        ntypes = int(sig_t.shape[0])
+        cfg = _Cfg(law, dt, nsteps, k, G, eps, q=q, types=types, kq=kq, ntypes=ntypes)
+    else:
+        cfg = _Cfg(law, dt, nsteps, k, G, eps)
+        sig_t = eps_t = torch.zeros(0, device=x0.device)
+    return NBodyLeapfrog.apply(x0, v0, m, sig_t, eps_t, cfg)

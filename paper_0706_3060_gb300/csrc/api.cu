@@ -28,10 +28,11 @@ int launch_diag_reduce(const double *part, int nblk, double *out, cudaStream_t s
 }
 
 int launch_kick_drift(float4 *pos, float4 *vel, const float4 *acc, int n, float dt,
-                      float4 *trace1, const int *sys_of, const void *sys, cudaStream_t s) {
+                      float4 *trace1, const int *sys_of, const void *sys, float4 *x_lo,
+                      float4 *v_lo, cudaStream_t s) {
   if (n <= 0) return NBODY_OK;
   kick_drift_kernel<<<(n + 255) / 256, 256, 0, s>>>(pos, vel, acc, n, dt, trace1, sys_of,
-                                                    static_cast<const SysInfo *>(sys));
+                                                    static_cast<const SysInfo *>(sys), x_lo, v_lo);
   NB_CUDA(cudaGetLastError());
   return NBODY_OK;
 }
@@ -70,6 +71,7 @@ int check_ptr(const void *p, const char *name, bool required = true) {
 
 // Scratch layout for one single-system evaluation.
 struct Scratch {
+  float4 *jbuf;
   float4 *part_hi;
   float4 *part_lo;
   double *diag_part;
@@ -81,9 +83,12 @@ int get_scratch(cudaStream_t s, int n, int slices, int diag_rows, Scratch *out) 
   const int nblk = std::max(1, (n + kFinThreads - 1) / kFinThreads);
   const size_t dpart = round_up(size_t(nblk) * kDiagFields * sizeof(double), 256);
   const size_t drows = round_up(size_t(std::max(diag_rows, 1)) * kDiagFields * sizeof(double), 256);
+  const size_t jb = round_up(size_t(n + 1) * sizeof(float4), 256);
   void *base = nullptr;
-  NB_TRY(workspace(s, 2 * part + dpart + drows, &base));
+  NB_TRY(workspace(s, jb + 2 * part + dpart + drows, &base));
   char *b = static_cast<char *>(base);
+  out->jbuf = reinterpret_cast<float4 *>(b);
+  b += jb;
   out->part_hi = reinterpret_cast<float4 *>(b);
   out->part_lo = reinterpret_cast<float4 *>(b + part);
   out->diag_part = reinterpret_cast<double *>(b + 2 * part);
@@ -95,8 +100,8 @@ int get_scratch(cudaStream_t s, int n, int slices, int diag_rows, Scratch *out) 
 int eval_and_finalize(const float4 *pos, const float4 *prm, const nbody_params &p, int n,
                       const Plan1 &plan, const Scratch &sc, int *err, bool pot,
                       FinalizeArgs f, cudaStream_t s, int *nblk) {
-  NB_TRY(launch_forces(pos, prm, p.law, p.flags, p.eps2, n, plan, sc.part_hi, sc.part_lo, err,
-                       pot, s));
+  NB_TRY(launch_forces(pos, prm, p.law, p.flags, p.eps2, n, plan, sc.part_hi, sc.part_lo,
+                       sc.jbuf, err, pot, s));
   f.part_hi = sc.part_hi;
   f.part_lo = sc.part_lo;
   f.stride = n;
@@ -128,7 +133,7 @@ int forces_device(const float4 *pos, const float4 *prm, float4 *acc, float4 *acc
 }
 
 int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n, float dt,
-                int nsteps, int report_every, double *diag_dev, float4 *trace,
+                int nsteps, int report_every, double *diag_dev, float4 *trace, float4 *state_lo,
                 const nbody_params &p, int sms, cudaStream_t s) {
   Plan1 plan{};
   NB_TRY(plan_single(p.law, n, p.tile, p.jsplit, sms, &plan));
@@ -148,6 +153,8 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
   f.acc = acc;
   f.acc_lo = nullptr;
   f.dt = dt;
+  f.x_lo = state_lo;
+  f.v_lo = state_lo ? state_lo + n : nullptr;
   // Step 0: a(x_0) from the caller or from one evaluation; then kick + drift.
   if (!(p.flags & NBODY_ACC_VALID) || report(0)) {
     int nblk = 0;
@@ -158,7 +165,7 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
     if (report(0)) NB_TRY(launch_diag_reduce(sc.diag_part, nblk, sc.diag_rows + kDiagFields * row++, s));
   } else if (nsteps > 0) {
     NB_TRY(launch_kick_drift(pos, vel, acc, n, dt, trace ? trace + size_t(n) : nullptr, nullptr,
-                             nullptr, s));
+                             nullptr, f.x_lo, f.v_lo, s));
   }
   for (int st = 1; st <= nsteps; ++st) {
     const bool rep = report(st);
@@ -269,7 +276,7 @@ int nbody_forces(const void *pos_m, const void *prm, void *acc, void *acc_lo, in
 }
 
 int nbody_step(void *pos_m, void *vel, void *acc, const void *prm, int64_t n, float dt,
-               int32_t nsteps, int32_t report_every, double *diag, void *trace,
+               int32_t nsteps, int32_t report_every, double *diag, void *trace, void *state_lo,
                const nbody_params *params, nbody_stream_t stream) {
   clear_error();
   if (n < 0 || n > kMaxN) return set_error_msg(NBODY_EINVAL, "n out of range: %lld", (long long)n);
@@ -285,6 +292,7 @@ int nbody_step(void *pos_m, void *vel, void *acc, const void *prm, int64_t n, fl
   NB_TRY(check_ptr(acc, "acc"));
   NB_TRY(check_ptr(prm, "prm", false));
   NB_TRY(check_ptr(trace, "trace", false));
+  NB_TRY(check_ptr(state_lo, "state_lo", false));
   int dev = 0, sms = 0;
   NB_TRY(check_device(&dev, &sms));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -295,27 +303,34 @@ int nbody_step(void *pos_m, void *vel, void *acc, const void *prm, int64_t n, fl
     return set_error_msg(NBODY_EINVAL, "pos_m, vel, acc and prm must be all host or all device");
   if (trace && is_host_pointer(trace))
     return set_error_msg(NBODY_EINVAL, "trace must be device memory");
+  if (state_lo && is_host_pointer(state_lo) != host)
+    return set_error_msg(NBODY_EINVAL, "state_lo must live where pos_m lives");
   const int rows = report_every > 0 ? nsteps / report_every + 1 : 0;
   const bool host_diag = rows > 0 && is_host_pointer(diag);
   const size_t bytes = size_t(n) * sizeof(float4);
   if (!host) {
     NB_TRY(step_device(static_cast<float4 *>(pos_m), static_cast<float4 *>(vel),
                        static_cast<float4 *>(acc), static_cast<const float4 *>(prm), int(n), dt,
-                       nsteps, report_every, diag, static_cast<float4 *>(trace), p, sms, s));
+                       nsteps, report_every, diag, static_cast<float4 *>(trace),
+                       static_cast<float4 *>(state_lo), p, sms, s));
     return host_diag ? sync_and_check(s) : NBODY_OK;
   }
   void *st = nullptr;
-  NB_TRY(staging(s, 4 * bytes, &st));
+  NB_TRY(staging(s, 6 * bytes, &st));
   float4 *d_pos = static_cast<float4 *>(st);
   float4 *d_vel = d_pos + n;
   float4 *d_acc = d_vel + n;
   float4 *d_prm = d_acc + n;
+  float4 *d_lo = d_prm + n;
+  if (state_lo) NB_CUDA(cudaMemcpyAsync(d_lo, state_lo, 2 * bytes, cudaMemcpyHostToDevice, s));
   NB_CUDA(cudaMemcpyAsync(d_pos, pos_m, bytes, cudaMemcpyHostToDevice, s));
   NB_CUDA(cudaMemcpyAsync(d_vel, vel, bytes, cudaMemcpyHostToDevice, s));
   if (p.flags & NBODY_ACC_VALID) NB_CUDA(cudaMemcpyAsync(d_acc, acc, bytes, cudaMemcpyHostToDevice, s));
   if (prm) NB_CUDA(cudaMemcpyAsync(d_prm, prm, bytes, cudaMemcpyHostToDevice, s));
   NB_TRY(step_device(d_pos, d_vel, d_acc, prm ? d_prm : nullptr, int(n), dt, nsteps,
-                     report_every, diag, static_cast<float4 *>(trace), p, sms, s));
+                     report_every, diag, static_cast<float4 *>(trace), state_lo ? d_lo : nullptr,
+                     p, sms, s));
+  if (state_lo) NB_CUDA(cudaMemcpyAsync(state_lo, d_lo, 2 * bytes, cudaMemcpyDeviceToHost, s));
   NB_CUDA(cudaMemcpyAsync(pos_m, d_pos, bytes, cudaMemcpyDeviceToHost, s));
   NB_CUDA(cudaMemcpyAsync(vel, d_vel, bytes, cudaMemcpyDeviceToHost, s));
   NB_CUDA(cudaMemcpyAsync(acc, d_acc, bytes, cudaMemcpyDeviceToHost, s));

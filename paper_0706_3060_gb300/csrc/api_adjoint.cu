@@ -28,7 +28,7 @@ struct VjpImpl {
   using T = VjpTile<LAW, NT, I, SW, JT>;
   static cudaError_t launch(const VjpArgs &a, int grid, cudaStream_t s) {
     auto k = vjp_kernel<LAW, NT, I, SW, JT>;
-    if (T::kSmemBytes > 48 * 1024) {
+    if (T::kSmemBytes > 32 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)T::kSmemBytes);
       if (e != cudaSuccess) return e;
@@ -39,7 +39,7 @@ struct VjpImpl {
   static int occupancy() {
     int nb = 0;
     auto k = vjp_kernel<LAW, NT, I, SW, JT>;
-    if (T::kSmemBytes > 48 * 1024)
+    if (T::kSmemBytes > 32 * 1024)
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, T::kThreads, T::kSmemBytes) !=
         cudaSuccess)

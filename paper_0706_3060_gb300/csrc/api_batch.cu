@@ -106,7 +106,8 @@ int enqueue_run(nbody_batch_plan *p, float4 *pos, float4 *vel, float4 *acc, cons
   if (!(flags & NBODY_ACC_VALID) || nsteps == 0) {
     NB_TRY(eval(kFinWriteAcc | (nsteps > 0 ? kFinKickDrift : 0)));
   } else {
-    NB_TRY(launch_kick_drift(pos, vel, acc, total, 0.0f, nullptr, p->d_sys_of, p->d_sys, s));
+    NB_TRY(launch_kick_drift(pos, vel, acc, total, 0.0f, nullptr, p->d_sys_of, p->d_sys,
+                             nullptr, nullptr, s));
   }
   for (int st = 1; st <= nsteps; ++st)
     NB_TRY(eval(kFinWriteAcc | kFinKickSync | (st == nsteps ? 0 : kFinKickDrift)));

@@ -347,10 +347,29 @@ int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out) {
   return NBODY_OK;
 }
 
+// Sources in pairs: jp[2p] = (x0, x1, y0, y1), jp[2p+1] = (z0, z1, m0, m1) for
+// particles 2p, 2p+1; an odd count is padded with a massless particle far away
+// (its pair terms are exactly zero).
+__global__ void interleave_pairs_kernel(const float4 *pos, float4 *jp, int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * p >= n) return;
+  const float4 a = pos[2 * p];
+  const float4 b = (2 * p + 1 < n) ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+  jp[2 * p] = make_float4(a.x, b.x, a.y, b.y);
+  jp[2 * p + 1] = make_float4(a.z, b.z, a.w, b.w);
+}
+
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
-                  int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, int *err, bool pot,
-                  cudaStream_t s) {
+                  int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
+                  int *err, bool pot, cudaStream_t s) {
+  if (p.tile->packed) {
+    if (!jbuf) return set_error_msg(NBODY_EINVAL, "packed tile without pair buffer");
+    const int np = (n + 1) / 2;
+    interleave_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, jbuf, n);
+    NB_CUDA(cudaGetLastError());
+  }
   ForceArgs a{};
+  a.jpair = jbuf;
   a.pos = pos;
   a.prm = prm;
   a.part_hi = part_hi;

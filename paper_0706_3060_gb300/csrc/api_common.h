@@ -66,9 +66,10 @@ struct Plan1 {
 int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out);
 
 // Launch: all-pairs partial sums into part_hi/lo (slices x n).
+// jbuf: scratch of n + 1 float4 for the pair-interleaved sources of packed tiles.
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
-                  int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, int *err, bool pot,
-                  cudaStream_t s);
+                  int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
+                  int *err, bool pot, cudaStream_t s);
 
 size_t round_up(size_t x, size_t a);
 
@@ -92,6 +93,7 @@ struct FinalizeArgs;
 int launch_finalize(const FinalizeArgs &f, cudaStream_t s, int *nblk_out);
 int launch_diag_reduce(const double *part, int nblk, double *out, cudaStream_t s);
 int launch_kick_drift(float4 *pos, float4 *vel, const float4 *acc, int n, float dt,
-                      float4 *trace1, const int *sys_of, const void *sys, cudaStream_t s);
+                      float4 *trace1, const int *sys_of, const void *sys, float4 *x_lo,
+                      float4 *v_lo, cudaStream_t s);
 
 }  // namespace nbody

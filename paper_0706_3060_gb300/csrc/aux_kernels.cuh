@@ -30,6 +30,19 @@ __device__ __forceinline__ void block_sum8(double v[kDiagFields], double *out) {
   }
 }
 
+// Two-float state update (hi, lo) += c * d on xyz: the increment and the old
+// low part are added first, then TwoSum splits the new value into the nearest
+// float and its exact residual, so rounding does not accumulate over steps.
+__device__ __forceinline__ void comp_axpy(float4 &hi, float4 &lo, float c, const float4 d) {
+  float e;
+  two_sum(hi.x, fmaf(c, d.x, lo.x), hi.x, e);
+  lo.x = e;
+  two_sum(hi.y, fmaf(c, d.y, lo.y), hi.y, e);
+  lo.y = e;
+  two_sum(hi.z, fmaf(c, d.z, lo.z), hi.z, e);
+  lo.z = e;
+}
+
 __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArgs f) {
   const int i = blockIdx.x * kFinThreads + threadIdx.x;
   double dv[kDiagFields] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -91,10 +104,17 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
       if (f.mode & (kFinKickSync | kFinDiag | kFinKickDrift)) {
         float4 v = f.vel[i];
         const float h = 0.5f * dt;
+        const bool two = f.x_lo != nullptr;
+        float4 xl = two ? f.x_lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 vl = two ? f.v_lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         if (f.mode & kFinKickSync) {
-          v.x = fmaf(h, a.x, v.x);
-          v.y = fmaf(h, a.y, v.y);
-          v.z = fmaf(h, a.z, v.z);
+          if (two) {
+            comp_axpy(v, vl, h, a);
+          } else {
+            v.x = fmaf(h, a.x, v.x);
+            v.y = fmaf(h, a.y, v.y);
+            v.z = fmaf(h, a.z, v.z);
+          }
         }
         if (f.mode & kFinDiag) {
           const double m = x.w;
@@ -110,16 +130,27 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
           dv[7] = m * (px * vy - py * vx);
         }
         if (f.mode & kFinKickDrift) {
-          v.x = fmaf(h, a.x, v.x);
-          v.y = fmaf(h, a.y, v.y);
-          v.z = fmaf(h, a.z, v.z);
-          x.x = fmaf(dt, v.x, x.x);
-          x.y = fmaf(dt, v.y, x.y);
-          x.z = fmaf(dt, v.z, x.z);
+          if (two) {
+            comp_axpy(v, vl, h, a);
+            // drift with the full two-float velocity
+            const float4 vv = make_float4(v.x + vl.x, v.y + vl.y, v.z + vl.z, 0.f);
+            comp_axpy(x, xl, dt, vv);
+          } else {
+            v.x = fmaf(h, a.x, v.x);
+            v.y = fmaf(h, a.y, v.y);
+            v.z = fmaf(h, a.z, v.z);
+            x.x = fmaf(dt, v.x, x.x);
+            x.y = fmaf(dt, v.y, x.y);
+            x.z = fmaf(dt, v.z, x.z);
+          }
           f.pos[i] = x;
           if (f.trace_next) f.trace_next[i] = x;
         }
         f.vel[i] = v;
+        if (two) {
+          f.x_lo[i] = xl;
+          f.v_lo[i] = vl;
+        }
       }
     }
   }
@@ -140,7 +171,8 @@ __global__ void __launch_bounds__(kFinThreads) diag_reduce_kernel(const double *
 // First half-kick and drift from a caller-supplied acceleration (NBODY_ACC_VALID).
 // Batched runs pass sys_of / sys for the per-system step size.
 __global__ void kick_drift_kernel(float4 *pos, float4 *vel, const float4 *acc, int n, float dt,
-                                  float4 *trace1, const int *sys_of, const SysInfo *sys) {
+                                  float4 *trace1, const int *sys_of, const SysInfo *sys,
+                                  float4 *x_lo, float4 *v_lo) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (sys_of) {
@@ -151,12 +183,21 @@ __global__ void kick_drift_kernel(float4 *pos, float4 *vel, const float4 *acc, i
   float4 x = pos[i], v = vel[i];
   const float4 a = acc[i];
   const float h = 0.5f * dt;
-  v.x = fmaf(h, a.x, v.x);
-  v.y = fmaf(h, a.y, v.y);
-  v.z = fmaf(h, a.z, v.z);
-  x.x = fmaf(dt, v.x, x.x);
-  x.y = fmaf(dt, v.y, x.y);
-  x.z = fmaf(dt, v.z, x.z);
+  if (x_lo) {
+    float4 xl = x_lo[i], vl = v_lo[i];
+    comp_axpy(v, vl, h, a);
+    const float4 vv = make_float4(v.x + vl.x, v.y + vl.y, v.z + vl.z, 0.f);
+    comp_axpy(x, xl, dt, vv);
+    x_lo[i] = xl;
+    v_lo[i] = vl;
+  } else {
+    v.x = fmaf(h, a.x, v.x);
+    v.y = fmaf(h, a.y, v.y);
+    v.z = fmaf(h, a.z, v.z);
+    x.x = fmaf(dt, v.x, x.x);
+    x.y = fmaf(dt, v.y, x.y);
+    x.z = fmaf(dt, v.z, x.z);
+  }
   pos[i] = x;
   vel[i] = v;
   if (trace1) trace1[i] = x;

@@ -36,6 +36,8 @@ struct FinalizeArgs {
   float4 *acc;
   float4 *acc_lo;        // may be null
   float4 *trace_next;    // positions after the drift, or null
+  float4 *x_lo;          // compensated state: low parts of x and v, or null
+  float4 *v_lo;
   int mode;
   double *diag_part;     // [gridDim.x][8]
 };

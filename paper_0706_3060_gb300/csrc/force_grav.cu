@@ -13,6 +13,13 @@ const TileDesc *grav_tiles(int *count) {
       TileImpl<kLawGrav, 128, 4, 1, 256>::desc(),  // 3: 512
       TileImpl<kLawGrav, 128, 2, 4, 256>::desc(),  // 4: 64 targets, 4 j-lanes (small N)
       TileImpl<kLawGrav, 64, 2, 8, 128>::desc(),   // 5: 16 targets, 8 j-lanes (tiny N)
+      // packed f32x2 math over source pairs
+      TileImpl<kLawGrav, 256, 2, 1, 256, true>::desc(),  // 6: 512 targets
+      TileImpl<kLawGrav, 256, 4, 1, 256, true>::desc(),  // 7: 1024
+      TileImpl<kLawGrav, 128, 4, 1, 256, true>::desc(),  // 8: 512
+      TileImpl<kLawGrav, 128, 2, 1, 256, true>::desc(),  // 9: 256
+      TileImpl<kLawGrav, 256, 2, 1, 512, true>::desc(),  // 10: 512, longer j-tiles
+      TileImpl<kLawGrav, 256, 3, 1, 256, true>::desc(),  // 11: 768
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;

@@ -45,6 +45,7 @@ struct WorkItem {
 struct ForceArgs {
   const float4 *pos;   // (x, y, z, m)
   const float4 *prm;   // LJC (q~, s~, e~, type) or null
+  const float4 *jpair; // packed gravity kernels: j-pairs (x0 x1 y0 y1)(z0 z1 m0 m1)
   float4 *part_hi;     // [slices][stride]
   float4 *part_lo;     // [slices][stride]
   long long stride;    // elements per slice
@@ -92,6 +93,33 @@ __device__ __forceinline__ void grav_pair(const float4 pj, float xi, float yi, f
   if (POT) acc.w += my;
 }
 
+// The same gravity pair for two sources at once with packed f32x2 arithmetic
+// (FADD2/FFMA2/FMUL2 issue one instruction for two lanes of work); the two
+// halves of each accumulator are the even and odd sources of the j-tile.
+template <bool POT, bool PRECISE>
+__device__ __forceinline__ void grav_pair2(float2 X, float2 Y, float2 Z, float2 M, float2 nxi,
+                                           float2 nyi, float2 nzi, float2 eps2, float2 &ax,
+                                           float2 &ay, float2 &az, float2 &pot) {
+  const float2 dx = __fadd2_rn(X, nxi);
+  const float2 dy = __fadd2_rn(Y, nyi);
+  const float2 dz = __fadd2_rn(Z, nzi);
+  float2 s2 = __ffma2_rn(dz, dz, eps2);
+  s2 = __ffma2_rn(dy, dy, s2);
+  s2 = __ffma2_rn(dx, dx, s2);
+  float2 y = make_float2(rsqrt_hw(s2.x), rsqrt_hw(s2.y));
+  if (PRECISE) {
+    const float2 hs = __fmul2_rn(s2, make_float2(-0.5f, -0.5f));
+    const float2 t = __ffma2_rn(hs, __fmul2_rn(y, y), make_float2(1.5f, 1.5f));
+    y = __fmul2_rn(y, t);
+  }
+  const float2 my = __fmul2_rn(M, y);
+  const float2 w = __fmul2_rn(my, __fmul2_rn(y, y));
+  ax = __ffma2_rn(w, dx, ax);
+  ay = __ffma2_rn(w, dy, ay);
+  az = __ffma2_rn(w, dz, az);
+  if (POT) pot = __fadd2_rn(pot, my);
+}
+
 // LJ 12-6 + Coulomb (Table 1 LJC(constant)) with pre-scaled parameters:
 // q~ = q sqrt(k/eps_r), s~ = sigma/2, e~ = sqrt(24 eps), so that
 // q~i q~j = k qi qj / eps_r, s~i + s~j = sigma_ij, e~i e~j = 24 eps_ij.
@@ -137,9 +165,10 @@ struct ForceTile {
 };
 
 // ---- the kernel -------------------------------------------------------------------
-template <int LAW, int NT, int I, int SW, int JT, bool POT, bool PRECISE>
+template <int LAW, int NT, int I, int SW, int JT, bool POT, bool PRECISE, bool PK = false>
 __global__ void __launch_bounds__(NT + 32) force_kernel(const ForceArgs a) {
   using T = ForceTile<LAW, NT, I, SW, JT>;
+  static_assert(!PK || (LAW == kLawGrav && SW == 1), "packed path: gravity, one j-lane");
   constexpr int NWARPS = NT / 32;
   constexpr int SLOTS = T::kSlots;
   constexpr int TI = T::kTileI;
@@ -182,10 +211,12 @@ __global__ void __launch_bounds__(NT + 32) force_kernel(const ForceArgs a) {
       if (flags & kChunkEnd) {
         mbar_arrive(&full_bar[st]);
       } else {
-        const uint32_t bytes = uint32_t(len) * 16u;
+        // Packed layout: a tile of len sources is ceil(len/2) pairs of two
+        // float4; the odd tail reads the zero-mass pad after the last source.
+        const uint32_t bytes = uint32_t(PK ? (len + 1) & ~1 : len) * 16u;
         const bool with_prm = (LAW == kLawLJC) || (LAW == kLawMixed && w.law == kLawLJC);
         mbar_arrive_expect_tx(&full_bar[st], with_prm ? 2u * bytes : bytes);
-        tma_load_1d(sm_pos + st * JT, a.pos + cj0, bytes, &full_bar[st]);
+        tma_load_1d(sm_pos + st * JT, (PK ? a.jpair : a.pos) + cj0, bytes, &full_bar[st]);
         if (with_prm) tma_load_1d(sm_prm + st * JT, a.prm + cj0, bytes, &full_bar[st]);
       }
       ++it;
@@ -247,6 +278,7 @@ __global__ void __launch_bounds__(NT + 32) force_kernel(const ForceArgs a) {
   float qi[I], si[I], ei[I];
   int ig[I];
   float4 p[I], hi[I], lo[I];
+  float2 pax[PK ? I : 1], pay[PK ? I : 1], paz[PK ? I : 1], ppt[PK ? I : 1];
   WorkItem cur{};
   int cur_law = LAW == kLawLJC ? kLawLJC : kLawGrav;
 
@@ -280,6 +312,7 @@ __global__ void __launch_bounds__(NT + 32) force_kernel(const ForceArgs a) {
         hi[r] = make_float4(0.f, 0.f, 0.f, 0.f);
         lo[r] = make_float4(0.f, 0.f, 0.f, 0.f);
         p[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (PK) pax[r] = pay[r] = paz[r] = ppt[r] = make_float2(0.f, 0.f);
       }
     }
     const float4 *sp = sm_pos + st * JT;
@@ -287,7 +320,43 @@ __global__ void __launch_bounds__(NT + 32) force_kernel(const ForceArgs a) {
     const bool masked = (cj0 < cur.i0 + cur.ni) && (cur.i0 < cj0 + len);
     const float eps2 = cur.eps2;
 
-    if (!T::kPrm || cur_law == kLawGrav) {
+    if (PK) {
+      if (!masked) {
+        const float2 e2 = make_float2(eps2, eps2);
+        const int npairs = (len + 1) >> 1;
+        float2 nx[PK ? I : 1], ny[PK ? I : 1], nz[PK ? I : 1];
+#pragma unroll
+        for (int r = 0; r < I; ++r) {
+          nx[r] = make_float2(-xi[r], -xi[r]);
+          ny[r] = make_float2(-yi[r], -yi[r]);
+          nz[r] = make_float2(-zi[r], -zi[r]);
+        }
+#pragma unroll 2
+        for (int pp = 0; pp < npairs; ++pp) {
+          const float4 A = sp[2 * pp];
+          const float4 B = sp[2 * pp + 1];
+          const float2 X = make_float2(A.x, A.y), Y = make_float2(A.z, A.w);
+          const float2 Z = make_float2(B.x, B.y), M = make_float2(B.z, B.w);
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            grav_pair2<POT, PRECISE>(X, Y, Z, M, nx[r], ny[r], nz[r], e2, pax[r], pay[r],
+                                     paz[r], ppt[r]);
+        }
+      } else {
+        // Diagonal tile: one source at a time from the pair layout, self masked.
+        for (int jj = 0; jj < len; ++jj) {
+          const float4 A = sp[2 * (jj >> 1)];
+          const float4 B = sp[2 * (jj >> 1) + 1];
+          const bool odd = jj & 1;
+          const float4 pj = make_float4(odd ? A.y : A.x, odd ? A.w : A.z, odd ? B.y : B.x,
+                                        odd ? B.w : B.z);
+          const int jg = cj0 + jj;
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            grav_pair<POT, PRECISE, true>(pj, xi[r], yi[r], zi[r], eps2, p[r], jg == ig[r]);
+        }
+      }
+    } else if (!T::kPrm || cur_law == kLawGrav) {
       if (!masked && len == JT) {
 #pragma unroll 4
         for (int jj = jl; jj < JT; jj += SW) {
@@ -353,6 +422,13 @@ __global__ void __launch_bounds__(NT + 32) force_kernel(const ForceArgs a) {
     // Fold this j-tile's plain FP32 partial into the compensated (hi, lo).
 #pragma unroll
     for (int r = 0; r < I; ++r) {
+      if (PK) {
+        p[r].x += pax[r].x + pax[r].y;
+        p[r].y += pay[r].x + pay[r].y;
+        p[r].z += paz[r].x + paz[r].y;
+        if (POT) p[r].w += ppt[r].x + ppt[r].y;
+        pax[r] = pay[r] = paz[r] = ppt[r] = make_float2(0.f, 0.f);
+      }
       if (a.comp) {
         comp_add(hi[r].x, lo[r].x, p[r].x);
         comp_add(hi[r].y, lo[r].y, p[r].y);

@@ -20,6 +20,7 @@ struct TileDesc {
   int tile_i; // targets per item
   int threads;
   size_t smem;
+  bool packed;  // gravity sources in the pair-interleaved layout (f32x2 math)
   ForceLauncher launch;
   ForceOccupancy occupancy;
 };
@@ -29,13 +30,13 @@ const TileDesc *grav_tiles(int *count);
 const TileDesc *ljc_tiles(int *count);
 const TileDesc *mixed_tiles(int *count);
 
-template <int LAW, int NT, int I, int SW, int JT>
+template <int LAW, int NT, int I, int SW, int JT, bool PK = false>
 struct TileImpl {
   using T = ForceTile<LAW, NT, I, SW, JT>;
   template <bool POT, bool PRE>
   static cudaError_t go(const ForceArgs &a, int grid, cudaStream_t s) {
-    auto k = force_kernel<LAW, NT, I, SW, JT, POT, PRE>;
-    if (T::kSmemBytes > 48 * 1024) {
+    auto k = force_kernel<LAW, NT, I, SW, JT, POT, PRE, PK>;
+    if (T::kSmemBytes > 32 * 1024) {
       cudaError_t e =
           cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
       if (e != cudaSuccess) return e;
@@ -50,8 +51,8 @@ struct TileImpl {
   }
   static int occupancy() {
     int nb = 0;
-    auto k = force_kernel<LAW, NT, I, SW, JT, false, false>;
-    if (T::kSmemBytes > 48 * 1024)
+    auto k = force_kernel<LAW, NT, I, SW, JT, false, false, PK>;
+    if (T::kSmemBytes > 32 * 1024)
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, T::kThreads, T::kSmemBytes) !=
         cudaSuccess)
@@ -59,7 +60,7 @@ struct TileImpl {
     return nb > 0 ? nb : 1;
   }
   static TileDesc desc() {
-    return TileDesc{LAW, NT, I, SW, JT, T::kTileI, T::kThreads, T::kSmemBytes, &launch,
+    return TileDesc{LAW, NT, I, SW, JT, T::kTileI, T::kThreads, T::kSmemBytes, PK, &launch,
                     &occupancy};
   }
 };

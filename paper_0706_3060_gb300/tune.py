@@ -1,0 +1,131 @@
+"""Autotuner for the all-pairs force kernels.
+
+For each law and problem size it times every compiled tile configuration
+(threads x targets-per-thread x j-lanes) with several j-splits through the
+C ABI, keeps the fastest, installs it with nbody_set_tuned for that size bucket
+(floor(log2 N)), and stores the table in a JSON cache keyed by the GPU name and
+SM count. ``load_cache()`` re-installs a stored table on the same kind of GPU.
+
+    python -m paper_0706_3060_gb300.tune --law grav --n 1024 16384 262144
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+
+import numpy as np
+
+from . import api
+from ._lib import LAW_GRAV, LAW_LJC
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+
+
+def _gpu_key(torch):
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}/{p.multi_processor_count}"
+
+
+def _inputs(torch, law, n, seed=0):
+    rng = np.random.default_rng(seed)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if law == LAW_GRAV:
+        x = rng.standard_normal((n, 3)).astype(np.float32)
+        pos = np.concatenate([x, np.full((n, 1), 1.0 / n, np.float32)], 1)
+        return torch.from_numpy(pos).to(dev).contiguous(), None
+    # atoms on a jittered cubic lattice (spacing 3.6 A, as in the 45 A / 8192 sphere)
+    side = int(math.ceil(n ** (1.0 / 3.0)))
+    g = np.stack(np.meshgrid(*[np.arange(side)] * 3, indexing="ij"), -1).reshape(-1, 3)[:n]
+    x = (g * 3.6 + rng.uniform(-0.5, 0.5, (n, 3))).astype(np.float32)
+    pos = np.concatenate([x, np.full((n, 1), 12.0, np.float32)], 1)
+    pos_t = torch.from_numpy(pos).to(dev).contiguous()
+    q = torch.from_numpy(rng.uniform(-0.8, 0.8, n)).to(dev)
+    s = torch.from_numpy(rng.uniform(2.5, 3.8, n)).to(dev)
+    e = torch.from_numpy(rng.uniform(0.05, 0.2, n)).to(dev)
+    t = torch.from_numpy(rng.integers(0, 4, n).astype(np.int32)).to(dev)
+    return pos_t, api.pack_ljc(q, s, e, t)
+
+
+def time_config(torch, law, pos, prm, tile, jsplit, reps=5):
+    """Median device milliseconds of one force evaluation."""
+    acc = torch.empty_like(pos)
+    kw = dict(law=law, eps=0.01, tile=tile, jsplit=jsplit, out=acc)
+    api.forces(pos, prm, **kw)
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        api.forces(pos, prm, **kw)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def tune(law: int, sizes, jsplits=(0, 1, 2, 4, 8, 16, 32), reps=5, verbose=True):
+    import torch
+    table = {}
+    for n in sizes:
+        pos, prm = _inputs(torch, law, n)
+        results = []
+        for tile in range(api.tile_count(law)):
+            info = api.tile_info(law, tile)
+            tile_i = info["threads"] // info["j_lanes"] * info["i_per_thread"]
+            for js in jsplits:
+                if js > 0 and js * info["j_tile"] > n:
+                    continue
+                if js == 0 and tile_i > 4 * n:
+                    continue
+                ms = time_config(torch, law, pos, prm, tile, js, reps)
+                results.append((ms, tile, js))
+                if verbose:
+                    print(f"law={law} n={n} tile={tile} jsplit={js}: {ms:.4f} ms "
+                          f"({n * n / ms / 1e6:.1f} G pairs/s)", flush=True)
+        ms, tile, js = min(results)
+        api.set_tuned(law, n, tile, js)
+        table[str(int(math.floor(math.log2(n))))] = {"n": n, "tile": tile, "jsplit": js, "ms": ms,
+                                                     "gpairs_per_s": n * n / ms / 1e6}
+    return table
+
+
+def save_cache(law: int, table: dict, path: str = CACHE):
+    import torch
+    data = json.load(open(path)) if os.path.exists(path) else {}
+    key = _gpu_key(torch)
+    data.setdefault(key, {})[str(law)] = table
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+
+
+def load_cache(path: str = CACHE) -> int:
+    """Install stored (tile, jsplit) entries for this GPU; returns how many."""
+    import torch
+    if not os.path.exists(path) or not torch.cuda.is_available():
+        return 0
+    data = json.load(open(path)).get(_gpu_key(torch), {})
+    count = 0
+    for law, table in data.items():
+        for bucket, ent in table.items():
+            api.set_tuned(int(law), 2 ** int(bucket), int(ent["tile"]), int(ent["jsplit"]))
+            count += 1
+    return count
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--law", choices=["grav", "ljc"], default="grav")
+    ap.add_argument("--n", type=int, nargs="+", default=[1024, 4096, 16384, 65536, 262144])
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--save", action="store_true")
+    a = ap.parse_args()
+    law = LAW_GRAV if a.law == "grav" else LAW_LJC
+    table = tune(law, a.n, reps=a.reps)
+    print(json.dumps(table))
+    if a.save:
+        save_cache(law, table)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,154 @@
+"""GPU parity of the reverse-mode path: single force VJPs (gravity and LJC, with
+mass and per-type sigma/epsilon derivatives) against the FP64 oracle's
+block-by-block Jacobian transpose, and the checkpointed reverse leapfrog
+(torch.autograd.Function) against the oracle's reverse leapfrog and against
+central finite differences of the oracle's FP64 loss."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from gpu_util import dev, grav_tensors, lib, ljc_tensors, oracle_ljc_system
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(got, ref):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("n", [3, 257, 1000, 9000])
+def test_grav_vjp(n):
+    nb = lib()
+    g = workloads.plummer(n, seed=60 + n, eps=0.01)
+    pos, _ = grav_tensors(g)
+    lam = np.random.default_rng(n).standard_normal((n, 4)).astype(np.float32)
+    gx, gm, _ = nb.adjoint(pos, torch.from_numpy(lam).to(dev()), eps=float(np.float32(g.eps)),
+                           alpha=1.0)
+    x, _, m = g.f32_as_f64()
+    rg, rm = oracle.grav_vjp(x, m, lam[:, :3].astype(np.float64), eps=float(np.float32(g.eps)))
+    assert _rel(gx[:, :3].cpu().numpy(), rg) <= 2e-5
+    assert _rel(gm.cpu().numpy(), rm) <= 2e-5
+
+
+def test_grav_vjp_alpha_and_accumulate():
+    nb = lib()
+    g = workloads.plummer(500, seed=3, eps=0.02)
+    pos, _ = grav_tensors(g)
+    lam = torch.randn((500, 4), device=dev())
+    gx1, gm1, _ = nb.adjoint(pos, lam, eps=float(np.float32(g.eps)), alpha=1.0)
+    gx2, gm2, _ = nb.adjoint(pos, lam, eps=float(np.float32(g.eps)), alpha=0.5)
+    nb.adjoint(pos, lam, eps=float(np.float32(g.eps)), alpha=0.5, grad_x=gx2, grad_m=gm2,
+               accumulate=True)
+    torch.testing.assert_close(gx2[:, :3], gx1[:, :3], rtol=1e-5, atol=1e-6)
+    torch.testing.assert_close(gm2, gm1, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("n", [20, 600, 3000])
+def test_ljc_vjp(n):
+    nb = lib()
+    s = workloads.ljc_sphere(n, seed=70 + n)
+    pos, _, prm = ljc_tensors(s)
+    lam = np.random.default_rng(n).standard_normal((n, 4)).astype(np.float32)
+    gx, gm, gt = nb.adjoint(pos, torch.from_numpy(lam).to(dev()), prm, alpha=1.0)
+    sysm, x, _ = oracle_ljc_system(s)
+    rg, rm, rs, re = sysm.vjp(x, lam[:, :3].astype(np.float64))
+    assert _rel(gx[:, :3].cpu().numpy(), rg) <= 2e-5
+    assert _rel(gm.cpu().numpy(), rm) <= 2e-5
+    got_t = gt.cpu().numpy()
+    assert _rel(got_t[:4], rs) <= 2e-5
+    assert _rel(got_t[4:], re) <= 2e-5
+
+
+def _grav_autograd_grads(g, dt, nsteps, k, target):
+    nb = lib()
+    from paper_0706_3060_gb300.autograd import leapfrog
+    x, v, m = g.f32()
+    d = dev()
+    x0 = torch.from_numpy(x).to(d).requires_grad_(True)
+    v0 = torch.from_numpy(v).to(d).requires_grad_(True)
+    m0 = torch.from_numpy(m).to(d).requires_grad_(True)
+    xT, _ = leapfrog(x0, v0, m0, dt=dt, nsteps=nsteps, k=k, eps=float(np.float32(g.eps)))
+    tgt = torch.from_numpy(target.astype(np.float32)).to(d)
+    loss = ((xT - tgt) ** 2).sum() / xT.shape[0]
+    loss.backward()
+    nb.sync_check()
+    return x0.grad.cpu().numpy(), v0.grad.cpu().numpy(), m0.grad.cpu().numpy(), float(loss)
+
+
+def test_reverse_leapfrog_vs_oracle_gradient():
+    """N = 1024 Plummer, 60 steps at dt = 1e-4, checkpoints every 20 steps."""
+    g = workloads.plummer(1024, seed=4, eps=0.01)
+    target = workloads.perturbed_target(g.f32_as_f64()[0], seed=4)
+    gx, gv, gm, _ = _grav_autograd_grads(g, 1e-4, 60, 20, target)
+    x, v, m = g.f32_as_f64()
+    sysm = oracle.GravSystem(m, eps=float(np.float32(g.eps)))
+    xs, _ = oracle.leapfrog(sysm, x, v, 1e-4, 60, store=True)
+    ref = oracle.adjoint_leapfrog(sysm, x, v, 1e-4, 60, oracle.target_loss_grad(xs[-1], target),
+                                  xs=xs)
+    assert _rel(gx, ref["x0"]) <= 1e-4
+    assert _rel(gv, ref["v0"]) <= 1e-4
+    assert _rel(gm, ref["m"]) <= 1e-3
+
+
+def test_reverse_leapfrog_checkpoint_invariance():
+    """k = 7 (ragged last chunk) and k = 60 (one chunk) give the same gradients."""
+    g = workloads.plummer(777, seed=9, eps=0.02)
+    target = workloads.perturbed_target(g.f32_as_f64()[0], seed=4)
+    a = _grav_autograd_grads(g, 1e-4, 60, 7, target)
+    b = _grav_autograd_grads(g, 1e-4, 60, 60, target)
+    for u, w in zip(a[:3], b[:3]):
+        np.testing.assert_allclose(u, w, rtol=1e-5, atol=1e-9 * np.abs(w).max())
+
+
+def test_reverse_leapfrog_vs_finite_differences():
+    """Directional central differences (h = 1e-4) of the FP64 oracle loss."""
+    g = workloads.plummer(256, seed=12, eps=0.05)
+    dt, T = 1e-3, 40
+    target = workloads.perturbed_target(g.f32_as_f64()[0], seed=4)
+    gx, gv, gm, _ = _grav_autograd_grads(g, dt, T, 20, target)
+    x, v, m = g.f32_as_f64()
+    eps = float(np.float32(g.eps))
+
+    def loss(x0, v0, m0):
+        xT, _ = oracle.leapfrog(oracle.GravSystem(m0, eps=eps), x0, v0, dt, T)
+        return oracle.target_loss(xT, target)
+
+    h = 1e-4
+    for d in workloads.random_directions((256, 7), 4, seed=5):
+        dx, dv, dm = d[:, :3], d[:, 3:6], d[:, 6] * 1e-2
+        fd = (loss(x + h * dx, v + h * dv, m + h * dm) - loss(x - h * dx, v - h * dv, m - h * dm)) / (2 * h)
+        an = np.sum(gx * dx) + np.sum(gv * dv) + np.sum(gm * dm)
+        assert abs(fd - an) <= 1e-3 * abs(an) + 1e-9, (fd, an)
+
+
+def test_ljc_reverse_leapfrog_vs_oracle():
+    nb = lib()
+    from paper_0706_3060_gb300.autograd import leapfrog
+    s = workloads.ljc_sphere(300, seed=14, radius=20.0)
+    x, v, m, q, st, et = s.f32()
+    d = dev()
+    x0 = torch.from_numpy(x).to(d).requires_grad_(True)
+    v0 = torch.from_numpy(v).to(d).requires_grad_(True)
+    m0 = torch.from_numpy(m).to(d).requires_grad_(True)
+    sig = torch.from_numpy(st).to(d).requires_grad_(True)
+    eps = torch.from_numpy(et).to(d).requires_grad_(True)
+    dt, T = 1e-4, 12
+    xT, _ = leapfrog(x0, v0, m0, dt=dt, nsteps=T, k=5, law=nb.LAW_LJC,
+                     q=torch.from_numpy(q.astype(np.float64)).to(d),
+                     types=torch.from_numpy(s.types).to(d), sig_t=sig, eps_t=eps)
+    target = workloads.perturbed_target(x.astype(np.float64), seed=4)
+    loss = ((xT - torch.from_numpy(target.astype(np.float32)).to(d)) ** 2).sum() / 300
+    loss.backward()
+    sysm, xo, vo = oracle_ljc_system(s)
+    xs, _ = oracle.leapfrog(sysm, xo, vo, dt, T, store=True)
+    ref = oracle.adjoint_leapfrog(sysm, xo, vo, dt, T, oracle.target_loss_grad(xs[-1], target),
+                                  xs=xs)
+    assert _rel(x0.grad.cpu().numpy(), ref["x0"]) <= 1e-4
+    assert _rel(v0.grad.cpu().numpy(), ref["v0"]) <= 1e-4
+    assert _rel(m0.grad.cpu().numpy(), ref["m"]) <= 1e-3
+    assert _rel(sig.grad.cpu().numpy(), ref["sig_t"]) <= 1e-3
+    assert _rel(eps.grad.cpu().numpy(), ref["eps_t"]) <= 1e-3

@@ -131,3 +131,24 @@ def test_ljc_steps():
     # velocities start at 0: compare against the velocity scale after 5 steps
     ev = traj_errors(vel[:, :3].cpu().numpy(), vs[-1])
     assert ev[0] <= 1e-5 and ev[1] <= 1e-4, ev
+
+
+def test_two_float_state_removes_rounding_drift():
+    """300 steps: with the compensated (hi, lo) state the positions stay at the
+    FP32 rounding of the FP64 trajectory; plain FP32 updates drift further."""
+    nb = lib()
+    g = workloads.plummer(2048, seed=17, eps=0.01)
+    eps = float(np.float32(g.eps))
+    sysm, xs, vs = _grav_ref_traj(g, 1e-4, 300)
+    errs = {}
+    for comp in (False, True):
+        pos, vel = grav_tensors(g)
+        acc = torch.empty_like(pos)
+        lo = torch.zeros((2 * 2048, 4), device=dev()) if comp else None
+        nb.step(pos, vel, acc, dt=1e-4, nsteps=300, eps=eps, state_lo=lo)
+        x = pos[:, :3].double().cpu().numpy()
+        if comp:
+            x = x + lo[:2048, :3].double().cpu().numpy()
+        errs[comp] = float(np.sqrt(np.mean(np.sum((x - xs[-1]) ** 2, axis=1))))
+    assert errs[True] <= 0.5 * errs[False], errs
+    assert errs[True] <= 1e-7, errs

@@ -77,7 +77,8 @@ def test_bad_arguments_rejected_without_gpu(lib):
     assert lib.nbody_forces(None, None, None, None, 0, ctypes.byref(p), None) == 0
     # negative steps
     assert lib.nbody_step(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), None, 8,
-                          ctypes.c_float(1e-3), -1, 0, None, None, ctypes.byref(p), None) == 1
+                          ctypes.c_float(1e-3), -1, 0, None, None, None, ctypes.byref(p),
+                          None) == 1
 
 
 def test_no_device_is_reported(lib):
