@@ -144,6 +144,27 @@ int nbody_pack_ljc(const double *q, const double *sigma, const double *eps,
 int nbody_forces(const void *pos_m, const void *prm, void *acc, void *acc_lo, int64_t n,
                  const nbody_params *params, nbody_stream_t stream);
 
+/* nbody_forces_static -- nbody_forces for callers that cannot allocate device
+ * memory (a fixed memory budget set at start-up, an allocator owned by another
+ * framework, a real-time loop that must not block in cudaMalloc). The paper has
+ * no counterpart; it is the same force evaluation, with its scratch in one
+ * static __device__ array of 32 MiB inside the library (held by every GPU that
+ * loads the library until the process exits) instead of an on-demand
+ * workspace. It calls no cudaMalloc, cudaFree or allocating routine.
+ *   pos_m, prm, acc, n, params, stream : as in nbody_forces (device pointers
+ *   only; no acc_lo; NBODY_COMPUTE_POT, NBODY_PRECISE_RSQRT and
+ *   NBODY_NO_COMPENSATION are honoured).
+ * n beyond what the scratch holds (about 699,000 particles) is rejected with
+ * NBODY_EINVAL before any GPU work; large n may run with fewer j-slices than
+ * nbody_forces would use. The first call on each device, with that device
+ * current, looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture. All calls share the array, which
+ * keeps the last call's contents; each call rewrites what it reads and clears
+ * its error word, but calls whose GPU work overlaps (e.g. on two streams) race
+ * on the array: serialize them. */
+int nbody_forces_static(const void *pos_m, const void *prm, void *acc, int64_t n,
+                        const nbody_params *params, nbody_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * nbody_step -- nsteps kick-drift-kick leapfrog steps of size dt (the update
  * step of Sec. 1), each consuming one all-pairs force evaluation:

@@ -1,0 +1,137 @@
+// api_static.cu -- nbody_forces_static: the force evaluation of nbody_forces for
+// callers that must not allocate device memory.
+//
+// Some callers cannot call cudaMalloc (or anything that does): code that runs
+// under a memory budget fixed at start-up, a host process whose allocator is
+// owned by another framework, or a real-time loop where an allocation could
+// block or fail in the middle of a run. nbody_forces grows a per-stream
+// workspace on demand; this entry point instead uses one scratch array that is
+// part of the library image itself.
+//
+// The scratch is a file-scope __device__ array of kStaticScratchBytes. Every
+// GPU that loads this library holds it until the process exits. In host code
+// the array's name is only a host-side stand-in, not a device address, so the
+// first call on each device (with that device current) asks the runtime for
+// the real address with cudaGetSymbolAddress and keeps it; make that first
+// call before any stream capture. All calls share the array and it keeps the
+// last call's contents: each call overwrites every scratch element it reads
+// before reading it and clears the error word, so nothing stale leaks into a
+// result, but two calls whose work overlaps on the GPU (for example on two
+// streams) race on the same memory and must be serialized by the caller.
+#include <cuda_runtime.h>
+
+#include <initializer_list>
+#include <mutex>
+
+#include "api_common.h"
+#include "aux_types.h"
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB
+constexpr int kMaxDevices = 64;
+
+// Partial sums and the pair-interleaved copy of the sources.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+// Bounded-wait error flag of this entry point's kernels (cleared every call).
+static __device__ __align__(256) int g_static_err;
+
+struct StaticAddr {
+  unsigned char *scratch = nullptr;
+  int *err = nullptr;
+};
+std::mutex g_static_mu;
+StaticAddr g_static_addr[kMaxDevices];
+
+int static_addresses(int dev, StaticAddr *out) {
+  if (dev < 0 || dev >= kMaxDevices)
+    return nbody::set_error_msg(NBODY_EUNSUPPORTED, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  StaticAddr &a = g_static_addr[dev];
+  if (!a.scratch) {
+    void *p = nullptr, *e = nullptr;
+    cudaError_t rc = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (rc == cudaSuccess) rc = cudaGetSymbolAddress(&e, g_static_err);
+    if (rc != cudaSuccess) {
+      cudaGetLastError();
+      return nbody::set_error_msg(NBODY_ECUDA, "cudaGetSymbolAddress failed: %s",
+                                  cudaGetErrorString(rc));
+    }
+    a.scratch = static_cast<unsigned char *>(p);
+    a.err = static_cast<int *>(e);
+  }
+  *out = a;
+  return NBODY_OK;
+}
+
+}  // namespace
+
+using namespace nbody;
+
+extern "C" int nbody_forces_static(const void *pos_m, const void *prm, void *acc, int64_t n,
+                                   const nbody_params *params, nbody_stream_t stream) {
+  clear_error();
+  if (!params) return set_error_msg(NBODY_EINVAL, "params is NULL");
+  if (n < 0 || n > 0x7fffffffLL)
+    return set_error_msg(NBODY_EINVAL, "n out of range: %lld", (long long)n);
+  if (n == 0) return NBODY_OK;
+  const nbody_params p = *params;
+  if (p.law != NBODY_LAW_GRAV && p.law != NBODY_LAW_LJC)
+    return set_error_msg(NBODY_EINVAL, "unknown law %d", p.law);
+  if (p.flags & ~(uint32_t)(NBODY_COMPUTE_POT | NBODY_PRECISE_RSQRT | NBODY_NO_COMPENSATION))
+    return set_error_msg(NBODY_EINVAL, "unsupported flag bits 0x%x", p.flags);
+  if (p.law == NBODY_LAW_LJC && !prm) return set_error_msg(NBODY_EINVAL, "LJC needs prm");
+  if (!(p.eps2 >= 0.0f)) return set_error_msg(NBODY_EINVAL, "eps2 must be >= 0");
+  if (!pos_m || !acc) return set_error_msg(NBODY_EINVAL, "pos_m and acc are required");
+  for (const void *q : {pos_m, prm, static_cast<const void *>(acc)})
+    if (q && !aligned16(q)) return set_error_msg(NBODY_EALIGN, "array not 16-byte aligned");
+  int cnt = 0;
+  tiles_for(p.law, &cnt);
+  if (p.tile < -1 || p.tile >= cnt) return set_error_msg(NBODY_EINVAL, "bad tile %d", p.tile);
+  if (p.jsplit < 0) return set_error_msg(NBODY_EINVAL, "bad jsplit %d", p.jsplit);
+
+  // Size check before touching the GPU: the pair copy of the sources plus two
+  // float4 partial sums per target must fit, with at least one j-slice.
+  const size_t jb = round_up(size_t(n + 1) * sizeof(float4), 256);
+  const size_t per_slice = round_up(size_t(n) * sizeof(float4), 256);
+  if (jb + 2 * per_slice > kStaticScratchBytes)
+    return set_error_msg(NBODY_EINVAL,
+                         "n = %lld needs %zu bytes of scratch; the static scratch of "
+                         "nbody_forces_static holds %zu bytes (n <= %zu)",
+                         (long long)n, jb + 2 * per_slice, kStaticScratchBytes,
+                         (kStaticScratchBytes - 1024) / (3 * sizeof(float4)));
+
+  int dev = 0, sms = 0;
+  NB_TRY(check_device(&dev, &sms));
+  for (const void *q : {pos_m, prm, static_cast<const void *>(acc)})
+    if (q && is_host_pointer(q))
+      return set_error_msg(NBODY_EINVAL, "nbody_forces_static takes device pointers only");
+  StaticAddr sa;
+  NB_TRY(static_addresses(dev, &sa));
+
+  Plan1 plan{};
+  NB_TRY(plan_single(p.law, n, p.tile, p.jsplit, sms, &plan));
+  const size_t max_slices = (kStaticScratchBytes - jb) / (2 * per_slice);
+  if (size_t(plan.slices) > max_slices)  // fewer j-slices so the partials fit
+    NB_TRY(plan_single(p.law, n, p.tile, int(max_slices), sms, &plan));
+  float4 *jbuf = reinterpret_cast<float4 *>(sa.scratch);
+  float4 *part_hi = reinterpret_cast<float4 *>(sa.scratch + jb);
+  float4 *part_lo = reinterpret_cast<float4 *>(sa.scratch + jb + size_t(plan.slices) * per_slice);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  NB_CUDA(cudaMemsetAsync(sa.err, 0, sizeof(int), s));
+  NB_TRY(launch_forces(static_cast<const float4 *>(pos_m), static_cast<const float4 *>(prm),
+                       p.law, p.flags, p.eps2, int(n), plan, part_hi, part_lo, jbuf, sa.err,
+                       (p.flags & NBODY_COMPUTE_POT) != 0, s));
+  FinalizeArgs f{};
+  f.part_hi = part_hi;
+  f.part_lo = part_lo;
+  f.stride = n;  // the force kernel indexes slice * n + i
+  f.slices = plan.slices;
+  f.n = int(n);
+  f.law = p.law;
+  f.G = p.G;
+  f.pos = const_cast<float4 *>(static_cast<const float4 *>(pos_m));
+  f.acc = static_cast<float4 *>(acc);
+  f.mode = kFinWriteAcc;
+  return launch_finalize(f, s, nullptr);
+}
