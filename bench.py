@@ -257,14 +257,16 @@ def main():
     if clk.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (sms * FP32_LANES_PER_SM * clk["sm_mhz"] * 1e6
                                                     / 1e12)
-    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(traffic_file):
-        try:
-            tr = json.load(open(traffic_file))
-            if tr.get("kernel_hash") == kernel_hash():
-                roof["traffic"] = tr.get("bytes_per_launch")
-        except Exception:
-            pass
+    # DRAM bytes per launch from the committed ncu summary, only if it was taken
+    # on the kernel that runs now (same sources and tuning table).
+    summary = os.path.join(ROOT, "profiles", "force_kernel_grav_plummer262144.md")
+    if os.path.exists(summary):
+        import re
+        txt = open(summary).read()
+        mh = re.search(r"^kernel_hash: (\S+)", txt, re.M)
+        mb = re.search(r"^dram_bytes_per_launch: (\d+)", txt, re.M)
+        if mh and mb and mh.group(1) == kernel_hash():
+            roof["traffic"] = int(mb.group(1))
 
     out = {"metric": metric_name(), "value": value, "unit": "G pair-interactions/s",
            "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": step_ms / K,
@@ -306,8 +308,9 @@ def main():
 def kernel_hash() -> str:
     import hashlib
     h = hashlib.sha1()
-    for f in ("force_kernel.cuh", "device_common.cuh", "force_grav.cu"):
-        with open(os.path.join(ROOT, "paper_0706_3060_gb300", "csrc", f), "rb") as fh:
+    for f in ("csrc/force_kernel.cuh", "csrc/device_common.cuh", "csrc/force_grav.cu",
+              "tuned.json"):
+        with open(os.path.join(ROOT, "paper_0706_3060_gb300", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -331,7 +334,120 @@ def extras(nb, torch, dev, g, eps):
     d = nb.step(pos, vel, a2, dt=DT, nsteps=100, eps=eps, report_every=100).cpu().numpy()
     E0, E1 = d[0, 0] + d[0, 1], d[1, 0] + d[1, 1]
     ex["energy_drift_100_steps"] = float((E1 - E0) / abs(E0))
+    ex.update(batched_extras(nb, torch, dev))
+    ex.update(adjoint_extras(nb, torch, dev))
     return ex
+
+
+def _ensemble_arrays(nb, torch, dev, ens):
+    """Concatenate an ensemble into shared float4 arrays and a system table."""
+    import workloads
+    total = sum(s.n for s in ens.systems)
+    pos = np.zeros((total, 4), np.float32)
+    vel = np.zeros((total, 4), np.float32)
+    q, sg, ep = np.zeros(total), np.full(total, 3.0), np.full(total, 0.1)
+    ty = np.zeros(total, np.int32)
+    table, off = [], 0
+    for s in ens.systems:
+        if isinstance(s, workloads.GravInput):
+            x, v, m = s.f32()
+            table.append(dict(offset=off, n=s.n, law=nb.LAW_GRAV, G=1.0,
+                              eps=float(np.float32(s.eps)), dt=1e-3))
+        else:
+            x, v, m, qq, st, et = s.f32()
+            q[off:off + s.n] = qq
+            sg[off:off + s.n] = st.astype(np.float64)[s.types]
+            ep[off:off + s.n] = et.astype(np.float64)[s.types]
+            ty[off:off + s.n] = s.types
+            table.append(dict(offset=off, n=s.n, law=nb.LAW_LJC, dt=1e-4))
+        pos[off:off + s.n, :3], pos[off:off + s.n, 3], vel[off:off + s.n, :3] = x, m, v
+        off += s.n
+    prm = nb.pack_ljc(torch.from_numpy(q).to(dev), torch.from_numpy(sg).to(dev),
+                      torch.from_numpy(ep).to(dev), torch.from_numpy(ty).to(dev),
+                      kq=332.0637 / 80.0)
+    return (torch.from_numpy(pos).to(dev).contiguous(), torch.from_numpy(vel).to(dev).contiguous(),
+            prm, table)
+
+
+def _time(torch, fn, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        best = min(best, time.perf_counter() - t0)
+    return best
+
+
+def batched_extras(nb, torch, dev, nsys=512, steps=50):
+    """512 systems, N log-uniform in [64, 4096], half gravity / half LJ + Coulomb,
+    50 leapfrog steps: one persistent launch per step under a CUDA graph, against
+    one nbody_step call per system."""
+    import workloads
+    ens = workloads.ensemble(nsys=nsys, seed=3)
+    pos, vel, prm, table = _ensemble_arrays(nb, torch, dev, ens)
+    acc = torch.zeros_like(pos)
+    plan = nb.BatchPlan(table)
+    p0, v0 = pos.clone(), vel.clone()
+
+    def batched():
+        pos.copy_(p0)
+        vel.copy_(v0)
+        plan.run(pos, vel, acc, prm, nsteps=steps, graph=True)
+
+    t_b = _time(torch, batched)
+    pairs = float(sum(s.n * s.n for s in ens.systems)) * (steps + 1)
+    views = [(pos[t["offset"]:t["offset"] + t["n"]], vel[t["offset"]:t["offset"] + t["n"]],
+              acc[t["offset"]:t["offset"] + t["n"]], prm[t["offset"]:t["offset"] + t["n"]], t)
+             for t in table]
+
+    def per_system():
+        pos.copy_(p0)
+        vel.copy_(v0)
+        for p, v, a, q, t in views:
+            if t["law"] == nb.LAW_GRAV:
+                nb.step(p, v, a, dt=t["dt"], nsteps=steps, eps=t["eps"])
+            else:
+                nb.step(p, v, a, q, dt=t["dt"], nsteps=steps)
+
+    t_s = _time(torch, per_system, reps=1)
+    return {"batched_systems": nsys, "batched_steps": steps,
+            "batched_system_steps_per_s": nsys * steps / t_b,
+            "batched_gpairs_per_s": pairs / t_b / 1e9,
+            "per_system_launch_system_steps_per_s": nsys * steps / t_s,
+            "batched_speedup_vs_per_system": t_s / t_b}
+
+
+def adjoint_extras(nb, torch, dev, n=16384, steps=200, k=20):
+    """Plummer N = 16384, 200 steps at dt = 1e-4, checkpoints every 20 steps:
+    backward (recompute + reverse sweep) time over forward time."""
+    import workloads
+    from paper_0706_3060_gb300.autograd import leapfrog
+    g = workloads.plummer(n, seed=4, eps=workloads.plummer_softening(n))
+    x, v, m = g.f32()
+    tgt = torch.from_numpy(workloads.perturbed_target(x.astype(np.float64), seed=4)
+                           .astype(np.float32)).to(dev)
+    eps = float(np.float32(g.eps))
+    best_f = best_b = float("inf")
+    for _ in range(3):
+        x0 = torch.from_numpy(x).to(dev).requires_grad_(True)
+        v0 = torch.from_numpy(v).to(dev).requires_grad_(True)
+        m0 = torch.from_numpy(m).to(dev).requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xT, _ = leapfrog(x0, v0, m0, dt=1e-4, nsteps=steps, k=k, eps=eps)
+        loss = ((xT - tgt) ** 2).sum() / n
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        best_f, best_b = min(best_f, t1 - t0), min(best_b, t2 - t1)
+    return {"adjoint_n": n, "adjoint_steps": steps, "adjoint_checkpoint_every": k,
+            "adjoint_forward_s": best_f, "adjoint_backward_s": best_b,
+            "adjoint_forward_ratio": best_b / best_f}
 
 
 if __name__ == "__main__":

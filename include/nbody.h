@@ -109,9 +109,11 @@ int nbody_timing_read(int32_t which, int64_t *launches, double *total_ms);
 /* Throughput microbenchmark of the units that bound the all-pairs kernels
  * (no counterpart in the paper; used to check the roofline denominators):
  * kind 0 = scalar FP32 FFMA, 1 = packed f32x2 FFMA (2 lane ops each),
- * 2 = MUFU rsqrt. Runs 8 x 256 threads per SM, 16 independent chains per
- * thread, `iters` iterations; returns lane operations per SM per clock and
- * per second. Synchronizes the device. */
+ * 2 = MUFU rsqrt, 3 = half FFMA2 / half FFMA chains, 4 = the packed gravity
+ * pair loop over shared memory, 5 = the scalar pair loop (kinds 4 and 5 count
+ * 12 lane ops per pair). Runs 8 x 256 threads per SM, `iters` iterations;
+ * returns lane operations per SM per clock and per second. Synchronizes the
+ * device. */
 int nbody_peak_probe(int32_t kind, int32_t iters, double *ops_per_clk_sm, double *ops_per_s);
 
 /* ---------------------------------------------------------------------------

@@ -20,6 +20,8 @@ const TileDesc *grav_tiles(int *count) {
       TileImpl<kLawGrav, 128, 2, 1, 256, true>::desc(),  // 9: 256
       TileImpl<kLawGrav, 256, 2, 1, 512, true>::desc(),  // 10: 512, longer j-tiles
       TileImpl<kLawGrav, 256, 3, 1, 256, true>::desc(),  // 11: 768
+      TileImpl<kLawGrav, 256, 2, 1, 512, true, 4>::desc(),  // 12: as 10, pair loop unrolled x4
+      TileImpl<kLawGrav, 128, 2, 1, 512, true, 4>::desc(),  // 13: 256, unrolled x4
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;

@@ -165,7 +165,8 @@ struct ForceTile {
 };
 
 // ---- the kernel -------------------------------------------------------------------
-template <int LAW, int NT, int I, int SW, int JT, bool POT, bool PRECISE, bool PK = false>
+template <int LAW, int NT, int I, int SW, int JT, bool POT, bool PRECISE, bool PK = false,
+          int PU = 2>
 __global__ void __launch_bounds__(NT + 32) force_kernel(const ForceArgs a) {
   using T = ForceTile<LAW, NT, I, SW, JT>;
   static_assert(!PK || (LAW == kLawGrav && SW == 1), "packed path: gravity, one j-lane");
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(NT + 32) force_kernel(const ForceArgs a) {
           ny[r] = make_float2(-yi[r], -yi[r]);
           nz[r] = make_float2(-zi[r], -zi[r]);
         }
-#pragma unroll 2
+#pragma unroll PU
         for (int pp = 0; pp < npairs; ++pp) {
           const float4 A = sp[2 * pp];
           const float4 B = sp[2 * pp + 1];

@@ -22,8 +22,10 @@ def main() -> dict:
     import torch
     props = torch.cuda.get_device_properties(0)
     out = {"gpu": props.name, "sms": props.multi_processor_count}
-    for kind, name in ((0, "ffma"), (1, "ffma2"), (2, "mufu_rsqrt")):
-        per_clk, per_s = probe(kind)
+    for kind, name, iters in ((0, "ffma", 1 << 16), (1, "ffma2", 1 << 16),
+                              (2, "mufu_rsqrt", 1 << 16), (3, "ffma2_ffma_mix", 1 << 16),
+                              (4, "grav_pair_loop_packed", 256), (5, "grav_pair_loop_scalar", 256)):
+        per_clk, per_s = probe(kind, iters)
         out[name] = {"lane_ops_per_clk_per_sm": per_clk, "lane_ops_per_s": per_s}
     print(json.dumps(out))
     return out
