@@ -231,15 +231,8 @@ def main():
     clk = clocks.stop()
     nb.sync_check()
     step_ms = float(sum(s.elapsed_time(e) for s, e in zip(starts, stops)))
-    t_local = step_ms / 1e3
-    if world > 1:
-        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
     pairs = float(N_BENCH) * N_BENCH
-    value = world * pairs * K / t_max / 1e9
+    t_max, value = aggregate(step_ms / 1e3, pairs, K, world, dev)
 
     # roofline of the dominant kernel (the all-pairs force kernel)
     props = torch.cuda.get_device_properties(dev)
@@ -303,6 +296,19 @@ def main():
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def aggregate(t_local: float, pairs_per_step: float, steps: int, world: int, device):
+    """Whole-job throughput: every rank ran `steps` steps of `pairs_per_step` pairs;
+    the job time is the slowest rank's (MAX all-reduce). Returns (t_max, G pairs/s)."""
+    import torch
+    t_max = t_local
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    return t_max, world * pairs_per_step * steps / t_max / 1e9
 
 
 def kernel_hash() -> str:

@@ -78,12 +78,12 @@ struct Scratch {
   double *diag_rows;
 };
 
-int get_scratch(cudaStream_t s, int n, int slices, int diag_rows, Scratch *out) {
+int get_scratch(cudaStream_t s, int law, int n, int slices, int diag_rows, Scratch *out) {
   const size_t part = round_up(size_t(slices) * size_t(n) * sizeof(float4), 256);
   const int nblk = std::max(1, (n + kFinThreads - 1) / kFinThreads);
   const size_t dpart = round_up(size_t(nblk) * kDiagFields * sizeof(double), 256);
   const size_t drows = round_up(size_t(std::max(diag_rows, 1)) * kDiagFields * sizeof(double), 256);
-  const size_t jb = round_up(size_t(n + 1) * sizeof(float4), 256);
+  const size_t jb = jbuf_bytes(law, n);
   void *base = nullptr;
   NB_TRY(workspace(s, jb + 2 * part + dpart + drows, &base));
   char *b = static_cast<char *>(base);
@@ -120,7 +120,7 @@ int forces_device(const float4 *pos, const float4 *prm, float4 *acc, float4 *acc
   Plan1 plan{};
   NB_TRY(plan_single(p.law, n, p.tile, p.jsplit, sms, &plan));
   Scratch sc{};
-  NB_TRY(get_scratch(s, n, plan.slices, 0, &sc));
+  NB_TRY(get_scratch(s, p.law, n, plan.slices, 0, &sc));
   int *err = nullptr;
   NB_TRY(error_word(&err));
   FinalizeArgs f{};
@@ -139,7 +139,7 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
   NB_TRY(plan_single(p.law, n, p.tile, p.jsplit, sms, &plan));
   const int rows = report_every > 0 ? nsteps / report_every + 1 : 0;
   Scratch sc{};
-  NB_TRY(get_scratch(s, n, plan.slices, rows, &sc));
+  NB_TRY(get_scratch(s, p.law, n, plan.slices, rows, &sc));
   int *err = nullptr;
   NB_TRY(error_word(&err));
   auto report = [&](int step) { return report_every > 0 && step % report_every == 0; };

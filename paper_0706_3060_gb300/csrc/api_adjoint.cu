@@ -19,15 +19,16 @@ struct VjpDesc {
   int jt;
   int threads;
   size_t smem;
+  bool packed;
   cudaError_t (*launch)(const VjpArgs &, int, cudaStream_t);
   int (*occupancy)();
 };
 
-template <int LAW, int NT, int I, int SW, int JT>
+template <int LAW, int NT, int I, int SW, int JT, bool PK = false>
 struct VjpImpl {
-  using T = VjpTile<LAW, NT, I, SW, JT>;
+  using T = VjpTile<LAW, NT, I, SW, JT, PK>;
   static cudaError_t launch(const VjpArgs &a, int grid, cudaStream_t s) {
-    auto k = vjp_kernel<LAW, NT, I, SW, JT>;
+    auto k = vjp_kernel<LAW, NT, I, SW, JT, PK>;
     if (T::kSmemBytes > 32 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)T::kSmemBytes);
@@ -38,7 +39,7 @@ struct VjpImpl {
   }
   static int occupancy() {
     int nb = 0;
-    auto k = vjp_kernel<LAW, NT, I, SW, JT>;
+    auto k = vjp_kernel<LAW, NT, I, SW, JT, PK>;
     if (T::kSmemBytes > 32 * 1024)
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, T::kThreads, T::kSmemBytes) !=
@@ -47,12 +48,12 @@ struct VjpImpl {
     return std::max(nb, 1);
   }
   static VjpDesc desc() {
-    return VjpDesc{T::kTileI, JT, T::kThreads, T::kSmemBytes, &launch, &occupancy};
+    return VjpDesc{T::kTileI, JT, T::kThreads, T::kSmemBytes, PK, &launch, &occupancy};
   }
 };
 
 const VjpDesc &vjp_tile(int law, int64_t n) {
-  static const VjpDesc grav_big = VjpImpl<kLawGrav, 256, 2, 1, 256>::desc();
+  static const VjpDesc grav_big = VjpImpl<kLawGrav, 256, 2, 1, 256, true>::desc();
   static const VjpDesc grav_small = VjpImpl<kLawGrav, 128, 2, 4, 256>::desc();
   static const VjpDesc ljc_big = VjpImpl<kLawLJC, 256, 2, 1, 256>::desc();
   static const VjpDesc ljc_small = VjpImpl<kLawLJC, 128, 1, 4, 256>::desc();
@@ -61,7 +62,7 @@ const VjpDesc &vjp_tile(int law, int64_t n) {
 }
 
 struct VjpScratch {
-  float4 *part_hi, *part_lo, *u;
+  float4 *part_hi, *part_lo, *u, *jp;
   double *type_part;
   int slices, slice_len, grid, nblk;
   long long bstride;
@@ -92,9 +93,11 @@ int vjp_prepare(int law, int n, int sms, cudaStream_t s, VjpScratch *sc) {
   const size_t ubytes = round_up(size_t(n) * sizeof(float4), 256);
   const int nblk = (n + 255) / 256;
   const size_t tbytes = round_up(size_t(nblk) * 8 * sizeof(double), 256);
+  const size_t jbytes = d.packed ? round_up(size_t((n + 1) / 2) * 4 * sizeof(float4), 256) : 0;
   void *base = nullptr;
-  NB_TRY(workspace(s, 2 * part + ubytes + tbytes, &base));
+  NB_TRY(workspace(s, 2 * part + ubytes + tbytes + jbytes, &base));
   char *b = static_cast<char *>(base);
+  sc->jp = d.packed ? reinterpret_cast<float4 *>(b + 2 * part + ubytes + tbytes) : nullptr;
   sc->part_hi = reinterpret_cast<float4 *>(b);
   sc->part_lo = reinterpret_cast<float4 *>(b + part);
   sc->u = reinterpret_cast<float4 *>(b + 2 * part);
@@ -121,10 +124,15 @@ int vjp_once(const float4 *pos, const float4 *prm, const float4 *lam, float4 *gr
     NB_CUDA(cudaGetLastError());
     src = sc.u;
   }
+  if (sc.d->packed) {
+    interleave_vjp_pairs_kernel<<<((n + 1) / 2 + 255) / 256, 256, 0, s>>>(pos, src, sc.jp, n);
+    NB_CUDA(cudaGetLastError());
+  }
   VjpArgs a{};
   a.pos = pos;
   a.lam = src;
   a.prm = prm;
+  a.jpair = sc.jp;
   a.part_hi = sc.part_hi;
   a.part_lo = sc.part_lo;
   a.stride = n;

@@ -280,6 +280,7 @@ static int log2_floor(int64_t n) {
 // Default tile when nothing is tuned: big register blocks for large N, j-lanes
 // inside the warp for small N (where there are too few targets to fill the GPU).
 static int default_tile(int law, int64_t n) {
+  if (law == 2) return 0;  // mixed-law batched kernel
   if (law == NBODY_LAW_GRAV) {
     if (n >= 65536) return 0;
     if (n >= 8192) return 3;
@@ -294,9 +295,9 @@ static int default_tile(int law, int64_t n) {
 
 int get_config(int law, int64_t n, int *tile, int *jsplit) {
   int t = -1, j = 0;
-  if (n > 0) {
+  if (n >= 0) {
     std::lock_guard<std::mutex> lk(g_mu);
-    const Tuned &tu = g_tuned[law][log2_floor(n)];
+    const Tuned &tu = g_tuned[law][log2_floor(n > 0 ? n : 1)];
     t = tu.tile;
     j = tu.jsplit;
   }
@@ -359,13 +360,36 @@ __global__ void interleave_pairs_kernel(const float4 *pos, float4 *jp, int n) {
   jp[2 * p + 1] = make_float4(a.z, b.z, a.w, b.w);
 }
 
+// LJC sources in pairs: (x0, x1, y0, y1), (z0, z1, q0, q1), (s0, s1, e0, e1); the
+// pad of an odd count is far away with no charge and no LJ well.
+__global__ void interleave_ljc_pairs_kernel(const float4 *pos, const float4 *prm, float4 *jp,
+                                            int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * p >= n) return;
+  const float4 a = pos[2 * p], qa = prm[2 * p];
+  const bool two = 2 * p + 1 < n;
+  const float4 b = two ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+  const float4 qb = two ? prm[2 * p + 1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  jp[3 * p] = make_float4(a.x, b.x, a.y, b.y);
+  jp[3 * p + 1] = make_float4(a.z, b.z, qa.x, qb.x);
+  jp[3 * p + 2] = make_float4(qa.y, qb.y, qa.z, qb.z);
+}
+
+size_t jbuf_bytes(int law, int64_t n) {
+  const size_t pairs = size_t((n + 1) / 2);
+  return round_up(pairs * (law == NBODY_LAW_LJC ? 3 : 2) * sizeof(float4), 256);
+}
+
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
                   int *err, bool pot, cudaStream_t s) {
   if (p.tile->packed) {
     if (!jbuf) return set_error_msg(NBODY_EINVAL, "packed tile without pair buffer");
     const int np = (n + 1) / 2;
-    interleave_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, jbuf, n);
+    if (law == NBODY_LAW_LJC)
+      interleave_ljc_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, prm, jbuf, n);
+    else
+      interleave_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, jbuf, n);
     NB_CUDA(cudaGetLastError());
   }
   ForceArgs a{};

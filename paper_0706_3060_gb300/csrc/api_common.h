@@ -66,7 +66,10 @@ struct Plan1 {
 int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out);
 
 // Launch: all-pairs partial sums into part_hi/lo (slices x n).
-// jbuf: scratch of n + 1 float4 for the pair-interleaved sources of packed tiles.
+// Bytes of the pair-interleaved source copy that packed tiles read.
+size_t jbuf_bytes(int law, int64_t n);
+
+// jbuf: scratch of jbuf_bytes(law, n) for the pair-interleaved sources of packed tiles.
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
                   int *err, bool pot, cudaStream_t s);

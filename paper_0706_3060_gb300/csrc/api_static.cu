@@ -92,14 +92,15 @@ extern "C" int nbody_forces_static(const void *pos_m, const void *prm, void *acc
 
   // Size check before touching the GPU: the pair copy of the sources plus two
   // float4 partial sums per target must fit, with at least one j-slice.
-  const size_t jb = round_up(size_t(n + 1) * sizeof(float4), 256);
+  const size_t jb = jbuf_bytes(p.law, n);
   const size_t per_slice = round_up(size_t(n) * sizeof(float4), 256);
   if (jb + 2 * per_slice > kStaticScratchBytes)
     return set_error_msg(NBODY_EINVAL,
                          "n = %lld needs %zu bytes of scratch; the static scratch of "
-                         "nbody_forces_static holds %zu bytes (n <= %zu)",
+                         "nbody_forces_static holds %zu bytes (n <= %.0f)",
                          (long long)n, jb + 2 * per_slice, kStaticScratchBytes,
-                         (kStaticScratchBytes - 1024) / (3 * sizeof(float4)));
+                         (kStaticScratchBytes - 1024) /
+                             ((p.law == NBODY_LAW_LJC ? 3.5 : 3.0) * sizeof(float4)));
 
   int dev = 0, sms = 0;
   NB_TRY(check_device(&dev, &sms));

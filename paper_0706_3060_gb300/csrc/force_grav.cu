@@ -22,6 +22,8 @@ const TileDesc *grav_tiles(int *count) {
       TileImpl<kLawGrav, 256, 3, 1, 256, true>::desc(),  // 11: 768
       TileImpl<kLawGrav, 256, 2, 1, 512, true, 4>::desc(),  // 12: as 10, pair loop unrolled x4
       TileImpl<kLawGrav, 128, 2, 1, 512, true, 4>::desc(),  // 13: 256, unrolled x4
+      TileImpl<kLawGrav, 256, 2, 1, 512, true, 2, 3>::desc(),  // 14: as 10, 3 CTAs/SM bound
+      TileImpl<kLawGrav, 128, 2, 1, 512, true, 2, 6>::desc(),  // 15: 256, 6 CTAs/SM bound
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;

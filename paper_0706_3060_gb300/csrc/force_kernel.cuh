@@ -155,6 +155,49 @@ __device__ __forceinline__ void ljc_pair(const float4 pj, const float4 qj, float
   }
 }
 
+// LJC for two sources at once in f32x2 arithmetic (same terms as ljc_pair).
+template <bool POT, bool PRECISE>
+__device__ __forceinline__ void ljc_pair2(float2 X, float2 Y, float2 Z, float2 Q, float2 S,
+                                          float2 E, float2 nxi, float2 nyi, float2 nzi,
+                                          float2 qi, float2 si, float2 ei, float2 &ax, float2 &ay,
+                                          float2 &az, float2 &pot) {
+  const float2 dx = __fadd2_rn(X, nxi);
+  const float2 dy = __fadd2_rn(Y, nyi);
+  const float2 dz = __fadd2_rn(Z, nzi);
+  float2 r2 = __fmul2_rn(dz, dz);
+  r2 = __ffma2_rn(dy, dy, r2);
+  r2 = __ffma2_rn(dx, dx, r2);
+  float2 y = make_float2(rsqrt_hw(r2.x), rsqrt_hw(r2.y));
+  if (PRECISE) {
+    const float2 hs = __fmul2_rn(r2, make_float2(-0.5f, -0.5f));
+    y = __fmul2_rn(y, __ffma2_rn(hs, __fmul2_rn(y, y), make_float2(1.5f, 1.5f)));
+  }
+  const float2 y2 = __fmul2_rn(y, y);
+  const float2 qq = __fmul2_rn(Q, qi);
+  const float2 s = __fadd2_rn(S, si);
+  const float2 t = __fmul2_rn(__fmul2_rn(s, s), y2);
+  const float2 u = __fmul2_rn(__fmul2_rn(t, t), t);
+  const float2 ee = __fmul2_rn(E, ei);
+  const float2 fc = __fmul2_rn(__fmul2_rn(qq, y), y2);
+  const float2 h = __fmul2_rn(__ffma2_rn(u, make_float2(2.0f, 2.0f), make_float2(-1.0f, -1.0f)), u);
+  const float2 f = __ffma2_rn(__fmul2_rn(ee, y2), h, fc);
+  ax = __ffma2_rn(f, dx, ax);
+  ay = __ffma2_rn(f, dy, ay);
+  az = __ffma2_rn(f, dz, az);
+  if (POT) {
+    pot = __ffma2_rn(qq, y, pot);
+    pot = __ffma2_rn(__fmul2_rn(ee, make_float2(1.0f / 6.0f, 1.0f / 6.0f)),
+                     __ffma2_rn(u, u, make_float2(-u.x, -u.y)), pot);
+  }
+}
+
+// float4s per pair of sources in the packed layouts: gravity (x x y y)(z z m m),
+// LJC (x x y y)(z z q q)(s s e e).
+template <int LAW>
+struct PairLayout {
+  static constexpr int kF4 = (LAW == kLawGrav) ? 2 : 3;
+};
+
 template <int LAW, int NT, int I, int SW, int JT>
 struct ForceTile {
   static constexpr int kThreads = NT + 32;  // + producer warp
@@ -166,10 +209,13 @@ struct ForceTile {
 
 // ---- the kernel -------------------------------------------------------------------
 template <int LAW, int NT, int I, int SW, int JT, bool POT, bool PRECISE, bool PK = false,
-          int PU = 2>
-__global__ void __launch_bounds__(NT + 32) force_kernel(const ForceArgs a) {
+          int PU = 2, int MINB = 1>
+__global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a) {
   using T = ForceTile<LAW, NT, I, SW, JT>;
-  static_assert(!PK || (LAW == kLawGrav && SW == 1), "packed path: gravity, one j-lane");
+  static_assert(!PK || ((LAW == kLawGrav || LAW == kLawLJC) && SW == 1),
+                "packed path: one law, one j-lane");
+  constexpr int PF4 = PairLayout<LAW == kLawLJC ? kLawLJC : kLawGrav>::kF4;
+  constexpr int STAGE_F4 = PK ? PF4 * JT / 2 : JT;  // float4s per ring stage
   constexpr int NWARPS = NT / 32;
   constexpr int SLOTS = T::kSlots;
   constexpr int TI = T::kTileI;
@@ -212,13 +258,19 @@ __global__ void __launch_bounds__(NT + 32) force_kernel(const ForceArgs a) {
       if (flags & kChunkEnd) {
         mbar_arrive(&full_bar[st]);
       } else {
-        // Packed layout: a tile of len sources is ceil(len/2) pairs of two
-        // float4; the odd tail reads the zero-mass pad after the last source.
-        const uint32_t bytes = uint32_t(PK ? (len + 1) & ~1 : len) * 16u;
-        const bool with_prm = (LAW == kLawLJC) || (LAW == kLawMixed && w.law == kLawLJC);
-        mbar_arrive_expect_tx(&full_bar[st], with_prm ? 2u * bytes : bytes);
-        tma_load_1d(sm_pos + st * JT, (PK ? a.jpair : a.pos) + cj0, bytes, &full_bar[st]);
-        if (with_prm) tma_load_1d(sm_prm + st * JT, a.prm + cj0, bytes, &full_bar[st]);
+        if (PK) {
+          // Packed layout: a tile of len sources is ceil(len/2) pairs of PF4
+          // float4; an odd tail reads the pad particle after the last source.
+          const uint32_t bytes = uint32_t((len + 1) >> 1) * PF4 * 16u;
+          mbar_arrive_expect_tx(&full_bar[st], bytes);
+          tma_load_1d(sm_pos + st * STAGE_F4, a.jpair + (cj0 >> 1) * PF4, bytes, &full_bar[st]);
+        } else {
+          const uint32_t bytes = uint32_t(len) * 16u;
+          const bool with_prm = (LAW == kLawLJC) || (LAW == kLawMixed && w.law == kLawLJC);
+          mbar_arrive_expect_tx(&full_bar[st], with_prm ? 2u * bytes : bytes);
+          tma_load_1d(sm_pos + st * JT, a.pos + cj0, bytes, &full_bar[st]);
+          if (with_prm) tma_load_1d(sm_prm + st * JT, a.prm + cj0, bytes, &full_bar[st]);
+        }
       }
       ++it;
     };
@@ -316,12 +368,53 @@ __global__ void __launch_bounds__(NT + 32) force_kernel(const ForceArgs a) {
         if (PK) pax[r] = pay[r] = paz[r] = ppt[r] = make_float2(0.f, 0.f);
       }
     }
-    const float4 *sp = sm_pos + st * JT;
+    const float4 *sp = sm_pos + st * STAGE_F4;
     const float4 *sq = sm_prm + st * JT;
     const bool masked = (cj0 < cur.i0 + cur.ni) && (cur.i0 < cj0 + len);
     const float eps2 = cur.eps2;
 
-    if (PK) {
+    if (PK && LAW == kLawLJC) {
+      if (!masked) {
+        const int npairs = (len + 1) >> 1;
+        float2 nx[PK ? I : 1], ny[PK ? I : 1], nz[PK ? I : 1];
+        float2 q2[PK ? I : 1], s2[PK ? I : 1], e2[PK ? I : 1];
+#pragma unroll
+        for (int r = 0; r < I; ++r) {
+          nx[r] = make_float2(-xi[r], -xi[r]);
+          ny[r] = make_float2(-yi[r], -yi[r]);
+          nz[r] = make_float2(-zi[r], -zi[r]);
+          q2[r] = make_float2(qi[r], qi[r]);
+          s2[r] = make_float2(si[r], si[r]);
+          e2[r] = make_float2(ei[r], ei[r]);
+        }
+#pragma unroll PU
+        for (int pp = 0; pp < npairs; ++pp) {
+          const float4 A = sp[3 * pp];
+          const float4 B = sp[3 * pp + 1];
+          const float4 C = sp[3 * pp + 2];
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            ljc_pair2<POT, PRECISE>(make_float2(A.x, A.y), make_float2(A.z, A.w),
+                                    make_float2(B.x, B.y), make_float2(B.z, B.w),
+                                    make_float2(C.x, C.y), make_float2(C.z, C.w), nx[r], ny[r],
+                                    nz[r], q2[r], s2[r], e2[r], pax[r], pay[r], paz[r], ppt[r]);
+        }
+      } else {
+        for (int jj = 0; jj < len; ++jj) {
+          const float4 A = sp[3 * (jj >> 1)];
+          const float4 B = sp[3 * (jj >> 1) + 1];
+          const float4 C = sp[3 * (jj >> 1) + 2];
+          const bool odd = jj & 1;
+          const float4 pj = make_float4(odd ? A.y : A.x, odd ? A.w : A.z, odd ? B.y : B.x, 0.f);
+          const float4 qj = make_float4(odd ? B.w : B.z, odd ? C.y : C.x, odd ? C.w : C.z, 0.f);
+          const int jg = cj0 + jj;
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            ljc_pair<POT, PRECISE, true>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r], p[r],
+                                         jg == ig[r]);
+        }
+      }
+    } else if (PK) {
       if (!masked) {
         const float2 e2 = make_float2(eps2, eps2);
         const int npairs = (len + 1) >> 1;
@@ -424,6 +517,7 @@ __global__ void __launch_bounds__(NT + 32) force_kernel(const ForceArgs a) {
 #pragma unroll
     for (int r = 0; r < I; ++r) {
       if (PK) {
+        // the diagonal (masked) tiles of the packed path accumulate in p
         p[r].x += pax[r].x + pax[r].y;
         p[r].y += pay[r].x + pay[r].y;
         p[r].z += paz[r].x + paz[r].y;

@@ -11,6 +11,11 @@ const TileDesc *ljc_tiles(int *count) {
       TileImpl<kLawLJC, 256, 4, 1, 256>::desc(),  // 2: 1024
       TileImpl<kLawLJC, 128, 2, 4, 256>::desc(),  // 3: 64 targets, 4 j-lanes
       TileImpl<kLawLJC, 64, 2, 8, 128>::desc(),   // 4: 16 targets, 8 j-lanes
+      // packed f32x2 math over source pairs
+      TileImpl<kLawLJC, 256, 2, 1, 256, true>::desc(),   // 5: 512 targets
+      TileImpl<kLawLJC, 128, 2, 1, 256, true>::desc(),   // 6: 256
+      TileImpl<kLawLJC, 64, 2, 1, 256, true>::desc(),    // 7: 128
+      TileImpl<kLawLJC, 256, 2, 1, 512, true>::desc(),   // 8: 512, longer j-tiles
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;

@@ -30,12 +30,12 @@ const TileDesc *grav_tiles(int *count);
 const TileDesc *ljc_tiles(int *count);
 const TileDesc *mixed_tiles(int *count);
 
-template <int LAW, int NT, int I, int SW, int JT, bool PK = false, int PU = 2>
+template <int LAW, int NT, int I, int SW, int JT, bool PK = false, int PU = 2, int MINB = 1>
 struct TileImpl {
   using T = ForceTile<LAW, NT, I, SW, JT>;
   template <bool POT, bool PRE>
   static cudaError_t go(const ForceArgs &a, int grid, cudaStream_t s) {
-    auto k = force_kernel<LAW, NT, I, SW, JT, POT, PRE, PK, PU>;
+    auto k = force_kernel<LAW, NT, I, SW, JT, POT, PRE, PK, PU, MINB>;
     if (T::kSmemBytes > 32 * 1024) {
       cudaError_t e =
           cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
@@ -51,7 +51,7 @@ struct TileImpl {
   }
   static int occupancy() {
     int nb = 0;
-    auto k = force_kernel<LAW, NT, I, SW, JT, false, false, PK, PU>;
+    auto k = force_kernel<LAW, NT, I, SW, JT, false, false, PK, PU, MINB>;
     if (T::kSmemBytes > 32 * 1024)
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, T::kThreads, T::kSmemBytes) !=

@@ -26,6 +26,7 @@ struct VjpArgs {
   const float4 *pos;   // (x, y, z, m)
   const float4 *lam;   // gravity: lam; LJC: u = lam / m
   const float4 *prm;   // LJC parameters or null
+  const float4 *jpair; // packed gravity: (x x y y)(z z m m)(lx lx ly ly)(lz lz 0 0) per pair
   float4 *part_hi;     // [2][slices][stride]: block A then block B (LJC)
   float4 *part_lo;
   long long stride;
@@ -69,6 +70,35 @@ __device__ __forceinline__ void grav_vjp_pair(const float4 pj, const float4 lj, 
   A.w = fmaf(ld, y3, A.w);
 }
 
+// The gravity VJP pair for two sources at once (f32x2); A holds (g.x, g.y, g.z,
+// mass term) as even/odd-source halves.
+__device__ __forceinline__ void grav_vjp_pair2(float2 X, float2 Y, float2 Z, float2 Mj, float2 LX,
+                                               float2 LY, float2 LZ, float2 nxk, float2 nyk,
+                                               float2 nzk, float2 mk, float2 lkx, float2 lky,
+                                               float2 lkz, float2 e2, float2 &ax, float2 &ay,
+                                               float2 &az, float2 &aw) {
+  const float2 dx = __fadd2_rn(X, nxk);
+  const float2 dy = __fadd2_rn(Y, nyk);
+  const float2 dz = __fadd2_rn(Z, nzk);
+  float2 s2 = __ffma2_rn(dz, dz, e2);
+  s2 = __ffma2_rn(dy, dy, s2);
+  s2 = __ffma2_rn(dx, dx, s2);
+  const float2 y = make_float2(rsqrt_hw(s2.x), rsqrt_hw(s2.y));
+  const float2 y2 = __fmul2_rn(y, y);
+  const float2 y3 = __fmul2_rn(y2, y);
+  const float2 nmj = make_float2(-Mj.x, -Mj.y);
+  const float2 wx = __ffma2_rn(mk, LX, __fmul2_rn(nmj, lkx));
+  const float2 wy = __ffma2_rn(mk, LY, __fmul2_rn(nmj, lky));
+  const float2 wz = __ffma2_rn(mk, LZ, __fmul2_rn(nmj, lkz));
+  const float2 dw = __ffma2_rn(dx, wx, __ffma2_rn(dy, wy, __fmul2_rn(dz, wz)));
+  const float2 c = __fmul2_rn(__fmul2_rn(dw, make_float2(-3.0f, -3.0f)), __fmul2_rn(y3, y2));
+  ax = __ffma2_rn(c, dx, __ffma2_rn(y3, wx, ax));
+  ay = __ffma2_rn(c, dy, __ffma2_rn(y3, wy, ay));
+  az = __ffma2_rn(c, dz, __ffma2_rn(y3, wz, az));
+  const float2 ld = __ffma2_rn(LX, dx, __ffma2_rn(LY, dy, __fmul2_rn(LZ, dz)));
+  aw = __ffma2_rn(ld, y3, aw);
+}
+
 template <bool MASK>
 __device__ __forceinline__ void ljc_vjp_pair(const float4 pj, const float4 uj, const float4 qj,
                                              float xk, float yk, float zk, float ukx, float uky,
@@ -110,13 +140,14 @@ __device__ __forceinline__ void ljc_vjp_pair(const float4 pj, const float4 uj, c
   B.w = fmaf(dw, phi_lj, B.w);
 }
 
-template <int LAW, int NT, int I, int SW, int JT>
+template <int LAW, int NT, int I, int SW, int JT, bool PK = false>
 struct VjpTile {
   static constexpr int kThreads = NT + 32;
   static constexpr int kSlots = NT / SW;
   static constexpr int kTileI = kSlots * I;
   static constexpr int kStreams = (LAW == kLawLJC) ? 3 : 2;
   static constexpr size_t kSmemBytes = size_t(kStages) * JT * 16 * kStreams;
+  static constexpr int kPairF4 = 4;  // packed gravity: float4s per source pair
 };
 
 __device__ __forceinline__ void comp_fold(float4 &hi, float4 &lo, float4 &p, int comp) {
@@ -155,9 +186,10 @@ __device__ __forceinline__ void shfl_combine(float4 &hi, float4 &lo, int off) {
   lo.w = __fadd_rn(__fadd_rn(lo.w, ol.w), e);
 }
 
-template <int LAW, int NT, int I, int SW, int JT>
+template <int LAW, int NT, int I, int SW, int JT, bool PK = false>
 __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
-  using T = VjpTile<LAW, NT, I, SW, JT>;
+  using T = VjpTile<LAW, NT, I, SW, JT, PK>;
+  static_assert(!PK || (LAW == kLawGrav && SW == 1), "packed VJP: gravity, one j-lane");
   constexpr int NWARPS = NT / 32;
   constexpr int SLOTS = T::kSlots;
   constexpr int TI = T::kTileI;
@@ -204,11 +236,18 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
       const int len = min(JT, jend - cj);
       meta_len[st] = len;
       meta_cj0[st] = cj;
-      const uint32_t bytes = uint32_t(len) * 16u;
-      mbar_arrive_expect_tx(&full_bar[st], bytes * T::kStreams);
-      tma_load_1d(sm_pos + st * JT, a.pos + cj, bytes, &full_bar[st]);
-      tma_load_1d(sm_lam + st * JT, a.lam + cj, bytes, &full_bar[st]);
-      if (LJ) tma_load_1d(sm_prm + st * JT, a.prm + cj, bytes, &full_bar[st]);
+      if (PK) {
+        // pairs of sources, 4 float4 each; the stage spans the pos + lam regions
+        const uint32_t bytes = uint32_t((len + 1) >> 1) * T::kPairF4 * 16u;
+        mbar_arrive_expect_tx(&full_bar[st], bytes);
+        tma_load_1d(sm_pos + st * 2 * JT, a.jpair + (cj >> 1) * T::kPairF4, bytes, &full_bar[st]);
+      } else {
+        const uint32_t bytes = uint32_t(len) * 16u;
+        mbar_arrive_expect_tx(&full_bar[st], bytes * T::kStreams);
+        tma_load_1d(sm_pos + st * JT, a.pos + cj, bytes, &full_bar[st]);
+        tma_load_1d(sm_lam + st * JT, a.lam + cj, bytes, &full_bar[st]);
+        if (LJ) tma_load_1d(sm_prm + st * JT, a.prm + cj, bytes, &full_bar[st]);
+      }
     }
     if (it < nchunks)  // timed out: bounded drain of copies in flight
       for (int k = max(0, it - kStages); k < it; ++k)
@@ -257,7 +296,53 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
     const float4 *sl = sm_lam + st * JT;
     const float4 *sq = sm_prm + st * JT;
     const bool masked = (cj0 < i0 + ni) && (i0 < cj0 + len);
-    if (!LJ) {
+    if (PK) {
+      const float4 *pk = sm_pos + st * 2 * JT;
+      if (!masked) {
+        const float2 e2 = make_float2(a.eps2, a.eps2);
+        const int npairs = (len + 1) >> 1;
+        float2 ax[PK ? I : 1], ay[PK ? I : 1], az[PK ? I : 1], aw[PK ? I : 1];
+#pragma unroll
+        for (int r = 0; r < I; ++r) ax[r] = ay[r] = az[r] = aw[r] = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int pp = 0; pp < npairs; ++pp) {
+          const float4 P0 = pk[4 * pp], P1 = pk[4 * pp + 1];
+          const float4 L0 = pk[4 * pp + 2], L1 = pk[4 * pp + 3];
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            grav_vjp_pair2(make_float2(P0.x, P0.y), make_float2(P0.z, P0.w),
+                           make_float2(P1.x, P1.y), make_float2(P1.z, P1.w),
+                           make_float2(L0.x, L0.y), make_float2(L0.z, L0.w),
+                           make_float2(L1.x, L1.y), make_float2(-xk[r], -xk[r]),
+                           make_float2(-yk[r], -yk[r]), make_float2(-zk[r], -zk[r]),
+                           make_float2(mk[r], mk[r]), make_float2(lx[r], lx[r]),
+                           make_float2(ly[r], ly[r]), make_float2(lz[r], lz[r]), e2, ax[r],
+                           ay[r], az[r], aw[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < I; ++r) {
+          pA[r].x += ax[r].x + ax[r].y;
+          pA[r].y += ay[r].x + ay[r].y;
+          pA[r].z += az[r].x + az[r].y;
+          pA[r].w += aw[r].x + aw[r].y;
+        }
+      } else {
+        for (int jj = 0; jj < len; ++jj) {
+          const int q = 4 * (jj >> 1);
+          const bool odd = jj & 1;
+          const float4 P0 = pk[q], P1 = pk[q + 1], L0 = pk[q + 2], L1 = pk[q + 3];
+          const float4 pj = make_float4(odd ? P0.y : P0.x, odd ? P0.w : P0.z, odd ? P1.y : P1.x,
+                                        odd ? P1.w : P1.z);
+          const float4 lj = make_float4(odd ? L0.y : L0.x, odd ? L0.w : L0.z, odd ? L1.y : L1.x,
+                                        0.f);
+          const int jg = cj0 + jj;
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            grav_vjp_pair<true>(pj, lj, xk[r], yk[r], zk[r], mk[r], lx[r], ly[r], lz[r], a.eps2,
+                                pA[r], jg == ig[r]);
+        }
+      }
+    } else if (!LJ) {
       if (!masked) {
 #pragma unroll 2
         for (int jj = jl; jj < len; jj += SW) {
@@ -460,6 +545,22 @@ __global__ void type_reduce_kernel(const double *part, int nblk, int ntypes, dou
   for (int b = 0; b < nblk; ++b) s += part[(size_t)b * 8 + k];
   const int t = k & 3, which = k >> 2;  // 0: sigma, 1: eps
   if (t < ntypes) out[which * ntypes + t] += s;
+}
+
+// Packed gravity VJP sources: per pair (x0 x1 y0 y1)(z0 z1 m0 m1)(lx0 lx1 ly0 ly1)
+// (lz0 lz1 0 0); an odd count is padded with a massless particle far away.
+__global__ void interleave_vjp_pairs_kernel(const float4 *pos, const float4 *lam, float4 *jp,
+                                            int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * p >= n) return;
+  const bool two = 2 * p + 1 < n;
+  const float4 a = pos[2 * p], la = lam[2 * p];
+  const float4 b = two ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+  const float4 lb = two ? lam[2 * p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+  jp[4 * p] = make_float4(a.x, b.x, a.y, b.y);
+  jp[4 * p + 1] = make_float4(a.z, b.z, a.w, b.w);
+  jp[4 * p + 2] = make_float4(la.x, lb.x, la.y, lb.y);
+  jp[4 * p + 3] = make_float4(la.z, lb.z, 0.f, 0.f);
 }
 
 // u = lam / m (LJC sources are weighted by 1 / m_j).

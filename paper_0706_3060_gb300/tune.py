@@ -90,6 +90,60 @@ def tune(law: int, sizes, jsplits=(0, 1, 2, 4, 8, 16, 32), reps=5, verbose=True)
     return table
 
 
+def tune_batched(reps=3, verbose=True, nsys=512, seed=3):
+    """Pick the mixed-law work-list tile for the batched ensemble (512 systems, N
+    log-uniform in [64, 4096]); stored as law 2, bucket 0."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rng = np.random.default_rng(seed)
+    sizes = np.clip(np.rint(np.exp(rng.uniform(math.log(64), math.log(4096), nsys))), 64, 4096)
+    sizes = sizes.astype(int)
+    total = int(sizes.sum())
+    pos = np.zeros((total, 4), np.float32)
+    table, off = [], 0
+    for k, n in enumerate(sizes):
+        if k % 2 == 0:
+            pos[off:off + n, :3] = rng.standard_normal((n, 3))
+            pos[off:off + n, 3] = 1.0 / n
+            table.append(dict(offset=off, n=int(n), law=LAW_GRAV, eps=0.01, dt=1e-3))
+        else:
+            side = int(math.ceil(n ** (1.0 / 3.0)))
+            g = np.stack(np.meshgrid(*[np.arange(side)] * 3, indexing="ij"), -1).reshape(-1, 3)
+            pos[off:off + n, :3] = g[:n] * 3.6 + rng.uniform(-0.5, 0.5, (n, 3))
+            pos[off:off + n, 3] = 12.0
+            table.append(dict(offset=off, n=int(n), law=LAW_LJC, dt=1e-4))
+        off += n
+    p = torch.from_numpy(pos).to(dev).contiguous()
+    prm = api.pack_ljc(torch.from_numpy(rng.uniform(-0.8, 0.8, total)).to(dev),
+                       torch.from_numpy(rng.uniform(2.5, 3.8, total)).to(dev),
+                       torch.from_numpy(rng.uniform(0.05, 0.2, total)).to(dev),
+                       torch.zeros(total, dtype=torch.int32, device=dev))
+    vel = torch.zeros_like(p)
+    acc = torch.zeros_like(p)
+    results = []
+    for tile in range(api.tile_count(2)):
+        plan = api.BatchPlan(table, tile=tile)
+        plan.run(p, vel, acc, prm, nsteps=0, graph=False)
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            plan.run(p, vel, acc, prm, nsteps=0, graph=False)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = float(np.median(ts))
+        results.append((ms, tile))
+        plan.close()
+        if verbose:
+            print(f"batched tile={tile}: {ms:.4f} ms "
+                  f"({float(np.sum(sizes.astype(float) ** 2)) / ms / 1e6:.1f} G pairs/s)",
+                  flush=True)
+    ms, tile = min(results)
+    api.set_tuned(2, 1, tile, 0)
+    return {"0": {"n": 0, "tile": tile, "jsplit": 0, "ms": ms}}
+
+
 def save_cache(law: int, table: dict, path: str = CACHE):
     import torch
     data = json.load(open(path)) if os.path.exists(path) else {}
@@ -115,11 +169,17 @@ def load_cache(path: str = CACHE) -> int:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--law", choices=["grav", "ljc"], default="grav")
+    ap.add_argument("--law", choices=["grav", "ljc", "batched"], default="grav")
     ap.add_argument("--n", type=int, nargs="+", default=[1024, 4096, 16384, 65536, 262144])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--save", action="store_true")
     a = ap.parse_args()
+    if a.law == "batched":
+        table = tune_batched(reps=a.reps)
+        print(json.dumps(table))
+        if a.save:
+            save_cache(2, table)
+        return
     law = LAW_GRAV if a.law == "grav" else LAW_LJC
     table = tune(law, a.n, reps=a.reps)
     print(json.dumps(table))

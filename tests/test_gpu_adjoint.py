@@ -20,7 +20,7 @@ def _rel(got, ref):
     return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
 
 
-@pytest.mark.parametrize("n", [3, 257, 1000, 9000])
+@pytest.mark.parametrize("n", [3, 257, 1000, 9000, 9001])
 def test_grav_vjp(n):
     nb = lib()
     g = workloads.plummer(n, seed=60 + n, eps=0.01)

@@ -37,7 +37,7 @@ def test_grav_default_config(n):
     assert_forces_close(acc[:, :3].cpu().numpy(), ref, what=f"n={n}")
 
 
-@pytest.mark.parametrize("tile", range(14))
+@pytest.mark.parametrize("tile", range(16))
 @pytest.mark.parametrize("jsplit", [1, 3])
 def test_grav_every_tile(tile, jsplit):
     nb = lib()
@@ -142,7 +142,7 @@ def test_ljc_forces(n):
     assert np.sqrt(np.mean(e * e)) <= 1e-5 and e.max() <= 1e-4
 
 
-@pytest.mark.parametrize("tile", range(5))
+@pytest.mark.parametrize("tile", range(9))
 def test_ljc_every_tile(tile):
     nb = lib()
     s = workloads.ljc_sphere(1500, seed=9)
