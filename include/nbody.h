@@ -146,6 +146,18 @@ int nbody_pack_ljc(const double *q, const double *sigma, const double *eps,
 int nbody_forces(const void *pos_m, const void *prm, void *acc, void *acc_lo, int64_t n,
                  const nbody_params *params, nbody_stream_t stream);
 
+/* nbody_forces_subset -- forces on n_active target particles idx[0..n_active)
+ * against all n sources (block time steps, Sec. 3.4: forces on only a subset of
+ * the particles at a time). Same laws, flags and accuracy as nbody_forces.
+ *   idx : n_active int32 indices into [0, n), device; duplicates allowed
+ *   acc : n_active float4 (device): acc[k] = (a, phi) of particle idx[k]
+ * The self pair of each target is excluded by its index. An index outside
+ * [0, n) is caught on the device (its row is computed for particle 0) and
+ * reported by the next nbody_check as NBODY_EINVAL. Device pointers only. */
+int nbody_forces_subset(const void *pos_m, const void *prm, const int32_t *idx,
+                        int64_t n_active, void *acc, int64_t n, const nbody_params *params,
+                        nbody_stream_t stream);
+
 /* nbody_forces_static -- nbody_forces for callers that cannot allocate device
  * memory (a fixed memory budget set at start-up, an allocator owned by another
  * framework, a real-time loop that must not block in cudaMalloc). The paper has

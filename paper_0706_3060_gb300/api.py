@@ -130,6 +130,23 @@ def forces(pos_m, prm=None, *, law=None, G=1.0, eps=0.0, pot=False, precise=Fals
     return (acc, lo) if want_lo else acc
 
 
+def forces_subset(pos_m, idx, prm=None, *, law=None, G=1.0, eps=0.0, pot=False, precise=False,
+                  compensated=True, tile=-1, jsplit=0, out=None, stream=None):
+    """Forces on the particles ``idx`` (int32 tensor of indices) against all
+    particles: returns (len(idx), 4) accelerations in the order of ``idx``."""
+    _check4(pos_m, "pos_m")
+    _check4(prm, "prm")
+    law = (LAW_LJC if prm is not None else LAW_GRAV) if law is None else law
+    idx = idx.to(torch.int32).contiguous()
+    acc = torch.empty((idx.shape[0], 4), dtype=torch.float32, device=pos_m.device) \
+        if out is None else out
+    p = params(law, G, eps, pot, precise, compensated, tile, jsplit)
+    check(_lib().nbody_forces_subset(_ptr(pos_m), _ptr(prm), _ptr(idx), idx.shape[0], _ptr(acc),
+                                     pos_m.shape[0], ctypes.byref(p),
+                                     _stream(stream, pos_m.device)), "nbody_forces_subset")
+    return acc
+
+
 def step(pos_m, vel, acc, prm=None, *, dt, nsteps=1, law=None, G=1.0, eps=0.0,
          report_every=0, acc_valid=False, pot=False, precise=False, compensated=True,
          tile=-1, jsplit=0, trace=None, diag=None, state_lo=None, stream=None):

@@ -76,6 +76,10 @@ int enqueue_run(nbody_batch_plan *p, float4 *pos, float4 *vel, float4 *acc, cons
     ForceArgs a{};
     a.pos = pos;
     a.prm = prm;
+    a.tpos = pos;
+    a.tprm = prm;
+    a.tidx = nullptr;
+    a.n_t = total;
     a.part_hi = part_hi;
     a.part_lo = part_lo;
     a.stride = stride;

@@ -308,14 +308,18 @@ int get_config(int law, int64_t n, int *tile, int *jsplit) {
 }
 
 int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out) {
+  return plan_targets(law, n, n, tile, jsplit, sms, out);
+}
+
+int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms, Plan1 *out) {
   int count = 0;
   const TileDesc *tiles = tiles_for(law, &count);
   int tj = 0;
-  if (tile < 0) get_config(law, n, &tile, &tj);
+  if (tile < 0) get_config(law, n_t, &tile, &tj);
   if (jsplit <= 0) jsplit = tj;
   if (tile < 0 || tile >= count) return set_error_msg(NBODY_EINVAL, "bad tile %d", tile);
   const TileDesc &d = tiles[tile];
-  const int n_it = int((n + d.tile_i - 1) / d.tile_i);
+  const int n_it = int((n_t + d.tile_i - 1) / d.tile_i);
   const int max_slices = int((n + d.jt - 1) / d.jt);
   int S = jsplit;
   if (S <= 0) {
@@ -382,7 +386,7 @@ size_t jbuf_bytes(int law, int64_t n) {
 
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
-                  int *err, bool pot, cudaStream_t s) {
+                  int *err, bool pot, cudaStream_t s, const Targets *tg) {
   if (p.tile->packed) {
     if (!jbuf) return set_error_msg(NBODY_EINVAL, "packed tile without pair buffer");
     const int np = (n + 1) / 2;
@@ -396,9 +400,13 @@ int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags,
   a.jpair = jbuf;
   a.pos = pos;
   a.prm = prm;
+  a.tpos = tg ? tg->tpos : pos;
+  a.tprm = tg ? tg->tprm : prm;
+  a.tidx = tg ? tg->tidx : nullptr;
+  a.n_t = tg ? tg->n_t : n;
   a.part_hi = part_hi;
   a.part_lo = part_lo;
-  a.stride = n;
+  a.stride = a.n_t;
   a.err = err;
   a.n = n;
   a.slices = p.slices;

@@ -64,6 +64,16 @@ struct Plan1 {
   int grid;
 };
 int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out);
+// Same for n_t targets against n sources (i-tiles over targets, j-slices over sources).
+int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms, Plan1 *out);
+
+// Optional separate targets for launch_forces (subset evaluations).
+struct Targets {
+  const float4 *tpos;  // gathered target positions (n_t)
+  const float4 *tprm;  // gathered target LJC parameters or null
+  const int *tidx;     // global index of each target (self mask)
+  int n_t;
+};
 
 // Launch: all-pairs partial sums into part_hi/lo (slices x n).
 // Bytes of the pair-interleaved source copy that packed tiles read.
@@ -72,7 +82,7 @@ size_t jbuf_bytes(int law, int64_t n);
 // jbuf: scratch of jbuf_bytes(law, n) for the pair-interleaved sources of packed tiles.
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
-                  int *err, bool pot, cudaStream_t s);
+                  int *err, bool pot, cudaStream_t s, const Targets *tg = nullptr);
 
 size_t round_up(size_t x, size_t a);
 

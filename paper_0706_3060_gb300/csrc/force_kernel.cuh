@@ -50,6 +50,13 @@ struct ForceArgs {
   float4 *part_lo;     // [slices][stride]
   long long stride;    // elements per slice
   int *err;            // device error word
+  // targets: by default the sources themselves (tpos == pos, tprm == prm,
+  // n_t == n); for a subset, a gathered copy plus the global index of each
+  // target (tidx), which then drives the self-pair mask in every tile
+  const float4 *tpos;
+  const float4 *tprm;
+  const int *tidx;
+  int n_t;
   // single system: items are (i-tile, j-slice) pairs enumerated by blockIdx.x
   int n;
   int slices;
@@ -289,7 +296,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
       WorkItem w;
       const int t = b / a.slices, s = b % a.slices;
       w.i0 = t * TI;
-      w.ni = min(TI, a.n - w.i0);
+      w.ni = min(TI, a.n_t - w.i0);
       w.j0 = s * a.slice_len;
       w.nj = min(a.slice_len, a.n - w.j0);
       w.law = LAW == kLawLJC ? kLawLJC : kLawGrav;
@@ -329,7 +336,8 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
 
   float xi[I], yi[I], zi[I];
   float qi[I], si[I], ei[I];
-  int ig[I];
+  int ig[I];      // global index of each target (self mask)
+  int slot_g[I];  // output slot of each target (-1: padding)
   float4 p[I], hi[I], lo[I];
   float2 pax[PK ? I : 1], pay[PK ? I : 1], paz[PK ? I : 1], ppt[PK ? I : 1];
   WorkItem cur{};
@@ -349,13 +357,14 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
       for (int r = 0; r < I; ++r) {
         const int il = r * SLOTS + slot;
         const int g = cur.i0 + min(il, cur.ni - 1);
-        ig[r] = (il < cur.ni) ? g : -1;
-        const float4 pi4 = __ldg(a.pos + g);
+        ig[r] = (il < cur.ni) ? (a.tidx ? __ldg(a.tidx + g) : g) : -1;
+        slot_g[r] = (il < cur.ni) ? g : -1;
+        const float4 pi4 = __ldg(a.tpos + g);
         xi[r] = pi4.x;
         yi[r] = pi4.y;
         zi[r] = pi4.z;
         if (T::kPrm && cur_law == kLawLJC) {
-          const float4 pr = __ldg(a.prm + g);
+          const float4 pr = __ldg(a.tprm + g);
           qi[r] = pr.x;
           si[r] = pr.y;
           ei[r] = pr.z;
@@ -370,7 +379,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
     }
     const float4 *sp = sm_pos + st * STAGE_F4;
     const float4 *sq = sm_prm + st * JT;
-    const bool masked = (cj0 < cur.i0 + cur.ni) && (cur.i0 < cj0 + len);
+    const bool masked = a.tidx != nullptr || ((cj0 < cur.i0 + cur.ni) && (cur.i0 < cj0 + len));
     const float eps2 = cur.eps2;
 
     if (PK && LAW == kLawLJC) {
@@ -569,9 +578,9 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
         const long long base = (long long)cur.slice * a.stride;
 #pragma unroll
         for (int r = 0; r < I; ++r) {
-          if (ig[r] >= 0) {
-            a.part_hi[base + ig[r]] = hi[r];
-            a.part_lo[base + ig[r]] = lo[r];
+          if (slot_g[r] >= 0) {
+            a.part_hi[base + slot_g[r]] = hi[r];
+            a.part_lo[base + slot_g[r]] = lo[r];
           }
         }
       }

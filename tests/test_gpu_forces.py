@@ -181,3 +181,41 @@ def test_invalid_arguments_are_rejected():
         nb.forces(pos, tile=99)
     acc = nb.forces(torch.zeros((0, 4), device=dev()))   # n == 0 is a no-op
     assert acc.shape == (0, 4)
+
+
+@pytest.mark.parametrize("n,na", [(1000, 1), (4099, 37), (20000, 900), (262144, 1000)])
+def test_grav_subset_matches_oracle(n, na):
+    """Block time steps (Sec. 3.4): forces on an active subset against all particles."""
+    nb = lib()
+    g = workloads.plummer(n, seed=200 + na, eps=0.01 if n < 100000 else
+                          workloads.plummer_softening(n))
+    pos, _ = grav_tensors(g)
+    idx = np.random.default_rng(na).choice(n, na, replace=False).astype(np.int32)
+    acc = nb.forces_subset(pos, torch.from_numpy(idx).to(dev()), eps=float(np.float32(g.eps)),
+                           pot=True).cpu().numpy()
+    ref, phi = _grav_ref(g, idx=idx, potential=True)
+    assert_forces_close(acc[:, :3], ref, what=f"subset n={n} na={na}")
+    e = np.abs(acc[:, 3] - phi) / np.abs(phi)
+    assert e.max() <= 1e-4
+
+
+def test_subset_equals_full_rows_and_unsoftened():
+    nb = lib()
+    g = workloads.plummer(3001, seed=8, eps=0.01)
+    pos, _ = grav_tensors(g)
+    full = nb.forces(pos, eps=0.0)
+    idx = torch.tensor([3000, 0, 17, 17, 1500], dtype=torch.int32, device=dev())
+    sub = nb.forces_subset(pos, idx, eps=0.0)   # eps = 0: the self mask is essential
+    assert torch.all(torch.isfinite(sub))
+    e = rel_errors(sub[:, :3].cpu().numpy(), full[idx.long()][:, :3].cpu().numpy())
+    assert e.max() <= 2e-6
+
+
+def test_ljc_subset():
+    nb = lib()
+    s = workloads.ljc_sphere(3000, seed=44)
+    pos, _, prm = ljc_tensors(s)
+    idx = np.arange(5, 3000, 7).astype(np.int32)
+    acc = nb.forces_subset(pos, torch.from_numpy(idx).to(dev()), prm).cpu().numpy()
+    sysm, x, _ = oracle_ljc_system(s)
+    assert_forces_close(acc[:, :3], sysm.accel(x)[idx], what="LJC subset")
