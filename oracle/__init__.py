@@ -9,6 +9,8 @@ What it computes (each item is the plain definition, no blocking or fusion):
 
 * :func:`grav_accel`     -- Eq. 1 (Sec. 3.3), Table 1 "Gravity (accel)":
   a_i = -G sum_{j!=i} m_j r_ij / (r_ij^2 + eps^2)^{3/2}, plus the potential.
+* :func:`grav_jerk`      -- Table 1 "Gravity (accel & jerk)": acceleration and
+  its time derivative (jerk) for a 4th-order Hermite scheme.
 * :func:`ljc_force`      -- Table 1 "LJC(constant)", read as the standard
   12-6 Lennard-Jones force plus Coulomb in a dielectric eps_r, with
   Lorentz-Berthelot mixing (the paper prints the LJ term without its 24/r^2
@@ -72,6 +74,9 @@ def _load():
             lib.oracle_grav.argtypes = [i64, d, d, ctypes.c_double, ctypes.c_double,
                                         i64, i64p, d, d]
             lib.oracle_ljc.argtypes = [i64, d, d, d, d, ctypes.c_double, i64, i64p, d, d]
+            lib.oracle_grav_jerk.argtypes = [i64, d, d, d, ctypes.c_double, ctypes.c_double,
+                                             d, d]
+            lib.oracle_grav_jerk.restype = None
             lib.oracle_grav_vjp.argtypes = [i64, d, d, ctypes.c_double, ctypes.c_double,
                                             d, d, d]
             lib.oracle_ljc_vjp.argtypes = [i64, d, d, d, i32p, ctypes.c_int32, d, d,
@@ -127,6 +132,21 @@ def grav_accel(x, m, G=1.0, eps=0.0, idx=None, potential=False):
     lib.oracle_grav(n, _dp(x), _dp(m), float(G), float(eps) ** 2, ni, idxp, _dp(acc),
                     _dp(phi))
     return (acc, phi) if potential else acc
+
+
+def grav_jerk(x, v, m, G=1.0, eps=0.0):
+    """Table 1 "Gravity (accel & jerk)": returns (acc (n,3), jerk (n,3)), the jerk
+    being the time derivative of the acceleration for particles moving at v."""
+    lib = _load()
+    x = _f64(x, (-1, 3))
+    v = _f64(v, (-1, 3))
+    m = _f64(m)
+    n = x.shape[0]
+    acc = np.zeros((n, 3))
+    jerk = np.zeros((n, 3))
+    lib.oracle_grav_jerk(n, _dp(x), _dp(v), _dp(m), float(G), float(eps) ** 2, _dp(acc),
+                         _dp(jerk))
+    return acc, jerk
 
 
 def ljc_force(x, q, sig, eps, kq=COULOMB_K / 80.0, idx=None, potential=False):

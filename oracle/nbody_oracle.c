@@ -11,6 +11,7 @@
  * with no blocking, fusion or reordering:
  *   - oracle_grav       Eq. 1 of Sec. 3.3 / Table 1 "Gravity (accel)"
  *   - oracle_ljc        Table 1 "LJC (constant)" (readings C1, C2, C4 below)
+ *   - oracle_grav_jerk  Table 1 "Gravity (accel & jerk)"
  *   - oracle_grav_vjp   transpose of the Jacobian of Eq. 1, block by block
  *   - oracle_ljc_vjp    transpose of the Jacobian of the LJC law, plus the
  *                       derivatives w.r.t. per-type sigma, epsilon and masses
@@ -76,6 +77,42 @@ void oracle_grav(int64_t n, const double *x, const double *m, double G,
         acc[3 * k + 2] = G * az;
         if (phi)
             phi[k] = G * p;
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Softened gravity with jerk, Table 1 "Gravity (accel & jerk)". With
+ * r = x_j - x_i, u = v_j - v_i and s^2 = |r|^2 + eps^2:
+ *   a_i = G sum_{j != i} m_j r / s^3
+ *   j_i = G sum_{j != i} m_j [ u / s^3 - 3 (r . u) r / s^5 ]   (= d a_i / dt)
+ * ------------------------------------------------------------------------- */
+void oracle_grav_jerk(int64_t n, const double *x, const double *v, const double *m, double G,
+                      double eps2, double *acc, double *jerk)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double a[3] = {0.0, 0.0, 0.0}, jk[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i)
+                continue;
+            double r[3], u[3];
+            for (int c = 0; c < 3; ++c) {
+                r[c] = x[3 * j + c] - x[3 * i + c];
+                u[c] = v[3 * j + c] - v[3 * i + c];
+            }
+            double s2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + eps2;
+            double s = sqrt(s2);
+            double s3 = s2 * s, s5 = s3 * s2;
+            double ru = r[0] * u[0] + r[1] * u[1] + r[2] * u[2];
+            for (int c = 0; c < 3; ++c) {
+                a[c] += m[j] * r[c] / s3;
+                jk[c] += m[j] * (u[c] / s3 - 3.0 * ru * r[c] / s5);
+            }
+        }
+        for (int c = 0; c < 3; ++c) {
+            acc[3 * i + c] = G * a[c];
+            jerk[3 * i + c] = G * jk[c];
+        }
     }
 }
 
