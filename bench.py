@@ -342,7 +342,47 @@ def extras(nb, torch, dev, g, eps):
     ex["energy_drift_100_steps"] = float((E1 - E0) / abs(E0))
     ex.update(batched_extras(nb, torch, dev))
     ex.update(adjoint_extras(nb, torch, dev))
+    ex.update(secondary_kernel_extras(nb, torch, dev, pos, eps))
     return ex
+
+
+def _device_ms(torch, fn, reps=5):
+    fn()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def secondary_kernel_extras(nb, torch, dev, pos, eps):
+    """Throughput of the other force forms on the same GPU (device time per call):
+    LJ + Coulomb on the 8192-atom sphere, acceleration + jerk and an active subset
+    of 1024 targets on the N = 262144 Plummer sphere."""
+    import workloads
+    out = {}
+    s = workloads.ljc_sphere(8192, seed=2)
+    x, v, m, q, st, et = s.f32()
+    lpos = torch.from_numpy(np.concatenate([x, m[:, None]], 1)).to(dev).contiguous()
+    prm = nb.pack_ljc(torch.from_numpy(q.astype(np.float64)).to(dev),
+                      torch.from_numpy(st.astype(np.float64)[s.types]).to(dev),
+                      torch.from_numpy(et.astype(np.float64)[s.types]).to(dev),
+                      torch.from_numpy(s.types).to(dev), kq=332.0637 / 80.0)
+    ms = _device_ms(torch, lambda: nb.forces(lpos, prm))
+    out["ljc_8192_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
+    n = pos.shape[0]
+    vel = torch.zeros_like(pos)
+    ms = _device_ms(torch, lambda: nb.forces_jerk(pos, vel, eps=eps), reps=3)
+    out["jerk_262144_gpairs_per_s"] = float(n) ** 2 / ms / 1e6
+    idx = torch.from_numpy(np.random.default_rng(1).choice(n, 1024, replace=False)
+                           .astype(np.int32)).to(dev)
+    ms = _device_ms(torch, lambda: nb.forces_subset(pos, idx, eps=eps))
+    out["subset_1024_of_262144_gpairs_per_s"] = 1024.0 * n / ms / 1e6
+    return out
 
 
 def _ensemble_arrays(nb, torch, dev, ens):

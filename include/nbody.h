@@ -146,6 +146,16 @@ int nbody_pack_ljc(const double *q, const double *sigma, const double *eps,
 int nbody_forces(const void *pos_m, const void *prm, void *acc, void *acc_lo, int64_t n,
                  const nbody_params *params, nbody_stream_t stream);
 
+/* nbody_forces_jerk -- acceleration and its time derivative (jerk), Table 1
+ * "Gravity (accel & jerk)", the force evaluation of 4th-order Hermite schemes:
+ *   a_i = G sum_{j!=i} m_j r / s^3,
+ *   j_i = G sum_{j!=i} m_j [ u / s^3 - 3 (r . u) r / s^5 ],
+ *   r = x_j - x_i, u = v_j - v_i, s^2 = |r|^2 + eps2.
+ *   pos_m, vel : n float4 in; acc, jerk : n float4 out (w = 0). Gravity law only;
+ *   NBODY_NO_COMPENSATION is the only accepted flag. Device pointers only. */
+int nbody_forces_jerk(const void *pos_m, const void *vel, void *acc, void *jerk, int64_t n,
+                      const nbody_params *params, nbody_stream_t stream);
+
 /* nbody_forces_subset -- forces on n_active target particles idx[0..n_active)
  * against all n sources (block time steps, Sec. 3.4: forces on only a subset of
  * the particles at a time). Same laws, flags and accuracy as nbody_forces.

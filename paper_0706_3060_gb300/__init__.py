@@ -9,14 +9,14 @@ from . import _lib
 from ._lib import (ACC_VALID, ACCUMULATE, COMPUTE_POT, LAW_GRAV, LAW_LJC, NO_COMPENSATION,
                    PRECISE_RSQRT, NBodyError)
 from .api import (COULOMB_K, BatchPlan, adjoint, adjoint_leapfrog, forces, forces_batched,
-                  forces_subset,
+                  forces_jerk, forces_subset,
                   get_config, pack_grav, pack_ljc, params, release, set_tuned, step, sync_check,
                   tile_count, tile_info, timing_enable, timing_read, version)
 
 __all__ = [
     "ACC_VALID", "ACCUMULATE", "COMPUTE_POT", "LAW_GRAV", "LAW_LJC", "NO_COMPENSATION",
     "PRECISE_RSQRT", "NBodyError", "COULOMB_K", "BatchPlan", "adjoint", "adjoint_leapfrog",
-    "forces", "forces_batched", "forces_subset", "get_config", "pack_grav", "pack_ljc", "params", "release",
+    "forces", "forces_batched", "forces_jerk", "forces_subset", "get_config", "pack_grav", "pack_ljc", "params", "release",
     "set_tuned", "step", "sync_check", "tile_count", "tile_info", "timing_enable",
     "timing_read", "version",
 ]

@@ -147,6 +147,19 @@ def forces_subset(pos_m, idx, prm=None, *, law=None, G=1.0, eps=0.0, pot=False, 
     return acc
 
 
+def forces_jerk(pos_m, vel, *, G=1.0, eps=0.0, compensated=True, stream=None):
+    """Acceleration and jerk (Table 1 GAJ): returns (acc, jerk), each (n, 4)."""
+    _check4(pos_m, "pos_m")
+    _check4(vel, "vel")
+    acc = torch.empty_like(pos_m)
+    jerk = torch.empty_like(pos_m)
+    p = params(LAW_GRAV, G, eps, compensated=compensated)
+    check(_lib().nbody_forces_jerk(_ptr(pos_m), _ptr(vel), _ptr(acc), _ptr(jerk), pos_m.shape[0],
+                                   ctypes.byref(p), _stream(stream, pos_m.device)),
+          "nbody_forces_jerk")
+    return acc, jerk
+
+
 def step(pos_m, vel, acc, prm=None, *, dt, nsteps=1, law=None, G=1.0, eps=0.0,
          report_every=0, acc_valid=False, pot=False, precise=False, compensated=True,
          tile=-1, jsplit=0, trace=None, diag=None, state_lo=None, stream=None):

@@ -57,7 +57,10 @@ const VjpDesc &vjp_tile(int law, int64_t n) {
   static const VjpDesc grav_small = VjpImpl<kLawGrav, 128, 2, 4, 256>::desc();
   static const VjpDesc ljc_big = VjpImpl<kLawLJC, 256, 2, 1, 256>::desc();
   static const VjpDesc ljc_small = VjpImpl<kLawLJC, 128, 1, 4, 256>::desc();
+  static const VjpDesc gaj_big = VjpImpl<kLawGAJ, 256, 2, 1, 256>::desc();
+  static const VjpDesc gaj_small = VjpImpl<kLawGAJ, 128, 2, 4, 256>::desc();
   if (law == NBODY_LAW_GRAV) return n >= 8192 ? grav_big : grav_small;
+  if (law == kLawGAJ) return n >= 8192 ? gaj_big : gaj_small;
   return n >= 8192 ? ljc_big : ljc_small;
 }
 
@@ -88,7 +91,7 @@ int vjp_prepare(int law, int n, int sms, cudaStream_t s, VjpScratch *sc) {
   }
   const int len = int(round_up(size_t((n + S - 1) / S), size_t(d.jt)));
   S = (n + len - 1) / len;
-  const int blocks = law == NBODY_LAW_LJC ? 2 : 1;
+  const int blocks = (law == NBODY_LAW_LJC || law == kLawGAJ) ? 2 : 1;
   const size_t part = round_up(size_t(blocks) * S * size_t(n) * sizeof(float4), 256);
   const size_t ubytes = round_up(size_t(n) * sizeof(float4), 256);
   const int nblk = (n + 255) / 256;
@@ -270,6 +273,56 @@ int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k
     NB_TRY(vjp_once(X + size_t(st) * size_t(n), q, lv, lx, grad_m, grad_types, ntypes, w, 1,
                     int(n), p, sc, st > 0 ? lv : nullptr, dt, s));
   }
+  return NBODY_OK;
+}
+
+int nbody_forces_jerk(const void *pos_m, const void *vel, void *acc, void *jerk, int64_t n,
+                      const nbody_params *params, nbody_stream_t stream) {
+  clear_error();
+  if (!params) return set_error_msg(NBODY_EINVAL, "params is NULL");
+  if (n < 0 || n > 0x7fffffffLL) return set_error_msg(NBODY_EINVAL, "n out of range");
+  if (n == 0) return NBODY_OK;
+  const nbody_params p = *params;
+  if (p.law != NBODY_LAW_GRAV)
+    return set_error_msg(NBODY_EINVAL, "acceleration + jerk is defined for gravity only");
+  if (p.flags & ~(uint32_t)NBODY_NO_COMPENSATION)
+    return set_error_msg(NBODY_EUNSUPPORTED, "nbody_forces_jerk supports NO_COMPENSATION only");
+  if (!(p.eps2 >= 0.0f) || !std::isfinite(p.G))
+    return set_error_msg(NBODY_EINVAL, "bad G or eps2");
+  NB_TRY(check_dev(pos_m, "pos_m", true));
+  NB_TRY(check_dev(vel, "vel", true));
+  NB_TRY(check_dev(acc, "acc", true));
+  NB_TRY(check_dev(jerk, "jerk", true));
+  int dev = 0, sms = 0;
+  NB_TRY(check_device(&dev, &sms));
+  NB_TRY(check_dev_ptrs({pos_m, vel, acc, jerk}));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  VjpScratch sc{};
+  NB_TRY(vjp_prepare(kLawGAJ, int(n), sms, s, &sc));
+  int *err = nullptr;
+  NB_TRY(error_word(&err));
+  VjpArgs a{};
+  a.pos = static_cast<const float4 *>(pos_m);
+  a.lam = static_cast<const float4 *>(vel);
+  a.part_hi = sc.part_hi;
+  a.part_lo = sc.part_lo;
+  a.stride = n;
+  a.bstride = sc.bstride;
+  a.err = err;
+  a.n = int(n);
+  a.slices = sc.slices;
+  a.slice_len = sc.slice_len;
+  a.eps2 = p.eps2;
+  a.comp = (p.flags & NBODY_NO_COMPENSATION) ? 0 : 1;
+  const TimerMark tm = timer_begin(0, s);
+  cudaError_t e = sc.d->launch(a, sc.grid, s);
+  timer_end(tm, s);
+  if (e != cudaSuccess)
+    return set_error_msg(NBODY_ECUDA, "jerk kernel launch failed: %s", cudaGetErrorString(e));
+  gaj_finalize_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(
+      sc.part_hi, sc.part_lo, n, sc.bstride, sc.slices, int(n), p.G, static_cast<float4 *>(acc),
+      static_cast<float4 *>(jerk));
+  NB_CUDA(cudaGetLastError());
   return NBODY_OK;
 }
 

@@ -22,9 +22,12 @@
 
 namespace nbody {
 
+// Table 1 "Gravity (accel & jerk)" runs on this kernel's two-accumulator pipeline.
+constexpr int kLawGAJ = 3;
+
 struct VjpArgs {
   const float4 *pos;   // (x, y, z, m)
-  const float4 *lam;   // gravity: lam; LJC: u = lam / m
+  const float4 *lam;   // gravity: lam; LJC: u = lam / m; GAJ: velocities
   const float4 *prm;   // LJC parameters or null
   const float4 *jpair; // packed gravity: (x x y y)(z z m m)(lx lx ly ly)(lz lz 0 0) per pair
   float4 *part_hi;     // [2][slices][stride]: block A then block B (LJC)
@@ -140,6 +143,33 @@ __device__ __forceinline__ void ljc_vjp_pair(const float4 pj, const float4 uj, c
   B.w = fmaf(dw, phi_lj, B.w);
 }
 
+// Acceleration and jerk (Table 1 GAJ): d = x_j - x_k, u = v_j - v_k, y = 1/s,
+// w = m_j y^3:  A += w d;  B += w (u - 3 (d.u) y^2 d).
+template <bool MASK>
+__device__ __forceinline__ void gaj_pair(const float4 pj, const float4 vj, float xk, float yk,
+                                         float zk, float vxk, float vyk, float vzk, float eps2,
+                                         float4 &A, float4 &B, bool self) {
+  const float dx = pj.x - xk;
+  const float dy = pj.y - yk;
+  const float dz = pj.z - zk;
+  const float ux = vj.x - vxk;
+  const float uy = vj.y - vyk;
+  const float uz = vj.z - vzk;
+  const float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+  float y = rsqrt_hw(s2);
+  if (MASK) y = self ? 0.0f : y;
+  const float y2 = y * y;
+  const float w = (pj.w * y) * y2;
+  const float ru = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+  const float c = ru * (3.0f * y2);
+  A.x = fmaf(w, dx, A.x);
+  A.y = fmaf(w, dy, A.y);
+  A.z = fmaf(w, dz, A.z);
+  B.x = fmaf(w, fmaf(-c, dx, ux), B.x);
+  B.y = fmaf(w, fmaf(-c, dy, uy), B.y);
+  B.z = fmaf(w, fmaf(-c, dz, uz), B.z);
+}
+
 template <int LAW, int NT, int I, int SW, int JT, bool PK = false>
 struct VjpTile {
   static constexpr int kThreads = NT + 32;
@@ -194,6 +224,8 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
   constexpr int SLOTS = T::kSlots;
   constexpr int TI = T::kTileI;
   constexpr bool LJ = (LAW == kLawLJC);
+  constexpr bool GJ = (LAW == kLawGAJ);
+  constexpr bool TWO = LJ || GJ;  // second accumulator block in use
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float4 *sm_pos = reinterpret_cast<float4 *>(smem_raw);
@@ -342,6 +374,28 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
                                 pA[r], jg == ig[r]);
         }
       }
+    } else if (GJ) {
+      if (!masked) {
+#pragma unroll 2
+        for (int jj = jl; jj < len; jj += SW) {
+          const float4 pj = sp[jj];
+          const float4 vj = sl[jj];
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            gaj_pair<false>(pj, vj, xk[r], yk[r], zk[r], lx[r], ly[r], lz[r], a.eps2, pA[r], pB[r],
+                            false);
+        }
+      } else {
+        for (int jj = jl; jj < len; jj += SW) {
+          const float4 pj = sp[jj];
+          const float4 vj = sl[jj];
+          const int jg = cj0 + jj;
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            gaj_pair<true>(pj, vj, xk[r], yk[r], zk[r], lx[r], ly[r], lz[r], a.eps2, pA[r], pB[r],
+                           jg == ig[r]);
+        }
+      }
     } else if (!LJ) {
       if (!masked) {
 #pragma unroll 2
@@ -393,7 +447,7 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
 #pragma unroll
     for (int r = 0; r < I; ++r) {
       comp_fold(hA[r], oA[r], pA[r], a.comp);
-      if (LJ) comp_fold(hB[r], oB[r], pB[r], a.comp);
+      if (TWO) comp_fold(hB[r], oB[r], pB[r], a.comp);
     }
   }
 
@@ -402,7 +456,7 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
 #pragma unroll
     for (int r = 0; r < I; ++r) {
       shfl_combine(hA[r], oA[r], off);
-      if (LJ) shfl_combine(hB[r], oB[r], off);
+      if (TWO) shfl_combine(hB[r], oB[r], off);
     }
   }
   if (jl == 0) {
@@ -412,7 +466,7 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
       if (ig[r] < 0) continue;
       a.part_hi[base + ig[r]] = hA[r];
       a.part_lo[base + ig[r]] = oA[r];
-      if (LJ) {
+      if (TWO) {
         a.part_hi[a.bstride + base + ig[r]] = hB[r];
         a.part_lo[a.bstride + base + ig[r]] = oB[r];
       }
@@ -535,6 +589,38 @@ __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs
       f.type_part[(size_t)blockIdx.x * 8 + threadIdx.x] = s;
     }
   }
+}
+
+// GAJ: fixed-order compensated sum of the per-slice partials of A (acceleration)
+// and B (jerk), scaled by G.
+__global__ void __launch_bounds__(256) gaj_finalize_kernel(const float4 *part_hi,
+                                                           const float4 *part_lo,
+                                                           long long stride, long long bstride,
+                                                           int slices, int n, float G,
+                                                           float4 *acc, float4 *jerk) {
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  if (i >= n) return;
+  float4 hA = part_hi[i], oA = part_lo[i];
+  float4 hB = part_hi[bstride + i], oB = part_lo[bstride + i];
+  for (int k = 1; k < slices; ++k) {
+    const long long o = (long long)k * stride + i;
+    const float4 a = part_hi[o], la = part_lo[o], b = part_hi[bstride + o],
+                 lb = part_lo[bstride + o];
+    comp_add(hA.x, oA.x, a.x);
+    comp_add(hA.y, oA.y, a.y);
+    comp_add(hA.z, oA.z, a.z);
+    comp_add(hB.x, oB.x, b.x);
+    comp_add(hB.y, oB.y, b.y);
+    comp_add(hB.z, oB.z, b.z);
+    oA.x += la.x;
+    oA.y += la.y;
+    oA.z += la.z;
+    oB.x += lb.x;
+    oB.y += lb.y;
+    oB.z += lb.z;
+  }
+  acc[i] = make_float4(G * (hA.x + oA.x), G * (hA.y + oA.y), G * (hA.z + oA.z), 0.0f);
+  jerk[i] = make_float4(G * (hB.x + oB.x), G * (hB.y + oB.y), G * (hB.z + oB.z), 0.0f);
 }
 
 // Sum per-block type partials in order and add them into out[0..2*ntypes).

@@ -219,3 +219,25 @@ def test_ljc_subset():
     acc = nb.forces_subset(pos, torch.from_numpy(idx).to(dev()), prm).cpu().numpy()
     sysm, x, _ = oracle_ljc_system(s)
     assert_forces_close(acc[:, :3], sysm.accel(x)[idx], what="LJC subset")
+
+
+@pytest.mark.parametrize("n", [2, 33, 1000, 9001])
+def test_grav_acceleration_and_jerk(n):
+    """Table 1 "Gravity (accel & jerk)" against the FP64 oracle."""
+    nb = lib()
+    g = workloads.plummer(n, seed=300 + n, eps=0.01)
+    pos, vel = grav_tensors(g)
+    acc, jerk = nb.forces_jerk(pos, vel, eps=float(np.float32(g.eps)))
+    x, v, m = g.f32_as_f64()
+    ra, rj = oracle.grav_jerk(x, v, m, eps=float(np.float32(g.eps)))
+    assert_forces_close(acc[:, :3].cpu().numpy(), ra, what=f"GAJ acc n={n}")
+    assert_forces_close(jerk[:, :3].cpu().numpy(), rj, what=f"GAJ jerk n={n}")
+
+
+def test_jerk_unsoftened_pair():
+    nb = lib()
+    pos = torch.tensor([[0, 0, 0, 5.0], [3, 4, 0, 2.0]], dtype=torch.float32, device=dev())
+    vel = torch.tensor([[0, 0, 0, 0], [1, 0, 0, 0]], dtype=torch.float32, device=dev())
+    acc, jerk = nb.forces_jerk(pos, vel, eps=0.0)
+    np.testing.assert_allclose(jerk[0, :3].cpu().numpy(), [-0.00128, -0.02304, 0.0], rtol=2e-6,
+                               atol=1e-9)
