@@ -77,6 +77,9 @@ def _load():
             lib.oracle_grav_jerk.argtypes = [i64, d, d, d, ctypes.c_double, ctypes.c_double,
                                              d, d]
             lib.oracle_grav_jerk.restype = None
+            lib.oracle_ljc_model.argtypes = [i64, d, d, d, d, ctypes.c_double, ctypes.c_int,
+                                             i64, i64p, d, d]
+            lib.oracle_ljc_model.restype = None
             lib.oracle_grav_vjp.argtypes = [i64, d, d, ctypes.c_double, ctypes.c_double,
                                             d, d, d]
             lib.oracle_ljc_vjp.argtypes = [i64, d, d, d, i32p, ctypes.c_int32, d, d,
@@ -149,12 +152,13 @@ def grav_jerk(x, v, m, G=1.0, eps=0.0):
     return acc, jerk
 
 
-def ljc_force(x, q, sig, eps, kq=COULOMB_K / 80.0, idx=None, potential=False):
+def ljc_force(x, q, sig, eps, kq=COULOMB_K / 80.0, idx=None, potential=False, linear=False):
     """Table 1 LJC(constant): Coulomb with dielectric plus 12-6 Lennard-Jones.
 
     Per-particle q, sig, eps (n,); ``kq`` = k_e / eps_r. Returns the force
     F (ni, 3) (acceleration is F / m) and optionally phi (ni,) with
-    U = 1/2 sum phi.
+    U = 1/2 sum phi. With ``linear`` the dielectric grows linearly with
+    distance (Table 1 LJC(linear)): Coulomb energy kq q_i q_j / r^2, kq = k_e / D.
     """
     lib = _load()
     x = _f64(x, (-1, 3))
@@ -164,8 +168,8 @@ def ljc_force(x, q, sig, eps, kq=COULOMB_K / 80.0, idx=None, potential=False):
     ni = n if idx is None else idx.shape[0]
     f = np.zeros((ni, 3))
     phi = np.zeros(ni) if potential else None
-    lib.oracle_ljc(n, _dp(x), _dp(q), _dp(sig), _dp(eps), float(kq), ni, idxp, _dp(f),
-                   _dp(phi))
+    lib.oracle_ljc_model(n, _dp(x), _dp(q), _dp(sig), _dp(eps), float(kq), 1 if linear else 0,
+                         ni, idxp, _dp(f), _dp(phi))
     return (f, phi) if potential else f
 
 
@@ -237,7 +241,8 @@ class LJCSystem:
 
     law = "ljc"
 
-    def __init__(self, m, q, types, sig_t, eps_t, kq=COULOMB_K / 80.0):
+    def __init__(self, m, q, types, sig_t, eps_t, kq=COULOMB_K / 80.0, linear=False):
+        self.linear = bool(linear)
         self.m = _f64(m)
         self.q = _f64(q)
         self.types = np.asarray(types, dtype=np.int32)
@@ -248,7 +253,7 @@ class LJCSystem:
     def accel(self, x, potential=False):
         sig = self.sig_t[self.types]
         eps = self.eps_t[self.types]
-        out = ljc_force(x, self.q, sig, eps, self.kq, potential=potential)
+        out = ljc_force(x, self.q, sig, eps, self.kq, potential=potential, linear=self.linear)
         if potential:
             f, phi = out
             return f / self.m[:, None], phi
@@ -257,7 +262,7 @@ class LJCSystem:
     def potential_energy(self, x):
         sig = self.sig_t[self.types]
         eps = self.eps_t[self.types]
-        _, phi = ljc_force(x, self.q, sig, eps, self.kq, potential=True)
+        _, phi = ljc_force(x, self.q, sig, eps, self.kq, potential=True, linear=self.linear)
         return 0.5 * float(np.sum(phi))
 
     def vjp(self, x, lam):

@@ -12,6 +12,7 @@
  *   - oracle_grav       Eq. 1 of Sec. 3.3 / Table 1 "Gravity (accel)"
  *   - oracle_ljc        Table 1 "LJC (constant)" (readings C1, C2, C4 below)
  *   - oracle_grav_jerk  Table 1 "Gravity (accel & jerk)"
+ *   - oracle_ljc_model  Table 1 "LJC (linear)" as well (reading C3 below)
  *   - oracle_grav_vjp   transpose of the Jacobian of Eq. 1, block by block
  *   - oracle_ljc_vjp    transpose of the Jacobian of the LJC law, plus the
  *                       derivatives w.r.t. per-type sigma, epsilon and masses
@@ -24,6 +25,9 @@
  *   C2  Coulomb in a continuum solvent of constant dielectric eps_r:
  *       force k_e q_i q_j r_ij / (eps_r r^3); the caller passes
  *       ke_over_epsr = k_e / eps_r.
+ *   C3  "LJC(linear)" prints q_i q_j r_ij / r^4 without the factor 2 of
+ *       -grad(1/r^2); we use the energy kq q_i q_j / r^2 (dielectric D r,
+ *       kq = k_e / D) and its force 2 kq q_i q_j r_ij / r^4.
  *   C4  Lorentz-Berthelot mixing: sigma_ij = (sigma_i + sigma_j)/2,
  *       eps_ij = sqrt(eps_i eps_j).
  *   C5  The self pair i == j is excluded by index, as in the Appendix
@@ -116,6 +120,10 @@ void oracle_grav_jerk(int64_t n, const double *x, const double *v, const double 
     }
 }
 
+void oracle_ljc_model(int64_t n, const double *x, const double *q, const double *sig,
+                      const double *eps, double kq, int model, int64_t ni,
+                      const int64_t *idx, double *force, double *phi);
+
 /* ---------------------------------------------------------------------------
  * Lennard-Jones + Coulomb with a constant dielectric, Table 1 "LJC(constant)"
  * with readings C1, C2, C4, C5:
@@ -128,6 +136,19 @@ void oracle_grav_jerk(int64_t n, const double *x, const double *v, const double 
 void oracle_ljc(int64_t n, const double *x, const double *q, const double *sig,
                 const double *eps, double kq, int64_t ni, const int64_t *idx,
                 double *force, double *phi)
+{
+    oracle_ljc_model(n, x, q, sig, eps, kq, 0, ni, idx, force, phi);
+}
+
+/* ---------------------------------------------------------------------------
+ * LJC with a dielectric model: model 0 is the constant dielectric above; model 1
+ * is Table 1 "LJC(linear)", a dielectric growing linearly with distance,
+ * eps(r) = D r (reading C3: the Coulomb energy is kq q_i q_j / r^2 with
+ * kq = k_e / D, so its force is 2 kq q_i q_j r_ij / r^4).
+ * ------------------------------------------------------------------------- */
+void oracle_ljc_model(int64_t n, const double *x, const double *q, const double *sig,
+                      const double *eps, double kq, int model, int64_t ni,
+                      const int64_t *idx, double *force, double *phi)
 {
 #pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < ni; ++k) {
@@ -145,13 +166,15 @@ void oracle_ljc(int64_t n, const double *x, const double *q, const double *sig,
             double eij = sqrt(eps[i] * eps[j]);
             double sr6 = pow(sij / r, 6.0);
             double sr12 = sr6 * sr6;
-            double fc = kq * q[i] * q[j] / (r2 * r);
+            double fc = model == 1 ? 2.0 * kq * q[i] * q[j] / (r2 * r2)
+                                   : kq * q[i] * q[j] / (r2 * r);
             double flj = 24.0 * eij * (2.0 * sr12 - sr6) / r2;
             double f = fc + flj;
             fx += f * rx;
             fy += f * ry;
             fz += f * rz;
-            p += kq * q[i] * q[j] / r + 4.0 * eij * (sr12 - sr6);
+            p += (model == 1 ? kq * q[i] * q[j] / r2 : kq * q[i] * q[j] / r)
+                 + 4.0 * eij * (sr12 - sr6);
         }
         force[3 * k + 0] = fx;
         force[3 * k + 1] = fy;

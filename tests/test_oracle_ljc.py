@@ -89,3 +89,32 @@ def test_generator_constraints():
     assert abs(s.q.sum()) < 1e-12 and np.all(np.abs(s.q) <= 1.6)
     assert np.all((s.sig_t >= 2.5) & (s.sig_t <= 3.8))
     assert np.all((s.eps_t >= 0.05) & (s.eps_t <= 0.2))
+
+
+def test_linear_dielectric_coulomb_hand_values():
+    # Table 1 LJC(linear) with dielectric D r, D = 4: kq = 332.0637 / 4 = 83.015925.
+    # Energy kq q1 q2 / r^2 = 83.015925 * (-0.2) / 16 = -1.0376990625,
+    # force magnitude 2 kq |q1 q2| / r^3 = 2 * 83.015925 * 0.2 / 64 = 0.518849531...
+    kq = 332.0637 / 4.0
+    x = np.array([[0.0, 0.0, 0.0], [4.0, 0.0, 0.0]])
+    f, phi = oracle.ljc_force(x, np.array([0.5, -0.4]), np.array([3.0, 3.0]), np.zeros(2),
+                              kq=kq, potential=True, linear=True)
+    np.testing.assert_allclose(f[0], [0.51884953125, 0.0, 0.0], rtol=1e-12)
+    np.testing.assert_allclose(phi, [-1.0376990625, -1.0376990625], rtol=1e-12)
+
+
+def test_linear_dielectric_force_is_minus_gradient():
+    s = workloads.ljc_sphere(150, seed=15)
+    sig, eps = s.sig_t[s.types], s.eps_t[s.types]
+    kq = 332.0637 / 4.0
+    f = oracle.ljc_force(s.x, s.q, sig, eps, kq, linear=True)
+    assert np.all(np.abs(f.sum(axis=0)) <= 1e-13 * np.abs(f).sum())
+    h = 1e-5
+    for i in (3, 77):
+        for a in range(3):
+            xp, xm = s.x.copy(), s.x.copy()
+            xp[i, a] += h
+            xm[i, a] -= h
+            _, pp = oracle.ljc_force(xp, s.q, sig, eps, kq, idx=[i], potential=True, linear=True)
+            _, pm = oracle.ljc_force(xm, s.q, sig, eps, kq, idx=[i], potential=True, linear=True)
+            assert abs(-(pp[0] - pm[0]) / (2 * h) - f[i, a]) <= 1e-6 * max(1e-3, np.abs(f[i]).max())
