@@ -59,8 +59,14 @@ typedef enum {
 
 /* Force laws (Table 1). */
 enum {
-    NBODY_LAW_GRAV = 0, /* "Gravity (accel)", Eq. 1                        */
-    NBODY_LAW_LJC = 1,  /* "LJC(constant)": LJ 12-6 + Coulomb / eps_r       */
+    NBODY_LAW_GRAV = 0,       /* "Gravity (accel)", Eq. 1                          */
+    NBODY_LAW_LJC = 1,        /* "LJC(constant)": LJ 12-6 + Coulomb / eps_r         */
+    NBODY_LAW_LJC_LINEAR = 2, /* "LJC(linear)": LJ 12-6 + Coulomb with a dielectric
+                                 growing linearly with distance, energy
+                                 kq q_i q_j / r^2 (kq = k_e / D, packed into prm
+                                 by nbody_pack_ljc), force 2 kq q_i q_j r_ij / r^4.
+                                 Forces, steps, subsets and the static variant
+                                 only (no batched or adjoint form).             */
 };
 
 /* nbody_params.flags */
@@ -292,15 +298,15 @@ int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k
 /* ---------------------------------------------------------------------------
  * Tile configurations and tuning.
  * --------------------------------------------------------------------------- */
-/* Number of compiled tile configurations for `law` (0 gravity, 1 LJC,
- * 2 the mixed-law batched kernel), or a negative status. */
+/* Number of compiled tile configurations for tile table `law` (0 gravity,
+ * 1 LJC, 2 LJC linear, 3 the mixed-law batched kernel), or a negative status. */
 int nbody_tile_count(int32_t law);
 /* Describe configuration `tile` of `law`: threads per CTA (consumer warps),
  * i-particles per thread, j-lanes per warp, j-tile length. */
 int nbody_tile_info(int32_t law, int32_t tile, int32_t *threads, int32_t *i_per_thread,
                     int32_t *j_lanes, int32_t *j_tile);
-/* Install the tuned (tile, jsplit) for (law, n-bucket); bucket = floor(log2 n).
- * Used by params->tile == -1. */
+/* Install the tuned (tile, jsplit) for (tile table law, n-bucket); bucket =
+ * floor(log2 n) (the batched table uses bucket 0). Used by params->tile == -1. */
 int nbody_set_tuned(int32_t law, int32_t log2n, int32_t tile, int32_t jsplit);
 /* Query the configuration a call with (law, n) and tile == -1 would use. */
 int nbody_get_config(int32_t law, int64_t n, int32_t *tile, int32_t *jsplit);

@@ -19,6 +19,8 @@ STATUS = {0: "NBODY_OK", 1: "NBODY_EINVAL", 2: "NBODY_EALIGN", 3: "NBODY_ENOMEM"
 
 LAW_GRAV = 0
 LAW_LJC = 1
+LAW_LJC_LINEAR = 2
+TABLE_BATCHED = 3  # tile table of the batched mixed-law kernel
 
 COMPUTE_POT = 1 << 0
 PRECISE_RSQRT = 1 << 1

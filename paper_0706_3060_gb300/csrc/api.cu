@@ -45,12 +45,12 @@ constexpr int kMaxN = 0x7fffffff;
 
 int check_params(const nbody_params *p, const void *prm) {
   if (!p) return set_error_msg(NBODY_EINVAL, "params is NULL");
-  if (p->law != NBODY_LAW_GRAV && p->law != NBODY_LAW_LJC)
+  if (p->law != NBODY_LAW_GRAV && p->law != NBODY_LAW_LJC && p->law != NBODY_LAW_LJC_LINEAR)
     return set_error_msg(NBODY_EINVAL, "unknown law %d", p->law);
   const uint32_t known = NBODY_COMPUTE_POT | NBODY_PRECISE_RSQRT | NBODY_NO_COMPENSATION |
                          NBODY_ACC_VALID | NBODY_ACCUMULATE;
   if (p->flags & ~known) return set_error_msg(NBODY_EINVAL, "unknown flag bits 0x%x", p->flags);
-  if (p->law == NBODY_LAW_LJC && !prm)
+  if (p->law != NBODY_LAW_GRAV && !prm)
     return set_error_msg(NBODY_EINVAL, "LJC law needs the prm array");
   if (p->law == NBODY_LAW_GRAV && !(p->eps2 >= 0.0f))
     return set_error_msg(NBODY_EINVAL, "eps2 must be >= 0");
@@ -349,7 +349,7 @@ int nbody_timing_read(int32_t which, int64_t *launches, double *total_ms) {
 
 int nbody_tile_count(int32_t law) {
   clear_error();
-  if (law < 0 || law > 2) return set_error_msg(-NBODY_EINVAL, "bad law %d", law);
+  if (law < 0 || law >= kTables) return set_error_msg(-NBODY_EINVAL, "bad law %d", law);
   int count = 0;
   tiles_for(law, &count);
   return count;
@@ -358,7 +358,7 @@ int nbody_tile_count(int32_t law) {
 int nbody_tile_info(int32_t law, int32_t tile, int32_t *threads, int32_t *i_per_thread,
                     int32_t *j_lanes, int32_t *j_tile) {
   clear_error();
-  if (law < 0 || law > 2) return set_error_msg(NBODY_EINVAL, "bad law %d", law);
+  if (law < 0 || law >= kTables) return set_error_msg(NBODY_EINVAL, "bad law %d", law);
   int count = 0;
   const TileDesc *t = tiles_for(law, &count);
   if (tile < 0 || tile >= count) return set_error_msg(NBODY_EINVAL, "bad tile %d", tile);
@@ -376,7 +376,7 @@ int nbody_set_tuned(int32_t law, int32_t log2n, int32_t tile, int32_t jsplit) {
 
 int nbody_get_config(int32_t law, int64_t n, int32_t *tile, int32_t *jsplit) {
   clear_error();
-  if (law < 0 || law > 2) return set_error_msg(NBODY_EINVAL, "bad law %d", law);
+  if (law < 0 || law >= kTables) return set_error_msg(NBODY_EINVAL, "bad law %d", law);
   if (!tile || !jsplit) return set_error_msg(NBODY_EINVAL, "NULL output");
   int t = 0, j = 0;
   get_config(law, n, &t, &j);

@@ -131,13 +131,13 @@ int nbody_batch_plan_create(const nbody_system *systems, int32_t nsys, uint32_t 
   if (flags & ~(uint32_t)(NBODY_PRECISE_RSQRT | NBODY_NO_COMPENSATION))
     return set_error_msg(NBODY_EINVAL, "unsupported plan flags 0x%x", flags);
   int count = 0;
-  const TileDesc *tiles = tiles_for(2, &count);
+  const TileDesc *tiles = tiles_for(kTableBatched, &count);
   if (tile < -1 || tile >= count) return set_error_msg(NBODY_EINVAL, "bad tile %d", tile);
   int dev = 0, sms = 0;
   NB_TRY(check_device(&dev, &sms));
   if (tile < 0) {
     int tj = 0;
-    get_config(2, 0, &tile, &tj);
+    get_config(kTableBatched, 0, &tile, &tj);
     if (tile < 0 || tile >= count) tile = 0;
   }
   const TileDesc *td = &tiles[tile];
@@ -150,7 +150,8 @@ int nbody_batch_plan_create(const nbody_system *systems, int32_t nsys, uint32_t 
     if (s.n < 1 || s.offset < 0 || s.offset + s.n > 0x7fffffffLL)
       return set_error_msg(NBODY_EINVAL, "system %d: bad offset/n", k);
     if (s.law != NBODY_LAW_GRAV && s.law != NBODY_LAW_LJC)
-      return set_error_msg(NBODY_EINVAL, "system %d: unknown law %d", k, s.law);
+      return set_error_msg(s.law == NBODY_LAW_LJC_LINEAR ? NBODY_EUNSUPPORTED : NBODY_EINVAL,
+                           "system %d: law %d not available in batched runs", k, s.law);
     if (!(s.eps2 >= 0.0f) || !std::isfinite(s.G) || !std::isfinite(s.dt))
       return set_error_msg(NBODY_EINVAL, "system %d: bad G / eps2 / dt", k);
     total = std::max<int64_t>(total, s.offset + s.n);

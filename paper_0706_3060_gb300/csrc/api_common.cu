@@ -28,7 +28,7 @@ struct Tuned {
   int tile = -1;
   int jsplit = 0;
 };
-Tuned g_tuned[3][64];
+Tuned g_tuned[kTables][64];
 
 int grow(std::map<std::pair<int, cudaStream_t>, Arena> &tab, cudaStream_t s, size_t bytes,
          void **out) {
@@ -255,11 +255,12 @@ int timing_read(int which, int64_t *launches, double *total_ms) {
 const TileDesc *tiles_for(int law, int *count) {
   if (law == NBODY_LAW_GRAV) return grav_tiles(count);
   if (law == NBODY_LAW_LJC) return ljc_tiles(count);
+  if (law == NBODY_LAW_LJC_LINEAR) return ljclin_tiles(count);
   return mixed_tiles(count);
 }
 
 int set_tuned(int law, int log2n, int tile, int jsplit) {
-  if (law < 0 || law > 2 || log2n < 0 || log2n >= 64)
+  if (law < 0 || law >= kTables || log2n < 0 || log2n >= 64)
     return set_error_msg(NBODY_EINVAL, "bad law %d or log2n %d", law, log2n);
   int count = 0;
   tiles_for(law, &count);
@@ -280,7 +281,8 @@ static int log2_floor(int64_t n) {
 // Default tile when nothing is tuned: big register blocks for large N, j-lanes
 // inside the warp for small N (where there are too few targets to fill the GPU).
 static int default_tile(int law, int64_t n) {
-  if (law == 2) return 0;  // mixed-law batched kernel
+  if (law == kTableBatched) return 0;
+  if (law == NBODY_LAW_LJC_LINEAR) return n >= 16384 ? 3 : (n >= 1024 ? 1 : 2);
   if (law == NBODY_LAW_GRAV) {
     if (n >= 65536) return 0;
     if (n >= 8192) return 3;
@@ -381,7 +383,7 @@ __global__ void interleave_ljc_pairs_kernel(const float4 *pos, const float4 *prm
 
 size_t jbuf_bytes(int law, int64_t n) {
   const size_t pairs = size_t((n + 1) / 2);
-  return round_up(pairs * (law == NBODY_LAW_LJC ? 3 : 2) * sizeof(float4), 256);
+  return round_up(pairs * (law == NBODY_LAW_GRAV ? 2 : 3) * sizeof(float4), 256);
 }
 
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
@@ -390,7 +392,7 @@ int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags,
   if (p.tile->packed) {
     if (!jbuf) return set_error_msg(NBODY_EINVAL, "packed tile without pair buffer");
     const int np = (n + 1) / 2;
-    if (law == NBODY_LAW_LJC)
+    if (law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR)
       interleave_ljc_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, prm, jbuf, n);
     else
       interleave_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, jbuf, n);

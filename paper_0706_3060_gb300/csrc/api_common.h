@@ -53,7 +53,9 @@ int error_word(int **out);
 // Synchronize `s`, then read and clear the error word.
 int sync_and_check(cudaStream_t s);
 
-// Tile tables.
+// Tile tables: 0 gravity, 1 LJC, 2 LJC linear, 3 the batched mixed-law kernel.
+constexpr int kTableBatched = 3;
+constexpr int kTables = 4;
 const TileDesc *tiles_for(int law, int *count);
 // Decide (tile, slices, slice_len) for a single-system evaluation.
 struct Plan1 {

@@ -76,11 +76,11 @@ extern "C" int nbody_forces_static(const void *pos_m, const void *prm, void *acc
     return set_error_msg(NBODY_EINVAL, "n out of range: %lld", (long long)n);
   if (n == 0) return NBODY_OK;
   const nbody_params p = *params;
-  if (p.law != NBODY_LAW_GRAV && p.law != NBODY_LAW_LJC)
+  if (p.law != NBODY_LAW_GRAV && p.law != NBODY_LAW_LJC && p.law != NBODY_LAW_LJC_LINEAR)
     return set_error_msg(NBODY_EINVAL, "unknown law %d", p.law);
   if (p.flags & ~(uint32_t)(NBODY_COMPUTE_POT | NBODY_PRECISE_RSQRT | NBODY_NO_COMPENSATION))
     return set_error_msg(NBODY_EINVAL, "unsupported flag bits 0x%x", p.flags);
-  if (p.law == NBODY_LAW_LJC && !prm) return set_error_msg(NBODY_EINVAL, "LJC needs prm");
+  if (p.law != NBODY_LAW_GRAV && !prm) return set_error_msg(NBODY_EINVAL, "LJC needs prm");
   if (!(p.eps2 >= 0.0f)) return set_error_msg(NBODY_EINVAL, "eps2 must be >= 0");
   if (!pos_m || !acc) return set_error_msg(NBODY_EINVAL, "pos_m and acc are required");
   for (const void *q : {pos_m, prm, static_cast<const void *>(acc)})
@@ -100,7 +100,7 @@ extern "C" int nbody_forces_static(const void *pos_m, const void *prm, void *acc
                          "nbody_forces_static holds %zu bytes (n <= %.0f)",
                          (long long)n, jb + 2 * per_slice, kStaticScratchBytes,
                          (kStaticScratchBytes - 1024) /
-                             ((p.law == NBODY_LAW_LJC ? 3.5 : 3.0) * sizeof(float4)));
+                             ((p.law == NBODY_LAW_GRAV ? 3.0 : 3.5) * sizeof(float4)));
 
   int dev = 0, sms = 0;
   NB_TRY(check_device(&dev, &sms));

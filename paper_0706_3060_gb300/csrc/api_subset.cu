@@ -44,11 +44,11 @@ extern "C" int nbody_forces_subset(const void *pos_m, const void *prm, const int
   if (n_active == 0) return NBODY_OK;
   if (n == 0) return set_error_msg(NBODY_EINVAL, "targets given but no sources (n = 0)");
   const nbody_params p = *params;
-  if (p.law != NBODY_LAW_GRAV && p.law != NBODY_LAW_LJC)
+  if (p.law != NBODY_LAW_GRAV && p.law != NBODY_LAW_LJC && p.law != NBODY_LAW_LJC_LINEAR)
     return set_error_msg(NBODY_EINVAL, "unknown law %d", p.law);
   if (p.flags & ~(uint32_t)(NBODY_COMPUTE_POT | NBODY_PRECISE_RSQRT | NBODY_NO_COMPENSATION))
     return set_error_msg(NBODY_EINVAL, "unsupported flag bits 0x%x", p.flags);
-  if (p.law == NBODY_LAW_LJC && !prm) return set_error_msg(NBODY_EINVAL, "LJC needs prm");
+  if (p.law != NBODY_LAW_GRAV && !prm) return set_error_msg(NBODY_EINVAL, "LJC needs prm");
   if (!(p.eps2 >= 0.0f)) return set_error_msg(NBODY_EINVAL, "eps2 must be >= 0");
   if (!pos_m || !acc || !idx) return set_error_msg(NBODY_EINVAL, "pos_m, idx and acc are required");
   for (const void *q : {pos_m, prm, static_cast<const void *>(acc)})

@@ -25,7 +25,10 @@
 
 namespace nbody {
 
-enum : int { kLawGrav = 0, kLawLJC = 1, kLawMixed = 2 };
+enum : int { kLawGrav = 0, kLawLJC = 1, kLawMixed = 2, kLawLJCLin = 4 };
+
+// LJ + Coulomb laws (constant or linear dielectric) share data layout and code.
+__host__ __device__ constexpr bool is_ljc(int law) { return law == kLawLJC || law == kLawLJCLin; }
 
 constexpr int kStages = 4;
 
@@ -133,7 +136,10 @@ __device__ __forceinline__ void grav_pair2(float2 X, float2 Y, float2 Z, float2 
 // With d = x_j - x_i, y = 1/r, u = (sigma_ij y)^6:
 //   f = q~q~ y^3 + e~e~ y^2 (2u^2 - u);  acc += f d  (force on i is -acc)
 //   pot += q~q~ y + (e~e~ / 6)(u^2 - u)
-template <bool POT, bool PRECISE, bool MASK>
+//
+// LIN (Table 1 LJC(linear), dielectric growing linearly with r): the Coulomb
+// terms become 2 q~q~ y^4 in f and q~q~ y^2 in pot.
+template <bool POT, bool PRECISE, bool MASK, bool LIN = false>
 __device__ __forceinline__ void ljc_pair(const float4 pj, const float4 qj, float xi, float yi,
                                          float zi, float qi, float si, float ei, float4 &acc,
                                          bool self) {
@@ -150,20 +156,20 @@ __device__ __forceinline__ void ljc_pair(const float4 pj, const float4 qj, float
   const float t = (s * s) * y2;
   const float u = (t * t) * t;
   const float ee = ei * qj.z;
-  const float fc = (qq * y) * y2;
+  const float fc = LIN ? (qq * y2) * (y2 + y2) : (qq * y) * y2;
   const float h = fmaf(u, 2.0f, -1.0f) * u;
   const float f = fmaf(ee * y2, h, fc);
   acc.x = fmaf(f, dx, acc.x);
   acc.y = fmaf(f, dy, acc.y);
   acc.z = fmaf(f, dz, acc.z);
   if (POT) {
-    acc.w = fmaf(qq, y, acc.w);
+    acc.w = fmaf(qq, LIN ? y2 : y, acc.w);
     acc.w = fmaf(ee * (1.0f / 6.0f), fmaf(u, u, -u), acc.w);
   }
 }
 
 // LJC for two sources at once in f32x2 arithmetic (same terms as ljc_pair).
-template <bool POT, bool PRECISE>
+template <bool POT, bool PRECISE, bool LIN = false>
 __device__ __forceinline__ void ljc_pair2(float2 X, float2 Y, float2 Z, float2 Q, float2 S,
                                           float2 E, float2 nxi, float2 nyi, float2 nzi,
                                           float2 qi, float2 si, float2 ei, float2 &ax, float2 &ay,
@@ -185,14 +191,15 @@ __device__ __forceinline__ void ljc_pair2(float2 X, float2 Y, float2 Z, float2 Q
   const float2 t = __fmul2_rn(__fmul2_rn(s, s), y2);
   const float2 u = __fmul2_rn(__fmul2_rn(t, t), t);
   const float2 ee = __fmul2_rn(E, ei);
-  const float2 fc = __fmul2_rn(__fmul2_rn(qq, y), y2);
+  const float2 fc = LIN ? __fmul2_rn(__fmul2_rn(qq, y2), __fadd2_rn(y2, y2))
+                        : __fmul2_rn(__fmul2_rn(qq, y), y2);
   const float2 h = __fmul2_rn(__ffma2_rn(u, make_float2(2.0f, 2.0f), make_float2(-1.0f, -1.0f)), u);
   const float2 f = __ffma2_rn(__fmul2_rn(ee, y2), h, fc);
   ax = __ffma2_rn(f, dx, ax);
   ay = __ffma2_rn(f, dy, ay);
   az = __ffma2_rn(f, dz, az);
   if (POT) {
-    pot = __ffma2_rn(qq, y, pot);
+    pot = __ffma2_rn(qq, LIN ? y2 : y, pot);
     pot = __ffma2_rn(__fmul2_rn(ee, make_float2(1.0f / 6.0f, 1.0f / 6.0f)),
                      __ffma2_rn(u, u, make_float2(-u.x, -u.y)), pot);
   }
@@ -204,6 +211,7 @@ template <int LAW>
 struct PairLayout {
   static constexpr int kF4 = (LAW == kLawGrav) ? 2 : 3;
 };
+// (is_ljc laws use the 3-float4 layout)
 
 template <int LAW, int NT, int I, int SW, int JT>
 struct ForceTile {
@@ -219,9 +227,10 @@ template <int LAW, int NT, int I, int SW, int JT, bool POT, bool PRECISE, bool P
           int PU = 2, int MINB = 1>
 __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a) {
   using T = ForceTile<LAW, NT, I, SW, JT>;
-  static_assert(!PK || ((LAW == kLawGrav || LAW == kLawLJC) && SW == 1),
+  static_assert(!PK || ((LAW == kLawGrav || is_ljc(LAW)) && SW == 1),
                 "packed path: one law, one j-lane");
-  constexpr int PF4 = PairLayout<LAW == kLawLJC ? kLawLJC : kLawGrav>::kF4;
+  constexpr bool LIN = (LAW == kLawLJCLin);
+  constexpr int PF4 = PairLayout<is_ljc(LAW) ? kLawLJC : kLawGrav>::kF4;
   constexpr int STAGE_F4 = PK ? PF4 * JT / 2 : JT;  // float4s per ring stage
   constexpr int NWARPS = NT / 32;
   constexpr int SLOTS = T::kSlots;
@@ -273,7 +282,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
           tma_load_1d(sm_pos + st * STAGE_F4, a.jpair + (cj0 >> 1) * PF4, bytes, &full_bar[st]);
         } else {
           const uint32_t bytes = uint32_t(len) * 16u;
-          const bool with_prm = (LAW == kLawLJC) || (LAW == kLawMixed && w.law == kLawLJC);
+          const bool with_prm = is_ljc(LAW) || (LAW == kLawMixed && w.law == kLawLJC);
           mbar_arrive_expect_tx(&full_bar[st], with_prm ? 2u * bytes : bytes);
           tma_load_1d(sm_pos + st * JT, a.pos + cj0, bytes, &full_bar[st]);
           if (with_prm) tma_load_1d(sm_prm + st * JT, a.prm + cj0, bytes, &full_bar[st]);
@@ -299,7 +308,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
       w.ni = min(TI, a.n_t - w.i0);
       w.j0 = s * a.slice_len;
       w.nj = min(a.slice_len, a.n - w.j0);
-      w.law = LAW == kLawLJC ? kLawLJC : kLawGrav;
+      w.law = is_ljc(LAW) ? kLawLJC : kLawGrav;
       w.slice = s;
       w.eps2 = a.eps2;
       w.pad = 0;
@@ -341,7 +350,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
   float4 p[I], hi[I], lo[I];
   float2 pax[PK ? I : 1], pay[PK ? I : 1], paz[PK ? I : 1], ppt[PK ? I : 1];
   WorkItem cur{};
-  int cur_law = LAW == kLawLJC ? kLawLJC : kLawGrav;
+  int cur_law = is_ljc(LAW) ? kLawLJC : kLawGrav;
 
   for (int it = 0;; ++it) {
     const int st = it % kStages;
@@ -382,7 +391,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
     const bool masked = a.tidx != nullptr || ((cj0 < cur.i0 + cur.ni) && (cur.i0 < cj0 + len));
     const float eps2 = cur.eps2;
 
-    if (PK && LAW == kLawLJC) {
+    if (PK && is_ljc(LAW)) {
       if (!masked) {
         const int npairs = (len + 1) >> 1;
         float2 nx[PK ? I : 1], ny[PK ? I : 1], nz[PK ? I : 1];
@@ -403,7 +412,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
           const float4 C = sp[3 * pp + 2];
 #pragma unroll
           for (int r = 0; r < I; ++r)
-            ljc_pair2<POT, PRECISE>(make_float2(A.x, A.y), make_float2(A.z, A.w),
+            ljc_pair2<POT, PRECISE, LIN>(make_float2(A.x, A.y), make_float2(A.z, A.w),
                                     make_float2(B.x, B.y), make_float2(B.z, B.w),
                                     make_float2(C.x, C.y), make_float2(C.z, C.w), nx[r], ny[r],
                                     nz[r], q2[r], s2[r], e2[r], pax[r], pay[r], paz[r], ppt[r]);
@@ -419,7 +428,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
           const int jg = cj0 + jj;
 #pragma unroll
           for (int r = 0; r < I; ++r)
-            ljc_pair<POT, PRECISE, true>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r], p[r],
+            ljc_pair<POT, PRECISE, true, LIN>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r], p[r],
                                          jg == ig[r]);
         }
       }
@@ -493,7 +502,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
           const float4 qj = sq[jj];
 #pragma unroll
           for (int r = 0; r < I; ++r)
-            ljc_pair<POT, PRECISE, false>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r],
+            ljc_pair<POT, PRECISE, false, LIN>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r],
                                           p[r], false);
         }
       } else if (!masked) {
@@ -502,7 +511,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
           const float4 qj = sq[jj];
 #pragma unroll
           for (int r = 0; r < I; ++r)
-            ljc_pair<POT, PRECISE, false>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r],
+            ljc_pair<POT, PRECISE, false, LIN>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r],
                                           p[r], false);
         }
       } else {
@@ -512,7 +521,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
           const int jg = cj0 + jj;
 #pragma unroll
           for (int r = 0; r < I; ++r)
-            ljc_pair<POT, PRECISE, true>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r],
+            ljc_pair<POT, PRECISE, true, LIN>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r],
                                          p[r], jg == ig[r]);
         }
       }

@@ -25,9 +25,10 @@ struct TileDesc {
   ForceOccupancy occupancy;
 };
 
-// Defined in force_grav.cu / force_ljc.cu / force_mixed.cu.
+// Defined in force_grav.cu / force_ljc.cu / force_ljclin.cu / force_mixed.cu.
 const TileDesc *grav_tiles(int *count);
 const TileDesc *ljc_tiles(int *count);
+const TileDesc *ljclin_tiles(int *count);
 const TileDesc *mixed_tiles(int *count);
 
 template <int LAW, int NT, int I, int SW, int JT, bool PK = false, int PU = 2, int MINB = 1>

@@ -18,7 +18,7 @@ import os
 import numpy as np
 
 from . import api
-from ._lib import LAW_GRAV, LAW_LJC
+from ._lib import LAW_GRAV, LAW_LJC, LAW_LJC_LINEAR, TABLE_BATCHED
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
@@ -92,7 +92,7 @@ def tune(law: int, sizes, jsplits=(0, 1, 2, 4, 8, 16, 32), reps=5, verbose=True)
 
 def tune_batched(reps=3, verbose=True, nsys=512, seed=3):
     """Pick the mixed-law work-list tile for the batched ensemble (512 systems, N
-    log-uniform in [64, 4096]); stored as law 2, bucket 0."""
+    log-uniform in [64, 4096]); stored as tile table 3 (batched), bucket 0."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     rng = np.random.default_rng(seed)
@@ -121,7 +121,7 @@ def tune_batched(reps=3, verbose=True, nsys=512, seed=3):
     vel = torch.zeros_like(p)
     acc = torch.zeros_like(p)
     results = []
-    for tile in range(api.tile_count(2)):
+    for tile in range(api.tile_count(TABLE_BATCHED)):
         plan = api.BatchPlan(table, tile=tile)
         plan.run(p, vel, acc, prm, nsteps=0, graph=False)
         ts = []
@@ -140,7 +140,7 @@ def tune_batched(reps=3, verbose=True, nsys=512, seed=3):
                   f"({float(np.sum(sizes.astype(float) ** 2)) / ms / 1e6:.1f} G pairs/s)",
                   flush=True)
     ms, tile = min(results)
-    api.set_tuned(2, 1, tile, 0)
+    api.set_tuned(TABLE_BATCHED, 1, tile, 0)
     return {"0": {"n": 0, "tile": tile, "jsplit": 0, "ms": ms}}
 
 
@@ -169,7 +169,7 @@ def load_cache(path: str = CACHE) -> int:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--law", choices=["grav", "ljc", "batched"], default="grav")
+    ap.add_argument("--law", choices=["grav", "ljc", "ljclin", "batched"], default="grav")
     ap.add_argument("--n", type=int, nargs="+", default=[1024, 4096, 16384, 65536, 262144])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--save", action="store_true")
@@ -178,9 +178,9 @@ def main():
         table = tune_batched(reps=a.reps)
         print(json.dumps(table))
         if a.save:
-            save_cache(2, table)
+            save_cache(TABLE_BATCHED, table)
         return
-    law = LAW_GRAV if a.law == "grav" else LAW_LJC
+    law = {"grav": LAW_GRAV, "ljc": LAW_LJC, "ljclin": LAW_LJC_LINEAR}[a.law]
     table = tune(law, a.n, reps=a.reps)
     print(json.dumps(table))
     if a.save:

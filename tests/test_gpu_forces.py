@@ -241,3 +241,47 @@ def test_jerk_unsoftened_pair():
     acc, jerk = nb.forces_jerk(pos, vel, eps=0.0)
     np.testing.assert_allclose(jerk[0, :3].cpu().numpy(), [-0.00128, -0.02304, 0.0], rtol=2e-6,
                                atol=1e-9)
+
+
+def _ljclin_tensors(s, D=4.0):
+    nb = lib()
+    x, v, m, q, st, et = s.f32()
+    d = dev()
+    pos = torch.from_numpy(np.concatenate([x, m[:, None]], 1).astype(np.float32)).to(d)
+    prm = nb.pack_ljc(torch.from_numpy(q.astype(np.float64)).to(d),
+                      torch.from_numpy(st.astype(np.float64)[s.types]).to(d),
+                      torch.from_numpy(et.astype(np.float64)[s.types]).to(d),
+                      torch.from_numpy(s.types).to(d), kq=332.0637 / D)
+    sysm = oracle.LJCSystem(m.astype(np.float64), q.astype(np.float64), s.types,
+                            st.astype(np.float64), et.astype(np.float64), 332.0637 / D,
+                            linear=True)
+    return pos.contiguous(), prm, sysm, x.astype(np.float64)
+
+
+@pytest.mark.parametrize("tile", range(5))
+@pytest.mark.parametrize("n", [257, 3000])
+def test_ljc_linear_dielectric(tile, n):
+    """Table 1 LJC(linear): dielectric D r with D = 4 (reading C3)."""
+    nb = lib()
+    s = workloads.ljc_sphere(n, seed=500 + n)
+    pos, prm, sysm, x = _ljclin_tensors(s)
+    acc = nb.forces(pos, prm, law=nb.LAW_LJC_LINEAR, pot=True, tile=tile, jsplit=2).cpu().numpy()
+    ref, phi = sysm.accel(x, potential=True)
+    assert_forces_close(acc[:, :3], ref, what=f"LJC(linear) tile={tile} n={n}")
+    e = np.abs(acc[:, 3] - phi) / np.maximum(np.abs(phi), 1e-3 * np.abs(phi).max())
+    assert np.sqrt(np.mean(e * e)) <= 1e-5 and e.max() <= 1e-4
+
+
+def test_ljc_linear_steps_and_subset():
+    nb = lib()
+    s = workloads.ljc_sphere(1500, seed=77)
+    pos, prm, sysm, x = _ljclin_tensors(s)
+    idx = np.arange(0, 1500, 11).astype(np.int32)
+    sub = nb.forces_subset(pos, torch.from_numpy(idx).to(dev()), prm, law=nb.LAW_LJC_LINEAR)
+    assert_forces_close(sub[:, :3].cpu().numpy(), sysm.accel(x)[idx], what="LJC(linear) subset")
+    vel = torch.zeros_like(pos)
+    acc = torch.empty_like(pos)
+    nb.step(pos, vel, acc, prm, law=nb.LAW_LJC_LINEAR, dt=1e-4, nsteps=4)
+    xs, _ = oracle.leapfrog(sysm, x, np.zeros_like(x), 1e-4, 4)
+    err = np.linalg.norm(pos[:, :3].cpu().numpy() - xs, axis=1) / np.sqrt(np.mean(np.sum(xs**2, 1)))
+    assert np.sqrt(np.mean(err ** 2)) <= 1e-6
