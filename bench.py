@@ -361,8 +361,8 @@ def _device_ms(torch, fn, reps=5):
 
 def secondary_kernel_extras(nb, torch, dev, pos, eps):
     """Throughput of the other force forms on the same GPU (device time per call):
-    LJ + Coulomb on the 8192-atom sphere, acceleration + jerk and an active subset
-    of 1024 targets on the N = 262144 Plummer sphere."""
+    LJ + Coulomb on the 8192-atom sphere; acceleration + jerk, an active subset of
+    1024 targets and the fixed-point mode on the N = 262144 Plummer sphere."""
     import workloads
     out = {}
     s = workloads.ljc_sphere(8192, seed=2)
@@ -382,6 +382,8 @@ def secondary_kernel_extras(nb, torch, dev, pos, eps):
                            .astype(np.int32)).to(dev)
     ms = _device_ms(torch, lambda: nb.forces_subset(pos, idx, eps=eps))
     out["subset_1024_of_262144_gpairs_per_s"] = 1024.0 * n / ms / 1e6
+    ms = _device_ms(torch, lambda: nb.forces(pos, eps=eps, fixed=True), reps=3)
+    out["fixed_point_262144_gpairs_per_s"] = float(n) ** 2 / ms / 1e6
     return out
 
 

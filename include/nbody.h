@@ -78,6 +78,12 @@ enum {
     NBODY_ACC_VALID = 1u << 3,       /* nbody_step: acc already holds a(x) for
                                         the entry positions                    */
     NBODY_ACCUMULATE = 1u << 4,      /* nbody_adjoint: add into the outputs    */
+    NBODY_FIXED_POINT = 1u << 5,     /* gravity, eps > 0, nbody_forces/step:
+                                        64-bit fixed-point accumulation of the
+                                        per-tile sums (Sec. 3.2, GRAPE-6);
+                                        results are bitwise independent of the
+                                        j-split. params->tile then indexes
+                                        tile table 4.                          */
 };
 
 typedef struct {
@@ -299,7 +305,8 @@ int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k
  * Tile configurations and tuning.
  * --------------------------------------------------------------------------- */
 /* Number of compiled tile configurations for tile table `law` (0 gravity,
- * 1 LJC, 2 LJC linear, 3 the mixed-law batched kernel), or a negative status. */
+ * 1 LJC, 2 LJC linear, 3 the mixed-law batched kernel, 4 gravity with
+ * fixed-point accumulation), or a negative status. */
 int nbody_tile_count(int32_t law);
 /* Describe configuration `tile` of `law`: threads per CTA (consumer warps),
  * i-particles per thread, j-lanes per warp, j-tile length. */

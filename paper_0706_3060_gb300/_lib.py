@@ -27,6 +27,8 @@ PRECISE_RSQRT = 1 << 1
 NO_COMPENSATION = 1 << 2
 ACC_VALID = 1 << 3
 ACCUMULATE = 1 << 4
+FIXED_POINT = 1 << 5
+TABLE_GRAV_FIXED = 4  # tile table of the fixed-point gravity kernels
 
 # Every symbol include/nbody.h declares.
 EXPORTS = (

@@ -14,8 +14,8 @@ import math
 import torch
 
 from . import _lib
-from ._lib import (ACC_VALID, ACCUMULATE, COMPUTE_POT, LAW_GRAV, LAW_LJC, NO_COMPENSATION,
-                   PRECISE_RSQRT, NBodyParams, NBodySystem, check, load)
+from ._lib import (ACC_VALID, ACCUMULATE, COMPUTE_POT, FIXED_POINT, LAW_GRAV, LAW_LJC,
+                   NO_COMPENSATION, PRECISE_RSQRT, NBodyParams, NBodySystem, check, load)
 
 COULOMB_K = 332.0637  # kcal A / (mol e^2): units A, kcal/mol, e, amu (AKMA time)
 
@@ -57,8 +57,8 @@ def _check4(t, name):
 
 
 def params(law=LAW_GRAV, G=1.0, eps=0.0, pot=False, precise=False, compensated=True,
-           tile=-1, jsplit=0, acc_valid=False, accumulate=False) -> NBodyParams:
-    flags = 0
+           tile=-1, jsplit=0, acc_valid=False, accumulate=False, fixed=False) -> NBodyParams:
+    flags = FIXED_POINT if fixed else 0
     flags |= COMPUTE_POT if pot else 0
     flags |= PRECISE_RSQRT if precise else 0
     flags |= 0 if compensated else NO_COMPENSATION
@@ -115,7 +115,7 @@ def pack_ljc(q, sigma, eps, types, kq=COULOMB_K / 80.0, out=None, stream=None):
 # ---------------------------------------------------------------------------
 def forces(pos_m, prm=None, *, law=None, G=1.0, eps=0.0, pot=False, precise=False,
            compensated=True, tile=-1, jsplit=0, out=None, out_lo=None, want_lo=False,
-           stream=None):
+           fixed=False, stream=None):
     """One all-pairs force evaluation. Returns acc (n, 4) = (ax, ay, az, phi), or
     (acc, acc_lo) with ``want_lo``."""
     _check4(pos_m, "pos_m")
@@ -124,7 +124,7 @@ def forces(pos_m, prm=None, *, law=None, G=1.0, eps=0.0, pot=False, precise=Fals
     n = pos_m.shape[0]
     acc = torch.empty_like(pos_m) if out is None else out
     lo = (torch.empty_like(pos_m) if out_lo is None else out_lo) if want_lo else None
-    p = params(law, G, eps, pot, precise, compensated, tile, jsplit)
+    p = params(law, G, eps, pot, precise, compensated, tile, jsplit, fixed=fixed)
     check(_lib().nbody_forces(_ptr(pos_m), _ptr(prm), _ptr(acc), _ptr(lo), n, ctypes.byref(p),
                               _stream(stream, pos_m.device)), "nbody_forces")
     return (acc, lo) if want_lo else acc
@@ -162,7 +162,7 @@ def forces_jerk(pos_m, vel, *, G=1.0, eps=0.0, compensated=True, stream=None):
 
 def step(pos_m, vel, acc, prm=None, *, dt, nsteps=1, law=None, G=1.0, eps=0.0,
          report_every=0, acc_valid=False, pot=False, precise=False, compensated=True,
-         tile=-1, jsplit=0, trace=None, diag=None, state_lo=None, stream=None):
+         tile=-1, jsplit=0, trace=None, diag=None, state_lo=None, fixed=False, stream=None):
     """``nsteps`` KDK leapfrog steps in place on (pos_m, vel); acc receives a(x_T).
 
     ``state_lo`` (2n, 4) float32, zero-initialised by the caller, turns on the
@@ -179,7 +179,7 @@ def step(pos_m, vel, acc, prm=None, *, dt, nsteps=1, law=None, G=1.0, eps=0.0,
     rows = nsteps // report_every + 1 if report_every > 0 else 0
     if rows and diag is None:
         diag = torch.zeros((rows, 8), dtype=torch.float64, device=pos_m.device)
-    p = params(law, G, eps, pot, precise, compensated, tile, jsplit, acc_valid)
+    p = params(law, G, eps, pot, precise, compensated, tile, jsplit, acc_valid, fixed=fixed)
     check(_lib().nbody_step(_ptr(pos_m), _ptr(vel), _ptr(acc), _ptr(prm), n, float(dt),
                             int(nsteps), int(report_every), _ptr(diag) if rows else None,
                             _ptr(trace), _ptr(state_lo), ctypes.byref(p),

@@ -43,12 +43,17 @@ namespace {
 
 constexpr int kMaxN = 0x7fffffff;
 
+// Tile table of a call: the law's own, or the fixed-point gravity table.
+int table_of(const nbody_params &p) {
+  return (p.flags & NBODY_FIXED_POINT) ? kTableGravFixed : p.law;
+}
+
 int check_params(const nbody_params *p, const void *prm) {
   if (!p) return set_error_msg(NBODY_EINVAL, "params is NULL");
   if (p->law != NBODY_LAW_GRAV && p->law != NBODY_LAW_LJC && p->law != NBODY_LAW_LJC_LINEAR)
     return set_error_msg(NBODY_EINVAL, "unknown law %d", p->law);
   const uint32_t known = NBODY_COMPUTE_POT | NBODY_PRECISE_RSQRT | NBODY_NO_COMPENSATION |
-                         NBODY_ACC_VALID | NBODY_ACCUMULATE;
+                         NBODY_ACC_VALID | NBODY_ACCUMULATE | NBODY_FIXED_POINT;
   if (p->flags & ~known) return set_error_msg(NBODY_EINVAL, "unknown flag bits 0x%x", p->flags);
   if (p->law != NBODY_LAW_GRAV && !prm)
     return set_error_msg(NBODY_EINVAL, "LJC law needs the prm array");
@@ -56,8 +61,14 @@ int check_params(const nbody_params *p, const void *prm) {
     return set_error_msg(NBODY_EINVAL, "eps2 must be >= 0");
   if (p->law == NBODY_LAW_GRAV && !std::isfinite(p->G))
     return set_error_msg(NBODY_EINVAL, "G must be finite");
+  if (p->flags & NBODY_FIXED_POINT) {
+    if (p->law != NBODY_LAW_GRAV)
+      return set_error_msg(NBODY_EUNSUPPORTED, "fixed-point accumulation is for gravity only");
+    if (!(p->eps2 > 0.0f))
+      return set_error_msg(NBODY_EINVAL, "fixed-point accumulation needs eps > 0 (its bound)");
+  }
   int count = 0;
-  tiles_for(p->law, &count);
+  tiles_for(table_of(*p), &count);
   if (p->tile < -1 || p->tile >= count) return set_error_msg(NBODY_EINVAL, "bad tile %d", p->tile);
   if (p->jsplit < 0) return set_error_msg(NBODY_EINVAL, "bad jsplit %d", p->jsplit);
   return NBODY_OK;
@@ -71,6 +82,8 @@ int check_ptr(const void *p, const char *name, bool required = true) {
 
 // Scratch layout for one single-system evaluation.
 struct Scratch {
+  float *fscale;  // fixed-point scale (device word) and its inverse
+  double *finv;
   float4 *jbuf;
   float4 *part_hi;
   float4 *part_lo;
@@ -85,8 +98,11 @@ int get_scratch(cudaStream_t s, int law, int n, int slices, int diag_rows, Scrat
   const size_t drows = round_up(size_t(std::max(diag_rows, 1)) * kDiagFields * sizeof(double), 256);
   const size_t jb = jbuf_bytes(law, n);
   void *base = nullptr;
-  NB_TRY(workspace(s, jb + 2 * part + dpart + drows, &base));
+  NB_TRY(workspace(s, 256 + jb + 2 * part + dpart + drows, &base));
   char *b = static_cast<char *>(base);
+  out->finv = reinterpret_cast<double *>(b);
+  out->fscale = reinterpret_cast<float *>(b + 8);
+  b += 256;
   out->jbuf = reinterpret_cast<float4 *>(b);
   b += jb;
   out->part_hi = reinterpret_cast<float4 *>(b);
@@ -100,8 +116,10 @@ int get_scratch(cudaStream_t s, int law, int n, int slices, int diag_rows, Scrat
 int eval_and_finalize(const float4 *pos, const float4 *prm, const nbody_params &p, int n,
                       const Plan1 &plan, const Scratch &sc, int *err, bool pot,
                       FinalizeArgs f, cudaStream_t s, int *nblk) {
+  const bool fx = (p.flags & NBODY_FIXED_POINT) != 0;
   NB_TRY(launch_forces(pos, prm, p.law, p.flags, p.eps2, n, plan, sc.part_hi, sc.part_lo,
-                       sc.jbuf, err, pot, s));
+                       sc.jbuf, err, pot, s, nullptr, fx ? sc.fscale : nullptr));
+  f.fx_inv = fx ? sc.finv : nullptr;
   f.part_hi = sc.part_hi;
   f.part_lo = sc.part_lo;
   f.stride = n;
@@ -115,12 +133,21 @@ int eval_and_finalize(const float4 *pos, const float4 *prm, const nbody_params &
   return launch_finalize(f, s, nblk);
 }
 
+int prepare_fixed(const float4 *pos, int n, const nbody_params &p, const Scratch &sc,
+                  cudaStream_t s) {
+  if (!(p.flags & NBODY_FIXED_POINT)) return NBODY_OK;
+  fixed_scale_kernel<<<1, 256, 0, s>>>(pos, n, p.eps2, sc.fscale, sc.finv);
+  NB_CUDA(cudaGetLastError());
+  return NBODY_OK;
+}
+
 int forces_device(const float4 *pos, const float4 *prm, float4 *acc, float4 *acc_lo, int n,
                   const nbody_params &p, int sms, cudaStream_t s) {
   Plan1 plan{};
-  NB_TRY(plan_single(p.law, n, p.tile, p.jsplit, sms, &plan));
+  NB_TRY(plan_single(table_of(p), n, p.tile, p.jsplit, sms, &plan));
   Scratch sc{};
   NB_TRY(get_scratch(s, p.law, n, plan.slices, 0, &sc));
+  NB_TRY(prepare_fixed(pos, n, p, sc, s));
   int *err = nullptr;
   NB_TRY(error_word(&err));
   FinalizeArgs f{};
@@ -136,10 +163,11 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
                 int nsteps, int report_every, double *diag_dev, float4 *trace, float4 *state_lo,
                 const nbody_params &p, int sms, cudaStream_t s) {
   Plan1 plan{};
-  NB_TRY(plan_single(p.law, n, p.tile, p.jsplit, sms, &plan));
+  NB_TRY(plan_single(table_of(p), n, p.tile, p.jsplit, sms, &plan));
   const int rows = report_every > 0 ? nsteps / report_every + 1 : 0;
   Scratch sc{};
   NB_TRY(get_scratch(s, p.law, n, plan.slices, rows, &sc));
+  NB_TRY(prepare_fixed(pos, n, p, sc, s));
   int *err = nullptr;
   NB_TRY(error_word(&err));
   auto report = [&](int step) { return report_every > 0 && step % report_every == 0; };

@@ -256,6 +256,7 @@ const TileDesc *tiles_for(int law, int *count) {
   if (law == NBODY_LAW_GRAV) return grav_tiles(count);
   if (law == NBODY_LAW_LJC) return ljc_tiles(count);
   if (law == NBODY_LAW_LJC_LINEAR) return ljclin_tiles(count);
+  if (law == kTableGravFixed) return grav_fixed_tiles(count);
   return mixed_tiles(count);
 }
 
@@ -282,6 +283,7 @@ static int log2_floor(int64_t n) {
 // inside the warp for small N (where there are too few targets to fill the GPU).
 static int default_tile(int law, int64_t n) {
   if (law == kTableBatched) return 0;
+  if (law == kTableGravFixed) return n >= 4096 ? 0 : (n >= 1024 ? 2 : 3);
   if (law == NBODY_LAW_LJC_LINEAR) return n >= 16384 ? 3 : (n >= 1024 ? 1 : 2);
   if (law == NBODY_LAW_GRAV) {
     if (n >= 65536) return 0;
@@ -388,7 +390,10 @@ size_t jbuf_bytes(int law, int64_t n) {
 
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
-                  int *err, bool pot, cudaStream_t s, const Targets *tg) {
+                  int *err, bool pot, cudaStream_t s, const Targets *tg,
+                  const float *fscale) {
+  if (p.tile->fixed != (fscale != nullptr))
+    return set_error_msg(NBODY_EINVAL, "fixed-point tile and scale must come together");
   if (p.tile->packed) {
     if (!jbuf) return set_error_msg(NBODY_EINVAL, "packed tile without pair buffer");
     const int np = (n + 1) / 2;
@@ -418,6 +423,7 @@ int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags,
   a.n_items = 0;
   a.counter = nullptr;
   a.comp = (flags & NBODY_NO_COMPENSATION) ? 0 : 1;
+  a.fscale = fscale;
   (void)law;
   const TimerMark tm = timer_begin(0, s);
   cudaError_t e = p.tile->launch(a, p.grid, pot, (flags & NBODY_PRECISE_RSQRT) != 0, s);

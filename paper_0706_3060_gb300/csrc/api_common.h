@@ -53,9 +53,11 @@ int error_word(int **out);
 // Synchronize `s`, then read and clear the error word.
 int sync_and_check(cudaStream_t s);
 
-// Tile tables: 0 gravity, 1 LJC, 2 LJC linear, 3 the batched mixed-law kernel.
+// Tile tables: 0 gravity, 1 LJC, 2 LJC linear, 3 the batched mixed-law kernel,
+// 4 gravity with fixed-point accumulation.
 constexpr int kTableBatched = 3;
-constexpr int kTables = 4;
+constexpr int kTableGravFixed = 4;
+constexpr int kTables = 5;
 const TileDesc *tiles_for(int law, int *count);
 // Decide (tile, slices, slice_len) for a single-system evaluation.
 struct Plan1 {
@@ -82,9 +84,11 @@ struct Targets {
 size_t jbuf_bytes(int law, int64_t n);
 
 // jbuf: scratch of jbuf_bytes(law, n) for the pair-interleaved sources of packed tiles.
+// fscale: device word with the fixed-point scale, required exactly for fixed tiles.
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
-                  int *err, bool pot, cudaStream_t s, const Targets *tg = nullptr);
+                  int *err, bool pot, cudaStream_t s, const Targets *tg = nullptr,
+                  const float *fscale = nullptr);
 
 size_t round_up(size_t x, size_t a);
 

@@ -63,30 +63,51 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
       }
     }
     if (live) {
-      float4 hi = f.part_hi[i];
-      float4 lo = f.part_lo[i];
-      for (int k = 1; k < slices; ++k) {
-        const float4 h = f.part_hi[(long long)k * f.stride + i];
-        const float4 l = f.part_lo[(long long)k * f.stride + i];
-        comp_add(hi.x, lo.x, h.x);
-        comp_add(hi.y, lo.y, h.y);
-        comp_add(hi.z, lo.z, h.z);
-        comp_add(hi.w, lo.w, h.w);
-        lo.x = __fadd_rn(lo.x, l.x);
-        lo.y = __fadd_rn(lo.y, l.y);
-        lo.z = __fadd_rn(lo.z, l.z);
-        lo.w = __fadd_rn(lo.w, l.w);
-      }
-      // Round hi + lo to FP32 and keep the residual (Fast2Sum, |hi| >= |lo|).
       float4 t, r;
-      t.x = __fadd_rn(hi.x, lo.x);
-      r.x = __fsub_rn(lo.x, __fsub_rn(t.x, hi.x));
-      t.y = __fadd_rn(hi.y, lo.y);
-      r.y = __fsub_rn(lo.y, __fsub_rn(t.y, hi.y));
-      t.z = __fadd_rn(hi.z, lo.z);
-      r.z = __fsub_rn(lo.z, __fsub_rn(t.z, hi.z));
-      t.w = __fadd_rn(hi.w, lo.w);
-      r.w = __fsub_rn(lo.w, __fsub_rn(t.w, hi.w));
+      if (f.fx_inv) {
+        // 64-bit fixed-point partials: exact integer sum, one rounding at the end
+        long long sx = 0, sy = 0, sz = 0, sw = 0;
+        for (int k = 0; k < slices; ++k) {
+          const long long *ph = reinterpret_cast<const long long *>(f.part_hi) +
+                                2 * ((long long)k * f.stride + i);
+          const long long *pl = reinterpret_cast<const long long *>(f.part_lo) +
+                                2 * ((long long)k * f.stride + i);
+          sx += ph[0];
+          sy += ph[1];
+          sz += pl[0];
+          sw += pl[1];
+        }
+        const double inv = *f.fx_inv;
+        const double dx = double(sx) * inv, dy = double(sy) * inv, dz = double(sz) * inv,
+                     dw = double(sw) * inv;
+        t = make_float4(float(dx), float(dy), float(dz), float(dw));
+        r = make_float4(float(dx - double(t.x)), float(dy - double(t.y)),
+                        float(dz - double(t.z)), float(dw - double(t.w)));
+      } else {
+        float4 hi = f.part_hi[i];
+        float4 lo = f.part_lo[i];
+        for (int k = 1; k < slices; ++k) {
+          const float4 h = f.part_hi[(long long)k * f.stride + i];
+          const float4 l = f.part_lo[(long long)k * f.stride + i];
+          comp_add(hi.x, lo.x, h.x);
+          comp_add(hi.y, lo.y, h.y);
+          comp_add(hi.z, lo.z, h.z);
+          comp_add(hi.w, lo.w, h.w);
+          lo.x = __fadd_rn(lo.x, l.x);
+          lo.y = __fadd_rn(lo.y, l.y);
+          lo.z = __fadd_rn(lo.z, l.z);
+          lo.w = __fadd_rn(lo.w, l.w);
+        }
+        // Round hi + lo to FP32 and keep the residual (Fast2Sum, |hi| >= |lo|).
+        t.x = __fadd_rn(hi.x, lo.x);
+        r.x = __fsub_rn(lo.x, __fsub_rn(t.x, hi.x));
+        t.y = __fadd_rn(hi.y, lo.y);
+        r.y = __fsub_rn(lo.y, __fsub_rn(t.y, hi.y));
+        t.z = __fadd_rn(hi.z, lo.z);
+        r.z = __fsub_rn(lo.z, __fsub_rn(t.z, hi.z));
+        t.w = __fadd_rn(hi.w, lo.w);
+        r.w = __fsub_rn(lo.w, __fsub_rn(t.w, hi.w));
+      }
       float4 x = f.pos[i];
       float4 a, alo;
       if (law == 0) {  // gravity: a = G sum m_j y^3 d, phi = -G sum m_j y
@@ -155,6 +176,29 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
     }
   }
   if (f.mode & kFinDiag) block_sum8(dv, f.diag_part + (size_t)blockIdx.x * kDiagFields);
+}
+
+// Scale of the fixed-point mode: a power of two 2^S such that the largest sum a
+// target can reach, |sum_j m_j d / s^3| <= M 2 / (3 sqrt(3) eps^2) and
+// |sum_j m_j / s| <= M / eps (M = sum |m_j|), stays below 2^62. One block; the
+// mass sum runs in FP64 in a fixed order.
+__global__ void __launch_bounds__(256) fixed_scale_kernel(const float4 *pos, int n, float eps2,
+                                                          float *scale, double *inv) {
+  __shared__ double part[256];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) m += fabs(double(pos[i].w));
+  part[threadIdx.x] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double M = 0.0;
+    for (int k = 0; k < 256; ++k) M += part[k];
+    const double e2 = double(eps2);
+    const double bound = fmax(M * 0.3849001794597505 / e2, M / sqrt(e2)) + 1e-300;
+    int S = int(floor(62.0 - log2(bound)));
+    S = S > 126 ? 126 : (S < -126 ? -126 : S);
+    *scale = ldexpf(1.0f, S);
+    *inv = ldexp(1.0, -S);
+  }
 }
 
 // Deterministic final sum of the per-block FP64 diagnostics: one block,

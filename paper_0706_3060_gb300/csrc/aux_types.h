@@ -36,6 +36,7 @@ struct FinalizeArgs {
   float4 *acc;
   float4 *acc_lo;        // may be null
   float4 *trace_next;    // positions after the drift, or null
+  const double *fx_inv;  // fixed-point partials (int64): value = sum * (*fx_inv); else null
   float4 *x_lo;          // compensated state: low parts of x and v, or null
   float4 *v_lo;
   int mode;

@@ -70,6 +70,7 @@ struct ForceArgs {
   int n_items;
   int *counter;        // null: single-system mode
   int comp;            // 1: compensated (hi, lo) sums per j-tile
+  const float *fscale; // fixed-point kernels: device word holding the scale 2^S
 };
 
 enum : int { kChunkFirst = 1, kChunkLast = 2, kChunkEnd = 4 };
@@ -223,8 +224,13 @@ struct ForceTile {
 };
 
 // ---- the kernel -------------------------------------------------------------------
+// FX: each j-tile's FP32 partial is rounded onto a 64-bit fixed-point grid
+// (scale 2^S from *a.fscale) and added as an integer, as GRAPE-6 accumulates
+// (Sec. 3.2). Integer addition is associative, so the result does not depend on
+// how the j-range is split across CTAs or lanes: bitwise the same for every
+// j-split and slice boundary.
 template <int LAW, int NT, int I, int SW, int JT, bool POT, bool PRECISE, bool PK = false,
-          int PU = 2, int MINB = 1>
+          int PU = 2, int MINB = 1, bool FX = false>
 __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a) {
   using T = ForceTile<LAW, NT, I, SW, JT>;
   static_assert(!PK || ((LAW == kLawGrav || is_ljc(LAW)) && SW == 1),
@@ -349,6 +355,8 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
   int slot_g[I];  // output slot of each target (-1: padding)
   float4 p[I], hi[I], lo[I];
   float2 pax[PK ? I : 1], pay[PK ? I : 1], paz[PK ? I : 1], ppt[PK ? I : 1];
+  long long fxa[FX ? I : 1][4];
+  const float fsc = FX ? __ldg(a.fscale) : 0.0f;
   WorkItem cur{};
   int cur_law = is_ljc(LAW) ? kLawLJC : kLawGrav;
 
@@ -384,6 +392,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
         lo[r] = make_float4(0.f, 0.f, 0.f, 0.f);
         p[r] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (PK) pax[r] = pay[r] = paz[r] = ppt[r] = make_float2(0.f, 0.f);
+        if (FX) fxa[r][0] = fxa[r][1] = fxa[r][2] = fxa[r][3] = 0;
       }
     }
     const float4 *sp = sm_pos + st * STAGE_F4;
@@ -542,7 +551,12 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
         if (POT) p[r].w += ppt[r].x + ppt[r].y;
         pax[r] = pay[r] = paz[r] = ppt[r] = make_float2(0.f, 0.f);
       }
-      if (a.comp) {
+      if (FX) {
+        fxa[r][0] += __float2ll_rn(p[r].x * fsc);
+        fxa[r][1] += __float2ll_rn(p[r].y * fsc);
+        fxa[r][2] += __float2ll_rn(p[r].z * fsc);
+        if (POT) fxa[r][3] += __float2ll_rn(p[r].w * fsc);
+      } else if (a.comp) {
         comp_add(hi[r].x, lo[r].x, p[r].x);
         comp_add(hi[r].y, lo[r].y, p[r].y);
         comp_add(hi[r].z, lo[r].z, p[r].z);
@@ -563,6 +577,11 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
       for (int off = SW / 2; off >= 1; off >>= 1) {
 #pragma unroll
         for (int r = 0; r < I; ++r) {
+          if (FX) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) fxa[r][c] += __shfl_xor_sync(0xffffffffu, fxa[r][c], off);
+            continue;
+          }
           float4 oh, ol;
           oh.x = __shfl_xor_sync(0xffffffffu, hi[r].x, off);
           oh.y = __shfl_xor_sync(0xffffffffu, hi[r].y, off);
@@ -588,8 +607,17 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
 #pragma unroll
         for (int r = 0; r < I; ++r) {
           if (slot_g[r] >= 0) {
-            a.part_hi[base + slot_g[r]] = hi[r];
-            a.part_lo[base + slot_g[r]] = lo[r];
+            if (FX) {  // four int64 per target: (x, y) in part_hi, (z, w) in part_lo
+              long long *ph = reinterpret_cast<long long *>(a.part_hi) + 2 * (base + slot_g[r]);
+              long long *pl = reinterpret_cast<long long *>(a.part_lo) + 2 * (base + slot_g[r]);
+              ph[0] = fxa[r][0];
+              ph[1] = fxa[r][1];
+              pl[0] = fxa[r][2];
+              pl[1] = fxa[r][3];
+            } else {
+              a.part_hi[base + slot_g[r]] = hi[r];
+              a.part_lo[base + slot_g[r]] = lo[r];
+            }
           }
         }
       }

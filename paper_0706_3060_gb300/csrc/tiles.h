@@ -21,6 +21,7 @@ struct TileDesc {
   int threads;
   size_t smem;
   bool packed;  // gravity sources in the pair-interleaved layout (f32x2 math)
+  bool fixed;   // 64-bit fixed-point partial sums (NBODY_FIXED_POINT)
   ForceLauncher launch;
   ForceOccupancy occupancy;
 };
@@ -29,14 +30,16 @@ struct TileDesc {
 const TileDesc *grav_tiles(int *count);
 const TileDesc *ljc_tiles(int *count);
 const TileDesc *ljclin_tiles(int *count);
+const TileDesc *grav_fixed_tiles(int *count);
 const TileDesc *mixed_tiles(int *count);
 
-template <int LAW, int NT, int I, int SW, int JT, bool PK = false, int PU = 2, int MINB = 1>
+template <int LAW, int NT, int I, int SW, int JT, bool PK = false, int PU = 2, int MINB = 1,
+          bool FX = false>
 struct TileImpl {
   using T = ForceTile<LAW, NT, I, SW, JT>;
   template <bool POT, bool PRE>
   static cudaError_t go(const ForceArgs &a, int grid, cudaStream_t s) {
-    auto k = force_kernel<LAW, NT, I, SW, JT, POT, PRE, PK, PU, MINB>;
+    auto k = force_kernel<LAW, NT, I, SW, JT, POT, PRE, PK, PU, MINB, FX>;
     if (T::kSmemBytes > 32 * 1024) {
       cudaError_t e =
           cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
@@ -52,7 +55,7 @@ struct TileImpl {
   }
   static int occupancy() {
     int nb = 0;
-    auto k = force_kernel<LAW, NT, I, SW, JT, false, false, PK, PU, MINB>;
+    auto k = force_kernel<LAW, NT, I, SW, JT, false, false, PK, PU, MINB, FX>;
     if (T::kSmemBytes > 32 * 1024)
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, T::kThreads, T::kSmemBytes) !=
@@ -61,7 +64,7 @@ struct TileImpl {
     return nb > 0 ? nb : 1;
   }
   static TileDesc desc() {
-    return TileDesc{LAW, NT, I, SW, JT, T::kTileI, T::kThreads, T::kSmemBytes, PK, &launch,
+    return TileDesc{LAW, NT, I, SW, JT, T::kTileI, T::kThreads, T::kSmemBytes, PK, FX, &launch,
                     &occupancy};
   }
 };

@@ -285,3 +285,45 @@ def test_ljc_linear_steps_and_subset():
     xs, _ = oracle.leapfrog(sysm, x, np.zeros_like(x), 1e-4, 4)
     err = np.linalg.norm(pos[:, :3].cpu().numpy() - xs, axis=1) / np.sqrt(np.mean(np.sum(xs**2, 1)))
     assert np.sqrt(np.mean(err ** 2)) <= 1e-6
+
+
+def test_fixed_point_accuracy_and_split_independence():
+    """64-bit fixed-point accumulation (Sec. 3.2, GRAPE-6): oracle accuracy, and the
+    same bits for every j-split because integer sums are associative."""
+    nb = lib()
+    g = workloads.plummer(20001, seed=91, eps=0.01)
+    pos, _ = grav_tensors(g)
+    eps = float(np.float32(g.eps))
+    ref, phi = _grav_ref(g, potential=True)
+    outs = []
+    for js in (1, 2, 3, 5, 8):
+        a = nb.forces(pos, eps=eps, fixed=True, tile=0, jsplit=js, pot=True)
+        outs.append(a)
+        assert_forces_close(a[:, :3].cpu().numpy(), ref, what=f"fixed jsplit={js}")
+    for a in outs[1:]:
+        assert torch.equal(a, outs[0])
+    e = np.abs(outs[0][:, 3].cpu().numpy() - phi) / np.abs(phi)
+    assert e.max() <= 1e-4
+    for tile in range(nb.tile_count(nb.TABLE_GRAV_FIXED)):
+        a = nb.forces(pos, eps=eps, fixed=True, tile=tile)
+        assert_forces_close(a[:, :3].cpu().numpy(), ref, what=f"fixed tile={tile}")
+
+
+def test_fixed_point_steps_split_independent_and_rejections():
+    nb = lib()
+    g = workloads.plummer(4097, seed=92, eps=0.01)
+    eps = float(np.float32(g.eps))
+    runs = []
+    for js in (1, 4):
+        pos, vel = grav_tensors(g)
+        acc = torch.empty_like(pos)
+        nb.step(pos, vel, acc, dt=1e-3, nsteps=5, eps=eps, fixed=True, tile=0, jsplit=js)
+        runs.append((pos, vel))
+    assert torch.equal(runs[0][0], runs[1][0]) and torch.equal(runs[0][1], runs[1][1])
+    pos, _ = grav_tensors(g)
+    with pytest.raises(nb.NBodyError):
+        nb.forces(pos, eps=0.0, fixed=True)     # no bound without softening
+    s = workloads.ljc_sphere(64, seed=1)
+    lpos, _, prm = ljc_tensors(s)
+    with pytest.raises(nb.NBodyError):
+        nb.forces(lpos, prm, fixed=True)

@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_version_and_tiles(lib):
     import paper_0706_3060_gb300 as nb
     assert nb.version() >= 10000
-    for law in (0, 1, 2, 3):
+    for law in (0, 1, 2, 3, 4):
         c = nb.tile_count(law)
         assert c >= 4
         for t in range(c):
