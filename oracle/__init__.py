@@ -21,6 +21,7 @@ What it computes (each item is the plain definition, no blocking or fusion):
   block by block from the Jacobian, with mass and per-type sigma/epsilon
   derivatives.
 * :func:`adjoint_leapfrog` -- reverse-mode KDK with every state stored.
+* :func:`hermite`        -- fourth-order Hermite steps on acceleration + jerk.
 * :func:`diagnostics`    -- kinetic and potential energy, momentum and
   angular momentum in FP64.
 
@@ -288,6 +289,33 @@ def leapfrog(system, x0, v0, dt, nsteps, store=False):
         x = x + dt * v
         a = system.accel(x)
         v = v + 0.5 * dt * a
+        if store:
+            xs.append(x.copy())
+            vs.append(v.copy())
+    if store:
+        return xs, vs
+    return x, v
+
+
+def hermite(x0, v0, m, dt, nsteps, G=1.0, eps=0.0, store=False):
+    """Fourth-order Hermite predictor-evaluate-correct steps (the integrator
+    that consumes Table 1's acceleration and jerk; Makino & Aarseth 1992):
+      predict  x_p = x + v dt + a dt^2/2 + j dt^3/6,   v_p = v + a dt + j dt^2/2
+      evaluate a_1, j_1 at (x_p, v_p)
+      correct  v_1 = v + (a + a_1) dt/2 + (j - j_1) dt^2/12
+               x_1 = x + (v + v_1) dt/2 + (a - a_1) dt^2/12
+    Returns (x, v) or, with ``store``, lists of all states."""
+    x = _f64(x0, (-1, 3)).copy()
+    v = _f64(v0, (-1, 3)).copy()
+    a, j = grav_jerk(x, v, m, G, eps)
+    xs, vs = [x.copy()], [v.copy()]
+    for _ in range(int(nsteps)):
+        xp = x + v * dt + a * (dt * dt / 2.0) + j * (dt ** 3 / 6.0)
+        vp = v + a * dt + j * (dt * dt / 2.0)
+        a1, j1 = grav_jerk(xp, vp, m, G, eps)
+        v1 = v + (a + a1) * (dt / 2.0) + (j - j1) * (dt * dt / 12.0)
+        x1 = x + (v + v1) * (dt / 2.0) + (a - a1) * (dt * dt / 12.0)
+        x, v, a, j = x1, v1, a1, j1
         if store:
             xs.append(x.copy())
             vs.append(v.copy())

@@ -67,3 +67,36 @@ def test_time_reversibility_and_momentum():
     P0 = np.sum(g.m[:, None] * g.v, axis=0)
     P1 = np.sum(g.m[:, None] * v1, axis=0)
     np.testing.assert_allclose(P1, P0, atol=1e-15)
+
+
+def _kepler_hermite(dt, T, e=0.5):
+    m1, m2 = 0.7, 0.3
+    rp = 1.0 - e
+    vp = math.sqrt((m1 + m2) * (1 + e) / (1.0 - e))
+    rel_x = np.array([rp, 0.0, 0.0])
+    rel_v = np.array([0.0, vp, 0.0])
+    x = np.array([-m2 / (m1 + m2) * rel_x, m1 / (m1 + m2) * rel_x])
+    v = np.array([-m2 / (m1 + m2) * rel_v, m1 / (m1 + m2) * rel_v])
+    xT, _ = oracle.hermite(x, v, np.array([m1, m2]), dt, int(round(T / dt)), eps=0.0)
+    return np.linalg.norm((xT[1] - xT[0]) - _kepler_orbit(T, 1.0, e, m1 + m2))
+
+
+def test_hermite_fourth_order_on_kepler():
+    """The Hermite scheme on acceleration + jerk converges at fourth order: halving dt
+    divides the error by about 16 (the closed-form Kepler orbit is the reference)."""
+    period = 2 * math.pi
+    errs = [_kepler_hermite(period / k, period) for k in (200, 400, 800)]
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 13.0 < r1 < 19.0 and 13.0 < r2 < 19.0, errs
+    assert errs[2] < 1e-6
+
+
+def test_hermite_conserves_momentum_and_energy():
+    g = workloads.plummer(48, seed=21)
+    sysm = oracle.GravSystem(g.m, eps=0.05)
+    xs, vs = oracle.hermite(g.x, g.v, g.m, 1e-3, 100, eps=0.05, store=True)
+    E0 = oracle.diagnostics(sysm, xs[0], vs[0])["E"]
+    E1 = oracle.diagnostics(sysm, xs[-1], vs[-1])["E"]
+    assert abs(E1 - E0) <= 1e-9 * abs(E0)
+    P = np.sum(g.m[:, None] * vs[-1], axis=0)
+    np.testing.assert_allclose(P, np.sum(g.m[:, None] * g.v, axis=0), atol=1e-15)
