@@ -168,6 +168,19 @@ int nbody_forces(const void *pos_m, const void *prm, void *acc, void *acc_lo, in
 int nbody_forces_jerk(const void *pos_m, const void *vel, void *acc, void *jerk, int64_t n,
                       const nbody_params *params, nbody_stream_t stream);
 
+/* nbody_hermite_step -- nsteps fourth-order Hermite predictor-evaluate-correct
+ * steps on the acceleration and jerk of nbody_forces_jerk (the integrator Table 1's
+ * GAJ kernel serves; Makino & Aarseth 1992):
+ *   predict  x_p = x + v dt + a dt^2/2 + j dt^3/6,  v_p = v + a dt + j dt^2/2
+ *   evaluate (a1, j1) at (x_p, v_p)
+ *   correct  v = v + (a + a1) dt/2 + (j - j1) dt^2/12,
+ *            x = x + (v_old + v) dt/2 + (a - a1) dt^2/12
+ *   pos_m, vel, acc, jerk : n float4, in/out; acc/jerk hold (a, j) of the exit
+ *   state and are read on entry only with NBODY_ACC_VALID. Gravity only.
+ *   Device pointers only. */
+int nbody_hermite_step(void *pos_m, void *vel, void *acc, void *jerk, int64_t n, float dt,
+                       int32_t nsteps, const nbody_params *params, nbody_stream_t stream);
+
 /* nbody_forces_subset -- forces on n_active target particles idx[0..n_active)
  * against all n sources (block time steps, Sec. 3.4: forces on only a subset of
  * the particles at a time). Same laws, flags and accuracy as nbody_forces.

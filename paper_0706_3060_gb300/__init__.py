@@ -10,7 +10,7 @@ from ._lib import (ACC_VALID, ACCUMULATE, COMPUTE_POT, FIXED_POINT, LAW_GRAV, LA
                    LAW_LJC_LINEAR, NO_COMPENSATION, PRECISE_RSQRT, TABLE_BATCHED,
                    TABLE_GRAV_FIXED, NBodyError)
 from .api import (COULOMB_K, BatchPlan, adjoint, adjoint_leapfrog, forces, forces_batched,
-                  forces_jerk, forces_subset,
+                  forces_jerk, forces_subset, hermite_step,
                   get_config, pack_grav, pack_ljc, params, release, set_tuned, step, sync_check,
                   tile_count, tile_info, timing_enable, timing_read, version)
 
@@ -18,7 +18,7 @@ __all__ = [
     "ACC_VALID", "ACCUMULATE", "COMPUTE_POT", "LAW_GRAV", "LAW_LJC", "LAW_LJC_LINEAR",
     "TABLE_BATCHED", "TABLE_GRAV_FIXED", "FIXED_POINT", "NO_COMPENSATION",
     "PRECISE_RSQRT", "NBodyError", "COULOMB_K", "BatchPlan", "adjoint", "adjoint_leapfrog",
-    "forces", "forces_batched", "forces_jerk", "forces_subset", "get_config", "pack_grav", "pack_ljc", "params", "release",
+    "forces", "forces_batched", "forces_jerk", "forces_subset", "hermite_step", "get_config", "pack_grav", "pack_ljc", "params", "release",
     "set_tuned", "step", "sync_check", "tile_count", "tile_info", "timing_enable",
     "timing_read", "version",
 ]

@@ -160,6 +160,17 @@ def forces_jerk(pos_m, vel, *, G=1.0, eps=0.0, compensated=True, stream=None):
     return acc, jerk
 
 
+def hermite_step(pos_m, vel, acc, jerk, *, dt, nsteps=1, G=1.0, eps=0.0, acc_valid=False,
+                 compensated=True, stream=None):
+    """``nsteps`` fourth-order Hermite steps in place; acc/jerk receive (a, j) at exit."""
+    for t, nm in ((pos_m, "pos_m"), (vel, "vel"), (acc, "acc"), (jerk, "jerk")):
+        _check4(t, nm)
+    p = params(LAW_GRAV, G, eps, compensated=compensated, acc_valid=acc_valid)
+    check(_lib().nbody_hermite_step(_ptr(pos_m), _ptr(vel), _ptr(acc), _ptr(jerk),
+                                    pos_m.shape[0], float(dt), int(nsteps), ctypes.byref(p),
+                                    _stream(stream, pos_m.device)), "nbody_hermite_step")
+
+
 def step(pos_m, vel, acc, prm=None, *, dt, nsteps=1, law=None, G=1.0, eps=0.0,
          report_every=0, acc_valid=False, pot=False, precise=False, compensated=True,
          tile=-1, jsplit=0, trace=None, diag=None, state_lo=None, fixed=False, stream=None):

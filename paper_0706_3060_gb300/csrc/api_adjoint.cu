@@ -66,13 +66,14 @@ const VjpDesc &vjp_tile(int law, int64_t n) {
 
 struct VjpScratch {
   float4 *part_hi, *part_lo, *u, *jp;
+  char *extra;  // caller-requested extra bytes
   double *type_part;
   int slices, slice_len, grid, nblk;
   long long bstride;
   const VjpDesc *d;
 };
 
-int vjp_prepare(int law, int n, int sms, cudaStream_t s, VjpScratch *sc) {
+int vjp_prepare(int law, int n, int sms, cudaStream_t s, VjpScratch *sc, size_t extra = 0) {
   const VjpDesc &d = vjp_tile(law, n);
   const int n_it = (n + d.tile_i - 1) / d.tile_i;
   const int cap = sms * d.occupancy();
@@ -98,8 +99,9 @@ int vjp_prepare(int law, int n, int sms, cudaStream_t s, VjpScratch *sc) {
   const size_t tbytes = round_up(size_t(nblk) * 8 * sizeof(double), 256);
   const size_t jbytes = d.packed ? round_up(size_t((n + 1) / 2) * 4 * sizeof(float4), 256) : 0;
   void *base = nullptr;
-  NB_TRY(workspace(s, 2 * part + ubytes + tbytes + jbytes, &base));
+  NB_TRY(workspace(s, 2 * part + ubytes + tbytes + jbytes + extra, &base));
   char *b = static_cast<char *>(base);
+  sc->extra = b + 2 * part + ubytes + tbytes + jbytes;
   sc->jp = d.packed ? reinterpret_cast<float4 *>(b + 2 * part + ubytes + tbytes) : nullptr;
   sc->part_hi = reinterpret_cast<float4 *>(b);
   sc->part_lo = reinterpret_cast<float4 *>(b + part);
@@ -206,6 +208,85 @@ int check_dev_ptrs(std::initializer_list<const void *> ptrs) {
   return NBODY_OK;
 }
 
+// Hermite predictor: x_p = x + dt (v + dt (a/2 + dt j/6)), v_p = v + dt (a + dt j/2).
+__global__ void hermite_predict_kernel(const float4 *pos, const float4 *vel, const float4 *acc,
+                                       const float4 *jerk, float dt, int n, float4 *xp,
+                                       float4 *vp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 x = pos[i], v = vel[i], a = acc[i], j = jerk[i];
+  const float h2 = 0.5f * dt, h6 = dt * (1.0f / 6.0f);
+  xp[i] = make_float4(fmaf(dt, fmaf(dt, fmaf(h6, j.x, 0.5f * a.x), v.x), x.x),
+                      fmaf(dt, fmaf(dt, fmaf(h6, j.y, 0.5f * a.y), v.y), x.y),
+                      fmaf(dt, fmaf(dt, fmaf(h6, j.z, 0.5f * a.z), v.z), x.z), x.w);
+  vp[i] = make_float4(fmaf(dt, fmaf(h2, j.x, a.x), v.x), fmaf(dt, fmaf(h2, j.y, a.y), v.y),
+                      fmaf(dt, fmaf(h2, j.z, a.z), v.z), 0.0f);
+}
+
+// Hermite corrector (time-symmetric form):
+//   v1 = v + dt/2 (a + a1) + dt^2/12 (j - j1),  x1 = x + dt/2 (v + v1) + dt^2/12 (a - a1)
+__global__ void hermite_correct_kernel(float4 *pos, float4 *vel, float4 *acc, float4 *jerk,
+                                       const float4 *a1v, const float4 *j1v, float dt, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 x = pos[i], v = vel[i], a = acc[i], j = jerk[i], a1 = a1v[i], j1 = j1v[i];
+  const float h = 0.5f * dt, q = dt * dt * (1.0f / 12.0f);
+  float4 v1, x1;
+  v1.x = fmaf(q, j.x - j1.x, fmaf(h, a.x + a1.x, v.x));
+  v1.y = fmaf(q, j.y - j1.y, fmaf(h, a.y + a1.y, v.y));
+  v1.z = fmaf(q, j.z - j1.z, fmaf(h, a.z + a1.z, v.z));
+  v1.w = v.w;
+  x1.x = fmaf(q, a.x - a1.x, fmaf(h, v.x + v1.x, x.x));
+  x1.y = fmaf(q, a.y - a1.y, fmaf(h, v.y + v1.y, x.y));
+  x1.z = fmaf(q, a.z - a1.z, fmaf(h, v.z + v1.z, x.z));
+  x1.w = x.w;
+  pos[i] = x1;
+  vel[i] = v1;
+  acc[i] = a1;
+  jerk[i] = j1;
+}
+
+// Acceleration and jerk at (pos, vel) into (acc, jerk): GAJ kernel + finalize.
+int gaj_eval(const float4 *pos, const float4 *vel, float4 *acc, float4 *jerk, int n,
+             const nbody_params &p, const VjpScratch &sc, cudaStream_t s) {
+  int *err = nullptr;
+  NB_TRY(error_word(&err));
+  VjpArgs a{};
+  a.pos = pos;
+  a.lam = vel;
+  a.part_hi = sc.part_hi;
+  a.part_lo = sc.part_lo;
+  a.stride = n;
+  a.bstride = sc.bstride;
+  a.err = err;
+  a.n = n;
+  a.slices = sc.slices;
+  a.slice_len = sc.slice_len;
+  a.eps2 = p.eps2;
+  a.comp = (p.flags & NBODY_NO_COMPENSATION) ? 0 : 1;
+  const TimerMark tm = timer_begin(0, s);
+  cudaError_t e = sc.d->launch(a, sc.grid, s);
+  timer_end(tm, s);
+  if (e != cudaSuccess)
+    return set_error_msg(NBODY_ECUDA, "jerk kernel launch failed: %s", cudaGetErrorString(e));
+  gaj_finalize_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(
+      sc.part_hi, sc.part_lo, n, sc.bstride, sc.slices, n, p.G, acc, jerk);
+  NB_CUDA(cudaGetLastError());
+  return NBODY_OK;
+}
+
+int check_jerk_params(const nbody_params *params, uint32_t extra_flags) {
+  if (!params) return set_error_msg(NBODY_EINVAL, "params is NULL");
+  const nbody_params &p = *params;
+  if (p.law != NBODY_LAW_GRAV)
+    return set_error_msg(NBODY_EINVAL, "acceleration + jerk is defined for gravity only");
+  if (p.flags & ~(uint32_t)(NBODY_NO_COMPENSATION | extra_flags))
+    return set_error_msg(NBODY_EUNSUPPORTED, "unsupported flag bits 0x%x", p.flags);
+  if (!(p.eps2 >= 0.0f) || !std::isfinite(p.G))
+    return set_error_msg(NBODY_EINVAL, "bad G or eps2");
+  return NBODY_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -279,16 +360,9 @@ int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k
 int nbody_forces_jerk(const void *pos_m, const void *vel, void *acc, void *jerk, int64_t n,
                       const nbody_params *params, nbody_stream_t stream) {
   clear_error();
-  if (!params) return set_error_msg(NBODY_EINVAL, "params is NULL");
+  NB_TRY(check_jerk_params(params, 0));
   if (n < 0 || n > 0x7fffffffLL) return set_error_msg(NBODY_EINVAL, "n out of range");
   if (n == 0) return NBODY_OK;
-  const nbody_params p = *params;
-  if (p.law != NBODY_LAW_GRAV)
-    return set_error_msg(NBODY_EINVAL, "acceleration + jerk is defined for gravity only");
-  if (p.flags & ~(uint32_t)NBODY_NO_COMPENSATION)
-    return set_error_msg(NBODY_EUNSUPPORTED, "nbody_forces_jerk supports NO_COMPENSATION only");
-  if (!(p.eps2 >= 0.0f) || !std::isfinite(p.G))
-    return set_error_msg(NBODY_EINVAL, "bad G or eps2");
   NB_TRY(check_dev(pos_m, "pos_m", true));
   NB_TRY(check_dev(vel, "vel", true));
   NB_TRY(check_dev(acc, "acc", true));
@@ -298,31 +372,49 @@ int nbody_forces_jerk(const void *pos_m, const void *vel, void *acc, void *jerk,
   NB_TRY(check_dev_ptrs({pos_m, vel, acc, jerk}));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   VjpScratch sc{};
-  NB_TRY(vjp_prepare(kLawGAJ, int(n), sms, s, &sc));
-  int *err = nullptr;
-  NB_TRY(error_word(&err));
-  VjpArgs a{};
-  a.pos = static_cast<const float4 *>(pos_m);
-  a.lam = static_cast<const float4 *>(vel);
-  a.part_hi = sc.part_hi;
-  a.part_lo = sc.part_lo;
-  a.stride = n;
-  a.bstride = sc.bstride;
-  a.err = err;
-  a.n = int(n);
-  a.slices = sc.slices;
-  a.slice_len = sc.slice_len;
-  a.eps2 = p.eps2;
-  a.comp = (p.flags & NBODY_NO_COMPENSATION) ? 0 : 1;
-  const TimerMark tm = timer_begin(0, s);
-  cudaError_t e = sc.d->launch(a, sc.grid, s);
-  timer_end(tm, s);
-  if (e != cudaSuccess)
-    return set_error_msg(NBODY_ECUDA, "jerk kernel launch failed: %s", cudaGetErrorString(e));
-  gaj_finalize_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(
-      sc.part_hi, sc.part_lo, n, sc.bstride, sc.slices, int(n), p.G, static_cast<float4 *>(acc),
-      static_cast<float4 *>(jerk));
-  NB_CUDA(cudaGetLastError());
+  NB_TRY(vjp_prepare(kLawGAJ, int(n), sms, s, &sc, 0));
+  return gaj_eval(static_cast<const float4 *>(pos_m), static_cast<const float4 *>(vel),
+                  static_cast<float4 *>(acc), static_cast<float4 *>(jerk), int(n), *params, sc, s);
+}
+
+int nbody_hermite_step(void *pos_m, void *vel, void *acc, void *jerk, int64_t n, float dt,
+                       int32_t nsteps, const nbody_params *params, nbody_stream_t stream) {
+  clear_error();
+  NB_TRY(check_jerk_params(params, NBODY_ACC_VALID));
+  if (n < 0 || n > 0x7fffffffLL) return set_error_msg(NBODY_EINVAL, "n out of range");
+  if (nsteps < 0) return set_error_msg(NBODY_EINVAL, "nsteps must be >= 0");
+  if (!std::isfinite(dt)) return set_error_msg(NBODY_EINVAL, "dt must be finite");
+  if (n == 0) return NBODY_OK;
+  NB_TRY(check_dev(pos_m, "pos_m", true));
+  NB_TRY(check_dev(vel, "vel", true));
+  NB_TRY(check_dev(acc, "acc", true));
+  NB_TRY(check_dev(jerk, "jerk", true));
+  int dev = 0, sms = 0;
+  NB_TRY(check_device(&dev, &sms));
+  NB_TRY(check_dev_ptrs({pos_m, vel, acc, jerk}));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // scratch: GAJ partials, then predicted (x, v) and the new (a, j)
+  VjpScratch sc{};
+  const size_t q = round_up(size_t(n) * sizeof(float4), 256);
+  NB_TRY(vjp_prepare(kLawGAJ, int(n), sms, s, &sc, 4 * q));
+  float4 *xp = reinterpret_cast<float4 *>(sc.extra);
+  float4 *vp = reinterpret_cast<float4 *>(sc.extra + q);
+  float4 *a1 = reinterpret_cast<float4 *>(sc.extra + 2 * q);
+  float4 *j1 = reinterpret_cast<float4 *>(sc.extra + 3 * q);
+  float4 *X = static_cast<float4 *>(pos_m);
+  float4 *V = static_cast<float4 *>(vel);
+  float4 *A = static_cast<float4 *>(acc);
+  float4 *J = static_cast<float4 *>(jerk);
+  const int nn = int(n);
+  if (!(params->flags & NBODY_ACC_VALID)) NB_TRY(gaj_eval(X, V, A, J, nn, *params, sc, s));
+  const unsigned blocks = unsigned((n + 255) / 256);
+  for (int st = 0; st < nsteps; ++st) {
+    hermite_predict_kernel<<<blocks, 256, 0, s>>>(X, V, A, J, dt, nn, xp, vp);
+    NB_CUDA(cudaGetLastError());
+    NB_TRY(gaj_eval(xp, vp, a1, j1, nn, *params, sc, s));
+    hermite_correct_kernel<<<blocks, 256, 0, s>>>(X, V, A, J, a1, j1, dt, nn);
+    NB_CUDA(cudaGetLastError());
+  }
   return NBODY_OK;
 }
 

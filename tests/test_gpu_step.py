@@ -152,3 +152,25 @@ def test_two_float_state_removes_rounding_drift():
         errs[comp] = float(np.sqrt(np.mean(np.sum((x - xs[-1]) ** 2, axis=1))))
     assert errs[True] <= 0.5 * errs[False], errs
     assert errs[True] <= 1e-7, errs
+
+
+def test_hermite_steps_match_oracle():
+    """Fourth-order Hermite steps on acceleration + jerk (Table 1 GAJ) against the
+    FP64 oracle's Hermite integrator."""
+    nb = lib()
+    g = workloads.plummer(2048, seed=23, eps=0.01)
+    pos, vel = grav_tensors(g)
+    acc = torch.empty_like(pos)
+    jerk = torch.empty_like(pos)
+    nb.hermite_step(pos, vel, acc, jerk, dt=1e-3, nsteps=6, eps=float(np.float32(g.eps)))
+    nb.hermite_step(pos, vel, acc, jerk, dt=1e-3, nsteps=4, eps=float(np.float32(g.eps)),
+                    acc_valid=True)
+    x, v, m = g.f32_as_f64()
+    xr, vr = oracle.hermite(x, v, m, 1e-3, 10, eps=float(np.float32(g.eps)))
+    ex = traj_errors(pos[:, :3].cpu().numpy(), xr)
+    ev = traj_errors(vel[:, :3].cpu().numpy(), vr)
+    assert ex[0] <= 1e-6 and ex[1] <= 1e-5, ex
+    assert ev[0] <= 1e-5 and ev[1] <= 1e-4, ev
+    ra, rj = oracle.grav_jerk(xr, vr, m, eps=float(np.float32(g.eps)))
+    e = np.linalg.norm(jerk[:, :3].cpu().numpy() - rj, axis=1) / np.linalg.norm(rj, axis=1)
+    assert np.sqrt(np.mean(e ** 2)) <= 1e-4
