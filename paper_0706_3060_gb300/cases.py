@@ -1,0 +1,81 @@
+"""Run one named workload a few times through the C ABI (for profilers such as
+``ncu -k regex:<kernel>``): each case builds its seeded inputs, runs ``--warmup``
+untimed calls and ``--iters`` more, then synchronizes.
+
+    python -m paper_0706_3060_gb300.cases grav262144 --warmup 1 --iters 2
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+import numpy as np
+
+
+def _grav(nb, torch, dev, n, seed=1):
+    import workloads
+    g = workloads.plummer(n, seed=seed, eps=workloads.plummer_softening(n))
+    x, v, m = g.f32()
+    pos = torch.from_numpy(np.concatenate([x, m[:, None]], 1)).to(dev).contiguous()
+    vel = torch.from_numpy(np.concatenate([v, np.zeros((n, 1), np.float32)], 1)).to(dev)
+    return pos, vel.contiguous(), float(np.float32(g.eps))
+
+
+def _ljc(nb, torch, dev, n, seed=2):
+    import workloads
+    s = workloads.ljc_sphere(n, seed=seed)
+    x, v, m, q, st, et = s.f32()
+    pos = torch.from_numpy(np.concatenate([x, m[:, None]], 1)).to(dev).contiguous()
+    prm = nb.pack_ljc(torch.from_numpy(q.astype(np.float64)).to(dev),
+                      torch.from_numpy(st.astype(np.float64)[s.types]).to(dev),
+                      torch.from_numpy(et.astype(np.float64)[s.types]).to(dev),
+                      torch.from_numpy(s.types).to(dev), kq=332.0637 / 80.0)
+    return pos, prm
+
+
+def build_case(name, nb, torch, dev):
+    """Return a zero-argument callable running one call of the named workload."""
+    if name == "grav262144":
+        pos, _, eps = _grav(nb, torch, dev, 262144)
+        acc = torch.empty_like(pos)
+        return lambda: nb.forces(pos, eps=eps, out=acc)
+    if name == "ljc8192":
+        pos, prm = _ljc(nb, torch, dev, 8192)
+        acc = torch.empty_like(pos)
+        return lambda: nb.forces(pos, prm, out=acc)
+    if name == "vjp16384":
+        pos, _, eps = _grav(nb, torch, dev, 16384, seed=4)
+        lam = torch.randn_like(pos)
+        gx = torch.empty_like(pos)
+        gm = torch.empty(pos.shape[0], device=dev)
+        return lambda: nb.adjoint(pos, lam, eps=eps, grad_x=gx, grad_m=gm)
+    if name == "jerk262144":
+        pos, vel, eps = _grav(nb, torch, dev, 262144)
+        return lambda: nb.forces_jerk(pos, vel, eps=eps)
+    raise ValueError(f"unknown case {name}")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["grav262144", "ljc8192", "vjp16384", "jerk262144"])
+    ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--iters", type=int, default=2)
+    a = ap.parse_args()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import torch
+
+    import paper_0706_3060_gb300 as nb
+    dev = torch.device("cuda", 0)
+    fn = build_case(a.case, nb, torch, dev)
+    for _ in range(a.warmup + a.iters):
+        fn()
+    torch.cuda.synchronize()
+    nb.sync_check()
+    print(f"{a.case}: ok")
+
+
+if __name__ == "__main__":
+    main()
