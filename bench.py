@@ -361,8 +361,9 @@ def _device_ms(torch, fn, reps=5):
 
 def secondary_kernel_extras(nb, torch, dev, pos, eps):
     """Throughput of the other force forms on the same GPU (device time per call):
-    LJ + Coulomb on the 8192-atom sphere; acceleration + jerk, an active subset of
-    1024 targets and the fixed-point mode on the N = 262144 Plummer sphere."""
+    LJ + Coulomb (constant and linear dielectric) on the 8192-atom sphere;
+    acceleration + jerk, a Hermite step, an active subset of 1024 targets and the
+    fixed-point mode on the N = 262144 Plummer sphere."""
     import workloads
     out = {}
     s = workloads.ljc_sphere(8192, seed=2)
@@ -384,6 +385,18 @@ def secondary_kernel_extras(nb, torch, dev, pos, eps):
     out["subset_1024_of_262144_gpairs_per_s"] = 1024.0 * n / ms / 1e6
     ms = _device_ms(torch, lambda: nb.forces(pos, eps=eps, fixed=True), reps=3)
     out["fixed_point_262144_gpairs_per_s"] = float(n) ** 2 / ms / 1e6
+    prm_lin = nb.pack_ljc(torch.from_numpy(q.astype(np.float64)).to(dev),
+                          torch.from_numpy(st.astype(np.float64)[s.types]).to(dev),
+                          torch.from_numpy(et.astype(np.float64)[s.types]).to(dev),
+                          torch.from_numpy(s.types).to(dev), kq=332.0637 / 4.0)
+    ms = _device_ms(torch, lambda: nb.forces(lpos, prm_lin, law=nb.LAW_LJC_LINEAR))
+    out["ljc_linear_8192_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
+    hp, hv = pos.clone(), vel.clone()
+    ha, hj = torch.empty_like(pos), torch.empty_like(pos)
+    nb.hermite_step(hp, hv, ha, hj, dt=DT, nsteps=0, eps=eps)
+    ms = _device_ms(torch, lambda: nb.hermite_step(hp, hv, ha, hj, dt=DT, nsteps=1, eps=eps,
+                                                    acc_valid=True), reps=3)
+    out["hermite_step_262144_gpairs_per_s"] = float(n) ** 2 / ms / 1e6
     return out
 
 

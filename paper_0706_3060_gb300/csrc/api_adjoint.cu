@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <initializer_list>
 #include <cmath>
 
@@ -37,15 +38,29 @@ struct VjpImpl {
     k<<<grid, T::kThreads, T::kSmemBytes, s>>>(a);
     return cudaGetLastError();
   }
-  static int occupancy() {
+  static int occupancy() {  // cached per device, as for the force tiles
+    static std::atomic<int> cached[kMaxDevicesTile];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesTile) {
+      cudaGetLastError();
+      dev = -1;
+    }
+    if (dev >= 0) {
+      const int c = cached[dev].load(std::memory_order_relaxed);
+      if (c > 0) return c;
+    }
     int nb = 0;
     auto k = vjp_kernel<LAW, NT, I, SW, JT, PK>;
     if (T::kSmemBytes > 32 * 1024)
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, T::kThreads, T::kSmemBytes) !=
-        cudaSuccess)
+        cudaSuccess) {
+      cudaGetLastError();
       return 1;
-    return std::max(nb, 1);
+    }
+    nb = std::max(nb, 1);
+    if (dev >= 0) cached[dev].store(nb, std::memory_order_relaxed);
+    return nb;
   }
   static VjpDesc desc() {
     return VjpDesc{T::kTileI, JT, T::kThreads, T::kSmemBytes, PK, &launch, &occupancy};

@@ -24,6 +24,10 @@ const TileDesc *grav_tiles(int *count) {
       TileImpl<kLawGrav, 128, 2, 1, 512, true, 4>::desc(),  // 13: 256, unrolled x4
       TileImpl<kLawGrav, 256, 2, 1, 512, true, 2, 3>::desc(),  // 14: as 10, 3 CTAs/SM bound
       TileImpl<kLawGrav, 128, 2, 1, 512, true, 2, 6>::desc(),  // 15: 256, 6 CTAs/SM bound
+      // packed with j-lanes (small N)
+      TileImpl<kLawGrav, 128, 2, 4, 256, true>::desc(),  // 16: 64 targets, 4 j-lanes
+      TileImpl<kLawGrav, 128, 2, 2, 256, true>::desc(),  // 17: 128 targets, 2 j-lanes
+      TileImpl<kLawGrav, 64, 2, 8, 256, true>::desc(),   // 18: 16 targets, 8 j-lanes
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;

@@ -233,8 +233,7 @@ template <int LAW, int NT, int I, int SW, int JT, bool POT, bool PRECISE, bool P
           int PU = 2, int MINB = 1, bool FX = false>
 __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a) {
   using T = ForceTile<LAW, NT, I, SW, JT>;
-  static_assert(!PK || ((LAW == kLawGrav || is_ljc(LAW)) && SW == 1),
-                "packed path: one law, one j-lane");
+  static_assert(!PK || LAW == kLawGrav || is_ljc(LAW), "packed path: one law per kernel");
   constexpr bool LIN = (LAW == kLawLJCLin);
   constexpr int PF4 = PairLayout<is_ljc(LAW) ? kLawLJC : kLawGrav>::kF4;
   constexpr int STAGE_F4 = PK ? PF4 * JT / 2 : JT;  // float4s per ring stage
@@ -415,7 +414,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
           e2[r] = make_float2(ei[r], ei[r]);
         }
 #pragma unroll PU
-        for (int pp = 0; pp < npairs; ++pp) {
+        for (int pp = jl; pp < npairs; pp += SW) {
           const float4 A = sp[3 * pp];
           const float4 B = sp[3 * pp + 1];
           const float4 C = sp[3 * pp + 2];
@@ -427,7 +426,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
                                     nz[r], q2[r], s2[r], e2[r], pax[r], pay[r], paz[r], ppt[r]);
         }
       } else {
-        for (int jj = 0; jj < len; ++jj) {
+        for (int jj = jl; jj < len; jj += SW) {
           const float4 A = sp[3 * (jj >> 1)];
           const float4 B = sp[3 * (jj >> 1) + 1];
           const float4 C = sp[3 * (jj >> 1) + 2];
@@ -453,7 +452,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
           nz[r] = make_float2(-zi[r], -zi[r]);
         }
 #pragma unroll PU
-        for (int pp = 0; pp < npairs; ++pp) {
+        for (int pp = jl; pp < npairs; pp += SW) {
           const float4 A = sp[2 * pp];
           const float4 B = sp[2 * pp + 1];
           const float2 X = make_float2(A.x, A.y), Y = make_float2(A.z, A.w);
@@ -465,7 +464,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
         }
       } else {
         // Diagonal tile: one source at a time from the pair layout, self masked.
-        for (int jj = 0; jj < len; ++jj) {
+        for (int jj = jl; jj < len; jj += SW) {
           const float4 A = sp[2 * (jj >> 1)];
           const float4 B = sp[2 * (jj >> 1) + 1];
           const bool odd = jj & 1;

@@ -16,6 +16,9 @@ const TileDesc *ljc_tiles(int *count) {
       TileImpl<kLawLJC, 128, 2, 1, 256, true>::desc(),   // 6: 256
       TileImpl<kLawLJC, 64, 2, 1, 256, true>::desc(),    // 7: 128
       TileImpl<kLawLJC, 256, 2, 1, 512, true>::desc(),   // 8: 512, longer j-tiles
+      TileImpl<kLawLJC, 128, 2, 4, 256, true>::desc(),   // 9: packed, 64 targets, 4 j-lanes
+      TileImpl<kLawLJC, 128, 2, 2, 256, true>::desc(),   // 10: packed, 128 targets, 2 j-lanes
+      TileImpl<kLawLJC, 64, 2, 8, 256, true>::desc(),    // 11: packed, 16 targets, 8 j-lanes
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;

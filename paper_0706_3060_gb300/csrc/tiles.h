@@ -3,9 +3,13 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "force_kernel.cuh"
 
 namespace nbody {
+
+constexpr int kMaxDevicesTile = 64;
 
 using ForceLauncher = cudaError_t (*)(const ForceArgs &, int grid, bool pot, bool precise,
                                       cudaStream_t);
@@ -53,15 +57,31 @@ struct TileImpl {
     if (pot) return precise ? go<true, true>(a, grid, s) : go<true, false>(a, grid, s);
     return precise ? go<false, true>(a, grid, s) : go<false, false>(a, grid, s);
   }
+  // Resident CTAs per SM, queried once per device and kept (the query costs a few
+  // microseconds, which small-N calls would otherwise pay every time).
   static int occupancy() {
+    static std::atomic<int> cached[kMaxDevicesTile];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesTile) {
+      cudaGetLastError();
+      dev = -1;
+    }
+    if (dev >= 0) {
+      const int c = cached[dev].load(std::memory_order_relaxed);
+      if (c > 0) return c;
+    }
     int nb = 0;
     auto k = force_kernel<LAW, NT, I, SW, JT, false, false, PK, PU, MINB, FX>;
     if (T::kSmemBytes > 32 * 1024)
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, T::kThreads, T::kSmemBytes) !=
-        cudaSuccess)
+        cudaSuccess) {
+      cudaGetLastError();
       return 1;
-    return nb > 0 ? nb : 1;
+    }
+    nb = nb > 0 ? nb : 1;
+    if (dev >= 0) cached[dev].store(nb, std::memory_order_relaxed);
+    return nb;
   }
   static TileDesc desc() {
     return TileDesc{LAW, NT, I, SW, JT, T::kTileI, T::kThreads, T::kSmemBytes, PK, FX, &launch,

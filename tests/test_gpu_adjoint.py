@@ -152,3 +152,20 @@ def test_ljc_reverse_leapfrog_vs_oracle():
     assert _rel(m0.grad.cpu().numpy(), ref["m"]) <= 1e-3
     assert _rel(sig.grad.cpu().numpy(), ref["sig_t"]) <= 1e-3
     assert _rel(eps.grad.cpu().numpy(), ref["eps_t"]) <= 1e-3
+
+
+def test_adjoint_workload_size_one_chunk():
+    """The adjoint workload's size (Plummer N = 16384, eps = 0.04 N^-1/3, dt = 1e-4)
+    over one 20-step checkpoint chunk, against the FP64 oracle's gradient."""
+    n = 16384
+    g = workloads.plummer(n, seed=4, eps=workloads.plummer_softening(n))
+    target = workloads.perturbed_target(g.f32_as_f64()[0], seed=4)
+    gx, gv, gm, _ = _grav_autograd_grads(g, 1e-4, 20, 20, target)
+    x, v, m = g.f32_as_f64()
+    sysm = oracle.GravSystem(m, eps=float(np.float32(g.eps)))
+    xs, _ = oracle.leapfrog(sysm, x, v, 1e-4, 20, store=True)
+    ref = oracle.adjoint_leapfrog(sysm, x, v, 1e-4, 20, oracle.target_loss_grad(xs[-1], target),
+                                  xs=xs)
+    assert _rel(gx, ref["x0"]) <= 1e-4
+    assert _rel(gv, ref["v0"]) <= 1e-4
+    assert _rel(gm, ref["m"]) <= 1e-3

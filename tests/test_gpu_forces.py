@@ -37,7 +37,7 @@ def test_grav_default_config(n):
     assert_forces_close(acc[:, :3].cpu().numpy(), ref, what=f"n={n}")
 
 
-@pytest.mark.parametrize("tile", range(16))
+@pytest.mark.parametrize("tile", range(19))
 @pytest.mark.parametrize("jsplit", [1, 3])
 def test_grav_every_tile(tile, jsplit):
     nb = lib()
@@ -142,7 +142,7 @@ def test_ljc_forces(n):
     assert np.sqrt(np.mean(e * e)) <= 1e-5 and e.max() <= 1e-4
 
 
-@pytest.mark.parametrize("tile", range(9))
+@pytest.mark.parametrize("tile", range(12))
 def test_ljc_every_tile(tile):
     nb = lib()
     s = workloads.ljc_sphere(1500, seed=9)
@@ -327,3 +327,25 @@ def test_fixed_point_steps_split_independent_and_rejections():
     lpos, _, prm = ljc_tensors(s)
     with pytest.raises(nb.NBodyError):
         nb.forces(lpos, prm, fixed=True)
+
+
+def test_force_call_captures_into_cuda_graph():
+    """A warmed-up nbody_forces call can be captured in a CUDA graph and replayed
+    (launch-bound small systems), giving the same bits as the direct call."""
+    nb = lib()
+    g = workloads.plummer(4096, seed=3, eps=0.01)
+    pos, _ = grav_tensors(g)
+    eps = float(np.float32(g.eps))
+    acc = torch.empty_like(pos)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        nb.forces(pos, eps=eps, out=acc)      # sizes the workspace outside capture
+    s.synchronize()
+    ref = acc.clone()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        nb.forces(pos, eps=eps, out=acc)
+    acc.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(acc, ref)
