@@ -128,6 +128,14 @@ int nbody_timing_read(int32_t which, int64_t *launches, double *total_ms);
  * device. */
 int nbody_peak_probe(int32_t kind, int32_t iters, double *ops_per_clk_sm, double *ops_per_s);
 
+/* Failure-path self test (no counterpart in the paper): enqueues one kernel that
+ * waits, with the bounded wait every pipeline uses but limited to limit_cycles
+ * (1 .. 1e8), on an mbarrier that nothing completes. The wait runs out, the
+ * kernel records NBODY_ETIMEOUT in the error word and returns, and the next
+ * nbody_check on `stream` reports NBODY_ETIMEOUT and clears it. Nothing faults
+ * or hangs; the context stays usable. */
+int nbody_selftest_timeout(int64_t limit_cycles, nbody_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * S0 pack (Sec. 2 "stream coordinates"; Appendix jpos/jmass float4).
  * Converts caller SoA data in double precision into the float4 streams above.

@@ -38,7 +38,7 @@ EXPORTS = (
     "nbody_batch_run", "nbody_forces_batched", "nbody_adjoint", "nbody_adjoint_leapfrog",
     "nbody_tile_count", "nbody_tile_info", "nbody_set_tuned", "nbody_get_config",
     "nbody_timing_enable", "nbody_timing_read", "nbody_peak_probe", "nbody_forces_static",
-    "nbody_forces_subset", "nbody_forces_jerk", "nbody_hermite_step",
+    "nbody_forces_subset", "nbody_forces_jerk", "nbody_hermite_step", "nbody_selftest_timeout",
 )
 
 
@@ -92,6 +92,7 @@ def load(path: str | None = None):
             "nbody_forces_subset": ([vp, vp, vp, i64, vp, i64, pp, vp], ctypes.c_int),
             "nbody_forces_jerk": ([vp, vp, vp, vp, i64, pp, vp], ctypes.c_int),
             "nbody_hermite_step": ([vp, vp, vp, vp, i64, f32, i32, pp, vp], ctypes.c_int),
+            "nbody_selftest_timeout": ([i64, vp], ctypes.c_int),
             "nbody_step": ([vp, vp, vp, vp, i64, f32, i32, i32, vp, vp, vp, pp, vp],
                            ctypes.c_int),
             "nbody_batch_plan_create": ([ctypes.POINTER(NBodySystem), i32, u32, i32,

@@ -30,6 +30,10 @@ struct nbody_batch_plan {
   int *d_counter = nullptr;  // one counter per force evaluation of a run
   int counters = 0;
   float4 *d_part = nullptr;  // [2][max_slices][total]
+  // packed tiles: per-law pair buffers and, per system, (offset, pair base, n, law)
+  float4 *d_jgrav = nullptr;
+  float4 *d_jljc = nullptr;
+  int4 *d_sysp = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   const void *gkey[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -48,6 +52,9 @@ void free_plan(nbody_batch_plan *p) {
   cudaFree(p->d_sys_of);
   cudaFree(p->d_counter);
   cudaFree(p->d_part);
+  cudaFree(p->d_jgrav);
+  cudaFree(p->d_jljc);
+  cudaFree(p->d_sysp);
   delete p;
 }
 
@@ -58,6 +65,54 @@ int ensure_counters(nbody_batch_plan *p, int need) {
   NB_CUDA(cudaMalloc(&p->d_counter, sizeof(int) * size_t(need)));
   p->counters = need;
   return NBODY_OK;
+}
+
+// Packed tiles: every particle writes its half of its system's source pair in the
+// layout of its law; the last particle of an odd system also writes the pad half
+// (far away, no mass, charge or well), whose pair terms are exactly zero.
+__global__ void interleave_systems_kernel(const float4 *pos, const float4 *prm,
+                                          const int *sys_of, const int4 *sysp, int total,
+                                          float4 *jgrav, float4 *jljc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int k = sys_of[i];
+  if (k < 0) return;
+  const int4 sp = sysp[k];  // offset, pair base, n, law
+  const int local = i - sp.x;
+  const int pair = sp.y + (local >> 1);
+  const int half = local & 1;
+  const bool pad = (local == sp.z - 1) && (sp.z & 1);
+  const float4 x = pos[i];
+  if (sp.w == NBODY_LAW_GRAV) {
+    float *jp = reinterpret_cast<float *>(jgrav + 2 * pair);
+    jp[0 + half] = x.x;
+    jp[2 + half] = x.y;
+    jp[4 + half] = x.z;
+    jp[6 + half] = x.w;
+    if (pad) {
+      jp[1] = 1e18f;
+      jp[3] = 1e18f;
+      jp[5] = 1e18f;
+      jp[7] = 0.0f;
+    }
+  } else {
+    const float4 q = prm[i];
+    float *jp = reinterpret_cast<float *>(jljc + 3 * pair);
+    jp[0 + half] = x.x;
+    jp[2 + half] = x.y;
+    jp[4 + half] = x.z;
+    jp[6 + half] = q.x;
+    jp[8 + half] = q.y;
+    jp[10 + half] = q.z;
+    if (pad) {
+      jp[1] = 1e18f;
+      jp[3] = 1e18f;
+      jp[5] = 1e18f;
+      jp[7] = 0.0f;
+      jp[9] = 0.0f;
+      jp[11] = 0.0f;
+    }
+  }
 }
 
 // Enqueue nsteps leapfrog steps (or one force evaluation when nsteps == 0).
@@ -73,7 +128,14 @@ int enqueue_run(nbody_batch_plan *p, float4 *pos, float4 *vel, float4 *acc, cons
   NB_CUDA(cudaMemsetAsync(p->d_counter, 0, sizeof(int) * size_t(evals), s));
   int counter_idx = 0;
   auto eval = [&](int mode) -> int {
+    if (p->td->packed) {
+      interleave_systems_kernel<<<(total + 255) / 256, 256, 0, s>>>(
+          pos, prm, p->d_sys_of, p->d_sysp, total, p->d_jgrav, p->d_jljc);
+      NB_CUDA(cudaGetLastError());
+    }
     ForceArgs a{};
+    a.jpair = p->d_jgrav;
+    a.jpair2 = p->d_jljc;
     a.pos = pos;
     a.prm = prm;
     a.tpos = pos;
@@ -174,9 +236,14 @@ int nbody_batch_plan_create(const nbody_system *systems, int32_t nsys, uint32_t 
   const double target = std::max(work / (double(grid) * 4.0), double(td->tile_i) * td->jt);
   std::vector<WorkItem> items;
   std::vector<SysInfo> info(nsys);
+  std::vector<int4> sysp(nsys);
   int max_slices = 1;
+  long long pairs_law[2] = {0, 0};  // pair-buffer sizes per law (packed tiles)
   for (int k = 0; k < nsys; ++k) {
     const nbody_system &s = systems[k];
+    const int pbase = int(pairs_law[s.law]);
+    pairs_law[s.law] += (s.n + 1) / 2;
+    sysp[k] = make_int4(int(s.offset), pbase, s.n, s.law);
     const int max_s = (s.n + td->jt - 1) / td->jt;
     int S = int(std::ceil(double(std::min(s.n, td->tile_i)) * s.n / target));
     S = std::max(1, std::min(S, max_s));
@@ -194,6 +261,7 @@ int nbody_batch_plan_create(const nbody_system *systems, int32_t nsys, uint32_t 
         w.law = s.law;
         w.slice = sl;
         w.eps2 = s.eps2;
+        w.pj0 = pbase + (sl * len) / 2;  // slices start at even local indices
         items.push_back(w);
       }
     }
@@ -231,7 +299,15 @@ int nbody_batch_plan_create(const nbody_system *systems, int32_t nsys, uint32_t 
       (e = cudaMemcpy(p->d_sys, info.data(), sizeof(SysInfo) * info.size(),
                       cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(p->d_sys_of, sys_of.data(), sizeof(int) * sys_of.size(),
-                      cudaMemcpyHostToDevice)) != cudaSuccess) {
+                      cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (td->packed &&
+       ((e = cudaMalloc(&p->d_jgrav, sizeof(float4) * 2 * size_t(pairs_law[0] + 1))) !=
+            cudaSuccess ||
+        (e = cudaMalloc(&p->d_jljc, sizeof(float4) * 3 * size_t(pairs_law[1] + 1))) !=
+            cudaSuccess ||
+        (e = cudaMalloc(&p->d_sysp, sizeof(int4) * sysp.size())) != cudaSuccess ||
+        (e = cudaMemcpy(p->d_sysp, sysp.data(), sizeof(int4) * sysp.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess))) {
     cudaGetLastError();
     return fail(set_error_msg(NBODY_ENOMEM, "batch plan allocation failed: %s",
                               cudaGetErrorString(e)));

@@ -42,13 +42,15 @@ struct WorkItem {
   int law;
   int slice;
   float eps2;
-  int pad;
+  int pj0;  // packed kernels: index of the source pair that starts at j0
 };
 
 struct ForceArgs {
   const float4 *pos;   // (x, y, z, m)
   const float4 *prm;   // LJC (q~, s~, e~, type) or null
-  const float4 *jpair; // packed gravity kernels: j-pairs (x0 x1 y0 y1)(z0 z1 m0 m1)
+  const float4 *jpair; // packed kernels: source pairs, gravity (x0 x1 y0 y1)(z0 z1 m0 m1)
+                       // or LJC (x0 x1 y0 y1)(z0 z1 q0 q1)(s0 s1 e0 e1)
+  const float4 *jpair2;// batched packed kernels: the LJC pair buffer (jpair: gravity)
   float4 *part_hi;     // [slices][stride]
   float4 *part_lo;     // [slices][stride]
   long long stride;    // elements per slice
@@ -233,9 +235,10 @@ template <int LAW, int NT, int I, int SW, int JT, bool POT, bool PRECISE, bool P
           int PU = 2, int MINB = 1, bool FX = false>
 __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a) {
   using T = ForceTile<LAW, NT, I, SW, JT>;
-  static_assert(!PK || LAW == kLawGrav || is_ljc(LAW), "packed path: one law per kernel");
   constexpr bool LIN = (LAW == kLawLJCLin);
-  constexpr int PF4 = PairLayout<is_ljc(LAW) ? kLawLJC : kLawGrav>::kF4;
+  constexpr bool MIX = (LAW == kLawMixed);
+  // float4s per source pair (the mixed kernel sizes its stages for the LJC layout)
+  constexpr int PF4 = PairLayout<(is_ljc(LAW) || MIX) ? kLawLJC : kLawGrav>::kF4;
   constexpr int STAGE_F4 = PK ? PF4 * JT / 2 : JT;  // float4s per ring stage
   constexpr int NWARPS = NT / 32;
   constexpr int SLOTS = T::kSlots;
@@ -280,11 +283,15 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
         mbar_arrive(&full_bar[st]);
       } else {
         if (PK) {
-          // Packed layout: a tile of len sources is ceil(len/2) pairs of PF4
-          // float4; an odd tail reads the pad particle after the last source.
-          const uint32_t bytes = uint32_t((len + 1) >> 1) * PF4 * 16u;
+          // Packed layout: a tile of len sources is ceil(len/2) pairs of pf4
+          // float4; an odd tail reads the pad particle after the system's last source.
+          const bool lj = is_ljc(LAW) || (MIX && w.law == kLawLJC);
+          const int pf4 = lj ? 3 : 2;
+          const float4 *src = (MIX && lj) ? a.jpair2 : a.jpair;
+          const uint32_t bytes = uint32_t((len + 1) >> 1) * pf4 * 16u;
           mbar_arrive_expect_tx(&full_bar[st], bytes);
-          tma_load_1d(sm_pos + st * STAGE_F4, a.jpair + (cj0 >> 1) * PF4, bytes, &full_bar[st]);
+          tma_load_1d(sm_pos + st * STAGE_F4, src + (w.pj0 + ((cj0 - w.j0) >> 1)) * pf4, bytes,
+                      &full_bar[st]);
         } else {
           const uint32_t bytes = uint32_t(len) * 16u;
           const bool with_prm = is_ljc(LAW) || (LAW == kLawMixed && w.law == kLawLJC);
@@ -316,7 +323,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
       w.law = is_ljc(LAW) ? kLawLJC : kLawGrav;
       w.slice = s;
       w.eps2 = a.eps2;
-      w.pad = 0;
+      w.pj0 = w.j0 >> 1;
       if (w.ni > 0 && w.nj > 0) push_item(w);
       else set_error(a.err, kDevBadItem);
     } else {
@@ -399,7 +406,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
     const bool masked = a.tidx != nullptr || ((cj0 < cur.i0 + cur.ni) && (cur.i0 < cj0 + len));
     const float eps2 = cur.eps2;
 
-    if (PK && is_ljc(LAW)) {
+    if (PK && (is_ljc(LAW) || (MIX && cur_law == kLawLJC))) {
       if (!masked) {
         const int npairs = (len + 1) >> 1;
         float2 nx[PK ? I : 1], ny[PK ? I : 1], nz[PK ? I : 1];

@@ -10,6 +10,11 @@ const TileDesc *mixed_tiles(int *count) {
       TileImpl<kLawMixed, 128, 2, 1, 256>::desc(),  // 1: 256 targets
       TileImpl<kLawMixed, 128, 2, 2, 256>::desc(),  // 2: 128 targets, 2 j-lanes
       TileImpl<kLawMixed, 64, 2, 8, 128>::desc(),   // 3: 16 targets, 8 j-lanes
+      // packed f32x2 over source pairs of each system (pair buffers per law)
+      TileImpl<kLawMixed, 128, 2, 4, 256, true>::desc(),  // 4: 64 targets, 4 j-lanes
+      TileImpl<kLawMixed, 128, 2, 2, 256, true>::desc(),  // 5: 128 targets, 2 j-lanes
+      TileImpl<kLawMixed, 128, 2, 1, 256, true>::desc(),  // 6: 256 targets
+      TileImpl<kLawMixed, 64, 2, 8, 256, true>::desc(),   // 7: 16 targets, 8 j-lanes
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;

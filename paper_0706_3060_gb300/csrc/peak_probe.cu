@@ -182,9 +182,32 @@ __global__ void __launch_bounds__(kThreads) probe_pairs(float *sink, int iters,
   if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// A wait that nothing completes: one thread initialises an mbarrier that expects
+// one arrival, never arrives, and waits on it with a short bound. The bounded
+// wait gives up after `limit` cycles, records the timeout in the error word and
+// the kernel returns -- the path every pipeline wait takes if a producer stalls.
+__global__ void expired_wait_kernel(long long limit, int *err) {
+  __shared__ __align__(8) uint64_t bar;
+  nbody::mbar_init(&bar, 1);
+  nbody::mbar_fence_init();
+  nbody::mbar_wait(&bar, 0, err, limit);
+}
+
 }  // namespace
 
 using namespace nbody;
+
+extern "C" int nbody_selftest_timeout(int64_t limit_cycles, nbody_stream_t stream) {
+  clear_error();
+  if (limit_cycles < 1 || limit_cycles > 100000000LL)
+    return set_error_msg(NBODY_EINVAL, "limit_cycles must be in [1, 1e8]");
+  NB_TRY(check_device(nullptr, nullptr));
+  int *err = nullptr;
+  NB_TRY(error_word(&err));
+  expired_wait_kernel<<<1, 1, 0, reinterpret_cast<cudaStream_t>(stream)>>>(limit_cycles, err);
+  NB_CUDA(cudaGetLastError());
+  return NBODY_OK;
+}
 
 extern "C" int nbody_peak_probe(int32_t kind, int32_t iters, double *ops_per_clk_sm,
                                 double *ops_per_s) {
