@@ -349,3 +349,34 @@ def test_force_call_captures_into_cuda_graph():
     graph.replay()
     torch.cuda.synchronize()
     assert torch.equal(acc, ref)
+
+
+def test_edge_cases_coincident_massless_and_far():
+    """Coincident distinct particles with eps > 0 stay finite (d = 0 gives no force);
+    massless tracers feel the others but pull on nobody; coordinates far from the
+    origin (1e4) keep the relative accuracy of the differences."""
+    nb = lib()
+    g = workloads.plummer(1000, seed=55, eps=0.05)
+    x, v, m = g.f32()
+    x = x.copy()
+    m = m.copy()
+    x[1] = x[0]                      # two distinct particles at one point
+    m[10:20] = 0.0                   # massless tracers
+    pos = torch.from_numpy(np.concatenate([x, m[:, None]], 1)).to(dev()).contiguous()
+    acc = nb.forces(pos, eps=0.05, pot=True).cpu().numpy()
+    assert np.all(np.isfinite(acc))
+    ref, phi = oracle.grav_accel(x.astype(np.float64), m.astype(np.float64), eps=0.05,
+                                 potential=True)
+    assert_forces_close(acc[:, :3], ref, what="coincident + massless")
+    # tracers do not act on anybody: removing them changes no other acceleration
+    keep = np.r_[0:10, 20:1000]
+    pos2 = pos[torch.from_numpy(keep).to(dev())].contiguous()
+    acc2 = nb.forces(pos2, eps=0.05).cpu().numpy()
+    e = rel_errors(acc2[:, :3], acc[keep, :3])
+    assert e.max() <= 1e-5
+    # shift far from the origin: positions of size 1e4 (FP32 ulp ~1e-3)
+    xf = (x.astype(np.float64) + 1e4).astype(np.float32)
+    posf = torch.from_numpy(np.concatenate([xf, m[:, None]], 1)).to(dev()).contiguous()
+    accf = nb.forces(posf, eps=0.05).cpu().numpy()
+    reff = oracle.grav_accel(xf.astype(np.float64), m.astype(np.float64), eps=0.05)
+    assert_forces_close(accf[:, :3], reff, what="far from origin")
