@@ -33,7 +33,8 @@ DT = 1e-4
 OPS_PER_PAIR = 12          # FP32 lane ops per pair of the plain gravity kernel (no potential)
 FP32_LANES_PER_SM = 128    # FFMA/FADD/FMUL lanes per SM per clock (4 SMSPs x 32)
 SM_MAX_MHZ = 2070.0
-CPU_SAMPLE_TARGETS = 16384  # oracle sample: targets x all N sources per timed "step"
+CPU_SAMPLE_TARGETS = 131072  # oracle sample: targets x all N sources (~10 s on 16 cores)
+CPU_SAMPLE_TARGETS_1T = 2048  # the same on one thread (~3 s)
 
 
 def _env_rank():
@@ -109,10 +110,13 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # oracle (CPU baseline / reference arm)
 # ---------------------------------------------------------------------------
-def oracle_rate(n_targets: int, seed: int = 1):
-    """Time the FP64 oracle on n_targets sampled targets against all N sources."""
+def oracle_rate(n_targets: int, seed: int = 1, threads: int | None = None):
+    """Time the FP64 oracle on n_targets sampled targets against all N sources,
+    on `threads` OpenMP threads (None: all host cores). Returns (pairs/s, s, threads)."""
     import oracle
     import workloads
+    prev = oracle.set_threads(None)
+    used = oracle.set_threads(threads if threads else os.cpu_count())
     g = workloads.plummer(N_BENCH, seed=seed, eps=workloads.plummer_softening(N_BENCH))
     x, _, m = g.f32_as_f64()
     idx = np.sort(np.random.default_rng(7).choice(N_BENCH, n_targets, replace=False))
@@ -121,7 +125,8 @@ def oracle_rate(n_targets: int, seed: int = 1):
     t0 = time.perf_counter()
     oracle.grav_accel(x, m, eps=eps, idx=idx)
     dt = time.perf_counter() - t0
-    return n_targets * N_BENCH / dt, dt
+    oracle.set_threads(prev)
+    return n_targets * N_BENCH / dt, dt, used
 
 
 def run_reference(args):
@@ -136,7 +141,7 @@ def run_reference(args):
         oracle_rate(n_t // 4)
     tot_pairs, tot_t = 0.0, 0.0
     for _ in range(args.steps):
-        r, dt = oracle_rate(n_t)
+        r, dt, cores = oracle_rate(n_t)
         tot_pairs += r * dt
         tot_t += dt
     val = tot_pairs / tot_t / 1e9
@@ -261,11 +266,14 @@ def main():
         if mh and mb and mh.group(1) == kernel_hash():
             roof["traffic"] = int(mb.group(1))
 
+    # kernels per timed step: kick-drift, [pair interleave,] force, finalize(+kick)
+    tile, _ = nb.get_config(nb.LAW_GRAV, N_BENCH)
+    per_step = 3 + int(nb.tile_info(nb.LAW_GRAV, tile)["packed"])
     out = {"metric": metric_name(), "value": value, "unit": "G pair-interactions/s",
            "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": step_ms / K,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded Plummer sphere)", "config": config(world),
-           "roofline": roof, "clocks": clk, "gpu_launches": 3 * K,
+           "roofline": roof, "clocks": clk, "gpu_launches": per_step * K,
            "wall_s_timed_region": t_wall}
 
     # end to end through the C ABI with pinned host buffers (copies inside)
@@ -284,11 +292,15 @@ def main():
                   "path": "nbody_step on pinned host buffers (staged H2D, step, D2H, sync)"}
 
     if rank == 0 and world == 1:
-        r, dt_cpu = oracle_rate(CPU_SAMPLE_TARGETS)
+        r, dt_cpu, used = oracle_rate(CPU_SAMPLE_TARGETS)
+        r1, dt1, _ = oracle_rate(CPU_SAMPLE_TARGETS_1T, threads=1)
         out["cpu_baseline"] = {"value": r / 1e9, "unit": "G pair-interactions/s",
-                               "cores": os.cpu_count(), "kind": "oracle",
+                               "cores": used, "kind": "oracle",
                                "sample": (f"{CPU_SAMPLE_TARGETS} seeded targets x all {N_BENCH} "
-                                          f"sources, FP64, {dt_cpu:.1f} s")}
+                                          f"sources, FP64, {dt_cpu:.1f} s"),
+                               "single_thread_value": r1 / 1e9,
+                               "single_thread_sample": (f"{CPU_SAMPLE_TARGETS_1T} targets, "
+                                                        f"{dt1:.1f} s")}
     if not args.no_extras and rank == 0:
         out["extras"] = extras(nb, torch, dev, g, eps)
     if world > 1:
@@ -340,6 +352,7 @@ def extras(nb, torch, dev, g, eps):
     d = nb.step(pos, vel, a2, dt=DT, nsteps=100, eps=eps, report_every=100).cpu().numpy()
     E0, E1 = d[0, 0] + d[0, 1], d[1, 0] + d[1, 1]
     ex["energy_drift_100_steps"] = float((E1 - E0) / abs(E0))
+    ex.update(size_sweep_extras(nb, torch, dev))
     ex.update(batched_extras(nb, torch, dev))
     ex.update(adjoint_extras(nb, torch, dev))
     ex.update(secondary_kernel_extras(nb, torch, dev, pos, eps))
@@ -398,6 +411,31 @@ def secondary_kernel_extras(nb, torch, dev, pos, eps):
                                                     acc_valid=True), reps=3)
     out["hermite_step_262144_gpairs_per_s"] = float(n) ** 2 / ms / 1e6
     return out
+
+
+def size_sweep_extras(nb, torch, dev, sizes=(16384, 65536, 262144, 1048576)):
+    """One force evaluation (tuned tile, device time) on seeded Plummer spheres of each
+    size with softening 0.04 N^(-1/3); at the largest size, the error of 256 sampled
+    targets against the FP64 oracle."""
+    import oracle
+    import workloads
+    rate, err = {}, {}
+    for n in sizes:
+        g = workloads.plummer(n, seed=1, eps=workloads.plummer_softening(n))
+        e32 = float(np.float32(g.eps))
+        x, _, m = g.f32()
+        p = torch.from_numpy(np.concatenate([x, m[:, None]], 1)).to(dev).contiguous()
+        ms = _device_ms(torch, lambda: nb.forces(p, eps=e32), reps=3)
+        rate[str(n)] = float(n) ** 2 / ms / 1e6
+        if n == sizes[-1]:
+            a = nb.forces(p, eps=e32).cpu().numpy()
+            idx = np.sort(np.random.default_rng(7).choice(n, 256, replace=False))
+            ref = oracle.grav_accel(x.astype(np.float64), m.astype(np.float64), eps=e32, idx=idx)
+            e = np.linalg.norm(a[idx, :3] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+            err = {"n": n, "rms": float(np.sqrt(np.mean(e * e))), "max": float(e.max()),
+                   "sample": "256 seeded targets vs FP64 oracle"}
+        del p
+    return {"forces_gpairs_per_s_by_n": rate, "force_err_largest_n": err}
 
 
 def _ensemble_arrays(nb, torch, dev, ens):

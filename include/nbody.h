@@ -330,9 +330,12 @@ int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k
  * fixed-point accumulation), or a negative status. */
 int nbody_tile_count(int32_t law);
 /* Describe configuration `tile` of `law`: threads per CTA (consumer warps),
- * i-particles per thread, j-lanes per warp, j-tile length. */
+ * i-particles per thread, j-lanes per warp, j-tile length, and whether it
+ * reads pair-interleaved sources (1: each force evaluation is preceded by one
+ * interleave launch; 0: it reads pos_m/prm directly). Any output pointer may
+ * be NULL. */
 int nbody_tile_info(int32_t law, int32_t tile, int32_t *threads, int32_t *i_per_thread,
-                    int32_t *j_lanes, int32_t *j_tile);
+                    int32_t *j_lanes, int32_t *j_tile, int32_t *packed);
 /* Install the tuned (tile, jsplit) for (tile table law, n-bucket); bucket =
  * floor(log2 n) (the batched table uses bucket 0). Used by params->tile == -1. */
 int nbody_set_tuned(int32_t law, int32_t log2n, int32_t tile, int32_t jsplit);

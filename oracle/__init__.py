@@ -85,6 +85,8 @@ def _load():
                                             d, d, d]
             lib.oracle_ljc_vjp.argtypes = [i64, d, d, d, i32p, ctypes.c_int32, d, d,
                                            ctypes.c_double, d, d, d, d, d]
+            lib.oracle_threads.argtypes = [ctypes.c_int]
+            lib.oracle_threads.restype = ctypes.c_int
             for f in (lib.oracle_grav, lib.oracle_ljc, lib.oracle_grav_vjp,
                       lib.oracle_ljc_vjp):
                 f.restype = None
@@ -110,10 +112,10 @@ def _idx(idx):
     return idx, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
 
 
-def set_threads(n: int | None) -> None:
-    """Set the OpenMP thread count used by the compiled oracle."""
-    if n is not None:
-        os.environ["OMP_NUM_THREADS"] = str(int(n))
+def set_threads(n: int | None) -> int:
+    """Set the OpenMP thread count of the compiled oracle (None: leave it);
+    returns the count in force."""
+    return int(_load().oracle_threads(0 if n is None else int(n)))
 
 
 # ---------------------------------------------------------------------------

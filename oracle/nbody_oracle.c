@@ -40,11 +40,22 @@
  * whether the host compiler fuses multiply-adds.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
 int oracle_version(void) { return 1; }
+
+/* Thread count of the OpenMP loops below (n < 1: leave it unchanged); returns
+ * the count now in force. The force sums do not depend on it (each target's
+ * sum runs in index order inside one thread); the VJPs' array reductions add
+ * per-thread partial sums, so their last bits do. */
+int oracle_threads(int n)
+{
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+}
 
 /* ---------------------------------------------------------------------------
  * Softened gravity, Eq. 1:

@@ -107,7 +107,8 @@ def load(path: str | None = None):
                                        ctypes.c_int),
             "nbody_tile_count": ([i32], ctypes.c_int),
             "nbody_tile_info": ([i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
-                                 ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
+                                 ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)],
+                                ctypes.c_int),
             "nbody_set_tuned": ([i32, i32, i32, i32], ctypes.c_int),
             "nbody_timing_enable": ([i32], ctypes.c_int),
             "nbody_peak_probe": ([i32, i32, ctypes.POINTER(f64), ctypes.POINTER(f64)],

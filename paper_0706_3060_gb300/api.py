@@ -301,10 +301,13 @@ def tile_count(law: int) -> int:
 
 
 def tile_info(law: int, tile: int) -> dict:
-    vals = [ctypes.c_int32() for _ in range(4)]
+    vals = [ctypes.c_int32() for _ in range(5)]
     check(load().nbody_tile_info(int(law), int(tile), *[ctypes.byref(v) for v in vals]),
           "nbody_tile_info")
-    return dict(zip(("threads", "i_per_thread", "j_lanes", "j_tile"), (v.value for v in vals)))
+    d = dict(zip(("threads", "i_per_thread", "j_lanes", "j_tile", "packed"),
+                 (v.value for v in vals)))
+    d["packed"] = bool(d["packed"])
+    return d
 
 
 def set_tuned(law: int, n: int, tile: int, jsplit: int = 0) -> None:

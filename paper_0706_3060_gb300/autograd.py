@@ -1,9 +1,10 @@
 """Reverse-mode leapfrog as a torch.autograd.Function with checkpointing.
 
 Forward: ``nsteps`` KDK steps through nbody_step with the compensated two-float
-state, storing (x, v, low parts) every ``k`` steps. Backward: for each chunk, newest first, recompute its positions with
-nbody_step's trace, then run the reverse sweep nbody_adjoint_leapfrog (force
-VJP kernels + fused adjoint updates). With merged half-kicks the sweep is
+state, storing (x, v, low parts) every ``k`` steps, and the positions of the
+newest chunk. Backward: for each chunk, newest first, recompute its positions
+with nbody_step's trace (the newest chunk's are already stored), then run the
+reverse sweep nbody_adjoint_leapfrog (force VJP kernels + fused adjoint updates). With merged half-kicks the sweep is
 
     lam_x += dt/2 J(x_T)^T lam_v                      (only if dL/dv_T != 0)
     for n = T-1 .. 0:  lam_v += dt lam_x;  lam_x += w_n J(x_n)^T lam_v
@@ -51,14 +52,20 @@ class NBodyLeapfrog(torch.autograd.Function):
         prm = _prm(cfg, sig_t, eps_t)
         ckpts = []
         done = 0
+        last_trace = None
         while done < cfg.nsteps:
             steps = min(cfg.k, cfg.nsteps - done)
             ckpts.append((pos.clone(), vel.clone(), lo.clone()))
+            # The newest chunk is the first one the backward pass needs: keep its
+            # positions now instead of recomputing them from the checkpoint.
+            if done + steps == cfg.nsteps:
+                last_trace = torch.empty(((steps + 1) * n, 4), dtype=torch.float32, device=dev)
             api.step(pos, vel, acc, prm, dt=cfg.dt, nsteps=steps, law=cfg.law, G=cfg.G,
-                     eps=cfg.eps, acc_valid=done > 0, state_lo=lo)
+                     eps=cfg.eps, acc_valid=done > 0, state_lo=lo, trace=last_trace)
             done += steps
         ctx.cfg = cfg
         ctx.ckpts = ckpts
+        ctx.last_trace = last_trace
         ctx.prm = prm
         ctx.save_for_backward(pos)
         return pos[:, :3].clone(), vel[:, :3].clone()
@@ -87,10 +94,13 @@ class NBodyLeapfrog(torch.autograd.Function):
         for c in range(len(ctx.ckpts) - 1, -1, -1):
             p0, v0, l0 = ctx.ckpts[c]
             steps = min(cfg.k, cfg.nsteps - starts[c])
-            pos, vel, lo = p0.clone(), v0.clone(), l0.clone()
-            trace = torch.empty(((steps + 1) * n, 4), dtype=torch.float32, device=dev)
-            api.step(pos, vel, acc, ctx.prm, dt=cfg.dt, nsteps=steps, law=cfg.law, G=cfg.G,
-                     eps=cfg.eps, trace=trace, state_lo=lo)
+            if c == len(ctx.ckpts) - 1 and ctx.last_trace is not None:
+                trace = ctx.last_trace
+            else:
+                pos, vel, lo = p0.clone(), v0.clone(), l0.clone()
+                trace = torch.empty(((steps + 1) * n, 4), dtype=torch.float32, device=dev)
+                api.step(pos, vel, acc, ctx.prm, dt=cfg.dt, nsteps=steps, law=cfg.law, G=cfg.G,
+                         eps=cfg.eps, trace=trace, state_lo=lo)
             api.adjoint_leapfrog(trace, lam_x, lam_v, ctx.prm, k=steps, dt=cfg.dt,
                                  first=starts[c] == 0, law=cfg.law, G=cfg.G, eps=cfg.eps,
                                  grad_m=grad_m, grad_types=gt, ntypes=cfg.ntypes)

@@ -384,7 +384,7 @@ int nbody_tile_count(int32_t law) {
 }
 
 int nbody_tile_info(int32_t law, int32_t tile, int32_t *threads, int32_t *i_per_thread,
-                    int32_t *j_lanes, int32_t *j_tile) {
+                    int32_t *j_lanes, int32_t *j_tile, int32_t *packed) {
   clear_error();
   if (law < 0 || law >= kTables) return set_error_msg(NBODY_EINVAL, "bad law %d", law);
   int count = 0;
@@ -394,6 +394,7 @@ int nbody_tile_info(int32_t law, int32_t tile, int32_t *threads, int32_t *i_per_
   if (i_per_thread) *i_per_thread = t[tile].i;
   if (j_lanes) *j_lanes = t[tile].sw;
   if (j_tile) *j_tile = t[tile].jt;
+  if (packed) *packed = t[tile].packed ? 1 : 0;
   return NBODY_OK;
 }
 

@@ -42,6 +42,8 @@ def test_version_and_tiles(lib):
             info = nb.tile_info(law, t)
             assert info["threads"] % 32 == 0 and 32 % info["j_lanes"] == 0
             assert info["j_tile"] % info["j_lanes"] == 0
+            if info["packed"]:   # packed tiles walk source pairs
+                assert info["j_tile"] % 2 == 0
     with pytest.raises(nb.NBodyError):
         nb.tile_info(0, 99)
 
