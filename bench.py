@@ -324,12 +324,21 @@ def aggregate(t_local: float, pairs_per_step: float, steps: int, world: int, dev
 
 
 def kernel_hash() -> str:
+    """Identity of the timed force kernel: its sources and the tuned gravity
+    entry for the bench size (other tuning-table entries do not change it)."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("csrc/force_kernel.cuh", "csrc/device_common.cuh", "csrc/force_grav.cu",
-              "tuned.json"):
-        with open(os.path.join(ROOT, "paper_0706_3060_gb300", f), "rb") as fh:
+    pkg = os.path.join(ROOT, "paper_0706_3060_gb300")
+    for f in ("csrc/force_kernel.cuh", "csrc/device_common.cuh", "csrc/force_grav.cu"):
+        with open(os.path.join(pkg, f), "rb") as fh:
             h.update(fh.read())
+    bucket = str(int(math.floor(math.log2(N_BENCH))))
+    with open(os.path.join(pkg, "tuned.json")) as fh:
+        data = json.load(fh)
+    ent = sorted((k, json.dumps({x: v.get("0", {}).get(bucket, {}).get(x)
+                                 for x in ("tile", "jsplit")}, sort_keys=True))
+                 for k, v in data.items())
+    h.update(json.dumps(ent).encode())
     return h.hexdigest()[:16]
 
 

@@ -91,7 +91,11 @@ typedef struct {
     uint32_t flags;  /* NBODY_* flags above                                  */
     float G;         /* gravitational constant (gravity)                     */
     float eps2;      /* squared softening eps^2 (gravity; the Appendix "eps") */
-    int32_t tile;    /* kernel tile configuration, -1 = tuned/default        */
+    int32_t tile;    /* kernel tile configuration, -1 = tuned/default: a row
+                        of the law's force table (0-2, 4 with FIXED_POINT);
+                        for nbody_adjoint / nbody_adjoint_leapfrog a row of
+                        table 5 (gravity VJP) or 6 (LJC VJP); for
+                        nbody_forces_jerk / nbody_hermite_step of table 7  */
     int32_t jsplit;  /* j-slices per i-tile ("replication", Sec. 3.4), 0 = auto */
 } nbody_params;
 
@@ -327,7 +331,8 @@ int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k
  * --------------------------------------------------------------------------- */
 /* Number of compiled tile configurations for tile table `law` (0 gravity,
  * 1 LJC, 2 LJC linear, 3 the mixed-law batched kernel, 4 gravity with
- * fixed-point accumulation), or a negative status. */
+ * fixed-point accumulation, 5 the gravity VJP, 6 the LJC VJP, 7 acceleration
+ * + jerk), or a negative status. */
 int nbody_tile_count(int32_t law);
 /* Describe configuration `tile` of `law`: threads per CTA (consumer warps),
  * i-particles per thread, j-lanes per warp, j-tile length, and whether it

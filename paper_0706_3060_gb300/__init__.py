@@ -8,7 +8,7 @@ that ABI. There is no CPU fallback: calls raise if the library is not built.
 from . import _lib
 from ._lib import (ACC_VALID, ACCUMULATE, COMPUTE_POT, FIXED_POINT, LAW_GRAV, LAW_LJC,
                    LAW_LJC_LINEAR, NO_COMPENSATION, PRECISE_RSQRT, TABLE_BATCHED,
-                   TABLE_GRAV_FIXED, NBodyError)
+                   TABLE_GRAV_FIXED, TABLE_JERK, TABLE_VJP_GRAV, TABLE_VJP_LJC, NBodyError)
 from .api import (COULOMB_K, BatchPlan, adjoint, adjoint_leapfrog, forces, forces_batched,
                   forces_jerk, forces_subset, hermite_step,
                   get_config, pack_grav, pack_ljc, params, release, set_tuned, step, sync_check,
@@ -16,7 +16,8 @@ from .api import (COULOMB_K, BatchPlan, adjoint, adjoint_leapfrog, forces, force
 
 __all__ = [
     "ACC_VALID", "ACCUMULATE", "COMPUTE_POT", "LAW_GRAV", "LAW_LJC", "LAW_LJC_LINEAR",
-    "TABLE_BATCHED", "TABLE_GRAV_FIXED", "FIXED_POINT", "NO_COMPENSATION",
+    "TABLE_BATCHED", "TABLE_GRAV_FIXED", "TABLE_JERK", "TABLE_VJP_GRAV", "TABLE_VJP_LJC",
+    "FIXED_POINT", "NO_COMPENSATION",
     "PRECISE_RSQRT", "NBodyError", "COULOMB_K", "BatchPlan", "adjoint", "adjoint_leapfrog",
     "forces", "forces_batched", "forces_jerk", "forces_subset", "hermite_step", "get_config", "pack_grav", "pack_ljc", "params", "release",
     "set_tuned", "step", "sync_check", "tile_count", "tile_info", "timing_enable",

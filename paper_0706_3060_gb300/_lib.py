@@ -29,6 +29,9 @@ ACC_VALID = 1 << 3
 ACCUMULATE = 1 << 4
 FIXED_POINT = 1 << 5
 TABLE_GRAV_FIXED = 4  # tile table of the fixed-point gravity kernels
+TABLE_VJP_GRAV = 5  # tile table of the gravity VJP kernels (nbody_adjoint*)
+TABLE_VJP_LJC = 6  # tile table of the LJC VJP kernels
+TABLE_JERK = 7  # tile table of the acceleration + jerk kernels
 
 # Every symbol include/nbody.h declares.
 EXPORTS = (

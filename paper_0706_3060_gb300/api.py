@@ -147,13 +147,15 @@ def forces_subset(pos_m, idx, prm=None, *, law=None, G=1.0, eps=0.0, pot=False, 
     return acc
 
 
-def forces_jerk(pos_m, vel, *, G=1.0, eps=0.0, compensated=True, stream=None):
-    """Acceleration and jerk (Table 1 GAJ): returns (acc, jerk), each (n, 4)."""
+def forces_jerk(pos_m, vel, *, G=1.0, eps=0.0, compensated=True, tile=-1, jsplit=0,
+                stream=None):
+    """Acceleration and jerk (Table 1 GAJ): returns (acc, jerk), each (n, 4).
+    ``tile`` indexes tile table 7 (-1: tuned/default)."""
     _check4(pos_m, "pos_m")
     _check4(vel, "vel")
     acc = torch.empty_like(pos_m)
     jerk = torch.empty_like(pos_m)
-    p = params(LAW_GRAV, G, eps, compensated=compensated)
+    p = params(LAW_GRAV, G, eps, compensated=compensated, tile=tile, jsplit=jsplit)
     check(_lib().nbody_forces_jerk(_ptr(pos_m), _ptr(vel), _ptr(acc), _ptr(jerk), pos_m.shape[0],
                                    ctypes.byref(p), _stream(stream, pos_m.device)),
           "nbody_forces_jerk")
@@ -161,11 +163,12 @@ def forces_jerk(pos_m, vel, *, G=1.0, eps=0.0, compensated=True, stream=None):
 
 
 def hermite_step(pos_m, vel, acc, jerk, *, dt, nsteps=1, G=1.0, eps=0.0, acc_valid=False,
-                 compensated=True, stream=None):
+                 compensated=True, tile=-1, jsplit=0, stream=None):
     """``nsteps`` fourth-order Hermite steps in place; acc/jerk receive (a, j) at exit."""
     for t, nm in ((pos_m, "pos_m"), (vel, "vel"), (acc, "acc"), (jerk, "jerk")):
         _check4(t, nm)
-    p = params(LAW_GRAV, G, eps, compensated=compensated, acc_valid=acc_valid)
+    p = params(LAW_GRAV, G, eps, compensated=compensated, acc_valid=acc_valid, tile=tile,
+               jsplit=jsplit)
     check(_lib().nbody_hermite_step(_ptr(pos_m), _ptr(vel), _ptr(acc), _ptr(jerk),
                                     pos_m.shape[0], float(dt), int(nsteps), ctypes.byref(p),
                                     _stream(stream, pos_m.device)), "nbody_hermite_step")
@@ -257,8 +260,10 @@ def forces_batched(systems, pos_m, vel, acc, prm=None, nsteps=0, acc_valid=False
 # Adjoint
 # ---------------------------------------------------------------------------
 def adjoint(pos_m, lam, prm=None, *, law=None, G=1.0, eps=0.0, alpha=1.0, grad_x=None,
-            grad_m=None, grad_types=None, ntypes=4, accumulate=False, stream=None):
-    """One force VJP: returns (grad_x (n,4), grad_m (n,), grad_types (2*ntypes,) or None)."""
+            grad_m=None, grad_types=None, ntypes=4, accumulate=False, tile=-1, jsplit=0,
+            stream=None):
+    """One force VJP: returns (grad_x (n,4), grad_m (n,), grad_types (2*ntypes,) or None).
+    ``tile`` indexes tile table 5 (gravity) or 6 (LJC); -1: tuned/default."""
     _check4(pos_m, "pos_m")
     _check4(lam, "lam")
     law = (LAW_LJC if prm is not None else LAW_GRAV) if law is None else law
@@ -269,7 +274,7 @@ def adjoint(pos_m, lam, prm=None, *, law=None, G=1.0, eps=0.0, alpha=1.0, grad_x
     gt = grad_types
     if gt is None and law == LAW_LJC:
         gt = torch.zeros(2 * ntypes, dtype=torch.float64, device=dev)
-    p = params(law, G, eps, accumulate=accumulate)
+    p = params(law, G, eps, accumulate=accumulate, tile=tile, jsplit=jsplit)
     check(_lib().nbody_adjoint(_ptr(pos_m), _ptr(prm), _ptr(lam), _ptr(gx), _ptr(gm), _ptr(gt),
                                int(ntypes), float(alpha), n, ctypes.byref(p),
                                _stream(stream, dev)), "nbody_adjoint")
@@ -277,12 +282,12 @@ def adjoint(pos_m, lam, prm=None, *, law=None, G=1.0, eps=0.0, alpha=1.0, grad_x
 
 
 def adjoint_leapfrog(xs, lam_x, lam_v, prm=None, *, k, dt, first, law=None, G=1.0, eps=0.0,
-                     grad_m=None, grad_types=None, ntypes=4, stream=None):
+                     grad_m=None, grad_types=None, ntypes=4, tile=-1, jsplit=0, stream=None):
     """Reverse sweep over k stored positions xs ((k or more) * n, 4); updates
     lam_x, lam_v, grad_m, grad_types in place."""
     n = lam_x.shape[0]
     law = (LAW_LJC if prm is not None else LAW_GRAV) if law is None else law
-    p = params(law, G, eps)
+    p = params(law, G, eps, tile=tile, jsplit=jsplit)
     check(_lib().nbody_adjoint_leapfrog(_ptr(xs), _ptr(prm), n, int(k), float(dt), int(first),
                                         _ptr(lam_x), _ptr(lam_v), _ptr(grad_m), _ptr(grad_types),
                                         int(ntypes), ctypes.byref(p),

@@ -1,6 +1,7 @@
 // api_adjoint.cu -- C-ABI entry points of the reverse-mode path: one force VJP
 // (nbody_adjoint) and the reverse leapfrog sweep over stored positions
-// (nbody_adjoint_leapfrog). Kernels in vjp_kernel.cuh.
+// (nbody_adjoint_leapfrog). Kernels in vjp_kernel.cuh and vjp_aux.cuh; tile
+// tables in vjp_tiles.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -9,75 +10,13 @@
 #include <cmath>
 
 #include "api_common.h"
+#include "vjp_aux.cuh"
 #include "vjp_kernel.cuh"
+#include "vjp_tiles.h"
 
 using namespace nbody;
 
 namespace {
-
-struct VjpDesc {
-  int tile_i;
-  int jt;
-  int threads;
-  size_t smem;
-  bool packed;
-  cudaError_t (*launch)(const VjpArgs &, int, cudaStream_t);
-  int (*occupancy)();
-};
-
-template <int LAW, int NT, int I, int SW, int JT, bool PK = false>
-struct VjpImpl {
-  using T = VjpTile<LAW, NT, I, SW, JT, PK>;
-  static cudaError_t launch(const VjpArgs &a, int grid, cudaStream_t s) {
-    auto k = vjp_kernel<LAW, NT, I, SW, JT, PK>;
-    if (T::kSmemBytes > 32 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)T::kSmemBytes);
-      if (e != cudaSuccess) return e;
-    }
-    k<<<grid, T::kThreads, T::kSmemBytes, s>>>(a);
-    return cudaGetLastError();
-  }
-  static int occupancy() {  // cached per device, as for the force tiles
-    static std::atomic<int> cached[kMaxDevicesTile];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesTile) {
-      cudaGetLastError();
-      dev = -1;
-    }
-    if (dev >= 0) {
-      const int c = cached[dev].load(std::memory_order_relaxed);
-      if (c > 0) return c;
-    }
-    int nb = 0;
-    auto k = vjp_kernel<LAW, NT, I, SW, JT, PK>;
-    if (T::kSmemBytes > 32 * 1024)
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, T::kThreads, T::kSmemBytes) !=
-        cudaSuccess) {
-      cudaGetLastError();
-      return 1;
-    }
-    nb = std::max(nb, 1);
-    if (dev >= 0) cached[dev].store(nb, std::memory_order_relaxed);
-    return nb;
-  }
-  static VjpDesc desc() {
-    return VjpDesc{T::kTileI, JT, T::kThreads, T::kSmemBytes, PK, &launch, &occupancy};
-  }
-};
-
-const VjpDesc &vjp_tile(int law, int64_t n) {
-  static const VjpDesc grav_big = VjpImpl<kLawGrav, 256, 2, 1, 256, true>::desc();
-  static const VjpDesc grav_small = VjpImpl<kLawGrav, 128, 2, 4, 256>::desc();
-  static const VjpDesc ljc_big = VjpImpl<kLawLJC, 256, 2, 1, 256>::desc();
-  static const VjpDesc ljc_small = VjpImpl<kLawLJC, 128, 1, 4, 256>::desc();
-  static const VjpDesc gaj_big = VjpImpl<kLawGAJ, 256, 2, 1, 256>::desc();
-  static const VjpDesc gaj_small = VjpImpl<kLawGAJ, 128, 2, 4, 256>::desc();
-  if (law == NBODY_LAW_GRAV) return n >= 8192 ? grav_big : grav_small;
-  if (law == kLawGAJ) return n >= 8192 ? gaj_big : gaj_small;
-  return n >= 8192 ? ljc_big : ljc_small;
-}
 
 struct VjpScratch {
   float4 *part_hi, *part_lo, *u, *jp;
@@ -88,21 +27,43 @@ struct VjpScratch {
   const VjpDesc *d;
 };
 
-int vjp_prepare(int law, int n, int sms, cudaStream_t s, VjpScratch *sc, size_t extra = 0) {
-  const VjpDesc &d = vjp_tile(law, n);
+// Tile table of a VJP-kernel law (gravity VJP, LJC VJP, acceleration + jerk).
+int vjp_table(int law) {
+  if (law == kLawGAJ) return kTableJerk;
+  return law == NBODY_LAW_LJC ? kTableVjpLJC : kTableVjpGrav;
+}
+
+// Tile (params tile >= 0, else the tuned or default row of the law's table)
+// and j-split (params jsplit > 0, else the tuned one, else the split whose
+// items best fill whole waves of resident CTAs), then the scratch layout.
+int vjp_prepare(int law, int n, int tile, int jsplit, int sms, cudaStream_t s, VjpScratch *sc,
+                size_t extra = 0) {
+  const int table = vjp_table(law);
+  int count = 0;
+  const VjpDesc *tiles = vjp_tiles(table, &count);
+  int tj = 0;
+  if (tile < 0) get_config(table, n, &tile, &tj);
+  if (jsplit <= 0) jsplit = tj;
+  if (!tiles || tile < 0 || tile >= count)
+    return set_error_msg(NBODY_EINVAL, "bad tile %d for table %d", tile, table);
+  const VjpDesc &d = tiles[tile];
   const int n_it = (n + d.tile_i - 1) / d.tile_i;
   const int cap = sms * d.occupancy();
   const int max_s = (n + d.jt - 1) / d.jt;
   int S = 1;
-  double best = -1.0;
-  for (int k = 1; k <= 64 && k <= max_s; ++k) {
-    const int len = int(round_up(size_t((n + k - 1) / k), size_t(d.jt)));
-    const int kk = (n + len - 1) / len;
-    const double waves = double(n_it) * kk / cap;
-    const double score = waves / std::ceil(waves) - 0.002 * kk;
-    if (score > best + 1e-12) {
-      best = score;
-      S = kk;
+  if (jsplit > 0) {
+    S = std::min(jsplit, max_s);
+  } else {
+    double best = -1.0;
+    for (int k = 1; k <= 64 && k <= max_s; ++k) {
+      const int len = int(round_up(size_t((n + k - 1) / k), size_t(d.jt)));
+      const int kk = (n + len - 1) / len;
+      const double waves = double(n_it) * kk / cap;
+      const double score = waves / std::ceil(waves) - 0.002 * kk;
+      if (score > best + 1e-12) {
+        best = score;
+        S = kk;
+      }
     }
   }
   const int len = int(round_up(size_t((n + S - 1) / S), size_t(d.jt)));
@@ -325,7 +286,7 @@ int nbody_adjoint(const void *pos_m, const void *prm, const void *lam, void *gra
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const nbody_params p = *params;
   VjpScratch sc{};
-  NB_TRY(vjp_prepare(p.law, int(n), sms, s, &sc));
+  NB_TRY(vjp_prepare(p.law, int(n), p.tile, p.jsplit, sms, s, &sc));
   const int acc = (p.flags & NBODY_ACCUMULATE) ? 1 : 0;
   if (grad_types && !acc && p.law == NBODY_LAW_LJC) {
     zero_doubles_kernel<<<1, 32, 0, s>>>(grad_types, 2 * ntypes);
@@ -355,7 +316,7 @@ int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const nbody_params p = *params;
   VjpScratch sc{};
-  NB_TRY(vjp_prepare(p.law, int(n), sms, s, &sc));
+  NB_TRY(vjp_prepare(p.law, int(n), p.tile, p.jsplit, sms, s, &sc));
   float4 *lx = static_cast<float4 *>(lam_x);
   float4 *lv = static_cast<float4 *>(lam_v);
   const float4 *X = static_cast<const float4 *>(xs);
@@ -387,7 +348,7 @@ int nbody_forces_jerk(const void *pos_m, const void *vel, void *acc, void *jerk,
   NB_TRY(check_dev_ptrs({pos_m, vel, acc, jerk}));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   VjpScratch sc{};
-  NB_TRY(vjp_prepare(kLawGAJ, int(n), sms, s, &sc, 0));
+  NB_TRY(vjp_prepare(kLawGAJ, int(n), params->tile, params->jsplit, sms, s, &sc, 0));
   return gaj_eval(static_cast<const float4 *>(pos_m), static_cast<const float4 *>(vel),
                   static_cast<float4 *>(acc), static_cast<float4 *>(jerk), int(n), *params, sc, s);
 }
@@ -411,7 +372,7 @@ int nbody_hermite_step(void *pos_m, void *vel, void *acc, void *jerk, int64_t n,
   // scratch: GAJ partials, then predicted (x, v) and the new (a, j)
   VjpScratch sc{};
   const size_t q = round_up(size_t(n) * sizeof(float4), 256);
-  NB_TRY(vjp_prepare(kLawGAJ, int(n), sms, s, &sc, 4 * q));
+  NB_TRY(vjp_prepare(kLawGAJ, int(n), params->tile, params->jsplit, sms, s, &sc, 4 * q));
   float4 *xp = reinterpret_cast<float4 *>(sc.extra);
   float4 *vp = reinterpret_cast<float4 *>(sc.extra + q);
   float4 *a1 = reinterpret_cast<float4 *>(sc.extra + 2 * q);

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "api_common.h"
+#include "vjp_tiles.h"
 
 namespace nbody {
 
@@ -253,6 +254,7 @@ int timing_read(int which, int64_t *launches, double *total_ms) {
 }
 
 const TileDesc *tiles_for(int law, int *count) {
+  if (law >= kTableVjpGrav) return vjp_tile_descs(law, count);
   if (law == NBODY_LAW_GRAV) return grav_tiles(count);
   if (law == NBODY_LAW_LJC) return ljc_tiles(count);
   if (law == NBODY_LAW_LJC_LINEAR) return ljclin_tiles(count);
@@ -283,6 +285,7 @@ static int log2_floor(int64_t n) {
 // inside the warp for small N (where there are too few targets to fill the GPU).
 static int default_tile(int law, int64_t n) {
   if (law == kTableBatched) return 0;
+  if (law >= kTableVjpGrav) return n >= 8192 ? 0 : 1;
   if (law == kTableGravFixed) return n >= 4096 ? 0 : (n >= 1024 ? 2 : 3);
   if (law == NBODY_LAW_LJC_LINEAR) return n >= 16384 ? 3 : (n >= 1024 ? 1 : 2);
   if (law == NBODY_LAW_GRAV) {
@@ -316,6 +319,8 @@ int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out) {
 }
 
 int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms, Plan1 *out) {
+  if (law < 0 || law >= kTableVjpGrav)
+    return set_error_msg(NBODY_EINVAL, "tile table %d is not a force table", law);
   int count = 0;
   const TileDesc *tiles = tiles_for(law, &count);
   int tj = 0;

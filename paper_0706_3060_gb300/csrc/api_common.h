@@ -54,10 +54,15 @@ int error_word(int **out);
 int sync_and_check(cudaStream_t s);
 
 // Tile tables: 0 gravity, 1 LJC, 2 LJC linear, 3 the batched mixed-law kernel,
-// 4 gravity with fixed-point accumulation.
+// 4 gravity with fixed-point accumulation, 5 the gravity VJP, 6 the LJC VJP,
+// 7 acceleration + jerk. Tables 5-7 describe kernels of vjp_kernel.cuh (their
+// TileDesc has no force launcher; vjp_tiles() gives the launchers).
 constexpr int kTableBatched = 3;
 constexpr int kTableGravFixed = 4;
-constexpr int kTables = 5;
+constexpr int kTableVjpGrav = 5;
+constexpr int kTableVjpLJC = 6;
+constexpr int kTableJerk = 7;
+constexpr int kTables = 8;
 const TileDesc *tiles_for(int law, int *count);
 // Decide (tile, slices, slice_len) for a single-system evaluation.
 struct Plan1 {

@@ -1,0 +1,211 @@
+// vjp_aux.cuh -- the O(N) kernels of the reverse sweep and of the jerk path
+// (finalize of the per-slice partials, per-type reduction, layout kernels).
+// Non-template kernels: included by exactly one translation unit (api_adjoint.cu).
+#pragma once
+
+#include "vjp_kernel.cuh"
+
+namespace nbody {
+
+// ---- O(N) kernels of the reverse sweep -------------------------------------------
+struct VjpFinalizeArgs {
+  const float4 *part_hi;
+  const float4 *part_lo;
+  long long stride;
+  long long bstride;
+  int slices;
+  int n;
+  int law;
+  float G;
+  float alpha;        // weight of this VJP (h or dt in the reverse sweep)
+  const float4 *pos;
+  const float4 *prm;
+  const float4 *lam;  // gravity: lam; LJC: u
+  float4 *grad_x;     // += alpha g (or = when !accumulate)
+  float *grad_m;      // may be null
+  int accumulate;
+  double *type_part;  // [gridDim.x][8] or null
+  float4 *lam_v;      // if non-null: lam_v += dt_next * grad_x afterwards
+  float dt_next;
+};
+
+__global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs f) {
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  double tv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (i < f.n) {
+    float4 hA = f.part_hi[i], oA = f.part_lo[i];
+    float4 hB = make_float4(0.f, 0.f, 0.f, 0.f), oB = hB;
+    const bool lj = (f.law == kLawLJC);
+    if (lj) {
+      hB = f.part_hi[f.bstride + i];
+      oB = f.part_lo[f.bstride + i];
+    }
+    for (int k = 1; k < f.slices; ++k) {
+      const long long o = (long long)k * f.stride + i;
+      float4 h = f.part_hi[o], l = f.part_lo[o];
+      comp_add(hA.x, oA.x, h.x);
+      comp_add(hA.y, oA.y, h.y);
+      comp_add(hA.z, oA.z, h.z);
+      comp_add(hA.w, oA.w, h.w);
+      oA.x += l.x;
+      oA.y += l.y;
+      oA.z += l.z;
+      oA.w += l.w;
+      if (lj) {
+        h = f.part_hi[f.bstride + o];
+        l = f.part_lo[f.bstride + o];
+        comp_add(hB.x, oB.x, h.x);
+        comp_add(hB.y, oB.y, h.y);
+        comp_add(hB.z, oB.z, h.z);
+        comp_add(hB.w, oB.w, h.w);
+        oB.x += l.x;
+        oB.y += l.y;
+        oB.z += l.z;
+        oB.w += l.w;
+      }
+    }
+    const float ax = hA.x + oA.x, ay = hA.y + oA.y, az = hA.z + oA.z, aw = hA.w + oA.w;
+    float gx, gy, gz, gm;
+    if (!lj) {
+      gx = f.G * ax;
+      gy = f.G * ay;
+      gz = f.G * az;
+      gm = -f.G * aw;
+    } else {
+      const float4 x = f.pos[i];
+      const float4 u = f.lam[i];
+      const float bx = hB.x + oB.x, by = hB.y + oB.y, bz = hB.z + oB.z, bw = hB.w + oB.w;
+      gx = ax;
+      gy = ay;
+      gz = az;
+      gm = (u.x * bx + u.y * by + u.z * bz) / x.w;
+      const float4 q = f.prm[i];
+      const int t = int(q.w);
+      if (f.type_part && t >= 0 && t < 4) {
+        const double e2 = double(q.z) * double(q.z);  // 24 eps_k
+        tv[t] = -3.0 * double(aw) * f.alpha;
+        tv[4 + t] = -12.0 / e2 * double(bw) * f.alpha;
+      }
+    }
+    float4 gxo = f.accumulate ? f.grad_x[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    gxo.x = fmaf(f.alpha, gx, gxo.x);
+    gxo.y = fmaf(f.alpha, gy, gxo.y);
+    gxo.z = fmaf(f.alpha, gz, gxo.z);
+    gxo.w = 0.0f;
+    f.grad_x[i] = gxo;
+    if (f.grad_m) {
+      const float gmo = f.accumulate ? f.grad_m[i] : 0.0f;
+      f.grad_m[i] = fmaf(f.alpha, gm, gmo);
+    }
+    if (f.lam_v) {
+      float4 v = f.lam_v[i];
+      v.x = fmaf(f.dt_next, gxo.x, v.x);
+      v.y = fmaf(f.dt_next, gxo.y, v.y);
+      v.z = fmaf(f.dt_next, gxo.z, v.z);
+      f.lam_v[i] = v;
+    }
+  }
+  if (f.type_part) {
+    // fixed-order block sum of the 8 per-type fields
+    __shared__ double red[8][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) tv[k] += __shfl_down_sync(0xffffffffu, tv[k], off);
+      if (lane == 0) red[warp][k] = tv[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+      f.type_part[(size_t)blockIdx.x * 8 + threadIdx.x] = s;
+    }
+  }
+}
+
+// GAJ: fixed-order compensated sum of the per-slice partials of A (acceleration)
+// and B (jerk), scaled by G.
+__global__ void __launch_bounds__(256) gaj_finalize_kernel(const float4 *part_hi,
+                                                           const float4 *part_lo,
+                                                           long long stride, long long bstride,
+                                                           int slices, int n, float G,
+                                                           float4 *acc, float4 *jerk) {
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  if (i >= n) return;
+  float4 hA = part_hi[i], oA = part_lo[i];
+  float4 hB = part_hi[bstride + i], oB = part_lo[bstride + i];
+  for (int k = 1; k < slices; ++k) {
+    const long long o = (long long)k * stride + i;
+    const float4 a = part_hi[o], la = part_lo[o], b = part_hi[bstride + o],
+                 lb = part_lo[bstride + o];
+    comp_add(hA.x, oA.x, a.x);
+    comp_add(hA.y, oA.y, a.y);
+    comp_add(hA.z, oA.z, a.z);
+    comp_add(hB.x, oB.x, b.x);
+    comp_add(hB.y, oB.y, b.y);
+    comp_add(hB.z, oB.z, b.z);
+    oA.x += la.x;
+    oA.y += la.y;
+    oA.z += la.z;
+    oB.x += lb.x;
+    oB.y += lb.y;
+    oB.z += lb.z;
+  }
+  acc[i] = make_float4(G * (hA.x + oA.x), G * (hA.y + oA.y), G * (hA.z + oA.z), 0.0f);
+  jerk[i] = make_float4(G * (hB.x + oB.x), G * (hB.y + oB.y), G * (hB.z + oB.z), 0.0f);
+}
+
+// Sum per-block type partials in order and add them into out[0..2*ntypes).
+__global__ void type_reduce_kernel(const double *part, int nblk, int ntypes, double *out) {
+  const int k = threadIdx.x;
+  if (k >= 8) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(size_t)b * 8 + k];
+  const int t = k & 3, which = k >> 2;  // 0: sigma, 1: eps
+  if (t < ntypes) out[which * ntypes + t] += s;
+}
+
+// Packed gravity VJP sources: per pair (x0 x1 y0 y1)(z0 z1 m0 m1)(lx0 lx1 ly0 ly1)
+// (lz0 lz1 0 0); an odd count is padded with a massless particle far away.
+__global__ void interleave_vjp_pairs_kernel(const float4 *pos, const float4 *lam, float4 *jp,
+                                            int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * p >= n) return;
+  const bool two = 2 * p + 1 < n;
+  const float4 a = pos[2 * p], la = lam[2 * p];
+  const float4 b = two ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+  const float4 lb = two ? lam[2 * p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+  jp[4 * p] = make_float4(a.x, b.x, a.y, b.y);
+  jp[4 * p + 1] = make_float4(a.z, b.z, a.w, b.w);
+  jp[4 * p + 2] = make_float4(la.x, lb.x, la.y, lb.y);
+  jp[4 * p + 3] = make_float4(la.z, lb.z, 0.f, 0.f);
+}
+
+// u = lam / m (LJC sources are weighted by 1 / m_j).
+__global__ void lam_over_m_kernel(const float4 *lam, const float4 *pos, float4 *u, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 l = lam[i];
+  const float inv = 1.0f / pos[i].w;
+  u[i] = make_float4(l.x * inv, l.y * inv, l.z * inv, 0.0f);
+}
+
+// y += alpha * x on float4 xyz.
+__global__ void axpy4_kernel(float alpha, const float4 *x, float4 *y, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 a = x[i];
+  float4 b = y[i];
+  b.x = fmaf(alpha, a.x, b.x);
+  b.y = fmaf(alpha, a.y, b.y);
+  b.z = fmaf(alpha, a.z, b.z);
+  y[i] = b;
+}
+
+__global__ void zero_doubles_kernel(double *p, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = 0.0;
+}
+
+}  // namespace nbody

@@ -4,7 +4,7 @@
 //
 // Gravity, target k, source j, d = x_j - x_k, s^2 = |d|^2 + eps^2, y = 1/s,
 // w = m_k lam_j - m_j lam_k:
-//   g_k  = G sum_j [ y^3 w - 3 y^5 (d.w) d ]        (T = I/s^3 - 3 d d^T / s^5)
+//   g_k  = G sum_j y^3 [ w - 3 y^2 (d.w) d ]        (T = I/s^3 - 3 d d^T / s^5)
 //   gm_k = -G sum_j (lam_j . d) y^3                   (d/dm_k of sum_i lam_i . a_i)
 // LJC with u = lam / m, w = u_k - u_j, y = 1/r, sigma = s~k + s~j,
 // u6 = (sigma y)^6, phi = q~q~ y^3 + e~e~ y^2 (2 u6^2 - u6) and
@@ -65,10 +65,10 @@ __device__ __forceinline__ void grav_vjp_pair(const float4 pj, const float4 lj, 
   const float wy = fmaf(mk, lj.y, -(mj * lky));
   const float wz = fmaf(mk, lj.z, -(mj * lkz));
   const float dw = fmaf(dx, wx, fmaf(dy, wy, dz * wz));
-  const float c = (-3.0f * dw) * (y3 * y2);
-  A.x = fmaf(c, dx, fmaf(y3, wx, A.x));
-  A.y = fmaf(c, dy, fmaf(y3, wy, A.y));
-  A.z = fmaf(c, dz, fmaf(y3, wz, A.z));
+  const float c = dw * (-3.0f * y2);
+  A.x = fmaf(y3, fmaf(c, dx, wx), A.x);
+  A.y = fmaf(y3, fmaf(c, dy, wy), A.y);
+  A.z = fmaf(y3, fmaf(c, dz, wz), A.z);
   const float ld = fmaf(lj.x, dx, fmaf(lj.y, dy, lj.z * dz));
   A.w = fmaf(ld, y3, A.w);
 }
@@ -94,10 +94,10 @@ __device__ __forceinline__ void grav_vjp_pair2(float2 X, float2 Y, float2 Z, flo
   const float2 wy = __ffma2_rn(mk, LY, __fmul2_rn(nmj, lky));
   const float2 wz = __ffma2_rn(mk, LZ, __fmul2_rn(nmj, lkz));
   const float2 dw = __ffma2_rn(dx, wx, __ffma2_rn(dy, wy, __fmul2_rn(dz, wz)));
-  const float2 c = __fmul2_rn(__fmul2_rn(dw, make_float2(-3.0f, -3.0f)), __fmul2_rn(y3, y2));
-  ax = __ffma2_rn(c, dx, __ffma2_rn(y3, wx, ax));
-  ay = __ffma2_rn(c, dy, __ffma2_rn(y3, wy, ay));
-  az = __ffma2_rn(c, dz, __ffma2_rn(y3, wz, az));
+  const float2 c = __fmul2_rn(dw, __fmul2_rn(y2, make_float2(-3.0f, -3.0f)));
+  ax = __ffma2_rn(y3, __ffma2_rn(c, dx, wx), ax);
+  ay = __ffma2_rn(y3, __ffma2_rn(c, dy, wy), ay);
+  az = __ffma2_rn(y3, __ffma2_rn(c, dz, wz), az);
   const float2 ld = __ffma2_rn(LX, dx, __ffma2_rn(LY, dy, __fmul2_rn(LZ, dz)));
   aw = __ffma2_rn(ld, y3, aw);
 }
@@ -216,7 +216,7 @@ __device__ __forceinline__ void shfl_combine(float4 &hi, float4 &lo, int off) {
   lo.w = __fadd_rn(__fadd_rn(lo.w, ol.w), e);
 }
 
-template <int LAW, int NT, int I, int SW, int JT, bool PK = false>
+template <int LAW, int NT, int I, int SW, int JT, bool PK = false, int PU = 2>
 __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
   using T = VjpTile<LAW, NT, I, SW, JT, PK>;
   static_assert(!PK || (LAW == kLawGrav && SW == 1), "packed VJP: gravity, one j-lane");
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
         float2 ax[PK ? I : 1], ay[PK ? I : 1], az[PK ? I : 1], aw[PK ? I : 1];
 #pragma unroll
         for (int r = 0; r < I; ++r) ax[r] = ay[r] = az[r] = aw[r] = make_float2(0.f, 0.f);
-#pragma unroll 2
+#pragma unroll PU
         for (int pp = 0; pp < npairs; ++pp) {
           const float4 P0 = pk[4 * pp], P1 = pk[4 * pp + 1];
           const float4 L0 = pk[4 * pp + 2], L1 = pk[4 * pp + 3];
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
       }
     } else if (GJ) {
       if (!masked) {
-#pragma unroll 2
+#pragma unroll PU
         for (int jj = jl; jj < len; jj += SW) {
           const float4 pj = sp[jj];
           const float4 vj = sl[jj];
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
       }
     } else if (!LJ) {
       if (!masked) {
-#pragma unroll 2
+#pragma unroll PU
         for (int jj = jl; jj < len; jj += SW) {
           const float4 pj = sp[jj];
           const float4 lj = sl[jj];
@@ -472,207 +472,6 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
       }
     }
   }
-}
-
-// ---- O(N) kernels of the reverse sweep -------------------------------------------
-struct VjpFinalizeArgs {
-  const float4 *part_hi;
-  const float4 *part_lo;
-  long long stride;
-  long long bstride;
-  int slices;
-  int n;
-  int law;
-  float G;
-  float alpha;        // weight of this VJP (h or dt in the reverse sweep)
-  const float4 *pos;
-  const float4 *prm;
-  const float4 *lam;  // gravity: lam; LJC: u
-  float4 *grad_x;     // += alpha g (or = when !accumulate)
-  float *grad_m;      // may be null
-  int accumulate;
-  double *type_part;  // [gridDim.x][8] or null
-  float4 *lam_v;      // if non-null: lam_v += dt_next * grad_x afterwards
-  float dt_next;
-};
-
-__global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs f) {
-  const int i = blockIdx.x * 256 + threadIdx.x;
-  double tv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  if (i < f.n) {
-    float4 hA = f.part_hi[i], oA = f.part_lo[i];
-    float4 hB = make_float4(0.f, 0.f, 0.f, 0.f), oB = hB;
-    const bool lj = (f.law == kLawLJC);
-    if (lj) {
-      hB = f.part_hi[f.bstride + i];
-      oB = f.part_lo[f.bstride + i];
-    }
-    for (int k = 1; k < f.slices; ++k) {
-      const long long o = (long long)k * f.stride + i;
-      float4 h = f.part_hi[o], l = f.part_lo[o];
-      comp_add(hA.x, oA.x, h.x);
-      comp_add(hA.y, oA.y, h.y);
-      comp_add(hA.z, oA.z, h.z);
-      comp_add(hA.w, oA.w, h.w);
-      oA.x += l.x;
-      oA.y += l.y;
-      oA.z += l.z;
-      oA.w += l.w;
-      if (lj) {
-        h = f.part_hi[f.bstride + o];
-        l = f.part_lo[f.bstride + o];
-        comp_add(hB.x, oB.x, h.x);
-        comp_add(hB.y, oB.y, h.y);
-        comp_add(hB.z, oB.z, h.z);
-        comp_add(hB.w, oB.w, h.w);
-        oB.x += l.x;
-        oB.y += l.y;
-        oB.z += l.z;
-        oB.w += l.w;
-      }
-    }
-    const float ax = hA.x + oA.x, ay = hA.y + oA.y, az = hA.z + oA.z, aw = hA.w + oA.w;
-    float gx, gy, gz, gm;
-    if (!lj) {
-      gx = f.G * ax;
-      gy = f.G * ay;
-      gz = f.G * az;
-      gm = -f.G * aw;
-    } else {
-      const float4 x = f.pos[i];
-      const float4 u = f.lam[i];
-      const float bx = hB.x + oB.x, by = hB.y + oB.y, bz = hB.z + oB.z, bw = hB.w + oB.w;
-      gx = ax;
-      gy = ay;
-      gz = az;
-      gm = (u.x * bx + u.y * by + u.z * bz) / x.w;
-      const float4 q = f.prm[i];
-      const int t = int(q.w);
-      if (f.type_part && t >= 0 && t < 4) {
-        const double e2 = double(q.z) * double(q.z);  // 24 eps_k
-        tv[t] = -3.0 * double(aw) * f.alpha;
-        tv[4 + t] = -12.0 / e2 * double(bw) * f.alpha;
-      }
-    }
-    float4 gxo = f.accumulate ? f.grad_x[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    gxo.x = fmaf(f.alpha, gx, gxo.x);
-    gxo.y = fmaf(f.alpha, gy, gxo.y);
-    gxo.z = fmaf(f.alpha, gz, gxo.z);
-    gxo.w = 0.0f;
-    f.grad_x[i] = gxo;
-    if (f.grad_m) {
-      const float gmo = f.accumulate ? f.grad_m[i] : 0.0f;
-      f.grad_m[i] = fmaf(f.alpha, gm, gmo);
-    }
-    if (f.lam_v) {
-      float4 v = f.lam_v[i];
-      v.x = fmaf(f.dt_next, gxo.x, v.x);
-      v.y = fmaf(f.dt_next, gxo.y, v.y);
-      v.z = fmaf(f.dt_next, gxo.z, v.z);
-      f.lam_v[i] = v;
-    }
-  }
-  if (f.type_part) {
-    // fixed-order block sum of the 8 per-type fields
-    __shared__ double red[8][8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-#pragma unroll
-      for (int off = 16; off >= 1; off >>= 1) tv[k] += __shfl_down_sync(0xffffffffu, tv[k], off);
-      if (lane == 0) red[warp][k] = tv[k];
-    }
-    __syncthreads();
-    if (threadIdx.x < 8) {
-      double s = 0.0;
-      for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
-      f.type_part[(size_t)blockIdx.x * 8 + threadIdx.x] = s;
-    }
-  }
-}
-
-// GAJ: fixed-order compensated sum of the per-slice partials of A (acceleration)
-// and B (jerk), scaled by G.
-__global__ void __launch_bounds__(256) gaj_finalize_kernel(const float4 *part_hi,
-                                                           const float4 *part_lo,
-                                                           long long stride, long long bstride,
-                                                           int slices, int n, float G,
-                                                           float4 *acc, float4 *jerk) {
-  const int i = blockIdx.x * 256 + threadIdx.x;
-  if (i >= n) return;
-  float4 hA = part_hi[i], oA = part_lo[i];
-  float4 hB = part_hi[bstride + i], oB = part_lo[bstride + i];
-  for (int k = 1; k < slices; ++k) {
-    const long long o = (long long)k * stride + i;
-    const float4 a = part_hi[o], la = part_lo[o], b = part_hi[bstride + o],
-                 lb = part_lo[bstride + o];
-    comp_add(hA.x, oA.x, a.x);
-    comp_add(hA.y, oA.y, a.y);
-    comp_add(hA.z, oA.z, a.z);
-    comp_add(hB.x, oB.x, b.x);
-    comp_add(hB.y, oB.y, b.y);
-    comp_add(hB.z, oB.z, b.z);
-    oA.x += la.x;
-    oA.y += la.y;
-    oA.z += la.z;
-    oB.x += lb.x;
-    oB.y += lb.y;
-    oB.z += lb.z;
-  }
-  acc[i] = make_float4(G * (hA.x + oA.x), G * (hA.y + oA.y), G * (hA.z + oA.z), 0.0f);
-  jerk[i] = make_float4(G * (hB.x + oB.x), G * (hB.y + oB.y), G * (hB.z + oB.z), 0.0f);
-}
-
-// Sum per-block type partials in order and add them into out[0..2*ntypes).
-__global__ void type_reduce_kernel(const double *part, int nblk, int ntypes, double *out) {
-  const int k = threadIdx.x;
-  if (k >= 8) return;
-  double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += part[(size_t)b * 8 + k];
-  const int t = k & 3, which = k >> 2;  // 0: sigma, 1: eps
-  if (t < ntypes) out[which * ntypes + t] += s;
-}
-
-// Packed gravity VJP sources: per pair (x0 x1 y0 y1)(z0 z1 m0 m1)(lx0 lx1 ly0 ly1)
-// (lz0 lz1 0 0); an odd count is padded with a massless particle far away.
-__global__ void interleave_vjp_pairs_kernel(const float4 *pos, const float4 *lam, float4 *jp,
-                                            int n) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (2 * p >= n) return;
-  const bool two = 2 * p + 1 < n;
-  const float4 a = pos[2 * p], la = lam[2 * p];
-  const float4 b = two ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
-  const float4 lb = two ? lam[2 * p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-  jp[4 * p] = make_float4(a.x, b.x, a.y, b.y);
-  jp[4 * p + 1] = make_float4(a.z, b.z, a.w, b.w);
-  jp[4 * p + 2] = make_float4(la.x, lb.x, la.y, lb.y);
-  jp[4 * p + 3] = make_float4(la.z, lb.z, 0.f, 0.f);
-}
-
-// u = lam / m (LJC sources are weighted by 1 / m_j).
-__global__ void lam_over_m_kernel(const float4 *lam, const float4 *pos, float4 *u, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float4 l = lam[i];
-  const float inv = 1.0f / pos[i].w;
-  u[i] = make_float4(l.x * inv, l.y * inv, l.z * inv, 0.0f);
-}
-
-// y += alpha * x on float4 xyz.
-__global__ void axpy4_kernel(float alpha, const float4 *x, float4 *y, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float4 a = x[i];
-  float4 b = y[i];
-  b.x = fmaf(alpha, a.x, b.x);
-  b.y = fmaf(alpha, a.y, b.y);
-  b.z = fmaf(alpha, a.z, b.z);
-  y[i] = b;
-}
-
-__global__ void zero_doubles_kernel(double *p, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = 0.0;
 }
 
 }  // namespace nbody

@@ -1,0 +1,126 @@
+// vjp_tiles.cu -- the compiled VJP (gravity, LJC) and acceleration + jerk tile
+// configurations: threads, targets per thread, j-lanes per warp, j-tile length,
+// packed f32x2 sources, unroll of the pair loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "api_common.h"
+#include "vjp_tiles.h"
+
+namespace nbody {
+namespace {
+
+template <int LAW, int NT, int I, int SW, int JT, bool PK = false, int PU = 2>
+struct VjpImpl {
+  using T = VjpTile<LAW, NT, I, SW, JT, PK>;
+  static cudaError_t launch(const VjpArgs &a, int grid, cudaStream_t s) {
+    auto k = vjp_kernel<LAW, NT, I, SW, JT, PK, PU>;
+    if (T::kSmemBytes > 32 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)T::kSmemBytes);
+      if (e != cudaSuccess) return e;
+    }
+    k<<<grid, T::kThreads, T::kSmemBytes, s>>>(a);
+    return cudaGetLastError();
+  }
+  static int occupancy() {  // cached per device, as for the force tiles
+    static std::atomic<int> cached[kMaxDevicesTile];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesTile) {
+      cudaGetLastError();
+      dev = -1;
+    }
+    if (dev >= 0) {
+      const int c = cached[dev].load(std::memory_order_relaxed);
+      if (c > 0) return c;
+    }
+    int nb = 0;
+    auto k = vjp_kernel<LAW, NT, I, SW, JT, PK, PU>;
+    if (T::kSmemBytes > 32 * 1024)
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, T::kThreads, T::kSmemBytes) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return 1;
+    }
+    nb = std::max(nb, 1);
+    if (dev >= 0) cached[dev].store(nb, std::memory_order_relaxed);
+    return nb;
+  }
+  static VjpDesc desc() {
+    return VjpDesc{T::kTileI, JT, T::kThreads, T::kSmemBytes, PK, &launch, &occupancy};
+  }
+  static TileDesc tile() {
+    return TileDesc{LAW, NT, I, SW, JT, T::kTileI, T::kThreads, T::kSmemBytes, PK, false,
+                    nullptr, &occupancy};
+  }
+};
+
+// Rows: (law, consumer threads, targets per thread, j-lanes, j-tile, packed,
+// unroll). Row 0 is the default for large N, row 1 for small N (below 8192).
+#define NB_VJP_GRAV_ROWS(X)                                         \
+  X(kLawGrav, 256, 2, 1, 256, true, 2)                              \
+  X(kLawGrav, 128, 2, 4, 256, false, 2)                             \
+  X(kLawGrav, 128, 2, 1, 512, true, 4)                              \
+  X(kLawGrav, 256, 2, 1, 512, true, 2)                              \
+  X(kLawGrav, 128, 2, 1, 256, true, 2)                              \
+  X(kLawGrav, 256, 1, 1, 256, true, 4)                              \
+  X(kLawGrav, 128, 4, 1, 256, true, 1)                              \
+  X(kLawGrav, 128, 1, 8, 256, false, 2)
+#define NB_VJP_LJC_ROWS(X)                                          \
+  X(kLawLJC, 256, 2, 1, 256, false, 2)                              \
+  X(kLawLJC, 128, 1, 4, 256, false, 2)                              \
+  X(kLawLJC, 128, 2, 1, 256, false, 2)                              \
+  X(kLawLJC, 256, 1, 1, 256, false, 2)                              \
+  X(kLawLJC, 128, 2, 2, 256, false, 2)
+#define NB_VJP_GAJ_ROWS(X)                                          \
+  X(kLawGAJ, 256, 2, 1, 256, false, 2)                              \
+  X(kLawGAJ, 128, 2, 4, 256, false, 2)                              \
+  X(kLawGAJ, 128, 2, 1, 256, false, 2)                              \
+  X(kLawGAJ, 256, 1, 1, 256, false, 2)                              \
+  X(kLawGAJ, 128, 2, 1, 512, false, 4)
+
+#define NB_VJP_DESC(L, NT, I, SW, JT, PK, PU) VjpImpl<L, NT, I, SW, JT, PK, PU>::desc(),
+#define NB_VJP_TILE(L, NT, I, SW, JT, PK, PU) VjpImpl<L, NT, I, SW, JT, PK, PU>::tile(),
+
+const VjpDesc kGravDesc[] = {NB_VJP_GRAV_ROWS(NB_VJP_DESC)};
+const VjpDesc kLjcDesc[] = {NB_VJP_LJC_ROWS(NB_VJP_DESC)};
+const VjpDesc kGajDesc[] = {NB_VJP_GAJ_ROWS(NB_VJP_DESC)};
+const TileDesc kGravTile[] = {NB_VJP_GRAV_ROWS(NB_VJP_TILE)};
+const TileDesc kLjcTile[] = {NB_VJP_LJC_ROWS(NB_VJP_TILE)};
+const TileDesc kGajTile[] = {NB_VJP_GAJ_ROWS(NB_VJP_TILE)};
+
+#undef NB_VJP_DESC
+#undef NB_VJP_TILE
+#undef NB_VJP_GRAV_ROWS
+#undef NB_VJP_LJC_ROWS
+#undef NB_VJP_GAJ_ROWS
+
+template <class T, size_t N>
+constexpr int count_of(const T (&)[N]) {
+  return int(N);
+}
+
+}  // namespace
+
+const VjpDesc *vjp_tiles(int table, int *count) {
+  switch (table) {
+    case kTableVjpGrav: *count = count_of(kGravDesc); return kGravDesc;
+    case kTableVjpLJC: *count = count_of(kLjcDesc); return kLjcDesc;
+    case kTableJerk: *count = count_of(kGajDesc); return kGajDesc;
+    default: *count = 0; return nullptr;
+  }
+}
+
+const TileDesc *vjp_tile_descs(int table, int *count) {
+  switch (table) {
+    case kTableVjpGrav: *count = count_of(kGravTile); return kGravTile;
+    case kTableVjpLJC: *count = count_of(kLjcTile); return kLjcTile;
+    case kTableJerk: *count = count_of(kGajTile); return kGajTile;
+    default: *count = 0; return nullptr;
+  }
+}
+
+}  // namespace nbody

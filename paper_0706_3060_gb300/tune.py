@@ -18,7 +18,8 @@ import os
 import numpy as np
 
 from . import api
-from ._lib import LAW_GRAV, LAW_LJC, LAW_LJC_LINEAR, TABLE_BATCHED
+from ._lib import (LAW_GRAV, LAW_LJC, LAW_LJC_LINEAR, TABLE_BATCHED, TABLE_JERK,
+                   TABLE_VJP_GRAV, TABLE_VJP_LJC)
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
@@ -64,11 +65,44 @@ def time_config(torch, law, pos, prm, tile, jsplit, reps=5):
     return float(np.median(ts))
 
 
+def _vjp_timer(torch, table):
+    """Timing function of one VJP (tables 5, 6) or acceleration + jerk (table 7)
+    evaluation, with the same signature as time_config."""
+    def run(torch_, law, pos, prm, tile, jsplit, reps=5):
+        n = pos.shape[0]
+        lam = torch.randn((n, 4), device=pos.device)
+        if table == TABLE_JERK:
+            fn = lambda: api.forces_jerk(pos, lam, eps=0.01, tile=tile, jsplit=jsplit)  # noqa: E731
+        else:
+            gx = torch.zeros_like(pos)
+            gm = torch.zeros(n, device=pos.device)
+            fn = lambda: api.adjoint(pos, lam, prm, eps=0.01, grad_x=gx, grad_m=gm,  # noqa: E731
+                                     tile=tile, jsplit=jsplit)
+        fn()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+    return run
+
+
 def tune(law: int, sizes, jsplits=(0, 1, 2, 4, 8, 16, 32), reps=5, verbose=True):
+    """Time every tile x j-split of tile table `law` (0-2 force laws, 5-7 the VJP
+    and jerk tables) at each size and install the fastest per size bucket."""
     import torch
+    timer = time_config
+    in_law = law
+    if law in (TABLE_VJP_GRAV, TABLE_VJP_LJC, TABLE_JERK):
+        timer = _vjp_timer(torch, law)
+        in_law = LAW_LJC if law == TABLE_VJP_LJC else LAW_GRAV
     table = {}
     for n in sizes:
-        pos, prm = _inputs(torch, law, n)
+        pos, prm = _inputs(torch, in_law, n)
         results = []
         for tile in range(api.tile_count(law)):
             info = api.tile_info(law, tile)
@@ -78,7 +112,7 @@ def tune(law: int, sizes, jsplits=(0, 1, 2, 4, 8, 16, 32), reps=5, verbose=True)
                     continue
                 if js == 0 and tile_i > 4 * n:
                     continue
-                ms = time_config(torch, law, pos, prm, tile, js, reps)
+                ms = timer(torch, law, pos, prm, tile, js, reps)
                 results.append((ms, tile, js))
                 if verbose:
                     print(f"law={law} n={n} tile={tile} jsplit={js}: {ms:.4f} ms "
@@ -169,7 +203,8 @@ def load_cache(path: str = CACHE) -> int:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--law", choices=["grav", "ljc", "ljclin", "batched"], default="grav")
+    ap.add_argument("--law", choices=["grav", "ljc", "ljclin", "batched", "vjp", "vjpljc",
+                                      "jerk"], default="grav")
     ap.add_argument("--n", type=int, nargs="+", default=[1024, 4096, 16384, 65536, 262144])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--save", action="store_true")
@@ -180,7 +215,8 @@ def main():
         if a.save:
             save_cache(TABLE_BATCHED, table)
         return
-    law = {"grav": LAW_GRAV, "ljc": LAW_LJC, "ljclin": LAW_LJC_LINEAR}[a.law]
+    law = {"grav": LAW_GRAV, "ljc": LAW_LJC, "ljclin": LAW_LJC_LINEAR, "vjp": TABLE_VJP_GRAV,
+           "vjpljc": TABLE_VJP_LJC, "jerk": TABLE_JERK}[a.law]
     table = tune(law, a.n, reps=a.reps)
     print(json.dumps(table))
     if a.save:

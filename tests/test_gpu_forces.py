@@ -234,6 +234,19 @@ def test_grav_acceleration_and_jerk(n):
     assert_forces_close(jerk[:, :3].cpu().numpy(), rj, what=f"GAJ jerk n={n}")
 
 
+@pytest.mark.parametrize("tile", range(5))
+def test_jerk_every_tile(tile):
+    nb = lib()
+    n = 1300
+    g = workloads.plummer(n, seed=301, eps=0.01)
+    pos, vel = grav_tensors(g)
+    acc, jerk = nb.forces_jerk(pos, vel, eps=float(np.float32(g.eps)), tile=tile)
+    x, v, m = g.f32_as_f64()
+    ra, rj = oracle.grav_jerk(x, v, m, eps=float(np.float32(g.eps)))
+    assert_forces_close(acc[:, :3].cpu().numpy(), ra, what=f"GAJ acc tile {tile}")
+    assert_forces_close(jerk[:, :3].cpu().numpy(), rj, what=f"GAJ jerk tile {tile}")
+
+
 def test_jerk_unsoftened_pair():
     nb = lib()
     pos = torch.tensor([[0, 0, 0, 5.0], [3, 4, 0, 2.0]], dtype=torch.float32, device=dev())

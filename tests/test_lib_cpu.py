@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_version_and_tiles(lib):
     import paper_0706_3060_gb300 as nb
     assert nb.version() >= 10000
-    for law in (0, 1, 2, 3, 4):
+    for law in range(8):
         c = nb.tile_count(law)
         assert c >= 4
         for t in range(c):
@@ -54,6 +54,14 @@ def test_tuned_table_roundtrip(lib):
     assert nb.get_config(nb.LAW_GRAV, 5000) == (3, 2)
     nb.set_tuned(nb.LAW_GRAV, 5000, -1, 0)
     assert nb.get_config(nb.LAW_GRAV, 5000)[1] == 0
+    # VJP tables: defaults (row 0 from 8192 up, row 1 below), then a tuned entry
+    assert nb.get_config(nb.TABLE_VJP_GRAV, 16384)[0] == 0
+    assert nb.get_config(nb.TABLE_JERK, 1000)[0] == 1
+    nb.set_tuned(nb.TABLE_VJP_GRAV, 16384, 2, 4)
+    assert nb.get_config(nb.TABLE_VJP_GRAV, 16384) == (2, 4)
+    nb.set_tuned(nb.TABLE_VJP_GRAV, 16384, -1, 0)
+    with pytest.raises(nb.NBodyError):
+        nb.tile_count(8)
 
 
 def test_bad_arguments_rejected_without_gpu(lib):
