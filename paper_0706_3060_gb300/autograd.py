@@ -2,9 +2,12 @@
 
 Forward: ``nsteps`` KDK steps through nbody_step with the compensated two-float
 state, storing (x, v, low parts) every ``k`` steps, and the positions of the
-newest chunk. Backward: for each chunk, newest first, recompute its positions
-with nbody_step's trace (the newest chunk's are already stored), then run the
-reverse sweep nbody_adjoint_leapfrog (force VJP kernels + fused adjoint updates). With merged half-kicks the sweep is
+newest chunk. Backward: for each chunk, newest first, run the reverse sweep
+nbody_adjoint_leapfrog (force VJP kernels + fused adjoint updates) over the
+chunk's positions; those are recomputed from the checkpoint with nbody_step's
+trace on a second stream while the sweep of the next-newer chunk runs, so the
+two fill each other's partial waves (the newest chunk's positions are stored).
+With merged half-kicks the sweep is
 
     lam_x += dt/2 J(x_T)^T lam_v                      (only if dL/dv_T != 0)
     for n = T-1 .. 0:  lam_v += dt lam_x;  lam_x += w_n J(x_n)^T lam_v
@@ -19,6 +22,15 @@ import torch
 
 from . import api
 from ._lib import LAW_GRAV, LAW_LJC
+
+_SIDE: dict = {}  # device index -> the stream that recomputes chunk positions
+
+
+def _side_stream(dev):
+    idx = dev.index if dev.index is not None else torch.cuda.current_device()
+    if idx not in _SIDE:
+        _SIDE[idx] = torch.cuda.Stream(device=dev)
+    return _SIDE[idx]
 
 
 class _Cfg:
@@ -89,21 +101,43 @@ class NBodyLeapfrog(torch.autograd.Function):
             api.adjoint(pos_T, lam_v, ctx.prm, law=cfg.law, G=cfg.G, eps=cfg.eps,
                         alpha=0.5 * cfg.dt, grad_x=lam_x, grad_m=grad_m, grad_types=gt,
                         ntypes=cfg.ntypes, accumulate=True)
-        acc = torch.empty_like(pos_T)
-        starts = [cfg.k * c for c in range(len(ctx.ckpts))]
-        for c in range(len(ctx.ckpts) - 1, -1, -1):
+        nck = len(ctx.ckpts)
+        starts = [cfg.k * c for c in range(nck)]
+        main = torch.cuda.current_stream(dev)
+        side = _side_stream(dev)
+        side.wait_stream(main)  # checkpoints and prm were written on the main stream
+        side_acc = []
+
+        def recompute(c):
+            """Enqueue chunk c's positions on the side stream; (trace, done event)."""
             p0, v0, l0 = ctx.ckpts[c]
             steps = min(cfg.k, cfg.nsteps - starts[c])
-            if c == len(ctx.ckpts) - 1 and ctx.last_trace is not None:
+            with torch.cuda.stream(side):
+                pos, vel, lo = p0.clone(), v0.clone(), l0.clone()
+                if not side_acc:
+                    side_acc.append(torch.empty_like(pos))
+                trace = torch.empty(((steps + 1) * n, 4), dtype=torch.float32, device=dev)
+                api.step(pos, vel, side_acc[0], ctx.prm, dt=cfg.dt, nsteps=steps, law=cfg.law,
+                         G=cfg.G, eps=cfg.eps, trace=trace, state_lo=lo, stream=side)
+            done = torch.cuda.Event()
+            done.record(side)
+            return trace, done
+
+        pending = None
+        if nck and ctx.last_trace is None:
+            pending = recompute(nck - 1)
+        for c in range(nck - 1, -1, -1):
+            steps = min(cfg.k, cfg.nsteps - starts[c])
+            if pending is None:  # the newest chunk, stored by the forward pass
                 trace = ctx.last_trace
             else:
-                pos, vel, lo = p0.clone(), v0.clone(), l0.clone()
-                trace = torch.empty(((steps + 1) * n, 4), dtype=torch.float32, device=dev)
-                api.step(pos, vel, acc, ctx.prm, dt=cfg.dt, nsteps=steps, law=cfg.law, G=cfg.G,
-                         eps=cfg.eps, trace=trace, state_lo=lo)
+                trace, done = pending
+                main.wait_event(done)
+                trace.record_stream(main)
+            pending = recompute(c - 1) if c > 0 else None
             api.adjoint_leapfrog(trace, lam_x, lam_v, ctx.prm, k=steps, dt=cfg.dt,
                                  first=starts[c] == 0, law=cfg.law, G=cfg.G, eps=cfg.eps,
-                                 grad_m=grad_m, grad_types=gt, ntypes=cfg.ntypes)
+                                 grad_m=grad_m, grad_types=gt, ntypes=cfg.ntypes, stream=main)
         g_sig = g_eps = None
         if cfg.law == LAW_LJC:
             g_sig = grad_t[:cfg.ntypes].to(torch.float32)
