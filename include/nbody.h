@@ -346,6 +346,23 @@ int nbody_tile_info(int32_t law, int32_t tile, int32_t *threads, int32_t *i_per_
 int nbody_set_tuned(int32_t law, int32_t log2n, int32_t tile, int32_t jsplit);
 /* Query the configuration a call with (law, n) and tile == -1 would use. */
 int nbody_get_config(int32_t law, int64_t n, int32_t *tile, int32_t *jsplit);
+/* Autotune tile table `table` at size n on the caller's device inputs (the
+ * paper tunes its unrolling by hand, Sec. 3.3; this searches the compiled
+ * configurations instead). Every tile x j-split in {0 (auto), 1, 2, 4, 8, 16,
+ * 32} that fits n is run once to warm up and `reps` (1..1000) more times, timed
+ * with CUDA events on `stream`; the median decides. The fastest is installed
+ * with nbody_set_tuned for bucket floor(log2 n) and returned in best_tile,
+ * best_jsplit and best_ms (milliseconds per call; any may be NULL). What is
+ * timed: tables 0-2 nbody_forces (law = table), 4 nbody_forces with
+ * NBODY_FIXED_POINT (eps2 > 0), 5 / 6 nbody_adjoint (gravity / LJC, with
+ * lambda = pos_m), 7 nbody_forces_jerk (velocities = pos_m); G = 1, softening
+ * eps2. prm: the LJC parameters for tables 1, 2 and 6, else ignored. Outputs
+ * go to library scratch. Table 3 (batched) returns NBODY_EUNSUPPORTED: the
+ * package tunes it over a system table. Synchronizes `stream`; on any error
+ * nothing is installed. */
+int nbody_tune(int32_t table, const void *pos_m, const void *prm, int64_t n, float eps2,
+               int32_t reps, int32_t *best_tile, int32_t *best_jsplit, float *best_ms,
+               nbody_stream_t stream);
 
 #ifdef __cplusplus
 }

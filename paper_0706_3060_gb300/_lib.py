@@ -42,6 +42,7 @@ EXPORTS = (
     "nbody_tile_count", "nbody_tile_info", "nbody_set_tuned", "nbody_get_config",
     "nbody_timing_enable", "nbody_timing_read", "nbody_peak_probe", "nbody_forces_static",
     "nbody_forces_subset", "nbody_forces_jerk", "nbody_hermite_step", "nbody_selftest_timeout",
+    "nbody_tune",
 )
 
 
@@ -119,6 +120,8 @@ def load(path: str | None = None):
             "nbody_timing_read": ([i32, ctypes.POINTER(i64), ctypes.POINTER(f64)], ctypes.c_int),
             "nbody_get_config": ([i32, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)],
                                  ctypes.c_int),
+            "nbody_tune": ([i32, vp, vp, i64, f32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                            ctypes.POINTER(f32), vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)

@@ -327,6 +327,17 @@ def get_config(law: int, n: int) -> tuple[int, int]:
     return t.value, j.value
 
 
+def tune_table(table: int, pos_m, prm=None, *, eps=0.01, reps=5, stream=None) -> dict:
+    """Autotune tile table ``table`` at n = len(pos_m) in the library (nbody_tune):
+    installs and returns the fastest (tile, jsplit) with its median milliseconds."""
+    _check4(pos_m, "pos_m")
+    t, j, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    check(_lib().nbody_tune(int(table), _ptr(pos_m), _ptr(prm), pos_m.shape[0], float(eps) ** 2,
+                            int(reps), ctypes.byref(t), ctypes.byref(j), ctypes.byref(ms),
+                            _stream(stream, pos_m.device)), "nbody_tune")
+    return {"tile": t.value, "jsplit": j.value, "ms": ms.value}
+
+
 # ---------------------------------------------------------------------------
 # Kernel timers
 # ---------------------------------------------------------------------------

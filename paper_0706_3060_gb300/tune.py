@@ -18,8 +18,8 @@ import os
 import numpy as np
 
 from . import api
-from ._lib import (LAW_GRAV, LAW_LJC, LAW_LJC_LINEAR, TABLE_BATCHED, TABLE_JERK,
-                   TABLE_VJP_GRAV, TABLE_VJP_LJC)
+from ._lib import (LAW_GRAV, LAW_LJC, LAW_LJC_LINEAR, TABLE_BATCHED, TABLE_GRAV_FIXED,
+                   TABLE_JERK, TABLE_VJP_GRAV, TABLE_VJP_LJC)
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
@@ -91,10 +91,28 @@ def _vjp_timer(torch, table):
     return run
 
 
-def tune(law: int, sizes, jsplits=(0, 1, 2, 4, 8, 16, 32), reps=5, verbose=True):
-    """Time every tile x j-split of tile table `law` (0-2 force laws, 5-7 the VJP
-    and jerk tables) at each size and install the fastest per size bucket."""
+def tune(law: int, sizes, jsplits=(0, 1, 2, 4, 8, 16, 32), reps=5, verbose=True,
+         native=True):
+    """Time every tile x j-split of tile table `law` (0-2 force laws, 4 fixed point,
+    5-7 the VJP and jerk tables) at each size and install the fastest per size
+    bucket. native=True runs the search inside the library (nbody_tune, the same
+    j-splits); native=False times each configuration from Python and prints it."""
     import torch
+    if native:
+        table = {}
+        in_law = LAW_LJC if law in (LAW_LJC, LAW_LJC_LINEAR, TABLE_VJP_LJC) else LAW_GRAV
+        for n in sizes:
+            pos, prm = _inputs(torch, in_law, n)
+            got = api.tune_table(law, pos, prm, eps=0.01, reps=reps)
+            table[str(int(math.floor(math.log2(n))))] = {
+                "n": n, "tile": got["tile"], "jsplit": got["jsplit"], "ms": got["ms"],
+                "gpairs_per_s": n * n / got["ms"] / 1e6}
+            if verbose:
+                print(f"table={law} n={n}: tile={got['tile']} jsplit={got['jsplit']} "
+                      f"{got['ms']:.4f} ms", flush=True)
+        return table
+    if law == TABLE_GRAV_FIXED:
+        raise ValueError("the fixed-point table is tuned by the library (native=True)")
     timer = time_config
     in_law = law
     if law in (TABLE_VJP_GRAV, TABLE_VJP_LJC, TABLE_JERK):
@@ -203,11 +221,14 @@ def load_cache(path: str = CACHE) -> int:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--law", choices=["grav", "ljc", "ljclin", "batched", "vjp", "vjpljc",
-                                      "jerk"], default="grav")
+    ap.add_argument("--law", choices=["grav", "ljc", "ljclin", "fixed", "batched", "vjp",
+                                      "vjpljc", "jerk"], default="grav")
     ap.add_argument("--n", type=int, nargs="+", default=[1024, 4096, 16384, 65536, 262144])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--save", action="store_true")
+    ap.add_argument("--python", action="store_true",
+                    help="time each configuration from Python and print it (default: the "
+                         "library's nbody_tune)")
     a = ap.parse_args()
     if a.law == "batched":
         table = tune_batched(reps=a.reps)
@@ -215,9 +236,9 @@ def main():
         if a.save:
             save_cache(TABLE_BATCHED, table)
         return
-    law = {"grav": LAW_GRAV, "ljc": LAW_LJC, "ljclin": LAW_LJC_LINEAR, "vjp": TABLE_VJP_GRAV,
-           "vjpljc": TABLE_VJP_LJC, "jerk": TABLE_JERK}[a.law]
-    table = tune(law, a.n, reps=a.reps)
+    law = {"grav": LAW_GRAV, "ljc": LAW_LJC, "ljclin": LAW_LJC_LINEAR, "fixed": TABLE_GRAV_FIXED,
+           "vjp": TABLE_VJP_GRAV, "vjpljc": TABLE_VJP_LJC, "jerk": TABLE_JERK}[a.law]
+    table = tune(law, a.n, reps=a.reps, native=not a.python)
     print(json.dumps(table))
     if a.save:
         save_cache(law, table)

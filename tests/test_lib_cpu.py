@@ -100,3 +100,17 @@ def test_no_device_is_reported(lib):
     st = lib.nbody_forces(ctypes.c_void_p(16), None, ctypes.c_void_p(32), None, 8,
                           ctypes.byref(p), None)
     assert st == 6  # NBODY_EUNSUPPORTED
+
+
+def test_tune_rejects_bad_arguments_without_gpu(lib):
+    t, j, ms = ctypes.c_int32(-7), ctypes.c_int32(-7), ctypes.c_float(0.0)
+    args = (ctypes.byref(t), ctypes.byref(j), ctypes.byref(ms), None)
+    # the batched table is tuned over a system table, not here
+    assert lib.nbody_tune(3, ctypes.c_void_p(16), None, 1024, 1e-4, 3, *args) == 6
+    assert lib.nbody_tune(8, ctypes.c_void_p(16), None, 1024, 1e-4, 3, *args) == 6
+    assert lib.nbody_tune(0, ctypes.c_void_p(16), None, 0, 1e-4, 3, *args) == 1
+    assert lib.nbody_tune(0, ctypes.c_void_p(16), None, 1024, 1e-4, 0, *args) == 1
+    assert lib.nbody_tune(0, None, None, 1024, 1e-4, 3, *args) == 1
+    assert lib.nbody_tune(1, ctypes.c_void_p(16), None, 1024, 0.0, 3, *args) == 1  # LJC: prm
+    assert lib.nbody_tune(4, ctypes.c_void_p(16), None, 1024, 0.0, 3, *args) == 1  # eps2 > 0
+    assert t.value == -7 and j.value == -7  # nothing written on error
