@@ -34,6 +34,36 @@ def _ljc(nb, torch, dev, n, seed=2):
     return pos, prm
 
 
+def _ensemble(nb, torch, dev, nsys=512, seed=3):
+    """The 512-system ensemble (N log-uniform in [64, 4096], even systems gravity,
+    odd LJ + Coulomb) packed back to back, with its system table."""
+    import workloads
+    ens = workloads.ensemble(nsys=nsys, seed=seed)
+    total = sum(s.n for s in ens.systems)
+    pos = np.zeros((total, 4), np.float32)
+    q, sg, ep = np.zeros(total), np.full(total, 3.0), np.full(total, 0.1)
+    ty = np.zeros(total, np.int32)
+    table, off = [], 0
+    for s in ens.systems:
+        if isinstance(s, workloads.GravInput):
+            x, _, m = s.f32()
+            table.append(dict(offset=off, n=s.n, law=nb.LAW_GRAV, eps=float(np.float32(s.eps)),
+                              dt=1e-3))
+        else:
+            x, _, m, qq, st, et = s.f32()
+            q[off:off + s.n] = qq
+            sg[off:off + s.n] = st.astype(np.float64)[s.types]
+            ep[off:off + s.n] = et.astype(np.float64)[s.types]
+            ty[off:off + s.n] = s.types
+            table.append(dict(offset=off, n=s.n, law=nb.LAW_LJC, dt=1e-4))
+        pos[off:off + s.n, :3], pos[off:off + s.n, 3] = x, m
+        off += s.n
+    prm = nb.pack_ljc(torch.from_numpy(q).to(dev), torch.from_numpy(sg).to(dev),
+                      torch.from_numpy(ep).to(dev), torch.from_numpy(ty).to(dev),
+                      kq=332.0637 / 80.0)
+    return torch.from_numpy(pos).to(dev).contiguous(), prm, table
+
+
 def build_case(name, nb, torch, dev):
     """Return a zero-argument callable running one call of the named workload."""
     if name == "grav262144":
@@ -53,12 +83,19 @@ def build_case(name, nb, torch, dev):
     if name == "jerk262144":
         pos, vel, eps = _grav(nb, torch, dev, 262144)
         return lambda: nb.forces_jerk(pos, vel, eps=eps)
+    if name == "batched512":
+        pos, prm, table = _ensemble(nb, torch, dev)
+        vel = torch.zeros_like(pos)
+        acc = torch.zeros_like(pos)
+        plan = nb.BatchPlan(table)
+        return lambda: plan.run(pos, vel, acc, prm, nsteps=0, graph=False)
     raise ValueError(f"unknown case {name}")
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["grav262144", "ljc8192", "vjp16384", "jerk262144"])
+    ap.add_argument("case", choices=["grav262144", "ljc8192", "vjp16384", "jerk262144",
+                                     "batched512"])
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--iters", type=int, default=2)
     a = ap.parse_args()
