@@ -227,9 +227,14 @@ int gaj_eval(const float4 *pos, const float4 *vel, float4 *acc, float4 *jerk, in
              const nbody_params &p, const VjpScratch &sc, cudaStream_t s) {
   int *err = nullptr;
   NB_TRY(error_word(&err));
+  if (sc.d->packed) {  // (x, m) and velocities of source pairs, interleaved
+    interleave_vjp_pairs_kernel<<<((n + 1) / 2 + 255) / 256, 256, 0, s>>>(pos, vel, sc.jp, n);
+    NB_CUDA(cudaGetLastError());
+  }
   VjpArgs a{};
   a.pos = pos;
   a.lam = vel;
+  a.jpair = sc.jp;
   a.part_hi = sc.part_hi;
   a.part_lo = sc.part_lo;
   a.stride = n;

@@ -170,6 +170,35 @@ __device__ __forceinline__ void gaj_pair(const float4 pj, const float4 vj, float
   B.z = fmaf(w, fmaf(-c, dz, uz), B.z);
 }
 
+// Acceleration and jerk for two sources at once (f32x2), the same terms as
+// gaj_pair: A += w d, B += w (u - 3 y^2 (d.u) d), w = m_j y^3.
+__device__ __forceinline__ void gaj_pair2(float2 X, float2 Y, float2 Z, float2 Mj, float2 VX,
+                                          float2 VY, float2 VZ, float2 nxk, float2 nyk,
+                                          float2 nzk, float2 nvx, float2 nvy, float2 nvz,
+                                          float2 e2, float2 &ax, float2 &ay, float2 &az,
+                                          float2 &bx, float2 &by, float2 &bz) {
+  const float2 dx = __fadd2_rn(X, nxk);
+  const float2 dy = __fadd2_rn(Y, nyk);
+  const float2 dz = __fadd2_rn(Z, nzk);
+  const float2 ux = __fadd2_rn(VX, nvx);
+  const float2 uy = __fadd2_rn(VY, nvy);
+  const float2 uz = __fadd2_rn(VZ, nvz);
+  float2 s2 = __ffma2_rn(dz, dz, e2);
+  s2 = __ffma2_rn(dy, dy, s2);
+  s2 = __ffma2_rn(dx, dx, s2);
+  const float2 y = make_float2(rsqrt_hw(s2.x), rsqrt_hw(s2.y));
+  const float2 y2 = __fmul2_rn(y, y);
+  const float2 w = __fmul2_rn(__fmul2_rn(Mj, y), y2);
+  const float2 ru = __ffma2_rn(dx, ux, __ffma2_rn(dy, uy, __fmul2_rn(dz, uz)));
+  const float2 c = __fmul2_rn(ru, __fmul2_rn(y2, make_float2(-3.0f, -3.0f)));
+  ax = __ffma2_rn(w, dx, ax);
+  ay = __ffma2_rn(w, dy, ay);
+  az = __ffma2_rn(w, dz, az);
+  bx = __ffma2_rn(w, __ffma2_rn(c, dx, ux), bx);
+  by = __ffma2_rn(w, __ffma2_rn(c, dy, uy), by);
+  bz = __ffma2_rn(w, __ffma2_rn(c, dz, uz), bz);
+}
+
 template <int LAW, int NT, int I, int SW, int JT, bool PK = false>
 struct VjpTile {
   static constexpr int kThreads = NT + 32;
@@ -219,7 +248,8 @@ __device__ __forceinline__ void shfl_combine(float4 &hi, float4 &lo, int off) {
 template <int LAW, int NT, int I, int SW, int JT, bool PK = false, int PU = 2>
 __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
   using T = VjpTile<LAW, NT, I, SW, JT, PK>;
-  static_assert(!PK || (LAW == kLawGrav && SW == 1), "packed VJP: gravity, one j-lane");
+  static_assert(!PK || ((LAW == kLawGrav || LAW == kLawGAJ) && SW == 1),
+                "packed: gravity VJP or acceleration + jerk, one j-lane");
   constexpr int NWARPS = NT / 32;
   constexpr int SLOTS = T::kSlots;
   constexpr int TI = T::kTileI;
@@ -328,7 +358,54 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
     const float4 *sl = sm_lam + st * JT;
     const float4 *sq = sm_prm + st * JT;
     const bool masked = (cj0 < i0 + ni) && (i0 < cj0 + len);
-    if (PK) {
+    if (PK && GJ) {
+      const float4 *pk = sm_pos + st * 2 * JT;
+      if (!masked) {
+        const float2 e2 = make_float2(a.eps2, a.eps2);
+        const int npairs = (len + 1) >> 1;
+        float2 ax[I], ay[I], az[I], bx[I], by[I], bz[I];
+#pragma unroll
+        for (int r = 0; r < I; ++r)
+          ax[r] = ay[r] = az[r] = bx[r] = by[r] = bz[r] = make_float2(0.f, 0.f);
+#pragma unroll PU
+        for (int pp = 0; pp < npairs; ++pp) {
+          const float4 P0 = pk[4 * pp], P1 = pk[4 * pp + 1];
+          const float4 V0 = pk[4 * pp + 2], V1 = pk[4 * pp + 3];
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            gaj_pair2(make_float2(P0.x, P0.y), make_float2(P0.z, P0.w), make_float2(P1.x, P1.y),
+                      make_float2(P1.z, P1.w), make_float2(V0.x, V0.y), make_float2(V0.z, V0.w),
+                      make_float2(V1.x, V1.y), make_float2(-xk[r], -xk[r]),
+                      make_float2(-yk[r], -yk[r]), make_float2(-zk[r], -zk[r]),
+                      make_float2(-lx[r], -lx[r]), make_float2(-ly[r], -ly[r]),
+                      make_float2(-lz[r], -lz[r]), e2, ax[r], ay[r], az[r], bx[r], by[r], bz[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < I; ++r) {
+          pA[r].x += ax[r].x + ax[r].y;
+          pA[r].y += ay[r].x + ay[r].y;
+          pA[r].z += az[r].x + az[r].y;
+          pB[r].x += bx[r].x + bx[r].y;
+          pB[r].y += by[r].x + by[r].y;
+          pB[r].z += bz[r].x + bz[r].y;
+        }
+      } else {
+        for (int jj = 0; jj < len; ++jj) {
+          const int q = 4 * (jj >> 1);
+          const bool odd = jj & 1;
+          const float4 P0 = pk[q], P1 = pk[q + 1], V0 = pk[q + 2], V1 = pk[q + 3];
+          const float4 pj = make_float4(odd ? P0.y : P0.x, odd ? P0.w : P0.z, odd ? P1.y : P1.x,
+                                        odd ? P1.w : P1.z);
+          const float4 vj = make_float4(odd ? V0.y : V0.x, odd ? V0.w : V0.z, odd ? V1.y : V1.x,
+                                        0.f);
+          const int jg = cj0 + jj;
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            gaj_pair<true>(pj, vj, xk[r], yk[r], zk[r], lx[r], ly[r], lz[r], a.eps2, pA[r], pB[r],
+                           jg == ig[r]);
+        }
+      }
+    } else if (PK) {
       const float4 *pk = sm_pos + st * 2 * JT;
       if (!masked) {
         const float2 e2 = make_float2(a.eps2, a.eps2);

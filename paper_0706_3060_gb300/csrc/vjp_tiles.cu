@@ -80,7 +80,11 @@ struct VjpImpl {
   X(kLawGAJ, 128, 2, 4, 256, false, 2)                              \
   X(kLawGAJ, 128, 2, 1, 256, false, 2)                              \
   X(kLawGAJ, 256, 1, 1, 256, false, 2)                              \
-  X(kLawGAJ, 128, 2, 1, 512, false, 4)
+  X(kLawGAJ, 128, 2, 1, 512, false, 4)                              \
+  X(kLawGAJ, 256, 2, 1, 256, true, 2)                               \
+  X(kLawGAJ, 128, 2, 1, 512, true, 4)                               \
+  X(kLawGAJ, 256, 1, 1, 256, true, 4)                               \
+  X(kLawGAJ, 128, 2, 1, 256, true, 2)
 
 #define NB_VJP_DESC(L, NT, I, SW, JT, PK, PU) VjpImpl<L, NT, I, SW, JT, PK, PU>::desc(),
 #define NB_VJP_TILE(L, NT, I, SW, JT, PK, PU) VjpImpl<L, NT, I, SW, JT, PK, PU>::tile(),
