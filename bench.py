@@ -365,7 +365,38 @@ def extras(nb, torch, dev, g, eps):
     ex.update(batched_extras(nb, torch, dev))
     ex.update(adjoint_extras(nb, torch, dev))
     ex.update(secondary_kernel_extras(nb, torch, dev, pos, eps))
+    ex["oracle_gpairs_per_s"] = oracle_family_rates()
     return ex
+
+
+def oracle_family_rates():
+    """The FP64 oracle's rate for each force form, timed on this host's cores on one
+    evaluation of a small case (gravity forms: Plummer N = 16384; LJC forms: the
+    8192-atom sphere), for comparison with the GPU rates beside them."""
+    import oracle
+    import workloads
+    g = workloads.plummer(16384, seed=4, eps=workloads.plummer_softening(16384))
+    x, v, m = g.f32_as_f64()
+    e = float(np.float32(g.eps))
+    s = workloads.ljc_sphere(8192, seed=2)
+    lx, _, lm, q, st, et = s.f32_as_f64()
+    lam_g = np.random.default_rng(0).standard_normal((16384, 3))
+    lam_l = np.random.default_rng(1).standard_normal((8192, 3))
+    cases = {
+        "grav": (16384, lambda: oracle.grav_accel(x, m, eps=e)),
+        "jerk": (16384, lambda: oracle.grav_jerk(x, v, m, eps=e)),
+        "grav_vjp": (16384, lambda: oracle.grav_vjp(x, m, lam_g, eps=e)),
+        "ljc": (8192, lambda: oracle.ljc_force(lx, q, st[s.types], et[s.types])),
+        "ljc_linear": (8192, lambda: oracle.ljc_force(lx, q, st[s.types], et[s.types],
+                                                      kq=oracle.COULOMB_K / 4.0, linear=True)),
+        "ljc_vjp": (8192, lambda: oracle.ljc_vjp(lx, lm, q, s.types, st, et, lam_l)),
+    }
+    out = {"cores": oracle.set_threads(None)}
+    for name, (n, fn) in cases.items():
+        t0 = time.perf_counter()
+        fn()
+        out[name] = float(n) * n / (time.perf_counter() - t0) / 1e9
+    return out
 
 
 def _device_ms(torch, fn, reps=5):
@@ -413,6 +444,12 @@ def secondary_kernel_extras(nb, torch, dev, pos, eps):
                           torch.from_numpy(s.types).to(dev), kq=332.0637 / 4.0)
     ms = _device_ms(torch, lambda: nb.forces(lpos, prm_lin, law=nb.LAW_LJC_LINEAR))
     out["ljc_linear_8192_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
+    lam = torch.randn_like(lpos)
+    lgx, lgm = torch.empty_like(lpos), torch.empty(lpos.shape[0], device=dev)
+    lgt = torch.zeros(8, dtype=torch.float64, device=dev)
+    ms = _device_ms(torch, lambda: nb.adjoint(lpos, lam, prm, grad_x=lgx, grad_m=lgm,
+                                               grad_types=lgt))
+    out["ljc_vjp_8192_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
     hp, hv = pos.clone(), vel.clone()
     ha, hj = torch.empty_like(pos), torch.empty_like(pos)
     nb.hermite_step(hp, hv, ha, hj, dt=DT, nsteps=0, eps=eps)
