@@ -73,7 +73,9 @@ int vjp_prepare(int law, int n, int tile, int jsplit, int sms, cudaStream_t s, V
   const size_t ubytes = round_up(size_t(n) * sizeof(float4), 256);
   const int nblk = (n + 255) / 256;
   const size_t tbytes = round_up(size_t(nblk) * 8 * sizeof(double), 256);
-  const size_t jbytes = d.packed ? round_up(size_t((n + 1) / 2) * 4 * sizeof(float4), 256) : 0;
+  const int pair_f4 = law == NBODY_LAW_LJC ? 5 : 4;  // float4s per packed source pair
+  const size_t jbytes =
+      d.packed ? round_up(size_t((n + 1) / 2) * pair_f4 * sizeof(float4), 256) : 0;
   void *base = nullptr;
   NB_TRY(workspace(s, 2 * part + ubytes + tbytes + jbytes + extra, &base));
   char *b = static_cast<char *>(base);
@@ -106,7 +108,11 @@ int vjp_once(const float4 *pos, const float4 *prm, const float4 *lam, float4 *gr
     src = sc.u;
   }
   if (sc.d->packed) {
-    interleave_vjp_pairs_kernel<<<((n + 1) / 2 + 255) / 256, 256, 0, s>>>(pos, src, sc.jp, n);
+    const unsigned pblocks = unsigned(((n + 1) / 2 + 255) / 256);
+    if (p.law == NBODY_LAW_LJC)
+      interleave_ljc_vjp_pairs_kernel<<<pblocks, 256, 0, s>>>(pos, src, prm, sc.jp, n);
+    else
+      interleave_vjp_pairs_kernel<<<pblocks, 256, 0, s>>>(pos, src, sc.jp, n);
     NB_CUDA(cudaGetLastError());
   }
   VjpArgs a{};

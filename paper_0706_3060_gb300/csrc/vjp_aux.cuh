@@ -182,6 +182,24 @@ __global__ void interleave_vjp_pairs_kernel(const float4 *pos, const float4 *lam
   jp[4 * p + 3] = make_float4(la.z, lb.z, 0.f, 0.f);
 }
 
+// LJC VJP source pairs: (x x y y)(z z q q)(s s e e)(-ux -ux -uy -uy)(-uz -uz 0 0);
+// an odd count ends with an uncharged, motionless pad at 1e18 with zero LJ terms.
+__global__ void interleave_ljc_vjp_pairs_kernel(const float4 *pos, const float4 *u,
+                                                const float4 *prm, float4 *jp, int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * p >= n) return;
+  const bool two = 2 * p + 1 < n;
+  const float4 a = pos[2 * p], ua = u[2 * p], qa = prm[2 * p];
+  const float4 b = two ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+  const float4 ub = two ? u[2 * p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 qb = two ? prm[2 * p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+  jp[5 * p] = make_float4(a.x, b.x, a.y, b.y);
+  jp[5 * p + 1] = make_float4(a.z, b.z, qa.x, qb.x);
+  jp[5 * p + 2] = make_float4(qa.y, qb.y, qa.z, qb.z);
+  jp[5 * p + 3] = make_float4(-ua.x, -ub.x, -ua.y, -ub.y);
+  jp[5 * p + 4] = make_float4(-ua.z, -ub.z, 0.f, 0.f);
+}
+
 // u = lam / m (LJC sources are weighted by 1 / m_j).
 __global__ void lam_over_m_kernel(const float4 *lam, const float4 *pos, float4 *u, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;

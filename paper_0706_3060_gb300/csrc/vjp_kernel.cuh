@@ -143,6 +143,51 @@ __device__ __forceinline__ void ljc_vjp_pair(const float4 pj, const float4 uj, c
   B.w = fmaf(dw, phi_lj, B.w);
 }
 
+// The LJC VJP pair for two sources at once (f32x2), the same terms in the same
+// order as ljc_vjp_pair. Sources arrive as (x x y y)(z z q q)(s s e e)
+// (-ux -ux -uy -uy)(-uz -uz 0 0): the negated u_j makes w = u_k - u_j one add.
+__device__ __forceinline__ void ljc_vjp_pair2(const float4 F0, const float4 F1, const float4 F2,
+                                              const float4 F3, const float4 F4, float2 nxk,
+                                              float2 nyk, float2 nzk, float2 ukx, float2 uky,
+                                              float2 ukz, float2 qk, float2 sk, float2 ek,
+                                              float2 (&A)[4], float2 (&B)[4]) {
+  const float2 dx = __fadd2_rn(make_float2(F0.x, F0.y), nxk);
+  const float2 dy = __fadd2_rn(make_float2(F0.z, F0.w), nyk);
+  const float2 dz = __fadd2_rn(make_float2(F1.x, F1.y), nzk);
+  const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+  const float2 y = make_float2(rsqrt_hw(r2.x), rsqrt_hw(r2.y));
+  const float2 y2 = __fmul2_rn(y, y);
+  const float2 qq = __fmul2_rn(qk, make_float2(F1.z, F1.w));
+  const float2 s = __fadd2_rn(sk, make_float2(F2.x, F2.y));
+  const float2 ee = __fmul2_rn(ek, make_float2(F2.z, F2.w));
+  const float2 t = __fmul2_rn(__fmul2_rn(s, s), y2);
+  const float2 u = __fmul2_rn(__fmul2_rn(t, t), t);
+  const float2 qy3 = __fmul2_rn(qq, __fmul2_rn(y, y2));
+  const float2 eey2 = __fmul2_rn(ee, y2);
+  const float2 h = __fmul2_rn(__ffma2_rn(u, make_float2(2.0f, 2.0f), make_float2(-1.0f, -1.0f)), u);
+  const float2 phi_lj = __fmul2_rn(eey2, h);
+  const float2 phi = __fadd2_rn(phi_lj, qy3);
+  const float2 k1 =
+      __fmul2_rn(__ffma2_rn(u, make_float2(-28.0f, -28.0f), make_float2(8.0f, 8.0f)), u);
+  const float2 tp =
+      __fmul2_rn(y2, __ffma2_rn(eey2, k1, __fmul2_rn(make_float2(-3.0f, -3.0f), qy3)));
+  const float2 wx = __fadd2_rn(ukx, make_float2(F3.x, F3.y));
+  const float2 wy = __fadd2_rn(uky, make_float2(F3.z, F3.w));
+  const float2 wz = __fadd2_rn(ukz, make_float2(F4.x, F4.y));
+  const float2 dw = __ffma2_rn(dx, wx, __ffma2_rn(dy, wy, __fmul2_rn(dz, wz)));
+  const float2 c = __fmul2_rn(tp, dw);
+  A[0] = __ffma2_rn(c, dx, __ffma2_rn(phi, wx, A[0]));
+  A[1] = __ffma2_rn(c, dy, __ffma2_rn(phi, wy, A[1]));
+  A[2] = __ffma2_rn(c, dz, __ffma2_rn(phi, wz, A[2]));
+  B[0] = __ffma2_rn(phi, dx, B[0]);
+  B[1] = __ffma2_rn(phi, dy, B[1]);
+  B[2] = __ffma2_rn(phi, dz, B[2]);
+  const float2 k2 = __fmul2_rn(__ffma2_rn(u, make_float2(4.0f, 4.0f), make_float2(-1.0f, -1.0f)), u);
+  const float2 rs = make_float2(rcp_hw(s.x), rcp_hw(s.y));
+  A[3] = __ffma2_rn(dw, __fmul2_rn(__fmul2_rn(eey2, k2), rs), A[3]);
+  B[3] = __ffma2_rn(dw, phi_lj, B[3]);
+}
+
 // Acceleration and jerk (Table 1 GAJ): d = x_j - x_k, u = v_j - v_k, y = 1/s,
 // w = m_j y^3:  A += w d;  B += w (u - 3 (d.u) y^2 d).
 template <bool MASK>
@@ -206,7 +251,10 @@ struct VjpTile {
   static constexpr int kTileI = kSlots * I;
   static constexpr int kStreams = (LAW == kLawLJC) ? 3 : 2;
   static constexpr size_t kSmemBytes = size_t(kStages) * JT * 16 * kStreams;
-  static constexpr int kPairF4 = 4;  // packed gravity: float4s per source pair
+  // packed sources: float4s per source pair (gravity VJP and jerk 4, LJC VJP 5)
+  static constexpr int kPairF4 = (LAW == kLawLJC) ? 5 : 4;
+  static constexpr int kStageF4 = kPairF4 * JT / 2;  // float4s of one ring stage
+  static_assert(!PK || kStageF4 <= JT * kStreams, "packed stage exceeds the ring");
 };
 
 __device__ __forceinline__ void comp_fold(float4 &hi, float4 &lo, float4 &p, int comp) {
@@ -248,8 +296,8 @@ __device__ __forceinline__ void shfl_combine(float4 &hi, float4 &lo, int off) {
 template <int LAW, int NT, int I, int SW, int JT, bool PK = false, int PU = 2>
 __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
   using T = VjpTile<LAW, NT, I, SW, JT, PK>;
-  static_assert(!PK || ((LAW == kLawGrav || LAW == kLawGAJ) && SW == 1),
-                "packed: gravity VJP or acceleration + jerk, one j-lane");
+  static_assert(!PK || SW == 1, "packed tiles: one j-lane");
+  static_assert(JT % 2 == 0, "j-tiles hold whole source pairs");
   constexpr int NWARPS = NT / 32;
   constexpr int SLOTS = T::kSlots;
   constexpr int TI = T::kTileI;
@@ -299,10 +347,11 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
       meta_len[st] = len;
       meta_cj0[st] = cj;
       if (PK) {
-        // pairs of sources, 4 float4 each; the stage spans the pos + lam regions
+        // pairs of sources, kPairF4 float4 each; stages of kStageF4 float4s
         const uint32_t bytes = uint32_t((len + 1) >> 1) * T::kPairF4 * 16u;
         mbar_arrive_expect_tx(&full_bar[st], bytes);
-        tma_load_1d(sm_pos + st * 2 * JT, a.jpair + (cj >> 1) * T::kPairF4, bytes, &full_bar[st]);
+        tma_load_1d(sm_pos + st * T::kStageF4, a.jpair + (cj >> 1) * T::kPairF4, bytes,
+                    &full_bar[st]);
       } else {
         const uint32_t bytes = uint32_t(len) * 16u;
         mbar_arrive_expect_tx(&full_bar[st], bytes * T::kStreams);
@@ -359,7 +408,7 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
     const float4 *sq = sm_prm + st * JT;
     const bool masked = (cj0 < i0 + ni) && (i0 < cj0 + len);
     if (PK && GJ) {
-      const float4 *pk = sm_pos + st * 2 * JT;
+      const float4 *pk = sm_pos + st * T::kStageF4;
       if (!masked) {
         const float2 e2 = make_float2(a.eps2, a.eps2);
         const int npairs = (len + 1) >> 1;
@@ -405,8 +454,59 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
                            jg == ig[r]);
         }
       }
+    } else if (PK && LJ) {
+      const float4 *pk = sm_pos + st * T::kStageF4;
+      if (!masked) {
+        const int npairs = (len + 1) >> 1;
+        float2 A2[I][4], B2[I][4];
+#pragma unroll
+        for (int r = 0; r < I; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) A2[r][c] = B2[r][c] = make_float2(0.f, 0.f);
+#pragma unroll PU
+        for (int pp = 0; pp < npairs; ++pp) {
+          const float4 F0 = pk[5 * pp], F1 = pk[5 * pp + 1], F2 = pk[5 * pp + 2];
+          const float4 F3 = pk[5 * pp + 3], F4 = pk[5 * pp + 4];
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            ljc_vjp_pair2(F0, F1, F2, F3, F4, make_float2(-xk[r], -xk[r]),
+                          make_float2(-yk[r], -yk[r]), make_float2(-zk[r], -zk[r]),
+                          make_float2(lx[r], lx[r]), make_float2(ly[r], ly[r]),
+                          make_float2(lz[r], lz[r]), make_float2(qk[r], qk[r]),
+                          make_float2(sk[r], sk[r]), make_float2(ek[r], ek[r]), A2[r], B2[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < I; ++r) {
+          pA[r].x += A2[r][0].x + A2[r][0].y;
+          pA[r].y += A2[r][1].x + A2[r][1].y;
+          pA[r].z += A2[r][2].x + A2[r][2].y;
+          pA[r].w += A2[r][3].x + A2[r][3].y;
+          pB[r].x += B2[r][0].x + B2[r][0].y;
+          pB[r].y += B2[r][1].x + B2[r][1].y;
+          pB[r].z += B2[r][2].x + B2[r][2].y;
+          pB[r].w += B2[r][3].x + B2[r][3].y;
+        }
+      } else {
+        for (int jj = 0; jj < len; ++jj) {
+          const int q = 5 * (jj >> 1);
+          const bool odd = jj & 1;
+          const float4 F0 = pk[q], F1 = pk[q + 1], F2 = pk[q + 2], F3 = pk[q + 3],
+                       F4 = pk[q + 4];
+          const float4 pj = make_float4(odd ? F0.y : F0.x, odd ? F0.w : F0.z, odd ? F1.y : F1.x,
+                                        0.f);
+          const float4 uj = make_float4(-(odd ? F3.y : F3.x), -(odd ? F3.w : F3.z),
+                                        -(odd ? F4.y : F4.x), 0.f);
+          const float4 qj = make_float4(odd ? F1.w : F1.z, odd ? F2.y : F2.x, odd ? F2.w : F2.z,
+                                        0.f);
+          const int jg = cj0 + jj;
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            ljc_vjp_pair<true>(pj, uj, qj, xk[r], yk[r], zk[r], lx[r], ly[r], lz[r], qk[r],
+                               sk[r], ek[r], pA[r], pB[r], jg == ig[r]);
+        }
+      }
     } else if (PK) {
-      const float4 *pk = sm_pos + st * 2 * JT;
+      const float4 *pk = sm_pos + st * T::kStageF4;
       if (!masked) {
         const float2 e2 = make_float2(a.eps2, a.eps2);
         const int npairs = (len + 1) >> 1;

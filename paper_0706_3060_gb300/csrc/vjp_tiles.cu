@@ -74,7 +74,11 @@ struct VjpImpl {
   X(kLawLJC, 128, 1, 4, 256, false, 2)                              \
   X(kLawLJC, 128, 2, 1, 256, false, 2)                              \
   X(kLawLJC, 256, 1, 1, 256, false, 2)                              \
-  X(kLawLJC, 128, 2, 2, 256, false, 2)
+  X(kLawLJC, 128, 2, 2, 256, false, 2)                              \
+  X(kLawLJC, 256, 2, 1, 256, true, 2)                               \
+  X(kLawLJC, 128, 2, 1, 256, true, 2)                               \
+  X(kLawLJC, 256, 1, 1, 256, true, 2)                               \
+  X(kLawLJC, 128, 1, 1, 512, true, 4)
 #define NB_VJP_GAJ_ROWS(X)                                          \
   X(kLawGAJ, 256, 2, 1, 256, false, 2)                              \
   X(kLawGAJ, 128, 2, 4, 256, false, 2)                              \

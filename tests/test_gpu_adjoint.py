@@ -52,7 +52,7 @@ def test_grav_vjp_every_tile(tile, jsplit):
     assert _rel(gm.cpu().numpy(), rm) <= 2e-5, tile
 
 
-@pytest.mark.parametrize("tile", range(5))
+@pytest.mark.parametrize("tile", range(9))
 def test_ljc_vjp_every_tile(tile):
     nb = lib()
     n = 700
