@@ -109,10 +109,13 @@ __device__ __forceinline__ void grav_pair(const float4 pj, float xi, float yi, f
 // The same gravity pair for two sources at once with packed f32x2 arithmetic
 // (FADD2/FFMA2/FMUL2 issue one instruction for two lanes of work); the two
 // halves of each accumulator are the even and odd sources of the j-tile.
-template <bool POT, bool PRECISE>
+// MASK: s0 / s1 flag a source that is the target itself; its term is dropped
+// (y = 0), the index exclusion of the scalar path.
+template <bool POT, bool PRECISE, bool MASK = false>
 __device__ __forceinline__ void grav_pair2(float2 X, float2 Y, float2 Z, float2 M, float2 nxi,
                                            float2 nyi, float2 nzi, float2 eps2, float2 &ax,
-                                           float2 &ay, float2 &az, float2 &pot) {
+                                           float2 &ay, float2 &az, float2 &pot, bool s0 = false,
+                                           bool s1 = false) {
   const float2 dx = __fadd2_rn(X, nxi);
   const float2 dy = __fadd2_rn(Y, nyi);
   const float2 dz = __fadd2_rn(Z, nzi);
@@ -124,6 +127,10 @@ __device__ __forceinline__ void grav_pair2(float2 X, float2 Y, float2 Z, float2 
     const float2 hs = __fmul2_rn(s2, make_float2(-0.5f, -0.5f));
     const float2 t = __ffma2_rn(hs, __fmul2_rn(y, y), make_float2(1.5f, 1.5f));
     y = __fmul2_rn(y, t);
+  }
+  if (MASK) {
+    y.x = s0 ? 0.0f : y.x;
+    y.y = s1 ? 0.0f : y.y;
   }
   const float2 my = __fmul2_rn(M, y);
   const float2 w = __fmul2_rn(my, __fmul2_rn(y, y));
@@ -172,11 +179,12 @@ __device__ __forceinline__ void ljc_pair(const float4 pj, const float4 qj, float
 }
 
 // LJC for two sources at once in f32x2 arithmetic (same terms as ljc_pair).
-template <bool POT, bool PRECISE, bool LIN = false>
+template <bool POT, bool PRECISE, bool LIN = false, bool MASK = false>
 __device__ __forceinline__ void ljc_pair2(float2 X, float2 Y, float2 Z, float2 Q, float2 S,
                                           float2 E, float2 nxi, float2 nyi, float2 nzi,
                                           float2 qi, float2 si, float2 ei, float2 &ax, float2 &ay,
-                                          float2 &az, float2 &pot) {
+                                          float2 &az, float2 &pot, bool s0 = false,
+                                          bool s1 = false) {
   const float2 dx = __fadd2_rn(X, nxi);
   const float2 dy = __fadd2_rn(Y, nyi);
   const float2 dz = __fadd2_rn(Z, nzi);
@@ -187,6 +195,10 @@ __device__ __forceinline__ void ljc_pair2(float2 X, float2 Y, float2 Z, float2 Q
   if (PRECISE) {
     const float2 hs = __fmul2_rn(r2, make_float2(-0.5f, -0.5f));
     y = __fmul2_rn(y, __ffma2_rn(hs, __fmul2_rn(y, y), make_float2(1.5f, 1.5f)));
+  }
+  if (MASK) {
+    y.x = s0 ? 0.0f : y.x;
+    y.y = s1 ? 0.0f : y.y;
   }
   const float2 y2 = __fmul2_rn(y, y);
   const float2 qq = __fmul2_rn(Q, qi);
@@ -403,8 +415,8 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
     }
     const float4 *sp = sm_pos + st * STAGE_F4;
     const float4 *sq = sm_prm + st * JT;
-    const bool masked = a.tidx != nullptr || ((cj0 < cur.i0 + cur.ni) && (cur.i0 < cj0 + len));
     const float eps2 = cur.eps2;
+    const bool masked = a.tidx != nullptr || ((cj0 < cur.i0 + cur.ni) && (cur.i0 < cj0 + len));
 
     if (PK && (is_ljc(LAW) || (MIX && cur_law == kLawLJC))) {
       if (!masked) {
@@ -433,18 +445,23 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
                                     nz[r], q2[r], s2[r], e2[r], pax[r], pay[r], paz[r], ppt[r]);
         }
       } else {
-        for (int jj = jl; jj < len; jj += SW) {
-          const float4 A = sp[3 * (jj >> 1)];
-          const float4 B = sp[3 * (jj >> 1) + 1];
-          const float4 C = sp[3 * (jj >> 1) + 2];
-          const bool odd = jj & 1;
-          const float4 pj = make_float4(odd ? A.y : A.x, odd ? A.w : A.z, odd ? B.y : B.x, 0.f);
-          const float4 qj = make_float4(odd ? B.w : B.z, odd ? C.y : C.x, odd ? C.w : C.z, 0.f);
-          const int jg = cj0 + jj;
+        // Diagonal tile (or subset targets): the same pair loop with the self
+        // source's term dropped by index.
+        const int npairs = (len + 1) >> 1;
+        for (int pp = jl; pp < npairs; pp += SW) {
+          const float4 A = sp[3 * pp];
+          const float4 B = sp[3 * pp + 1];
+          const float4 C = sp[3 * pp + 2];
+          const int jg = cj0 + 2 * pp;
 #pragma unroll
           for (int r = 0; r < I; ++r)
-            ljc_pair<POT, PRECISE, true, LIN>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r], p[r],
-                                         jg == ig[r]);
+            ljc_pair2<POT, PRECISE, LIN, true>(
+                make_float2(A.x, A.y), make_float2(A.z, A.w), make_float2(B.x, B.y),
+                make_float2(B.z, B.w), make_float2(C.x, C.y), make_float2(C.z, C.w),
+                make_float2(-xi[r], -xi[r]), make_float2(-yi[r], -yi[r]),
+                make_float2(-zi[r], -zi[r]), make_float2(qi[r], qi[r]),
+                make_float2(si[r], si[r]), make_float2(ei[r], ei[r]), pax[r], pay[r], paz[r],
+                ppt[r], jg == ig[r], jg + 1 == ig[r]);
         }
       }
     } else if (PK) {
@@ -470,17 +487,21 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
                                      paz[r], ppt[r]);
         }
       } else {
-        // Diagonal tile: one source at a time from the pair layout, self masked.
-        for (int jj = jl; jj < len; jj += SW) {
-          const float4 A = sp[2 * (jj >> 1)];
-          const float4 B = sp[2 * (jj >> 1) + 1];
-          const bool odd = jj & 1;
-          const float4 pj = make_float4(odd ? A.y : A.x, odd ? A.w : A.z, odd ? B.y : B.x,
-                                        odd ? B.w : B.z);
-          const int jg = cj0 + jj;
+        // Diagonal tile (or subset targets): the same pair loop with the self
+        // source's term dropped by index.
+        const float2 e2 = make_float2(eps2, eps2);
+        const int npairs = (len + 1) >> 1;
+        for (int pp = jl; pp < npairs; pp += SW) {
+          const float4 A = sp[2 * pp];
+          const float4 B = sp[2 * pp + 1];
+          const int jg = cj0 + 2 * pp;
 #pragma unroll
           for (int r = 0; r < I; ++r)
-            grav_pair<POT, PRECISE, true>(pj, xi[r], yi[r], zi[r], eps2, p[r], jg == ig[r]);
+            grav_pair2<POT, PRECISE, true>(
+                make_float2(A.x, A.y), make_float2(A.z, A.w), make_float2(B.x, B.y),
+                make_float2(B.z, B.w), make_float2(-xi[r], -xi[r]), make_float2(-yi[r], -yi[r]),
+                make_float2(-zi[r], -zi[r]), e2, pax[r], pay[r], paz[r], ppt[r], jg == ig[r],
+                jg + 1 == ig[r]);
         }
       }
     } else if (!T::kPrm || cur_law == kLawGrav) {
@@ -550,7 +571,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
 #pragma unroll
     for (int r = 0; r < I; ++r) {
       if (PK) {
-        // the diagonal (masked) tiles of the packed path accumulate in p
+        // packed partial sums (diagonal tiles included) into the tile partial p
         p[r].x += pax[r].x + pax[r].y;
         p[r].y += pay[r].x + pay[r].y;
         p[r].z += paz[r].x + paz[r].y;
