@@ -200,7 +200,8 @@ def save_cache(law: int, table: dict, path: str = CACHE):
     import torch
     data = json.load(open(path)) if os.path.exists(path) else {}
     key = _gpu_key(torch)
-    data.setdefault(key, {})[str(law)] = table
+    # merge: buckets not re-tuned now keep their stored entries
+    data.setdefault(key, {}).setdefault(str(law), {}).update(table)
     with open(path, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)
 
