@@ -412,8 +412,37 @@ def _device_ms(torch, fn, reps=5):
     return float(np.median(ts))
 
 
+def _graph_ms(torch, fn, calls=10, reps=5):
+    """Device milliseconds per call with the calls replayed from a CUDA graph (no
+    host launch overhead between them): warm up on the capture stream, capture
+    `calls` calls, replay."""
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        for _ in range(3):
+            fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        for _ in range(calls):
+            fn()
+    g.replay()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b) / calls)
+    return float(np.median(ts))
+
+
 def secondary_kernel_extras(nb, torch, dev, pos, eps):
-    """Throughput of the other force forms on the same GPU (device time per call):
+    """Throughput of the other force forms on the same GPU (device time per call,
+    and for the 8192-atom cases also per call replayed from a CUDA graph, which
+    removes the host launch overhead that dominates calls this small):
     LJ + Coulomb (constant and linear dielectric) on the 8192-atom sphere;
     acceleration + jerk, a Hermite step, an active subset of 1024 targets and the
     fixed-point mode on the N = 262144 Plummer sphere."""
@@ -426,8 +455,11 @@ def secondary_kernel_extras(nb, torch, dev, pos, eps):
                       torch.from_numpy(st.astype(np.float64)[s.types]).to(dev),
                       torch.from_numpy(et.astype(np.float64)[s.types]).to(dev),
                       torch.from_numpy(s.types).to(dev), kq=332.0637 / 80.0)
+    lacc = torch.empty_like(lpos)
     ms = _device_ms(torch, lambda: nb.forces(lpos, prm))
     out["ljc_8192_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
+    ms = _graph_ms(torch, lambda: nb.forces(lpos, prm, out=lacc))
+    out["ljc_8192_graph_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
     n = pos.shape[0]
     vel = torch.zeros_like(pos)
     ms = _device_ms(torch, lambda: nb.forces_jerk(pos, vel, eps=eps), reps=3)
@@ -444,12 +476,16 @@ def secondary_kernel_extras(nb, torch, dev, pos, eps):
                           torch.from_numpy(s.types).to(dev), kq=332.0637 / 4.0)
     ms = _device_ms(torch, lambda: nb.forces(lpos, prm_lin, law=nb.LAW_LJC_LINEAR))
     out["ljc_linear_8192_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
+    ms = _graph_ms(torch, lambda: nb.forces(lpos, prm_lin, law=nb.LAW_LJC_LINEAR, out=lacc))
+    out["ljc_linear_8192_graph_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
     lam = torch.randn_like(lpos)
     lgx, lgm = torch.empty_like(lpos), torch.empty(lpos.shape[0], device=dev)
     lgt = torch.zeros(8, dtype=torch.float64, device=dev)
-    ms = _device_ms(torch, lambda: nb.adjoint(lpos, lam, prm, grad_x=lgx, grad_m=lgm,
-                                               grad_types=lgt))
+    vjp = lambda: nb.adjoint(lpos, lam, prm, grad_x=lgx, grad_m=lgm, grad_types=lgt)  # noqa: E731
+    ms = _device_ms(torch, vjp)
     out["ljc_vjp_8192_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
+    ms = _graph_ms(torch, vjp)
+    out["ljc_vjp_8192_graph_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
     hp, hv = pos.clone(), vel.clone()
     ha, hj = torch.empty_like(pos), torch.empty_like(pos)
     nb.hermite_step(hp, hv, ha, hj, dt=DT, nsteps=0, eps=eps)

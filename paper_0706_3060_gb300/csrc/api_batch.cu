@@ -227,13 +227,15 @@ int nbody_batch_plan_create(const nbody_system *systems, int32_t nsys, uint32_t 
       return set_error_msg(NBODY_EINVAL, "systems %d and %d overlap", order[k - 1], order[k]);
   }
 
-  // Work list: one item per (system, i-tile, j-slice). j-slices only where an
-  // item would exceed the average work per persistent CTA by a wide margin.
+  // Work list: one item per (system, i-tile, j-slice). Items are cut to about
+  // 1/16 of the average work per persistent CTA, so that the last items leave
+  // little imbalance (measured on the 512-system ensemble: kernel 595 us with
+  // 1/4, 577 us with 1/8, 561 us with 1/16; the finalize grows with the slices).
   const int occ = td->occupancy();
   const int grid = sms * occ;
   double work = 0.0;
   for (int k = 0; k < nsys; ++k) work += double(systems[k].n) * double(systems[k].n);
-  const double target = std::max(work / (double(grid) * 4.0), double(td->tile_i) * td->jt);
+  const double target = std::max(work / (double(grid) * 16.0), double(td->tile_i) * td->jt);
   std::vector<WorkItem> items;
   std::vector<SysInfo> info(nsys);
   std::vector<int4> sysp(nsys);
