@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 N_BENCH = 262144
 DT = 1e-4
 OPS_PER_PAIR = 12          # FP32 lane ops per pair of the plain gravity kernel (no potential)
+PAPER_FLOPS_PER_PAIR = 19  # the paper's flop count per gravity interaction (Table 1, Appendix)
 FP32_LANES_PER_SM = 128    # FFMA/FADD/FMUL lanes per SM per clock (4 SMSPs x 32)
 SM_MAX_MHZ = 2070.0
 CPU_SAMPLE_TARGETS = 131072  # oracle sample: targets x all N sources (~10 s on 16 cores)
@@ -274,6 +275,7 @@ def main():
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded Plummer sphere)", "config": config(world),
            "roofline": roof, "clocks": clk, "gpu_launches": per_step * K,
+           "paper_convention_gflops": paper_gflops(value),
            "wall_s_timed_region": t_wall}
 
     # end to end through the C ABI with pinned host buffers (copies inside)
@@ -308,6 +310,12 @@ def main():
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def paper_gflops(gpairs_per_s: float) -> float:
+    """Interactions per second in the paper's convention (19 flops per gravity
+    interaction, rsqrt counted as one), for comparison with Table 1."""
+    return PAPER_FLOPS_PER_PAIR * gpairs_per_s
 
 
 def aggregate(t_local: float, pairs_per_step: float, steps: int, world: int, device):
@@ -594,7 +602,27 @@ def batched_extras(nb, torch, dev, nsys=512, steps=50):
                 nb.step(p, v, a, q, dt=t["dt"], nsteps=steps)
 
     t_s = _time(torch, per_system, reps=1)
+    # accuracy beside the rate: forces of every 32nd system against the FP64 oracle
+    import oracle
+    pos.copy_(p0)
+    plan.run(pos, vel, acc, prm, nsteps=0, graph=False)
+    a = acc.cpu().numpy()
+    worst_rms = worst_max = 0.0
+    for k in range(0, nsys, 32):
+        s, t = ens.systems[k], table[k]
+        if isinstance(s, workloads.GravInput):
+            xs, _, ms = s.f32_as_f64()
+            ref = oracle.grav_accel(xs, ms, eps=t["eps"])
+        else:
+            xs, _, ms, q, st, et = s.f32_as_f64()
+            ref = oracle.LJCSystem(ms, q, s.types, st, et, 332.0637 / 80.0).accel(xs)
+        got = a[t["offset"]:t["offset"] + t["n"], :3]
+        e = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        worst_rms = max(worst_rms, float(np.sqrt(np.mean(e * e))))
+        worst_max = max(worst_max, float(e.max()))
     return {"batched_systems": nsys, "batched_steps": steps,
+            "batched_force_err_rms_worst": worst_rms, "batched_force_err_max_worst": worst_max,
+            "batched_force_err_sample": f"systems 0, 32, ..., {nsys - 32} vs FP64 oracle",
             "batched_system_steps_per_s": nsys * steps / t_b,
             "batched_gpairs_per_s": pairs / t_b / 1e9,
             "per_system_launch_system_steps_per_s": nsys * steps / t_s,
@@ -626,9 +654,41 @@ def adjoint_extras(nb, torch, dev, n=16384, steps=200, k=20):
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         best_f, best_b = min(best_f, t1 - t0), min(best_b, t2 - t1)
-    return {"adjoint_n": n, "adjoint_steps": steps, "adjoint_checkpoint_every": k,
-            "adjoint_forward_s": best_f, "adjoint_backward_s": best_b,
-            "adjoint_forward_ratio": best_b / best_f}
+    out = {"adjoint_n": n, "adjoint_steps": steps, "adjoint_checkpoint_every": k,
+           "adjoint_forward_s": best_f, "adjoint_backward_s": best_b,
+           "adjoint_forward_ratio": best_b / best_f}
+    out.update(adjoint_accuracy(torch, dev))
+    return out
+
+
+def adjoint_accuracy(torch, dev, n=1024, steps=60, k=20, dt=1e-4):
+    """The same reverse leapfrog at a size the FP64 oracle finishes in a second:
+    relative L2 error of dL/dx0, dL/dv0, dL/dm against the oracle's adjoint."""
+    import oracle
+    import workloads
+    from paper_0706_3060_gb300.autograd import leapfrog
+    g = workloads.plummer(n, seed=4, eps=0.01)
+    x, v, m = g.f32()
+    xd, vd, md = g.f32_as_f64()
+    eps = float(np.float32(g.eps))
+    target = workloads.perturbed_target(xd, seed=4)
+    x0 = torch.from_numpy(x).to(dev).requires_grad_(True)
+    v0 = torch.from_numpy(v).to(dev).requires_grad_(True)
+    m0 = torch.from_numpy(m).to(dev).requires_grad_(True)
+    xT, _ = leapfrog(x0, v0, m0, dt=dt, nsteps=steps, k=k, eps=eps)
+    loss = ((xT - torch.from_numpy(target.astype(np.float32)).to(dev)) ** 2).sum() / n
+    loss.backward()
+    sysm = oracle.GravSystem(md, eps=eps)
+    xs, _ = oracle.leapfrog(sysm, xd, vd, dt, steps, store=True)
+    ref = oracle.adjoint_leapfrog(sysm, xd, vd, dt, steps,
+                                  oracle.target_loss_grad(xs[-1], target), xs=xs)
+
+    def rel(got, want):
+        return float(np.linalg.norm(got.detach().cpu().numpy() - want) / np.linalg.norm(want))
+    return {"adjoint_grad_err_x0": rel(x0.grad, ref["x0"]),
+            "adjoint_grad_err_v0": rel(v0.grad, ref["v0"]),
+            "adjoint_grad_err_m": rel(m0.grad, ref["m"]),
+            "adjoint_grad_err_case": f"Plummer N = {n}, {steps} steps, k = {k}, vs FP64 oracle"}
 
 
 if __name__ == "__main__":
