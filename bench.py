@@ -150,7 +150,7 @@ def run_reference(args):
            "unit": "G pair-interactions/s", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": config(args.gpus),
+           "data": "synthetic (seeded Plummer sphere)", "config": config(args.gpus),
            "cpu_baseline": {"value": val, "unit": "G pair-interactions/s", "cores": cores,
                             "kind": "oracle",
                             "sample": f"{n_t} seeded targets x all {N_BENCH} sources per step"},

@@ -70,8 +70,8 @@ def build_case(name, nb, torch, dev):
         pos, _, eps = _grav(nb, torch, dev, 262144)
         acc = torch.empty_like(pos)
         return lambda: nb.forces(pos, eps=eps, out=acc)
-    if name == "ljc8192":
-        pos, prm = _ljc(nb, torch, dev, 8192)
+    if name in ("ljc8192", "ljc65536"):
+        pos, prm = _ljc(nb, torch, dev, int(name[3:]))
         acc = torch.empty_like(pos)
         return lambda: nb.forces(pos, prm, out=acc)
     if name == "vjp16384":
@@ -94,8 +94,8 @@ def build_case(name, nb, torch, dev):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["grav262144", "ljc8192", "vjp16384", "jerk262144",
-                                     "batched512"])
+    ap.add_argument("case", choices=["grav262144", "ljc8192", "ljc65536", "vjp16384",
+                                     "jerk262144", "batched512"])
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--iters", type=int, default=2)
     a = ap.parse_args()
