@@ -19,6 +19,9 @@ const TileDesc *ljc_tiles(int *count) {
       TileImpl<kLawLJC, 128, 2, 4, 256, true>::desc(),   // 9: packed, 64 targets, 4 j-lanes
       TileImpl<kLawLJC, 128, 2, 2, 256, true>::desc(),   // 10: packed, 128 targets, 2 j-lanes
       TileImpl<kLawLJC, 64, 2, 8, 256, true>::desc(),    // 11: packed, 16 targets, 8 j-lanes
+      // as 10 and 9 with registers capped for 3 CTAs per SM (more warps at small N)
+      TileImpl<kLawLJC, 128, 2, 2, 256, true, 2, 3>::desc(),  // 12: 128 targets, 2 j-lanes
+      TileImpl<kLawLJC, 128, 2, 4, 256, true, 2, 3>::desc(),  // 13: 64 targets, 4 j-lanes
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;

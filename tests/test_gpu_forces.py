@@ -142,7 +142,7 @@ def test_ljc_forces(n):
     assert np.sqrt(np.mean(e * e)) <= 1e-5 and e.max() <= 1e-4
 
 
-@pytest.mark.parametrize("tile", range(12))
+@pytest.mark.parametrize("tile", range(14))
 def test_ljc_every_tile(tile):
     nb = lib()
     s = workloads.ljc_sphere(1500, seed=9)
