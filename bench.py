@@ -363,6 +363,19 @@ def extras(nb, torch, dev, g, eps):
     ex["force_err_rms"] = float(np.sqrt(np.mean(e * e)))
     ex["force_err_max"] = float(e.max())
     ex["force_err_sample"] = "1024 seeded targets vs FP64 oracle"
+    ex["default_mode"] = "hardware rsqrt, compensated per-tile sums"
+    # the other precision modes on the same targets: Newton-refined rsqrt, plain
+    # FP32 sums, 64-bit fixed-point sums (error and device time per evaluation)
+    out_acc = torch.empty_like(pos)
+    for name, kw in (("precise_rsqrt", {"precise": True}),
+                     ("uncompensated", {"compensated": False}),
+                     ("fixed_point", {"fixed": True})):
+        am = nb.forces(pos, eps=eps, **kw).cpu().numpy()
+        em = np.linalg.norm(am[idx, :3] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        ms = _device_ms(torch, lambda: nb.forces(pos, eps=eps, out=out_acc, **kw), reps=3)
+        ex[f"{name}_err_rms"] = float(np.sqrt(np.mean(em * em)))
+        ex[f"{name}_err_max"] = float(em.max())
+        ex[f"{name}_262144_gpairs_per_s"] = float(N_BENCH) ** 2 / ms / 1e6
     # energy drift over 100 steps at dt = 1e-4 (FP64 diagnostics on the GPU)
     vel = torch.from_numpy(np.concatenate([v, np.zeros((N_BENCH, 1), np.float32)], 1)).to(dev)
     a2 = torch.empty_like(pos)
@@ -476,8 +489,6 @@ def secondary_kernel_extras(nb, torch, dev, pos, eps):
                            .astype(np.int32)).to(dev)
     ms = _device_ms(torch, lambda: nb.forces_subset(pos, idx, eps=eps))
     out["subset_1024_of_262144_gpairs_per_s"] = 1024.0 * n / ms / 1e6
-    ms = _device_ms(torch, lambda: nb.forces(pos, eps=eps, fixed=True), reps=3)
-    out["fixed_point_262144_gpairs_per_s"] = float(n) ** 2 / ms / 1e6
     prm_lin = nb.pack_ljc(torch.from_numpy(q.astype(np.float64)).to(dev),
                           torch.from_numpy(st.astype(np.float64)[s.types]).to(dev),
                           torch.from_numpy(et.astype(np.float64)[s.types]).to(dev),
