@@ -304,7 +304,10 @@ def main():
                                "single_thread_sample": (f"{CPU_SAMPLE_TARGETS_1T} targets, "
                                                         f"{dt1:.1f} s")}
     if not args.no_extras and rank == 0:
-        out["extras"] = extras(nb, torch, dev, g, eps)
+        try:
+            out["extras"] = extras(nb, torch, dev, g, eps)
+        except Exception as exc:  # the headline line still prints; the failure is reported
+            out["extras"] = {"error": repr(exc)}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
