@@ -6,6 +6,7 @@ C ABI of ``include/nbody.h``); this package only marshals torch tensors into
 that ABI. There is no CPU fallback: calls raise if the library is not built.
 """
 from . import _lib
+from .checkpoint import load_state, save_state
 from ._lib import (ACC_VALID, ACCUMULATE, COMPUTE_POT, FIXED_POINT, LAW_GRAV, LAW_LJC,
                    LAW_LJC_LINEAR, NO_COMPENSATION, PRECISE_RSQRT, TABLE_BATCHED,
                    TABLE_GRAV_FIXED, TABLE_JERK, TABLE_VJP_GRAV, TABLE_VJP_LJC, NBodyError)
@@ -21,5 +22,5 @@ __all__ = [
     "PRECISE_RSQRT", "NBodyError", "COULOMB_K", "BatchPlan", "adjoint", "adjoint_leapfrog",
     "forces", "forces_batched", "forces_jerk", "forces_subset", "hermite_step", "get_config", "pack_grav", "pack_ljc", "params", "release",
     "set_tuned", "step", "sync_check", "tile_count", "tile_info", "timing_enable",
-    "timing_read", "tune_table", "version",
+    "timing_read", "tune_table", "version", "save_state", "load_state",
 ]

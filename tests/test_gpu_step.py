@@ -62,6 +62,31 @@ def test_resume_and_acc_valid_equivalence():
     assert torch.equal(p1, p2) and torch.equal(v1, v2) and torch.equal(a1, a2)
 
 
+def test_resume_from_state_file(tmp_path):
+    """5 steps, state saved to a file and loaded into fresh tensors, 5 more steps:
+    bitwise equal to 10 uninterrupted steps (two-float state included)."""
+    nb = lib()
+    g = workloads.plummer(2000, seed=12, eps=0.01)
+    eps = float(np.float32(g.eps))
+    p1, v1 = grav_tensors(g)
+    a1 = torch.empty_like(p1)
+    lo1 = torch.zeros((2 * 2000, 4), device=dev())
+    nb.step(p1, v1, a1, dt=1e-3, nsteps=10, eps=eps, state_lo=lo1)
+    p2, v2 = grav_tensors(g)
+    a2 = torch.empty_like(p2)
+    lo2 = torch.zeros_like(lo1)
+    nb.step(p2, v2, a2, dt=1e-3, nsteps=5, eps=eps, state_lo=lo2)
+    f = tmp_path / "state.npz"
+    nb.save_state(f, p2, v2, a2, step=5, params={"dt": 1e-3, "eps": eps}, state_lo=lo2)
+    st = nb.load_state(f, device=dev())
+    assert st["step"] == 5
+    p3, v3, a3, lo3 = st["pos_m"], st["vel"], st["acc"], st["state_lo"]
+    nb.step(p3, v3, a3, dt=st["params"]["dt"], nsteps=5, eps=st["params"]["eps"],
+            acc_valid=True, state_lo=lo3)
+    assert torch.equal(p1, p3) and torch.equal(v1, v3) and torch.equal(a1, a3)
+    assert torch.equal(lo1, lo3)
+
+
 def test_trace_holds_every_position():
     nb = lib()
     g = workloads.plummer(700, seed=12, eps=0.02)

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -114,3 +115,20 @@ def test_tune_rejects_bad_arguments_without_gpu(lib):
     assert lib.nbody_tune(1, ctypes.c_void_p(16), None, 1024, 0.0, 3, *args) == 1  # LJC: prm
     assert lib.nbody_tune(4, ctypes.c_void_p(16), None, 1024, 0.0, 3, *args) == 1  # eps2 > 0
     assert t.value == -7 and j.value == -7  # nothing written on error
+
+
+def test_state_file_round_trip(tmp_path):
+    import torch
+
+    from paper_0706_3060_gb300.checkpoint import load_state, save_state
+    rng = np.random.default_rng(0)
+    pos = torch.from_numpy(rng.standard_normal((7, 4)).astype(np.float32))
+    vel = torch.from_numpy(rng.standard_normal((7, 4)).astype(np.float32))
+    acc = torch.from_numpy(rng.standard_normal((7, 4)).astype(np.float32))
+    lo = torch.from_numpy(rng.standard_normal((14, 4)).astype(np.float32))
+    f = tmp_path / "run.npz"
+    save_state(f, pos, vel, acc, step=42, params={"dt": 1e-3, "eps": 0.01}, state_lo=lo)
+    st = load_state(f, device=torch.device("cpu"))
+    assert st["step"] == 42 and st["params"] == {"dt": 1e-3, "eps": 0.01}
+    for k, t in (("pos_m", pos), ("vel", vel), ("acc", acc), ("state_lo", lo)):
+        assert torch.equal(st[k], t)
