@@ -267,6 +267,7 @@ int nbody_pack_ljc(const double *q, const double *sigma, const double *eps, cons
 int nbody_forces(const void *pos_m, const void *prm, void *acc, void *acc_lo, int64_t n,
                  const nbody_params *params, nbody_stream_t stream) {
   clear_error();
+  const NvtxRange nvtx_range("nbody_forces");
   if (n < 0 || n > kMaxN) return set_error_msg(NBODY_EINVAL, "n out of range: %lld", (long long)n);
   if (!params) return set_error_msg(NBODY_EINVAL, "params is NULL");
   if (n == 0) return NBODY_OK;
@@ -307,6 +308,7 @@ int nbody_step(void *pos_m, void *vel, void *acc, const void *prm, int64_t n, fl
                int32_t nsteps, int32_t report_every, double *diag, void *trace, void *state_lo,
                const nbody_params *params, nbody_stream_t stream) {
   clear_error();
+  const NvtxRange nvtx_range("nbody_step");
   if (n < 0 || n > kMaxN) return set_error_msg(NBODY_EINVAL, "n out of range: %lld", (long long)n);
   if (nsteps < 0) return set_error_msg(NBODY_EINVAL, "nsteps must be >= 0");
   if (report_every < 0) return set_error_msg(NBODY_EINVAL, "report_every must be >= 0");

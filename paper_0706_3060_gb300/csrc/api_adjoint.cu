@@ -282,6 +282,7 @@ int nbody_adjoint(const void *pos_m, const void *prm, const void *lam, void *gra
                   float *grad_m, double *grad_types, int32_t ntypes, float alpha, int64_t n,
                   const nbody_params *params, nbody_stream_t stream) {
   clear_error();
+  const NvtxRange nvtx_range("nbody_adjoint");
   NB_TRY(check_common(params, pos_m, prm, n, ntypes, grad_types));
   NB_TRY(check_dev(pos_m, "pos_m", true));
   NB_TRY(check_dev(lam, "lam", true));
@@ -313,6 +314,7 @@ int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k
                            double *grad_types, int32_t ntypes, const nbody_params *params,
                            nbody_stream_t stream) {
   clear_error();
+  const NvtxRange nvtx_range("nbody_adjoint_leapfrog");
   NB_TRY(check_common(params, xs, prm, n, ntypes, grad_types));
   if (k < 0) return set_error_msg(NBODY_EINVAL, "k must be >= 0");
   if (!std::isfinite(dt)) return set_error_msg(NBODY_EINVAL, "dt must be finite");
@@ -347,6 +349,7 @@ int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k
 int nbody_forces_jerk(const void *pos_m, const void *vel, void *acc, void *jerk, int64_t n,
                       const nbody_params *params, nbody_stream_t stream) {
   clear_error();
+  const NvtxRange nvtx_range("nbody_forces_jerk");
   NB_TRY(check_jerk_params(params, 0));
   if (n < 0 || n > 0x7fffffffLL) return set_error_msg(NBODY_EINVAL, "n out of range");
   if (n == 0) return NBODY_OK;
@@ -367,6 +370,7 @@ int nbody_forces_jerk(const void *pos_m, const void *vel, void *acc, void *jerk,
 int nbody_hermite_step(void *pos_m, void *vel, void *acc, void *jerk, int64_t n, float dt,
                        int32_t nsteps, const nbody_params *params, nbody_stream_t stream) {
   clear_error();
+  const NvtxRange nvtx_range("nbody_hermite_step");
   NB_TRY(check_jerk_params(params, NBODY_ACC_VALID));
   if (n < 0 || n > 0x7fffffffLL) return set_error_msg(NBODY_EINVAL, "n out of range");
   if (nsteps < 0) return set_error_msg(NBODY_EINVAL, "nsteps must be >= 0");

@@ -334,6 +334,7 @@ int64_t nbody_batch_plan_particles(const nbody_batch_plan *plan) {
 int nbody_batch_run(nbody_batch_plan *plan, void *pos_m, void *vel, void *acc, const void *prm,
                     int32_t nsteps, uint32_t flags, int32_t use_graph, nbody_stream_t stream) {
   clear_error();
+  const NvtxRange nvtx_range("nbody_batch_run");
   if (!plan) return set_error_msg(NBODY_EINVAL, "plan is NULL");
   if (nsteps < 0) return set_error_msg(NBODY_EINVAL, "nsteps must be >= 0");
   if (flags & ~(uint32_t)NBODY_ACC_VALID)
@@ -399,6 +400,7 @@ int nbody_forces_batched(const nbody_system *systems, int32_t nsys, void *pos_m,
                          void *acc, const void *prm, int32_t nsteps, uint32_t flags,
                          nbody_stream_t stream) {
   clear_error();
+  const NvtxRange nvtx_range("nbody_forces_batched");
   nbody_batch_plan *p = nullptr;
   NB_TRY(nbody_batch_plan_create(systems, nsys,
                                  flags & (NBODY_PRECISE_RSQRT | NBODY_NO_COMPENSATION), -1, &p));

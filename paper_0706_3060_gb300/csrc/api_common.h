@@ -11,10 +11,21 @@
 #include <mutex>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nbody.h"
 #include "tiles.h"
 
 namespace nbody {
+
+// NVTX range over one C-ABI call, for timeline profilers and ncu's --nvtx
+// filters (a no-op unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 int set_error_msg(int code, const char *fmt, ...);
 void clear_error();

@@ -38,6 +38,7 @@ extern "C" int nbody_forces_subset(const void *pos_m, const void *prm, const int
                                    int64_t n_active, void *acc, int64_t n,
                                    const nbody_params *params, nbody_stream_t stream) {
   clear_error();
+  const NvtxRange nvtx_range("nbody_forces_subset");
   if (!params) return set_error_msg(NBODY_EINVAL, "params is NULL");
   if (n < 0 || n > 0x7fffffffLL || n_active < 0 || n_active > 0x7fffffffLL)
     return set_error_msg(NBODY_EINVAL, "n or n_active out of range");

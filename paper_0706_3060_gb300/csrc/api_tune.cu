@@ -57,6 +57,7 @@ int nbody_tune(int32_t table, const void *pos_m, const void *prm, int64_t n, flo
                int32_t reps, int32_t *best_tile, int32_t *best_jsplit, float *best_ms,
                nbody_stream_t stream) {
   clear_error();
+  const NvtxRange nvtx_range("nbody_tune");
   if (table < 0 || table >= kTables || table == kTableBatched)
     return set_error_msg(NBODY_EUNSUPPORTED, "table %d is not tuned by nbody_tune", table);
   if (n < 1 || n > 0x7fffffffLL) return set_error_msg(NBODY_EINVAL, "n out of range");
