@@ -210,3 +210,27 @@ def test_adjoint_workload_size_one_chunk():
     assert _rel(gx, ref["x0"]) <= 1e-4
     assert _rel(gv, ref["v0"]) <= 1e-4
     assert _rel(gm, ref["m"]) <= 1e-3
+
+
+def test_every_family_bitwise_repeatable():
+    """Fixed-order reductions: the same call twice gives identical bits for the
+    LJC forces, both VJPs and acceleration + jerk (a race in a ring stage or a
+    reduction would show up here)."""
+    nb = lib()
+    s = workloads.ljc_sphere(3000, seed=72)
+    lpos, _, prm = ljc_tensors(s)
+    g = workloads.plummer(5000, seed=73, eps=0.01)
+    pos, vel = grav_tensors(g)
+    lam = torch.randn((5000, 4), device=dev())
+    llam = torch.randn((3000, 4), device=dev())
+    runs = [
+        lambda: (nb.forces(lpos, prm),),
+        lambda: nb.adjoint(lpos, llam, prm)[:2],
+        lambda: nb.adjoint(pos, lam, eps=0.01)[:2],
+        lambda: nb.forces_jerk(pos, vel, eps=0.01),
+    ]
+    for k, fn in enumerate(runs):
+        a = [t.clone() for t in fn()]
+        b = [t.clone() for t in fn()]
+        for u, w in zip(a, b):
+            assert torch.equal(u, w), k
