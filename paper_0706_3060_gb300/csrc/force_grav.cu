@@ -28,6 +28,11 @@ const TileDesc *grav_tiles(int *count) {
       TileImpl<kLawGrav, 128, 2, 4, 256, true>::desc(),  // 16: 64 targets, 4 j-lanes
       TileImpl<kLawGrav, 128, 2, 2, 256, true>::desc(),  // 17: 128 targets, 2 j-lanes
       TileImpl<kLawGrav, 64, 2, 8, 256, true>::desc(),   // 18: 16 targets, 8 j-lanes
+      // finer items for mid N (more CTAs, fuller last wave), pair loop unrolled x4
+      TileImpl<kLawGrav, 64, 2, 1, 512, true, 4>::desc(),    // 19: 128 targets, 1 warp
+      TileImpl<kLawGrav, 64, 4, 1, 512, true, 4>::desc(),    // 20: 256 targets, 1 warp
+      TileImpl<kLawGrav, 128, 2, 2, 512, true, 4>::desc(),   // 21: 128 targets, 2 j-lanes
+      TileImpl<kLawGrav, 256, 1, 1, 512, true, 4>::desc(),   // 22: 256 targets, 1 each
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;
