@@ -346,6 +346,17 @@ int nbody_tile_info(int32_t law, int32_t tile, int32_t *threads, int32_t *i_per_
 int nbody_set_tuned(int32_t law, int32_t log2n, int32_t tile, int32_t jsplit);
 /* Query the configuration a call with (law, n) and tile == -1 would use. */
 int nbody_get_config(int32_t law, int64_t n, int32_t *tile, int32_t *jsplit);
+/* Device scratch bytes a call of nbody_forces / nbody_step with these params
+ * and n requests from the library's per-(device, stream) workspace: the
+ * pair-interleaved source copy of packed tiles, the per-slice partial sums and
+ * (nbody_step with report_every) `report_rows` rows of diagnostics. The arena
+ * grows to the largest request and is reused; a call made while a stream is
+ * being captured into a CUDA graph must not need more than that stream already
+ * holds (run it once uncaptured first). Needs the device (the j-split depends
+ * on its SM count). The paper has no counterpart (it keeps everything in GPU
+ * textures). */
+int nbody_workspace_size(const nbody_params *params, int64_t n, int32_t report_rows,
+                         size_t *bytes);
 /* Autotune tile table `table` at size n on the caller's device inputs (the
  * paper tunes its unrolling by hand, Sec. 3.3; this searches the compiled
  * configurations instead). Every tile x j-split in {0 (auto), 1, 2, 4, 8, 16,

@@ -13,7 +13,8 @@ from ._lib import (ACC_VALID, ACCUMULATE, COMPUTE_POT, FIXED_POINT, LAW_GRAV, LA
 from .api import (COULOMB_K, BatchPlan, adjoint, adjoint_leapfrog, forces, forces_batched,
                   forces_jerk, forces_subset, hermite_step,
                   get_config, pack_grav, pack_ljc, params, release, set_tuned, step, sync_check,
-                  tile_count, tile_info, timing_enable, timing_read, tune_table, version)
+                  tile_count, tile_info, timing_enable, timing_read, tune_table, version,
+                  workspace_size)
 
 __all__ = [
     "ACC_VALID", "ACCUMULATE", "COMPUTE_POT", "LAW_GRAV", "LAW_LJC", "LAW_LJC_LINEAR",
@@ -22,5 +23,5 @@ __all__ = [
     "PRECISE_RSQRT", "NBodyError", "COULOMB_K", "BatchPlan", "adjoint", "adjoint_leapfrog",
     "forces", "forces_batched", "forces_jerk", "forces_subset", "hermite_step", "get_config", "pack_grav", "pack_ljc", "params", "release",
     "set_tuned", "step", "sync_check", "tile_count", "tile_info", "timing_enable",
-    "timing_read", "tune_table", "version", "save_state", "load_state",
+    "timing_read", "tune_table", "version", "save_state", "load_state", "workspace_size",
 ]

@@ -42,7 +42,7 @@ EXPORTS = (
     "nbody_tile_count", "nbody_tile_info", "nbody_set_tuned", "nbody_get_config",
     "nbody_timing_enable", "nbody_timing_read", "nbody_peak_probe", "nbody_forces_static",
     "nbody_forces_subset", "nbody_forces_jerk", "nbody_hermite_step", "nbody_selftest_timeout",
-    "nbody_tune",
+    "nbody_tune", "nbody_workspace_size",
 )
 
 
@@ -122,6 +122,8 @@ def load(path: str | None = None):
                                  ctypes.c_int),
             "nbody_tune": ([i32, vp, vp, i64, f32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
                             ctypes.POINTER(f32), vp], ctypes.c_int),
+            "nbody_workspace_size": ([pp, i64, i32, ctypes.POINTER(ctypes.c_size_t)],
+                                     ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)

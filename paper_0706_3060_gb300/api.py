@@ -327,6 +327,17 @@ def get_config(law: int, n: int) -> tuple[int, int]:
     return t.value, j.value
 
 
+def workspace_size(n: int, *, law=LAW_GRAV, eps=0.0, tile=-1, jsplit=0, fixed=False,
+                   report_rows=0) -> int:
+    """Device scratch bytes a forces/step call with these settings requests from
+    the library's per-stream workspace (nbody_workspace_size)."""
+    b = ctypes.c_size_t()
+    p = params(law, 1.0, eps, tile=tile, jsplit=jsplit, fixed=fixed)
+    check(_lib().nbody_workspace_size(ctypes.byref(p), int(n), int(report_rows), ctypes.byref(b)),
+          "nbody_workspace_size")
+    return b.value
+
+
 def tune_table(table: int, pos_m, prm=None, *, eps=0.01, reps=5, stream=None) -> dict:
     """Autotune tile table ``table`` at n = len(pos_m) in the library (nbody_tune):
     installs and returns the fastest (tile, jsplit) with its median milliseconds."""

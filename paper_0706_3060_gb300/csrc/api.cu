@@ -91,14 +91,22 @@ struct Scratch {
   double *diag_rows;
 };
 
-int get_scratch(cudaStream_t s, int law, int n, int slices, int diag_rows, Scratch *out) {
+// Bytes of the Scratch layout below (scale words, pair buffer, partials, diagnostics).
+size_t scratch_bytes(int law, int n, int slices, int diag_rows) {
   const size_t part = round_up(size_t(slices) * size_t(n) * sizeof(float4), 256);
   const int nblk = std::max(1, (n + kFinThreads - 1) / kFinThreads);
   const size_t dpart = round_up(size_t(nblk) * kDiagFields * sizeof(double), 256);
   const size_t drows = round_up(size_t(std::max(diag_rows, 1)) * kDiagFields * sizeof(double), 256);
+  return 256 + jbuf_bytes(law, n) + 2 * part + dpart + drows;
+}
+
+int get_scratch(cudaStream_t s, int law, int n, int slices, int diag_rows, Scratch *out) {
+  const size_t part = round_up(size_t(slices) * size_t(n) * sizeof(float4), 256);
+  const int nblk = std::max(1, (n + kFinThreads - 1) / kFinThreads);
+  const size_t dpart = round_up(size_t(nblk) * kDiagFields * sizeof(double), 256);
   const size_t jb = jbuf_bytes(law, n);
   void *base = nullptr;
-  NB_TRY(workspace(s, 256 + jb + 2 * part + dpart + drows, &base));
+  NB_TRY(workspace(s, scratch_bytes(law, n, slices, diag_rows), &base));
   char *b = static_cast<char *>(base);
   out->finv = reinterpret_cast<double *>(b);
   out->fscale = reinterpret_cast<float *>(b + 8);
@@ -302,6 +310,27 @@ int nbody_forces(const void *pos_m, const void *prm, void *acc, void *acc_lo, in
   NB_CUDA(cudaMemcpyAsync(acc, d_acc, bytes, cudaMemcpyDeviceToHost, s));
   if (acc_lo) NB_CUDA(cudaMemcpyAsync(acc_lo, d_lo, bytes, cudaMemcpyDeviceToHost, s));
   return sync_and_check(s);
+}
+
+int nbody_workspace_size(const nbody_params *params, int64_t n, int32_t report_rows,
+                         size_t *bytes) {
+  clear_error();
+  if (!bytes) return set_error_msg(NBODY_EINVAL, "bytes is NULL");
+  if (n < 0 || n > kMaxN) return set_error_msg(NBODY_EINVAL, "n out of range: %lld", (long long)n);
+  if (report_rows < 0) return set_error_msg(NBODY_EINVAL, "report_rows must be >= 0");
+  if (!params) return set_error_msg(NBODY_EINVAL, "params is NULL");
+  // prm only matters for the LJC laws' presence check: any non-null marker will do
+  NB_TRY(check_params(params, params->law == NBODY_LAW_GRAV ? nullptr : params));
+  if (n == 0) {
+    *bytes = 0;
+    return NBODY_OK;
+  }
+  int dev = 0, sms = 0;
+  NB_TRY(check_device(&dev, &sms));
+  Plan1 plan{};
+  NB_TRY(plan_single(table_of(*params), n, params->tile, params->jsplit, sms, &plan));
+  *bytes = scratch_bytes(params->law, int(n), plan.slices, report_rows);
+  return NBODY_OK;
 }
 
 int nbody_step(void *pos_m, void *vel, void *acc, const void *prm, int64_t n, float dt,

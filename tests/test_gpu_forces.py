@@ -395,3 +395,16 @@ def test_edge_cases_coincident_massless_and_far():
     accf = nb.forces(posf, eps=0.05).cpu().numpy()
     reff = oracle.grav_accel(xf.astype(np.float64), m.astype(np.float64), eps=0.05)
     assert_forces_close(accf[:, :3], reff, what="far from origin")
+
+
+def test_workspace_size_covers_the_partials():
+    """nbody_workspace_size: at least the two partial-sum arrays of the chosen
+    j-split plus the packed source copy, and growing with the j-split."""
+    nb = lib()
+    n = 4096
+    tile = 13  # packed, 256 targets per item, j-tile 512
+    w2 = nb.workspace_size(n, eps=0.01, tile=tile, jsplit=2)
+    w8 = nb.workspace_size(n, eps=0.01, tile=tile, jsplit=8)
+    assert w2 >= 2 * 2 * n * 16 + (n // 2) * 32
+    assert w8 - w2 == 2 * 6 * n * 16
+    assert nb.workspace_size(n, eps=0.01, report_rows=10) > nb.workspace_size(n, eps=0.01)

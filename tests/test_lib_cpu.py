@@ -132,3 +132,14 @@ def test_state_file_round_trip(tmp_path):
     assert st["step"] == 42 and st["params"] == {"dt": 1e-3, "eps": 0.01}
     for k, t in (("pos_m", pos), ("vel", vel), ("acc", acc), ("state_lo", lo)):
         assert torch.equal(st[k], t)
+
+
+def test_workspace_size_rejects_bad_arguments_without_gpu(lib):
+    from paper_0706_3060_gb300._lib import NBodyParams
+    p = NBodyParams(0, 0, 1.0, 1e-4, -1, 0)
+    b = ctypes.c_size_t(7)
+    assert lib.nbody_workspace_size(ctypes.byref(p), 100, 0, None) == 1
+    assert lib.nbody_workspace_size(None, 100, 0, ctypes.byref(b)) == 1
+    assert lib.nbody_workspace_size(ctypes.byref(p), -1, 0, ctypes.byref(b)) == 1
+    assert lib.nbody_workspace_size(ctypes.byref(p), 100, -1, ctypes.byref(b)) == 1
+    assert lib.nbody_workspace_size(ctypes.byref(p), 0, 0, ctypes.byref(b)) == 0 and b.value == 0
