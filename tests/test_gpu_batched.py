@@ -179,3 +179,46 @@ def test_batched_every_tile(small_ensemble, tile):
         o = table[k]["offset"]
         ex = traj_errors(pn[o:o + s.n, :3], xr)
         assert ex[0] <= 1e-6, (tile, k, ex)
+
+
+def test_batched_tiny_and_large_systems():
+    """Systems of 1, 2, 3 and 5 particles (the single one feels no force) beside
+    one of 20000 split into many j-slices, gravity and LJC, every tile."""
+    nb = lib()
+    rng = np.random.default_rng(44)
+    sizes = [1, 2, 3, 5, 20000, 3, 1]
+    gs = [workloads.plummer(n, seed=100 + k, eps=0.02) if n > 1 else None
+          for k, n in enumerate(sizes)]
+    total = sum(sizes)
+    pos = np.zeros((total, 4), np.float32)
+    table, off = [], 0
+    for k, n in enumerate(sizes):
+        if n == 1:
+            pos[off] = [rng.standard_normal(), rng.standard_normal(), 0.5, 1.0]
+        else:
+            x, _, m = gs[k].f32()
+            pos[off:off + n, :3], pos[off:off + n, 3] = x, m
+        table.append(dict(offset=off, n=n, law=nb.LAW_GRAV, eps=float(np.float32(0.02)),
+                          dt=1e-3))
+        off += n
+    d = dev()
+    p = torch.from_numpy(pos).to(d)
+    for tile in range(nb.tile_count(nb.TABLE_BATCHED)):
+        acc = torch.full_like(p, float("nan"))
+        plan = nb.BatchPlan(table, tile=tile)
+        plan.run(p, torch.zeros_like(p), acc, None, nsteps=0, graph=False)
+        a = acc.cpu().numpy()
+        for k, t in enumerate(table):
+            o, n = t["offset"], t["n"]
+            if n == 1:
+                assert np.all(a[o, :3] == 0.0), (tile, k)
+                continue
+            x, _, m = gs[k].f32_as_f64()
+            if n > 5000:
+                idx = np.sort(rng.choice(n, 512, replace=False))
+                ref = oracle.grav_accel(x, m, eps=float(np.float32(0.02)), idx=idx)
+                assert_forces_close(a[o + idx, :3], ref, what=f"tile {tile} n={n}")
+            else:
+                ref = oracle.grav_accel(x, m, eps=float(np.float32(0.02)))
+                assert_forces_close(a[o:o + n, :3], ref, what=f"tile {tile} n={n}")
+        plan.close()
