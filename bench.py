@@ -653,24 +653,31 @@ def adjoint_extras(nb, torch, dev, n=16384, steps=200, k=20):
     tgt = torch.from_numpy(workloads.perturbed_target(x.astype(np.float64), seed=4)
                            .astype(np.float32)).to(dev)
     eps = float(np.float32(g.eps))
-    best_f = best_b = float("inf")
-    for _ in range(3):
-        x0 = torch.from_numpy(x).to(dev).requires_grad_(True)
-        v0 = torch.from_numpy(v).to(dev).requires_grad_(True)
-        m0 = torch.from_numpy(m).to(dev).requires_grad_(True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        xT, _ = leapfrog(x0, v0, m0, dt=1e-4, nsteps=steps, k=k, eps=eps)
-        loss = ((xT - tgt) ** 2).sum() / n
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        loss.backward()
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        best_f, best_b = min(best_f, t1 - t0), min(best_b, t2 - t1)
+    def timed(kk):
+        best_f = best_b = float("inf")
+        for _ in range(3):
+            x0 = torch.from_numpy(x).to(dev).requires_grad_(True)
+            v0 = torch.from_numpy(v).to(dev).requires_grad_(True)
+            m0 = torch.from_numpy(m).to(dev).requires_grad_(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            xT, _ = leapfrog(x0, v0, m0, dt=1e-4, nsteps=steps, k=kk, eps=eps)
+            loss = ((xT - tgt) ** 2).sum() / n
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            loss.backward()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            best_f, best_b = min(best_f, t1 - t0), min(best_b, t2 - t1)
+        return best_f, best_b
+
+    best_f, best_b = timed(k)
+    all_f, all_b = timed(steps)  # one chunk: every position kept, nothing recomputed
     out = {"adjoint_n": n, "adjoint_steps": steps, "adjoint_checkpoint_every": k,
            "adjoint_forward_s": best_f, "adjoint_backward_s": best_b,
-           "adjoint_forward_ratio": best_b / best_f}
+           "adjoint_forward_ratio": best_b / best_f,
+           "adjoint_forward_ratio_all_positions_kept": all_b / all_f,
+           "adjoint_positions_kept_bytes": (steps + 1) * n * 16}
     out.update(adjoint_accuracy(torch, dev))
     return out
 
