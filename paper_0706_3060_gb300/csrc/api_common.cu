@@ -383,9 +383,10 @@ __global__ void interleave_ljc_pairs_kernel(const float4 *pos, const float4 *prm
   const bool two = 2 * p + 1 < n;
   const float4 b = two ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
   const float4 qb = two ? prm[2 * p + 1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  jp[3 * p] = make_float4(a.x, b.x, a.y, b.y);
-  jp[3 * p + 1] = make_float4(a.z, b.z, qa.x, qb.x);
-  jp[3 * p + 2] = make_float4(qa.y, qb.y, qa.z, qb.z);
+  const long long q = 3LL * p;  // 64-bit: 3p passes 2^31 for n above ~1.4e9
+  jp[q] = make_float4(a.x, b.x, a.y, b.y);
+  jp[q + 1] = make_float4(a.z, b.z, qa.x, qb.x);
+  jp[q + 2] = make_float4(qa.y, qb.y, qa.z, qb.z);
 }
 
 size_t jbuf_bytes(int law, int64_t n) {

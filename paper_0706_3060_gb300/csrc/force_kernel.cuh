@@ -302,7 +302,8 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
           const float4 *src = (MIX && lj) ? a.jpair2 : a.jpair;
           const uint32_t bytes = uint32_t((len + 1) >> 1) * pf4 * 16u;
           mbar_arrive_expect_tx(&full_bar[st], bytes);
-          tma_load_1d(sm_pos + st * STAGE_F4, src + (w.pj0 + ((cj0 - w.j0) >> 1)) * pf4, bytes,
+          tma_load_1d(sm_pos + st * STAGE_F4,
+                      src + size_t(w.pj0 + ((cj0 - w.j0) >> 1)) * size_t(pf4), bytes,
                       &full_bar[st]);
         } else {
           const uint32_t bytes = uint32_t(len) * 16u;

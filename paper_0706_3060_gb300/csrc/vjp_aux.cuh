@@ -176,10 +176,11 @@ __global__ void interleave_vjp_pairs_kernel(const float4 *pos, const float4 *lam
   const float4 a = pos[2 * p], la = lam[2 * p];
   const float4 b = two ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
   const float4 lb = two ? lam[2 * p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-  jp[4 * p] = make_float4(a.x, b.x, a.y, b.y);
-  jp[4 * p + 1] = make_float4(a.z, b.z, a.w, b.w);
-  jp[4 * p + 2] = make_float4(la.x, lb.x, la.y, lb.y);
-  jp[4 * p + 3] = make_float4(la.z, lb.z, 0.f, 0.f);
+  const long long q = 4LL * p;  // 64-bit: 4p passes 2^31 for n above ~1.07e9
+  jp[q] = make_float4(a.x, b.x, a.y, b.y);
+  jp[q + 1] = make_float4(a.z, b.z, a.w, b.w);
+  jp[q + 2] = make_float4(la.x, lb.x, la.y, lb.y);
+  jp[q + 3] = make_float4(la.z, lb.z, 0.f, 0.f);
 }
 
 // LJC VJP source pairs: (x x y y)(z z q q)(s s e e)(-ux -ux -uy -uy)(-uz -uz 0 0);
@@ -193,11 +194,12 @@ __global__ void interleave_ljc_vjp_pairs_kernel(const float4 *pos, const float4 
   const float4 b = two ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
   const float4 ub = two ? u[2 * p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
   const float4 qb = two ? prm[2 * p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-  jp[5 * p] = make_float4(a.x, b.x, a.y, b.y);
-  jp[5 * p + 1] = make_float4(a.z, b.z, qa.x, qb.x);
-  jp[5 * p + 2] = make_float4(qa.y, qb.y, qa.z, qb.z);
-  jp[5 * p + 3] = make_float4(-ua.x, -ub.x, -ua.y, -ub.y);
-  jp[5 * p + 4] = make_float4(-ua.z, -ub.z, 0.f, 0.f);
+  const long long q = 5LL * p;  // 64-bit: 5p passes 2^31 for n above ~8.6e8
+  jp[q] = make_float4(a.x, b.x, a.y, b.y);
+  jp[q + 1] = make_float4(a.z, b.z, qa.x, qb.x);
+  jp[q + 2] = make_float4(qa.y, qb.y, qa.z, qb.z);
+  jp[q + 3] = make_float4(-ua.x, -ub.x, -ua.y, -ub.y);
+  jp[q + 4] = make_float4(-ua.z, -ub.z, 0.f, 0.f);
 }
 
 // u = lam / m (LJC sources are weighted by 1 / m_j).

@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
         // pairs of sources, kPairF4 float4 each; stages of kStageF4 float4s
         const uint32_t bytes = uint32_t((len + 1) >> 1) * T::kPairF4 * 16u;
         mbar_arrive_expect_tx(&full_bar[st], bytes);
-        tma_load_1d(sm_pos + st * T::kStageF4, a.jpair + (cj >> 1) * T::kPairF4, bytes,
+        tma_load_1d(sm_pos + st * T::kStageF4, a.jpair + size_t(cj >> 1) * T::kPairF4, bytes,
                     &full_bar[st]);
       } else {
         const uint32_t bytes = uint32_t(len) * 16u;
