@@ -68,7 +68,11 @@ struct VjpImpl {
   X(kLawGrav, 128, 2, 1, 256, true, 2)                              \
   X(kLawGrav, 256, 1, 1, 256, true, 4)                              \
   X(kLawGrav, 128, 4, 1, 256, true, 1)                              \
-  X(kLawGrav, 128, 1, 8, 256, false, 2)
+  X(kLawGrav, 128, 1, 8, 256, false, 2)                             \
+  X(kLawGrav, 256, 1, 1, 512, true, 4)                              \
+  X(kLawGrav, 128, 1, 1, 256, true, 4)                              \
+  X(kLawGrav, 512, 1, 1, 256, true, 4)                              \
+  X(kLawGrav, 128, 2, 1, 256, true, 4)
 #define NB_VJP_LJC_ROWS(X)                                          \
   X(kLawLJC, 256, 2, 1, 256, false, 2)                              \
   X(kLawLJC, 128, 1, 4, 256, false, 2)                              \
