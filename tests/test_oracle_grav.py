@@ -141,3 +141,18 @@ def test_softening_limit():
     a0 = oracle.grav_accel(g.x, g.m, eps=0.0)
     a1 = oracle.grav_accel(g.x, g.m, eps=1e-7)
     np.testing.assert_allclose(a1, a0, rtol=1e-6, atol=1e-9)
+
+
+def test_thread_count_does_not_change_the_forces():
+    """Each target's sum runs in index order inside one thread, so the oracle's
+    forces are bitwise the same on one thread and on all of them."""
+    g = workloads.plummer(300, seed=17)
+    prev = oracle.set_threads(None)
+    try:
+        oracle.set_threads(1)
+        a1 = oracle.grav_accel(g.x, g.m, eps=0.01)
+        oracle.set_threads(max(2, prev))
+        a2 = oracle.grav_accel(g.x, g.m, eps=0.01)
+    finally:
+        oracle.set_threads(prev)
+    assert np.array_equal(a1, a2)
