@@ -76,7 +76,7 @@ def _load():
                                         i64, i64p, d, d]
             lib.oracle_ljc.argtypes = [i64, d, d, d, d, ctypes.c_double, i64, i64p, d, d]
             lib.oracle_grav_jerk.argtypes = [i64, d, d, d, ctypes.c_double, ctypes.c_double,
-                                             d, d]
+                                             i64, i64p, d, d]
             lib.oracle_grav_jerk.restype = None
             lib.oracle_ljc_model.argtypes = [i64, d, d, d, d, ctypes.c_double, ctypes.c_int,
                                              i64, i64p, d, d]
@@ -140,18 +140,21 @@ def grav_accel(x, m, G=1.0, eps=0.0, idx=None, potential=False):
     return (acc, phi) if potential else acc
 
 
-def grav_jerk(x, v, m, G=1.0, eps=0.0):
-    """Table 1 "Gravity (accel & jerk)": returns (acc (n,3), jerk (n,3)), the jerk
-    being the time derivative of the acceleration for particles moving at v."""
+def grav_jerk(x, v, m, G=1.0, eps=0.0, idx=None):
+    """Table 1 "Gravity (accel & jerk)": returns (acc (ni,3), jerk (ni,3)) on the
+    targets ``idx`` (all particles if None), the jerk being the time derivative of
+    the acceleration for particles moving at v."""
     lib = _load()
     x = _f64(x, (-1, 3))
     v = _f64(v, (-1, 3))
     m = _f64(m)
     n = x.shape[0]
-    acc = np.zeros((n, 3))
-    jerk = np.zeros((n, 3))
-    lib.oracle_grav_jerk(n, _dp(x), _dp(v), _dp(m), float(G), float(eps) ** 2, _dp(acc),
-                         _dp(jerk))
+    idx, ip = _idx(idx)
+    ni = n if idx is None else idx.shape[0]
+    acc = np.zeros((ni, 3))
+    jerk = np.zeros((ni, 3))
+    lib.oracle_grav_jerk(n, _dp(x), _dp(v), _dp(m), float(G), float(eps) ** 2, ni, ip,
+                         _dp(acc), _dp(jerk))
     return acc, jerk
 
 

@@ -102,10 +102,12 @@ void oracle_grav(int64_t n, const double *x, const double *m, double G,
  *   j_i = G sum_{j != i} m_j [ u / s^3 - 3 (r . u) r / s^5 ]   (= d a_i / dt)
  * ------------------------------------------------------------------------- */
 void oracle_grav_jerk(int64_t n, const double *x, const double *v, const double *m, double G,
-                      double eps2, double *acc, double *jerk)
+                      double eps2, int64_t ni, const int64_t *idx, double *acc, double *jerk)
 {
+    /* idx (length ni) selects the targets; idx == NULL means all n (ni = n) */
 #pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < n; ++i) {
+    for (int64_t k = 0; k < ni; ++k) {
+        const int64_t i = idx ? idx[k] : k;
         double a[3] = {0.0, 0.0, 0.0}, jk[3] = {0.0, 0.0, 0.0};
         for (int64_t j = 0; j < n; ++j) {
             if (j == i)
@@ -125,8 +127,8 @@ void oracle_grav_jerk(int64_t n, const double *x, const double *v, const double 
             }
         }
         for (int c = 0; c < 3; ++c) {
-            acc[3 * i + c] = G * a[c];
-            jerk[3 * i + c] = G * jk[c];
+            acc[3 * k + c] = G * a[c];
+            jerk[3 * k + c] = G * jk[c];
         }
     }
 }

@@ -117,6 +117,30 @@ def test_grav_full_size_sampled():
     assert_forces_close(acc[idx, :3], ref, what="N=262144 sample")
 
 
+def test_full_size_secondary_forms_sampled():
+    """The bench's other forms at N = 262144 in their launch configurations, on
+    sampled targets against the oracle one by one: acceleration + jerk, the
+    1024-target subset, fixed-point and Newton-refined sums."""
+    nb = lib()
+    n = 262144
+    g = workloads.plummer(n, seed=1, eps=workloads.plummer_softening(n))
+    eps = float(np.float32(g.eps))
+    pos, vel = grav_tensors(g)
+    x, v, m = g.f32_as_f64()
+    idx = np.sort(np.random.default_rng(3).choice(n, 512, replace=False))
+    acc, jerk = nb.forces_jerk(pos, vel, eps=eps)
+    ra, rj = oracle.grav_jerk(x, v, m, eps=eps, idx=idx)
+    assert_forces_close(acc[idx, :3].cpu().numpy(), ra, what="jerk path acc")
+    assert_forces_close(jerk[idx, :3].cpu().numpy(), rj, what="jerk")
+    ref = _grav_ref(g, idx=idx)
+    for kw in ({"fixed": True}, {"precise": True}, {"compensated": False}):
+        a = nb.forces(pos, eps=eps, **kw).cpu().numpy()
+        assert_forces_close(a[idx, :3], ref, what=str(kw))
+    sub = np.random.default_rng(1).choice(n, 1024, replace=False).astype(np.int32)
+    a = nb.forces_subset(pos, torch.from_numpy(sub).to(dev()), eps=eps).cpu().numpy()
+    assert_forces_close(a[:, :3], _grav_ref(g, idx=sub.astype(np.int64)), what="subset")
+
+
 @pytest.mark.slow
 def test_grav_million_sampled():
     nb = lib()
@@ -274,7 +298,7 @@ def _ljclin_tensors(s, D=4.0):
 
 
 @pytest.mark.parametrize("tile", range(5))
-@pytest.mark.parametrize("n", [257, 3000])
+@pytest.mark.parametrize("n", [257, 3000, 8192])
 def test_ljc_linear_dielectric(tile, n):
     """Table 1 LJC(linear): dielectric D r with D = 4 (reading C3)."""
     nb = lib()

@@ -39,3 +39,12 @@ def test_newton_third_law_for_jerk():
     g = workloads.plummer(200, seed=4)
     _, j = oracle.grav_jerk(g.x, g.v, g.m, eps=0.01)
     assert np.all(np.abs(np.sum(g.m[:, None] * j, axis=0)) <= 1e-14 * np.sum(g.m[:, None] * np.abs(j)))
+
+
+def test_target_subset_matches_full():
+    g = workloads.plummer(200, seed=23)
+    v = np.random.default_rng(2).standard_normal((200, 3))
+    a, j = oracle.grav_jerk(g.x, v, g.m, eps=0.02)
+    idx = np.array([199, 0, 57, 58])
+    a2, j2 = oracle.grav_jerk(g.x, v, g.m, eps=0.02, idx=idx)
+    assert np.array_equal(a2, a[idx]) and np.array_equal(j2, j[idx])
