@@ -65,8 +65,8 @@ enum {
                                  growing linearly with distance, energy
                                  kq q_i q_j / r^2 (kq = k_e / D, packed into prm
                                  by nbody_pack_ljc), force 2 kq q_i q_j r_ij / r^4.
-                                 Forces, steps, subsets and the static variant
-                                 only (no batched or adjoint form).             */
+                                 Forces, steps, subsets, batched systems and the
+                                 static variant (no adjoint form).              */
 };
 
 /* nbody_params.flags */
@@ -263,7 +263,8 @@ int nbody_step(void *pos_m, void *vel, void *acc, const void *prm, int64_t n, fl
 typedef struct {
     int64_t offset; /* first particle; a multiple of 4                        */
     int32_t n;      /* particles in the system, >= 1                          */
-    int32_t law;    /* NBODY_LAW_*                                            */
+    int32_t law;    /* NBODY_LAW_*: gravity, LJC or LJC(linear) per system;
+                       LJC systems read prm packed with their own kq          */
     float G;        /* gravity constant (gravity systems)                     */
     float eps2;     /* squared softening (gravity systems)                    */
     float dt;       /* leapfrog step of this system                           */

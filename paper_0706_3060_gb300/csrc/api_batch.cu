@@ -211,9 +211,8 @@ int nbody_batch_plan_create(const nbody_system *systems, int32_t nsys, uint32_t 
     const nbody_system &s = systems[k];
     if (s.n < 1 || s.offset < 0 || s.offset + s.n > 0x7fffffffLL)
       return set_error_msg(NBODY_EINVAL, "system %d: bad offset/n", k);
-    if (s.law != NBODY_LAW_GRAV && s.law != NBODY_LAW_LJC)
-      return set_error_msg(s.law == NBODY_LAW_LJC_LINEAR ? NBODY_EUNSUPPORTED : NBODY_EINVAL,
-                           "system %d: law %d not available in batched runs", k, s.law);
+    if (s.law != NBODY_LAW_GRAV && s.law != NBODY_LAW_LJC && s.law != NBODY_LAW_LJC_LINEAR)
+      return set_error_msg(NBODY_EINVAL, "system %d: unknown law %d", k, s.law);
     if (!(s.eps2 >= 0.0f) || !std::isfinite(s.G) || !std::isfinite(s.dt))
       return set_error_msg(NBODY_EINVAL, "system %d: bad G / eps2 / dt", k);
     total = std::max<int64_t>(total, s.offset + s.n);
@@ -243,8 +242,9 @@ int nbody_batch_plan_create(const nbody_system *systems, int32_t nsys, uint32_t 
   long long pairs_law[2] = {0, 0};  // pair-buffer sizes per law (packed tiles)
   for (int k = 0; k < nsys; ++k) {
     const nbody_system &s = systems[k];
-    const int pbase = int(pairs_law[s.law]);
-    pairs_law[s.law] += (s.n + 1) / 2;
+    const int pl = (s.law == NBODY_LAW_GRAV) ? 0 : 1;  // both LJC laws share one layout
+    const int pbase = int(pairs_law[pl]);
+    pairs_law[pl] += (s.n + 1) / 2;
     sysp[k] = make_int4(int(s.offset), pbase, s.n, s.law);
     const int max_s = (s.n + td->jt - 1) / td->jt;
     int S = int(std::ceil(double(std::min(s.n, td->tile_i)) * s.n / target));
@@ -260,7 +260,7 @@ int nbody_batch_plan_create(const nbody_system *systems, int32_t nsys, uint32_t 
         w.ni = std::min(td->tile_i, s.n - i0);
         w.j0 = int(s.offset) + sl * len;
         w.nj = std::min(len, s.n - sl * len);
-        w.law = s.law;
+        w.law = (s.law == NBODY_LAW_LJC_LINEAR) ? kLawLJCLin : s.law;
         w.slice = sl;
         w.eps2 = s.eps2;
         w.pj0 = pbase + (sl * len) / 2;  // slices start at even local indices
@@ -345,7 +345,7 @@ int nbody_batch_run(nbody_batch_plan *plan, void *pos_m, void *vel, void *acc, c
   for (const void *q : std::initializer_list<const void *>{pos_m, vel, acc, prm})
     if (q && !aligned16(q)) return set_error_msg(NBODY_EALIGN, "array not 16-byte aligned");
   bool any_ljc = false;
-  for (const auto &s : plan->sys) any_ljc |= (s.law == NBODY_LAW_LJC);
+  for (const auto &s : plan->sys) any_ljc |= (s.law != NBODY_LAW_GRAV);
   if (any_ljc && !prm) return set_error_msg(NBODY_EINVAL, "LJC systems need prm");
   for (const void *q : std::initializer_list<const void *>{pos_m, vel, acc, prm})
     if (q && is_host_pointer(q)) return set_error_msg(NBODY_EINVAL, "device pointers only");

@@ -21,6 +21,8 @@
 // only in tiles whose j-range overlaps the CTA's i-range.
 #pragma once
 
+#include <type_traits>
+
 #include "device_common.cuh"
 
 namespace nbody {
@@ -297,7 +299,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
         if (PK) {
           // Packed layout: a tile of len sources is ceil(len/2) pairs of pf4
           // float4; an odd tail reads the pad particle after the system's last source.
-          const bool lj = is_ljc(LAW) || (MIX && w.law == kLawLJC);
+          const bool lj = is_ljc(LAW) || (MIX && w.law != kLawGrav);
           const int pf4 = lj ? 3 : 2;
           const float4 *src = (MIX && lj) ? a.jpair2 : a.jpair;
           const uint32_t bytes = uint32_t((len + 1) >> 1) * pf4 * 16u;
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
                       &full_bar[st]);
         } else {
           const uint32_t bytes = uint32_t(len) * 16u;
-          const bool with_prm = is_ljc(LAW) || (LAW == kLawMixed && w.law == kLawLJC);
+          const bool with_prm = is_ljc(LAW) || (MIX && w.law != kLawGrav);
           mbar_arrive_expect_tx(&full_bar[st], with_prm ? 2u * bytes : bytes);
           tma_load_1d(sm_pos + st * JT, a.pos + cj0, bytes, &full_bar[st]);
           if (with_prm) tma_load_1d(sm_prm + st * JT, a.prm + cj0, bytes, &full_bar[st]);
@@ -399,7 +401,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
         xi[r] = pi4.x;
         yi[r] = pi4.y;
         zi[r] = pi4.z;
-        if (T::kPrm && cur_law == kLawLJC) {
+        if (T::kPrm && cur_law != kLawGrav) {
           const float4 pr = __ldg(a.tprm + g);
           qi[r] = pr.x;
           si[r] = pr.y;
@@ -419,51 +421,61 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
     const float eps2 = cur.eps2;
     const bool masked = a.tidx != nullptr || ((cj0 < cur.i0 + cur.ni) && (cur.i0 < cj0 + len));
 
-    if (PK && (is_ljc(LAW) || (MIX && cur_law == kLawLJC))) {
-      if (!masked) {
-        const int npairs = (len + 1) >> 1;
-        float2 nx[PK ? I : 1], ny[PK ? I : 1], nz[PK ? I : 1];
-        float2 q2[PK ? I : 1], s2[PK ? I : 1], e2[PK ? I : 1];
+    if (PK && (is_ljc(LAW) || (MIX && cur_law != kLawGrav))) {
+      // L: the linear dielectric (fixed by LAW, or per item in the mixed kernel)
+      auto ljc_chunk = [&](auto lin_tag) {
+        constexpr bool L = decltype(lin_tag)::value;
+        if (!masked) {
+          const int npairs = (len + 1) >> 1;
+          float2 nx[PK ? I : 1], ny[PK ? I : 1], nz[PK ? I : 1];
+          float2 q2[PK ? I : 1], s2[PK ? I : 1], e2[PK ? I : 1];
 #pragma unroll
-        for (int r = 0; r < I; ++r) {
-          nx[r] = make_float2(-xi[r], -xi[r]);
-          ny[r] = make_float2(-yi[r], -yi[r]);
-          nz[r] = make_float2(-zi[r], -zi[r]);
-          q2[r] = make_float2(qi[r], qi[r]);
-          s2[r] = make_float2(si[r], si[r]);
-          e2[r] = make_float2(ei[r], ei[r]);
-        }
+          for (int r = 0; r < I; ++r) {
+            nx[r] = make_float2(-xi[r], -xi[r]);
+            ny[r] = make_float2(-yi[r], -yi[r]);
+            nz[r] = make_float2(-zi[r], -zi[r]);
+            q2[r] = make_float2(qi[r], qi[r]);
+            s2[r] = make_float2(si[r], si[r]);
+            e2[r] = make_float2(ei[r], ei[r]);
+          }
 #pragma unroll PU
-        for (int pp = jl; pp < npairs; pp += SW) {
-          const float4 A = sp[3 * pp];
-          const float4 B = sp[3 * pp + 1];
-          const float4 C = sp[3 * pp + 2];
+          for (int pp = jl; pp < npairs; pp += SW) {
+            const float4 A = sp[3 * pp];
+            const float4 B = sp[3 * pp + 1];
+            const float4 C = sp[3 * pp + 2];
 #pragma unroll
-          for (int r = 0; r < I; ++r)
-            ljc_pair2<POT, PRECISE, LIN>(make_float2(A.x, A.y), make_float2(A.z, A.w),
-                                    make_float2(B.x, B.y), make_float2(B.z, B.w),
-                                    make_float2(C.x, C.y), make_float2(C.z, C.w), nx[r], ny[r],
-                                    nz[r], q2[r], s2[r], e2[r], pax[r], pay[r], paz[r], ppt[r]);
+            for (int r = 0; r < I; ++r)
+              ljc_pair2<POT, PRECISE, L>(make_float2(A.x, A.y), make_float2(A.z, A.w),
+                                      make_float2(B.x, B.y), make_float2(B.z, B.w),
+                                      make_float2(C.x, C.y), make_float2(C.z, C.w), nx[r], ny[r],
+                                      nz[r], q2[r], s2[r], e2[r], pax[r], pay[r], paz[r], ppt[r]);
+          }
+        } else {
+          // Diagonal tile (or subset targets): the same pair loop with the self
+          // source's term dropped by index.
+          const int npairs = (len + 1) >> 1;
+          for (int pp = jl; pp < npairs; pp += SW) {
+            const float4 A = sp[3 * pp];
+            const float4 B = sp[3 * pp + 1];
+            const float4 C = sp[3 * pp + 2];
+            const int jg = cj0 + 2 * pp;
+#pragma unroll
+            for (int r = 0; r < I; ++r)
+              ljc_pair2<POT, PRECISE, L, true>(
+                  make_float2(A.x, A.y), make_float2(A.z, A.w), make_float2(B.x, B.y),
+                  make_float2(B.z, B.w), make_float2(C.x, C.y), make_float2(C.z, C.w),
+                  make_float2(-xi[r], -xi[r]), make_float2(-yi[r], -yi[r]),
+                  make_float2(-zi[r], -zi[r]), make_float2(qi[r], qi[r]),
+                  make_float2(si[r], si[r]), make_float2(ei[r], ei[r]), pax[r], pay[r], paz[r],
+                  ppt[r], jg == ig[r], jg + 1 == ig[r]);
+          }
         }
+      };
+      if constexpr (MIX) {
+        if (cur_law == kLawLJCLin) ljc_chunk(std::true_type{});
+        else ljc_chunk(std::false_type{});
       } else {
-        // Diagonal tile (or subset targets): the same pair loop with the self
-        // source's term dropped by index.
-        const int npairs = (len + 1) >> 1;
-        for (int pp = jl; pp < npairs; pp += SW) {
-          const float4 A = sp[3 * pp];
-          const float4 B = sp[3 * pp + 1];
-          const float4 C = sp[3 * pp + 2];
-          const int jg = cj0 + 2 * pp;
-#pragma unroll
-          for (int r = 0; r < I; ++r)
-            ljc_pair2<POT, PRECISE, LIN, true>(
-                make_float2(A.x, A.y), make_float2(A.z, A.w), make_float2(B.x, B.y),
-                make_float2(B.z, B.w), make_float2(C.x, C.y), make_float2(C.z, C.w),
-                make_float2(-xi[r], -xi[r]), make_float2(-yi[r], -yi[r]),
-                make_float2(-zi[r], -zi[r]), make_float2(qi[r], qi[r]),
-                make_float2(si[r], si[r]), make_float2(ei[r], ei[r]), pax[r], pay[r], paz[r],
-                ppt[r], jg == ig[r], jg + 1 == ig[r]);
-        }
+        ljc_chunk(std::integral_constant<bool, LIN>{});
       }
     } else if (PK) {
       if (!masked) {
@@ -532,35 +544,44 @@ __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a)
         }
       }
     } else {
-      if (!masked && len == JT) {
+      auto ljc_chunk = [&](auto lin_tag) {
+        constexpr bool L = decltype(lin_tag)::value;
+        if (!masked && len == JT) {
 #pragma unroll 2
-        for (int jj = jl; jj < JT; jj += SW) {
-          const float4 pj = sp[jj];
-          const float4 qj = sq[jj];
+          for (int jj = jl; jj < JT; jj += SW) {
+            const float4 pj = sp[jj];
+            const float4 qj = sq[jj];
 #pragma unroll
-          for (int r = 0; r < I; ++r)
-            ljc_pair<POT, PRECISE, false, LIN>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r],
-                                          p[r], false);
-        }
-      } else if (!masked) {
-        for (int jj = jl; jj < len; jj += SW) {
-          const float4 pj = sp[jj];
-          const float4 qj = sq[jj];
+            for (int r = 0; r < I; ++r)
+              ljc_pair<POT, PRECISE, false, L>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r],
+                                            p[r], false);
+          }
+        } else if (!masked) {
+          for (int jj = jl; jj < len; jj += SW) {
+            const float4 pj = sp[jj];
+            const float4 qj = sq[jj];
 #pragma unroll
-          for (int r = 0; r < I; ++r)
-            ljc_pair<POT, PRECISE, false, LIN>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r],
-                                          p[r], false);
+            for (int r = 0; r < I; ++r)
+              ljc_pair<POT, PRECISE, false, L>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r],
+                                            p[r], false);
+          }
+        } else {
+          for (int jj = jl; jj < len; jj += SW) {
+            const float4 pj = sp[jj];
+            const float4 qj = sq[jj];
+            const int jg = cj0 + jj;
+#pragma unroll
+            for (int r = 0; r < I; ++r)
+              ljc_pair<POT, PRECISE, true, L>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r],
+                                           p[r], jg == ig[r]);
+          }
         }
+      };
+      if constexpr (MIX) {
+        if (cur_law == kLawLJCLin) ljc_chunk(std::true_type{});
+        else ljc_chunk(std::false_type{});
       } else {
-        for (int jj = jl; jj < len; jj += SW) {
-          const float4 pj = sp[jj];
-          const float4 qj = sq[jj];
-          const int jg = cj0 + jj;
-#pragma unroll
-          for (int r = 0; r < I; ++r)
-            ljc_pair<POT, PRECISE, true, LIN>(pj, qj, xi[r], yi[r], zi[r], qi[r], si[r], ei[r],
-                                         p[r], jg == ig[r]);
-        }
+        ljc_chunk(std::integral_constant<bool, LIN>{});
       }
     }
 

@@ -15,6 +15,9 @@ const TileDesc *mixed_tiles(int *count) {
       TileImpl<kLawMixed, 128, 2, 2, 256, true>::desc(),  // 5: 128 targets, 2 j-lanes
       TileImpl<kLawMixed, 128, 2, 1, 256, true>::desc(),  // 6: 256 targets
       TileImpl<kLawMixed, 64, 2, 8, 256, true>::desc(),   // 7: 16 targets, 8 j-lanes
+      // as 6 and 5 with registers capped for 3 CTAs per SM
+      TileImpl<kLawMixed, 128, 2, 1, 256, true, 2, 3>::desc(),  // 8: 256 targets
+      TileImpl<kLawMixed, 128, 2, 2, 256, true, 2, 3>::desc(),  // 9: 128 targets, 2 j-lanes
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;

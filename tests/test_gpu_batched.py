@@ -155,7 +155,7 @@ def test_one_shot_and_bad_tables():
         nb.BatchPlan([dict(offset=0, n=0, law=0, dt=1e-3)])
 
 
-@pytest.mark.parametrize("tile", range(8))
+@pytest.mark.parametrize("tile", range(10))
 def test_batched_every_tile(small_ensemble, tile):
     """Every compiled batched tile (scalar and packed f32x2, with odd-sized systems
     padded inside their pair buffers) against the oracle, then 3 steps."""
@@ -222,3 +222,61 @@ def test_batched_tiny_and_large_systems():
                 ref = oracle.grav_accel(x, m, eps=float(np.float32(0.02)))
                 assert_forces_close(a[o:o + n, :3], ref, what=f"tile {tile} n={n}")
         plan.close()
+
+
+def test_batched_linear_dielectric_systems():
+    """Gravity, LJC(constant) and LJC(linear) systems in one plan (each LJC
+    system packed with its own kq), on every batched tile, against the oracle;
+    then 3 graph-replayed steps of a linear-dielectric system."""
+    nb = lib()
+    K = 332.0637
+    laws = [nb.LAW_GRAV, nb.LAW_LJC, nb.LAW_LJC_LINEAR, nb.LAW_LJC_LINEAR, nb.LAW_LJC]
+    sizes = [300, 257, 410, 129, 600]
+    d = dev()
+    total = sum(sizes)
+    pos = np.zeros((total, 4), np.float32)
+    vel = np.zeros((total, 4), np.float32)
+    prm = torch.zeros((total, 4), dtype=torch.float32, device=d)
+    table, refs, off = [], [], 0
+    for k, (law, n) in enumerate(zip(laws, sizes)):
+        if law == nb.LAW_GRAV:
+            g = workloads.plummer(n, seed=200 + k, eps=0.02)
+            x, v, m = g.f32()
+            eps = float(np.float32(0.02))
+            table.append(dict(offset=off, n=n, law=law, eps=eps, dt=1e-3))
+            xd, vd, md = g.f32_as_f64()
+            refs.append((oracle.GravSystem(md, eps=eps), xd, vd))
+        else:
+            s = workloads.ljc_sphere(n, seed=200 + k)
+            x, v, m, q, st, et = s.f32()
+            kq = K / 80.0 if law == nb.LAW_LJC else K / 4.0
+            prm[off:off + n] = nb.pack_ljc(torch.from_numpy(q.astype(np.float64)).to(d),
+                                           torch.from_numpy(st.astype(np.float64)[s.types]).to(d),
+                                           torch.from_numpy(et.astype(np.float64)[s.types]).to(d),
+                                           torch.from_numpy(s.types).to(d), kq=kq)
+            table.append(dict(offset=off, n=n, law=law, dt=1e-4))
+            xd, vd, md, qd, std, etd = s.f32_as_f64()
+            refs.append((oracle.LJCSystem(md, qd, s.types, std, etd, kq,
+                                          linear=law == nb.LAW_LJC_LINEAR), xd, vd))
+        pos[off:off + n, :3], pos[off:off + n, 3], vel[off:off + n, :3] = x, m, v
+        off += n
+    p0 = torch.from_numpy(pos).to(d)
+    v0 = torch.from_numpy(vel).to(d)
+    for tile in range(nb.tile_count(nb.TABLE_BATCHED)):
+        acc = torch.zeros_like(p0)
+        plan = nb.BatchPlan(table, tile=tile)
+        plan.run(p0, v0, acc, prm, nsteps=0, graph=False)
+        a = acc.cpu().numpy()
+        for k, (sysm, x, _) in enumerate(refs):
+            o, n = table[k]["offset"], table[k]["n"]
+            assert_forces_close(a[o:o + n, :3], sysm.accel(x), what=f"tile {tile} system {k}")
+        plan.close()
+    p1, v1 = p0.clone(), v0.clone()
+    acc = torch.zeros_like(p1)
+    plan = nb.BatchPlan(table)
+    plan.run(p1, v1, acc, prm, nsteps=3, graph=True)
+    sysm, x, v = refs[2]
+    xr, _ = oracle.leapfrog(sysm, x, v, 1e-4, 3)
+    o, n = table[2]["offset"], table[2]["n"]
+    ex = traj_errors(p1[o:o + n, :3].cpu().numpy(), xr)
+    assert ex[0] <= 1e-6, ex
