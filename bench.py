@@ -335,14 +335,19 @@ def aggregate(t_local: float, pairs_per_step: float, steps: int, world: int, dev
 
 
 def kernel_hash() -> str:
-    """Identity of the timed force kernel: its sources and the tuned gravity
+    """Identity of the timed force kernel: its sources with comments and spacing
+    removed (a comment edit does not change the kernel) and the tuned gravity
     entry for the bench size (other tuning-table entries do not change it)."""
     import hashlib
+    import re
     h = hashlib.sha1()
     pkg = os.path.join(ROOT, "paper_0706_3060_gb300")
     for f in ("csrc/force_kernel.cuh", "csrc/device_common.cuh", "csrc/force_grav.cu"):
-        with open(os.path.join(pkg, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(pkg, f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     bucket = str(int(math.floor(math.log2(N_BENCH))))
     with open(os.path.join(pkg, "tuned.json")) as fh:
         data = json.load(fh)

@@ -5,8 +5,8 @@
  * "N-Body Simulations on GPUs" (arXiv 0706.3060) -- softened gravity (Eq. 1,
  * Table 1 "Gravity (accel)") and Lennard-Jones plus Coulomb in a continuum
  * solvent of constant dielectric (Table 1 "LJC(constant)") -- and the update
- * step that consumes them (Sec. 1: "a force evaluation step ... and an update
- * step"), which it implements as kick-drift-kick leapfrog.
+ * step that consumes them (Sec. 1 splits each time step into a force
+ * evaluation and an update), which it implements as kick-drift-kick leapfrog.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -141,7 +141,8 @@ int nbody_peak_probe(int32_t kind, int32_t iters, double *ops_per_clk_sm, double
 int nbody_selftest_timeout(int64_t limit_cycles, nbody_stream_t stream);
 
 /* ---------------------------------------------------------------------------
- * S0 pack (Sec. 2 "stream coordinates"; Appendix jpos/jmass float4).
+ * Packing (Sec. 2 keeps the coordinates as GPU streams; the Appendix listing
+ * reads positions and masses as float4).
  * Converts caller SoA data in double precision into the float4 streams above.
  *   x, y, z, m : n doubles each (device).      pos_m : n float4 (device, out)
  *   nbody_pack_ljc additionally takes q, sigma, eps (per particle, doubles),
@@ -256,7 +257,7 @@ int nbody_step(void *pos_m, void *vel, void *acc, const void *prm, int64_t n, fl
                const nbody_params *params, nbody_stream_t stream);
 
 /* ---------------------------------------------------------------------------
- * Batched ensembles (Sec. 3.4 "optimization for small systems"): many
+ * Batched ensembles (Sec. 3.4, small systems): many
  * independent systems of uneven size in one persistent launch per step.
  * System k occupies particles [offset, offset + n) of the shared arrays.
  * --------------------------------------------------------------------------- */

@@ -15,7 +15,7 @@ What it computes (each item is the plain definition, no blocking or fusion):
   12-6 Lennard-Jones force plus Coulomb in a dielectric eps_r, with
   Lorentz-Berthelot mixing (the paper prints the LJ term without its 24/r^2
   factor; see ``nbody_oracle.c``).
-* :func:`leapfrog`       -- kick-drift-kick leapfrog, the "update step" of
+* :func:`leapfrog`       -- kick-drift-kick leapfrog, the update step of
   Sec. 1 (the paper leaves the integrator open; KDK is the reading used).
 * :func:`grav_vjp`, :func:`ljc_vjp` -- J^T lambda of the force laws above,
   block by block from the Jacobian, with mass and per-type sigma/epsilon
@@ -277,7 +277,7 @@ class LJCSystem:
 
 
 # ---------------------------------------------------------------------------
-# Update step: kick-drift-kick leapfrog (Sec. 1 "update step"; reading C7)
+# Update step of Sec. 1: kick-drift-kick leapfrog (the paper names no integrator)
 # ---------------------------------------------------------------------------
 def leapfrog(system, x0, v0, dt, nsteps, store=False):
     """Advance (x, v) by ``nsteps`` KDK steps of size ``dt`` in FP64.

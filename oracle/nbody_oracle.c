@@ -30,8 +30,8 @@
  *       kq = k_e / D) and its force 2 kq q_i q_j r_ij / r^4.
  *   C4  Lorentz-Berthelot mixing: sigma_ij = (sigma_i + sigma_j)/2,
  *       eps_ij = sqrt(eps_i eps_j).
- *   C5  The self pair i == j is excluded by index, as in the Appendix
- *       listing's "don't add force due to ourself" test.
+ *   C5  The self pair i == j is excluded by its index, as the Appendix
+ *       listing does with an index comparison.
  *   C6  r_ij = x_i - x_j; Eq. 1 carries the leading minus (attraction);
  *       the Appendix's "eps" is the squared softening eps^2.
  *

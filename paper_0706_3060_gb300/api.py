@@ -82,7 +82,7 @@ def sync_check(stream=None) -> None:
 
 
 # ---------------------------------------------------------------------------
-# S0 pack
+# Packing
 # ---------------------------------------------------------------------------
 def pack_grav(x: torch.Tensor, m: torch.Tensor, out: torch.Tensor | None = None, stream=None):
     """(n, 3) float64 positions and (n,) float64 masses on the GPU -> (n, 4) float32."""

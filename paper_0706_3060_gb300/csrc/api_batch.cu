@@ -1,6 +1,6 @@
 // api_batch.cu -- batched ensembles: many independent systems of uneven size in
-// one persistent launch per force evaluation (Sec. 3.4, "optimization for small
-// systems": more parallel work by splitting the i- and j-ranges), with the
+// one persistent launch per force evaluation (Sec. 3.4 on small systems: more
+// parallel work by splitting the i- and j-ranges), with the
 // whole leapfrog loop captured once into a CUDA graph and replayed.
 #include <cuda_runtime.h>
 

@@ -1,8 +1,8 @@
 // aux_kernels.cuh -- O(N) kernels around the all-pairs force kernel:
-//   S0 pack (caller SoA doubles -> float4 streams),
-//   S4/S5 finalize (fixed-order compensated sum of the per-slice partials,
-//         law scaling, leapfrog kick/drift, position trace),
-//   S6 FP64 diagnostics (block partials, then one deterministic final sum).
+//   packing (caller SoA doubles -> float4 streams),
+//   finalize (fixed-order compensated sum of the per-slice partials, law
+//         scaling, leapfrog kick/drift, position trace),
+//   FP64 diagnostics (block partials, then one deterministic final sum).
 #pragma once
 
 #include <cstdint>
@@ -252,14 +252,14 @@ __global__ void copy_float4_kernel(const float4 *src, float4 *dst, int n) {
   if (i < n) dst[i] = src[i];
 }
 
-// S0: caller SoA doubles -> (x, y, z, m) float4.
+// Packing: caller SoA doubles -> (x, y, z, m) float4.
 __global__ void pack_grav_kernel(const double *x, const double *y, const double *z,
                                  const double *m, float4 *out, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = make_float4((float)x[i], (float)y[i], (float)z[i], (float)m[i]);
 }
 
-// S0: LJC parameters (q~, s~, e~, type) with q~ = q sqrt(kq), s~ = sigma / 2,
+// Packing: LJC parameters (q~, s~, e~, type) with q~ = q sqrt(kq), s~ = sigma / 2,
 // e~ = sqrt(24 eps); computed in FP64 and rounded once.
 __global__ void pack_ljc_kernel(const double *q, const double *sig, const double *eps,
                                 const int32_t *type, double sqrt_kq, float4 *out, long long n) {

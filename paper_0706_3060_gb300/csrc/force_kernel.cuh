@@ -5,17 +5,17 @@
 // thread of a CTA, as in the paper's kforce kernel. GB300 mapping:
 //   * one producer warp streams j-tiles of JT particles (16 B each, plus 16 B
 //     of LJC parameters) from global memory into a STAGES-deep shared-memory
-//     ring with 1-D TMA bulk copies completing on mbarriers (S1);
+//     ring with 1-D TMA bulk copies completing on mbarriers;
 //   * NT consumer threads each hold I target particles in registers -- the
-//     "i unrolled" half of the paper's A x B unrolling (Sec. 3.3) -- and read
-//     every staged j once per I interactions; the j-loop is unrolled (S2);
+//     i-side half of the paper's A x B unrolling (Sec. 3.3) -- and read
+//     every staged j once per I interactions; the j-loop is unrolled;
 //   * each j-tile's contribution is summed plainly in FP32 and then folded into
 //     a (hi, lo) pair with TwoSum, so the compensation costs a few operations
-//     per tile rather than per pair (S3, precision policy of Sec. 3.2);
+//     per tile rather than per pair (the precision policy of Sec. 3.2);
 //   * SW j-lanes per warp split the j-range inside a warp and are combined
 //     with __shfl_xor in a fixed butterfly; several CTAs may split the
 //     j-range of one i-tile ("replication", Sec. 3.4) and write per-slice
-//     partials that the finalize kernel adds in a fixed order (S4). Results
+//     partials that the finalize kernel adds in a fixed order. Results
 //     are therefore bitwise reproducible run to run.
 // The self pair is excluded by index (the Appendix's Ilist != Jlist test)
 // only in tiles whose j-range overlaps the CTA's i-range.

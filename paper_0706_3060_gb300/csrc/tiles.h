@@ -45,9 +45,16 @@ struct TileImpl {
   static cudaError_t go(const ForceArgs &a, int grid, cudaStream_t s) {
     auto k = force_kernel<LAW, NT, I, SW, JT, POT, PRE, PK, PU, MINB, FX>;
     if (T::kSmemBytes > 32 * 1024) {
-      cudaError_t e =
-          cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
-      if (e != cudaSuccess) return e;
+      // the opt-in is a per-device function attribute: set it once per device
+      static std::atomic<bool> opted[kMaxDevicesTile];
+      int dev = 0;
+      const bool known = cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDevicesTile;
+      if (!known || !opted[dev].load(std::memory_order_acquire)) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)T::kSmemBytes);
+        if (e != cudaSuccess) return e;
+        if (known) opted[dev].store(true, std::memory_order_release);
+      }
     }
     k<<<grid, T::kThreads, T::kSmemBytes, s>>>(a);
     return cudaGetLastError();

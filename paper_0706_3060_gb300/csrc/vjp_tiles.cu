@@ -17,10 +17,16 @@ struct VjpImpl {
   using T = VjpTile<LAW, NT, I, SW, JT, PK>;
   static cudaError_t launch(const VjpArgs &a, int grid, cudaStream_t s) {
     auto k = vjp_kernel<LAW, NT, I, SW, JT, PK, PU>;
-    if (T::kSmemBytes > 32 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)T::kSmemBytes);
-      if (e != cudaSuccess) return e;
+    if (T::kSmemBytes > 32 * 1024) {  // per-device attribute: set once per device
+      static std::atomic<bool> opted[kMaxDevicesTile];
+      int dev = 0;
+      const bool known = cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDevicesTile;
+      if (!known || !opted[dev].load(std::memory_order_acquire)) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)T::kSmemBytes);
+        if (e != cudaSuccess) return e;
+        if (known) opted[dev].store(true, std::memory_order_release);
+      }
     }
     k<<<grid, T::kThreads, T::kSmemBytes, s>>>(a);
     return cudaGetLastError();

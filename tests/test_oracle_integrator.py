@@ -1,4 +1,4 @@
-"""Pins for the FP64 kick-drift-kick leapfrog ("update step", Sec. 1).
+"""Pins for the FP64 kick-drift-kick leapfrog (the update step of Sec. 1).
 
 Kepler's two-body orbit in closed form (solved through Kepler's equation)
 gives second-order convergence; the energy error of a Plummer cluster scales
