@@ -15,7 +15,7 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(config, items):
     # GPU tests must not silently pass on a CPU fallback: with no GPU they are
-    # skipped here, and on a GPU machine the library raises if it is not built.
+    # skipped; with one, the library raises if it is not built.
     try:
         import torch
         have_gpu = torch.cuda.is_available()
