@@ -85,6 +85,9 @@ def _load():
                                             d, d, d]
             lib.oracle_ljc_vjp.argtypes = [i64, d, d, d, i32p, ctypes.c_int32, d, d,
                                            ctypes.c_double, d, d, d, d, d]
+            lib.oracle_ljc_vjp_model.argtypes = [i64, d, d, d, i32p, ctypes.c_int32, d, d,
+                                                 ctypes.c_double, ctypes.c_int, d, d, d, d, d]
+            lib.oracle_ljc_vjp_model.restype = None
             lib.oracle_threads.argtypes = [ctypes.c_int]
             lib.oracle_threads.restype = ctypes.c_int
             for f in (lib.oracle_grav, lib.oracle_ljc, lib.oracle_grav_vjp,
@@ -193,8 +196,9 @@ def grav_vjp(x, m, lam, G=1.0, eps=0.0):
     return g, gm
 
 
-def ljc_vjp(x, m, q, types, sig_t, eps_t, lam, kq=COULOMB_K / 80.0):
-    """J^T lam for a = F/m of the LJC law, with mass and per-type derivatives.
+def ljc_vjp(x, m, q, types, sig_t, eps_t, lam, kq=COULOMB_K / 80.0, linear=False):
+    """J^T lam for a = F/m of the LJC law (constant dielectric, or linear with
+    ``linear``: Table 1 LJC(linear), reading C3), with mass and per-type derivatives.
 
     Returns (g (n,3), gm (n,), gsig (ntypes,), geps (ntypes,)).
     """
@@ -210,10 +214,10 @@ def ljc_vjp(x, m, q, types, sig_t, eps_t, lam, kq=COULOMB_K / 80.0):
     gm = np.zeros(n)
     gs = np.zeros(nt)
     ge = np.zeros(nt)
-    lib.oracle_ljc_vjp(n, _dp(x), _dp(m), _dp(q),
-                       types.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), nt,
-                       _dp(sig_t), _dp(eps_t), float(kq), _dp(lam), _dp(g), _dp(gm),
-                       _dp(gs), _dp(ge))
+    lib.oracle_ljc_vjp_model(n, _dp(x), _dp(m), _dp(q),
+                             types.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), nt,
+                             _dp(sig_t), _dp(eps_t), float(kq), 1 if linear else 0, _dp(lam),
+                             _dp(g), _dp(gm), _dp(gs), _dp(ge))
     return g, gm, gs, ge
 
 
@@ -273,7 +277,8 @@ class LJCSystem:
 
     def vjp(self, x, lam):
         """Returns (J^T lam, d/dm, d/dsig_t, d/deps_t) of lam . a."""
-        return ljc_vjp(x, self.m, self.q, self.types, self.sig_t, self.eps_t, lam, self.kq)
+        return ljc_vjp(x, self.m, self.q, self.types, self.sig_t, self.eps_t, lam, self.kq,
+                       linear=self.linear)
 
 
 # ---------------------------------------------------------------------------

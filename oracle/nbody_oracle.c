@@ -262,11 +262,13 @@ void oracle_grav_vjp(int64_t n, const double *x, const double *m, double G,
  *   d a_i / d m_i      = -F_i / m_i^2
  * Outputs: g (n x 3), gm (n, may be NULL), gsig and geps (ntypes, may be NULL).
  * ------------------------------------------------------------------------- */
-void oracle_ljc_vjp(int64_t n, const double *x, const double *m,
-                    const double *q, const int32_t *type, int32_t ntypes,
-                    const double *sig_t, const double *eps_t, double kq,
-                    const double *lam, double *g, double *gm, double *gsig,
-                    double *geps)
+/* model 0: constant dielectric (force coefficient kq q_i q_j / rho^{3/2});
+ * model 1: linear dielectric, reading C3 (2 kq q_i q_j / rho^2). rho = r^2. */
+void oracle_ljc_vjp_model(int64_t n, const double *x, const double *m,
+                          const double *q, const int32_t *type, int32_t ntypes,
+                          const double *sig_t, const double *eps_t, double kq, int model,
+                          const double *lam, double *g, double *gm, double *gsig,
+                          double *geps)
 {
     double *gl = (double *)calloc((size_t)(3 * n), sizeof(double));
     double *ml = (double *)calloc((size_t)n, sizeof(double));
@@ -290,9 +292,12 @@ void oracle_ljc_vjp(int64_t n, const double *x, const double *m,
             double e = sqrt(eps_t[ti] * eps_t[tj]);
             double qq = kq * q[i] * q[j];
             double s6 = pow(s, 6.0), s12 = s6 * s6;
-            double phi = qq * pow(rho, -1.5)
+            /* Coulomb part of the force coefficient and of its rho-derivative */
+            double phi_c = model ? 2.0 * qq * pow(rho, -2.0) : qq * pow(rho, -1.5);
+            double dphi_c = model ? -4.0 * qq * pow(rho, -3.0) : -1.5 * qq * pow(rho, -2.5);
+            double phi = phi_c
                        + 24.0 * e * (2.0 * s12 * pow(rho, -7.0) - s6 * pow(rho, -4.0));
-            double dphi = -1.5 * qq * pow(rho, -2.5)
+            double dphi = dphi_c
                         + 24.0 * e * (-14.0 * s12 * pow(rho, -8.0) + 4.0 * s6 * pow(rho, -5.0));
             double H[3][3];
             for (int a = 0; a < 3; ++a)
@@ -330,4 +335,14 @@ void oracle_ljc_vjp(int64_t n, const double *x, const double *m,
     free(ml);
     free(sl);
     free(el);
+}
+
+void oracle_ljc_vjp(int64_t n, const double *x, const double *m,
+                    const double *q, const int32_t *type, int32_t ntypes,
+                    const double *sig_t, const double *eps_t, double kq,
+                    const double *lam, double *g, double *gm, double *gsig,
+                    double *geps)
+{
+    oracle_ljc_vjp_model(n, x, m, q, type, ntypes, sig_t, eps_t, kq, 0, lam, g, gm, gsig,
+                         geps);
 }

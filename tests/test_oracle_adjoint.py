@@ -49,10 +49,13 @@ def test_grav_mass_derivative():
     assert abs(fd - gm @ dm) <= 1e-9 * np.abs(gm * dm).sum()
 
 
-def test_ljc_vjp_dot_product_and_parameters():
+@pytest.mark.parametrize("linear", [False, True])
+def test_ljc_vjp_dot_product_and_parameters(linear):
+    """J^T lam against central differences of the oracle's forces, for both
+    dielectric models (constant eps_r = 80; linear D r with D = 4)."""
     s = _ljc_case()
-    kq = oracle.COULOMB_K / 80.0
-    sysm = oracle.LJCSystem(s.m, s.q, s.types, s.sig_t, s.eps_t, kq)
+    kq = oracle.COULOMB_K / (4.0 if linear else 80.0)
+    sysm = oracle.LJCSystem(s.m, s.q, s.types, s.sig_t, s.eps_t, kq, linear=linear)
     rng = np.random.default_rng(5)
     lam = rng.standard_normal(s.x.shape)
     g, gm, gs, ge = sysm.vjp(s.x, lam)
@@ -63,7 +66,8 @@ def test_ljc_vjp_dot_product_and_parameters():
         assert abs(np.sum(lam * Ju) - np.sum(g * u)) <= 1e-6 * np.abs(g * u).sum()
 
     def lam_a(m=s.m, sig_t=s.sig_t, eps_t=s.eps_t):
-        return np.sum(lam * oracle.LJCSystem(m, s.q, s.types, sig_t, eps_t, kq).accel(s.x))
+        return np.sum(lam * oracle.LJCSystem(m, s.q, s.types, sig_t, eps_t, kq,
+                                             linear=linear).accel(s.x))
 
     for t in range(len(s.sig_t)):
         e = np.zeros_like(s.sig_t)
@@ -128,18 +132,19 @@ def test_reverse_leapfrog_directional_fd():
         assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-12), (fd, an)
 
 
-def test_reverse_leapfrog_ljc_directional_fd():
+@pytest.mark.parametrize("linear", [False, True])
+def test_reverse_leapfrog_ljc_directional_fd(linear):
     s = workloads.ljc_sphere(12, seed=23, radius=5.0)
-    kq = oracle.COULOMB_K / 80.0
+    kq = oracle.COULOMB_K / (4.0 if linear else 80.0)
     dt, T = 2e-3, 10
 
     def loss(x0, v0, sig_t, eps_t):
-        sysm = oracle.LJCSystem(s.m, s.q, s.types, sig_t, eps_t, kq)
+        sysm = oracle.LJCSystem(s.m, s.q, s.types, sig_t, eps_t, kq, linear=linear)
         xT, _ = oracle.leapfrog(sysm, x0, v0, dt, T)
         return oracle.target_loss(xT, target)
 
     target = workloads.perturbed_target(s.x, seed=4)
-    sysm = oracle.LJCSystem(s.m, s.q, s.types, s.sig_t, s.eps_t, kq)
+    sysm = oracle.LJCSystem(s.m, s.q, s.types, s.sig_t, s.eps_t, kq, linear=linear)
     xs, _ = oracle.leapfrog(sysm, s.x, s.v, dt, T, store=True)
     grad = oracle.adjoint_leapfrog(sysm, s.x, s.v, dt, T,
                                    oracle.target_loss_grad(xs[-1], target), xs=xs)
