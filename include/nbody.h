@@ -65,8 +65,8 @@ enum {
                                  growing linearly with distance, energy
                                  kq q_i q_j / r^2 (kq = k_e / D, packed into prm
                                  by nbody_pack_ljc), force 2 kq q_i q_j r_ij / r^4.
-                                 Forces, steps, subsets, batched systems and the
-                                 static variant (no adjoint form).              */
+                                 Every entry point that takes a law accepts it
+                                 except the jerk and Hermite calls.             */
 };
 
 /* nbody_params.flags */
@@ -94,7 +94,8 @@ typedef struct {
     int32_t tile;    /* kernel tile configuration, -1 = tuned/default: a row
                         of the law's force table (0-2, 4 with FIXED_POINT);
                         for nbody_adjoint / nbody_adjoint_leapfrog a row of
-                        table 5 (gravity VJP) or 6 (LJC VJP); for
+                        table 5 (gravity VJP), 6 (LJC VJP) or 8 (LJC linear
+                        VJP); for
                         nbody_forces_jerk / nbody_hermite_step of table 7  */
     int32_t jsplit;  /* j-slices per i-tile ("replication", Sec. 3.4), 0 = auto */
 } nbody_params;
@@ -304,7 +305,8 @@ int nbody_forces_batched(const nbody_system *systems, int32_t nsys, void *pos_m,
  *   grad_x[k] (+)= alpha * sum_i (d a_i / d x_k)^T lam_i
  *   grad_m[k] (+)= alpha * sum_i lam_i . d a_i / d m_k
  *   grad_types (+)= alpha * (d/d sigma_t, d/d eps_t of sum_i lam_i . a_i),
- *                  2 * ntypes doubles (LJC only; NULL to skip)
+ *                  2 * ntypes doubles (both LJC laws; NULL to skip)
+ *   params->law : gravity, LJC or LJC(linear)
  *   pos_m, prm : as in nbody_forces; lam : n float4 (w ignored)
  *   grad_x : n float4 (w ignored on input, 0 on output); grad_m : n floats
  * With NBODY_ACCUMULATE the outputs are added to, else overwritten.
@@ -334,7 +336,7 @@ int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k
 /* Number of compiled tile configurations for tile table `law` (0 gravity,
  * 1 LJC, 2 LJC linear, 3 the mixed-law batched kernel, 4 gravity with
  * fixed-point accumulation, 5 the gravity VJP, 6 the LJC VJP, 7 acceleration
- * + jerk), or a negative status. */
+ * + jerk, 8 the LJC(linear) VJP), or a negative status. */
 int nbody_tile_count(int32_t law);
 /* Describe configuration `tile` of `law`: threads per CTA (consumer warps),
  * i-particles per thread, j-lanes per warp, j-tile length, and whether it
@@ -367,9 +369,10 @@ int nbody_workspace_size(const nbody_params *params, int64_t n, int32_t report_r
  * with nbody_set_tuned for bucket floor(log2 n) and returned in best_tile,
  * best_jsplit and best_ms (milliseconds per call; any may be NULL). What is
  * timed: tables 0-2 nbody_forces (law = table), 4 nbody_forces with
- * NBODY_FIXED_POINT (eps2 > 0), 5 / 6 nbody_adjoint (gravity / LJC, with
- * lambda = pos_m), 7 nbody_forces_jerk (velocities = pos_m); G = 1, softening
- * eps2. prm: the LJC parameters for tables 1, 2 and 6, else ignored. Outputs
+ * NBODY_FIXED_POINT (eps2 > 0), 5 / 6 / 8 nbody_adjoint (gravity / LJC / LJC
+ * linear, with lambda = pos_m), 7 nbody_forces_jerk (velocities = pos_m); G = 1,
+ * softening eps2. prm: the LJC parameters for tables 1, 2, 6 and 8, else
+ * ignored. Outputs
  * go to library scratch. Table 3 (batched) returns NBODY_EUNSUPPORTED: the
  * package tunes it over a system table. Synchronizes `stream`; on any error
  * nothing is installed. */

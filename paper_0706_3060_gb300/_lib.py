@@ -32,6 +32,7 @@ TABLE_GRAV_FIXED = 4  # tile table of the fixed-point gravity kernels
 TABLE_VJP_GRAV = 5  # tile table of the gravity VJP kernels (nbody_adjoint*)
 TABLE_VJP_LJC = 6  # tile table of the LJC VJP kernels
 TABLE_JERK = 7  # tile table of the acceleration + jerk kernels
+TABLE_VJP_LJC_LINEAR = 8  # tile table of the LJC(linear) VJP kernels
 
 # Every symbol include/nbody.h declares.
 EXPORTS = (

@@ -15,7 +15,8 @@ import torch
 
 from . import _lib
 from ._lib import (ACC_VALID, ACCUMULATE, COMPUTE_POT, FIXED_POINT, LAW_GRAV, LAW_LJC,
-                   NO_COMPENSATION, PRECISE_RSQRT, NBodyParams, NBodySystem, check, load)
+                   LAW_LJC_LINEAR, NO_COMPENSATION, PRECISE_RSQRT, NBodyParams, NBodySystem,
+                   check, load)
 
 COULOMB_K = 332.0637  # kcal A / (mol e^2): units A, kcal/mol, e, amu (AKMA time)
 
@@ -263,7 +264,8 @@ def adjoint(pos_m, lam, prm=None, *, law=None, G=1.0, eps=0.0, alpha=1.0, grad_x
             grad_m=None, grad_types=None, ntypes=4, accumulate=False, tile=-1, jsplit=0,
             stream=None):
     """One force VJP: returns (grad_x (n,4), grad_m (n,), grad_types (2*ntypes,) or None).
-    ``tile`` indexes tile table 5 (gravity) or 6 (LJC); -1: tuned/default."""
+    ``tile`` indexes tile table 5 (gravity), 6 (LJC) or 8 (LJC linear); -1:
+    tuned/default."""
     _check4(pos_m, "pos_m")
     _check4(lam, "lam")
     law = (LAW_LJC if prm is not None else LAW_GRAV) if law is None else law
@@ -272,7 +274,7 @@ def adjoint(pos_m, lam, prm=None, *, law=None, G=1.0, eps=0.0, alpha=1.0, grad_x
     gx = torch.zeros_like(pos_m) if grad_x is None else grad_x
     gm = torch.zeros(n, dtype=torch.float32, device=dev) if grad_m is None else grad_m
     gt = grad_types
-    if gt is None and law == LAW_LJC:
+    if gt is None and law in (LAW_LJC, LAW_LJC_LINEAR):
         gt = torch.zeros(2 * ntypes, dtype=torch.float64, device=dev)
     p = params(law, G, eps, accumulate=accumulate, tile=tile, jsplit=jsplit)
     check(_lib().nbody_adjoint(_ptr(pos_m), _ptr(prm), _ptr(lam), _ptr(gx), _ptr(gm), _ptr(gt),

@@ -21,7 +21,9 @@ from __future__ import annotations
 import torch
 
 from . import api
-from ._lib import LAW_GRAV, LAW_LJC
+from ._lib import LAW_GRAV, LAW_LJC, LAW_LJC_LINEAR
+
+_LJC_LAWS = (LAW_LJC, LAW_LJC_LINEAR)
 
 _SIDE: dict = {}  # device index -> the stream that recomputes chunk positions
 
@@ -41,7 +43,7 @@ class _Cfg:
 
 
 def _prm(cfg, sig_t, eps_t):
-    if cfg.law != LAW_LJC:
+    if cfg.law not in _LJC_LAWS:
         return None
     t = cfg.types.long()
     return api.pack_ljc(cfg.q, sig_t.double()[t], eps_t.double()[t], cfg.types, kq=cfg.kq)
@@ -96,7 +98,7 @@ class NBodyLeapfrog(torch.autograd.Function):
             lam_v[:, :3] = gv
         grad_m = torch.zeros(n, dtype=torch.float32, device=dev)
         grad_t = torch.zeros(2 * cfg.ntypes, dtype=torch.float64, device=dev)
-        gt = grad_t if cfg.law == LAW_LJC else None
+        gt = grad_t if cfg.law in _LJC_LAWS else None
         if gv is not None and bool(torch.any(gv != 0)):
             api.adjoint(pos_T, lam_v, ctx.prm, law=cfg.law, G=cfg.G, eps=cfg.eps,
                         alpha=0.5 * cfg.dt, grad_x=lam_x, grad_m=grad_m, grad_types=gt,
@@ -139,7 +141,7 @@ class NBodyLeapfrog(torch.autograd.Function):
                                  first=starts[c] == 0, law=cfg.law, G=cfg.G, eps=cfg.eps,
                                  grad_m=grad_m, grad_types=gt, ntypes=cfg.ntypes, stream=main)
         g_sig = g_eps = None
-        if cfg.law == LAW_LJC:
+        if cfg.law in _LJC_LAWS:
             g_sig = grad_t[:cfg.ntypes].to(torch.float32)
             g_eps = grad_t[cfg.ntypes:].to(torch.float32)
         return lam_x[:, :3].clone(), lam_v[:, :3].clone(), grad_m, g_sig, g_eps, None
@@ -148,10 +150,13 @@ class NBodyLeapfrog(torch.autograd.Function):
 def leapfrog(x0, v0, m, *, dt, nsteps, k=20, G=1.0, eps=0.0, law=LAW_GRAV, q=None,
              types=None, sig_t=None, eps_t=None, kq=None):
     """Differentiable leapfrog: returns (x_T, v_T); gradients flow to x0, v0, m
-    and (LJC) sig_t, eps_t. Gravity by default; pass law=LAW_LJC with per-atom
-    charges q (float64), int32 types and per-type sig_t, eps_t for LJ + Coulomb."""
-    if law == LAW_LJC:
-        kq = api.COULOMB_K / 80.0 if kq is None else kq
+    and (LJC) sig_t, eps_t. Gravity by default; pass law=LAW_LJC (or
+    LAW_LJC_LINEAR, the linear dielectric) with per-atom charges q (float64),
+    int32 types and per-type sig_t, eps_t for LJ + Coulomb; kq defaults to
+    k_e / 80 (constant) or k_e / 4 (linear, dielectric 4 r)."""
+    if law in _LJC_LAWS:
+        if kq is None:
+            kq = api.COULOMB_K / (80.0 if law == LAW_LJC else 4.0)
         ntypes = int(sig_t.shape[0])
         cfg = _Cfg(law, dt, nsteps, k, G, eps, q=q, types=types, kq=kq, ntypes=ntypes)
     else:

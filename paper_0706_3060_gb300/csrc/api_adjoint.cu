@@ -30,6 +30,7 @@ struct VjpScratch {
 // Tile table of a VJP-kernel law (gravity VJP, LJC VJP, acceleration + jerk).
 int vjp_table(int law) {
   if (law == kLawGAJ) return kTableJerk;
+  if (law == NBODY_LAW_LJC_LINEAR) return kTableVjpLJCLin;
   return law == NBODY_LAW_LJC ? kTableVjpLJC : kTableVjpGrav;
 }
 
@@ -68,12 +69,13 @@ int vjp_prepare(int law, int n, int tile, int jsplit, int sms, cudaStream_t s, V
   }
   const int len = int(round_up(size_t((n + S - 1) / S), size_t(d.jt)));
   S = (n + len - 1) / len;
-  const int blocks = (law == NBODY_LAW_LJC || law == kLawGAJ) ? 2 : 1;
+  const bool ljc = (law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR);
+  const int blocks = (ljc || law == kLawGAJ) ? 2 : 1;
   const size_t part = round_up(size_t(blocks) * S * size_t(n) * sizeof(float4), 256);
   const size_t ubytes = round_up(size_t(n) * sizeof(float4), 256);
   const int nblk = (n + 255) / 256;
   const size_t tbytes = round_up(size_t(nblk) * 8 * sizeof(double), 256);
-  const int pair_f4 = law == NBODY_LAW_LJC ? 5 : 4;  // float4s per packed source pair
+  const int pair_f4 = ljc ? 5 : 4;  // float4s per packed source pair
   const size_t jbytes =
       d.packed ? round_up(size_t((n + 1) / 2) * pair_f4 * sizeof(float4), 256) : 0;
   void *base = nullptr;
@@ -102,14 +104,15 @@ int vjp_once(const float4 *pos, const float4 *prm, const float4 *lam, float4 *gr
   int *err = nullptr;
   NB_TRY(error_word(&err));
   const float4 *src = lam;
-  if (p.law == NBODY_LAW_LJC) {
+  const bool ljc = (p.law == NBODY_LAW_LJC || p.law == NBODY_LAW_LJC_LINEAR);
+  if (ljc) {
     lam_over_m_kernel<<<(n + 255) / 256, 256, 0, s>>>(lam, pos, sc.u, n);
     NB_CUDA(cudaGetLastError());
     src = sc.u;
   }
   if (sc.d->packed) {
     const unsigned pblocks = unsigned(((n + 1) / 2 + 255) / 256);
-    if (p.law == NBODY_LAW_LJC)
+    if (ljc)
       interleave_ljc_vjp_pairs_kernel<<<pblocks, 256, 0, s>>>(pos, src, prm, sc.jp, n);
     else
       interleave_vjp_pairs_kernel<<<pblocks, 256, 0, s>>>(pos, src, sc.jp, n);
@@ -151,7 +154,7 @@ int vjp_once(const float4 *pos, const float4 *prm, const float4 *lam, float4 *gr
   f.grad_x = grad_x;
   f.grad_m = grad_m;
   f.accumulate = accumulate;
-  const bool types = grad_types && p.law == NBODY_LAW_LJC;
+  const bool types = grad_types && ljc;
   f.type_part = types ? sc.type_part : nullptr;
   f.lam_v = lam_v;
   f.dt_next = dt_next;
@@ -167,11 +170,11 @@ int vjp_once(const float4 *pos, const float4 *prm, const float4 *lam, float4 *gr
 int check_common(const nbody_params *p, const void *pos, const void *prm, int64_t n,
                  int ntypes, const double *grad_types) {
   if (!p) return set_error_msg(NBODY_EINVAL, "params is NULL");
-  if (p->law != NBODY_LAW_GRAV && p->law != NBODY_LAW_LJC)
+  if (p->law != NBODY_LAW_GRAV && p->law != NBODY_LAW_LJC && p->law != NBODY_LAW_LJC_LINEAR)
     return set_error_msg(NBODY_EINVAL, "unknown law %d", p->law);
   if (n < 0 || n > 0x7fffffffLL) return set_error_msg(NBODY_EINVAL, "n out of range");
   if (!pos) return set_error_msg(NBODY_EINVAL, "pos_m is NULL");
-  if (p->law == NBODY_LAW_LJC && !prm) return set_error_msg(NBODY_EINVAL, "LJC needs prm");
+  if (p->law != NBODY_LAW_GRAV && !prm) return set_error_msg(NBODY_EINVAL, "LJC needs prm");
   if (grad_types && (ntypes < 1 || ntypes > 4))
     return set_error_msg(NBODY_EUNSUPPORTED, "per-type gradients support 1..4 types");
   if (!(p->eps2 >= 0.0f)) return set_error_msg(NBODY_EINVAL, "eps2 must be >= 0");
@@ -300,7 +303,7 @@ int nbody_adjoint(const void *pos_m, const void *prm, const void *lam, void *gra
   VjpScratch sc{};
   NB_TRY(vjp_prepare(p.law, int(n), p.tile, p.jsplit, sms, s, &sc));
   const int acc = (p.flags & NBODY_ACCUMULATE) ? 1 : 0;
-  if (grad_types && !acc && p.law == NBODY_LAW_LJC) {
+  if (grad_types && !acc && p.law != NBODY_LAW_GRAV) {
     zero_doubles_kernel<<<1, 32, 0, s>>>(grad_types, 2 * ntypes);
     NB_CUDA(cudaGetLastError());
   }

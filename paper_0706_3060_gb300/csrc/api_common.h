@@ -66,14 +66,16 @@ int sync_and_check(cudaStream_t s);
 
 // Tile tables: 0 gravity, 1 LJC, 2 LJC linear, 3 the batched mixed-law kernel,
 // 4 gravity with fixed-point accumulation, 5 the gravity VJP, 6 the LJC VJP,
-// 7 acceleration + jerk. Tables 5-7 describe kernels of vjp_kernel.cuh (their
+// 7 acceleration + jerk, 8 the LJC(linear) VJP. Tables 5-8 describe kernels of
+// vjp_kernel.cuh (their
 // TileDesc has no force launcher; vjp_tiles() gives the launchers).
 constexpr int kTableBatched = 3;
 constexpr int kTableGravFixed = 4;
 constexpr int kTableVjpGrav = 5;
 constexpr int kTableVjpLJC = 6;
 constexpr int kTableJerk = 7;
-constexpr int kTables = 8;
+constexpr int kTableVjpLJCLin = 8;
+constexpr int kTables = 9;
 const TileDesc *tiles_for(int law, int *count);
 // Decide (tile, slices, slice_len) for a single-system evaluation.
 struct Plan1 {

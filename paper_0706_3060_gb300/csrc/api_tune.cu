@@ -37,9 +37,12 @@ int run_once(int table, const void *pos, const void *prm, int64_t n, float eps2,
       return nbody_forces(pos, prm, out0, nullptr, n, &p, st);
     case kTableVjpGrav:
     case kTableVjpLJC:
+    case kTableVjpLJCLin:
       // lambda = the positions: any finite values time the same
-      p.law = table == kTableVjpLJC ? NBODY_LAW_LJC : NBODY_LAW_GRAV;
-      return nbody_adjoint(pos, table == kTableVjpLJC ? prm : nullptr, pos, out0, outm,
+      p.law = table == kTableVjpLJC      ? NBODY_LAW_LJC
+              : table == kTableVjpLJCLin ? NBODY_LAW_LJC_LINEAR
+                                         : NBODY_LAW_GRAV;
+      return nbody_adjoint(pos, table == kTableVjpGrav ? nullptr : prm, pos, out0, outm,
                            nullptr, 0, 1.0f, n, &p, st);
     case kTableJerk:
       p.law = NBODY_LAW_GRAV;
@@ -64,7 +67,7 @@ int nbody_tune(int32_t table, const void *pos_m, const void *prm, int64_t n, flo
   if (reps < 1 || reps > 1000) return set_error_msg(NBODY_EINVAL, "reps must be in 1..1000");
   if (!pos_m) return set_error_msg(NBODY_EINVAL, "pos_m is NULL");
   const bool needs_prm = table == NBODY_LAW_LJC || table == NBODY_LAW_LJC_LINEAR ||
-                         table == kTableVjpLJC;
+                         table == kTableVjpLJC || table == kTableVjpLJCLin;
   if (needs_prm && !prm) return set_error_msg(NBODY_EINVAL, "this table needs prm");
   if (table == kTableGravFixed && !(eps2 > 0.0f))
     return set_error_msg(NBODY_EINVAL, "fixed-point tuning needs eps2 > 0");

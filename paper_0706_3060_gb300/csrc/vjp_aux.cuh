@@ -3,6 +3,7 @@
 // Non-template kernels: included by exactly one translation unit (api_adjoint.cu).
 #pragma once
 
+#include "nbody.h"
 #include "vjp_kernel.cuh"
 
 namespace nbody {
@@ -35,7 +36,7 @@ __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs
   if (i < f.n) {
     float4 hA = f.part_hi[i], oA = f.part_lo[i];
     float4 hB = make_float4(0.f, 0.f, 0.f, 0.f), oB = hB;
-    const bool lj = (f.law == kLawLJC);
+    const bool lj = (f.law == NBODY_LAW_LJC || f.law == NBODY_LAW_LJC_LINEAR);
     if (lj) {
       hB = f.part_hi[f.bstride + i];
       oB = f.part_lo[f.bstride + i];

@@ -102,7 +102,10 @@ __device__ __forceinline__ void grav_vjp_pair2(float2 X, float2 Y, float2 Z, flo
   aw = __ffma2_rn(ld, y3, aw);
 }
 
-template <bool MASK>
+// LIN: linear dielectric (Table 1 LJC(linear)): the Coulomb part of phi is
+// 2 q~q~ y^4 instead of q~q~ y^3, and its share of 2 phi' is -4 y^2 times it
+// instead of -3 y^2 times it.
+template <bool MASK, bool LIN = false>
 __device__ __forceinline__ void ljc_vjp_pair(const float4 pj, const float4 uj, const float4 qj,
                                              float xk, float yk, float zk, float ukx, float uky,
                                              float ukz, float qk, float sk, float ek, float4 &A,
@@ -119,13 +122,13 @@ __device__ __forceinline__ void ljc_vjp_pair(const float4 pj, const float4 uj, c
   const float ee = ek * qj.z;
   const float t = (s * s) * y2;
   const float u = (t * t) * t;
-  const float qy3 = qq * (y * y2);
+  const float qy3 = LIN ? (qq * y2) * (y2 + y2) : qq * (y * y2);  // Coulomb part of phi
   const float eey2 = ee * y2;
   const float h = fmaf(u, 2.0f, -1.0f) * u;
   const float phi_lj = eey2 * h;
   const float phi = phi_lj + qy3;
   const float k1 = fmaf(u, -28.0f, 8.0f) * u;
-  const float tp = y2 * fmaf(eey2, k1, -3.0f * qy3);
+  const float tp = y2 * fmaf(eey2, k1, (LIN ? -4.0f : -3.0f) * qy3);
   const float wx = ukx - uj.x;
   const float wy = uky - uj.y;
   const float wz = ukz - uj.z;
@@ -146,6 +149,7 @@ __device__ __forceinline__ void ljc_vjp_pair(const float4 pj, const float4 uj, c
 // The LJC VJP pair for two sources at once (f32x2), the same terms in the same
 // order as ljc_vjp_pair. Sources arrive as (x x y y)(z z q q)(s s e e)
 // (-ux -ux -uy -uy)(-uz -uz 0 0): the negated u_j makes w = u_k - u_j one add.
+template <bool LIN = false>
 __device__ __forceinline__ void ljc_vjp_pair2(const float4 F0, const float4 F1, const float4 F2,
                                               const float4 F3, const float4 F4, float2 nxk,
                                               float2 nyk, float2 nzk, float2 ukx, float2 uky,
@@ -162,15 +166,16 @@ __device__ __forceinline__ void ljc_vjp_pair2(const float4 F0, const float4 F1, 
   const float2 ee = __fmul2_rn(ek, make_float2(F2.z, F2.w));
   const float2 t = __fmul2_rn(__fmul2_rn(s, s), y2);
   const float2 u = __fmul2_rn(__fmul2_rn(t, t), t);
-  const float2 qy3 = __fmul2_rn(qq, __fmul2_rn(y, y2));
+  const float2 qy3 = LIN ? __fmul2_rn(__fmul2_rn(qq, y2), __fadd2_rn(y2, y2))
+                         : __fmul2_rn(qq, __fmul2_rn(y, y2));
   const float2 eey2 = __fmul2_rn(ee, y2);
   const float2 h = __fmul2_rn(__ffma2_rn(u, make_float2(2.0f, 2.0f), make_float2(-1.0f, -1.0f)), u);
   const float2 phi_lj = __fmul2_rn(eey2, h);
   const float2 phi = __fadd2_rn(phi_lj, qy3);
   const float2 k1 =
       __fmul2_rn(__ffma2_rn(u, make_float2(-28.0f, -28.0f), make_float2(8.0f, 8.0f)), u);
-  const float2 tp =
-      __fmul2_rn(y2, __ffma2_rn(eey2, k1, __fmul2_rn(make_float2(-3.0f, -3.0f), qy3)));
+  const float kc = LIN ? -4.0f : -3.0f;
+  const float2 tp = __fmul2_rn(y2, __ffma2_rn(eey2, k1, __fmul2_rn(make_float2(kc, kc), qy3)));
   const float2 wx = __fadd2_rn(ukx, make_float2(F3.x, F3.y));
   const float2 wy = __fadd2_rn(uky, make_float2(F3.z, F3.w));
   const float2 wz = __fadd2_rn(ukz, make_float2(F4.x, F4.y));
@@ -249,10 +254,10 @@ struct VjpTile {
   static constexpr int kThreads = NT + 32;
   static constexpr int kSlots = NT / SW;
   static constexpr int kTileI = kSlots * I;
-  static constexpr int kStreams = (LAW == kLawLJC) ? 3 : 2;
+  static constexpr int kStreams = is_ljc(LAW) ? 3 : 2;
   static constexpr size_t kSmemBytes = size_t(kStages) * JT * 16 * kStreams;
   // packed sources: float4s per source pair (gravity VJP and jerk 4, LJC VJP 5)
-  static constexpr int kPairF4 = (LAW == kLawLJC) ? 5 : 4;
+  static constexpr int kPairF4 = is_ljc(LAW) ? 5 : 4;
   static constexpr int kStageF4 = kPairF4 * JT / 2;  // float4s of one ring stage
   static_assert(!PK || kStageF4 <= JT * kStreams, "packed stage exceeds the ring");
 };
@@ -301,7 +306,8 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
   constexpr int NWARPS = NT / 32;
   constexpr int SLOTS = T::kSlots;
   constexpr int TI = T::kTileI;
-  constexpr bool LJ = (LAW == kLawLJC);
+  constexpr bool LJ = is_ljc(LAW);
+  constexpr bool LIN = (LAW == kLawLJCLin);  // linear dielectric
   constexpr bool GJ = (LAW == kLawGAJ);
   constexpr bool TWO = LJ || GJ;  // second accumulator block in use
 
@@ -469,7 +475,7 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
           const float4 F3 = pk[5 * pp + 3], F4 = pk[5 * pp + 4];
 #pragma unroll
           for (int r = 0; r < I; ++r)
-            ljc_vjp_pair2(F0, F1, F2, F3, F4, make_float2(-xk[r], -xk[r]),
+            ljc_vjp_pair2<LIN>(F0, F1, F2, F3, F4, make_float2(-xk[r], -xk[r]),
                           make_float2(-yk[r], -yk[r]), make_float2(-zk[r], -zk[r]),
                           make_float2(lx[r], lx[r]), make_float2(ly[r], ly[r]),
                           make_float2(lz[r], lz[r]), make_float2(qk[r], qk[r]),
@@ -501,7 +507,7 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
           const int jg = cj0 + jj;
 #pragma unroll
           for (int r = 0; r < I; ++r)
-            ljc_vjp_pair<true>(pj, uj, qj, xk[r], yk[r], zk[r], lx[r], ly[r], lz[r], qk[r],
+            ljc_vjp_pair<true, LIN>(pj, uj, qj, xk[r], yk[r], zk[r], lx[r], ly[r], lz[r], qk[r],
                                sk[r], ek[r], pA[r], pB[r], jg == ig[r]);
         }
       }
@@ -603,7 +609,7 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
           const float4 qj = sq[jj];
 #pragma unroll
           for (int r = 0; r < I; ++r)
-            ljc_vjp_pair<false>(pj, uj, qj, xk[r], yk[r], zk[r], lx[r], ly[r], lz[r], qk[r],
+            ljc_vjp_pair<false, LIN>(pj, uj, qj, xk[r], yk[r], zk[r], lx[r], ly[r], lz[r], qk[r],
                                 sk[r], ek[r], pA[r], pB[r], false);
         }
       } else {
@@ -614,7 +620,7 @@ __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
           const int jg = cj0 + jj;
 #pragma unroll
           for (int r = 0; r < I; ++r)
-            ljc_vjp_pair<true>(pj, uj, qj, xk[r], yk[r], zk[r], lx[r], ly[r], lz[r], qk[r],
+            ljc_vjp_pair<true, LIN>(pj, uj, qj, xk[r], yk[r], zk[r], lx[r], ly[r], lz[r], qk[r],
                                sk[r], ek[r], pA[r], pB[r], jg == ig[r]);
         }
       }

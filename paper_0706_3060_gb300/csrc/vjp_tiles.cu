@@ -66,6 +66,7 @@ struct VjpImpl {
 
 // Rows: (law, consumer threads, targets per thread, j-lanes, j-tile, packed,
 // unroll). Row 0 is the default for large N, row 1 for small N (below 8192).
+// Tables: gravity VJP, LJC VJP, LJC(linear) VJP, acceleration + jerk.
 #define NB_VJP_GRAV_ROWS(X)                                         \
   X(kLawGrav, 256, 2, 1, 256, true, 2)                              \
   X(kLawGrav, 128, 2, 4, 256, false, 2)                             \
@@ -89,6 +90,11 @@ struct VjpImpl {
   X(kLawLJC, 128, 2, 1, 256, true, 2)                               \
   X(kLawLJC, 256, 1, 1, 256, true, 2)                               \
   X(kLawLJC, 128, 1, 1, 512, true, 4)
+#define NB_VJP_LJCLIN_ROWS(X)                                       \
+  X(kLawLJCLin, 128, 2, 1, 256, true, 2)                            \
+  X(kLawLJCLin, 128, 1, 4, 256, false, 2)                           \
+  X(kLawLJCLin, 256, 1, 1, 256, true, 2)                            \
+  X(kLawLJCLin, 256, 2, 1, 256, false, 2)
 #define NB_VJP_GAJ_ROWS(X)                                          \
   X(kLawGAJ, 256, 2, 1, 256, false, 2)                              \
   X(kLawGAJ, 128, 2, 4, 256, false, 2)                              \
@@ -106,15 +112,18 @@ struct VjpImpl {
 const VjpDesc kGravDesc[] = {NB_VJP_GRAV_ROWS(NB_VJP_DESC)};
 const VjpDesc kLjcDesc[] = {NB_VJP_LJC_ROWS(NB_VJP_DESC)};
 const VjpDesc kGajDesc[] = {NB_VJP_GAJ_ROWS(NB_VJP_DESC)};
+const VjpDesc kLjcLinDesc[] = {NB_VJP_LJCLIN_ROWS(NB_VJP_DESC)};
 const TileDesc kGravTile[] = {NB_VJP_GRAV_ROWS(NB_VJP_TILE)};
 const TileDesc kLjcTile[] = {NB_VJP_LJC_ROWS(NB_VJP_TILE)};
 const TileDesc kGajTile[] = {NB_VJP_GAJ_ROWS(NB_VJP_TILE)};
+const TileDesc kLjcLinTile[] = {NB_VJP_LJCLIN_ROWS(NB_VJP_TILE)};
 
 #undef NB_VJP_DESC
 #undef NB_VJP_TILE
 #undef NB_VJP_GRAV_ROWS
 #undef NB_VJP_LJC_ROWS
 #undef NB_VJP_GAJ_ROWS
+#undef NB_VJP_LJCLIN_ROWS
 
 template <class T, size_t N>
 constexpr int count_of(const T (&)[N]) {
@@ -128,6 +137,7 @@ const VjpDesc *vjp_tiles(int table, int *count) {
     case kTableVjpGrav: *count = count_of(kGravDesc); return kGravDesc;
     case kTableVjpLJC: *count = count_of(kLjcDesc); return kLjcDesc;
     case kTableJerk: *count = count_of(kGajDesc); return kGajDesc;
+    case kTableVjpLJCLin: *count = count_of(kLjcLinDesc); return kLjcLinDesc;
     default: *count = 0; return nullptr;
   }
 }
@@ -137,6 +147,7 @@ const TileDesc *vjp_tile_descs(int table, int *count) {
     case kTableVjpGrav: *count = count_of(kGravTile); return kGravTile;
     case kTableVjpLJC: *count = count_of(kLjcTile); return kLjcTile;
     case kTableJerk: *count = count_of(kGajTile); return kGajTile;
+    case kTableVjpLJCLin: *count = count_of(kLjcLinTile); return kLjcLinTile;
     default: *count = 0; return nullptr;
   }
 }

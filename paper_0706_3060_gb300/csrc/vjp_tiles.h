@@ -19,7 +19,8 @@ struct VjpDesc {
   int (*occupancy)();  // resident CTAs per SM, cached per device
 };
 
-// Launchers of tile table `table` (kTableVjpGrav, kTableVjpLJC or kTableJerk);
+// Launchers of tile table `table` (kTableVjpGrav, kTableVjpLJC, kTableJerk or
+// kTableVjpLJCLin);
 // nullptr for any other table.
 const VjpDesc *vjp_tiles(int table, int *count);
 // The same tables as TileDesc rows (for tile_count / tile_info / tuning).

@@ -19,7 +19,7 @@ import numpy as np
 
 from . import api
 from ._lib import (LAW_GRAV, LAW_LJC, LAW_LJC_LINEAR, TABLE_BATCHED, TABLE_GRAV_FIXED,
-                   TABLE_JERK, TABLE_VJP_GRAV, TABLE_VJP_LJC)
+                   TABLE_JERK, TABLE_VJP_GRAV, TABLE_VJP_LJC, TABLE_VJP_LJC_LINEAR)
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
@@ -76,8 +76,10 @@ def _vjp_timer(torch, table):
         else:
             gx = torch.zeros_like(pos)
             gm = torch.zeros(n, device=pos.device)
-            fn = lambda: api.adjoint(pos, lam, prm, eps=0.01, grad_x=gx, grad_m=gm,  # noqa: E731
-                                     tile=tile, jsplit=jsplit)
+            vlaw = {TABLE_VJP_GRAV: LAW_GRAV, TABLE_VJP_LJC: LAW_LJC,
+                    TABLE_VJP_LJC_LINEAR: LAW_LJC_LINEAR}[table]
+            fn = lambda: api.adjoint(pos, lam, prm, law=vlaw, eps=0.01, grad_x=gx,  # noqa: E731
+                                     grad_m=gm, tile=tile, jsplit=jsplit)
         fn()
         ts = []
         for _ in range(reps):
@@ -100,7 +102,8 @@ def tune(law: int, sizes, jsplits=(0, 1, 2, 4, 8, 16, 32), reps=5, verbose=True,
     import torch
     if native:
         table = {}
-        in_law = LAW_LJC if law in (LAW_LJC, LAW_LJC_LINEAR, TABLE_VJP_LJC) else LAW_GRAV
+        in_law = (LAW_LJC if law in (LAW_LJC, LAW_LJC_LINEAR, TABLE_VJP_LJC, TABLE_VJP_LJC_LINEAR)
+                  else LAW_GRAV)
         for n in sizes:
             pos, prm = _inputs(torch, in_law, n)
             got = api.tune_table(law, pos, prm, eps=0.01, reps=reps)
@@ -115,9 +118,9 @@ def tune(law: int, sizes, jsplits=(0, 1, 2, 4, 8, 16, 32), reps=5, verbose=True,
         raise ValueError("the fixed-point table is tuned by the library (native=True)")
     timer = time_config
     in_law = law
-    if law in (TABLE_VJP_GRAV, TABLE_VJP_LJC, TABLE_JERK):
+    if law in (TABLE_VJP_GRAV, TABLE_VJP_LJC, TABLE_VJP_LJC_LINEAR, TABLE_JERK):
         timer = _vjp_timer(torch, law)
-        in_law = LAW_LJC if law == TABLE_VJP_LJC else LAW_GRAV
+        in_law = LAW_LJC if law in (TABLE_VJP_LJC, TABLE_VJP_LJC_LINEAR) else LAW_GRAV
     table = {}
     for n in sizes:
         pos, prm = _inputs(torch, in_law, n)
@@ -223,7 +226,7 @@ def load_cache(path: str = CACHE) -> int:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--law", choices=["grav", "ljc", "ljclin", "fixed", "batched", "vjp",
-                                      "vjpljc", "jerk"], default="grav")
+                                      "vjpljc", "vjpljclin", "jerk"], default="grav")
     ap.add_argument("--n", type=int, nargs="+", default=[1024, 4096, 16384, 65536, 262144])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--save", action="store_true")
@@ -238,7 +241,8 @@ def main():
             save_cache(TABLE_BATCHED, table)
         return
     law = {"grav": LAW_GRAV, "ljc": LAW_LJC, "ljclin": LAW_LJC_LINEAR, "fixed": TABLE_GRAV_FIXED,
-           "vjp": TABLE_VJP_GRAV, "vjpljc": TABLE_VJP_LJC, "jerk": TABLE_JERK}[a.law]
+           "vjp": TABLE_VJP_GRAV, "vjpljc": TABLE_VJP_LJC, "vjpljclin": TABLE_VJP_LJC_LINEAR,
+           "jerk": TABLE_JERK}[a.law]
     table = tune(law, a.n, reps=a.reps, native=not a.python)
     print(json.dumps(table))
     if a.save:

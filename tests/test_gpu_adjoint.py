@@ -119,7 +119,7 @@ def _grav_autograd_grads(g, dt, nsteps, k, target):
     loss = ((xT - tgt) ** 2).sum() / xT.shape[0]
     loss.backward()
     nb.sync_check()
-    return x0.grad.cpu().numpy(), v0.grad.cpu().numpy(), m0.grad.cpu().numpy(), float(loss)
+    return x0.grad.cpu().numpy(), v0.grad.cpu().numpy(), m0.grad.cpu().numpy(), float(loss.detach())
 
 
 def test_reverse_leapfrog_vs_oracle_gradient():
@@ -236,3 +236,68 @@ def test_every_family_bitwise_repeatable():
         b = [t.clone() for t in fn()]
         for u, w in zip(a, b):
             assert torch.equal(u, w), k
+
+
+def _ljclin_setup(n, seed):
+    """Positions, masses and LJ(linear) parameters packed with kq = k_e / 4 (the
+    dielectric 4 r), and the matching oracle system."""
+    nb = lib()
+    K = 332.0637
+    s = workloads.ljc_sphere(n, seed=seed)
+    x, v, m, q, st, et = s.f32()
+    d = dev()
+    pos = torch.from_numpy(np.concatenate([x, m[:, None]], 1).astype(np.float32)).to(d)
+    prm = nb.pack_ljc(torch.from_numpy(q.astype(np.float64)).to(d),
+                      torch.from_numpy(st.astype(np.float64)[s.types]).to(d),
+                      torch.from_numpy(et.astype(np.float64)[s.types]).to(d),
+                      torch.from_numpy(s.types).to(d), kq=K / 4.0)
+    xd, vd, md, qd, std, etd = s.f32_as_f64()
+    sysm = oracle.LJCSystem(md, qd, s.types, std, etd, K / 4.0, linear=True)
+    return s, pos.contiguous(), prm, sysm, xd, vd
+
+
+@pytest.mark.parametrize("tile", range(4))
+@pytest.mark.parametrize("n", [600, 3001])
+def test_ljc_linear_vjp_every_tile(tile, n):
+    """LJC(linear) VJP (dielectric 4 r) with mass and per-type derivatives, every
+    tile of its table, against the oracle."""
+    nb = lib()
+    s, pos, prm, sysm, x, _ = _ljclin_setup(n, 80 + n)
+    lam = np.random.default_rng(n).standard_normal((n, 4)).astype(np.float32)
+    gx, gm, gt = nb.adjoint(pos, torch.from_numpy(lam).to(dev()), prm,
+                            law=nb.LAW_LJC_LINEAR, tile=tile)
+    rg, rm, rs, re = sysm.vjp(x, lam[:, :3].astype(np.float64))
+    assert _rel(gx[:, :3].cpu().numpy(), rg) <= 2e-5, tile
+    assert _rel(gm.cpu().numpy(), rm) <= 2e-5, tile
+    got_t = gt.cpu().numpy()
+    assert _rel(got_t[:4], rs) <= 2e-5 and _rel(got_t[4:], re) <= 2e-5, tile
+
+
+def test_ljc_linear_reverse_leapfrog_vs_oracle():
+    nb = lib()
+    from paper_0706_3060_gb300.autograd import leapfrog
+    s = workloads.ljc_sphere(300, seed=15, radius=20.0)
+    x, v, m, q, st, et = s.f32()
+    d = dev()
+    x0 = torch.from_numpy(x).to(d).requires_grad_(True)
+    v0 = torch.from_numpy(v).to(d).requires_grad_(True)
+    m0 = torch.from_numpy(m).to(d).requires_grad_(True)
+    sig = torch.from_numpy(st).to(d).requires_grad_(True)
+    eps = torch.from_numpy(et).to(d).requires_grad_(True)
+    dt, T = 1e-4, 12
+    xT, _ = leapfrog(x0, v0, m0, dt=dt, nsteps=T, k=5, law=nb.LAW_LJC_LINEAR,
+                     q=torch.from_numpy(q.astype(np.float64)).to(d),
+                     types=torch.from_numpy(s.types).to(d), sig_t=sig, eps_t=eps)
+    target = workloads.perturbed_target(x.astype(np.float64), seed=4)
+    loss = ((xT - torch.from_numpy(target.astype(np.float32)).to(d)) ** 2).sum() / 300
+    loss.backward()
+    xo, vo, mo, qo, so, eo = s.f32_as_f64()
+    sysm = oracle.LJCSystem(mo, qo, s.types, so, eo, 332.0637 / 4.0, linear=True)
+    xs, _ = oracle.leapfrog(sysm, xo, vo, dt, T, store=True)
+    ref = oracle.adjoint_leapfrog(sysm, xo, vo, dt, T, oracle.target_loss_grad(xs[-1], target),
+                                  xs=xs)
+    assert _rel(x0.grad.cpu().numpy(), ref["x0"]) <= 1e-4
+    assert _rel(v0.grad.cpu().numpy(), ref["v0"]) <= 1e-4
+    assert _rel(m0.grad.cpu().numpy(), ref["m"]) <= 1e-3
+    assert _rel(sig.grad.cpu().numpy(), ref["sig_t"]) <= 1e-3
+    assert _rel(eps.grad.cpu().numpy(), ref["eps_t"]) <= 1e-3

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_version_and_tiles(lib):
     import paper_0706_3060_gb300 as nb
     assert nb.version() >= 10000
-    for law in range(8):
+    for law in range(9):
         c = nb.tile_count(law)
         assert c >= 4
         for t in range(c):
@@ -62,7 +62,7 @@ def test_tuned_table_roundtrip(lib):
     assert nb.get_config(nb.TABLE_VJP_GRAV, 16384) == (2, 4)
     nb.set_tuned(nb.TABLE_VJP_GRAV, 16384, -1, 0)
     with pytest.raises(nb.NBodyError):
-        nb.tile_count(8)
+        nb.tile_count(9)
 
 
 def test_bad_arguments_rejected_without_gpu(lib):
@@ -108,7 +108,8 @@ def test_tune_rejects_bad_arguments_without_gpu(lib):
     args = (ctypes.byref(t), ctypes.byref(j), ctypes.byref(ms), None)
     # the batched table is tuned over a system table, not here
     assert lib.nbody_tune(3, ctypes.c_void_p(16), None, 1024, 1e-4, 3, *args) == 6
-    assert lib.nbody_tune(8, ctypes.c_void_p(16), None, 1024, 1e-4, 3, *args) == 6
+    assert lib.nbody_tune(9, ctypes.c_void_p(16), None, 1024, 1e-4, 3, *args) == 6
+    assert lib.nbody_tune(8, ctypes.c_void_p(16), None, 1024, 1e-4, 3, *args) == 1  # prm
     assert lib.nbody_tune(0, ctypes.c_void_p(16), None, 0, 1e-4, 3, *args) == 1
     assert lib.nbody_tune(0, ctypes.c_void_p(16), None, 1024, 1e-4, 0, *args) == 1
     assert lib.nbody_tune(0, None, None, 1024, 1e-4, 3, *args) == 1
