@@ -394,8 +394,99 @@ def extras(nb, torch, dev, g, eps):
     ex.update(batched_extras(nb, torch, dev))
     ex.update(adjoint_extras(nb, torch, dev))
     ex.update(secondary_kernel_extras(nb, torch, dev, pos, eps))
+    ex["roofline_by_form"] = roofline_by_form(nb, torch, dev)
     ex["oracle_gpairs_per_s"] = oracle_family_rates()
     return ex
+
+
+def roofline_by_form(nb, torch, dev):
+    """Each all-pairs kernel against the FP32 lane peak: its FP32 lane ops per
+    pair (counted from the source; MUFU apart) times the pairs of one launch,
+    over the launch's device time from the library's kernel timers (CUDA events
+    on the launching stream), median of 3 timed launches after one warm-up."""
+    import workloads
+    props = torch.cuda.get_device_properties(dev)
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    K = 332.0637
+
+    def kernel_ms(fn, which):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            nb.timing_read(which)
+            nb.timing_enable(True)
+            fn()
+            torch.cuda.synchronize()
+            nb.timing_enable(False)
+            k, ms = nb.timing_read(which)
+            ts.append(ms / max(k, 1))
+        return float(np.median(ts))
+
+    def grav(n, seed=1):
+        g = workloads.plummer(n, seed=seed, eps=workloads.plummer_softening(n))
+        x, v, m = g.f32()
+        p = torch.from_numpy(np.concatenate([x, m[:, None]], 1)).to(dev).contiguous()
+        vv = torch.from_numpy(np.concatenate([v, np.zeros((n, 1), np.float32)], 1)).to(dev)
+        return p, vv.contiguous(), float(np.float32(g.eps))
+
+    def ljc(n, kq):
+        s = workloads.ljc_sphere(n, seed=2)
+        x, _, m, q, st, et = s.f32()
+        p = torch.from_numpy(np.concatenate([x, m[:, None]], 1)).to(dev).contiguous()
+        prm = nb.pack_ljc(torch.from_numpy(q.astype(np.float64)).to(dev),
+                          torch.from_numpy(st.astype(np.float64)[s.types]).to(dev),
+                          torch.from_numpy(et.astype(np.float64)[s.types]).to(dev),
+                          torch.from_numpy(s.types).to(dev), kq=kq)
+        return p, prm
+
+    out = {"peak_tflops": peak, "basis": "FP32 lane ops per pair x pairs / kernel time"}
+    rows = []
+    pg, vg, eg = grav(262144)
+    acc = torch.empty_like(pg)
+    rows.append(("gravity forces", 262144, 12,
+                 kernel_ms(lambda: nb.forces(pg, eps=eg, out=acc), 0)))
+    rows.append(("acceleration + jerk", 262144, 26,
+                 kernel_ms(lambda: nb.forces_jerk(pg, vg, eps=eg), 0)))
+    lp, lprm = ljc(65536, K / 80.0)
+    lacc = torch.empty_like(lp)
+    rows.append(("LJC forces", 65536, 23, kernel_ms(lambda: nb.forces(lp, lprm, out=lacc), 0)))
+    lp2, lprm2 = ljc(65536, K / 4.0)
+    rows.append(("LJC(linear) forces", 65536, 24,
+                 kernel_ms(lambda: nb.forces(lp2, lprm2, law=nb.LAW_LJC_LINEAR, out=lacc), 0)))
+    pv, _, ev = grav(65536, seed=4)
+    lam = torch.randn_like(pv)
+    gx, gm = torch.empty_like(pv), torch.empty(65536, device=dev)
+    rows.append(("gravity VJP", 65536, 29,
+                 kernel_ms(lambda: nb.adjoint(pv, lam, eps=ev, grad_x=gx, grad_m=gm), 1)))
+    gt = torch.zeros(8, dtype=torch.float64, device=dev)
+    rows.append(("LJC VJP", 65536, 48,
+                 kernel_ms(lambda: nb.adjoint(lp, lam, lprm, grad_x=gx, grad_m=gm,
+                                              grad_types=gt), 1)))
+    rows.append(("LJC(linear) VJP", 65536, 49,
+                 kernel_ms(lambda: nb.adjoint(lp2, lam, lprm2, law=nb.LAW_LJC_LINEAR, grad_x=gx,
+                                              grad_m=gm, grad_types=gt), 1)))
+    for name, n, ops, ms in rows:
+        pairs = float(n) * n
+        t = ops * pairs / (ms * 1e-3) / 1e12
+        out[name] = {"n": n, "ops_per_pair": ops, "kernel_ms": ms,
+                     "gpairs_per_s": pairs / (ms * 1e-3) / 1e9, "achieved_tflops": t,
+                     "frac": t / peak}
+    # the batched persistent kernel over the 512-system ensemble (12 ops per
+    # gravity pair, 23 per LJC pair)
+    ens = workloads.ensemble(nsys=512, seed=3)
+    bpos, bvel, bprm, table = _ensemble_arrays(nb, torch, dev, ens)
+    bacc = torch.zeros_like(bpos)
+    plan = nb.BatchPlan(table)
+    ms = kernel_ms(lambda: plan.run(bpos, bvel, bacc, bprm, nsteps=0, graph=False), 0)
+    plan.close()
+    pg2 = sum(float(x.n) ** 2 for x in ens.systems if isinstance(x, workloads.GravInput))
+    pl2 = sum(float(x.n) ** 2 for x in ens.systems if not isinstance(x, workloads.GravInput))
+    t = (12 * pg2 + 23 * pl2) / (ms * 1e-3) / 1e12
+    out["batched ensemble"] = {"systems": 512, "pairs": pg2 + pl2, "kernel_ms": ms,
+                               "gpairs_per_s": (pg2 + pl2) / (ms * 1e-3) / 1e9,
+                               "achieved_tflops": t, "frac": t / peak}
+    return out
 
 
 def oracle_family_rates():
