@@ -280,3 +280,25 @@ def test_batched_linear_dielectric_systems():
     o, n = table[2]["offset"], table[2]["n"]
     ex = traj_errors(p1[o:o + n, :3].cpu().numpy(), xr)
     assert ex[0] <= 1e-6, ex
+
+
+def test_batched_50_steps_against_conditioning_floor(small_ensemble):
+    """The batched workload's 50 steps (graph-replayed) for a 24-system ensemble:
+    each system's trajectory against the oracle, within 10x the oracle's own
+    conditioning floor (its run from positions perturbed by 1e-7 relative)."""
+    nb = lib()
+    pos, vel, prm, table = _pack_ensemble(small_ensemble)
+    acc = torch.zeros_like(pos)
+    plan = nb.BatchPlan(table)
+    plan.run(pos, vel, acc, prm, nsteps=50, graph=True)
+    pn = pos.cpu().numpy()
+    rng = np.random.default_rng(6)
+    for k, s in enumerate(small_ensemble.systems):
+        sysm, x, v = _oracle_system(s)
+        dt = DT_GRAV if isinstance(s, workloads.GravInput) else DT_LJC
+        xr, _ = oracle.leapfrog(sysm, x, v, dt, 50)
+        xp, _ = oracle.leapfrog(sysm, x * (1.0 + 1e-7 * rng.standard_normal(x.shape)), v, dt, 50)
+        floor = traj_errors(xp, xr)
+        o = table[k]["offset"]
+        got = traj_errors(pn[o:o + s.n, :3], xr)
+        assert got[0] <= 10.0 * floor[0] + 1e-7, (k, got, floor)
