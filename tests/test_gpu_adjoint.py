@@ -214,6 +214,34 @@ def test_adjoint_workload_size_one_chunk():
     assert _rel(gm, ref["m"]) <= 1e-3
 
 
+def test_adjoint_workload_translation_identities():
+    """The full adjoint workload in the bench's configuration (N = 16384, 200 steps
+    at dt = 1e-4, checkpoints every 20): properties that hold at any size. The
+    forces are translation invariant, so shifting every x0 by e shifts x_T by e
+    and boosting every v0 by e shifts x_T by T dt e; hence
+      sum_i dL/dx0_i = (2/N) sum_i (x_T,i - x*_i),  sum_i dL/dv0_i = T dt times it."""
+    nb = lib()
+    from paper_0706_3060_gb300.autograd import leapfrog
+    n, T, dt = 16384, 200, 1e-4
+    g = workloads.plummer(n, seed=4, eps=workloads.plummer_softening(n))
+    target = workloads.perturbed_target(g.f32_as_f64()[0], seed=4)
+    x, v, m = g.f32()
+    d = dev()
+    x0 = torch.from_numpy(x).to(d).requires_grad_(True)
+    v0 = torch.from_numpy(v).to(d).requires_grad_(True)
+    m0 = torch.from_numpy(m).to(d).requires_grad_(True)
+    xT, _ = leapfrog(x0, v0, m0, dt=dt, nsteps=T, k=20, eps=float(np.float32(g.eps)))
+    loss = ((xT - torch.from_numpy(target.astype(np.float32)).to(d)) ** 2).sum() / n
+    loss.backward()
+    nb.sync_check()
+    resid = (xT.detach().double().cpu().numpy() - target).sum(axis=0) * 2.0 / n
+    sx = x0.grad.double().cpu().numpy().sum(axis=0)
+    sv = v0.grad.double().cpu().numpy().sum(axis=0)
+    scale = np.abs(x0.grad.double().cpu().numpy()).sum(axis=0)
+    assert np.all(np.abs(sx - resid) <= 1e-5 * scale + 1e-12), (sx, resid)
+    assert np.all(np.abs(sv - T * dt * resid) <= 1e-5 * T * dt * scale + 1e-12), (sv, resid)
+
+
 def test_every_family_bitwise_repeatable():
     """Fixed-order reductions: the same call twice gives identical bits for the
     LJC forces, both VJPs and acceleration + jerk (a race in a ring stage or a
