@@ -432,3 +432,17 @@ def test_workspace_size_covers_the_partials():
     assert w2 >= 2 * 2 * n * 16 + (n // 2) * 32
     assert w8 - w2 == 2 * 6 * n * 16
     assert nb.workspace_size(n, eps=0.01, report_rows=10) > nb.workspace_size(n, eps=0.01)
+
+
+@pytest.mark.slow
+def test_subset_largest_size():
+    """N = 2^24 Plummer particles (16.8 M sources, 268 MB of positions): forces on 512
+    sampled targets through the subset path, against the oracle one by one."""
+    nb = lib()
+    n = 1 << 24
+    g = workloads.plummer(n, seed=9, eps=workloads.plummer_softening(n))
+    pos, _ = grav_tensors(g)
+    idx = np.sort(np.random.default_rng(2).choice(n, 512, replace=False)).astype(np.int32)
+    eps = float(np.float32(g.eps))
+    a = nb.forces_subset(pos, torch.from_numpy(idx).to(dev()), eps=eps).cpu().numpy()
+    assert_forces_close(a[:, :3], _grav_ref(g, idx=idx.astype(np.int64)), what="N=2^24 subset")
