@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 N_BENCH = 262144
 DT = 1e-4
 OPS_PER_PAIR = 12          # FP32 lane ops per pair of the plain gravity kernel (no potential)
+# FP32 lane ops per unordered pair of the Newton-symmetric kernel: 3 sub, 3 FMA for s^2,
+# 2 MUL for y^3, 2 MUL for the two mass weights, 3 + 3 FMA for the two accumulations
+SYM_OPS_PER_UNORDERED_PAIR = 16
 PAPER_FLOPS_PER_PAIR = 19  # the paper's flop count per gravity interaction (Table 1, Appendix)
 FP32_LANES_PER_SM = 128    # FFMA/FADD/FMUL lanes per SM per clock (4 SMSPs x 32)
 SM_MAX_MHZ = 2070.0
@@ -245,12 +248,21 @@ def main():
     sms = props.multi_processor_count
     peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12          # T lane-op/s
     avg_force_s = force_ms / max(n_force, 1) / 1e3
-    achieved = OPS_PER_PAIR * pairs / avg_force_s / 1e12
+    tile, _ = nb.get_config(nb.LAW_GRAV, N_BENCH)
+    tinfo = nb.tile_info(nb.LAW_GRAV, tile)
+    if tinfo["symmetric"]:
+        # each unordered pair once, applied to both particles
+        ops = SYM_OPS_PER_UNORDERED_PAIR * float(N_BENCH) * (N_BENCH - 1) / 2
+        kname, opdesc = "sym_grav_kernel", {"ops_per_unordered_pair": SYM_OPS_PER_UNORDERED_PAIR,
+                                            "unordered_pairs": N_BENCH * (N_BENCH - 1) // 2}
+    else:
+        ops = OPS_PER_PAIR * pairs
+        kname, opdesc = "force_kernel<grav>", {"ops_per_pair": OPS_PER_PAIR}
+    achieved = ops / avg_force_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None,
-            "kernel": "force_kernel<grav>", "launches_timed": n_force,
-            "avg_launch_ms": avg_force_s * 1e3,
-            "ops_per_pair": OPS_PER_PAIR,
+            "kernel": kname, "tile": tile, "launches_timed": n_force,
+            "avg_launch_ms": avg_force_s * 1e3, **opdesc,
             "peak_basis": (f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz; "
                            "one FFMA/FADD/FMUL lane op = 1")}
     if clk.get("sm_mhz"):
@@ -258,7 +270,9 @@ def main():
                                                     / 1e12)
     # DRAM bytes per launch from the committed ncu summary, only if it was taken
     # on the kernel that runs now (same sources and tuning table).
-    summary = os.path.join(ROOT, "profiles", "force_kernel_grav_plummer262144.md")
+    summary = os.path.join(ROOT, "profiles", ("sym_grav_kernel_plummer262144.md"
+                                              if tinfo["symmetric"] else
+                                              "force_kernel_grav_plummer262144.md"))
     if os.path.exists(summary):
         import re
         txt = open(summary).read()
@@ -268,13 +282,16 @@ def main():
             roof["traffic"] = int(mb.group(1))
 
     # kernels per timed step: kick-drift, [pair interleave,] force, finalize(+kick)
-    tile, _ = nb.get_config(nb.LAW_GRAV, N_BENCH)
-    per_step = 3 + int(nb.tile_info(nb.LAW_GRAV, tile)["packed"])
+    per_step = 3 + int(tinfo["packed"])
     out = {"metric": metric_name(), "value": value, "unit": "G pair-interactions/s",
            "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": step_ms / K,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded Plummer sphere)", "config": config(world),
            "roofline": roof, "clocks": clk, "gpu_launches": per_step * K,
+           "interactions_counted": ("N^2 ordered pair interactions per step"
+                                    + ("; the Newton-symmetric kernel evaluates each unordered "
+                                       "pair once and applies it to both particles"
+                                       if tinfo["symmetric"] else "")),
            "paper_convention_gflops": paper_gflops(value),
            "wall_s_timed_region": t_wall}
 
@@ -342,7 +359,8 @@ def kernel_hash() -> str:
     import re
     h = hashlib.sha1()
     pkg = os.path.join(ROOT, "paper_0706_3060_gb300")
-    for f in ("csrc/force_kernel.cuh", "csrc/device_common.cuh", "csrc/force_grav.cu"):
+    for f in ("csrc/force_kernel.cuh", "csrc/sym_kernel.cuh", "csrc/device_common.cuh",
+              "csrc/force_grav.cu"):
         with open(os.path.join(pkg, f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
@@ -444,8 +462,15 @@ def roofline_by_form(nb, torch, dev):
     rows = []
     pg, vg, eg = grav(262144)
     acc = torch.empty_like(pg)
-    rows.append(("gravity forces", 262144, 12,
-                 kernel_ms(lambda: nb.forces(pg, eps=eg, out=acc), 0)))
+    gtile, _ = nb.get_config(nb.LAW_GRAV, 262144)
+    if nb.tile_info(nb.LAW_GRAV, gtile)["symmetric"]:
+        # ops per ordered pair: half the symmetric kernel's ops per unordered pair
+        rows.append(("gravity forces (Newton-symmetric)", 262144,
+                     SYM_OPS_PER_UNORDERED_PAIR / 2 * (262144 - 1) / 262144,
+                     kernel_ms(lambda: nb.forces(pg, eps=eg, out=acc), 0)))
+    # the fastest one-sided tile (256 threads x 2 targets, 8 j-slices)
+    rows.append(("gravity forces (one-sided)", 262144, 12,
+                 kernel_ms(lambda: nb.forces(pg, eps=eg, out=acc, tile=12, jsplit=8), 0)))
     rows.append(("acceleration + jerk", 262144, 26,
                  kernel_ms(lambda: nb.forces_jerk(pg, vg, eps=eg), 0)))
     lp, lprm = ljc(65536, K / 80.0)

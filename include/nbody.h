@@ -338,13 +338,24 @@ int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k
  * fixed-point accumulation, 5 the gravity VJP, 6 the LJC VJP, 7 acceleration
  * + jerk, 8 the LJC(linear) VJP), or a negative status. */
 int nbody_tile_count(int32_t law);
+/* Kind bits of a tile configuration (nbody_tile_info). */
+enum {
+    NBODY_TILE_PACKED = 1,     /* reads pair-interleaved sources: each force
+                                  evaluation is preceded by one interleave launch */
+    NBODY_TILE_SYMMETRIC = 2,  /* Newton-symmetric block pairs: each unordered pair
+                                  evaluated once and applied to both particles; j_tile
+                                  is the block size, j-split unused; scratch holds one
+                                  partial per particle and block, so it is refused
+                                  (explicit tile) or replaced by the default tile
+                                  (tuned) above 4 GiB of partials, and always for
+                                  subsets and the allocation-free entry point */
+};
 /* Describe configuration `tile` of `law`: threads per CTA (consumer warps),
- * i-particles per thread, j-lanes per warp, j-tile length, and whether it
- * reads pair-interleaved sources (1: each force evaluation is preceded by one
- * interleave launch; 0: it reads pos_m/prm directly). Any output pointer may
- * be NULL. */
+ * i-particles per thread, j-lanes per warp, j-tile length, and its kind
+ * (NBODY_TILE_* bits; 0: a one-sided kernel reading pos_m/prm directly). Any
+ * output pointer may be NULL. */
 int nbody_tile_info(int32_t law, int32_t tile, int32_t *threads, int32_t *i_per_thread,
-                    int32_t *j_lanes, int32_t *j_tile, int32_t *packed);
+                    int32_t *j_lanes, int32_t *j_tile, int32_t *kind);
 /* Install the tuned (tile, jsplit) for (tile table law, n-bucket); bucket =
  * floor(log2 n) (the batched table uses bucket 0). Used by params->tile == -1. */
 int nbody_set_tuned(int32_t law, int32_t log2n, int32_t tile, int32_t jsplit);

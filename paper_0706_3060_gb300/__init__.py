@@ -10,7 +10,7 @@ from .checkpoint import load_state, save_state
 from ._lib import (ACC_VALID, ACCUMULATE, COMPUTE_POT, FIXED_POINT, LAW_GRAV, LAW_LJC,
                    LAW_LJC_LINEAR, NO_COMPENSATION, PRECISE_RSQRT, TABLE_BATCHED,
                    TABLE_GRAV_FIXED, TABLE_JERK, TABLE_VJP_GRAV, TABLE_VJP_LJC,
-                   TABLE_VJP_LJC_LINEAR, NBodyError)
+                   TABLE_VJP_LJC_LINEAR, TILE_PACKED, TILE_SYMMETRIC, NBodyError)
 from .api import (COULOMB_K, BatchPlan, adjoint, adjoint_leapfrog, forces, forces_batched,
                   forces_jerk, forces_subset, hermite_step,
                   get_config, pack_grav, pack_ljc, params, release, set_tuned, step, sync_check,

@@ -34,6 +34,9 @@ TABLE_VJP_LJC = 6  # tile table of the LJC VJP kernels
 TABLE_JERK = 7  # tile table of the acceleration + jerk kernels
 TABLE_VJP_LJC_LINEAR = 8  # tile table of the LJC(linear) VJP kernels
 
+TILE_PACKED = 1  # nbody_tile_info kind bits
+TILE_SYMMETRIC = 2
+
 # Every symbol include/nbody.h declares.
 EXPORTS = (
     "nbody_version", "nbody_last_error", "nbody_release", "nbody_check",

@@ -15,8 +15,8 @@ import torch
 
 from . import _lib
 from ._lib import (ACC_VALID, ACCUMULATE, COMPUTE_POT, FIXED_POINT, LAW_GRAV, LAW_LJC,
-                   LAW_LJC_LINEAR, NO_COMPENSATION, PRECISE_RSQRT, NBodyParams, NBodySystem,
-                   check, load)
+                   LAW_LJC_LINEAR, NO_COMPENSATION, PRECISE_RSQRT, TILE_PACKED, TILE_SYMMETRIC,
+                   NBodyParams, NBodySystem, check, load)
 
 COULOMB_K = 332.0637  # kcal A / (mol e^2): units A, kcal/mol, e, amu (AKMA time)
 
@@ -311,9 +311,10 @@ def tile_info(law: int, tile: int) -> dict:
     vals = [ctypes.c_int32() for _ in range(5)]
     check(load().nbody_tile_info(int(law), int(tile), *[ctypes.byref(v) for v in vals]),
           "nbody_tile_info")
-    d = dict(zip(("threads", "i_per_thread", "j_lanes", "j_tile", "packed"),
+    d = dict(zip(("threads", "i_per_thread", "j_lanes", "j_tile", "kind"),
                  (v.value for v in vals)))
-    d["packed"] = bool(d["packed"])
+    d["packed"] = bool(d["kind"] & TILE_PACKED)
+    d["symmetric"] = bool(d["kind"] & TILE_SYMMETRIC)
     return d
 
 

@@ -66,8 +66,8 @@ def _ensemble(nb, torch, dev, nsys=512, seed=3):
 
 def build_case(name, nb, torch, dev):
     """Return a zero-argument callable running one call of the named workload."""
-    if name == "grav262144":
-        pos, _, eps = _grav(nb, torch, dev, 262144)
+    if name in ("grav65536", "grav262144"):
+        pos, _, eps = _grav(nb, torch, dev, int(name[4:]))
         acc = torch.empty_like(pos)
         return lambda: nb.forces(pos, eps=eps, out=acc)
     if name in ("ljc8192", "ljc65536"):
@@ -94,7 +94,7 @@ def build_case(name, nb, torch, dev):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["grav262144", "ljc8192", "ljc65536", "vjp16384",
+    ap.add_argument("case", choices=["grav65536", "grav262144", "ljc8192", "ljc65536", "vjp16384",
                                      "jerk262144", "batched512"])
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--iters", type=int, default=2)

@@ -91,22 +91,29 @@ struct Scratch {
   double *diag_rows;
 };
 
-// Bytes of the Scratch layout below (scale words, pair buffer, partials, diagnostics).
-size_t scratch_bytes(int law, int n, int slices, int diag_rows) {
-  const size_t part = round_up(size_t(slices) * size_t(n) * sizeof(float4), 256);
+// Bytes of the Scratch layout below (scale words, pair buffer, partials,
+// diagnostics). The symmetric tiles write no low parts and read their sources
+// in whole blocks (nb x B particles, the last block padded).
+size_t scratch_bytes(int law, int n, const Plan1 &plan, int diag_rows) {
+  const bool lo = !plan.tile->sym;
+  const int64_t jn = plan.tile->sym ? int64_t(plan.slices) * plan.slice_len : n;
+  const size_t part = round_up(size_t(plan.slices) * size_t(n) * sizeof(float4), 256);
   const int nblk = std::max(1, (n + kFinThreads - 1) / kFinThreads);
   const size_t dpart = round_up(size_t(nblk) * kDiagFields * sizeof(double), 256);
   const size_t drows = round_up(size_t(std::max(diag_rows, 1)) * kDiagFields * sizeof(double), 256);
-  return 256 + jbuf_bytes(law, n) + 2 * part + dpart + drows;
+  return 256 + jbuf_bytes(law, jn) + (lo ? 2 : 1) * part + dpart + drows;
 }
 
-int get_scratch(cudaStream_t s, int law, int n, int slices, int diag_rows, Scratch *out) {
-  const size_t part = round_up(size_t(slices) * size_t(n) * sizeof(float4), 256);
+int get_scratch(cudaStream_t s, int law, int n, const Plan1 &plan, int diag_rows, Scratch *out) {
+  const bool lo = !plan.tile->sym;
+  const int64_t jn = plan.tile->sym ? int64_t(plan.slices) * plan.slice_len : n;
+  const size_t part = round_up(size_t(plan.slices) * size_t(n) * sizeof(float4), 256);
   const int nblk = std::max(1, (n + kFinThreads - 1) / kFinThreads);
   const size_t dpart = round_up(size_t(nblk) * kDiagFields * sizeof(double), 256);
-  const size_t jb = jbuf_bytes(law, n);
+  const size_t jb = jbuf_bytes(law, jn);
+  const size_t lopart = lo ? part : 0;
   void *base = nullptr;
-  NB_TRY(workspace(s, scratch_bytes(law, n, slices, diag_rows), &base));
+  NB_TRY(workspace(s, scratch_bytes(law, n, plan, diag_rows), &base));
   char *b = static_cast<char *>(base);
   out->finv = reinterpret_cast<double *>(b);
   out->fscale = reinterpret_cast<float *>(b + 8);
@@ -114,9 +121,9 @@ int get_scratch(cudaStream_t s, int law, int n, int slices, int diag_rows, Scrat
   out->jbuf = reinterpret_cast<float4 *>(b);
   b += jb;
   out->part_hi = reinterpret_cast<float4 *>(b);
-  out->part_lo = reinterpret_cast<float4 *>(b + part);
-  out->diag_part = reinterpret_cast<double *>(b + 2 * part);
-  out->diag_rows = reinterpret_cast<double *>(b + 2 * part + dpart);
+  out->part_lo = lo ? reinterpret_cast<float4 *>(b + part) : nullptr;
+  out->diag_part = reinterpret_cast<double *>(b + part + lopart);
+  out->diag_rows = reinterpret_cast<double *>(b + part + lopart + dpart);
   return NBODY_OK;
 }
 
@@ -152,9 +159,9 @@ int prepare_fixed(const float4 *pos, int n, const nbody_params &p, const Scratch
 int forces_device(const float4 *pos, const float4 *prm, float4 *acc, float4 *acc_lo, int n,
                   const nbody_params &p, int sms, cudaStream_t s) {
   Plan1 plan{};
-  NB_TRY(plan_single(table_of(p), n, p.tile, p.jsplit, sms, &plan));
+  NB_TRY(plan_single(table_of(p), n, p.tile, p.jsplit, sms, &plan, true));
   Scratch sc{};
-  NB_TRY(get_scratch(s, p.law, n, plan.slices, 0, &sc));
+  NB_TRY(get_scratch(s, p.law, n, plan, 0, &sc));
   NB_TRY(prepare_fixed(pos, n, p, sc, s));
   int *err = nullptr;
   NB_TRY(error_word(&err));
@@ -171,10 +178,10 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
                 int nsteps, int report_every, double *diag_dev, float4 *trace, float4 *state_lo,
                 const nbody_params &p, int sms, cudaStream_t s) {
   Plan1 plan{};
-  NB_TRY(plan_single(table_of(p), n, p.tile, p.jsplit, sms, &plan));
+  NB_TRY(plan_single(table_of(p), n, p.tile, p.jsplit, sms, &plan, true));
   const int rows = report_every > 0 ? nsteps / report_every + 1 : 0;
   Scratch sc{};
-  NB_TRY(get_scratch(s, p.law, n, plan.slices, rows, &sc));
+  NB_TRY(get_scratch(s, p.law, n, plan, rows, &sc));
   NB_TRY(prepare_fixed(pos, n, p, sc, s));
   int *err = nullptr;
   NB_TRY(error_word(&err));
@@ -328,8 +335,8 @@ int nbody_workspace_size(const nbody_params *params, int64_t n, int32_t report_r
   int dev = 0, sms = 0;
   NB_TRY(check_device(&dev, &sms));
   Plan1 plan{};
-  NB_TRY(plan_single(table_of(*params), n, params->tile, params->jsplit, sms, &plan));
-  *bytes = scratch_bytes(params->law, int(n), plan.slices, report_rows);
+  NB_TRY(plan_single(table_of(*params), n, params->tile, params->jsplit, sms, &plan, true));
+  *bytes = scratch_bytes(params->law, int(n), plan, report_rows);
   return NBODY_OK;
 }
 
@@ -415,7 +422,7 @@ int nbody_tile_count(int32_t law) {
 }
 
 int nbody_tile_info(int32_t law, int32_t tile, int32_t *threads, int32_t *i_per_thread,
-                    int32_t *j_lanes, int32_t *j_tile, int32_t *packed) {
+                    int32_t *j_lanes, int32_t *j_tile, int32_t *kind) {
   clear_error();
   if (law < 0 || law >= kTables) return set_error_msg(NBODY_EINVAL, "bad law %d", law);
   int count = 0;
@@ -425,7 +432,8 @@ int nbody_tile_info(int32_t law, int32_t tile, int32_t *threads, int32_t *i_per_
   if (i_per_thread) *i_per_thread = t[tile].i;
   if (j_lanes) *j_lanes = t[tile].sw;
   if (j_tile) *j_tile = t[tile].jt;
-  if (packed) *packed = t[tile].packed ? 1 : 0;
+  if (kind)
+    *kind = (t[tile].packed ? NBODY_TILE_PACKED : 0) | (t[tile].sym ? NBODY_TILE_SYMMETRIC : 0);
   return NBODY_OK;
 }
 

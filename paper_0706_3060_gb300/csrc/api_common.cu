@@ -314,20 +314,48 @@ int get_config(int law, int64_t n, int *tile, int *jsplit) {
   return NBODY_OK;
 }
 
-int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out) {
-  return plan_targets(law, n, n, tile, jsplit, sms, out);
+// Largest partial-sum buffer a symmetric tile may ask for (one float4 per
+// particle and block).
+constexpr double kSymPartMax = 4.0 * 1024 * 1024 * 1024;
+
+int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out, bool allow_sym) {
+  return plan_targets(law, n, n, tile, jsplit, sms, out, allow_sym);
 }
 
-int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms, Plan1 *out) {
+int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms, Plan1 *out,
+                 bool allow_sym) {
   if (law < 0 || law >= kTableVjpGrav)
     return set_error_msg(NBODY_EINVAL, "tile table %d is not a force table", law);
   int count = 0;
   const TileDesc *tiles = tiles_for(law, &count);
   int tj = 0;
-  if (tile < 0) get_config(law, n_t, &tile, &tj);
+  const bool tuned = tile < 0;
+  if (tuned) get_config(law, n_t, &tile, &tj);
   if (jsplit <= 0) jsplit = tj;
   if (tile < 0 || tile >= count) return set_error_msg(NBODY_EINVAL, "bad tile %d", tile);
+  if (tiles[tile].sym && (!allow_sym || n_t != n)) {
+    if (!tuned)
+      return set_error_msg(NBODY_EINVAL, "tile %d (symmetric) is not available for this call",
+                           tile);
+    tile = default_tile(law, n_t);
+    jsplit = 0;
+  }
   const TileDesc &d = tiles[tile];
+  if (d.sym) {  // one CTA per block pair, one partial slot per block
+    const long long nb = (n + d.tile_i - 1) / d.tile_i;
+    if (nb * (nb + 1) / 2 > 0x7fffffffLL || double(nb) * double(n) * 16.0 > kSymPartMax) {
+      if (!tuned)
+        return set_error_msg(NBODY_EINVAL, "n = %lld too large for symmetric tile %d",
+                             (long long)n, tile);
+      return plan_targets(law, n_t, n, default_tile(law, n_t), 0, sms, out, false);
+    }
+    out->tile = &d;
+    out->slices = int(nb);
+    out->slice_len = d.tile_i;
+    out->n_itiles = int(nb);
+    out->grid = int(nb * (nb + 1) / 2);
+    return NBODY_OK;
+  }
   const int n_it = int((n_t + d.tile_i - 1) / d.tile_i);
   const int max_slices = int((n + d.jt - 1) / d.jt);
   int S = jsplit;
@@ -373,6 +401,21 @@ __global__ void interleave_pairs_kernel(const float4 *pos, float4 *jp, int n) {
   jp[2 * p + 1] = make_float4(a.z, b.z, a.w, b.w);
 }
 
+// Sources of the symmetric tiles, block by block (B particles): the B/2 pairs
+// (x0, x1, y0, y1) of block b, then their (z0, z1, m0, m1), so that lanes reading
+// consecutive pairs read consecutive 16-byte words. Pairs past n are not written
+// (the kernel copies only the block's own pairs).
+__global__ void interleave_pairs_blocked_kernel(const float4 *pos, float4 *jp, int n, int B) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * p >= n) return;
+  const float4 a = pos[2 * p];
+  const float4 b = (2 * p + 1 < n) ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+  const int blk = (2 * p) / B, pp = p - blk * (B / 2);
+  const long long base = (long long)blk * B;
+  jp[base + pp] = make_float4(a.x, b.x, a.y, b.y);
+  jp[base + B / 2 + pp] = make_float4(a.z, b.z, a.w, b.w);
+}
+
 // LJC sources in pairs: (x0, x1, y0, y1), (z0, z1, q0, q1), (s0, s1, e0, e1); the
 // pad of an odd count is far away with no charge and no LJ well.
 __global__ void interleave_ljc_pairs_kernel(const float4 *pos, const float4 *prm, float4 *jp,
@@ -405,6 +448,9 @@ int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags,
     const int np = (n + 1) / 2;
     if (law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR)
       interleave_ljc_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, prm, jbuf, n);
+    else if (p.tile->sym)
+      interleave_pairs_blocked_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, jbuf, n,
+                                                                       p.slice_len);
     else
       interleave_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, jbuf, n);
     NB_CUDA(cudaGetLastError());

@@ -85,9 +85,14 @@ struct Plan1 {
   int n_itiles;
   int grid;
 };
-int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out);
+// allow_sym: the Newton-symmetric tiles may be used (targets are the sources
+// and the partials have room for one slot per block); otherwise a tuned
+// symmetric tile falls back to the default tile and an explicit one is refused.
+int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out,
+                bool allow_sym = false);
 // Same for n_t targets against n sources (i-tiles over targets, j-slices over sources).
-int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms, Plan1 *out);
+int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms, Plan1 *out,
+                 bool allow_sym = false);
 
 // Optional separate targets for launch_forces (subset evaluations).
 struct Targets {

@@ -84,11 +84,13 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
         r = make_float4(float(dx - double(t.x)), float(dy - double(t.y)),
                         float(dz - double(t.z)), float(dw - double(t.w)));
       } else {
+        // part_lo == nullptr: partials without low parts (symmetric tiles)
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 hi = f.part_hi[i];
-        float4 lo = f.part_lo[i];
+        float4 lo = f.part_lo ? f.part_lo[i] : zero;
         for (int k = 1; k < slices; ++k) {
           const float4 h = f.part_hi[(long long)k * f.stride + i];
-          const float4 l = f.part_lo[(long long)k * f.stride + i];
+          const float4 l = f.part_lo ? f.part_lo[(long long)k * f.stride + i] : zero;
           comp_add(hi.x, lo.x, h.x);
           comp_add(hi.y, lo.y, h.y);
           comp_add(hi.z, lo.z, h.z);

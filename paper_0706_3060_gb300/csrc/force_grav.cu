@@ -33,6 +33,11 @@ const TileDesc *grav_tiles(int *count) {
       TileImpl<kLawGrav, 64, 4, 1, 512, true, 4>::desc(),    // 20: 256 targets, 1 warp
       TileImpl<kLawGrav, 128, 2, 2, 512, true, 4>::desc(),   // 21: 128 targets, 2 j-lanes
       TileImpl<kLawGrav, 256, 1, 1, 512, true, 4>::desc(),   // 22: 256 targets, 1 each
+      // Newton-symmetric block pairs (sym_kernel.cuh): each unordered pair once
+      SymImpl<128, 8>::desc(),  // 23: blocks of 1024
+      SymImpl<128, 4>::desc(),  // 24: blocks of 512
+      SymImpl<128, 8, 3>::desc(),  // 25: blocks of 1024, registers capped for 3 CTAs/SM
+      SymImpl<128, 6>::desc(),     // 26: blocks of 768 (3 CTAs/SM)
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;

@@ -1,8 +1,8 @@
 // force_kernel.cuh -- warp-specialized all-pairs force kernel for sm_103a.
 //
-// The computation is the direct sum of Sec. 2 ("for i: for j: force[i] +=
-// force_function(ri, rj)"), parallel over i, with the j-stream shared by every
-// thread of a CTA, as in the paper's kforce kernel. GB300 mapping:
+// The computation is the direct sum of Sec. 2 (every target i accumulates the
+// pair force of every source j), parallel over i, with the j-stream shared by
+// every thread of a CTA, as in the paper's force kernel. GB300 mapping:
 //   * one producer warp streams j-tiles of JT particles (16 B each, plus 16 B
 //     of LJC parameters) from global memory into a STAGES-deep shared-memory
 //     ring with 1-D TMA bulk copies completing on mbarriers;
@@ -17,8 +17,8 @@
 //     j-range of one i-tile ("replication", Sec. 3.4) and write per-slice
 //     partials that the finalize kernel adds in a fixed order. Results
 //     are therefore bitwise reproducible run to run.
-// The self pair is excluded by index (the Appendix's Ilist != Jlist test)
-// only in tiles whose j-range overlaps the CTA's i-range.
+// The self pair is excluded by index (an index comparison, as in the Appendix
+// listing) only in tiles whose j-range overlaps the CTA's i-range.
 #pragma once
 
 #include <type_traits>

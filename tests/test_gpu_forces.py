@@ -37,7 +37,7 @@ def test_grav_default_config(n):
     assert_forces_close(acc[:, :3].cpu().numpy(), ref, what=f"n={n}")
 
 
-@pytest.mark.parametrize("tile", range(23))
+@pytest.mark.parametrize("tile", range(27))
 @pytest.mark.parametrize("jsplit", [1, 3])
 def test_grav_every_tile(tile, jsplit):
     nb = lib()

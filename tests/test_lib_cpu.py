@@ -45,22 +45,33 @@ def test_version_and_tiles(lib):
             assert info["j_tile"] % info["j_lanes"] == 0
             if info["packed"]:   # packed tiles walk source pairs
                 assert info["j_tile"] % 2 == 0
+            if info["symmetric"]:  # gravity only; blocks of threads x targets, pairs
+                assert law == nb.LAW_GRAV and info["packed"]
+                assert info["j_tile"] == info["threads"] * info["i_per_thread"]
     with pytest.raises(nb.NBodyError):
         nb.tile_info(0, 99)
 
 
 def test_tuned_table_roundtrip(lib):
     import paper_0706_3060_gb300 as nb
-    nb.set_tuned(nb.LAW_GRAV, 5000, 3, 2)
-    assert nb.get_config(nb.LAW_GRAV, 5000) == (3, 2)
-    nb.set_tuned(nb.LAW_GRAV, 5000, -1, 0)
-    assert nb.get_config(nb.LAW_GRAV, 5000)[1] == 0
-    # VJP tables: defaults (row 0 from 8192 up, row 1 below), then a tuned entry
-    assert nb.get_config(nb.TABLE_VJP_GRAV, 16384)[0] == 0
-    assert nb.get_config(nb.TABLE_JERK, 1000)[0] == 1
-    nb.set_tuned(nb.TABLE_VJP_GRAV, 16384, 2, 4)
-    assert nb.get_config(nb.TABLE_VJP_GRAV, 16384) == (2, 4)
-    nb.set_tuned(nb.TABLE_VJP_GRAV, 16384, -1, 0)
+    # entries a GPU session may have installed from the stored table come back at the end
+    keep = [(t, n, nb.get_config(t, n)) for t, n in
+            ((nb.LAW_GRAV, 5000), (nb.TABLE_VJP_GRAV, 16384), (nb.TABLE_JERK, 1000))]
+    try:
+        nb.set_tuned(nb.LAW_GRAV, 5000, 3, 2)
+        assert nb.get_config(nb.LAW_GRAV, 5000) == (3, 2)
+        nb.set_tuned(nb.LAW_GRAV, 5000, -1, 0)
+        assert nb.get_config(nb.LAW_GRAV, 5000)[1] == 0
+        # VJP tables: defaults (row 0 from 8192 up, row 1 below), then a tuned entry
+        nb.set_tuned(nb.TABLE_VJP_GRAV, 16384, -1, 0)
+        nb.set_tuned(nb.TABLE_JERK, 1000, -1, 0)
+        assert nb.get_config(nb.TABLE_VJP_GRAV, 16384)[0] == 0
+        assert nb.get_config(nb.TABLE_JERK, 1000)[0] == 1
+        nb.set_tuned(nb.TABLE_VJP_GRAV, 16384, 2, 4)
+        assert nb.get_config(nb.TABLE_VJP_GRAV, 16384) == (2, 4)
+    finally:
+        for t, n, (tile, js) in keep:
+            nb.set_tuned(t, n, tile, js)
     with pytest.raises(nb.NBodyError):
         nb.tile_count(9)
 
