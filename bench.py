@@ -34,6 +34,9 @@ OPS_PER_PAIR = 12          # FP32 lane ops per pair of the plain gravity kernel 
 # FP32 lane ops per unordered pair of the Newton-symmetric kernel: 3 sub, 3 FMA for s^2,
 # 2 MUL for y^3, 2 MUL for the two mass weights, 3 + 3 FMA for the two accumulations
 SYM_OPS_PER_UNORDERED_PAIR = 16
+# the same for the Newton-symmetric gravity VJP: 6 for d and s^2, 2 for y^2, y^3, 6 for
+# w, 6 for lam_j.d and lam_k.d, 2 for d.w, 2 for c, 3 for c d + w, 4 + 4 for the two sides
+SYM_VJP_OPS_PER_UNORDERED_PAIR = 35
 PAPER_FLOPS_PER_PAIR = 19  # the paper's flop count per gravity interaction (Table 1, Appendix)
 FP32_LANES_PER_SM = 128    # FFMA/FADD/FMUL lanes per SM per clock (4 SMSPs x 32)
 SM_MAX_MHZ = 2070.0
@@ -482,8 +485,15 @@ def roofline_by_form(nb, torch, dev):
     pv, _, ev = grav(65536, seed=4)
     lam = torch.randn_like(pv)
     gx, gm = torch.empty_like(pv), torch.empty(65536, device=dev)
-    rows.append(("gravity VJP", 65536, 29,
-                 kernel_ms(lambda: nb.adjoint(pv, lam, eps=ev, grad_x=gx, grad_m=gm), 1)))
+    vtile, _ = nb.get_config(nb.TABLE_VJP_GRAV, 65536)
+    if nb.tile_info(nb.TABLE_VJP_GRAV, vtile)["symmetric"]:
+        rows.append(("gravity VJP (Newton-symmetric)", 65536,
+                     SYM_VJP_OPS_PER_UNORDERED_PAIR / 2 * (65536 - 1) / 65536,
+                     kernel_ms(lambda: nb.adjoint(pv, lam, eps=ev, grad_x=gx, grad_m=gm), 1)))
+    # the fastest one-sided VJP tile at this size (256 threads x 1 target, unrolled x4)
+    rows.append(("gravity VJP (one-sided)", 65536, 29,
+                 kernel_ms(lambda: nb.adjoint(pv, lam, eps=ev, grad_x=gx, grad_m=gm, tile=8,
+                                              jsplit=16), 1)))
     gt = torch.zeros(8, dtype=torch.float64, device=dev)
     rows.append(("LJC VJP", 65536, 48,
                  kernel_ms(lambda: nb.adjoint(lp, lam, lprm, grad_x=gx, grad_m=gm,

@@ -43,11 +43,41 @@ int vjp_prepare(int law, int n, int tile, int jsplit, int sms, cudaStream_t s, V
   int count = 0;
   const VjpDesc *tiles = vjp_tiles(table, &count);
   int tj = 0;
-  if (tile < 0) get_config(table, n, &tile, &tj);
+  const bool tuned = tile < 0;
+  if (tuned) get_config(table, n, &tile, &tj);
   if (jsplit <= 0) jsplit = tj;
   if (!tiles || tile < 0 || tile >= count)
     return set_error_msg(NBODY_EINVAL, "bad tile %d for table %d", tile, table);
+  if (tiles[tile].sym && !sym_fits(n, tiles[tile].tile_i)) {
+    if (tuned)  // a tuned symmetric entry above the cap: the default tile instead
+      return vjp_prepare(law, n, default_tile(table, n), 0, sms, s, sc, extra);
+    return set_error_msg(NBODY_EINVAL, "n = %d too large for symmetric tile %d", n, tile);
+  }
   const VjpDesc &d = tiles[tile];
+  if (d.sym) {  // one CTA per block pair, one partial slot per block, no low parts
+    const int nb = (n + d.tile_i - 1) / d.tile_i;
+    const size_t part = round_up(size_t(nb) * size_t(n) * sizeof(float4), 256);
+    const size_t ubytes = round_up(size_t(n) * sizeof(float4), 256);
+    const int nblk = (n + 255) / 256;
+    const size_t tbytes = round_up(size_t(nblk) * 8 * sizeof(double), 256);
+    const size_t jbytes = round_up(size_t(nb) * d.tile_i * 2 * sizeof(float4), 256);
+    void *base = nullptr;
+    NB_TRY(workspace(s, part + ubytes + tbytes + jbytes + extra, &base));
+    char *b = static_cast<char *>(base);
+    sc->part_hi = reinterpret_cast<float4 *>(b);
+    sc->part_lo = nullptr;
+    sc->u = reinterpret_cast<float4 *>(b + part);
+    sc->type_part = reinterpret_cast<double *>(b + part + ubytes);
+    sc->jp = reinterpret_cast<float4 *>(b + part + ubytes + tbytes);
+    sc->extra = b + part + ubytes + tbytes + jbytes;
+    sc->slices = nb;
+    sc->slice_len = d.tile_i;
+    sc->grid = int((long long)nb * (nb + 1) / 2);
+    sc->nblk = nblk;
+    sc->bstride = (long long)nb * n;
+    sc->d = &d;
+    return NBODY_OK;
+  }
   const int n_it = (n + d.tile_i - 1) / d.tile_i;
   const int cap = sms * d.occupancy();
   const int max_s = (n + d.jt - 1) / d.jt;
@@ -112,7 +142,10 @@ int vjp_once(const float4 *pos, const float4 *prm, const float4 *lam, float4 *gr
   }
   if (sc.d->packed) {
     const unsigned pblocks = unsigned(((n + 1) / 2 + 255) / 256);
-    if (ljc)
+    if (sc.d->sym)
+      interleave_vjp_pairs_blocked_kernel<<<pblocks, 256, 0, s>>>(pos, src, sc.jp, n,
+                                                                  sc.slice_len);
+    else if (ljc)
       interleave_ljc_vjp_pairs_kernel<<<pblocks, 256, 0, s>>>(pos, src, prm, sc.jp, n);
     else
       interleave_vjp_pairs_kernel<<<pblocks, 256, 0, s>>>(pos, src, sc.jp, n);

@@ -283,7 +283,7 @@ static int log2_floor(int64_t n) {
 
 // Default tile when nothing is tuned: big register blocks for large N, j-lanes
 // inside the warp for small N (where there are too few targets to fill the GPU).
-static int default_tile(int law, int64_t n) {
+int default_tile(int law, int64_t n) {
   if (law == kTableBatched) return 0;
   if (law >= kTableVjpGrav) return n >= 8192 ? 0 : 1;
   if (law == kTableGravFixed) return n >= 4096 ? 0 : (n >= 1024 ? 2 : 3);
@@ -318,6 +318,11 @@ int get_config(int law, int64_t n, int *tile, int *jsplit) {
 // particle and block).
 constexpr double kSymPartMax = 4.0 * 1024 * 1024 * 1024;
 
+bool sym_fits(int64_t n, int block) {
+  const long long nb = (n + block - 1) / block;
+  return nb * (nb + 1) / 2 <= 0x7fffffffLL && double(nb) * double(n) * 16.0 <= kSymPartMax;
+}
+
 int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out, bool allow_sym) {
   return plan_targets(law, n, n, tile, jsplit, sms, out, allow_sym);
 }
@@ -343,7 +348,7 @@ int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms,
   const TileDesc &d = tiles[tile];
   if (d.sym) {  // one CTA per block pair, one partial slot per block
     const long long nb = (n + d.tile_i - 1) / d.tile_i;
-    if (nb * (nb + 1) / 2 > 0x7fffffffLL || double(nb) * double(n) * 16.0 > kSymPartMax) {
+    if (!sym_fits(n, d.tile_i)) {
       if (!tuned)
         return set_error_msg(NBODY_EINVAL, "n = %lld too large for symmetric tile %d",
                              (long long)n, tile);

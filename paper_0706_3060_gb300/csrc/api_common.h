@@ -88,6 +88,12 @@ struct Plan1 {
 // allow_sym: the Newton-symmetric tiles may be used (targets are the sources
 // and the partials have room for one slot per block); otherwise a tuned
 // symmetric tile falls back to the default tile and an explicit one is refused.
+// The untuned tile of a table at size n (never a symmetric one).
+int default_tile(int law, int64_t n);
+// Whether a Newton-symmetric tile with blocks of `block` particles may run at n:
+// nb (nb + 1) / 2 block pairs within the grid limit and nb x n float4 partials
+// (nb = ceil(n / block)) within 4 GiB.
+bool sym_fits(int64_t n, int block);
 int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out,
                 bool allow_sym = false);
 // Same for n_t targets against n sources (i-tiles over targets, j-slices over sources).

@@ -105,13 +105,7 @@ int nbody_tune(int32_t table, const void *pos_m, const void *prm, int64_t n, flo
     for (int js : kSplits) {
       if (js > 0 && int64_t(js) * tiles[t].jt > n) continue;  // slices shorter than a j-tile
       if (js > 0 && tiles[t].sym) continue;                   // symmetric tiles: no j-split
-      if (tiles[t].sym) {  // above the partial-sum cap the plan refuses the tile
-        Plan1 probe{};
-        if (plan_single(table, n, t, 0, sms, &probe, true) != NBODY_OK) {
-          clear_error();
-          continue;
-        }
-      }
+      if (tiles[t].sym && !sym_fits(n, tiles[t].tile_i)) continue;  // refused by the plan
       if (js == 0 && tiles[t].tile_i > 4 * n) continue;       // far more targets than particles
       st = run_once(table, pos_m, prm, n, eps2, t, js, o0, o1, om, s);  // warm-up
       for (int r = 0; r < reps && st == NBODY_OK; ++r) {

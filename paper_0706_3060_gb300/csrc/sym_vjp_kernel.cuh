@@ -1,0 +1,219 @@
+// sym_vjp_kernel.cuh -- gravity force VJP (J^T lambda and the mass derivative)
+// with each unordered pair evaluated once and applied to both particles.
+//
+// For target k and source j (d = x_j - x_k, y = 1/s, w = m_k lam_j - m_j lam_k)
+// the J^T lambda term y^3 [w - 3 y^2 (d.w) d] changes sign when k and j swap
+// (d and w both do), so the source receives the negated term. The mass term
+// (lam_j . d) y^3 of the target becomes (lam_k . (-d)) y^3 for the source. With
+// ldj = lam_j . d and ldk = lam_k . d, d.w = m_k ldj - m_j ldk, so the pair costs
+// 35 FP32 lane ops for both particles (29 for one in vjp_kernel.cuh).
+//
+// Blocks, block pairs, the per-block partial slots, the rotating lane schedule
+// of the source-side sums and the diagonal blocks (one-sided, self pair masked)
+// follow sym_kernel.cuh. Sources come in the blocked layout of
+// interleave_vjp_pairs_blocked_kernel: per block of B particles the B/2 pairs'
+// (x x y y), then (z z m m), (lx lx ly ly) and (lz lz 0 0) words.
+#pragma once
+
+#include "sym_kernel.cuh"
+#include "vjp_kernel.cuh"
+
+namespace nbody {
+
+template <int NT, int I>
+struct SymVjpTile {
+  static constexpr int kB = NT * I;
+  static constexpr int kPairs = kB / 2;
+  static constexpr int kWarps = NT / 32;
+  static constexpr size_t kSrcBytes = size_t(kPairs) * 64;  // four float4 per pair
+  // source-side sums per warp: g.x, g.y, g.z and the mass term of both halves
+  static constexpr size_t kSmemBytes = kSrcBytes + size_t(kWarps) * 8 * kPairs * sizeof(float);
+};
+
+// One target against one source pair (the halves of the f32x2 values are the
+// two sources). nM = -m_j. Adds the target's terms to (ax, ay, az, aw); with JS
+// also adds the terms the sources receive, before their sign change, to
+// (jx, jy, jz, jw). MASK drops a source half equal to the target (y = 0).
+template <bool JS, bool MASK>
+__device__ __forceinline__ void sym_gvjp_pair2(float2 X, float2 Y, float2 Z, float2 nM,
+                                               float2 LX, float2 LY, float2 LZ, float2 nx,
+                                               float2 ny, float2 nz, float2 mk, float2 lkx,
+                                               float2 lky, float2 lkz, float2 e2, float2 &ax,
+                                               float2 &ay, float2 &az, float2 &aw, float2 &jx,
+                                               float2 &jy, float2 &jz, float2 &jw,
+                                               bool self0 = false, bool self1 = false) {
+  const float2 dx = __fadd2_rn(X, nx);
+  const float2 dy = __fadd2_rn(Y, ny);
+  const float2 dz = __fadd2_rn(Z, nz);
+  float2 s2 = __ffma2_rn(dz, dz, e2);
+  s2 = __ffma2_rn(dy, dy, s2);
+  s2 = __ffma2_rn(dx, dx, s2);
+  float2 y = make_float2(rsqrt_hw(s2.x), rsqrt_hw(s2.y));
+  if (MASK) {
+    y.x = self0 ? 0.0f : y.x;
+    y.y = self1 ? 0.0f : y.y;
+  }
+  const float2 y2 = __fmul2_rn(y, y);
+  const float2 y3 = __fmul2_rn(y2, y);
+  const float2 wx = __ffma2_rn(mk, LX, __fmul2_rn(nM, lkx));
+  const float2 wy = __ffma2_rn(mk, LY, __fmul2_rn(nM, lky));
+  const float2 wz = __ffma2_rn(mk, LZ, __fmul2_rn(nM, lkz));
+  const float2 ldj = __ffma2_rn(LX, dx, __ffma2_rn(LY, dy, __fmul2_rn(LZ, dz)));
+  const float2 ldk = __ffma2_rn(lkx, dx, __ffma2_rn(lky, dy, __fmul2_rn(lkz, dz)));
+  const float2 dw = __ffma2_rn(mk, ldj, __fmul2_rn(nM, ldk));
+  const float2 c = __fmul2_rn(dw, __fmul2_rn(y2, make_float2(-3.0f, -3.0f)));
+  const float2 vx = __ffma2_rn(c, dx, wx);
+  const float2 vy = __ffma2_rn(c, dy, wy);
+  const float2 vz = __ffma2_rn(c, dz, wz);
+  ax = __ffma2_rn(y3, vx, ax);
+  ay = __ffma2_rn(y3, vy, ay);
+  az = __ffma2_rn(y3, vz, az);
+  aw = __ffma2_rn(ldj, y3, aw);
+  if (JS) {
+    jx = __ffma2_rn(y3, vx, jx);
+    jy = __ffma2_rn(y3, vy, jy);
+    jz = __ffma2_rn(y3, vz, jz);
+    jw = __ffma2_rn(ldk, y3, jw);
+  }
+}
+
+// Partials: slot ob of part_hi holds (g.x, g.y, g.z, mass term) of block ob's
+// contribution, before the G scaling of vjp_finalize_kernel.
+template <int NT, int I, int MINB = 1>
+__global__ void __launch_bounds__(NT, MINB) sym_gvjp_kernel(const VjpArgs a) {
+  using T = SymVjpTile<NT, I>;
+  constexpr int B = T::kB;
+  constexpr int P = T::kPairs;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float4 *s0 = reinterpret_cast<float4 *>(smem_raw);  // (x x y y)
+  float4 *s1 = s0 + P;                                 // (z z m m)
+  float4 *s2 = s1 + P;                                 // (lx lx ly ly)
+  float4 *s3 = s2 + P;                                 // (lz lz 0 0)
+  float *jsum = reinterpret_cast<float *>(smem_raw + T::kSrcBytes);
+  __shared__ __align__(8) uint64_t bar;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = a.n;
+  const int nb = a.slices;
+  int bi, bj;
+  sym_tile_of(blockIdx.x, nb, bi, bj);
+  if (bj >= nb) {  // outside the triangle: a launch-shape error
+    if (tid == 0) set_error(a.err, kDevBadItem);
+    return;
+  }
+  const int j0 = bj * B;
+  const int nsrc = min(B, n - j0);
+  const int npairs = (nsrc + 1) >> 1;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t bytes = uint32_t(npairs) * 16u;
+    const float4 *blk = a.jpair + size_t(bj) * 2 * B;  // four arrays of P float4 per block
+    mbar_arrive_expect_tx(&bar, 4 * bytes);
+    tma_load_1d(s0, blk, bytes, &bar);
+    tma_load_1d(s1, blk + P, bytes, &bar);
+    tma_load_1d(s2, blk + 2 * P, bytes, &bar);
+    tma_load_1d(s3, blk + 3 * P, bytes, &bar);
+  }
+  const bool diag = (bi == bj);
+  if (!diag)
+    for (int k = tid; k < T::kWarps * 8 * P; k += NT) jsum[k] = 0.0f;
+
+  // targets of block bi; missing ones are massless, far away and carry no lambda
+  float2 nx[I], ny[I], nz[I], mk[I], lkx[I], lky[I], lkz[I], ax[I], ay[I], az[I], aw[I];
+  int ig[I];
+#pragma unroll
+  for (int r = 0; r < I; ++r) {
+    const int g = bi * B + r * NT + tid;
+    ig[r] = g < n ? g : -1;
+    const float4 p = g < n ? __ldg(a.pos + g) : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+    const float4 l = g < n ? __ldg(a.lam + g) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    nx[r] = make_float2(-p.x, -p.x);
+    ny[r] = make_float2(-p.y, -p.y);
+    nz[r] = make_float2(-p.z, -p.z);
+    mk[r] = make_float2(p.w, p.w);
+    lkx[r] = make_float2(l.x, l.x);
+    lky[r] = make_float2(l.y, l.y);
+    lkz[r] = make_float2(l.z, l.z);
+    ax[r] = ay[r] = az[r] = aw[r] = make_float2(0.0f, 0.0f);
+  }
+  __syncthreads();  // jsum cleared
+  const bool ok = mbar_wait(&bar, 0, a.err);
+  if (!__syncthreads_and(ok)) return;
+  const float2 e2 = make_float2(a.eps2, a.eps2);
+
+  if (diag) {
+    float2 dummy = make_float2(0.0f, 0.0f);
+    for (int pp = 0; pp < npairs; ++pp) {
+      const float4 A = s0[pp], Bq = s1[pp], C = s2[pp], D = s3[pp];
+      const float2 nM = make_float2(-Bq.z, -Bq.w);
+      const int jg = j0 + 2 * pp;
+#pragma unroll
+      for (int r = 0; r < I; ++r)
+        sym_gvjp_pair2<false, true>(make_float2(A.x, A.y), make_float2(A.z, A.w),
+                                    make_float2(Bq.x, Bq.y), nM, make_float2(C.x, C.y),
+                                    make_float2(C.z, C.w), make_float2(D.x, D.y), nx[r], ny[r],
+                                    nz[r], mk[r], lkx[r], lky[r], lkz[r], e2, ax[r], ay[r], az[r],
+                                    aw[r], dummy, dummy, dummy, dummy, jg == ig[r],
+                                    jg + 1 == ig[r]);
+    }
+  } else {
+    float *J = jsum + size_t(warp) * 8 * P;
+    for (int g0 = 0; g0 < npairs; g0 += 32) {
+#pragma unroll 1
+      for (int st = 0; st < 32; ++st) {
+        const int pp = g0 + ((lane + st) & 31);
+        if (pp < npairs) {
+          const float4 A = s0[pp], Bq = s1[pp], C = s2[pp], D = s3[pp];
+          const float2 X = make_float2(A.x, A.y), Y = make_float2(A.z, A.w);
+          const float2 Z = make_float2(Bq.x, Bq.y), nM = make_float2(-Bq.z, -Bq.w);
+          const float2 LX = make_float2(C.x, C.y), LY = make_float2(C.z, C.w);
+          const float2 LZ = make_float2(D.x, D.y);
+          float2 jx = make_float2(0.0f, 0.0f), jy = jx, jz = jx, jw = jx;
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            sym_gvjp_pair2<true, false>(X, Y, Z, nM, LX, LY, LZ, nx[r], ny[r], nz[r], mk[r],
+                                        lkx[r], lky[r], lkz[r], e2, ax[r], ay[r], az[r], aw[r],
+                                        jx, jy, jz, jw);
+          // the sources receive the negated terms
+          J[0 * P + pp] -= jx.x;
+          J[1 * P + pp] -= jx.y;
+          J[2 * P + pp] -= jy.x;
+          J[3 * P + pp] -= jy.y;
+          J[4 * P + pp] -= jz.x;
+          J[5 * P + pp] -= jz.y;
+          J[6 * P + pp] -= jw.x;
+          J[7 * P + pp] -= jw.y;
+        }
+        __syncwarp();  // at the next step lane l - 1 updates the slot lane l just wrote
+      }
+    }
+  }
+
+  const long long ibase = (long long)bj * a.stride;
+#pragma unroll
+  for (int r = 0; r < I; ++r)
+    if (ig[r] >= 0)
+      a.part_hi[ibase + ig[r]] = make_float4(ax[r].x + ax[r].y, ay[r].x + ay[r].y,
+                                             az[r].x + az[r].y, aw[r].x + aw[r].y);
+  if (diag) return;
+  __syncthreads();
+  const long long jbase = (long long)bi * a.stride + j0;
+  for (int q = tid; q < nsrc; q += NT) {
+    const int pp = q >> 1, h = q & 1;
+    float vx = 0.0f, vy = 0.0f, vz = 0.0f, vw = 0.0f;
+    for (int w = 0; w < T::kWarps; ++w) {
+      const float *Jw = jsum + size_t(w) * 8 * P;
+      vx += Jw[(0 + h) * P + pp];
+      vy += Jw[(2 + h) * P + pp];
+      vz += Jw[(4 + h) * P + pp];
+      vw += Jw[(6 + h) * P + pp];
+    }
+    a.part_hi[jbase + q] = make_float4(vx, vy, vz, vw);
+  }
+}
+
+}  // namespace nbody

@@ -34,7 +34,9 @@ __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs
   const int i = blockIdx.x * 256 + threadIdx.x;
   double tv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (i < f.n) {
-    float4 hA = f.part_hi[i], oA = f.part_lo[i];
+    // part_lo == nullptr: partials without low parts (Newton-symmetric gravity tiles)
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 hA = f.part_hi[i], oA = f.part_lo ? f.part_lo[i] : zero;
     float4 hB = make_float4(0.f, 0.f, 0.f, 0.f), oB = hB;
     const bool lj = (f.law == NBODY_LAW_LJC || f.law == NBODY_LAW_LJC_LINEAR);
     if (lj) {
@@ -43,7 +45,7 @@ __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs
     }
     for (int k = 1; k < f.slices; ++k) {
       const long long o = (long long)k * f.stride + i;
-      float4 h = f.part_hi[o], l = f.part_lo[o];
+      float4 h = f.part_hi[o], l = f.part_lo ? f.part_lo[o] : zero;
       comp_add(hA.x, oA.x, h.x);
       comp_add(hA.y, oA.y, h.y);
       comp_add(hA.z, oA.z, h.z);
@@ -165,6 +167,26 @@ __global__ void type_reduce_kernel(const double *part, int nblk, int ntypes, dou
   for (int b = 0; b < nblk; ++b) s += part[(size_t)b * 8 + k];
   const int t = k & 3, which = k >> 2;  // 0: sigma, 1: eps
   if (t < ntypes) out[which * ntypes + t] += s;
+}
+
+// Gravity VJP sources of the Newton-symmetric tiles, block by block (B
+// particles, 2B float4 per block): the B/2 pairs' (x0 x1 y0 y1), then their
+// (z0 z1 m0 m1), (lx0 lx1 ly0 ly1) and (lz0 lz1 0 0). Pairs past n are not written
+// (the kernel copies only the block's own pairs).
+__global__ void interleave_vjp_pairs_blocked_kernel(const float4 *pos, const float4 *lam,
+                                                    float4 *jp, int n, int B) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * p >= n) return;
+  const bool two = 2 * p + 1 < n;
+  const float4 a = pos[2 * p], la = lam[2 * p];
+  const float4 b = two ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+  const float4 lb = two ? lam[2 * p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const int blk = (2 * p) / B, P = B / 2, pp = p - blk * P;
+  const long long q = (long long)blk * 2 * B + pp;
+  jp[q] = make_float4(a.x, b.x, a.y, b.y);
+  jp[q + P] = make_float4(a.z, b.z, a.w, b.w);
+  jp[q + 2 * P] = make_float4(la.x, lb.x, la.y, lb.y);
+  jp[q + 3 * P] = make_float4(la.z, lb.z, 0.f, 0.f);
 }
 
 // Packed gravity VJP sources: per pair (x0 x1 y0 y1)(z0 z1 m0 m1)(lx0 lx1 ly0 ly1)

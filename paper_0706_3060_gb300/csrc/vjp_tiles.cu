@@ -64,6 +64,63 @@ struct VjpImpl {
   }
 };
 
+// Newton-symmetric gravity VJP tiles: blocks of NT * I particles, one CTA per
+// block pair; `tile_i` and `jt` report the block size.
+template <int NT, int I, int MINB = 1>
+struct SymVjpImpl {
+  using T = SymVjpTile<NT, I>;
+  static cudaError_t launch(const VjpArgs &a, int grid, cudaStream_t s) {
+    auto k = sym_gvjp_kernel<NT, I, MINB>;
+    {  // opt in always: the static mbarrier counts against the 48 KB default too
+      static std::atomic<bool> opted[kMaxDevicesTile];
+      int dev = 0;
+      const bool known = cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDevicesTile;
+      if (!known || !opted[dev].load(std::memory_order_acquire)) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)T::kSmemBytes);
+        if (e != cudaSuccess) return e;
+        if (known) opted[dev].store(true, std::memory_order_release);
+      }
+    }
+    k<<<grid, NT, T::kSmemBytes, s>>>(a);
+    return cudaGetLastError();
+  }
+  static int occupancy() {
+    static std::atomic<int> cached[kMaxDevicesTile];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesTile) {
+      cudaGetLastError();
+      dev = -1;
+    }
+    if (dev >= 0) {
+      const int c = cached[dev].load(std::memory_order_relaxed);
+      if (c > 0) return c;
+    }
+    int nb = 0;
+    auto k = sym_gvjp_kernel<NT, I, MINB>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, T::kSmemBytes) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return 1;
+    }
+    nb = std::max(nb, 1);
+    if (dev >= 0) cached[dev].store(nb, std::memory_order_relaxed);
+    return nb;
+  }
+  static VjpDesc desc() {
+    VjpDesc d{T::kB, T::kB, NT, T::kSmemBytes, true, &launch, &occupancy};
+    d.sym = true;
+    return d;
+  }
+  static TileDesc tile() {
+    TileDesc d{kLawGrav, NT, I, 1, T::kB, T::kB, NT, T::kSmemBytes, true, false,
+               nullptr, &occupancy};
+    d.sym = true;
+    return d;
+  }
+};
+
 // Rows: (law, consumer threads, targets per thread, j-lanes, j-tile, packed,
 // unroll). Row 0 is the default for large N, row 1 for small N (below 8192).
 // Tables: gravity VJP, LJC VJP, LJC(linear) VJP, acceleration + jerk.
@@ -109,11 +166,17 @@ struct VjpImpl {
 #define NB_VJP_DESC(L, NT, I, SW, JT, PK, PU) VjpImpl<L, NT, I, SW, JT, PK, PU>::desc(),
 #define NB_VJP_TILE(L, NT, I, SW, JT, PK, PU) VjpImpl<L, NT, I, SW, JT, PK, PU>::tile(),
 
-const VjpDesc kGravDesc[] = {NB_VJP_GRAV_ROWS(NB_VJP_DESC)};
+// the gravity VJP table ends with the Newton-symmetric tiles: blocks of 512, 256,
+// 512 with registers capped for 3 CTAs/SM, 256 in 2-warp CTAs (6 per SM), 384
+#define NB_VJP_GRAV_SYM(F)                                                         \
+  SymVjpImpl<128, 4>::F(), SymVjpImpl<128, 2>::F(), SymVjpImpl<128, 4, 3>::F(),    \
+      SymVjpImpl<64, 4, 6>::F(), SymVjpImpl<128, 3, 4>::F(),
+
+const VjpDesc kGravDesc[] = {NB_VJP_GRAV_ROWS(NB_VJP_DESC) NB_VJP_GRAV_SYM(desc)};
 const VjpDesc kLjcDesc[] = {NB_VJP_LJC_ROWS(NB_VJP_DESC)};
 const VjpDesc kGajDesc[] = {NB_VJP_GAJ_ROWS(NB_VJP_DESC)};
 const VjpDesc kLjcLinDesc[] = {NB_VJP_LJCLIN_ROWS(NB_VJP_DESC)};
-const TileDesc kGravTile[] = {NB_VJP_GRAV_ROWS(NB_VJP_TILE)};
+const TileDesc kGravTile[] = {NB_VJP_GRAV_ROWS(NB_VJP_TILE) NB_VJP_GRAV_SYM(tile)};
 const TileDesc kLjcTile[] = {NB_VJP_LJC_ROWS(NB_VJP_TILE)};
 const TileDesc kGajTile[] = {NB_VJP_GAJ_ROWS(NB_VJP_TILE)};
 const TileDesc kLjcLinTile[] = {NB_VJP_LJCLIN_ROWS(NB_VJP_TILE)};
@@ -121,6 +184,7 @@ const TileDesc kLjcLinTile[] = {NB_VJP_LJCLIN_ROWS(NB_VJP_TILE)};
 #undef NB_VJP_DESC
 #undef NB_VJP_TILE
 #undef NB_VJP_GRAV_ROWS
+#undef NB_VJP_GRAV_SYM
 #undef NB_VJP_LJC_ROWS
 #undef NB_VJP_GAJ_ROWS
 #undef NB_VJP_LJCLIN_ROWS

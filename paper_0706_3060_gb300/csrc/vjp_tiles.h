@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "tiles.h"
+#include "sym_vjp_kernel.cuh"
 #include "vjp_kernel.cuh"
 
 namespace nbody {
@@ -17,6 +18,8 @@ struct VjpDesc {
   bool packed;  // gravity sources and lambdas in the pair-interleaved layout
   cudaError_t (*launch)(const VjpArgs &, int grid, cudaStream_t);
   int (*occupancy)();  // resident CTAs per SM, cached per device
+  bool sym = false;    // Newton-symmetric block pairs (sym_vjp_kernel.cuh): tile_i and
+                       // jt are the block size; one partial slot per block, no low parts
 };
 
 // Launchers of tile table `table` (kTableVjpGrav, kTableVjpLJC, kTableJerk or

@@ -34,7 +34,7 @@ def test_grav_vjp(n):
     assert _rel(gm.cpu().numpy(), rm) <= 2e-5
 
 
-@pytest.mark.parametrize("tile", range(12))
+@pytest.mark.parametrize("tile", range(17))
 @pytest.mark.parametrize("jsplit", [0, 3])
 def test_grav_vjp_every_tile(tile, jsplit):
     """Every compiled gravity VJP tile (packed and scalar, j-lanes, unrolls) at a

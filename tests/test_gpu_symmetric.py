@@ -1,9 +1,10 @@
 """GPU parity of the Newton-symmetric gravity tiles (each unordered pair evaluated
-once and applied to both particles) against the FP64 oracle: block sizes 512
-and 1024, every ragged case of one and several blocks (odd N ends with the pad
-particle), eps = 0 with the self pair masked on diagonal blocks, the potential,
-both rsqrt modes, leapfrog trajectories, run-to-run bitwise reproducibility,
-and the planning rules (no subsets, a cap on the partial-sum memory)."""
+once and applied to both particles) against the FP64 oracle: forces (blocks of
+512, 768 and 1024) and the force VJP (blocks of 256 and 512), every ragged case
+of one and several blocks (odd N ends with the pad particle), eps = 0 with the
+self pair masked on diagonal blocks, the potential, both rsqrt modes, leapfrog
+trajectories, run-to-run bitwise reproducibility, and the planning rules (no
+subsets, a cap on the partial-sum memory)."""
 import numpy as np
 import pytest
 import torch
@@ -135,3 +136,108 @@ def test_symmetric_planning_rules():
     finally:
         nb.set_tuned(nb.LAW_GRAV, n_big, *old)
         nb.set_tuned(nb.LAW_GRAV, 4096, *old_small)
+
+
+def _sym_vjp_tiles():
+    nb = lib()
+    tiles = [t for t in range(nb.tile_count(nb.TABLE_VJP_GRAV))
+             if nb.tile_info(nb.TABLE_VJP_GRAV, t)["symmetric"]]
+    assert tiles, "no symmetric gravity VJP tile compiled"
+    return tiles
+
+
+def _rel(got, ref):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 255, 256, 257, 511, 512, 513, 1025, 3001])
+def test_symmetric_vjp_ragged_sizes(n):
+    nb = lib()
+    g = workloads.plummer(n, seed=700 + n, eps=0.01)
+    pos, _ = grav_tensors(g)
+    eps = float(np.float32(g.eps))
+    lam = np.random.default_rng(n).standard_normal((n, 4)).astype(np.float32)
+    x, _, m = g.f32_as_f64()
+    rg, rm = oracle.grav_vjp(x, m, lam[:, :3].astype(np.float64), G=0.7, eps=eps)
+    for tile in _sym_vjp_tiles():
+        gx, gm, _ = nb.adjoint(pos, torch.from_numpy(lam).to(dev()), G=0.7, eps=eps, tile=tile)
+        gxh, gmh = gx[:, :3].cpu().numpy(), gm.cpu().numpy()
+        assert np.all(np.isfinite(gxh)) and np.all(np.isfinite(gmh))
+        if n == 1:
+            assert np.all(gxh == 0.0) and np.all(gmh == 0.0)
+            continue
+        assert _rel(gxh, rg) <= 2e-5, (tile, n)
+        assert _rel(gmh, rm) <= 2e-5, (tile, n)
+
+
+def test_symmetric_vjp_unsoftened_and_repeatable():
+    """eps = 0: only the diagonal blocks meet the self pair, masked there."""
+    nb = lib()
+    rng = np.random.default_rng(12)
+    for n in (3, 700):
+        x = rng.normal(size=(n, 3))
+        m = rng.uniform(0.5, 2.0, n)
+        pos = torch.from_numpy(np.concatenate([x, m[:, None]], 1).astype(np.float32)).to(dev())
+        lam = rng.standard_normal((n, 4)).astype(np.float32)
+        xd = pos[:, :3].double().cpu().numpy()
+        md = pos[:, 3].double().cpu().numpy()
+        rg, rm = oracle.grav_vjp(xd, md, lam[:, :3].astype(np.float64), eps=0.0)
+        for tile in _sym_vjp_tiles():
+            lt = torch.from_numpy(lam).to(dev())
+            gx, gm, _ = nb.adjoint(pos.contiguous(), lt, eps=0.0, tile=tile)
+            gx2, gm2, _ = nb.adjoint(pos.contiguous(), lt, eps=0.0, tile=tile)
+            assert torch.equal(gx, gx2) and torch.equal(gm, gm2)
+            assert _rel(gx[:, :3].cpu().numpy(), rg) <= 2e-5, (tile, n)
+            assert _rel(gm.cpu().numpy(), rm) <= 2e-5, (tile, n)
+
+
+def test_symmetric_vjp_planning_rules():
+    nb = lib()
+    t = _sym_vjp_tiles()[0]
+    B = nb.tile_info(nb.TABLE_VJP_GRAV, t)["j_tile"]
+    n_big = 1 << 21  # partials (n / B) x n x 16 B far above the 4 GiB cap
+    assert (n_big // B) * n_big * 16 > 4 << 30
+    pos = torch.zeros((n_big, 4), device=dev())
+    pos[:, 0] = torch.arange(n_big, device=dev(), dtype=torch.float32)
+    with pytest.raises(nb.NBodyError):
+        nb.adjoint(pos, torch.zeros_like(pos), eps=0.01, tile=t)
+
+
+def test_symmetric_forces_and_vjp_in_reverse_leapfrog():
+    """The checkpointed reverse leapfrog (torch.autograd.Function) with the
+    Newton-symmetric force tile in the forward pass and recompute and each
+    symmetric VJP tile in the reverse sweep (installed as the tuned entries for
+    N = 1024), against the FP64 oracle's gradient."""
+    nb = lib()
+    from paper_0706_3060_gb300.autograd import leapfrog
+    g = workloads.plummer(1024, seed=4, eps=0.01)
+    eps = float(np.float32(g.eps))
+    target = workloads.perturbed_target(g.f32_as_f64()[0], seed=4)
+    x, v, m = g.f32_as_f64()
+    sysm = oracle.GravSystem(m, eps=eps)
+    xs, _ = oracle.leapfrog(sysm, x, v, 1e-4, 60, store=True)
+    ref = oracle.adjoint_leapfrog(sysm, x, v, 1e-4, 60, oracle.target_loss_grad(xs[-1], target),
+                                  xs=xs)
+    old_f = nb.get_config(nb.LAW_GRAV, 1024)
+    old_v = nb.get_config(nb.TABLE_VJP_GRAV, 1024)
+    try:
+        nb.set_tuned(nb.LAW_GRAV, 1024, _sym_tiles()[-1], 0)
+        for tile in _sym_vjp_tiles():
+            nb.set_tuned(nb.TABLE_VJP_GRAV, 1024, tile, 0)
+            xf, vf, mf = g.f32()
+            d = dev()
+            x0 = torch.from_numpy(xf).to(d).requires_grad_(True)
+            v0 = torch.from_numpy(vf).to(d).requires_grad_(True)
+            m0 = torch.from_numpy(mf).to(d).requires_grad_(True)
+            xT, _ = leapfrog(x0, v0, m0, dt=1e-4, nsteps=60, k=20, eps=eps)
+            tgt = torch.from_numpy(target.astype(np.float32)).to(d)
+            (((xT - tgt) ** 2).sum() / 1024).backward()
+            nb.sync_check()
+            assert _rel(x0.grad.cpu().numpy(), ref["x0"]) <= 1e-4, tile
+            assert _rel(v0.grad.cpu().numpy(), ref["v0"]) <= 1e-4, tile
+            assert _rel(m0.grad.cpu().numpy(), ref["m"]) <= 1e-3, tile
+    finally:
+        nb.set_tuned(nb.LAW_GRAV, 1024, *old_f)
+        nb.set_tuned(nb.TABLE_VJP_GRAV, 1024, *old_v)

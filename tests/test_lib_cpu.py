@@ -45,8 +45,8 @@ def test_version_and_tiles(lib):
             assert info["j_tile"] % info["j_lanes"] == 0
             if info["packed"]:   # packed tiles walk source pairs
                 assert info["j_tile"] % 2 == 0
-            if info["symmetric"]:  # gravity only; blocks of threads x targets, pairs
-                assert law == nb.LAW_GRAV and info["packed"]
+            if info["symmetric"]:  # gravity forces and VJP; blocks of threads x targets
+                assert law in (nb.LAW_GRAV, nb.TABLE_VJP_GRAV) and info["packed"]
                 assert info["j_tile"] == info["threads"] * info["i_per_thread"]
     with pytest.raises(nb.NBodyError):
         nb.tile_info(0, 99)
