@@ -37,6 +37,10 @@ SYM_OPS_PER_UNORDERED_PAIR = 16
 # the same for the Newton-symmetric gravity VJP: 6 for d and s^2, 2 for y^2, y^3, 6 for
 # w, 6 for lam_j.d and lam_k.d, 2 for d.w, 2 for c, 3 for c d + w, 4 + 4 for the two sides
 SYM_VJP_OPS_PER_UNORDERED_PAIR = 35
+# and for the Newton-symmetric LJC kernel: the one-sided pair (23, 24 with the linear
+# dielectric) plus 3 FMA for the source side
+SYM_LJC_OPS_PER_UNORDERED_PAIR = 26
+SYM_LJCLIN_OPS_PER_UNORDERED_PAIR = 27
 PAPER_FLOPS_PER_PAIR = 19  # the paper's flop count per gravity interaction (Table 1, Appendix)
 FP32_LANES_PER_SM = 128    # FFMA/FADD/FMUL lanes per SM per clock (4 SMSPs x 32)
 SM_MAX_MHZ = 2070.0
@@ -478,10 +482,20 @@ def roofline_by_form(nb, torch, dev):
                  kernel_ms(lambda: nb.forces_jerk(pg, vg, eps=eg), 0)))
     lp, lprm = ljc(65536, K / 80.0)
     lacc = torch.empty_like(lp)
-    rows.append(("LJC forces", 65536, 23, kernel_ms(lambda: nb.forces(lp, lprm, out=lacc), 0)))
     lp2, lprm2 = ljc(65536, K / 4.0)
-    rows.append(("LJC(linear) forces", 65536, 24,
-                 kernel_ms(lambda: nb.forces(lp2, lprm2, law=nb.LAW_LJC_LINEAR, out=lacc), 0)))
+    for name, law, prm_, one, sym, one_tile in (
+            ("LJC forces", nb.LAW_LJC, lprm, 23, SYM_LJC_OPS_PER_UNORDERED_PAIR, (6, 32)),
+            ("LJC(linear) forces", nb.LAW_LJC_LINEAR, lprm2, 24,
+             SYM_LJCLIN_OPS_PER_UNORDERED_PAIR, (3, 32))):
+        p_ = lp if law == nb.LAW_LJC else lp2
+        lt, _ = nb.get_config(law, 65536)
+        if nb.tile_info(law, lt)["symmetric"]:
+            rows.append((f"{name} (Newton-symmetric)", 65536, sym / 2 * (65536 - 1) / 65536,
+                         kernel_ms(lambda: nb.forces(p_, prm_, law=law, out=lacc), 0)))
+        # the fastest one-sided tile at this size
+        rows.append((f"{name} (one-sided)", 65536, one,
+                     kernel_ms(lambda: nb.forces(p_, prm_, law=law, out=lacc, tile=one_tile[0],
+                                                 jsplit=one_tile[1]), 0)))
     pv, _, ev = grav(65536, seed=4)
     lam = torch.randn_like(pv)
     gx, gm = torch.empty_like(pv), torch.empty(65536, device=dev)

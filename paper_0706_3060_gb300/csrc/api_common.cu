@@ -421,6 +421,24 @@ __global__ void interleave_pairs_blocked_kernel(const float4 *pos, float4 *jp, i
   jp[base + B / 2 + pp] = make_float4(a.z, b.z, a.w, b.w);
 }
 
+// LJC sources of the symmetric tiles, block by block (B particles, 3B/2 float4
+// per block): the B/2 pairs' (x0 x1 y0 y1), then (z0 z1 q0 q1), then
+// (s0 s1 e0 e1). Pairs past n are not written.
+__global__ void interleave_ljc_pairs_blocked_kernel(const float4 *pos, const float4 *prm,
+                                                    float4 *jp, int n, int B) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * p >= n) return;
+  const float4 a = pos[2 * p], qa = prm[2 * p];
+  const bool two = 2 * p + 1 < n;
+  const float4 b = two ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+  const float4 qb = two ? prm[2 * p + 1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const int blk = (2 * p) / B, P = B / 2, pp = p - blk * P;
+  const long long q = (long long)blk * 3 * P + pp;
+  jp[q] = make_float4(a.x, b.x, a.y, b.y);
+  jp[q + P] = make_float4(a.z, b.z, qa.x, qb.x);
+  jp[q + 2 * P] = make_float4(qa.y, qb.y, qa.z, qb.z);
+}
+
 // LJC sources in pairs: (x0, x1, y0, y1), (z0, z1, q0, q1), (s0, s1, e0, e1); the
 // pad of an odd count is far away with no charge and no LJ well.
 __global__ void interleave_ljc_pairs_kernel(const float4 *pos, const float4 *prm, float4 *jp,
@@ -451,7 +469,10 @@ int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags,
   if (p.tile->packed) {
     if (!jbuf) return set_error_msg(NBODY_EINVAL, "packed tile without pair buffer");
     const int np = (n + 1) / 2;
-    if (law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR)
+    if ((law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR) && p.tile->sym)
+      interleave_ljc_pairs_blocked_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, prm, jbuf, n,
+                                                                           p.slice_len);
+    else if (law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR)
       interleave_ljc_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, prm, jbuf, n);
     else if (p.tile->sym)
       interleave_pairs_blocked_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, jbuf, n,

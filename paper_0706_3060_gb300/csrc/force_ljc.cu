@@ -22,6 +22,11 @@ const TileDesc *ljc_tiles(int *count) {
       // as 10 and 9 with registers capped for 3 CTAs per SM (more warps at small N)
       TileImpl<kLawLJC, 128, 2, 2, 256, true, 2, 3>::desc(),  // 12: 128 targets, 2 j-lanes
       TileImpl<kLawLJC, 128, 2, 4, 256, true, 2, 3>::desc(),  // 13: 64 targets, 4 j-lanes
+      // Newton-symmetric block pairs (sym_ljc_kernel.cuh): each unordered pair once
+      SymLjcImpl<kLawLJC, 128, 4>::desc(),     // 14: blocks of 512
+      SymLjcImpl<kLawLJC, 128, 2>::desc(),     // 15: blocks of 256
+      SymLjcImpl<kLawLJC, 64, 4>::desc(),      // 16: blocks of 256, 2-warp CTAs
+      SymLjcImpl<kLawLJC, 128, 8, 2>::desc(),  // 17: blocks of 1024
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;

@@ -11,6 +11,10 @@ const TileDesc *ljclin_tiles(int *count) {
       TileImpl<kLawLJCLin, 64, 2, 8, 128>::desc(),         // 2: 16 targets, 8 j-lanes
       TileImpl<kLawLJCLin, 128, 2, 1, 256, true>::desc(),  // 3: packed, 256 targets
       TileImpl<kLawLJCLin, 256, 2, 1, 512, true>::desc(),  // 4: packed, 512 targets
+      // Newton-symmetric block pairs (sym_ljc_kernel.cuh)
+      SymLjcImpl<kLawLJCLin, 128, 4>::desc(),  // 5: blocks of 512
+      SymLjcImpl<kLawLJCLin, 128, 2>::desc(),  // 6: blocks of 256
+      SymLjcImpl<kLawLJCLin, 64, 4>::desc(),   // 7: blocks of 256, 2-warp CTAs
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;

@@ -7,6 +7,7 @@
 
 #include "force_kernel.cuh"
 #include "sym_kernel.cuh"
+#include "sym_ljc_kernel.cuh"
 
 namespace nbody {
 
@@ -152,6 +153,64 @@ struct SymImpl {
   }
   static TileDesc desc() {
     TileDesc d{kLawGrav, NT, I, 1, T::kB, T::kB, NT, T::smem_bytes(false), true, false,
+               &launch, &occupancy};
+    d.sym = true;
+    return d;
+  }
+};
+
+// Newton-symmetric LJC tiles (constant or linear dielectric), as SymImpl.
+template <int LAW, int NT, int I, int MINB = 1>
+struct SymLjcImpl {
+  using T = SymLjcTile<NT, I>;
+  template <bool POT, bool PRE>
+  static cudaError_t go(const ForceArgs &a, int grid, cudaStream_t s) {
+    auto k = sym_ljc_kernel<LAW, NT, I, POT, PRE, MINB>;
+    const size_t smem = T::smem_bytes(POT);
+    {  // opt in always: the static mbarrier counts against the 48 KB default too
+      static std::atomic<bool> opted[kMaxDevicesTile];
+      int dev = 0;
+      const bool known = cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDevicesTile;
+      if (!known || !opted[dev].load(std::memory_order_acquire)) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (known) opted[dev].store(true, std::memory_order_release);
+      }
+    }
+    k<<<grid, NT, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t launch(const ForceArgs &a, int grid, bool pot, bool precise,
+                            cudaStream_t s) {
+    if (pot) return precise ? go<true, true>(a, grid, s) : go<true, false>(a, grid, s);
+    return precise ? go<false, true>(a, grid, s) : go<false, false>(a, grid, s);
+  }
+  static int occupancy() {
+    static std::atomic<int> cached[kMaxDevicesTile];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesTile) {
+      cudaGetLastError();
+      dev = -1;
+    }
+    if (dev >= 0) {
+      const int c = cached[dev].load(std::memory_order_relaxed);
+      if (c > 0) return c;
+    }
+    int nb = 0;
+    auto k = sym_ljc_kernel<LAW, NT, I, false, false, MINB>;
+    const size_t smem = T::smem_bytes(false);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 1;
+    }
+    nb = std::max(nb, 1);
+    if (dev >= 0) cached[dev].store(nb, std::memory_order_relaxed);
+    return nb;
+  }
+  static TileDesc desc() {
+    TileDesc d{LAW, NT, I, 1, T::kB, T::kB, NT, T::smem_bytes(false), true, false,
                &launch, &occupancy};
     d.sym = true;
     return d;

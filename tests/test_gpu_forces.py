@@ -166,7 +166,7 @@ def test_ljc_forces(n):
     assert np.sqrt(np.mean(e * e)) <= 1e-5 and e.max() <= 1e-4
 
 
-@pytest.mark.parametrize("tile", range(14))
+@pytest.mark.parametrize("tile", range(18))
 def test_ljc_every_tile(tile):
     nb = lib()
     s = workloads.ljc_sphere(1500, seed=9)
@@ -297,7 +297,7 @@ def _ljclin_tensors(s, D=4.0):
     return pos.contiguous(), prm, sysm, x.astype(np.float64)
 
 
-@pytest.mark.parametrize("tile", range(5))
+@pytest.mark.parametrize("tile", range(8))
 @pytest.mark.parametrize("n", [257, 3000, 8192])
 def test_ljc_linear_dielectric(tile, n):
     """Table 1 LJC(linear): dielectric D r with D = 4 (reading C3)."""

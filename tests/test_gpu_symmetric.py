@@ -1,6 +1,7 @@
 """GPU parity of the Newton-symmetric gravity tiles (each unordered pair evaluated
-once and applied to both particles) against the FP64 oracle: forces (blocks of
-512, 768 and 1024) and the force VJP (blocks of 256 and 512), every ragged case
+once and applied to both particles) against the FP64 oracle: gravity forces
+(blocks of 512, 768 and 1024), LJC forces with constant and linear dielectric
+(blocks of 256 to 1024) and the gravity force VJP (blocks of 256 to 512), every ragged case
 of one and several blocks (odd N ends with the pad particle), eps = 0 with the
 self pair masked on diagonal blocks, the potential, both rsqrt modes, leapfrog
 trajectories, run-to-run bitwise reproducibility, and the planning rules (no
@@ -241,3 +242,40 @@ def test_symmetric_forces_and_vjp_in_reverse_leapfrog():
     finally:
         nb.set_tuned(nb.LAW_GRAV, 1024, *old_f)
         nb.set_tuned(nb.TABLE_VJP_GRAV, 1024, *old_v)
+
+
+def _sym_ljc_tiles(law):
+    nb = lib()
+    return [t for t in range(nb.tile_count(law)) if nb.tile_info(law, t)["symmetric"]]
+
+
+@pytest.mark.parametrize("linear", [False, True])
+@pytest.mark.parametrize("n", [2, 3, 255, 256, 257, 513, 1025, 3001])
+def test_symmetric_ljc_ragged_sizes(n, linear):
+    """Table 1 LJC(constant) (dielectric 80) and LJC(linear) (D = 4) through every
+    symmetric tile, with the potential and both rsqrt modes."""
+    nb = lib()
+    law = nb.LAW_LJC_LINEAR if linear else nb.LAW_LJC
+    D = 4.0 if linear else 80.0
+    s = workloads.ljc_sphere(n, seed=800 + n)
+    x, v, m, q, st, et = s.f32()
+    d = dev()
+    pos = torch.from_numpy(np.concatenate([x, m[:, None]], 1).astype(np.float32)).to(d)
+    prm = nb.pack_ljc(torch.from_numpy(q.astype(np.float64)).to(d),
+                      torch.from_numpy(st.astype(np.float64)[s.types]).to(d),
+                      torch.from_numpy(et.astype(np.float64)[s.types]).to(d),
+                      torch.from_numpy(s.types).to(d), kq=332.0637 / D)
+    sysm = oracle.LJCSystem(m.astype(np.float64), q.astype(np.float64), s.types,
+                            st.astype(np.float64), et.astype(np.float64), 332.0637 / D,
+                            linear=linear)
+    ref, phi = sysm.accel(x.astype(np.float64), potential=True)
+    tiles = _sym_ljc_tiles(law)
+    assert tiles
+    for tile in tiles:
+        for precise in (False, True):
+            acc = nb.forces(pos.contiguous(), prm, law=law, pot=True, precise=precise,
+                            tile=tile).cpu().numpy()
+            assert np.all(np.isfinite(acc)), (tile, n)
+            assert_forces_close(acc[:, :3], ref, what=f"LJC linear={linear} tile={tile} n={n}")
+            e = np.abs(acc[:, 3] - phi) / np.maximum(np.abs(phi), 1e-3 * np.abs(phi).max())
+            assert np.sqrt(np.mean(e * e)) <= 1e-5 and e.max() <= 1e-4, (tile, n)

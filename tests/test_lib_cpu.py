@@ -45,8 +45,9 @@ def test_version_and_tiles(lib):
             assert info["j_tile"] % info["j_lanes"] == 0
             if info["packed"]:   # packed tiles walk source pairs
                 assert info["j_tile"] % 2 == 0
-            if info["symmetric"]:  # gravity forces and VJP; blocks of threads x targets
-                assert law in (nb.LAW_GRAV, nb.TABLE_VJP_GRAV) and info["packed"]
+            if info["symmetric"]:  # force laws and the gravity VJP; blocks of threads x targets
+                assert law in (nb.LAW_GRAV, nb.LAW_LJC, nb.LAW_LJC_LINEAR, nb.TABLE_VJP_GRAV)
+                assert info["packed"]
                 assert info["j_tile"] == info["threads"] * info["i_per_thread"]
     with pytest.raises(nb.NBodyError):
         nb.tile_info(0, 99)
