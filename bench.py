@@ -41,6 +41,9 @@ SYM_VJP_OPS_PER_UNORDERED_PAIR = 35
 # dielectric) plus 3 FMA for the source side
 SYM_LJC_OPS_PER_UNORDERED_PAIR = 26
 SYM_LJCLIN_OPS_PER_UNORDERED_PAIR = 27
+# and for the Newton-symmetric acceleration + jerk: 6 for d and u, 3 for s^2, 2 for y^2,
+# y^3, 3 for d.u, 2 for c, 3 for u + c d, then per side 1 weight + 3 + 3 FMA
+SYM_GAJ_OPS_PER_UNORDERED_PAIR = 33
 PAPER_FLOPS_PER_PAIR = 19  # the paper's flop count per gravity interaction (Table 1, Appendix)
 FP32_LANES_PER_SM = 128    # FFMA/FADD/FMUL lanes per SM per clock (4 SMSPs x 32)
 SM_MAX_MHZ = 2070.0
@@ -478,8 +481,14 @@ def roofline_by_form(nb, torch, dev):
     # the fastest one-sided tile (256 threads x 2 targets, 8 j-slices)
     rows.append(("gravity forces (one-sided)", 262144, 12,
                  kernel_ms(lambda: nb.forces(pg, eps=eg, out=acc, tile=12, jsplit=8), 0)))
-    rows.append(("acceleration + jerk", 262144, 26,
-                 kernel_ms(lambda: nb.forces_jerk(pg, vg, eps=eg), 0)))
+    jt, _ = nb.get_config(nb.TABLE_JERK, 262144)
+    if nb.tile_info(nb.TABLE_JERK, jt)["symmetric"]:
+        rows.append(("acceleration + jerk (Newton-symmetric)", 262144,
+                     SYM_GAJ_OPS_PER_UNORDERED_PAIR / 2 * (262144 - 1) / 262144,
+                     kernel_ms(lambda: nb.forces_jerk(pg, vg, eps=eg), 0)))
+    # the fastest one-sided jerk tile (packed, 128 threads x 2 targets, 32 j-slices)
+    rows.append(("acceleration + jerk (one-sided)", 262144, 26,
+                 kernel_ms(lambda: nb.forces_jerk(pg, vg, eps=eg, tile=6, jsplit=32), 0)))
     lp, lprm = ljc(65536, K / 80.0)
     lacc = torch.empty_like(lp)
     lp2, lprm2 = ljc(65536, K / 4.0)

@@ -80,8 +80,8 @@ def build_case(name, nb, torch, dev):
         gx = torch.empty_like(pos)
         gm = torch.empty(pos.shape[0], device=dev)
         return lambda: nb.adjoint(pos, lam, eps=eps, grad_x=gx, grad_m=gm)
-    if name == "jerk262144":
-        pos, vel, eps = _grav(nb, torch, dev, 262144)
+    if name in ("jerk65536", "jerk262144"):
+        pos, vel, eps = _grav(nb, torch, dev, int(name[4:]))
         return lambda: nb.forces_jerk(pos, vel, eps=eps)
     if name == "batched512":
         pos, prm, table = _ensemble(nb, torch, dev)
@@ -95,7 +95,7 @@ def build_case(name, nb, torch, dev):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["grav65536", "grav262144", "ljc8192", "ljc65536", "vjp16384",
-                                     "jerk262144", "batched512"])
+                                     "jerk65536", "jerk262144", "batched512"])
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--iters", type=int, default=2)
     a = ap.parse_args()

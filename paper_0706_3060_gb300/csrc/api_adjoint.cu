@@ -56,7 +56,8 @@ int vjp_prepare(int law, int n, int tile, int jsplit, int sms, cudaStream_t s, V
   const VjpDesc &d = tiles[tile];
   if (d.sym) {  // one CTA per block pair, one partial slot per block, no low parts
     const int nb = (n + d.tile_i - 1) / d.tile_i;
-    const size_t part = round_up(size_t(nb) * size_t(n) * sizeof(float4), 256);
+    const int nblocks = (law == kLawGAJ) ? 2 : 1;  // acceleration and jerk partials
+    const size_t part = round_up(size_t(nblocks) * nb * size_t(n) * sizeof(float4), 256);
     const size_t ubytes = round_up(size_t(n) * sizeof(float4), 256);
     const int nblk = (n + 255) / 256;
     const size_t tbytes = round_up(size_t(nblk) * 8 * sizeof(double), 256);
@@ -270,7 +271,12 @@ int gaj_eval(const float4 *pos, const float4 *vel, float4 *acc, float4 *jerk, in
   int *err = nullptr;
   NB_TRY(error_word(&err));
   if (sc.d->packed) {  // (x, m) and velocities of source pairs, interleaved
-    interleave_vjp_pairs_kernel<<<((n + 1) / 2 + 255) / 256, 256, 0, s>>>(pos, vel, sc.jp, n);
+    const unsigned pblocks = unsigned(((n + 1) / 2 + 255) / 256);
+    if (sc.d->sym)
+      interleave_vjp_pairs_blocked_kernel<<<pblocks, 256, 0, s>>>(pos, vel, sc.jp, n,
+                                                                  sc.slice_len);
+    else
+      interleave_vjp_pairs_kernel<<<pblocks, 256, 0, s>>>(pos, vel, sc.jp, n);
     NB_CUDA(cudaGetLastError());
   }
   VjpArgs a{};

@@ -136,12 +136,14 @@ __global__ void __launch_bounds__(256) gaj_finalize_kernel(const float4 *part_hi
                                                            float4 *acc, float4 *jerk) {
   const int i = blockIdx.x * 256 + threadIdx.x;
   if (i >= n) return;
-  float4 hA = part_hi[i], oA = part_lo[i];
-  float4 hB = part_hi[bstride + i], oB = part_lo[bstride + i];
+  // part_lo == nullptr: partials without low parts (Newton-symmetric tiles)
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 hA = part_hi[i], oA = part_lo ? part_lo[i] : zero;
+  float4 hB = part_hi[bstride + i], oB = part_lo ? part_lo[bstride + i] : zero;
   for (int k = 1; k < slices; ++k) {
     const long long o = (long long)k * stride + i;
-    const float4 a = part_hi[o], la = part_lo[o], b = part_hi[bstride + o],
-                 lb = part_lo[bstride + o];
+    const float4 a = part_hi[o], la = part_lo ? part_lo[o] : zero, b = part_hi[bstride + o],
+                 lb = part_lo ? part_lo[bstride + o] : zero;
     comp_add(hA.x, oA.x, a.x);
     comp_add(hA.y, oA.y, a.y);
     comp_add(hA.z, oA.z, a.z);

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "api_common.h"
 #include "vjp_tiles.h"
@@ -64,13 +65,20 @@ struct VjpImpl {
   }
 };
 
-// Newton-symmetric gravity VJP tiles: blocks of NT * I particles, one CTA per
-// block pair; `tile_i` and `jt` report the block size.
-template <int NT, int I, int MINB = 1>
-struct SymVjpImpl {
-  using T = SymVjpTile<NT, I>;
+// Newton-symmetric gravity VJP (GAJ false) and acceleration + jerk (GAJ true)
+// tiles: blocks of NT * I particles, one CTA per block pair; `tile_i` and `jt`
+// report the block size.
+template <bool GAJ, int NT, int I, int MINB>
+struct SymVjpImplT {
+  using T = std::conditional_t<GAJ, SymGajTile<NT, I>, SymVjpTile<NT, I>>;
+  static constexpr auto kernel() {
+    if constexpr (GAJ)
+      return sym_gaj_kernel<NT, I, MINB>;
+    else
+      return sym_gvjp_kernel<NT, I, MINB>;
+  }
   static cudaError_t launch(const VjpArgs &a, int grid, cudaStream_t s) {
-    auto k = sym_gvjp_kernel<NT, I, MINB>;
+    auto k = kernel();
     {  // opt in always: the static mbarrier counts against the 48 KB default too
       static std::atomic<bool> opted[kMaxDevicesTile];
       int dev = 0;
@@ -97,7 +105,7 @@ struct SymVjpImpl {
       if (c > 0) return c;
     }
     int nb = 0;
-    auto k = sym_gvjp_kernel<NT, I, MINB>;
+    auto k = kernel();
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, T::kSmemBytes) !=
         cudaSuccess) {
@@ -114,12 +122,17 @@ struct SymVjpImpl {
     return d;
   }
   static TileDesc tile() {
-    TileDesc d{kLawGrav, NT, I, 1, T::kB, T::kB, NT, T::kSmemBytes, true, false,
-               nullptr, &occupancy};
+    TileDesc d{GAJ ? kLawGAJ : kLawGrav, NT, I, 1, T::kB, T::kB, NT, T::kSmemBytes, true,
+               false, nullptr, &occupancy};
     d.sym = true;
     return d;
   }
 };
+
+template <int NT, int I, int MINB = 1>
+using SymVjpImpl = SymVjpImplT<false, NT, I, MINB>;
+template <int NT, int I, int MINB = 1>
+using SymGajImpl = SymVjpImplT<true, NT, I, MINB>;
 
 // Rows: (law, consumer threads, targets per thread, j-lanes, j-tile, packed,
 // unroll). Row 0 is the default for large N, row 1 for small N (below 8192).
@@ -174,17 +187,23 @@ struct SymVjpImpl {
 
 const VjpDesc kGravDesc[] = {NB_VJP_GRAV_ROWS(NB_VJP_DESC) NB_VJP_GRAV_SYM(desc)};
 const VjpDesc kLjcDesc[] = {NB_VJP_LJC_ROWS(NB_VJP_DESC)};
-const VjpDesc kGajDesc[] = {NB_VJP_GAJ_ROWS(NB_VJP_DESC)};
+// the jerk table ends with its Newton-symmetric tiles: blocks of 512 (3 CTAs/SM),
+// 256 in 2-warp CTAs, 256
+#define NB_GAJ_SYM(F) \
+  SymGajImpl<128, 4, 3>::F(), SymGajImpl<64, 4, 6>::F(), SymGajImpl<128, 2>::F(),
+
+const VjpDesc kGajDesc[] = {NB_VJP_GAJ_ROWS(NB_VJP_DESC) NB_GAJ_SYM(desc)};
 const VjpDesc kLjcLinDesc[] = {NB_VJP_LJCLIN_ROWS(NB_VJP_DESC)};
 const TileDesc kGravTile[] = {NB_VJP_GRAV_ROWS(NB_VJP_TILE) NB_VJP_GRAV_SYM(tile)};
 const TileDesc kLjcTile[] = {NB_VJP_LJC_ROWS(NB_VJP_TILE)};
-const TileDesc kGajTile[] = {NB_VJP_GAJ_ROWS(NB_VJP_TILE)};
+const TileDesc kGajTile[] = {NB_VJP_GAJ_ROWS(NB_VJP_TILE) NB_GAJ_SYM(tile)};
 const TileDesc kLjcLinTile[] = {NB_VJP_LJCLIN_ROWS(NB_VJP_TILE)};
 
 #undef NB_VJP_DESC
 #undef NB_VJP_TILE
 #undef NB_VJP_GRAV_ROWS
 #undef NB_VJP_GRAV_SYM
+#undef NB_GAJ_SYM
 #undef NB_VJP_LJC_ROWS
 #undef NB_VJP_GAJ_ROWS
 #undef NB_VJP_LJCLIN_ROWS

@@ -258,7 +258,7 @@ def test_grav_acceleration_and_jerk(n):
     assert_forces_close(jerk[:, :3].cpu().numpy(), rj, what=f"GAJ jerk n={n}")
 
 
-@pytest.mark.parametrize("tile", range(9))
+@pytest.mark.parametrize("tile", range(12))
 def test_jerk_every_tile(tile):
     """Every acceleration + jerk tile (scalar and packed f32x2) at an odd size
     spanning several j-tiles (the packed source buffer ends in a pad particle)."""

@@ -1,7 +1,8 @@
 """GPU parity of the Newton-symmetric gravity tiles (each unordered pair evaluated
 once and applied to both particles) against the FP64 oracle: gravity forces
 (blocks of 512, 768 and 1024), LJC forces with constant and linear dielectric
-(blocks of 256 to 1024) and the gravity force VJP (blocks of 256 to 512), every ragged case
+(blocks of 256 to 1024), the gravity force VJP and acceleration + jerk (blocks
+of 256 to 512), every ragged case
 of one and several blocks (odd N ends with the pad particle), eps = 0 with the
 self pair masked on diagonal blocks, the potential, both rsqrt modes, leapfrog
 trajectories, run-to-run bitwise reproducibility, and the planning rules (no
@@ -279,3 +280,45 @@ def test_symmetric_ljc_ragged_sizes(n, linear):
             assert_forces_close(acc[:, :3], ref, what=f"LJC linear={linear} tile={tile} n={n}")
             e = np.abs(acc[:, 3] - phi) / np.maximum(np.abs(phi), 1e-3 * np.abs(phi).max())
             assert np.sqrt(np.mean(e * e)) <= 1e-5 and e.max() <= 1e-4, (tile, n)
+
+
+@pytest.mark.parametrize("n", [2, 3, 255, 256, 257, 513, 1025, 3001])
+def test_symmetric_jerk_ragged_sizes(n):
+    """Acceleration + jerk (Table 1 GAJ) through every symmetric tile of its table."""
+    nb = lib()
+    g = workloads.plummer(n, seed=900 + n, eps=0.01)
+    pos, vel = grav_tensors(g)
+    eps = float(np.float32(g.eps))
+    x, v, m = g.f32_as_f64()
+    ra, rj = oracle.grav_jerk(x, v, m, G=1.3, eps=eps)
+    tiles = _sym_ljc_tiles(nb.TABLE_JERK)
+    assert tiles
+    for tile in tiles:
+        acc, jerk = nb.forces_jerk(pos, vel, G=1.3, eps=eps, tile=tile)
+        assert_forces_close(acc[:, :3].cpu().numpy(), ra, what=f"GAJ acc tile {tile} n {n}")
+        assert_forces_close(jerk[:, :3].cpu().numpy(), rj, what=f"GAJ jerk tile {tile} n {n}")
+
+
+def test_symmetric_jerk_unsoftened_and_hermite():
+    """eps = 0 (self pair masked on diagonal blocks; the closed-form two-body jerk)
+    and fourth-order Hermite steps through each symmetric jerk tile against the
+    FP64 oracle's Hermite integrator."""
+    nb = lib()
+    pos = torch.tensor([[0, 0, 0, 5.0], [3, 4, 0, 2.0]], dtype=torch.float32, device=dev())
+    vel = torch.tensor([[0, 0, 0, 0], [1, 0, 0, 0]], dtype=torch.float32, device=dev())
+    g = workloads.plummer(2048, seed=23, eps=0.01)
+    eps = float(np.float32(g.eps))
+    x, v, m = g.f32_as_f64()
+    xr, vr = oracle.hermite(x, v, m, 1e-3, 10, eps=eps)
+    for tile in _sym_ljc_tiles(nb.TABLE_JERK):
+        _, jerk = nb.forces_jerk(pos, vel, eps=0.0, tile=tile)
+        np.testing.assert_allclose(jerk[0, :3].cpu().numpy(), [-0.00128, -0.02304, 0.0],
+                                   rtol=2e-6, atol=1e-9)
+        p, vv = grav_tensors(g)
+        acc = torch.empty_like(p)
+        jk = torch.empty_like(p)
+        nb.hermite_step(p, vv, acc, jk, dt=1e-3, nsteps=10, eps=eps, tile=tile)
+        ex = traj_errors(p[:, :3].cpu().numpy(), xr)
+        ev = traj_errors(vv[:, :3].cpu().numpy(), vr)
+        assert ex[0] <= 1e-6 and ex[1] <= 1e-5, (tile, ex)
+        assert ev[0] <= 1e-5 and ev[1] <= 1e-4, (tile, ev)
