@@ -530,20 +530,32 @@ def roofline_by_form(nb, torch, dev):
         out[name] = {"n": n, "ops_per_pair": ops, "kernel_ms": ms,
                      "gpairs_per_s": pairs / (ms * 1e-3) / 1e9, "achieved_tflops": t,
                      "frac": t / peak}
-    # the batched persistent kernel over the 512-system ensemble (12 ops per
-    # gravity pair, 23 per LJC pair)
+    # the batched persistent kernel over the 512-system ensemble: one-sided tiles do
+    # 12 ops per gravity pair and 23 per LJC pair; the Newton-symmetric tiles 16 and
+    # 26 per unordered pair
     ens = workloads.ensemble(nsys=512, seed=3)
     bpos, bvel, bprm, table = _ensemble_arrays(nb, torch, dev, ens)
     bacc = torch.zeros_like(bpos)
-    plan = nb.BatchPlan(table)
-    ms = kernel_ms(lambda: plan.run(bpos, bvel, bacc, bprm, nsteps=0, graph=False), 0)
-    plan.close()
     pg2 = sum(float(x.n) ** 2 for x in ens.systems if isinstance(x, workloads.GravInput))
     pl2 = sum(float(x.n) ** 2 for x in ens.systems if not isinstance(x, workloads.GravInput))
-    t = (12 * pg2 + 23 * pl2) / (ms * 1e-3) / 1e12
-    out["batched ensemble"] = {"systems": 512, "pairs": pg2 + pl2, "kernel_ms": ms,
-                               "gpairs_per_s": (pg2 + pl2) / (ms * 1e-3) / 1e9,
-                               "achieved_tflops": t, "frac": t / peak}
+    pgu = sum(x.n * (x.n - 1) / 2 for x in ens.systems if isinstance(x, workloads.GravInput))
+    plu = sum(x.n * (x.n - 1) / 2 for x in ens.systems if not isinstance(x, workloads.GravInput))
+    btile, _ = nb.get_config(nb.TABLE_BATCHED, 0)
+    forms = [("batched ensemble (one-sided)", 9)]
+    if nb.tile_info(nb.TABLE_BATCHED, btile)["symmetric"]:
+        forms.insert(0, ("batched ensemble (Newton-symmetric)", btile))
+    for name, tl in forms:
+        plan = nb.BatchPlan(table, tile=tl)
+        ms = kernel_ms(lambda: plan.run(bpos, bvel, bacc, bprm, nsteps=0, graph=False), 0)
+        plan.close()
+        if nb.tile_info(nb.TABLE_BATCHED, tl)["symmetric"]:
+            ops = SYM_OPS_PER_UNORDERED_PAIR * pgu + SYM_LJC_OPS_PER_UNORDERED_PAIR * plu
+        else:
+            ops = 12 * pg2 + 23 * pl2
+        t = ops / (ms * 1e-3) / 1e12
+        out[name] = {"systems": 512, "tile": tl, "pairs": pg2 + pl2, "kernel_ms": ms,
+                     "gpairs_per_s": (pg2 + pl2) / (ms * 1e-3) / 1e9,
+                     "achieved_tflops": t, "frac": t / peak}
     return out
 
 

@@ -115,20 +115,82 @@ __global__ void interleave_systems_kernel(const float4 *pos, const float4 *prm,
   }
 }
 
+// Newton-symmetric tiles: sources block by block (B particles) per system, in
+// the law's layout: gravity (x x y y) then (z z m m) words of the block's pairs,
+// LJC (x x y y), (z z q q), (s s e e); sysp = (offset, first float4 of the
+// system's blocks, n, law). The last particle of an odd system also writes the
+// pad half of its pair.
+__global__ void interleave_systems_blocked_kernel(const float4 *pos, const float4 *prm,
+                                                  const int *sys_of, const int4 *sysp,
+                                                  int total, float4 *jgrav, float4 *jljc,
+                                                  int B) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int k = sys_of[i];
+  if (k < 0) return;
+  const int4 sp = sysp[k];
+  const int local = i - sp.x;
+  const int blk = local / B, P = B / 2;
+  const int pp = (local - blk * B) >> 1;
+  const int half = local & 1;
+  const bool pad = (local == sp.z - 1) && (sp.z & 1);
+  const float4 x = pos[i];
+  if (sp.w == NBODY_LAW_GRAV) {
+    const long long base = (long long)sp.y + (long long)blk * B + pp;
+    float *a0 = reinterpret_cast<float *>(jgrav + base);
+    float *a1 = reinterpret_cast<float *>(jgrav + base + P);
+    a0[half] = x.x;
+    a0[2 + half] = x.y;
+    a1[half] = x.z;
+    a1[2 + half] = x.w;
+    if (pad) {
+      a0[1] = 1e18f;
+      a0[3] = 1e18f;
+      a1[1] = 1e18f;
+      a1[3] = 0.0f;
+    }
+  } else {
+    const float4 q = prm[i];
+    const long long base = (long long)sp.y + (long long)blk * 3 * P + pp;
+    float *a0 = reinterpret_cast<float *>(jljc + base);
+    float *a1 = reinterpret_cast<float *>(jljc + base + P);
+    float *a2 = reinterpret_cast<float *>(jljc + base + 2 * P);
+    a0[half] = x.x;
+    a0[2 + half] = x.y;
+    a1[half] = x.z;
+    a1[2 + half] = q.x;
+    a2[half] = q.y;
+    a2[2 + half] = q.z;
+    if (pad) {
+      a0[1] = 1e18f;
+      a0[3] = 1e18f;
+      a1[1] = 1e18f;
+      a1[3] = 0.0f;
+      a2[1] = 0.0f;
+      a2[3] = 0.0f;
+    }
+  }
+}
+
 // Enqueue nsteps leapfrog steps (or one force evaluation when nsteps == 0).
 int enqueue_run(nbody_batch_plan *p, float4 *pos, float4 *vel, float4 *acc, const float4 *prm,
                 int nsteps, uint32_t flags, int *err, cudaStream_t s) {
   const int total = int(p->total);
   const long long stride = p->total;
   float4 *part_hi = p->d_part;
-  float4 *part_lo = p->d_part + size_t(p->max_slices) * size_t(stride);
+  // the symmetric tiles write one partial per particle and block, without low parts
+  float4 *part_lo = p->td->sym ? nullptr : p->d_part + size_t(p->max_slices) * size_t(stride);
   const int evals = nsteps + ((flags & NBODY_ACC_VALID) && nsteps > 0 ? 0 : 1);
   // Every evaluation has its own work counter so that the graph needs no
   // reset between launches of different steps; all are zeroed up front.
   NB_CUDA(cudaMemsetAsync(p->d_counter, 0, sizeof(int) * size_t(evals), s));
   int counter_idx = 0;
   auto eval = [&](int mode) -> int {
-    if (p->td->packed) {
+    if (p->td->sym) {
+      interleave_systems_blocked_kernel<<<(total + 255) / 256, 256, 0, s>>>(
+          pos, prm, p->d_sys_of, p->d_sysp, total, p->d_jgrav, p->d_jljc, p->td->tile_i);
+      NB_CUDA(cudaGetLastError());
+    } else if (p->td->packed) {
       interleave_systems_kernel<<<(total + 255) / 256, 256, 0, s>>>(
           pos, prm, p->d_sys_of, p->d_sysp, total, p->d_jgrav, p->d_jljc);
       NB_CUDA(cudaGetLastError());
@@ -240,7 +302,40 @@ int nbody_batch_plan_create(const nbody_system *systems, int32_t nsys, uint32_t 
   std::vector<int4> sysp(nsys);
   int max_slices = 1;
   long long pairs_law[2] = {0, 0};  // pair-buffer sizes per law (packed tiles)
-  for (int k = 0; k < nsys; ++k) {
+  long long f4_law[2] = {0, 0};     // float4 sizes of the blocked buffers (symmetric tiles)
+  for (int k = 0; k < nsys && td->sym; ++k) {
+    // Newton-symmetric tiles: one item per block pair (bi <= bj) of each system,
+    // one partial slot per block
+    const nbody_system &s = systems[k];
+    const int B = td->tile_i;
+    const int nb = (s.n + B - 1) / B;
+    if (nb > 0xffff)
+      return set_error_msg(NBODY_EINVAL, "system %d: n = %d too large for symmetric tile %d",
+                           k, s.n, tile);
+    const int pl = (s.law == NBODY_LAW_GRAV) ? 0 : 1;
+    const long long per_block = pl ? 3LL * (B / 2) : (long long)B;  // float4 per block
+    const long long jb = f4_law[pl];
+    f4_law[pl] += per_block * nb;
+    if (f4_law[pl] > 0x7fffffffLL)
+      return set_error_msg(NBODY_EINVAL, "ensemble too large for symmetric tile %d", tile);
+    sysp[k] = make_int4(int(s.offset), int(jb), s.n, s.law);
+    max_slices = std::max(max_slices, nb);
+    info[k] = SysInfo{s.law, nb, s.G, s.dt};
+    for (int bi = 0; bi < nb; ++bi)
+      for (int bj = bi; bj < nb; ++bj) {
+        WorkItem w{};
+        w.i0 = int(s.offset) + bi * B;
+        w.ni = std::min(B, s.n - bi * B);
+        w.j0 = int(s.offset) + bj * B;
+        w.nj = std::min(B, s.n - bj * B);
+        w.law = (s.law == NBODY_LAW_LJC_LINEAR) ? kLawLJCLin : s.law;
+        w.slice = bj | (bi << 16);
+        w.eps2 = s.eps2;
+        w.pj0 = int(jb + per_block * bj);
+        items.push_back(w);
+      }
+  }
+  for (int k = 0; k < nsys && !td->sym; ++k) {
     const nbody_system &s = systems[k];
     const int pl = (s.law == NBODY_LAW_GRAV) ? 0 : 1;  // both LJC laws share one layout
     const int pbase = int(pairs_law[pl]);
@@ -294,8 +389,8 @@ int nbody_batch_plan_create(const nbody_system *systems, int32_t nsys, uint32_t 
   if ((e = cudaMalloc(&p->d_items, sizeof(WorkItem) * items.size())) != cudaSuccess ||
       (e = cudaMalloc(&p->d_sys, sizeof(SysInfo) * info.size())) != cudaSuccess ||
       (e = cudaMalloc(&p->d_sys_of, sizeof(int) * sys_of.size())) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_part, sizeof(float4) * 2 * size_t(max_slices) * size_t(total))) !=
-          cudaSuccess ||
+      (e = cudaMalloc(&p->d_part, sizeof(float4) * (td->sym ? 1 : 2) * size_t(max_slices) *
+                                      size_t(total))) != cudaSuccess ||
       (e = cudaMemcpy(p->d_items, items.data(), sizeof(WorkItem) * items.size(),
                       cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(p->d_sys, info.data(), sizeof(SysInfo) * info.size(),
@@ -303,9 +398,11 @@ int nbody_batch_plan_create(const nbody_system *systems, int32_t nsys, uint32_t 
       (e = cudaMemcpy(p->d_sys_of, sys_of.data(), sizeof(int) * sys_of.size(),
                       cudaMemcpyHostToDevice)) != cudaSuccess ||
       (td->packed &&
-       ((e = cudaMalloc(&p->d_jgrav, sizeof(float4) * 2 * size_t(pairs_law[0] + 1))) !=
+       ((e = cudaMalloc(&p->d_jgrav, sizeof(float4) * (td->sym ? size_t(f4_law[0] + 1)
+                                                                 : 2 * size_t(pairs_law[0] + 1)))) !=
             cudaSuccess ||
-        (e = cudaMalloc(&p->d_jljc, sizeof(float4) * 3 * size_t(pairs_law[1] + 1))) !=
+        (e = cudaMalloc(&p->d_jljc, sizeof(float4) * (td->sym ? size_t(f4_law[1] + 1)
+                                                                : 3 * size_t(pairs_law[1] + 1)))) !=
             cudaSuccess ||
         (e = cudaMalloc(&p->d_sysp, sizeof(int4) * sysp.size())) != cudaSuccess ||
         (e = cudaMemcpy(p->d_sysp, sysp.data(), sizeof(int4) * sysp.size(),

@@ -18,6 +18,11 @@ const TileDesc *mixed_tiles(int *count) {
       // as 6 and 5 with registers capped for 3 CTAs per SM
       TileImpl<kLawMixed, 128, 2, 1, 256, true, 2, 3>::desc(),  // 8: 256 targets
       TileImpl<kLawMixed, 128, 2, 2, 256, true, 2, 3>::desc(),  // 9: 128 targets, 2 j-lanes
+      // Newton-symmetric block-pair items (sym_batch_kernel.cuh)
+      SymBatchImpl<128, 2>::desc(),     // 10: blocks of 256
+      SymBatchImpl<64, 4>::desc(),      // 11: blocks of 256, 2-warp CTAs
+      SymBatchImpl<128, 4>::desc(),     // 12: blocks of 512
+      SymBatchImpl<64, 2>::desc(),      // 13: blocks of 128, 2-warp CTAs
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;

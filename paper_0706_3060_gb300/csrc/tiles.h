@@ -8,6 +8,7 @@
 #include "force_kernel.cuh"
 #include "sym_kernel.cuh"
 #include "sym_ljc_kernel.cuh"
+#include "sym_batch_kernel.cuh"
 
 namespace nbody {
 
@@ -212,6 +213,64 @@ struct SymLjcImpl {
   static TileDesc desc() {
     TileDesc d{LAW, NT, I, 1, T::kB, T::kB, NT, T::smem_bytes(false), true, false,
                &launch, &occupancy};
+    d.sym = true;
+    return d;
+  }
+};
+
+// Newton-symmetric batched tiles (persistent work list of block-pair items over
+// systems of mixed law; no potential).
+template <int NT, int I, int MINB = 1>
+struct SymBatchImpl {
+  using T = SymMixedTile<NT, I>;
+  template <bool PRE>
+  static cudaError_t go(const ForceArgs &a, int grid, cudaStream_t s) {
+    auto k = sym_batch_kernel<NT, I, PRE, MINB>;
+    {  // opt in always: the static shared words count against the 48 KB default too
+      static std::atomic<bool> opted[kMaxDevicesTile];
+      int dev = 0;
+      const bool known = cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDevicesTile;
+      if (!known || !opted[dev].load(std::memory_order_acquire)) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)T::kSmemBytes);
+        if (e != cudaSuccess) return e;
+        if (known) opted[dev].store(true, std::memory_order_release);
+      }
+    }
+    k<<<grid, NT, T::kSmemBytes, s>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t launch(const ForceArgs &a, int grid, bool pot, bool precise,
+                            cudaStream_t s) {
+    if (pot) return cudaErrorInvalidValue;  // batched runs compute no potential
+    return precise ? go<true>(a, grid, s) : go<false>(a, grid, s);
+  }
+  static int occupancy() {
+    static std::atomic<int> cached[kMaxDevicesTile];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesTile) {
+      cudaGetLastError();
+      dev = -1;
+    }
+    if (dev >= 0) {
+      const int c = cached[dev].load(std::memory_order_relaxed);
+      if (c > 0) return c;
+    }
+    int nb = 0;
+    auto k = sym_batch_kernel<NT, I, false, MINB>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::kSmemBytes);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, T::kSmemBytes) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return 1;
+    }
+    nb = std::max(nb, 1);
+    if (dev >= 0) cached[dev].store(nb, std::memory_order_relaxed);
+    return nb;
+  }
+  static TileDesc desc() {
+    TileDesc d{kLawMixed, NT, I, 1, T::kB, T::kB, NT, T::kSmemBytes, true, false, &launch,
+               &occupancy};
     d.sym = true;
     return d;
   }

@@ -155,7 +155,7 @@ def test_one_shot_and_bad_tables():
         nb.BatchPlan([dict(offset=0, n=0, law=0, dt=1e-3)])
 
 
-@pytest.mark.parametrize("tile", range(10))
+@pytest.mark.parametrize("tile", range(14))
 def test_batched_every_tile(small_ensemble, tile):
     """Every compiled batched tile (scalar and packed f32x2, with odd-sized systems
     padded inside their pair buffers) against the oracle, then 3 steps."""
