@@ -44,6 +44,10 @@ SYM_LJCLIN_OPS_PER_UNORDERED_PAIR = 27
 # and for the Newton-symmetric acceleration + jerk: 6 for d and u, 3 for s^2, 2 for y^2,
 # y^3, 3 for d.u, 2 for c, 3 for u + c d, then per side 1 weight + 3 + 3 FMA
 SYM_GAJ_OPS_PER_UNORDERED_PAIR = 33
+# and for the Newton-symmetric LJC VJP: the one-sided pair (48, 49 with the linear
+# dielectric) plus 6 for the source's g, 3 for its F, 4 more for the D and E terms
+SYM_LJC_VJP_OPS_PER_UNORDERED_PAIR = 61
+SYM_LJCLIN_VJP_OPS_PER_UNORDERED_PAIR = 62
 PAPER_FLOPS_PER_PAIR = 19  # the paper's flop count per gravity interaction (Table 1, Appendix)
 FP32_LANES_PER_SM = 128    # FFMA/FADD/FMUL lanes per SM per clock (4 SMSPs x 32)
 SM_MAX_MHZ = 2070.0
@@ -518,12 +522,21 @@ def roofline_by_form(nb, torch, dev):
                  kernel_ms(lambda: nb.adjoint(pv, lam, eps=ev, grad_x=gx, grad_m=gm, tile=8,
                                               jsplit=16), 1)))
     gt = torch.zeros(8, dtype=torch.float64, device=dev)
-    rows.append(("LJC VJP", 65536, 48,
-                 kernel_ms(lambda: nb.adjoint(lp, lam, lprm, grad_x=gx, grad_m=gm,
-                                              grad_types=gt), 1)))
-    rows.append(("LJC(linear) VJP", 65536, 49,
-                 kernel_ms(lambda: nb.adjoint(lp2, lam, lprm2, law=nb.LAW_LJC_LINEAR, grad_x=gx,
-                                              grad_m=gm, grad_types=gt), 1)))
+    for name, law, table, p_, prm_, one, sym, one_tile in (
+            ("LJC VJP", nb.LAW_LJC, nb.TABLE_VJP_LJC, lp, lprm, 48,
+             SYM_LJC_VJP_OPS_PER_UNORDERED_PAIR, (6, 16)),
+            ("LJC(linear) VJP", nb.LAW_LJC_LINEAR, nb.TABLE_VJP_LJC_LINEAR, lp2, lprm2, 49,
+             SYM_LJCLIN_VJP_OPS_PER_UNORDERED_PAIR, (0, 16))):
+        vt, _ = nb.get_config(table, 65536)
+        if nb.tile_info(table, vt)["symmetric"]:
+            rows.append((f"{name} (Newton-symmetric)", 65536, sym / 2 * (65536 - 1) / 65536,
+                         kernel_ms(lambda: nb.adjoint(p_, lam, prm_, law=law, grad_x=gx,
+                                                      grad_m=gm, grad_types=gt), 1)))
+        # the fastest one-sided tile at this size
+        rows.append((f"{name} (one-sided)", 65536, one,
+                     kernel_ms(lambda: nb.adjoint(p_, lam, prm_, law=law, grad_x=gx, grad_m=gm,
+                                                  grad_types=gt, tile=one_tile[0],
+                                                  jsplit=one_tile[1]), 1)))
     for name, n, ops, ms in rows:
         pairs = float(n) * n
         t = ops * pairs / (ms * 1e-3) / 1e12

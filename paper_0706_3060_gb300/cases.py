@@ -74,6 +74,13 @@ def build_case(name, nb, torch, dev):
         pos, prm = _ljc(nb, torch, dev, int(name[3:]))
         acc = torch.empty_like(pos)
         return lambda: nb.forces(pos, prm, out=acc)
+    if name == "ljcvjp8192":
+        pos, prm = _ljc(nb, torch, dev, 8192)
+        lam = torch.randn_like(pos)
+        gx = torch.empty_like(pos)
+        gm = torch.empty(pos.shape[0], device=dev)
+        gt = torch.zeros(8, dtype=torch.float64, device=dev)
+        return lambda: nb.adjoint(pos, lam, prm, grad_x=gx, grad_m=gm, grad_types=gt)
     if name == "vjp16384":
         pos, _, eps = _grav(nb, torch, dev, 16384, seed=4)
         lam = torch.randn_like(pos)
@@ -94,7 +101,7 @@ def build_case(name, nb, torch, dev):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["grav65536", "grav262144", "ljc8192", "ljc65536", "vjp16384",
+    ap.add_argument("case", choices=["grav65536", "grav262144", "ljc8192", "ljcvjp8192", "ljc65536", "vjp16384",
                                      "jerk65536", "jerk262144", "batched512"])
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--iters", type=int, default=2)

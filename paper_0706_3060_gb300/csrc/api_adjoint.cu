@@ -56,12 +56,15 @@ int vjp_prepare(int law, int n, int tile, int jsplit, int sms, cudaStream_t s, V
   const VjpDesc &d = tiles[tile];
   if (d.sym) {  // one CTA per block pair, one partial slot per block, no low parts
     const int nb = (n + d.tile_i - 1) / d.tile_i;
-    const int nblocks = (law == kLawGAJ) ? 2 : 1;  // acceleration and jerk partials
+    const bool lj = (law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR);
+    const int nblocks = (law == kLawGAJ || lj) ? 2 : 1;  // two partial blocks
     const size_t part = round_up(size_t(nblocks) * nb * size_t(n) * sizeof(float4), 256);
     const size_t ubytes = round_up(size_t(n) * sizeof(float4), 256);
     const int nblk = (n + 255) / 256;
     const size_t tbytes = round_up(size_t(nblk) * 8 * sizeof(double), 256);
-    const size_t jbytes = round_up(size_t(nb) * d.tile_i * 2 * sizeof(float4), 256);
+    const int pair_f4 = lj ? 5 : 4;  // float4 per source pair in the blocked layout
+    const size_t jbytes =
+        round_up(size_t(nb) * (d.tile_i / 2) * pair_f4 * sizeof(float4), 256);
     void *base = nullptr;
     NB_TRY(workspace(s, part + ubytes + tbytes + jbytes + extra, &base));
     char *b = static_cast<char *>(base);
@@ -143,7 +146,10 @@ int vjp_once(const float4 *pos, const float4 *prm, const float4 *lam, float4 *gr
   }
   if (sc.d->packed) {
     const unsigned pblocks = unsigned(((n + 1) / 2 + 255) / 256);
-    if (sc.d->sym)
+    if (sc.d->sym && ljc)
+      interleave_ljc_vjp_pairs_blocked_kernel<<<pblocks, 256, 0, s>>>(pos, src, prm, sc.jp, n,
+                                                                      sc.slice_len);
+    else if (sc.d->sym)
       interleave_vjp_pairs_blocked_kernel<<<pblocks, 256, 0, s>>>(pos, src, sc.jp, n,
                                                                   sc.slice_len);
     else if (ljc)

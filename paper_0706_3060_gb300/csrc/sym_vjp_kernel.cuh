@@ -418,4 +418,218 @@ __global__ void __launch_bounds__(NT, MINB) sym_gaj_kernel(const VjpArgs a) {
   }
 }
 
+// LJC VJP (constant or linear dielectric). With u = lam / m, w = u_k - u_j and the
+// pair quantities of vjp_kernel.cuh (phi, 2 phi' = tp, c = tp (d.w)), target k
+// gets g += c d + phi w, F += phi d, D += (d.w) e~e~ y^2 (4 u6^2 - u6) / sigma and
+// E += (d.w) phi_lj. Swapping the pair flips d and w and keeps d.w, phi and tp,
+// so the source gets -(c d + phi w) and -phi d and the same D and E terms:
+// 59 FP32 lane ops per unordered pair against 48 (49) per ordered pair one-sided.
+// Sources in a five-array blocked layout (x x y y), (z z q q), (s s e e),
+// (-ux -ux -uy -uy), (-uz -uz 0 0); partial block A holds (g, D), block B (F, E).
+template <int NT, int I>
+struct SymLjcVjpTile {
+  static constexpr int kB = NT * I;
+  static constexpr int kPairs = kB / 2;
+  static constexpr int kWarps = NT / 32;
+  static constexpr size_t kSrcBytes = size_t(kPairs) * 80;  // five float4 per pair
+  // source-side sums per warp: g, D, F, E components of both halves
+  static constexpr size_t kSmemBytes = kSrcBytes + size_t(kWarps) * 16 * kPairs * sizeof(float);
+};
+
+// One target against one source pair. J (JS) receives the source-side terms in
+// the order g.x, g.y, g.z, D, F.x, F.y, F.z, E, before the sign change of g and F.
+template <bool LIN, bool JS, bool MASK>
+__device__ __forceinline__ void sym_ljc_vjp_pair2(const float4 F0, const float4 F1,
+                                                  const float4 F2, const float4 F3,
+                                                  const float4 F4, float2 nxk, float2 nyk,
+                                                  float2 nzk, float2 ukx, float2 uky, float2 ukz,
+                                                  float2 qk, float2 sk, float2 ek,
+                                                  float2 (&A)[4], float2 (&B)[4], float2 *J,
+                                                  bool self0 = false, bool self1 = false) {
+  const float2 dx = __fadd2_rn(make_float2(F0.x, F0.y), nxk);
+  const float2 dy = __fadd2_rn(make_float2(F0.z, F0.w), nyk);
+  const float2 dz = __fadd2_rn(make_float2(F1.x, F1.y), nzk);
+  const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+  float2 y = make_float2(rsqrt_hw(r2.x), rsqrt_hw(r2.y));
+  if (MASK) {
+    y.x = self0 ? 0.0f : y.x;
+    y.y = self1 ? 0.0f : y.y;
+  }
+  const float2 y2 = __fmul2_rn(y, y);
+  const float2 qq = __fmul2_rn(qk, make_float2(F1.z, F1.w));
+  const float2 s = __fadd2_rn(sk, make_float2(F2.x, F2.y));
+  const float2 ee = __fmul2_rn(ek, make_float2(F2.z, F2.w));
+  const float2 t = __fmul2_rn(__fmul2_rn(s, s), y2);
+  const float2 u = __fmul2_rn(__fmul2_rn(t, t), t);
+  const float2 qy3 = LIN ? __fmul2_rn(__fmul2_rn(qq, y2), __fadd2_rn(y2, y2))
+                         : __fmul2_rn(qq, __fmul2_rn(y, y2));
+  const float2 eey2 = __fmul2_rn(ee, y2);
+  const float2 h = __fmul2_rn(__ffma2_rn(u, make_float2(2.0f, 2.0f), make_float2(-1.0f, -1.0f)), u);
+  const float2 phi_lj = __fmul2_rn(eey2, h);
+  const float2 phi = __fadd2_rn(phi_lj, qy3);
+  const float2 k1 =
+      __fmul2_rn(__ffma2_rn(u, make_float2(-28.0f, -28.0f), make_float2(8.0f, 8.0f)), u);
+  const float kc = LIN ? -4.0f : -3.0f;
+  const float2 tp = __fmul2_rn(y2, __ffma2_rn(eey2, k1, __fmul2_rn(make_float2(kc, kc), qy3)));
+  const float2 wx = __fadd2_rn(ukx, make_float2(F3.x, F3.y));
+  const float2 wy = __fadd2_rn(uky, make_float2(F3.z, F3.w));
+  const float2 wz = __fadd2_rn(ukz, make_float2(F4.x, F4.y));
+  const float2 dw = __ffma2_rn(dx, wx, __ffma2_rn(dy, wy, __fmul2_rn(dz, wz)));
+  const float2 c = __fmul2_rn(tp, dw);
+  const float2 k2 = __fmul2_rn(__ffma2_rn(u, make_float2(4.0f, 4.0f), make_float2(-1.0f, -1.0f)), u);
+  const float2 rs = make_float2(rcp_hw(s.x), rcp_hw(s.y));
+  const float2 dterm = __fmul2_rn(dw, __fmul2_rn(__fmul2_rn(eey2, k2), rs));
+  const float2 eterm = __fmul2_rn(dw, phi_lj);
+  A[0] = __ffma2_rn(c, dx, __ffma2_rn(phi, wx, A[0]));
+  A[1] = __ffma2_rn(c, dy, __ffma2_rn(phi, wy, A[1]));
+  A[2] = __ffma2_rn(c, dz, __ffma2_rn(phi, wz, A[2]));
+  A[3] = __fadd2_rn(A[3], dterm);
+  B[0] = __ffma2_rn(phi, dx, B[0]);
+  B[1] = __ffma2_rn(phi, dy, B[1]);
+  B[2] = __ffma2_rn(phi, dz, B[2]);
+  B[3] = __fadd2_rn(B[3], eterm);
+  if (JS) {
+    J[0] = __ffma2_rn(c, dx, __ffma2_rn(phi, wx, J[0]));
+    J[1] = __ffma2_rn(c, dy, __ffma2_rn(phi, wy, J[1]));
+    J[2] = __ffma2_rn(c, dz, __ffma2_rn(phi, wz, J[2]));
+    J[3] = __fadd2_rn(J[3], dterm);
+    J[4] = __ffma2_rn(phi, dx, J[4]);
+    J[5] = __ffma2_rn(phi, dy, J[5]);
+    J[6] = __ffma2_rn(phi, dz, J[6]);
+    J[7] = __fadd2_rn(J[7], eterm);
+  }
+}
+
+template <int NT, int I, bool LIN, int MINB = 1>
+__global__ void __launch_bounds__(NT, MINB) sym_ljc_vjp_kernel(const VjpArgs a) {
+  using T = SymLjcVjpTile<NT, I>;
+  constexpr int B = T::kB;
+  constexpr int P = T::kPairs;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float4 *src = reinterpret_cast<float4 *>(smem_raw);  // five arrays of P float4
+  float *jsum = reinterpret_cast<float *>(smem_raw + T::kSrcBytes);
+  __shared__ __align__(8) uint64_t bar;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = a.n;
+  const int nb = a.slices;
+  int bi, bj;
+  sym_tile_of(blockIdx.x, nb, bi, bj);
+  if (bj >= nb) {  // outside the triangle: a launch-shape error
+    if (tid == 0) set_error(a.err, kDevBadItem);
+    return;
+  }
+  const int j0 = bj * B;
+  const int nsrc = min(B, n - j0);
+  const int npairs = (nsrc + 1) >> 1;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t bytes = uint32_t(npairs) * 16u;
+    const float4 *blk = a.jpair + size_t(bj) * 5 * P;
+    mbar_arrive_expect_tx(&bar, 5 * bytes);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) tma_load_1d(src + c * P, blk + c * P, bytes, &bar);
+  }
+  const bool diag = (bi == bj);
+  if (!diag)
+    for (int k = tid; k < T::kWarps * 16 * P; k += NT) jsum[k] = 0.0f;
+
+  // targets of block bi (a.lam holds u = lam / m); missing ones have no charge, well or u
+  float2 nx[I], ny[I], nz[I], ux[I], uy[I], uz[I], qk[I], sk[I], ek[I];
+  float2 A[I][4], Bv[I][4];
+  int ig[I];
+#pragma unroll
+  for (int r = 0; r < I; ++r) {
+    const int g = bi * B + r * NT + tid;
+    ig[r] = g < n ? g : -1;
+    const float4 p = g < n ? __ldg(a.pos + g) : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+    const float4 l = g < n ? __ldg(a.lam + g) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const float4 q = g < n ? __ldg(a.prm + g) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    nx[r] = make_float2(-p.x, -p.x);
+    ny[r] = make_float2(-p.y, -p.y);
+    nz[r] = make_float2(-p.z, -p.z);
+    ux[r] = make_float2(l.x, l.x);
+    uy[r] = make_float2(l.y, l.y);
+    uz[r] = make_float2(l.z, l.z);
+    qk[r] = make_float2(q.x, q.x);
+    sk[r] = make_float2(q.y, q.y);
+    ek[r] = make_float2(q.z, q.z);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) A[r][c] = Bv[r][c] = make_float2(0.0f, 0.0f);
+  }
+  __syncthreads();  // jsum cleared
+  const bool ok = mbar_wait(&bar, 0, a.err);
+  if (!__syncthreads_and(ok)) return;
+  const float4 *s0 = src, *s1 = src + P, *s2 = src + 2 * P, *s3 = src + 3 * P,
+               *s4 = src + 4 * P;
+
+  if (diag) {
+    for (int pp = 0; pp < npairs; ++pp) {
+      const float4 F0 = s0[pp], F1 = s1[pp], F2 = s2[pp], F3 = s3[pp], F4 = s4[pp];
+      const int jg = j0 + 2 * pp;
+#pragma unroll
+      for (int r = 0; r < I; ++r)
+        sym_ljc_vjp_pair2<LIN, false, true>(F0, F1, F2, F3, F4, nx[r], ny[r], nz[r], ux[r],
+                                            uy[r], uz[r], qk[r], sk[r], ek[r], A[r], Bv[r],
+                                            nullptr, jg == ig[r], jg + 1 == ig[r]);
+    }
+  } else {
+    float *J = jsum + size_t(warp) * 16 * P;
+    for (int g0 = 0; g0 < npairs; g0 += 32) {
+#pragma unroll 1
+      for (int st = 0; st < 32; ++st) {
+        const int pp = g0 + ((lane + st) & 31);
+        if (pp < npairs) {
+          const float4 F0 = s0[pp], F1 = s1[pp], F2 = s2[pp], F3 = s3[pp], F4 = s4[pp];
+          float2 js[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) js[c] = make_float2(0.0f, 0.0f);
+#pragma unroll
+          for (int r = 0; r < I; ++r)
+            sym_ljc_vjp_pair2<LIN, true, false>(F0, F1, F2, F3, F4, nx[r], ny[r], nz[r], ux[r],
+                                                uy[r], uz[r], qk[r], sk[r], ek[r], A[r], Bv[r],
+                                                js);
+          // g and F change sign for the sources, D and E do not
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const bool sym = (c == 3 || c == 7);
+            J[(2 * c) * P + pp] += sym ? js[c].x : -js[c].x;
+            J[(2 * c + 1) * P + pp] += sym ? js[c].y : -js[c].y;
+          }
+        }
+        __syncwarp();  // at the next step lane l - 1 updates the slot lane l just wrote
+      }
+    }
+  }
+
+  const long long ibase = (long long)bj * a.stride;
+#pragma unroll
+  for (int r = 0; r < I; ++r)
+    if (ig[r] >= 0) {
+      a.part_hi[ibase + ig[r]] = make_float4(A[r][0].x + A[r][0].y, A[r][1].x + A[r][1].y,
+                                             A[r][2].x + A[r][2].y, A[r][3].x + A[r][3].y);
+      a.part_hi[a.bstride + ibase + ig[r]] =
+          make_float4(Bv[r][0].x + Bv[r][0].y, Bv[r][1].x + Bv[r][1].y,
+                      Bv[r][2].x + Bv[r][2].y, Bv[r][3].x + Bv[r][3].y);
+    }
+  if (diag) return;
+  __syncthreads();
+  const long long jbase = (long long)bi * a.stride + j0;
+  for (int q = tid; q < nsrc; q += NT) {
+    const int pp = q >> 1, h = q & 1;
+    float v[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    for (int w = 0; w < T::kWarps; ++w) {
+      const float *Jw = jsum + size_t(w) * 16 * P;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) v[c] += Jw[(2 * c + h) * P + pp];
+    }
+    a.part_hi[jbase + q] = make_float4(v[0], v[1], v[2], v[3]);
+    a.part_hi[a.bstride + jbase + q] = make_float4(v[4], v[5], v[6], v[7]);
+  }
+}
+
 }  // namespace nbody

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs
     const bool lj = (f.law == NBODY_LAW_LJC || f.law == NBODY_LAW_LJC_LINEAR);
     if (lj) {
       hB = f.part_hi[f.bstride + i];
-      oB = f.part_lo[f.bstride + i];
+      oB = f.part_lo ? f.part_lo[f.bstride + i] : zero;
     }
     for (int k = 1; k < f.slices; ++k) {
       const long long o = (long long)k * f.stride + i;
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs
       oA.w += l.w;
       if (lj) {
         h = f.part_hi[f.bstride + o];
-        l = f.part_lo[f.bstride + o];
+        l = f.part_lo ? f.part_lo[f.bstride + o] : zero;
         comp_add(hB.x, oB.x, h.x);
         comp_add(hB.y, oB.y, h.y);
         comp_add(hB.z, oB.z, h.z);
@@ -225,6 +225,28 @@ __global__ void interleave_ljc_vjp_pairs_kernel(const float4 *pos, const float4 
   jp[q + 2] = make_float4(qa.y, qb.y, qa.z, qb.z);
   jp[q + 3] = make_float4(-ua.x, -ub.x, -ua.y, -ub.y);
   jp[q + 4] = make_float4(-ua.z, -ub.z, 0.f, 0.f);
+}
+
+// LJC VJP sources of the Newton-symmetric tiles, block by block (B particles,
+// 5B/2 float4 per block): the B/2 pairs' (x x y y), then (z z q q), (s s e e),
+// (-ux -ux -uy -uy) and (-uz -uz 0 0). Pairs past n are not written.
+__global__ void interleave_ljc_vjp_pairs_blocked_kernel(const float4 *pos, const float4 *u,
+                                                        const float4 *prm, float4 *jp, int n,
+                                                        int B) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * p >= n) return;
+  const bool two = 2 * p + 1 < n;
+  const float4 a = pos[2 * p], ua = u[2 * p], qa = prm[2 * p];
+  const float4 b = two ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+  const float4 ub = two ? u[2 * p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 qb = two ? prm[2 * p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const int blk = (2 * p) / B, P = B / 2, pp = p - blk * P;
+  const long long q = (long long)blk * 5 * P + pp;
+  jp[q] = make_float4(a.x, b.x, a.y, b.y);
+  jp[q + P] = make_float4(a.z, b.z, qa.x, qb.x);
+  jp[q + 2 * P] = make_float4(qa.y, qb.y, qa.z, qb.z);
+  jp[q + 3 * P] = make_float4(-ua.x, -ub.x, -ua.y, -ub.y);
+  jp[q + 4 * P] = make_float4(-ua.z, -ub.z, 0.f, 0.f);
 }
 
 // u = lam / m (LJC sources are weighted by 1 / m_j).

@@ -68,12 +68,16 @@ struct VjpImpl {
 // Newton-symmetric gravity VJP (GAJ false) and acceleration + jerk (GAJ true)
 // tiles: blocks of NT * I particles, one CTA per block pair; `tile_i` and `jt`
 // report the block size.
-template <bool GAJ, int NT, int I, int MINB>
+template <int LAW, int NT, int I, int MINB>
 struct SymVjpImplT {
-  using T = std::conditional_t<GAJ, SymGajTile<NT, I>, SymVjpTile<NT, I>>;
+  using T = std::conditional_t<
+      LAW == kLawGAJ, SymGajTile<NT, I>,
+      std::conditional_t<is_ljc(LAW), SymLjcVjpTile<NT, I>, SymVjpTile<NT, I>>>;
   static constexpr auto kernel() {
-    if constexpr (GAJ)
+    if constexpr (LAW == kLawGAJ)
       return sym_gaj_kernel<NT, I, MINB>;
+    else if constexpr (is_ljc(LAW))
+      return sym_ljc_vjp_kernel<NT, I, LAW == kLawLJCLin, MINB>;
     else
       return sym_gvjp_kernel<NT, I, MINB>;
   }
@@ -122,17 +126,19 @@ struct SymVjpImplT {
     return d;
   }
   static TileDesc tile() {
-    TileDesc d{GAJ ? kLawGAJ : kLawGrav, NT, I, 1, T::kB, T::kB, NT, T::kSmemBytes, true,
-               false, nullptr, &occupancy};
+    TileDesc d{LAW, NT, I, 1, T::kB, T::kB, NT, T::kSmemBytes, true, false, nullptr,
+               &occupancy};
     d.sym = true;
     return d;
   }
 };
 
 template <int NT, int I, int MINB = 1>
-using SymVjpImpl = SymVjpImplT<false, NT, I, MINB>;
+using SymVjpImpl = SymVjpImplT<kLawGrav, NT, I, MINB>;
 template <int NT, int I, int MINB = 1>
-using SymGajImpl = SymVjpImplT<true, NT, I, MINB>;
+using SymGajImpl = SymVjpImplT<kLawGAJ, NT, I, MINB>;
+template <int LAW, int NT, int I, int MINB = 1>
+using SymLjcVjpImpl = SymVjpImplT<LAW, NT, I, MINB>;
 
 // Rows: (law, consumer threads, targets per thread, j-lanes, j-tile, packed,
 // unroll). Row 0 is the default for large N, row 1 for small N (below 8192).
@@ -186,24 +192,32 @@ using SymGajImpl = SymVjpImplT<true, NT, I, MINB>;
       SymVjpImpl<64, 4, 6>::F(), SymVjpImpl<128, 3, 4>::F(),
 
 const VjpDesc kGravDesc[] = {NB_VJP_GRAV_ROWS(NB_VJP_DESC) NB_VJP_GRAV_SYM(desc)};
-const VjpDesc kLjcDesc[] = {NB_VJP_LJC_ROWS(NB_VJP_DESC)};
+// the LJC VJP tables end with their Newton-symmetric tiles: blocks of 256 (4 warps
+// x 2 targets), 256 in 2-warp CTAs (x 4 targets), 128 in 2-warp CTAs
+#define NB_LJC_VJP_SYM(L, F)                                             \
+  SymLjcVjpImpl<L, 128, 2>::F(), SymLjcVjpImpl<L, 64, 4>::F(), SymLjcVjpImpl<L, 64, 2>::F(),
+
+const VjpDesc kLjcDesc[] = {NB_VJP_LJC_ROWS(NB_VJP_DESC) NB_LJC_VJP_SYM(kLawLJC, desc)};
 // the jerk table ends with its Newton-symmetric tiles: blocks of 512 (3 CTAs/SM),
 // 256 in 2-warp CTAs, 256
 #define NB_GAJ_SYM(F) \
   SymGajImpl<128, 4, 3>::F(), SymGajImpl<64, 4, 6>::F(), SymGajImpl<128, 2>::F(),
 
 const VjpDesc kGajDesc[] = {NB_VJP_GAJ_ROWS(NB_VJP_DESC) NB_GAJ_SYM(desc)};
-const VjpDesc kLjcLinDesc[] = {NB_VJP_LJCLIN_ROWS(NB_VJP_DESC)};
+const VjpDesc kLjcLinDesc[] = {NB_VJP_LJCLIN_ROWS(NB_VJP_DESC)
+                                   NB_LJC_VJP_SYM(kLawLJCLin, desc)};
 const TileDesc kGravTile[] = {NB_VJP_GRAV_ROWS(NB_VJP_TILE) NB_VJP_GRAV_SYM(tile)};
-const TileDesc kLjcTile[] = {NB_VJP_LJC_ROWS(NB_VJP_TILE)};
+const TileDesc kLjcTile[] = {NB_VJP_LJC_ROWS(NB_VJP_TILE) NB_LJC_VJP_SYM(kLawLJC, tile)};
 const TileDesc kGajTile[] = {NB_VJP_GAJ_ROWS(NB_VJP_TILE) NB_GAJ_SYM(tile)};
-const TileDesc kLjcLinTile[] = {NB_VJP_LJCLIN_ROWS(NB_VJP_TILE)};
+const TileDesc kLjcLinTile[] = {NB_VJP_LJCLIN_ROWS(NB_VJP_TILE)
+                                    NB_LJC_VJP_SYM(kLawLJCLin, tile)};
 
 #undef NB_VJP_DESC
 #undef NB_VJP_TILE
 #undef NB_VJP_GRAV_ROWS
 #undef NB_VJP_GRAV_SYM
 #undef NB_GAJ_SYM
+#undef NB_LJC_VJP_SYM
 #undef NB_VJP_LJC_ROWS
 #undef NB_VJP_GAJ_ROWS
 #undef NB_VJP_LJCLIN_ROWS

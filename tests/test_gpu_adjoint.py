@@ -52,7 +52,7 @@ def test_grav_vjp_every_tile(tile, jsplit):
     assert _rel(gm.cpu().numpy(), rm) <= 2e-5, tile
 
 
-@pytest.mark.parametrize("tile", range(9))
+@pytest.mark.parametrize("tile", range(12))
 def test_ljc_vjp_every_tile(tile):
     nb = lib()
     n = 700
@@ -284,7 +284,7 @@ def _ljclin_setup(n, seed):
     return s, pos.contiguous(), prm, sysm, xd, vd
 
 
-@pytest.mark.parametrize("tile", range(4))
+@pytest.mark.parametrize("tile", range(7))
 @pytest.mark.parametrize("n", [600, 3001])
 def test_ljc_linear_vjp_every_tile(tile, n):
     """LJC(linear) VJP (dielectric 4 r) with mass and per-type derivatives, every

@@ -1,8 +1,8 @@
 """GPU parity of the Newton-symmetric gravity tiles (each unordered pair evaluated
 once and applied to both particles) against the FP64 oracle: gravity forces
 (blocks of 512, 768 and 1024), LJC forces with constant and linear dielectric
-(blocks of 256 to 1024), the gravity force VJP and acceleration + jerk (blocks
-of 256 to 512), every ragged case
+(blocks of 256 to 1024), the gravity and LJC force VJPs and acceleration + jerk
+(blocks of 128 to 512), every ragged case
 of one and several blocks (odd N ends with the pad particle), eps = 0 with the
 self pair masked on diagonal blocks, the potential, both rsqrt modes, leapfrog
 trajectories, run-to-run bitwise reproducibility, and the planning rules (no
@@ -13,7 +13,8 @@ import torch
 
 import oracle
 import workloads
-from gpu_util import assert_forces_close, dev, grav_tensors, lib, traj_errors
+from gpu_util import (assert_forces_close, dev, grav_tensors, lib, oracle_ljc_system,
+                      traj_errors)
 
 pytestmark = pytest.mark.gpu
 
@@ -322,3 +323,81 @@ def test_symmetric_jerk_unsoftened_and_hermite():
         ev = traj_errors(vv[:, :3].cpu().numpy(), vr)
         assert ex[0] <= 1e-6 and ex[1] <= 1e-5, (tile, ex)
         assert ev[0] <= 1e-5 and ev[1] <= 1e-4, (tile, ev)
+
+
+@pytest.mark.parametrize("linear", [False, True])
+@pytest.mark.parametrize("n", [2, 3, 127, 128, 129, 257, 1025, 3001])
+def test_symmetric_ljc_vjp_ragged_sizes(n, linear):
+    """LJC VJP with mass and per-type sigma/epsilon derivatives (both dielectric
+    models) through every symmetric tile, against the oracle."""
+    nb = lib()
+    law = nb.LAW_LJC_LINEAR if linear else nb.LAW_LJC
+    table = nb.TABLE_VJP_LJC_LINEAR if linear else nb.TABLE_VJP_LJC
+    D = 4.0 if linear else 80.0
+    s = workloads.ljc_sphere(n, seed=950 + n)
+    x, v, m, q, st, et = s.f32()
+    d = dev()
+    pos = torch.from_numpy(np.concatenate([x, m[:, None]], 1).astype(np.float32)).to(d)
+    prm = nb.pack_ljc(torch.from_numpy(q.astype(np.float64)).to(d),
+                      torch.from_numpy(st.astype(np.float64)[s.types]).to(d),
+                      torch.from_numpy(et.astype(np.float64)[s.types]).to(d),
+                      torch.from_numpy(s.types).to(d), kq=332.0637 / D)
+    sysm = oracle.LJCSystem(m.astype(np.float64), q.astype(np.float64), s.types,
+                            st.astype(np.float64), et.astype(np.float64), 332.0637 / D,
+                            linear=linear)
+    lam = np.random.default_rng(n).standard_normal((n, 4)).astype(np.float32)
+    rg, rm, rs, re = sysm.vjp(x.astype(np.float64), lam[:, :3].astype(np.float64))
+    tiles = _sym_ljc_tiles(table)
+    assert tiles
+    for tile in tiles:
+        gx, gm, gt = nb.adjoint(pos.contiguous(), torch.from_numpy(lam).to(d), prm, law=law,
+                                tile=tile)
+        assert _rel(gx[:, :3].cpu().numpy(), rg) <= 2e-5, (tile, n)
+        assert _rel(gm.cpu().numpy(), rm) <= 2e-5, (tile, n)
+        got_t = gt.cpu().numpy()
+        present = np.unique(s.types)
+        assert _rel(got_t[:4][present], rs[present]) <= 2e-5, (tile, n)
+        assert _rel(got_t[4:][present], re[present]) <= 2e-5, (tile, n)
+
+
+def test_symmetric_ljc_reverse_leapfrog():
+    """LJC reverse leapfrog (torch.autograd.Function) with each symmetric LJC
+    VJP tile and the symmetric LJC force tile installed as the tuned entries for
+    the size, against the FP64 oracle's gradients (positions, velocities,
+    masses, per-type sigma and epsilon)."""
+    nb = lib()
+    from paper_0706_3060_gb300.autograd import leapfrog
+    s = workloads.ljc_sphere(300, seed=14, radius=20.0)
+    x, v, m, q, st, et = s.f32()
+    d = dev()
+    dt, T = 1e-4, 12
+    target = workloads.perturbed_target(x.astype(np.float64), seed=4)
+    sysm, xo, vo = oracle_ljc_system(s)
+    xs, _ = oracle.leapfrog(sysm, xo, vo, dt, T, store=True)
+    ref = oracle.adjoint_leapfrog(sysm, xo, vo, dt, T, oracle.target_loss_grad(xs[-1], target),
+                                  xs=xs)
+    old_f = nb.get_config(nb.LAW_LJC, 300)
+    old_v = nb.get_config(nb.TABLE_VJP_LJC, 300)
+    try:
+        nb.set_tuned(nb.LAW_LJC, 300, _sym_ljc_tiles(nb.LAW_LJC)[0], 0)
+        for tile in _sym_ljc_tiles(nb.TABLE_VJP_LJC):
+            nb.set_tuned(nb.TABLE_VJP_LJC, 300, tile, 0)
+            x0 = torch.from_numpy(x).to(d).requires_grad_(True)
+            v0 = torch.from_numpy(v).to(d).requires_grad_(True)
+            m0 = torch.from_numpy(m).to(d).requires_grad_(True)
+            sig = torch.from_numpy(st).to(d).requires_grad_(True)
+            eps = torch.from_numpy(et).to(d).requires_grad_(True)
+            xT, _ = leapfrog(x0, v0, m0, dt=dt, nsteps=T, k=5, law=nb.LAW_LJC,
+                             q=torch.from_numpy(q.astype(np.float64)).to(d),
+                             types=torch.from_numpy(s.types).to(d), sig_t=sig, eps_t=eps)
+            loss = ((xT - torch.from_numpy(target.astype(np.float32)).to(d)) ** 2).sum() / 300
+            loss.backward()
+            nb.sync_check()
+            assert _rel(x0.grad.cpu().numpy(), ref["x0"]) <= 1e-4, tile
+            assert _rel(v0.grad.cpu().numpy(), ref["v0"]) <= 1e-4, tile
+            assert _rel(m0.grad.cpu().numpy(), ref["m"]) <= 1e-3, tile
+            assert _rel(sig.grad.cpu().numpy(), ref["sig_t"]) <= 1e-3, tile
+            assert _rel(eps.grad.cpu().numpy(), ref["eps_t"]) <= 1e-3, tile
+    finally:
+        nb.set_tuned(nb.LAW_LJC, 300, *old_f)
+        nb.set_tuned(nb.TABLE_VJP_LJC, 300, *old_v)
