@@ -95,7 +95,7 @@ struct Scratch {
 // diagnostics). The symmetric tiles write no low parts and read their sources
 // in whole blocks (nb x B particles, the last block padded).
 size_t scratch_bytes(int law, int n, const Plan1 &plan, int diag_rows) {
-  const bool lo = !plan.tile->sym;
+  const bool lo = !plan.tile->sym || plan.tile->fixed;  // fixed point: int64 (z, w) there
   const int64_t jn = plan.tile->sym ? int64_t(plan.slices) * plan.slice_len : n;
   const size_t part = round_up(size_t(plan.slices) * size_t(n) * sizeof(float4), 256);
   const int nblk = std::max(1, (n + kFinThreads - 1) / kFinThreads);
@@ -105,7 +105,7 @@ size_t scratch_bytes(int law, int n, const Plan1 &plan, int diag_rows) {
 }
 
 int get_scratch(cudaStream_t s, int law, int n, const Plan1 &plan, int diag_rows, Scratch *out) {
-  const bool lo = !plan.tile->sym;
+  const bool lo = !plan.tile->sym || plan.tile->fixed;
   const int64_t jn = plan.tile->sym ? int64_t(plan.slices) * plan.slice_len : n;
   const size_t part = round_up(size_t(plan.slices) * size_t(n) * sizeof(float4), 256);
   const int nblk = std::max(1, (n + kFinThreads - 1) / kFinThreads);

@@ -24,6 +24,9 @@
 // from the j side of tile (ob, b) when ob < b. Partial ob goes to slot ob of
 // part_hi; the finalize kernel adds the slots in index order (compensated), so
 // the result is bitwise reproducible. Per-tile sums are plain FP32 over B terms.
+// FX (NBODY_FIXED_POINT, Sec. 3.2): each partial is rounded onto the 64-bit
+// fixed-point grid 2^S (S from *a.fscale) and stored as four int64, (x, y) in
+// part_hi and (z, w) in part_lo, which the finalize adds as integers.
 #pragma once
 
 #include <cmath>
@@ -58,7 +61,24 @@ __device__ __forceinline__ void sym_tile_of(long long t, int nb, int &bi, int &b
   bj = b + int(t - start(b));
 }
 
-template <int NT, int I, bool POT, bool PRECISE, int MINB = 1>
+// Store one partial of particle `idx` in slot `base` (FP32, or four int64 with FX).
+template <bool FX>
+__device__ __forceinline__ void sym_store(const ForceArgs &a, long long idx, float x, float y,
+                                          float z, float w) {
+  if constexpr (FX) {
+    const float sc = __ldg(a.fscale);
+    long long *ph = reinterpret_cast<long long *>(a.part_hi) + 2 * idx;
+    long long *pl = reinterpret_cast<long long *>(a.part_lo) + 2 * idx;
+    ph[0] = __float2ll_rn(x * sc);
+    ph[1] = __float2ll_rn(y * sc);
+    pl[0] = __float2ll_rn(z * sc);
+    pl[1] = __float2ll_rn(w * sc);
+  } else {
+    a.part_hi[idx] = make_float4(x, y, z, w);
+  }
+}
+
+template <int NT, int I, bool POT, bool PRECISE, int MINB = 1, bool FX = false>
 __global__ void __launch_bounds__(NT, MINB) sym_grav_kernel(const ForceArgs a) {
   using T = SymTile<NT, I>;
   constexpr int B = T::kB;
@@ -189,8 +209,8 @@ __global__ void __launch_bounds__(NT, MINB) sym_grav_kernel(const ForceArgs a) {
 #pragma unroll
   for (int r = 0; r < I; ++r)
     if (ig[r] >= 0)
-      a.part_hi[ibase + ig[r]] = make_float4(ax[r].x + ax[r].y, ay[r].x + ay[r].y,
-                                             az[r].x + az[r].y, aw[r].x + aw[r].y);
+      sym_store<FX>(a, ibase + ig[r], ax[r].x + ax[r].y, ay[r].x + ay[r].y, az[r].x + az[r].y,
+                    aw[r].x + aw[r].y);
   if (diag) return;
   // j side: slot bi of every source of block bj, warps added in index order
   __syncthreads();
@@ -205,7 +225,7 @@ __global__ void __launch_bounds__(NT, MINB) sym_grav_kernel(const ForceArgs a) {
       vz += Jw[(4 + h) * T::kPairs + pp];
       if (POT) vw += Jw[(6 + h) * T::kPairs + pp];
     }
-    a.part_hi[jbase + q] = make_float4(vx, vy, vz, vw);
+    sym_store<FX>(a, jbase + q, vx, vy, vz, vw);
   }
 }
 

@@ -102,13 +102,13 @@ struct TileImpl {
 };
 
 // Newton-symmetric gravity tiles: blocks of NT * I particles, one CTA per block
-// pair; `jt` and `tile_i` report the block size.
-template <int NT, int I, int MINB = 1>
+// pair; `jt` and `tile_i` report the block size. FX: 64-bit fixed-point partials.
+template <int NT, int I, int MINB = 1, bool FX = false>
 struct SymImpl {
   using T = SymTile<NT, I>;
   template <bool POT, bool PRE>
   static cudaError_t go(const ForceArgs &a, int grid, cudaStream_t s) {
-    auto k = sym_grav_kernel<NT, I, POT, PRE, MINB>;
+    auto k = sym_grav_kernel<NT, I, POT, PRE, MINB, FX>;
     const size_t smem = T::smem_bytes(POT);
     {  // opt in always: the static mbarrier counts against the 48 KB default too
       static std::atomic<bool> opted[kMaxDevicesTile];
@@ -141,7 +141,7 @@ struct SymImpl {
       if (c > 0) return c;
     }
     int nb = 0;
-    auto k = sym_grav_kernel<NT, I, false, false, MINB>;
+    auto k = sym_grav_kernel<NT, I, false, false, MINB, FX>;
     const size_t smem = T::smem_bytes(false);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, smem) != cudaSuccess) {
@@ -153,7 +153,7 @@ struct SymImpl {
     return nb;
   }
   static TileDesc desc() {
-    TileDesc d{kLawGrav, NT, I, 1, T::kB, T::kB, NT, T::smem_bytes(false), true, false,
+    TileDesc d{kLawGrav, NT, I, 1, T::kB, T::kB, NT, T::smem_bytes(false), true, FX,
                &launch, &occupancy};
     d.sym = true;
     return d;

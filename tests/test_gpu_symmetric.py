@@ -401,3 +401,33 @@ def test_symmetric_ljc_reverse_leapfrog():
     finally:
         nb.set_tuned(nb.LAW_LJC, 300, *old_f)
         nb.set_tuned(nb.TABLE_VJP_LJC, 300, *old_v)
+
+
+@pytest.mark.parametrize("n", [2, 3, 511, 1025, 3001])
+def test_symmetric_fixed_point(n):
+    """64-bit fixed-point partials (Sec. 3.2) from the symmetric tiles: oracle
+    accuracy for forces and potential, bitwise repeatable, and 10 leapfrog steps."""
+    nb = lib()
+    tiles = _sym_ljc_tiles(nb.TABLE_GRAV_FIXED)
+    assert tiles
+    g = workloads.plummer(n, seed=1100 + n, eps=0.01)
+    pos, _ = grav_tensors(g)
+    eps = float(np.float32(g.eps))
+    ref, phi = _ref(g, potential=True)
+    for tile in tiles:
+        a = nb.forces(pos, eps=eps, fixed=True, pot=True, tile=tile)
+        b = nb.forces(pos, eps=eps, fixed=True, pot=True, tile=tile)
+        assert torch.equal(a, b)
+        assert_forces_close(a[:, :3].cpu().numpy(), ref, what=f"fixed sym tile={tile} n={n}")
+        e = np.abs(a[:, 3].cpu().numpy() - phi) / np.abs(phi)
+        assert e.max() <= 1e-4, (tile, n)
+    if n >= 1000:
+        x, v, m = g.f32_as_f64()
+        sysm = oracle.GravSystem(m, G=g.G, eps=eps)
+        xs, vs = oracle.leapfrog(sysm, x, v, 1e-3, 10, store=True)
+        for tile in tiles:
+            p, vel = grav_tensors(g)
+            acc = torch.empty_like(p)
+            nb.step(p, vel, acc, dt=1e-3, nsteps=10, eps=eps, fixed=True, tile=tile)
+            ex = traj_errors(p[:, :3].cpu().numpy(), xs[-1])
+            assert ex[0] <= 1e-6 and ex[1] <= 1e-5, (tile, ex)

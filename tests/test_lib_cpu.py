@@ -47,8 +47,8 @@ def test_version_and_tiles(lib):
                 assert info["j_tile"] % 2 == 0
             if info["symmetric"]:  # force laws and the gravity VJP; blocks of threads x targets
                 assert law in (nb.LAW_GRAV, nb.LAW_LJC, nb.LAW_LJC_LINEAR, nb.TABLE_BATCHED,
-                               nb.TABLE_VJP_GRAV, nb.TABLE_VJP_LJC, nb.TABLE_JERK,
-                               nb.TABLE_VJP_LJC_LINEAR)
+                               nb.TABLE_GRAV_FIXED, nb.TABLE_VJP_GRAV, nb.TABLE_VJP_LJC,
+                               nb.TABLE_JERK, nb.TABLE_VJP_LJC_LINEAR)
                 assert info["packed"]
                 assert info["j_tile"] == info["threads"] * info["i_per_thread"]
     with pytest.raises(nb.NBodyError):
