@@ -88,9 +88,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
         const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 hi = f.part_hi[i];
         float4 lo = f.part_lo ? f.part_lo[i] : zero;
-        for (int k = 1; k < slices; ++k) {
-          const float4 h = f.part_hi[(long long)k * f.stride + i];
-          const float4 l = f.part_lo ? f.part_lo[(long long)k * f.stride + i] : zero;
+        auto add = [&](const float4 &h, const float4 &l) {
           comp_add(hi.x, lo.x, h.x);
           comp_add(hi.y, lo.y, h.y);
           comp_add(hi.z, lo.z, h.z);
@@ -99,7 +97,23 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
           lo.y = __fadd_rn(lo.y, l.y);
           lo.z = __fadd_rn(lo.z, l.z);
           lo.w = __fadd_rn(lo.w, l.w);
+        };
+        // slots in index order; loads issued four slots ahead of the adds (the
+        // symmetric tiles leave one slot per block: hundreds at large N)
+        int k = 1;
+        for (; k + 3 < slices; k += 4) {
+          float4 h[4], l[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            h[u] = f.part_hi[(long long)(k + u) * f.stride + i];
+            l[u] = f.part_lo ? f.part_lo[(long long)(k + u) * f.stride + i] : zero;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) add(h[u], l[u]);
         }
+        for (; k < slices; ++k)
+          add(f.part_hi[(long long)k * f.stride + i],
+              f.part_lo ? f.part_lo[(long long)k * f.stride + i] : zero);
         // Round hi + lo to FP32 and keep the residual (Fast2Sum, |hi| >= |lo|).
         t.x = __fadd_rn(hi.x, lo.x);
         r.x = __fsub_rn(lo.x, __fsub_rn(t.x, hi.x));
