@@ -11,7 +11,13 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  *  - Interactions are ordered pairs (i, j), i != j, as in Sec. 2: the force on
- *    i sums over all j and Newton's third law is not used to halve the work.
+ *    i sums over all j. One-sided tiles evaluate each ordered pair for its
+ *    target, as the paper does; Newton-symmetric tiles (NBODY_TILE_SYMMETRIC,
+ *    the tuned choice at mid and large N for gravity, LJC, their VJPs,
+ *    acceleration + jerk and batched ensembles) evaluate each unordered pair
+ *    once and apply it to both particles, the pair terms being antisymmetric
+ *    (or, for the sigma/epsilon derivatives, symmetric) under the swap. Both
+ *    give the same sums up to FP32 rounding order and are each reproducible.
  *  - Particle data are arrays of float4, 16-byte aligned, one element per
  *    particle:
  *      pos_m[i] = (x, y, z, m)                          both laws
@@ -74,7 +80,10 @@ enum {
     NBODY_COMPUTE_POT = 1u << 0,     /* also compute phi (acc[i].w)            */
     NBODY_PRECISE_RSQRT = 1u << 1,   /* one Newton step on the hardware rsqrt  */
     NBODY_NO_COMPENSATION = 1u << 2, /* plain FP32 sums (default: per-tile
-                                        TwoSum compensated sums)               */
+                                        TwoSum compensated sums); Newton-
+                                        symmetric tiles sum each block pair
+                                        plainly and always add the per-block
+                                        partials compensated, flag or not      */
     NBODY_ACC_VALID = 1u << 3,       /* nbody_step: acc already holds a(x) for
                                         the entry positions                    */
     NBODY_ACCUMULATE = 1u << 4,      /* nbody_adjoint: add into the outputs    */
