@@ -384,7 +384,8 @@ int nbody_workspace_size(const nbody_params *params, int64_t n, int32_t report_r
 /* Autotune tile table `table` at size n on the caller's device inputs (the
  * paper tunes its unrolling by hand, Sec. 3.3; this searches the compiled
  * configurations instead). Every tile x j-split in {0 (auto), 1, 2, 4, 8, 16,
- * 32} that fits n is run once to warm up and `reps` (1..1000) more times, timed
+ * 32} that fits n (Newton-symmetric tiles: j-split 0 only, and only where their
+ * partial-sum cap admits n) is run once to warm up and `reps` (1..1000) more times, timed
  * with CUDA events on `stream`; the median decides. The fastest is installed
  * with nbody_set_tuned for bucket floor(log2 n) and returned in best_tile,
  * best_jsplit and best_ms (milliseconds per call; any may be NULL). What is
