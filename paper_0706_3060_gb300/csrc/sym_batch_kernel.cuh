@@ -115,7 +115,10 @@ __device__ __forceinline__ bool sym_batch_item(const ForceArgs &a, const WorkIte
   }
   __syncthreads();  // jsum cleared
   const bool ok = mbar_wait(bar, phase, a.err);
-  if (!__syncthreads_and(ok)) return false;
+  if (!__syncthreads_and(ok)) {  // a copy may still be landing: bounded drain, then leave
+    if (tid == 0) mbar_wait(bar, phase, a.err);
+    return false;
+  }
   const float4 *s0 = src, *s1 = src + P, *s2 = src + 2 * P;
   const float2 e2 = make_float2(w.eps2, w.eps2);
   float2 dummy = make_float2(0.0f, 0.0f);

@@ -134,7 +134,10 @@ __global__ void __launch_bounds__(NT, MINB) sym_grav_kernel(const ForceArgs a) {
   __syncthreads();  // jsum cleared
   // bounded wait for the source block; the CTA leaves together if any wait ran out
   const bool ok = mbar_wait(&bar, 0, a.err);
-  if (!__syncthreads_and(ok)) return;
+  if (!__syncthreads_and(ok)) {  // a copy may still be landing: bounded drain, then leave
+    if (tid == 0) mbar_wait(&bar, 0, a.err);
+    return;
+  }
   const float2 e2 = make_float2(a.eps2, a.eps2);
 
   if (diag) {

@@ -143,7 +143,10 @@ __global__ void __launch_bounds__(NT, MINB) sym_ljc_kernel(const ForceArgs a) {
   }
   __syncthreads();  // jsum cleared
   const bool ok = mbar_wait(&bar, 0, a.err);
-  if (!__syncthreads_and(ok)) return;
+  if (!__syncthreads_and(ok)) {  // a copy may still be landing: bounded drain, then leave
+    if (tid == 0) mbar_wait(&bar, 0, a.err);
+    return;
+  }
 
   if (diag) {
     for (int pp = 0; pp < npairs; ++pp) {

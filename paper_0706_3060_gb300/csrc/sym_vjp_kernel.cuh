@@ -143,7 +143,10 @@ __global__ void __launch_bounds__(NT, MINB) sym_gvjp_kernel(const VjpArgs a) {
   }
   __syncthreads();  // jsum cleared
   const bool ok = mbar_wait(&bar, 0, a.err);
-  if (!__syncthreads_and(ok)) return;
+  if (!__syncthreads_and(ok)) {  // a copy may still be landing: bounded drain, then leave
+    if (tid == 0) mbar_wait(&bar, 0, a.err);
+    return;
+  }
   const float2 e2 = make_float2(a.eps2, a.eps2);
 
   if (diag) {
@@ -345,7 +348,10 @@ __global__ void __launch_bounds__(NT, MINB) sym_gaj_kernel(const VjpArgs a) {
   }
   __syncthreads();  // jsum cleared
   const bool ok = mbar_wait(&bar, 0, a.err);
-  if (!__syncthreads_and(ok)) return;
+  if (!__syncthreads_and(ok)) {  // a copy may still be landing: bounded drain, then leave
+    if (tid == 0) mbar_wait(&bar, 0, a.err);
+    return;
+  }
   const float2 e2 = make_float2(a.eps2, a.eps2);
 
   if (diag) {
@@ -563,7 +569,10 @@ __global__ void __launch_bounds__(NT, MINB) sym_ljc_vjp_kernel(const VjpArgs a) 
   }
   __syncthreads();  // jsum cleared
   const bool ok = mbar_wait(&bar, 0, a.err);
-  if (!__syncthreads_and(ok)) return;
+  if (!__syncthreads_and(ok)) {  // a copy may still be landing: bounded drain, then leave
+    if (tid == 0) mbar_wait(&bar, 0, a.err);
+    return;
+  }
   const float4 *s0 = src, *s1 = src + P, *s2 = src + 2 * P, *s3 = src + 3 * P,
                *s4 = src + 4 * P;
 
