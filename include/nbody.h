@@ -356,7 +356,8 @@ enum {
                                   is the block size, j-split unused; scratch holds one
                                   partial per particle and block, so it is refused
                                   (explicit tile) or replaced by the default tile
-                                  (tuned) above 4 GiB of partials, and always for
+                                  (tuned) when the partials would exceed an eighth of
+                                  the device's memory or 16 GiB, and always for
                                   subsets and the allocation-free entry point */
 };
 /* Describe configuration `tile` of `law`: threads per CTA (consumer warps),

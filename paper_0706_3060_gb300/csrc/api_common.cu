@@ -1,6 +1,8 @@
 // api_common.cu -- host helpers behind the C ABI (see api_common.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <utility>
@@ -315,12 +317,31 @@ int get_config(int law, int64_t n, int *tile, int *jsplit) {
 }
 
 // Largest partial-sum buffer a symmetric tile may ask for (one float4 per
-// particle and block).
-constexpr double kSymPartMax = 4.0 * 1024 * 1024 * 1024;
+// particle and block): an eighth of the device's memory, at most 16 GiB (4 GiB
+// when the device cannot be queried). Cached per device.
+double sym_part_cap() {
+  constexpr double kGiB = 1024.0 * 1024.0 * 1024.0;
+  static std::atomic<double> cached[kMaxDevicesTile];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesTile) {
+    cudaGetLastError();
+    return 4.0 * kGiB;
+  }
+  double c = cached[dev].load(std::memory_order_relaxed);
+  if (c > 0.0) return c;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return 4.0 * kGiB;
+  }
+  c = std::min(16.0 * kGiB, double(total_b) / 8.0);
+  cached[dev].store(c, std::memory_order_relaxed);
+  return c;
+}
 
 bool sym_fits(int64_t n, int block) {
   const long long nb = (n + block - 1) / block;
-  return nb * (nb + 1) / 2 <= 0x7fffffffLL && double(nb) * double(n) * 16.0 <= kSymPartMax;
+  return nb * (nb + 1) / 2 <= 0x7fffffffLL && double(nb) * double(n) * 16.0 <= sym_part_cap();
 }
 
 int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out, bool allow_sym) {

@@ -92,7 +92,7 @@ struct Plan1 {
 int default_tile(int law, int64_t n);
 // Whether a Newton-symmetric tile with blocks of `block` particles may run at n:
 // nb (nb + 1) / 2 block pairs within the grid limit and nb x n float4 partials
-// (nb = ceil(n / block)) within 4 GiB.
+// (nb = ceil(n / block)) within an eighth of the device's memory, at most 16 GiB.
 bool sym_fits(int64_t n, int block);
 int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out,
                 bool allow_sym = false);

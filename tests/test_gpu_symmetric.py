@@ -118,10 +118,10 @@ def test_symmetric_planning_rules():
     # targets that are not the sources: refused for an explicit symmetric tile
     with pytest.raises(nb.NBodyError):
         nb.forces_subset(pos, idx, eps=0.01, tile=t)
-    # partials above the cap (one float4 per particle and block, 4 GiB)
+    # partials above the cap (one float4 per particle and block; at most 16 GiB)
     B = nb.tile_info(nb.LAW_GRAV, t)["j_tile"]
-    n_big = 1 << 20
-    assert (n_big // B) * n_big * 16 > 4 << 30
+    n_big = 1 << 21
+    assert (n_big // B) * n_big * 16 > 16 << 30
     with pytest.raises(nb.NBodyError):
         nb.workspace_size(n_big, eps=0.01, tile=t)
     assert nb.workspace_size(1 << 16, eps=0.01, tile=t) > 0
@@ -200,8 +200,8 @@ def test_symmetric_vjp_planning_rules():
     nb = lib()
     t = _sym_vjp_tiles()[0]
     B = nb.tile_info(nb.TABLE_VJP_GRAV, t)["j_tile"]
-    n_big = 1 << 21  # partials (n / B) x n x 16 B far above the 4 GiB cap
-    assert (n_big // B) * n_big * 16 > 4 << 30
+    n_big = 1 << 21  # partials (n / B) x n x 16 B far above the 16 GiB cap
+    assert (n_big // B) * n_big * 16 > 16 << 30
     pos = torch.zeros((n_big, 4), device=dev())
     pos[:, 0] = torch.arange(n_big, device=dev(), dtype=torch.float32)
     with pytest.raises(nb.NBodyError):
