@@ -353,7 +353,10 @@ enum {
                                   evaluation is preceded by one interleave launch */
     NBODY_TILE_SYMMETRIC = 2,  /* Newton-symmetric block pairs: each unordered pair
                                   evaluated once and applied to both particles; j_tile
-                                  is the block size, j-split unused; scratch holds one
+                                  is the block size; for the force laws the j-split
+                                  cuts each block's sources into 1, 2, 4 or 8 parts
+                                  (one CTA each; 0: one part, other values rounded
+                                  down); scratch holds one
                                   partial per particle and block, so it is refused
                                   (explicit tile) or replaced by the default tile
                                   (tuned) when the partials would exceed an eighth of
@@ -385,8 +388,8 @@ int nbody_workspace_size(const nbody_params *params, int64_t n, int32_t report_r
 /* Autotune tile table `table` at size n on the caller's device inputs (the
  * paper tunes its unrolling by hand, Sec. 3.3; this searches the compiled
  * configurations instead). Every tile x j-split in {0 (auto), 1, 2, 4, 8, 16,
- * 32} that fits n (Newton-symmetric tiles: j-split 0 only, and only where their
- * partial-sum cap admits n) is run once to warm up and `reps` (1..1000) more times, timed
+ * 32} that fits n (Newton-symmetric tiles: the splits their plan takes, and only
+ * where their partial-sum cap admits n) is run once to warm up and `reps` (1..1000) more times, timed
  * with CUDA events on `stream`; the median decides. The fastest is installed
  * with nbody_set_tuned for bucket floor(log2 n) and returned in best_tile,
  * best_jsplit and best_ms (milliseconds per call; any may be NULL). What is

@@ -139,6 +139,8 @@ int eval_and_finalize(const float4 *pos, const float4 *prm, const nbody_params &
   f.part_lo = sc.part_lo;
   f.stride = n;
   f.slices = plan.slices;
+  f.sym_block = plan.tile->sym ? plan.tile->tile_i : 0;
+  f.sym_split = plan.tile->sym ? plan.sym_split : 1;
   f.sys_of = nullptr;
   f.sys = nullptr;
   f.n = n;

@@ -367,7 +367,7 @@ int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms,
     jsplit = 0;
   }
   const TileDesc &d = tiles[tile];
-  if (d.sym) {  // one CTA per block pair, one partial slot per block
+  if (d.sym) {  // one CTA per block pair and source part, one partial slot per block and part
     const long long nb = (n + d.tile_i - 1) / d.tile_i;
     if (!sym_fits(n, d.tile_i)) {
       if (!tuned)
@@ -375,11 +375,25 @@ int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms,
                              (long long)n, tile);
       return plan_targets(law, n_t, n, default_tile(law, n_t), 0, sms, out, false);
     }
+    // Source parts per block: the j-split rounded down to a power of two of at
+    // most 8 with each part at least 32 source pairs (as the one-sided tiles clamp
+    // theirs); none when it is 0. More parts fill the GPU at small N but add slots
+    // to the finalize, so the tuner, which times whole calls, chooses.
+    const long long pairs = nb * (nb + 1) / 2;
+    const int max_split = (law <= NBODY_LAW_LJC_LINEAR || law == kTableGravFixed)
+                              ? std::min(8, std::max(1, d.tile_i / 64))
+                              : 1;
+    int S = 1;
+    while (jsplit > 0 && S * 2 <= std::min(jsplit, max_split)) S *= 2;
+    if (pairs * S > 0x7fffffffLL || double(nb) * S * double(n) * 16.0 > sym_part_cap())
+      return set_error_msg(NBODY_EINVAL, "n = %lld too large for symmetric tile %d split %d",
+                           (long long)n, tile, S);
     out->tile = &d;
-    out->slices = int(nb);
-    out->slice_len = d.tile_i;
+    out->slices = int(nb * S);
+    out->slice_len = d.tile_i / S;
     out->n_itiles = int(nb);
-    out->grid = int(nb * (nb + 1) / 2);
+    out->grid = int(pairs * S);
+    out->sym_split = S;
     return NBODY_OK;
   }
   const int n_it = int((n_t + d.tile_i - 1) / d.tile_i);
@@ -412,6 +426,7 @@ int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms,
   out->slice_len = len;
   out->n_itiles = n_it;
   out->grid = n_it * S;
+  out->sym_split = 1;
   return NBODY_OK;
 }
 
@@ -492,12 +507,12 @@ int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags,
     const int np = (n + 1) / 2;
     if ((law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR) && p.tile->sym)
       interleave_ljc_pairs_blocked_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, prm, jbuf, n,
-                                                                           p.slice_len);
+                                                                           p.tile->tile_i);
     else if (law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR)
       interleave_ljc_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, prm, jbuf, n);
     else if (p.tile->sym)
       interleave_pairs_blocked_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, jbuf, n,
-                                                                       p.slice_len);
+                                                                       p.tile->tile_i);
     else
       interleave_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, jbuf, n);
     NB_CUDA(cudaGetLastError());

@@ -80,10 +80,11 @@ const TileDesc *tiles_for(int law, int *count);
 // Decide (tile, slices, slice_len) for a single-system evaluation.
 struct Plan1 {
   const TileDesc *tile;
-  int slices;
-  int slice_len;
+  int slices;      // partial slots per particle
+  int slice_len;   // sources per slice (symmetric tiles: per part of a block)
   int n_itiles;
   int grid;
+  int sym_split;   // symmetric tiles: source parts per block (1 otherwise)
 };
 // allow_sym: the Newton-symmetric tiles may be used (targets are the sources
 // and the partials have room for one slot per block); otherwise a tuned

@@ -104,8 +104,18 @@ int nbody_tune(int32_t table, const void *pos_m, const void *prm, int64_t n, flo
   for (int t = 0; t < count && st == NBODY_OK; ++t) {
     for (int js : kSplits) {
       if (js > 0 && int64_t(js) * tiles[t].jt > n) continue;  // slices shorter than a j-tile
-      if (js > 0 && tiles[t].sym) continue;                   // symmetric tiles: no j-split
-      if (tiles[t].sym && !sym_fits(n, tiles[t].tile_i)) continue;  // refused by the plan
+      if (tiles[t].sym) {  // j-split = source parts per block; skip what the plan refuses
+        if (!sym_fits(n, tiles[t].tile_i)) continue;
+        if (js > 0) {  // only splits the plan takes as given (not rounded or refused)
+          Plan1 probe{};
+          if (table >= kTableVjpGrav || table == kTableBatched ||
+              plan_single(table, n, t, js, sms, &probe, true) != NBODY_OK ||
+              probe.sym_split != js) {
+            clear_error();
+            continue;
+          }
+        }
+      }
       if (js == 0 && tiles[t].tile_i > 4 * n) continue;       // far more targets than particles
       st = run_once(table, pos_m, prm, n, eps2, t, js, o0, o1, om, s);  // warm-up
       for (int r = 0; r < reps && st == NBODY_OK; ++r) {

@@ -64,10 +64,18 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
     }
     if (live) {
       float4 t, r;
+      // The slots that count, in index order: with the symmetric tiles' source
+      // split (sp parts per block) a particle of block own_b and part own_s gets,
+      // below its own block, only its part's slot of each block (kb * sp + own_s),
+      // and from its own block on every slot; without a split, every slot.
+      const int sp = f.sym_split > 1 ? f.sym_split : 1;
+      const int own_b = sp > 1 ? i / f.sym_block : 0;
+      const int own_s = sp > 1 ? ((i - own_b * f.sym_block) >> 1) / (f.sym_block / 2 / sp) : 0;
+      const int k_all = own_b * sp;  // first slot from which every slot counts
       if (f.fx_inv) {
         // 64-bit fixed-point partials: exact integer sum, one rounding at the end
         long long sx = 0, sy = 0, sz = 0, sw = 0;
-        for (int k = 0; k < slices; ++k) {
+        auto take = [&](int k) {
           const long long *ph = reinterpret_cast<const long long *>(f.part_hi) +
                                 2 * ((long long)k * f.stride + i);
           const long long *pl = reinterpret_cast<const long long *>(f.part_lo) +
@@ -76,7 +84,9 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
           sy += ph[1];
           sz += pl[0];
           sw += pl[1];
-        }
+        };
+        for (int kb = 0; kb < own_b; ++kb) take(kb * sp + own_s);
+        for (int k = k_all; k < slices; ++k) take(k);
         const double inv = *f.fx_inv;
         const double dx = double(sx) * inv, dy = double(sy) * inv, dz = double(sz) * inv,
                      dw = double(sw) * inv;
@@ -86,8 +96,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
       } else {
         // part_lo == nullptr: partials without low parts (symmetric tiles)
         const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 hi = f.part_hi[i];
-        float4 lo = f.part_lo ? f.part_lo[i] : zero;
+        float4 hi = zero, lo = zero;
         auto add = [&](const float4 &h, const float4 &l) {
           comp_add(hi.x, lo.x, h.x);
           comp_add(hi.y, lo.y, h.y);
@@ -98,22 +107,28 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
           lo.z = __fadd_rn(lo.z, l.z);
           lo.w = __fadd_rn(lo.w, l.w);
         };
-        // slots in index order; loads issued four slots ahead of the adds (the
-        // symmetric tiles leave one slot per block: hundreds at large N)
-        int k = 1;
-        for (; k + 3 < slices; k += 4) {
-          float4 h[4], l[4];
+        // `count` slots k0, k0 + step, ...; loads issued four slots ahead of the
+        // adds (the symmetric tiles leave one slot per block: hundreds at large N)
+        auto run = [&](int k0, int count, int step) {
+          int c = 0;
+          for (; c + 3 < count; c += 4) {
+            float4 h[4], l[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            h[u] = f.part_hi[(long long)(k + u) * f.stride + i];
-            l[u] = f.part_lo ? f.part_lo[(long long)(k + u) * f.stride + i] : zero;
+            for (int u = 0; u < 4; ++u) {
+              const long long o = (long long)(k0 + (c + u) * step) * f.stride + i;
+              h[u] = f.part_hi[o];
+              l[u] = f.part_lo ? f.part_lo[o] : zero;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) add(h[u], l[u]);
           }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) add(h[u], l[u]);
-        }
-        for (; k < slices; ++k)
-          add(f.part_hi[(long long)k * f.stride + i],
-              f.part_lo ? f.part_lo[(long long)k * f.stride + i] : zero);
+          for (; c < count; ++c) {
+            const long long o = (long long)(k0 + c * step) * f.stride + i;
+            add(f.part_hi[o], f.part_lo ? f.part_lo[o] : zero);
+          }
+        };
+        run(own_s, own_b, sp);
+        run(k_all, slices - k_all, 1);
         // Round hi + lo to FP32 and keep the residual (Fast2Sum, |hi| >= |lo|).
         t.x = __fadd_rn(hi.x, lo.x);
         r.x = __fsub_rn(lo.x, __fsub_rn(t.x, hi.x));

@@ -41,6 +41,11 @@ struct FinalizeArgs {
   float4 *v_lo;
   int mode;
   double *diag_part;     // [gridDim.x][8]
+  // Newton-symmetric tiles with the source split (sym_kernel.cuh): block size
+  // and parts per block; slot k of particle i counts only if k / split >=
+  // i / block or k % split is i's part. sym_split <= 1: every slot counts.
+  int sym_block;
+  int sym_split;
 };
 
 constexpr int kFinThreads = 256;

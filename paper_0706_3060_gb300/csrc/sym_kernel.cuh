@@ -24,6 +24,12 @@
 // from the j side of tile (ob, b) when ob < b. Partial ob goes to slot ob of
 // part_hi; the finalize kernel adds the slots in index order (compensated), so
 // the result is bitwise reproducible. Per-tile sums are plain FP32 over B terms.
+// Source split (small N, more CTAs than block pairs): each block's B/2 source
+// pairs are cut into S equal parts, a.slice_len = B / S sources each, and CTA
+// t * S + s takes part s of block pair t. Its target-side partial goes to slot
+// bj * S + s, its source-side partial to slot bi * S + s, so a particle of block
+// b and part s_p receives every slot k with k / S >= b and, below that, those with
+// k % S == s_p; the finalize kernel skips the rest. S = 1 is the plain scheme.
 // FX (NBODY_FIXED_POINT, Sec. 3.2): each partial is rounded onto the 64-bit
 // fixed-point grid 2^S (S from *a.fscale) and stored as four int64, (x, y) in
 // part_hi and (z, w) in part_lo, which the finalize adds as integers.
@@ -88,30 +94,40 @@ __global__ void __launch_bounds__(NT, MINB) sym_grav_kernel(const ForceArgs a) {
   float4 *src1 = src0 + T::kPairs;                       // (z z m m) of each pair
   float *jsum = reinterpret_cast<float *>(smem_raw + T::kSrcBytes);
   __shared__ __align__(8) uint64_t bar;
+  __shared__ int part_meta[3];  // (parts per block, part, first pair), read after the loop
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = a.n;
-  const int nb = a.slices;
+  const int nparts = B / a.slice_len;  // source parts per block
+  const int nb = a.slices / nparts;
+  const int t = int(blockIdx.x) / nparts, s = int(blockIdx.x) - t * nparts;
   int bi, bj;
-  sym_tile_of(blockIdx.x, nb, bi, bj);
+  sym_tile_of(t, nb, bi, bj);
   if (bj >= nb) {  // outside the triangle: a launch-shape error
     if (tid == 0) set_error(a.err, kDevBadItem);
     return;
   }
   const int j0 = bj * B;
   const int nsrc = min(B, n - j0);
-  const int npairs = (nsrc + 1) >> 1;  // an odd count ends with the pad particle
+  const int p0 = s * (T::kPairs / nparts);  // first source pair of this part
+  // an odd count ends with the pad particle; the last block's late parts may be empty
+  const int npairs = max(0, min(T::kPairs / nparts, ((nsrc + 1) >> 1) - p0));
   if (tid == 0) {
     mbar_init(&bar, 1);
     mbar_fence_init();
+    part_meta[0] = nparts;  // kept in shared memory, not in registers, across the loop
+    part_meta[1] = s;
+    part_meta[2] = p0;
   }
   __syncthreads();
   if (tid == 0) {
     const uint32_t bytes = uint32_t(npairs) * 16u;
-    const float4 *blk = a.jpair + size_t(bj) * B;  // blocked layout: B float4 per block
+    const float4 *blk = a.jpair + size_t(bj) * B + p0;  // blocked layout: B float4 per block
     mbar_arrive_expect_tx(&bar, 2 * bytes);
-    tma_load_1d(src0, blk, bytes, &bar);
-    tma_load_1d(src1, blk + T::kPairs, bytes, &bar);
+    if (npairs > 0) {
+      tma_load_1d(src0, blk, bytes, &bar);
+      tma_load_1d(src1, blk + T::kPairs, bytes, &bar);
+    }
   }
   const bool diag = (bi == bj);
   if (!diag)
@@ -144,7 +160,7 @@ __global__ void __launch_bounds__(NT, MINB) sym_grav_kernel(const ForceArgs a) {
     // one-sided over all ordered pairs of the block, self pair dropped
     for (int pp = 0; pp < npairs; ++pp) {
       const float4 A = src0[pp], Bq = src1[pp];
-      const int jg = j0 + 2 * pp;
+      const int jg = j0 + 2 * (p0 + pp);
 #pragma unroll
       for (int r = 0; r < I; ++r)
         grav_pair2<POT, PRECISE, true>(make_float2(A.x, A.y), make_float2(A.z, A.w),
@@ -207,18 +223,20 @@ __global__ void __launch_bounds__(NT, MINB) sym_grav_kernel(const ForceArgs a) {
     }
   }
 
-  // i side: slot bj of every target of block bi
-  const long long ibase = (long long)bj * a.stride;
+  // i side: slot bj (part s) of every target of block bi
+  const int np_ = part_meta[0], s_ = part_meta[1], p0_ = part_meta[2];
+  const long long ibase = (long long)(bj * np_ + s_) * a.stride;
 #pragma unroll
   for (int r = 0; r < I; ++r)
     if (ig[r] >= 0)
       sym_store<FX>(a, ibase + ig[r], ax[r].x + ax[r].y, ay[r].x + ay[r].y, az[r].x + az[r].y,
                     aw[r].x + aw[r].y);
   if (diag) return;
-  // j side: slot bi of every source of block bj, warps added in index order
+  // j side: slot bi (part s) of every source of the part, warps added in index order
   __syncthreads();
-  const long long jbase = (long long)bi * a.stride + j0;
-  for (int q = tid; q < nsrc; q += NT) {
+  const long long jbase = (long long)(bi * np_ + s_) * a.stride + j0 + 2 * p0_;
+  const int nq = min(2 * npairs, nsrc - 2 * p0_);
+  for (int q = tid; q < nq; q += NT) {
     const int pp = q >> 1, h = q & 1;
     float vx = 0.0f, vy = 0.0f, vz = 0.0f, vw = 0.0f;
     for (int w = 0; w < T::kWarps; ++w) {

@@ -10,9 +10,10 @@
 // pair: 26 FP32 lane ops (27 for the linear dielectric) against 23 (24) per
 // ordered pair one-sided.
 //
-// Blocks, block pairs, the per-block partial slots, the rotating lane schedule
-// of the source-side sums and the diagonal blocks (one-sided, self pair masked)
-// follow sym_kernel.cuh. Sources come in the blocked layout of
+// Blocks, block pairs, the per-block partial slots, the source split (S parts
+// per block at small N), the rotating lane schedule of the source-side sums and
+// the diagonal blocks (one-sided, self pair masked) follow sym_kernel.cuh.
+// Sources come in the blocked layout of
 // interleave_ljc_pairs_blocked_kernel: per block of B particles the B/2 pairs'
 // (x x y y), then (z z q q), then (s s e e) words.
 #pragma once
@@ -94,31 +95,40 @@ __global__ void __launch_bounds__(NT, MINB) sym_ljc_kernel(const ForceArgs a) {
   float4 *s2 = s1 + P;                                 // (s s e e)
   float *jsum = reinterpret_cast<float *>(smem_raw + T::kSrcBytes);
   __shared__ __align__(8) uint64_t bar;
+  __shared__ int part_meta[3];  // (parts per block, part, first pair), read after the loop
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = a.n;
-  const int nb = a.slices;
+  const int nparts = B / a.slice_len;  // source parts per block
+  const int nb = a.slices / nparts;
+  const int t = int(blockIdx.x) / nparts, sp = int(blockIdx.x) - t * nparts;
   int bi, bj;
-  sym_tile_of(blockIdx.x, nb, bi, bj);
+  sym_tile_of(t, nb, bi, bj);
   if (bj >= nb) {  // outside the triangle: a launch-shape error
     if (tid == 0) set_error(a.err, kDevBadItem);
     return;
   }
   const int j0 = bj * B;
   const int nsrc = min(B, n - j0);
-  const int npairs = (nsrc + 1) >> 1;
+  const int p0 = sp * (P / nparts);  // first source pair of this part
+  const int npairs = max(0, min(P / nparts, ((nsrc + 1) >> 1) - p0));
   if (tid == 0) {
     mbar_init(&bar, 1);
     mbar_fence_init();
+    part_meta[0] = nparts;  // kept in shared memory, not in registers, across the loop
+    part_meta[1] = sp;
+    part_meta[2] = p0;
   }
   __syncthreads();
   if (tid == 0) {
     const uint32_t bytes = uint32_t(npairs) * 16u;
-    const float4 *blk = a.jpair + size_t(bj) * 3 * P;  // three arrays of P float4 per block
+    const float4 *blk = a.jpair + size_t(bj) * 3 * P + p0;  // three arrays of P per block
     mbar_arrive_expect_tx(&bar, 3 * bytes);
-    tma_load_1d(s0, blk, bytes, &bar);
-    tma_load_1d(s1, blk + P, bytes, &bar);
-    tma_load_1d(s2, blk + 2 * P, bytes, &bar);
+    if (npairs > 0) {
+      tma_load_1d(s0, blk, bytes, &bar);
+      tma_load_1d(s1, blk + P, bytes, &bar);
+      tma_load_1d(s2, blk + 2 * P, bytes, &bar);
+    }
   }
   const bool diag = (bi == bj);
   if (!diag)
@@ -151,7 +161,7 @@ __global__ void __launch_bounds__(NT, MINB) sym_ljc_kernel(const ForceArgs a) {
   if (diag) {
     for (int pp = 0; pp < npairs; ++pp) {
       const float4 A = s0[pp], Bq = s1[pp], C = s2[pp];
-      const int jg = j0 + 2 * pp;
+      const int jg = j0 + 2 * (p0 + pp);
 #pragma unroll
       for (int r = 0; r < I; ++r)
         ljc_pair2<POT, PRECISE, LIN, true>(
@@ -193,7 +203,8 @@ __global__ void __launch_bounds__(NT, MINB) sym_ljc_kernel(const ForceArgs a) {
     }
   }
 
-  const long long ibase = (long long)bj * a.stride;
+  const int np_ = part_meta[0], s_ = part_meta[1], p0_ = part_meta[2];
+  const long long ibase = (long long)(bj * np_ + s_) * a.stride;
 #pragma unroll
   for (int r = 0; r < I; ++r)
     if (ig[r] >= 0)
@@ -201,8 +212,9 @@ __global__ void __launch_bounds__(NT, MINB) sym_ljc_kernel(const ForceArgs a) {
                                              az[r].x + az[r].y, aw[r].x + aw[r].y);
   if (diag) return;
   __syncthreads();
-  const long long jbase = (long long)bi * a.stride + j0;
-  for (int q = tid; q < nsrc; q += NT) {
+  const long long jbase = (long long)(bi * np_ + s_) * a.stride + j0 + 2 * p0_;
+  const int nq = min(2 * npairs, nsrc - 2 * p0_);
+  for (int q = tid; q < nq; q += NT) {
     const int pp = q >> 1, h = q & 1;
     float vx = 0.0f, vy = 0.0f, vz = 0.0f, vw = 0.0f;
     for (int w = 0; w < T::kWarps; ++w) {

@@ -431,3 +431,54 @@ def test_symmetric_fixed_point(n):
             nb.step(p, vel, acc, dt=1e-3, nsteps=10, eps=eps, fixed=True, tile=tile)
             ex = traj_errors(p[:, :3].cpu().numpy(), xs[-1])
             assert ex[0] <= 1e-6 and ex[1] <= 1e-5, (tile, ex)
+
+
+@pytest.mark.parametrize("n", [3, 700, 1025, 3001, 8192])
+@pytest.mark.parametrize("jsplit", [2, 4, 8])
+def test_symmetric_source_split(n, jsplit):
+    """The source split (each block's sources cut into 2, 4 or 8 parts, one CTA
+    each, the finalize counting only the slots a particle receives) for every
+    symmetric force tile: gravity with the potential, fixed point, and LJC."""
+    nb = lib()
+    g = workloads.plummer(n, seed=1300 + n, eps=0.01)
+    pos, _ = grav_tensors(g)
+    eps = float(np.float32(g.eps))
+    ref, phi = _ref(g, potential=True)
+    for tile in _sym_tiles():
+        a = nb.forces(pos, eps=eps, pot=True, tile=tile, jsplit=jsplit)
+        b = nb.forces(pos, eps=eps, pot=True, tile=tile, jsplit=jsplit)
+        assert torch.equal(a, b)
+        assert_forces_close(a[:, :3].cpu().numpy(), ref, what=f"tile={tile} split={jsplit} n={n}")
+        e = np.abs(a[:, 3].cpu().numpy() - phi) / np.abs(phi)
+        assert e.max() <= 1e-4, (tile, jsplit, n)
+    for tile in _sym_ljc_tiles(nb.TABLE_GRAV_FIXED):
+        a = nb.forces(pos, eps=eps, fixed=True, tile=tile, jsplit=jsplit)
+        assert_forces_close(a[:, :3].cpu().numpy(), ref, what=f"fixed tile={tile} split={jsplit}")
+    s = workloads.ljc_sphere(n, seed=1400 + n)
+    x, v, m, q, st, et = s.f32()
+    d = dev()
+    lpos = torch.from_numpy(np.concatenate([x, m[:, None]], 1).astype(np.float32)).to(d)
+    prm = nb.pack_ljc(torch.from_numpy(q.astype(np.float64)).to(d),
+                      torch.from_numpy(st.astype(np.float64)[s.types]).to(d),
+                      torch.from_numpy(et.astype(np.float64)[s.types]).to(d),
+                      torch.from_numpy(s.types).to(d))
+    sysm, xo, _ = oracle_ljc_system(s)
+    lref = sysm.accel(xo)
+    for tile in _sym_ljc_tiles(nb.LAW_LJC):
+        a = nb.forces(lpos.contiguous(), prm, tile=tile, jsplit=jsplit)
+        assert_forces_close(a[:, :3].cpu().numpy(), lref, what=f"LJC tile={tile} split={jsplit}")
+
+
+def test_symmetric_split_leapfrog():
+    nb = lib()
+    g = workloads.plummer(3001, seed=31, eps=0.01)
+    eps = float(np.float32(g.eps))
+    x, v, m = g.f32_as_f64()
+    sysm = oracle.GravSystem(m, G=g.G, eps=eps)
+    xs, vs = oracle.leapfrog(sysm, x, v, 1e-3, 10, store=True)
+    for tile in _sym_tiles():
+        pos, vel = grav_tensors(g)
+        acc = torch.empty_like(pos)
+        nb.step(pos, vel, acc, dt=1e-3, nsteps=10, eps=eps, tile=tile, jsplit=4)
+        ex = traj_errors(pos[:, :3].cpu().numpy(), xs[-1])
+        assert ex[0] <= 1e-6 and ex[1] <= 1e-5, (tile, ex)

@@ -72,3 +72,35 @@ def test_one_partial_per_block_and_copies_in_bounds(n, B):
             assert npairs <= P
             base = bj * arrays * P
             assert base + (arrays - 1) * P + npairs <= size
+
+
+@pytest.mark.parametrize("n", [2, 3, 300, 511, 1025, 3001, 8192])
+@pytest.mark.parametrize("B,S", [(512, 1), (512, 2), (512, 4), (1024, 8), (256, 4), (768, 2)])
+def test_source_split_slots_match_the_finalize_rule(n, B, S):
+    """With the source split, CTA (t, s) writes its targets' partial to slot
+    bj*S + s and its part's sources' partial to slot bi*S + s; the finalize
+    counts slot k of particle p iff k // S >= p // B or k % S is p's part. Every
+    counted slot is written exactly once, no other slot is written, and the part
+    copies stay inside the block."""
+    nb = (n + B - 1) // B
+    P = B // 2
+    PS = P // S
+    written = {}
+    for t in range(nb * (nb + 1) // 2):
+        bi, bj = tile_of(t, nb)
+        nsrc = min(B, n - bj * B)
+        for s in range(S):
+            p0 = s * PS
+            npairs = max(0, min(PS, (nsrc + 1) // 2 - p0))
+            assert p0 + npairs <= P  # copy inside the block's arrays
+            for p in range(bi * B, min(n, bi * B + B)):
+                written.setdefault(p, []).append(bj * S + s)
+            if bi != bj:
+                nq = min(2 * npairs, nsrc - 2 * p0)
+                for q in range(max(0, nq)):
+                    written.setdefault(bj * B + 2 * p0 + q, []).append(bi * S + s)
+    for p in range(n):
+        own_b = p // B
+        own_s = ((p - own_b * B) >> 1) // PS
+        counted = [k for k in range(nb * S) if k // S >= own_b or k % S == own_s]
+        assert sorted(written[p]) == counted, (p, sorted(written[p]), counted)
