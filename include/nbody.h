@@ -353,7 +353,8 @@ enum {
                                   evaluation is preceded by one interleave launch */
     NBODY_TILE_SYMMETRIC = 2,  /* Newton-symmetric block pairs: each unordered pair
                                   evaluated once and applied to both particles; j_tile
-                                  is the block size; for the force laws the j-split
+                                  is the block size; for the force laws and the
+                                  gravity VJP the j-split
                                   cuts each block's sources into 1, 2, 4 or 8 parts
                                   (one CTA each; 0: one part, other values rounded
                                   down); scratch holds one

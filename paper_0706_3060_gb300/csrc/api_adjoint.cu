@@ -25,6 +25,7 @@ struct VjpScratch {
   int slices, slice_len, grid, nblk;
   long long bstride;
   const VjpDesc *d;
+  int sym_split;  // symmetric gravity VJP: source parts per block (1 otherwise)
 };
 
 // Tile table of a VJP-kernel law (gravity VJP, LJC VJP, acceleration + jerk).
@@ -54,11 +55,21 @@ int vjp_prepare(int law, int n, int tile, int jsplit, int sms, cudaStream_t s, V
     return set_error_msg(NBODY_EINVAL, "n = %d too large for symmetric tile %d", n, tile);
   }
   const VjpDesc &d = tiles[tile];
-  if (d.sym) {  // one CTA per block pair, one partial slot per block, no low parts
+  if (d.sym) {  // one CTA per block pair (and source part), one slot per block (and part)
     const int nb = (n + d.tile_i - 1) / d.tile_i;
     const bool lj = (law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR);
     const int nblocks = (law == kLawGAJ || lj) ? 2 : 1;  // two partial blocks
-    const size_t part = round_up(size_t(nblocks) * nb * size_t(n) * sizeof(float4), 256);
+    // the gravity VJP takes the source split of the force tiles (j-split rounded down
+    // to a power of two of at most 8, parts of at least 32 source pairs)
+    const int max_split = (law == NBODY_LAW_GRAV) ? std::min(8, std::max(1, d.tile_i / 64)) : 1;
+    int S = 1;
+    while (jsplit > 0 && S * 2 <= std::min(jsplit, max_split)) S *= 2;
+    const long long pairs = (long long)nb * (nb + 1) / 2;
+    if (pairs * S > 0x7fffffffLL)
+      return set_error_msg(NBODY_EINVAL, "n = %d too large for symmetric tile %d split %d", n,
+                           tile, S);
+    const size_t part =
+        round_up(size_t(nblocks) * size_t(nb) * S * size_t(n) * sizeof(float4), 256);
     const size_t ubytes = round_up(size_t(n) * sizeof(float4), 256);
     const int nblk = (n + 255) / 256;
     const size_t tbytes = round_up(size_t(nblk) * 8 * sizeof(double), 256);
@@ -74,12 +85,13 @@ int vjp_prepare(int law, int n, int tile, int jsplit, int sms, cudaStream_t s, V
     sc->type_part = reinterpret_cast<double *>(b + part + ubytes);
     sc->jp = reinterpret_cast<float4 *>(b + part + ubytes + tbytes);
     sc->extra = b + part + ubytes + tbytes + jbytes;
-    sc->slices = nb;
-    sc->slice_len = d.tile_i;
-    sc->grid = int((long long)nb * (nb + 1) / 2);
+    sc->slices = nb * S;
+    sc->slice_len = d.tile_i / S;
+    sc->grid = int(pairs * S);
     sc->nblk = nblk;
-    sc->bstride = (long long)nb * n;
+    sc->bstride = (long long)nb * S * n;
     sc->d = &d;
+    sc->sym_split = S;
     return NBODY_OK;
   }
   const int n_it = (n + d.tile_i - 1) / d.tile_i;
@@ -127,6 +139,7 @@ int vjp_prepare(int law, int n, int tile, int jsplit, int sms, cudaStream_t s, V
   sc->nblk = nblk;
   sc->bstride = (long long)S * n;
   sc->d = &d;
+  sc->sym_split = 1;
   return NBODY_OK;
 }
 
@@ -148,10 +161,10 @@ int vjp_once(const float4 *pos, const float4 *prm, const float4 *lam, float4 *gr
     const unsigned pblocks = unsigned(((n + 1) / 2 + 255) / 256);
     if (sc.d->sym && ljc)
       interleave_ljc_vjp_pairs_blocked_kernel<<<pblocks, 256, 0, s>>>(pos, src, prm, sc.jp, n,
-                                                                      sc.slice_len);
+                                                                      sc.d->tile_i);
     else if (sc.d->sym)
       interleave_vjp_pairs_blocked_kernel<<<pblocks, 256, 0, s>>>(pos, src, sc.jp, n,
-                                                                  sc.slice_len);
+                                                                  sc.d->tile_i);
     else if (ljc)
       interleave_ljc_vjp_pairs_kernel<<<pblocks, 256, 0, s>>>(pos, src, prm, sc.jp, n);
     else
@@ -184,6 +197,8 @@ int vjp_once(const float4 *pos, const float4 *prm, const float4 *lam, float4 *gr
   f.stride = n;
   f.bstride = sc.bstride;
   f.slices = sc.slices;
+  f.sym_block = sc.d->sym ? sc.d->tile_i : 0;
+  f.sym_split = sc.sym_split;
   f.n = n;
   f.law = p.law;
   f.G = p.G;
@@ -280,7 +295,7 @@ int gaj_eval(const float4 *pos, const float4 *vel, float4 *acc, float4 *jerk, in
     const unsigned pblocks = unsigned(((n + 1) / 2 + 255) / 256);
     if (sc.d->sym)
       interleave_vjp_pairs_blocked_kernel<<<pblocks, 256, 0, s>>>(pos, vel, sc.jp, n,
-                                                                  sc.slice_len);
+                                                                  sc.d->tile_i);
     else
       interleave_vjp_pairs_kernel<<<pblocks, 256, 0, s>>>(pos, vel, sc.jp, n);
     NB_CUDA(cudaGetLastError());

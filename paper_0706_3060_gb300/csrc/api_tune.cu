@@ -106,7 +106,9 @@ int nbody_tune(int32_t table, const void *pos_m, const void *prm, int64_t n, flo
       if (js > 0 && int64_t(js) * tiles[t].jt > n) continue;  // slices shorter than a j-tile
       if (tiles[t].sym) {  // j-split = source parts per block; skip what the plan refuses
         if (!sym_fits(n, tiles[t].tile_i)) continue;
-        if (js > 0) {  // only splits the plan takes as given (not rounded or refused)
+        if (js > 0 && table == kTableVjpGrav) {  // the VJP plan takes powers of two
+          if ((js & (js - 1)) != 0 || js > std::min(8, tiles[t].tile_i / 64)) continue;
+        } else if (js > 0) {  // only splits the plan takes as given (not rounded or refused)
           Plan1 probe{};
           if (table >= kTableVjpGrav || table == kTableBatched ||
               plan_single(table, n, t, js, sms, &probe, true) != NBODY_OK ||

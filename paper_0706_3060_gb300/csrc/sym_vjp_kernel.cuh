@@ -92,32 +92,42 @@ __global__ void __launch_bounds__(NT, MINB) sym_gvjp_kernel(const VjpArgs a) {
   float4 *s3 = s2 + P;                                 // (lz lz 0 0)
   float *jsum = reinterpret_cast<float *>(smem_raw + T::kSrcBytes);
   __shared__ __align__(8) uint64_t bar;
+  __shared__ int part_meta[3];  // (parts per block, part, first pair), read after the loop
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = a.n;
-  const int nb = a.slices;
+  // source split as in sym_kernel.cuh: a.slice_len sources per part
+  const int nparts = B / a.slice_len;
+  const int nb = a.slices / nparts;
+  const int t = int(blockIdx.x) / nparts, sp = int(blockIdx.x) - t * nparts;
   int bi, bj;
-  sym_tile_of(blockIdx.x, nb, bi, bj);
+  sym_tile_of(t, nb, bi, bj);
   if (bj >= nb) {  // outside the triangle: a launch-shape error
     if (tid == 0) set_error(a.err, kDevBadItem);
     return;
   }
   const int j0 = bj * B;
   const int nsrc = min(B, n - j0);
-  const int npairs = (nsrc + 1) >> 1;
+  const int p0 = sp * (P / nparts);  // first source pair of this part
+  const int npairs = max(0, min(P / nparts, ((nsrc + 1) >> 1) - p0));
   if (tid == 0) {
     mbar_init(&bar, 1);
     mbar_fence_init();
+    part_meta[0] = nparts;
+    part_meta[1] = sp;
+    part_meta[2] = p0;
   }
   __syncthreads();
   if (tid == 0) {
     const uint32_t bytes = uint32_t(npairs) * 16u;
-    const float4 *blk = a.jpair + size_t(bj) * 2 * B;  // four arrays of P float4 per block
+    const float4 *blk = a.jpair + size_t(bj) * 2 * B + p0;  // four arrays of P per block
     mbar_arrive_expect_tx(&bar, 4 * bytes);
-    tma_load_1d(s0, blk, bytes, &bar);
-    tma_load_1d(s1, blk + P, bytes, &bar);
-    tma_load_1d(s2, blk + 2 * P, bytes, &bar);
-    tma_load_1d(s3, blk + 3 * P, bytes, &bar);
+    if (npairs > 0) {
+      tma_load_1d(s0, blk, bytes, &bar);
+      tma_load_1d(s1, blk + P, bytes, &bar);
+      tma_load_1d(s2, blk + 2 * P, bytes, &bar);
+      tma_load_1d(s3, blk + 3 * P, bytes, &bar);
+    }
   }
   const bool diag = (bi == bj);
   if (!diag)
@@ -154,7 +164,7 @@ __global__ void __launch_bounds__(NT, MINB) sym_gvjp_kernel(const VjpArgs a) {
     for (int pp = 0; pp < npairs; ++pp) {
       const float4 A = s0[pp], Bq = s1[pp], C = s2[pp], D = s3[pp];
       const float2 nM = make_float2(-Bq.z, -Bq.w);
-      const int jg = j0 + 2 * pp;
+      const int jg = j0 + 2 * (p0 + pp);
 #pragma unroll
       for (int r = 0; r < I; ++r)
         sym_gvjp_pair2<false, true>(make_float2(A.x, A.y), make_float2(A.z, A.w),
@@ -197,7 +207,8 @@ __global__ void __launch_bounds__(NT, MINB) sym_gvjp_kernel(const VjpArgs a) {
     }
   }
 
-  const long long ibase = (long long)bj * a.stride;
+  const int np_ = part_meta[0], s_ = part_meta[1], p0_ = part_meta[2];
+  const long long ibase = (long long)(bj * np_ + s_) * a.stride;
 #pragma unroll
   for (int r = 0; r < I; ++r)
     if (ig[r] >= 0)
@@ -205,8 +216,9 @@ __global__ void __launch_bounds__(NT, MINB) sym_gvjp_kernel(const VjpArgs a) {
                                              az[r].x + az[r].y, aw[r].x + aw[r].y);
   if (diag) return;
   __syncthreads();
-  const long long jbase = (long long)bi * a.stride + j0;
-  for (int q = tid; q < nsrc; q += NT) {
+  const long long jbase = (long long)(bi * np_ + s_) * a.stride + j0 + 2 * p0_;
+  const int nq = min(2 * npairs, nsrc - 2 * p0_);
+  for (int q = tid; q < nq; q += NT) {
     const int pp = q >> 1, h = q & 1;
     float vx = 0.0f, vy = 0.0f, vz = 0.0f, vw = 0.0f;
     for (int w = 0; w < T::kWarps; ++w) {

@@ -28,6 +28,11 @@ struct VjpFinalizeArgs {
   double *type_part;  // [gridDim.x][8] or null
   float4 *lam_v;      // if non-null: lam_v += dt_next * grad_x afterwards
   float dt_next;
+  // symmetric gravity VJP with the source split (block size, parts per block):
+  // the slots a particle receives are its own part's slot of each lower block and
+  // every slot from its own block on (sym_split <= 1: every slot)
+  int sym_block;
+  int sym_split;
 };
 
 __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs f) {
@@ -36,14 +41,16 @@ __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs
   if (i < f.n) {
     // part_lo == nullptr: partials without low parts (Newton-symmetric gravity tiles)
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 hA = f.part_hi[i], oA = f.part_lo ? f.part_lo[i] : zero;
-    float4 hB = make_float4(0.f, 0.f, 0.f, 0.f), oB = hB;
+    float4 hA = zero, oA = zero, hB = zero, oB = zero;
     const bool lj = (f.law == NBODY_LAW_LJC || f.law == NBODY_LAW_LJC_LINEAR);
-    if (lj) {
-      hB = f.part_hi[f.bstride + i];
-      oB = f.part_lo ? f.part_lo[f.bstride + i] : zero;
-    }
-    for (int k = 1; k < f.slices; ++k) {
+    const int sp = f.sym_split > 1 ? f.sym_split : 1;
+    const int own_b = sp > 1 ? i / f.sym_block : 0;
+    const int own_s = sp > 1 ? ((i - own_b * f.sym_block) >> 1) / (f.sym_block / 2 / sp) : 0;
+    const int below = own_b;        // slots own_s, own_s + sp, ... below the own block
+    const int k_all = own_b * sp;   // every slot from here on
+    const int count = below + (f.slices - k_all);
+    for (int c = 0; c < count; ++c) {
+      const int k = c < below ? c * sp + own_s : k_all + (c - below);
       const long long o = (long long)k * f.stride + i;
       float4 h = f.part_hi[o], l = f.part_lo ? f.part_lo[o] : zero;
       comp_add(hA.x, oA.x, h.x);

@@ -482,3 +482,55 @@ def test_symmetric_split_leapfrog():
         nb.step(pos, vel, acc, dt=1e-3, nsteps=10, eps=eps, tile=tile, jsplit=4)
         ex = traj_errors(pos[:, :3].cpu().numpy(), xs[-1])
         assert ex[0] <= 1e-6 and ex[1] <= 1e-5, (tile, ex)
+
+
+@pytest.mark.parametrize("n", [3, 700, 1025, 3001])
+@pytest.mark.parametrize("jsplit", [2, 4])
+def test_symmetric_vjp_source_split(n, jsplit):
+    """The gravity VJP with each block's sources cut into parts (one CTA each, the
+    finalize walking the slots a particle receives), every symmetric VJP tile."""
+    nb = lib()
+    g = workloads.plummer(n, seed=1500 + n, eps=0.01)
+    pos, _ = grav_tensors(g)
+    eps = float(np.float32(g.eps))
+    lam = np.random.default_rng(n).standard_normal((n, 4)).astype(np.float32)
+    x, _, m = g.f32_as_f64()
+    rg, rm = oracle.grav_vjp(x, m, lam[:, :3].astype(np.float64), eps=eps)
+    for tile in _sym_vjp_tiles():
+        lt = torch.from_numpy(lam).to(dev())
+        gx, gm, _ = nb.adjoint(pos, lt, eps=eps, tile=tile, jsplit=jsplit)
+        gx2, gm2, _ = nb.adjoint(pos, lt, eps=eps, tile=tile, jsplit=jsplit)
+        assert torch.equal(gx, gx2) and torch.equal(gm, gm2)
+        assert _rel(gx[:, :3].cpu().numpy(), rg) <= 2e-5, (tile, jsplit, n)
+        assert _rel(gm.cpu().numpy(), rm) <= 2e-5, (tile, jsplit, n)
+
+
+def test_symmetric_vjp_split_in_reverse_leapfrog():
+    """The reverse leapfrog with a split symmetric VJP installed as the tuned entry."""
+    nb = lib()
+    from paper_0706_3060_gb300.autograd import leapfrog
+    g = workloads.plummer(1024, seed=4, eps=0.01)
+    eps = float(np.float32(g.eps))
+    target = workloads.perturbed_target(g.f32_as_f64()[0], seed=4)
+    x, v, m = g.f32_as_f64()
+    sysm = oracle.GravSystem(m, eps=eps)
+    xs, _ = oracle.leapfrog(sysm, x, v, 1e-4, 60, store=True)
+    ref = oracle.adjoint_leapfrog(sysm, x, v, 1e-4, 60, oracle.target_loss_grad(xs[-1], target),
+                                  xs=xs)
+    old_v = nb.get_config(nb.TABLE_VJP_GRAV, 1024)
+    try:
+        nb.set_tuned(nb.TABLE_VJP_GRAV, 1024, _sym_vjp_tiles()[0], 2)
+        xf, vf, mf = g.f32()
+        d = dev()
+        x0 = torch.from_numpy(xf).to(d).requires_grad_(True)
+        v0 = torch.from_numpy(vf).to(d).requires_grad_(True)
+        m0 = torch.from_numpy(mf).to(d).requires_grad_(True)
+        xT, _ = leapfrog(x0, v0, m0, dt=1e-4, nsteps=60, k=20, eps=eps)
+        tgt = torch.from_numpy(target.astype(np.float32)).to(d)
+        (((xT - tgt) ** 2).sum() / 1024).backward()
+        nb.sync_check()
+        assert _rel(x0.grad.cpu().numpy(), ref["x0"]) <= 1e-4
+        assert _rel(v0.grad.cpu().numpy(), ref["v0"]) <= 1e-4
+        assert _rel(m0.grad.cpu().numpy(), ref["m"]) <= 1e-3
+    finally:
+        nb.set_tuned(nb.TABLE_VJP_GRAV, 1024, *old_v)
