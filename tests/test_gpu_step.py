@@ -47,6 +47,32 @@ def test_plummer_1024_ten_steps():
         np.testing.assert_allclose(row[5:8], ref["L"], atol=1e-6)
 
 
+def test_diagnostics_with_momentum_and_spin():
+    """The FP64 diagnostics on a system whose momentum and angular momentum are far
+    from zero: unequal masses, a bulk velocity and a rigid rotation added to a
+    Plummer sphere, so that P and L are O(0.1-1) and a dropped mass factor, a
+    wrong sum or a swapped cross product would show."""
+    nb = lib()
+    n = 2000
+    g = workloads.plummer(n, seed=21, eps=0.01)
+    rng = np.random.default_rng(21)
+    g.m = g.m * rng.uniform(0.2, 1.8, n)
+    omega = np.array([0.1, -0.2, 0.5])
+    g.v = g.v + np.array([0.3, -0.2, 0.1]) + np.cross(omega, g.x)
+    pos, vel = grav_tensors(g)
+    acc = torch.empty_like(pos)
+    diag = nb.step(pos, vel, acc, dt=1e-3, nsteps=10, eps=float(np.float32(g.eps)),
+                   report_every=5).cpu().numpy()
+    sysm, xs, vs = _grav_ref_traj(g, 1e-3, 10)
+    for row, k in zip(diag, (0, 5, 10)):
+        ref = oracle.diagnostics(sysm, xs[k], vs[k])
+        assert np.linalg.norm(ref["P"]) > 0.1 and np.linalg.norm(ref["L"]) > 0.01
+        np.testing.assert_allclose(row[2:5], ref["P"], rtol=1e-6)
+        np.testing.assert_allclose(row[5:8], ref["L"], rtol=1e-5)
+        assert abs(row[0] - ref["K"]) <= 1e-6 * abs(ref["K"])
+        assert abs(row[1] - ref["U"]) <= 1e-5 * abs(ref["U"])
+
+
 def test_resume_and_acc_valid_equivalence():
     """2 x 5 steps (second call reusing acc) is bitwise equal to 10 steps."""
     nb = lib()

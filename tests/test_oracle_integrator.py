@@ -69,6 +69,58 @@ def test_time_reversibility_and_momentum():
     np.testing.assert_allclose(P1, P0, atol=1e-15)
 
 
+def test_diagnostics_hand_values():
+    """K, P and L of two particles worked by hand (distinct masses, motion in
+    different planes), so that a swapped cross product, a dropped mass or a
+    missing factor 1/2 each change a printed value:
+      m1 = 3 at (1, 0, 0) moving (0, 2, 0):  m x x v = 3 (0, 0, 2) = (0, 0, 6)
+      m2 = 2 at (0, 0, 1) moving (1, 0, 0):  m x x v = 2 (0, 1, 0) = (0, 2, 0)
+    L = (0, 2, 6); P = (2, 6, 0); K = 3 * 4 / 2 + 2 * 1 / 2 = 7."""
+    x = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    v = np.array([[0.0, 2.0, 0.0], [1.0, 0.0, 0.0]])
+    sysm = oracle.GravSystem(np.array([3.0, 2.0]), eps=0.0)
+    d = oracle.diagnostics(sysm, x, v)
+    np.testing.assert_array_equal(d["L"], [0.0, 2.0, 6.0])
+    np.testing.assert_array_equal(d["P"], [2.0, 6.0, 0.0])
+    assert d["K"] == 7.0
+    # U of the pair: -G m1 m2 / r with r = sqrt(2)
+    assert abs(d["U"] + 6.0 / math.sqrt(2.0)) <= 1e-15 * 6.0
+
+
+def test_angular_momentum_of_a_circular_orbit():
+    """Two bodies on a circular orbit about their resting centre of mass, moving
+    counter-clockwise in the x-y plane: L = mu r v_rel along +z, with
+    mu = m1 m2 / (m1 + m2) and v_rel = sqrt(G (m1 + m2) / r) (closed form)."""
+    m1, m2, r, G = 0.7, 0.3, 2.0, 1.0
+    vrel = math.sqrt(G * (m1 + m2) / r)
+    rel_x, rel_v = np.array([r, 0.0, 0.0]), np.array([0.0, vrel, 0.0])
+    x = np.array([-m2 / (m1 + m2) * rel_x, m1 / (m1 + m2) * rel_x])
+    v = np.array([-m2 / (m1 + m2) * rel_v, m1 / (m1 + m2) * rel_v])
+    sysm = oracle.GravSystem(np.array([m1, m2]), G=G, eps=0.0)
+    L = oracle.diagnostics(sysm, x, v)["L"]
+    mu = m1 * m2 / (m1 + m2)
+    np.testing.assert_allclose(L, [0.0, 0.0, mu * r * vrel], rtol=1e-15, atol=1e-16)
+    # a quarter period later the orbit has turned; L is the same vector
+    period = 2.0 * math.pi * r / vrel
+    xs, vs = oracle.leapfrog(sysm, x, v, period / 4000.0, 1000)
+    np.testing.assert_allclose(oracle.diagnostics(sysm, xs, vs)["L"], L, rtol=1e-13,
+                               atol=1e-15)
+
+
+def test_leapfrog_conserves_angular_momentum_to_rounding():
+    """Central pair forces change sum m x x v by sum_(i<j) (x_i - x_j) x F_ij = 0 in a
+    kick, and a drift adds m v x v = 0, so KDK conserves L exactly up to FP64
+    rounding, while the energy (not conserved by KDK) drifts."""
+    g = workloads.plummer(64, seed=8)
+    sysm = oracle.GravSystem(g.m, eps=0.02)
+    L0 = oracle.diagnostics(sysm, g.x, g.v)["L"]
+    x, v = oracle.leapfrog(sysm, g.x, g.v, 1e-2, 200)
+    L1 = oracle.diagnostics(sysm, x, v)["L"]
+    scale = float(np.sum(g.m * np.linalg.norm(np.cross(g.x, g.v), axis=1)))
+    assert np.all(np.abs(L1 - L0) <= 1e-13 * scale), (L0, L1)
+    assert np.linalg.norm(L0) > 1e-3 * scale  # a rotating sample: the check is not 0 = 0
+
+
 def _kepler_hermite(dt, T, e=0.5):
     m1, m2 = 0.7, 0.3
     rp = 1.0 - e
