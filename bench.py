@@ -405,7 +405,8 @@ def extras(nb, torch, dev, g, eps):
     ex["force_err_max"] = float(e.max())
     ex["force_err_sample"] = "1024 seeded targets vs FP64 oracle"
     ex["default_mode"] = ("hardware rsqrt; Newton-symmetric tile: plain sums per block pair, "
-                          "per-block partials added with compensation")
+                          "per-block partials added with compensation (plain with "
+                          "NBODY_NO_COMPENSATION)")
     # the other precision modes on the same targets: Newton-refined rsqrt, plain
     # FP32 sums, 64-bit fixed-point sums (error and device time per evaluation)
     out_acc = torch.empty_like(pos)
@@ -863,35 +864,50 @@ def adjoint_extras(nb, torch, dev, n=16384, steps=200, k=20):
     return out
 
 
-def adjoint_accuracy(torch, dev, n=1024, steps=60, k=20, dt=1e-4):
-    """The same reverse leapfrog at a size the FP64 oracle finishes in a second:
-    relative L2 error of dL/dx0, dL/dv0, dL/dm against the oracle's adjoint."""
-    import oracle
+def adjoint_accuracy(torch, dev, n=16384, steps=200, k=20, dt=1e-4):
+    """The gradients of the timed adjoint configuration itself against the FP64
+    oracle's answer stored in tests/golden/adjoint_plummer16384.json (written by
+    make_adjoint_golden.py from oracle/ only): per-particle error of dL/dx0,
+    dL/dv0, dL/dm on its 256 seeded particles (denominator floored at 10% of the
+    RMS gradient), and the directional derivatives against central differences
+    (h = 1e-4) of the oracle loss."""
+    import json
     import workloads
     from paper_0706_3060_gb300.autograd import leapfrog
-    g = workloads.plummer(n, seed=4, eps=0.01)
+    path = os.path.join(ROOT, "tests", "golden", "adjoint_plummer16384.json")
+    golden = json.load(open(path))
+    assert (golden["n"], golden["steps"], golden["k"]) == (n, steps, k)
+    g = workloads.plummer(n, seed=4, eps=workloads.plummer_softening(n))
     x, v, m = g.f32()
-    xd, vd, md = g.f32_as_f64()
-    eps = float(np.float32(g.eps))
-    target = workloads.perturbed_target(xd, seed=4)
+    target = workloads.perturbed_target(x.astype(np.float64), seed=4).astype(np.float32)
     x0 = torch.from_numpy(x).to(dev).requires_grad_(True)
     v0 = torch.from_numpy(v).to(dev).requires_grad_(True)
     m0 = torch.from_numpy(m).to(dev).requires_grad_(True)
-    xT, _ = leapfrog(x0, v0, m0, dt=dt, nsteps=steps, k=k, eps=eps)
-    loss = ((xT - torch.from_numpy(target.astype(np.float32)).to(dev)) ** 2).sum() / n
+    xT, _ = leapfrog(x0, v0, m0, dt=dt, nsteps=steps, k=k, eps=float(np.float32(g.eps)))
+    loss = ((xT - torch.from_numpy(target).to(dev)) ** 2).sum() / n
     loss.backward()
-    sysm = oracle.GravSystem(md, eps=eps)
-    xs, _ = oracle.leapfrog(sysm, xd, vd, dt, steps, store=True)
-    ref = oracle.adjoint_leapfrog(sysm, xd, vd, dt, steps,
-                                  oracle.target_loss_grad(xs[-1], target), xs=xs)
-
-    def rel(got, want):
-        return float(np.linalg.norm(got.detach().cpu().numpy() - want) / np.linalg.norm(want))
-    return {"adjoint_grad_err_x0": rel(x0.grad, ref["x0"]),
-            "adjoint_grad_err_v0": rel(v0.grad, ref["v0"]),
-            "adjoint_grad_err_m": rel(m0.grad, ref["m"]),
-            "adjoint_grad_err_case": f"Plummer N = {n}, {steps} steps, k = {k}, vs FP64 oracle"}
-
+    got = {"x0": x0.grad.double().cpu().numpy(), "v0": v0.grad.double().cpu().numpy(),
+           "m": m0.grad.double().cpu().numpy()}
+    idx = np.asarray(golden["index"])
+    out = {"adjoint_grad_err_case": f"Plummer N = {n}, {steps} steps, k = {k}: 256 seeded "
+                                    "particles vs the stored FP64 oracle gradient "
+                                    "(per particle, floor 10% of RMS); directional "
+                                    "derivatives vs oracle central differences (h = 1e-4)",
+           "adjoint_loss_rel_err": abs(float(loss) - golden["loss"]) / golden["loss"]}
+    for key in ("x0", "v0", "m"):
+        ref = np.reshape(np.asarray(golden[key]), (len(idx), -1))
+        num = np.linalg.norm(np.reshape(got[key][idx], (len(idx), -1)) - ref, axis=1)
+        e = num / np.maximum(np.linalg.norm(ref, axis=1), 0.1 * golden["rms"][key])
+        out[f"adjoint_grad_err_{key}_rms"] = float(np.sqrt(np.mean(e * e)))
+        out[f"adjoint_grad_err_{key}_max"] = float(e.max())
+    dirs = workloads.random_directions((n, 7), len(golden["fd"]), seed=golden["dir_seed"])
+    worst = 0.0
+    for d, fd in zip(dirs, golden["fd"]):
+        an = float(np.sum(got["x0"] * d[:, :3]) + np.sum(got["v0"] * d[:, 3:6])
+                   + np.sum(got["m"] * d[:, 6] * 1e-2))
+        worst = max(worst, abs(an - fd["fd"]) / abs(fd["fd"]))
+    out["adjoint_fd_rel_err_max"] = worst
+    return out
 
 if __name__ == "__main__":
     main()

@@ -81,3 +81,64 @@ def traj_errors(got, ref):
     scale = np.sqrt(np.mean(np.sum(ref * ref, axis=1)))
     e = np.linalg.norm(got - ref, axis=1) / scale
     return float(np.sqrt(np.mean(e * e))), float(e.max())
+
+
+# Per-particle parity of VJPs and gradients. Each output is a sum over all
+# particles of terms of both signs (J^T lambda with a random lambda, the scalar
+# mass derivative), so at a few particles it cancels to nearly zero and a plain
+# relative error would divide an FP32 rounding error of the size of the terms by
+# a vanishing value. The denominator is floored at a fraction of the RMS output
+# magnitude: 1% for 3-vector outputs, 10% for scalar ones (which cancel more).
+FLOOR_VEC = 0.01
+FLOOR_SCALAR = 0.1
+GRAD_TOL_RMS = 1e-4  # reverse-leapfrog gradients: FP32 x_T against a 0.01 residual
+GRAD_TOL_MAX = 1e-3
+
+
+def floored_errors(got, ref, floor):
+    """|got_i - ref_i| / max(|ref_i|, floor * RMS_j |ref_j|), per particle (row)."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    n = ref.shape[0]
+    got = got.reshape(n, -1)
+    ref = ref.reshape(n, -1)
+    num = np.linalg.norm(got - ref, axis=1)
+    den = np.linalg.norm(ref, axis=1)
+    rms = float(np.sqrt(np.mean(den * den)))
+    return num / np.maximum(den, max(floor * rms, 1e-300))
+
+
+def assert_per_particle(got, ref, floor, rms=TOL_RMS, mx=TOL_MAX, what=""):
+    """RMS and max of floored_errors within (rms, mx); returns them."""
+    e = floored_errors(got, ref, floor)
+    r, m = float(np.sqrt(np.mean(e * e))), float(e.max())
+    assert r <= rms and m <= mx, (f"{what}: per-particle rms {r:.3e} (tol {rms}), "
+                                  f"max {m:.3e} (tol {mx}), floor {floor}")
+    return r, m
+
+
+def assert_vjp_close(gx, gm, rg, rm, what=""):
+    """A force VJP (J^T lambda, mass derivative) against the oracle, per particle."""
+    assert_per_particle(gx, rg, FLOOR_VEC, what=f"{what} J^T lambda")
+    assert_per_particle(gm, rm, FLOOR_SCALAR, what=f"{what} d/dm")
+
+
+def assert_types_close(got_t, rs, re, rtol=1e-4, what=""):
+    """Per-type sigma and epsilon derivatives (2 x ntypes), each entry against its
+    own magnitude floored at 10% of the RMS of its kind."""
+    got_t = np.asarray(got_t, dtype=np.float64)
+    nt = len(rs)
+    assert_per_particle(got_t[:nt], rs, FLOOR_SCALAR, rms=rtol, mx=rtol, what=f"{what} d/dsigma")
+    assert_per_particle(got_t[nt:], re, FLOOR_SCALAR, rms=rtol, mx=rtol, what=f"{what} d/deps")
+
+
+def assert_grads_close(gx, gv, gm, ref, what=""):
+    """Reverse-leapfrog gradients against the oracle's, per particle."""
+    assert_per_particle(gx, ref["x0"], FLOOR_SCALAR, GRAD_TOL_RMS, GRAD_TOL_MAX, f"{what} dL/dx0")
+    assert_per_particle(gv, ref["v0"], FLOOR_SCALAR, GRAD_TOL_RMS, GRAD_TOL_MAX, f"{what} dL/dv0")
+    assert_per_particle(gm, ref["m"], FLOOR_SCALAR, GRAD_TOL_RMS, GRAD_TOL_MAX, f"{what} dL/dm")
+
+
+def as_f32(a):
+    """FP64 copy of the FP32 rounding of `a` (what the GPU side was given)."""
+    return np.asarray(a, dtype=np.float32).astype(np.float64)

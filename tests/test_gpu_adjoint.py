@@ -3,21 +3,20 @@ mass and per-type sigma/epsilon derivatives) against the FP64 oracle's
 block-by-block Jacobian transpose, and the checkpointed reverse leapfrog
 (torch.autograd.Function) against the oracle's reverse leapfrog and against
 central finite differences of the oracle's FP64 loss."""
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import workloads
-from gpu_util import dev, grav_tensors, lib, ljc_tensors, oracle_ljc_system
+from gpu_util import (FLOOR_SCALAR, GRAD_TOL_MAX, GRAD_TOL_RMS, as_f32, assert_grads_close,
+                      assert_per_particle, assert_types_close, assert_vjp_close, dev,
+                      grav_tensors, lib, ljc_tensors, oracle_ljc_system, traj_errors)
 
 pytestmark = pytest.mark.gpu
-
-
-def _rel(got, ref):
-    got = np.asarray(got, np.float64)
-    ref = np.asarray(ref, np.float64)
-    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
 
 
 @pytest.mark.parametrize("n", [3, 257, 1000, 9000, 9001])
@@ -30,8 +29,7 @@ def test_grav_vjp(n):
                            alpha=1.0)
     x, _, m = g.f32_as_f64()
     rg, rm = oracle.grav_vjp(x, m, lam[:, :3].astype(np.float64), eps=float(np.float32(g.eps)))
-    assert _rel(gx[:, :3].cpu().numpy(), rg) <= 2e-5
-    assert _rel(gm.cpu().numpy(), rm) <= 2e-5
+    assert_vjp_close(gx[:, :3].cpu().numpy(), gm.cpu().numpy(), rg, rm, what=f"n={n}")
 
 
 @pytest.mark.parametrize("tile", range(17))
@@ -48,8 +46,7 @@ def test_grav_vjp_every_tile(tile, jsplit):
                            tile=tile, jsplit=jsplit)
     x, _, m = g.f32_as_f64()
     rg, rm = oracle.grav_vjp(x, m, lam[:, :3].astype(np.float64), eps=float(np.float32(g.eps)))
-    assert _rel(gx[:, :3].cpu().numpy(), rg) <= 2e-5, tile
-    assert _rel(gm.cpu().numpy(), rm) <= 2e-5, tile
+    assert_vjp_close(gx[:, :3].cpu().numpy(), gm.cpu().numpy(), rg, rm, what=str(tile))
 
 
 @pytest.mark.parametrize("tile", range(12))
@@ -62,10 +59,9 @@ def test_ljc_vjp_every_tile(tile):
     gx, gm, gt = nb.adjoint(pos, torch.from_numpy(lam).to(dev()), prm, tile=tile)
     sysm, x, _ = oracle_ljc_system(s)
     rg, rm, rs, re = sysm.vjp(x, lam[:, :3].astype(np.float64))
-    assert _rel(gx[:, :3].cpu().numpy(), rg) <= 2e-5, tile
-    assert _rel(gm.cpu().numpy(), rm) <= 2e-5, tile
+    assert_vjp_close(gx[:, :3].cpu().numpy(), gm.cpu().numpy(), rg, rm, what=str(tile))
     got_t = gt.cpu().numpy()
-    assert _rel(got_t[:4], rs) <= 2e-5 and _rel(got_t[4:], re) <= 2e-5, tile
+    assert_types_close(got_t, rs, re, what=str(tile))
 
 
 def test_vjp_bad_tile_is_rejected():
@@ -99,14 +95,12 @@ def test_ljc_vjp(n):
     gx, gm, gt = nb.adjoint(pos, torch.from_numpy(lam).to(dev()), prm, alpha=1.0)
     sysm, x, _ = oracle_ljc_system(s)
     rg, rm, rs, re = sysm.vjp(x, lam[:, :3].astype(np.float64))
-    assert _rel(gx[:, :3].cpu().numpy(), rg) <= 2e-5
-    assert _rel(gm.cpu().numpy(), rm) <= 2e-5
+    assert_vjp_close(gx[:, :3].cpu().numpy(), gm.cpu().numpy(), rg, rm, what=f"n={n}")
     got_t = gt.cpu().numpy()
-    assert _rel(got_t[:4], rs) <= 2e-5
-    assert _rel(got_t[4:], re) <= 2e-5
+    assert_types_close(got_t, rs, re)
 
 
-def _grav_autograd_grads(g, dt, nsteps, k, target):
+def _grav_autograd_grads(g, dt, nsteps, k, target, want_xT=False):
     nb = lib()
     from paper_0706_3060_gb300.autograd import leapfrog
     x, v, m = g.f32()
@@ -119,7 +113,9 @@ def _grav_autograd_grads(g, dt, nsteps, k, target):
     loss = ((xT - tgt) ** 2).sum() / xT.shape[0]
     loss.backward()
     nb.sync_check()
-    return x0.grad.cpu().numpy(), v0.grad.cpu().numpy(), m0.grad.cpu().numpy(), float(loss.detach())
+    out = (x0.grad.cpu().numpy(), v0.grad.cpu().numpy(), m0.grad.cpu().numpy(),
+           float(loss.detach()))
+    return out + (xT.detach().double().cpu().numpy(),) if want_xT else out
 
 
 def test_reverse_leapfrog_vs_oracle_gradient():
@@ -130,11 +126,9 @@ def test_reverse_leapfrog_vs_oracle_gradient():
     x, v, m = g.f32_as_f64()
     sysm = oracle.GravSystem(m, eps=float(np.float32(g.eps)))
     xs, _ = oracle.leapfrog(sysm, x, v, 1e-4, 60, store=True)
-    ref = oracle.adjoint_leapfrog(sysm, x, v, 1e-4, 60, oracle.target_loss_grad(xs[-1], target),
+    ref = oracle.adjoint_leapfrog(sysm, x, v, 1e-4, 60, oracle.target_loss_grad(xs[-1], as_f32(target)),
                                   xs=xs)
-    assert _rel(gx, ref["x0"]) <= 1e-4
-    assert _rel(gv, ref["v0"]) <= 1e-4
-    assert _rel(gm, ref["m"]) <= 1e-3
+    assert_grads_close(gx, gv, gm, ref, what="")
 
 
 def test_reverse_leapfrog_checkpoint_invariance():
@@ -158,7 +152,7 @@ def test_reverse_leapfrog_vs_finite_differences():
 
     def loss(x0, v0, m0):
         xT, _ = oracle.leapfrog(oracle.GravSystem(m0, eps=eps), x0, v0, dt, T)
-        return oracle.target_loss(xT, target)
+        return oracle.target_loss(xT, as_f32(target))
 
     h = 1e-4
     for d in workloads.random_directions((256, 7), 4, seed=5):
@@ -188,13 +182,11 @@ def test_ljc_reverse_leapfrog_vs_oracle():
     loss.backward()
     sysm, xo, vo = oracle_ljc_system(s)
     xs, _ = oracle.leapfrog(sysm, xo, vo, dt, T, store=True)
-    ref = oracle.adjoint_leapfrog(sysm, xo, vo, dt, T, oracle.target_loss_grad(xs[-1], target),
+    ref = oracle.adjoint_leapfrog(sysm, xo, vo, dt, T, oracle.target_loss_grad(xs[-1], as_f32(target)),
                                   xs=xs)
-    assert _rel(x0.grad.cpu().numpy(), ref["x0"]) <= 1e-4
-    assert _rel(v0.grad.cpu().numpy(), ref["v0"]) <= 1e-4
-    assert _rel(m0.grad.cpu().numpy(), ref["m"]) <= 1e-3
-    assert _rel(sig.grad.cpu().numpy(), ref["sig_t"]) <= 1e-3
-    assert _rel(eps.grad.cpu().numpy(), ref["eps_t"]) <= 1e-3
+    assert_grads_close(x0.grad.cpu().numpy(), v0.grad.cpu().numpy(), m0.grad.cpu().numpy(), ref, what="")
+    assert_per_particle(sig.grad.cpu().numpy(), ref["sig_t"], FLOOR_SCALAR, 1e-3, 1e-3, "sig_t")
+    assert_per_particle(eps.grad.cpu().numpy(), ref["eps_t"], FLOOR_SCALAR, 1e-3, 1e-3, "eps_t")
 
 
 def test_adjoint_workload_size_one_chunk():
@@ -207,11 +199,81 @@ def test_adjoint_workload_size_one_chunk():
     x, v, m = g.f32_as_f64()
     sysm = oracle.GravSystem(m, eps=float(np.float32(g.eps)))
     xs, _ = oracle.leapfrog(sysm, x, v, 1e-4, 20, store=True)
-    ref = oracle.adjoint_leapfrog(sysm, x, v, 1e-4, 20, oracle.target_loss_grad(xs[-1], target),
+    ref = oracle.adjoint_leapfrog(sysm, x, v, 1e-4, 20, oracle.target_loss_grad(xs[-1], as_f32(target)),
                                   xs=xs)
-    assert _rel(gx, ref["x0"]) <= 1e-4
-    assert _rel(gv, ref["v0"]) <= 1e-4
-    assert _rel(gm, ref["m"]) <= 1e-3
+    assert_grads_close(gx, gv, gm, ref, what="")
+
+
+GOLDEN_ADJOINT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                              "adjoint_plummer16384.json")
+
+
+def _adjoint_workload():
+    n = 16384
+    g = workloads.plummer(n, seed=4, eps=workloads.plummer_softening(n))
+    target = workloads.perturbed_target(g.f32_as_f64()[0], seed=4)
+    return g, target
+
+
+def _fd_directions(n, golden):
+    d = workloads.random_directions((n, 7), len(golden["fd"]), seed=golden["dir_seed"])
+    return [np.concatenate([di[:, :6], di[:, 6:7] * 1e-2], axis=1) for di in d]
+
+
+def _check_fd(gx, gv, gm, golden):
+    """GPU gradient along each stored direction against central differences
+    (h = 1e-4) of the oracle's FP64 loss: within 1e-3 of the derivative plus 1e-6
+    of the gradient's norm (a unit direction can make the derivative itself small)."""
+    gnorm = float(np.sqrt(np.sum(gx * gx) + np.sum(gv * gv) + np.sum((gm * 1e-2) ** 2)))
+    for k, d in enumerate(_fd_directions(gx.shape[0], golden)):
+        an = float(np.sum(gx * d[:, :3]) + np.sum(gv * d[:, 3:6]) + np.sum(gm * d[:, 6]))
+        fd = golden["fd"][k]["fd"]
+        assert abs(fd - an) <= 1e-3 * abs(fd) + 1e-6 * gnorm, (k, fd, an, gnorm)
+
+
+def test_adjoint_workload_against_stored_oracle():
+    """The adjoint workload in the bench's configuration (Plummer N = 16384,
+    200 KDK steps at dt = 1e-4, checkpoints every 20, tuned tiles) against the
+    oracle's answer stored by tests/golden/make_adjoint_golden.py: the loss, the
+    gradient of 256 seeded particles per particle, and directional derivatives
+    against central differences of the oracle loss along 4 seeded directions."""
+    golden = json.load(open(GOLDEN_ADJOINT))
+    g, target = _adjoint_workload()
+    gx, gv, gm, loss = _grav_autograd_grads(g, golden["dt"], golden["steps"], golden["k"],
+                                            target)
+    assert abs(loss - golden["loss"]) <= 1e-5 * golden["loss"], (loss, golden["loss"])
+    idx = np.asarray(golden["index"])
+    ref = {"x0": np.asarray(golden["x0"]), "v0": np.asarray(golden["v0"]),
+           "m": np.asarray(golden["m"])}
+    # the floor of the per-particle metric comes from the full gradient's RMS
+    for key, got in (("x0", gx[idx]), ("v0", gv[idx]), ("m", gm[idx])):
+        num = np.linalg.norm(np.reshape(got, (len(idx), -1)) - np.reshape(ref[key], (len(idx), -1)),
+                             axis=1)
+        den = np.linalg.norm(np.reshape(ref[key], (len(idx), -1)), axis=1)
+        e = num / np.maximum(den, FLOOR_SCALAR * golden["rms"][key])
+        assert np.sqrt(np.mean(e * e)) <= GRAD_TOL_RMS and e.max() <= GRAD_TOL_MAX, (key, e.max())
+    _check_fd(gx, gv, gm, golden)
+
+
+@pytest.mark.slow
+def test_adjoint_workload_full_against_oracle():
+    """The same workload on every particle: the GPU's x_T against the oracle's
+    FP64 trajectory, and dL/dx0, dL/dv0, dL/dm against the oracle's reverse
+    leapfrog (every state stored, two VJPs per step) element by element. The
+    oracle sweep takes a few minutes on the host cores."""
+    golden = json.load(open(GOLDEN_ADJOINT))
+    g, target = _adjoint_workload()
+    T, dt, k = golden["steps"], golden["dt"], golden["k"]
+    gx, gv, gm, loss, xT = _grav_autograd_grads(g, dt, T, k, target, want_xT=True)
+    x, v, m = g.f32_as_f64()
+    sysm = oracle.GravSystem(m, eps=float(np.float32(g.eps)))
+    xs, _ = oracle.leapfrog(sysm, x, v, dt, T, store=True)
+    r, mx = traj_errors(xT, xs[-1])
+    assert r <= 1e-6 and mx <= 1e-5, (r, mx)
+    ref = oracle.adjoint_leapfrog(sysm, x, v, dt, T, oracle.target_loss_grad(xs[-1], as_f32(target)),
+                                  xs=xs)
+    assert_grads_close(gx, gv, gm, ref, what="full adjoint workload")
+    _check_fd(gx, gv, gm, golden)
 
 
 def test_adjoint_workload_translation_identities():
@@ -295,10 +357,9 @@ def test_ljc_linear_vjp_every_tile(tile, n):
     gx, gm, gt = nb.adjoint(pos, torch.from_numpy(lam).to(dev()), prm,
                             law=nb.LAW_LJC_LINEAR, tile=tile)
     rg, rm, rs, re = sysm.vjp(x, lam[:, :3].astype(np.float64))
-    assert _rel(gx[:, :3].cpu().numpy(), rg) <= 2e-5, tile
-    assert _rel(gm.cpu().numpy(), rm) <= 2e-5, tile
+    assert_vjp_close(gx[:, :3].cpu().numpy(), gm.cpu().numpy(), rg, rm, what=str(tile))
     got_t = gt.cpu().numpy()
-    assert _rel(got_t[:4], rs) <= 2e-5 and _rel(got_t[4:], re) <= 2e-5, tile
+    assert_types_close(got_t, rs, re, what=str(tile))
 
 
 def test_ljc_linear_reverse_leapfrog_vs_oracle():
@@ -322,10 +383,8 @@ def test_ljc_linear_reverse_leapfrog_vs_oracle():
     xo, vo, mo, qo, so, eo = s.f32_as_f64()
     sysm = oracle.LJCSystem(mo, qo, s.types, so, eo, 332.0637 / 4.0, linear=True)
     xs, _ = oracle.leapfrog(sysm, xo, vo, dt, T, store=True)
-    ref = oracle.adjoint_leapfrog(sysm, xo, vo, dt, T, oracle.target_loss_grad(xs[-1], target),
+    ref = oracle.adjoint_leapfrog(sysm, xo, vo, dt, T, oracle.target_loss_grad(xs[-1], as_f32(target)),
                                   xs=xs)
-    assert _rel(x0.grad.cpu().numpy(), ref["x0"]) <= 1e-4
-    assert _rel(v0.grad.cpu().numpy(), ref["v0"]) <= 1e-4
-    assert _rel(m0.grad.cpu().numpy(), ref["m"]) <= 1e-3
-    assert _rel(sig.grad.cpu().numpy(), ref["sig_t"]) <= 1e-3
-    assert _rel(eps.grad.cpu().numpy(), ref["eps_t"]) <= 1e-3
+    assert_grads_close(x0.grad.cpu().numpy(), v0.grad.cpu().numpy(), m0.grad.cpu().numpy(), ref, what="")
+    assert_per_particle(sig.grad.cpu().numpy(), ref["sig_t"], FLOOR_SCALAR, 1e-3, 1e-3, "sig_t")
+    assert_per_particle(eps.grad.cpu().numpy(), ref["eps_t"], FLOOR_SCALAR, 1e-3, 1e-3, "eps_t")
