@@ -2,7 +2,7 @@
 ``ncu -k regex:<kernel>``): each case builds its seeded inputs, runs ``--warmup``
 untimed calls and ``--iters`` more, then synchronizes.
 
-    python -m paper_0706_3060_gb300.cases grav262144 --warmup 1 --iters 2
+    python cases.py grav262144 --warmup 1 --iters 2
 """
 from __future__ import annotations
 
@@ -106,7 +106,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--iters", type=int, default=2)
     a = ap.parse_args()
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    root = os.path.dirname(os.path.abspath(__file__))
     if root not in sys.path:
         sys.path.insert(0, root)
     import torch

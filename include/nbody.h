@@ -80,10 +80,12 @@ enum {
     NBODY_COMPUTE_POT = 1u << 0,     /* also compute phi (acc[i].w)            */
     NBODY_PRECISE_RSQRT = 1u << 1,   /* one Newton step on the hardware rsqrt  */
     NBODY_NO_COMPENSATION = 1u << 2, /* plain FP32 sums (default: per-tile
-                                        TwoSum compensated sums); Newton-
-                                        symmetric tiles sum each block pair
-                                        plainly and always add the per-block
-                                        partials compensated, flag or not      */
+                                        TwoSum compensated sums, and the
+                                        per-slice or per-block partials added
+                                        with compensation); Newton-symmetric
+                                        tiles always sum within a block pair
+                                        plainly, and with this flag also add
+                                        their per-block partials plainly      */
     NBODY_ACC_VALID = 1u << 3,       /* nbody_step: acc already holds a(x) for
                                         the entry positions                    */
     NBODY_ACCUMULATE = 1u << 4,      /* nbody_adjoint: add into the outputs    */
@@ -120,8 +122,11 @@ const char *nbody_last_error(void);
 int nbody_release(void);
 
 /* Synchronize `stream`, then report (and clear) any error a kernel recorded
- * since the last check: NBODY_ETIMEOUT for a bounded wait that ran out,
- * NBODY_EINVAL for a work item that failed its bounds check. */
+ * since the last check on the current device, by any entry point (including
+ * nbody_forces_static): NBODY_ETIMEOUT for a bounded wait that ran out,
+ * NBODY_EINVAL for a work item that failed its bounds check. The device error
+ * word is a __device__ variable of the library, so recording and reading it
+ * allocates nothing. */
 int nbody_check(nbody_stream_t stream);
 
 /* Kernel timers. While enabled, every all-pairs kernel launch made outside
@@ -226,14 +231,19 @@ int nbody_forces_subset(const void *pos_m, const void *prm, const int32_t *idx,
  *   pos_m, prm, acc, n, params, stream : as in nbody_forces (device pointers
  *   only; no acc_lo; NBODY_COMPUTE_POT, NBODY_PRECISE_RSQRT and
  *   NBODY_NO_COMPENSATION are honoured).
- * n beyond what the scratch holds (about 699,000 particles) is rejected with
- * NBODY_EINVAL before any GPU work; large n may run with fewer j-slices than
- * nbody_forces would use. The first call on each device, with that device
- * current, looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture. All calls share the array, which
- * keeps the last call's contents; each call rewrites what it reads and clears
- * its error word, but calls whose GPU work overlaps (e.g. on two streams) race
- * on the array: serialize them. */
+ * Only one-sided tiles run here: an explicit Newton-symmetric tile
+ * (NBODY_TILE_SYMMETRIC) is refused with NBODY_EINVAL, and with tile = -1 a
+ * tuned symmetric entry is replaced by the law's default one-sided tile. n
+ * beyond what the scratch holds (about 699,000 particles for gravity) is
+ * rejected with NBODY_EINVAL before any GPU work; at large n the call runs with
+ * fewer j-slices than nbody_forces would use, so that the partial sums fit. The
+ * first call on each device, with that device current, looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture. All calls share the array, which keeps the last call's contents;
+ * each call rewrites what it reads, but calls whose GPU work overlaps (e.g. on
+ * two streams) race on the array: serialize them. A bounded wait that runs out
+ * in its kernels is recorded in the library's device error word (no allocation
+ * either) and reported by the next nbody_check, like any other call's. */
 int nbody_forces_static(const void *pos_m, const void *prm, void *acc, int64_t n,
                         const nbody_params *params, nbody_stream_t stream);
 

@@ -331,11 +331,11 @@ def get_config(law: int, n: int) -> tuple[int, int]:
 
 
 def workspace_size(n: int, *, law=LAW_GRAV, eps=0.0, tile=-1, jsplit=0, fixed=False,
-                   report_rows=0) -> int:
+                   compensated=True, report_rows=0) -> int:
     """Device scratch bytes a forces/step call with these settings requests from
     the library's per-stream workspace (nbody_workspace_size)."""
     b = ctypes.c_size_t()
-    p = params(law, 1.0, eps, tile=tile, jsplit=jsplit, fixed=fixed)
+    p = params(law, 1.0, eps, compensated=compensated, tile=tile, jsplit=jsplit, fixed=fixed)
     check(_lib().nbody_workspace_size(ctypes.byref(p), int(n), int(report_rows), ctypes.byref(b)),
           "nbody_workspace_size")
     return b.value

@@ -80,50 +80,74 @@ int check_ptr(const void *p, const char *name, bool required = true) {
   return NBODY_OK;
 }
 
+// Whether a symmetric gravity plan of this call may add its per-block partials
+// atomically in 64-bit fixed point: the scale needs eps > 0 (the bound on every
+// sum), and NBODY_NO_COMPENSATION asks for plain FP32 sums instead.
+bool atomic_ok(const nbody_params &p) {
+  if (p.law != NBODY_LAW_GRAV || !(p.eps2 > 0.0f)) return false;
+  return (p.flags & NBODY_FIXED_POINT) || !(p.flags & NBODY_NO_COMPENSATION);
+}
+
 // Scratch layout for one single-system evaluation.
 struct Scratch {
-  float *fscale;  // fixed-point scale (device word) and its inverse
+  float *fscale;  // fixed-point scale (device word) and its inverse: arena header
   double *finv;
+  unsigned *ticket;  // atomic plans: last-block ticket of the scale's mass sum (header)
+  double *msum;      // atomic plans: per-block |m| sums of the interleave launch
   float4 *jbuf;
   float4 *part_hi;
   float4 *part_lo;
+  long long *acc64;  // atomic plans: four int64 accumulators per particle
   double *diag_part;
   double *diag_rows;
 };
 
-// Bytes of the Scratch layout below (scale words, pair buffer, partials,
-// diagnostics). The symmetric tiles write no low parts and read their sources
-// in whole blocks (nb x B particles, the last block padded).
-size_t scratch_bytes(int law, int n, const Plan1 &plan, int diag_rows) {
-  const bool lo = !plan.tile->sym || plan.tile->fixed;  // fixed point: int64 (z, w) there
+// Byte sizes of the Scratch regions: scale words, pair buffer, partials (or the
+// atomic plan's accumulators), diagnostics. The symmetric tiles write no low
+// parts and read their sources in whole blocks (nb x B particles, the last block
+// padded).
+struct ScratchSizes {
+  size_t jb, part, lopart, dpart, drows, msum;
+  size_t body() const { return jb + part + lopart + dpart + drows + msum; }  // past the header
+  size_t total() const { return kArenaHeader + body(); }
+};
+
+ScratchSizes scratch_sizes(int law, int n, const Plan1 &plan, int diag_rows) {
+  ScratchSizes z{};
+  const bool lo = !plan.atomic && (!plan.tile->sym || plan.tile->fixed);  // FX: int64 (z, w)
   const int64_t jn = plan.tile->sym ? int64_t(plan.slices) * plan.slice_len : n;
-  const size_t part = round_up(size_t(plan.slices) * size_t(n) * sizeof(float4), 256);
+  z.part = plan.atomic ? round_up(size_t(4) * size_t(n) * sizeof(long long), 256)
+                       : round_up(size_t(plan.slices) * size_t(n) * sizeof(float4), 256);
+  z.lopart = lo ? z.part : 0;
   const int nblk = std::max(1, (n + kFinThreads - 1) / kFinThreads);
-  const size_t dpart = round_up(size_t(nblk) * kDiagFields * sizeof(double), 256);
-  const size_t drows = round_up(size_t(std::max(diag_rows, 1)) * kDiagFields * sizeof(double), 256);
-  return 256 + jbuf_bytes(law, jn) + (lo ? 2 : 1) * part + dpart + drows;
+  z.dpart = round_up(size_t(nblk) * kDiagFields * sizeof(double), 256);
+  z.drows = round_up(size_t(std::max(diag_rows, 1)) * kDiagFields * sizeof(double), 256);
+  z.jb = jbuf_bytes(law, jn);
+  z.msum = plan.atomic ? round_up(size_t((n + 511) / 512) * sizeof(double), 256) : 0;
+  return z;
+}
+
+size_t scratch_bytes(int law, int n, const Plan1 &plan, int diag_rows) {
+  return scratch_sizes(law, n, plan, diag_rows).total();
 }
 
 int get_scratch(cudaStream_t s, int law, int n, const Plan1 &plan, int diag_rows, Scratch *out) {
-  const bool lo = !plan.tile->sym || plan.tile->fixed;
-  const int64_t jn = plan.tile->sym ? int64_t(plan.slices) * plan.slice_len : n;
-  const size_t part = round_up(size_t(plan.slices) * size_t(n) * sizeof(float4), 256);
-  const int nblk = std::max(1, (n + kFinThreads - 1) / kFinThreads);
-  const size_t dpart = round_up(size_t(nblk) * kDiagFields * sizeof(double), 256);
-  const size_t jb = jbuf_bytes(law, jn);
-  const size_t lopart = lo ? part : 0;
+  const ScratchSizes z = scratch_sizes(law, n, plan, diag_rows);
   void *base = nullptr;
-  NB_TRY(workspace(s, scratch_bytes(law, n, plan, diag_rows), &base));
+  char *hdr = nullptr;
+  NB_TRY(workspace(s, z.body(), &base, &hdr));
+  out->finv = reinterpret_cast<double *>(hdr);
+  out->fscale = reinterpret_cast<float *>(hdr + 8);
+  out->ticket = reinterpret_cast<unsigned *>(hdr + 16);
   char *b = static_cast<char *>(base);
-  out->finv = reinterpret_cast<double *>(b);
-  out->fscale = reinterpret_cast<float *>(b + 8);
-  b += 256;
+  out->msum = plan.atomic ? reinterpret_cast<double *>(b + z.body() - z.msum) : nullptr;
   out->jbuf = reinterpret_cast<float4 *>(b);
-  b += jb;
-  out->part_hi = reinterpret_cast<float4 *>(b);
-  out->part_lo = lo ? reinterpret_cast<float4 *>(b + part) : nullptr;
-  out->diag_part = reinterpret_cast<double *>(b + part + lopart);
-  out->diag_rows = reinterpret_cast<double *>(b + part + lopart + dpart);
+  b += z.jb;
+  out->acc64 = plan.atomic ? reinterpret_cast<long long *>(b) : nullptr;
+  out->part_hi = plan.atomic ? nullptr : reinterpret_cast<float4 *>(b);
+  out->part_lo = z.lopart ? reinterpret_cast<float4 *>(b + z.part) : nullptr;
+  out->diag_part = reinterpret_cast<double *>(b + z.part + z.lopart);
+  out->diag_rows = reinterpret_cast<double *>(b + z.part + z.lopart + z.dpart);
   return NBODY_OK;
 }
 
@@ -131,28 +155,34 @@ int get_scratch(cudaStream_t s, int law, int n, const Plan1 &plan, int diag_rows
 int eval_and_finalize(const float4 *pos, const float4 *prm, const nbody_params &p, int n,
                       const Plan1 &plan, const Scratch &sc, int *err, bool pot,
                       FinalizeArgs f, cudaStream_t s, int *nblk) {
-  const bool fx = (p.flags & NBODY_FIXED_POINT) != 0;
+  const bool fx = (p.flags & NBODY_FIXED_POINT) != 0 || plan.atomic;
+  const AtomicPrep at{sc.acc64, sc.msum, sc.ticket, p.eps2, sc.fscale, sc.finv};
   NB_TRY(launch_forces(pos, prm, p.law, p.flags, p.eps2, n, plan, sc.part_hi, sc.part_lo,
-                       sc.jbuf, err, pot, s, nullptr, fx ? sc.fscale : nullptr));
+                       sc.jbuf, err, pot, s, nullptr,
+                       (fx && !plan.atomic) ? sc.fscale : nullptr,
+                       plan.atomic ? &at : nullptr));
   f.fx_inv = fx ? sc.finv : nullptr;
+  f.acc64 = sc.acc64;
   f.part_hi = sc.part_hi;
   f.part_lo = sc.part_lo;
   f.stride = n;
-  f.slices = plan.slices;
-  f.sym_block = plan.tile->sym ? plan.tile->tile_i : 0;
-  f.sym_split = plan.tile->sym ? plan.sym_split : 1;
+  f.slices = plan.atomic ? 1 : plan.slices;
+  f.sym_block = (plan.tile->sym && !plan.atomic) ? plan.tile->tile_i : 0;
+  f.sym_split = (plan.tile->sym && !plan.atomic) ? plan.sym_split : 1;
   f.sys_of = nullptr;
   f.sys = nullptr;
   f.n = n;
   f.law = p.law;
   f.G = p.G;
   f.diag_part = sc.diag_part;
+  f.plain = (p.flags & NBODY_NO_COMPENSATION) ? 1 : 0;
   return launch_finalize(f, s, nblk);
 }
 
-int prepare_fixed(const float4 *pos, int n, const nbody_params &p, const Scratch &sc,
-                  cudaStream_t s) {
-  if (!(p.flags & NBODY_FIXED_POINT)) return NBODY_OK;
+int prepare_fixed(const float4 *pos, int n, const nbody_params &p, const Plan1 &plan,
+                  const Scratch &sc, cudaStream_t s) {
+  // atomic plans form their scale inside the interleave launch
+  if (!(p.flags & NBODY_FIXED_POINT) || plan.atomic) return NBODY_OK;
   fixed_scale_kernel<<<1, 256, 0, s>>>(pos, n, p.eps2, sc.fscale, sc.finv);
   NB_CUDA(cudaGetLastError());
   return NBODY_OK;
@@ -161,10 +191,10 @@ int prepare_fixed(const float4 *pos, int n, const nbody_params &p, const Scratch
 int forces_device(const float4 *pos, const float4 *prm, float4 *acc, float4 *acc_lo, int n,
                   const nbody_params &p, int sms, cudaStream_t s) {
   Plan1 plan{};
-  NB_TRY(plan_single(table_of(p), n, p.tile, p.jsplit, sms, &plan, true));
+  NB_TRY(plan_single(table_of(p), n, p.tile, p.jsplit, sms, &plan, true, atomic_ok(p)));
   Scratch sc{};
   NB_TRY(get_scratch(s, p.law, n, plan, 0, &sc));
-  NB_TRY(prepare_fixed(pos, n, p, sc, s));
+  NB_TRY(prepare_fixed(pos, n, p, plan, sc, s));
   int *err = nullptr;
   NB_TRY(error_word(&err));
   FinalizeArgs f{};
@@ -180,11 +210,11 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
                 int nsteps, int report_every, double *diag_dev, float4 *trace, float4 *state_lo,
                 const nbody_params &p, int sms, cudaStream_t s) {
   Plan1 plan{};
-  NB_TRY(plan_single(table_of(p), n, p.tile, p.jsplit, sms, &plan, true));
+  NB_TRY(plan_single(table_of(p), n, p.tile, p.jsplit, sms, &plan, true, atomic_ok(p)));
   const int rows = report_every > 0 ? nsteps / report_every + 1 : 0;
   Scratch sc{};
   NB_TRY(get_scratch(s, p.law, n, plan, rows, &sc));
-  NB_TRY(prepare_fixed(pos, n, p, sc, s));
+  NB_TRY(prepare_fixed(pos, n, p, plan, sc, s));
   int *err = nullptr;
   NB_TRY(error_word(&err));
   auto report = [&](int step) { return report_every > 0 && step % report_every == 0; };
@@ -337,7 +367,8 @@ int nbody_workspace_size(const nbody_params *params, int64_t n, int32_t report_r
   int dev = 0, sms = 0;
   NB_TRY(check_device(&dev, &sms));
   Plan1 plan{};
-  NB_TRY(plan_single(table_of(*params), n, params->tile, params->jsplit, sms, &plan, true));
+  NB_TRY(plan_single(table_of(*params), n, params->tile, params->jsplit, sms, &plan, true,
+                     atomic_ok(*params)));
   *bytes = scratch_bytes(params->law, int(n), plan, report_rows);
   return NBODY_OK;
 }

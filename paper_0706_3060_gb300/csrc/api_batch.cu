@@ -229,6 +229,7 @@ int enqueue_run(nbody_batch_plan *p, float4 *pos, float4 *vel, float4 *acc, cons
     f.vel = vel;
     f.acc = acc;
     f.mode = mode;
+    f.plain = (p->flags & NBODY_NO_COMPENSATION) ? 1 : 0;
     return launch_finalize(f, s, nullptr);
   };
   if (!(flags & NBODY_ACC_VALID) || nsteps == 0) {

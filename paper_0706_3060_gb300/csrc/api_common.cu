@@ -13,6 +13,11 @@
 
 namespace nbody {
 
+// The device error word: one int per device in the library image itself (zero
+// when the module loads), so reporting a kernel's error never allocates. Kernels
+// record the first error with atomicCAS; sync_and_check reads and clears it.
+__device__ int g_dev_err_word;
+
 namespace {
 thread_local std::string t_err;
 
@@ -24,7 +29,7 @@ struct Arena {
 std::mutex g_mu;
 std::map<std::pair<int, cudaStream_t>, Arena> g_ws;
 std::map<std::pair<int, cudaStream_t>, Arena> g_stage;
-std::map<int, int *> g_err_word;
+std::map<int, int *> g_err_word;  // device -> address of g_dev_err_word there
 std::map<int, int> g_checked;  // device -> sms
 
 struct Tuned {
@@ -61,6 +66,9 @@ int grow(std::map<std::pair<int, cudaStream_t>, Arena> &tab, cudaStream_t s, siz
                            cudaGetErrorString(e));
     }
     a.cap = want;
+    // a workspace arena's header holds per-call words (the fixed-point scale and
+    // the ticket of its last-block sum), which must start at zero
+    NB_CUDA(cudaMemsetAsync(a.ptr, 0, kArenaHeader, s));
   }
   *out = a.ptr;
   return NBODY_OK;
@@ -126,7 +134,13 @@ int is_host_pointer(const void *p) {
   return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 0 : 1;
 }
 
-int workspace(cudaStream_t s, size_t bytes, void **out) { return grow(g_ws, s, bytes, out); }
+int workspace(cudaStream_t s, size_t bytes, void **out, char **header) {
+  void *p = nullptr;
+  NB_TRY(grow(g_ws, s, bytes + kArenaHeader, &p));
+  *out = static_cast<char *>(p) + kArenaHeader;
+  if (header) *header = static_cast<char *>(p);
+  return NBODY_OK;
+}
 int staging(cudaStream_t s, size_t bytes, void **out) { return grow(g_stage, s, bytes, out); }
 
 int error_word(int **out) {
@@ -135,11 +149,9 @@ int error_word(int **out) {
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_err_word.find(dev);
   if (it == g_err_word.end()) {
-    int *p = nullptr;
-    NB_CUDA(cudaMalloc(&p, sizeof(int)));
-    NB_CUDA(cudaMemset(p, 0, sizeof(int)));
-    NB_CUDA(cudaDeviceSynchronize());
-    it = g_err_word.emplace(dev, p).first;
+    void *p = nullptr;
+    NB_CUDA(cudaGetSymbolAddress(&p, g_dev_err_word));
+    it = g_err_word.emplace(dev, static_cast<int *>(p)).first;
   }
   *out = it->second;
   return NBODY_OK;
@@ -168,8 +180,6 @@ void release_all() {
       if (kv.second.ptr) cudaFree(kv.second.ptr);
     tab->clear();
   }
-  for (auto &kv : g_err_word) cudaFree(kv.second);
-  g_err_word.clear();
 }
 
 namespace {
@@ -344,12 +354,16 @@ bool sym_fits(int64_t n, int block) {
   return nb * (nb + 1) / 2 <= 0x7fffffffLL && double(nb) * double(n) * 16.0 <= sym_part_cap();
 }
 
-int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out, bool allow_sym) {
-  return plan_targets(law, n, n, tile, jsplit, sms, out, allow_sym);
+bool sym_atomic_law(int law) { return law == NBODY_LAW_GRAV || law == kTableGravFixed; }
+
+int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out, bool allow_sym,
+                bool atomic_ok) {
+  return plan_targets(law, n, n, tile, jsplit, sms, out, allow_sym, atomic_ok);
 }
 
 int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms, Plan1 *out,
-                 bool allow_sym) {
+                 bool allow_sym, bool atomic_ok) {
+  out->atomic = false;
   if (law < 0 || law >= kTableVjpGrav)
     return set_error_msg(NBODY_EINVAL, "tile table %d is not a force table", law);
   int count = 0;
@@ -369,7 +383,10 @@ int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms,
   const TileDesc &d = tiles[tile];
   if (d.sym) {  // one CTA per block pair and source part, one partial slot per block and part
     const long long nb = (n + d.tile_i - 1) / d.tile_i;
-    if (!sym_fits(n, d.tile_i)) {
+    // atomic accumulation needs no partial slots: only the grid limit applies
+    const bool atomic = atomic_ok && sym_atomic_law(law);
+    const bool fits = atomic ? nb * (nb + 1) / 2 <= 0x7fffffffLL : sym_fits(n, d.tile_i);
+    if (!fits) {
       if (!tuned)
         return set_error_msg(NBODY_EINVAL, "n = %lld too large for symmetric tile %d",
                              (long long)n, tile);
@@ -385,9 +402,11 @@ int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms,
                               : 1;
     int S = 1;
     while (jsplit > 0 && S * 2 <= std::min(jsplit, max_split)) S *= 2;
-    if (pairs * S > 0x7fffffffLL || double(nb) * S * double(n) * 16.0 > sym_part_cap())
+    if (pairs * S > 0x7fffffffLL ||
+        (!atomic && double(nb) * S * double(n) * 16.0 > sym_part_cap()))
       return set_error_msg(NBODY_EINVAL, "n = %lld too large for symmetric tile %d split %d",
                            (long long)n, tile, S);
+    out->atomic = atomic;
     out->tile = &d;
     out->slices = int(nb * S);
     out->slice_len = d.tile_i / S;
@@ -446,15 +465,64 @@ __global__ void interleave_pairs_kernel(const float4 *pos, float4 *jp, int n) {
 // (x0, x1, y0, y1) of block b, then their (z0, z1, m0, m1), so that lanes reading
 // consecutive pairs read consecutive 16-byte words. Pairs past n are not written
 // (the kernel copies only the block's own pairs).
-__global__ void interleave_pairs_blocked_kernel(const float4 *pos, float4 *jp, int n, int B) {
+// With at.acc64 (atomic plans) the kernel also zeroes the accumulators of its
+// particles and forms the fixed-point scale without a launch of its own: every
+// block sums |m| of its particles in FP64 in a fixed order, and the block that
+// finishes last (atomicInc ticket, which wraps back to zero) adds the block sums
+// in index order and writes the scale -- the same bits whichever block is last.
+__global__ void __launch_bounds__(256) interleave_pairs_blocked_kernel(const float4 *pos,
+                                                                       float4 *jp, int n, int B,
+                                                                       AtomicPrep at) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (2 * p >= n) return;
-  const float4 a = pos[2 * p];
-  const float4 b = (2 * p + 1 < n) ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
-  const int blk = (2 * p) / B, pp = p - blk * (B / 2);
-  const long long base = (long long)blk * B;
-  jp[base + pp] = make_float4(a.x, b.x, a.y, b.y);
-  jp[base + B / 2 + pp] = make_float4(a.z, b.z, a.w, b.w);
+  double am = 0.0;
+  if (2 * p < n) {
+    const float4 a = pos[2 * p];
+    const float4 b =
+        (2 * p + 1 < n) ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+    const int blk = (2 * p) / B, pp = p - blk * (B / 2);
+    const long long base = (long long)blk * B;
+    jp[base + pp] = make_float4(a.x, b.x, a.y, b.y);
+    jp[base + B / 2 + pp] = make_float4(a.z, b.z, a.w, b.w);
+    if (at.acc64) {
+      am = fabs(double(a.w)) + fabs(double(b.w));
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        at.acc64[(long long)c * n + 2 * p] = 0;
+        if (2 * p + 1 < n) at.acc64[(long long)c * n + 2 * p + 1] = 0;
+      }
+    }
+  }
+  if (!at.acc64) return;  // the same for every thread of the launch
+  __shared__ double red[8];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) am += __shfl_down_sync(0xffffffffu, am, off);
+  if (lane == 0) red[warp] = am;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bs = 0.0;
+    for (int w = 0; w < 8; ++w) bs += red[w];
+    at.msum[blockIdx.x] = bs;
+    __threadfence();  // the block sum is visible before the ticket is taken
+    last = atomicInc(at.ticket, gridDim.x - 1) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v = 0.0;
+  for (int k = threadIdx.x; k < int(gridDim.x); k += 256)
+    v += reinterpret_cast<volatile double *>(at.msum)[k];
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double M = 0.0;
+    for (int w = 0; w < 8; ++w) M += red[w];
+    fixed_scale_of(M, at.eps2, at.scale, at.inv);
+  }
 }
 
 // LJC sources of the symmetric tiles, block by block (B particles, 3B/2 float4
@@ -499,8 +567,13 @@ size_t jbuf_bytes(int law, int64_t n) {
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
                   int *err, bool pot, cudaStream_t s, const Targets *tg,
-                  const float *fscale) {
-  if (p.tile->fixed != (fscale != nullptr))
+                  const float *fscale, const AtomicPrep *at) {
+  const bool atomic = at && at->acc64;
+  if (p.atomic != atomic || (atomic && (law != NBODY_LAW_GRAV || tg || !at->msum ||
+                                        !at->ticket || !at->scale || !at->inv)))
+    return set_error_msg(NBODY_EINVAL, "atomic plan and accumulators must come together");
+  if (atomic) fscale = at->scale;
+  if ((p.tile->fixed || p.atomic) != (fscale != nullptr))
     return set_error_msg(NBODY_EINVAL, "fixed-point tile and scale must come together");
   if (p.tile->packed) {
     if (!jbuf) return set_error_msg(NBODY_EINVAL, "packed tile without pair buffer");
@@ -511,8 +584,8 @@ int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags,
     else if (law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR)
       interleave_ljc_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, prm, jbuf, n);
     else if (p.tile->sym)
-      interleave_pairs_blocked_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, jbuf, n,
-                                                                       p.tile->tile_i);
+      interleave_pairs_blocked_kernel<<<(np + 255) / 256, 256, 0, s>>>(
+          pos, jbuf, n, p.tile->tile_i, atomic ? *at : AtomicPrep{});
     else
       interleave_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, jbuf, n);
     NB_CUDA(cudaGetLastError());
@@ -538,7 +611,7 @@ int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags,
   a.counter = nullptr;
   a.comp = (flags & NBODY_NO_COMPENSATION) ? 0 : 1;
   a.fscale = fscale;
-  (void)law;
+  a.acc64 = atomic ? at->acc64 : nullptr;
   const TimerMark tm = timer_begin(0, s);
   cudaError_t e = p.tile->launch(a, p.grid, pot, (flags & NBODY_PRECISE_RSQRT) != 0, s);
   timer_end(tm, s);

@@ -57,9 +57,14 @@ int is_host_pointer(const void *p);
 
 // Scratch owned by the library, one arena per (device, stream). The pointer
 // stays valid until the next call on the same (device, stream) asks for more.
-int workspace(cudaStream_t s, size_t bytes, void **out);
+// Each workspace arena starts with a header of kArenaHeader bytes for per-call
+// device words (zeroed when the arena is allocated; no layout overlaps it):
+// *out points past it, *header (if asked) at it.
+constexpr size_t kArenaHeader = 256;
+int workspace(cudaStream_t s, size_t bytes, void **out, char **header = nullptr);
 int staging(cudaStream_t s, size_t bytes, void **out);
-// Device error word of the current device (zeroed at creation).
+// Device error word of the current device (a __device__ int of the library, zero
+// when the module loads; no allocation).
 int error_word(int **out);
 // Synchronize `s`, then read and clear the error word.
 int sync_and_check(cudaStream_t s);
@@ -85,6 +90,9 @@ struct Plan1 {
   int n_itiles;
   int grid;
   int sym_split;   // symmetric tiles: source parts per block (1 otherwise)
+  bool atomic;     // symmetric gravity: per-block partials added with integer atomics
+                   // into one 64-bit fixed-point accumulator per particle (scratch
+                   // 32 bytes per particle) instead of one slot per block
 };
 // allow_sym: the Newton-symmetric tiles may be used (targets are the sources
 // and the partials have room for one slot per block); otherwise a tuned
@@ -95,11 +103,17 @@ int default_tile(int law, int64_t n);
 // nb (nb + 1) / 2 block pairs within the grid limit and nb x n float4 partials
 // (nb = ceil(n / block)) within an eighth of the device's memory, at most 16 GiB.
 bool sym_fits(int64_t n, int block);
+// atomic_ok: a symmetric gravity tile may accumulate atomically in fixed point
+// (the caller has eps > 0 and does not ask for plain FP32 sums); such a plan has
+// no partial-sum cap, only the grid limit on block pairs.
 int plan_single(int law, int64_t n, int tile, int jsplit, int sms, Plan1 *out,
-                bool allow_sym = false);
+                bool allow_sym = false, bool atomic_ok = false);
 // Same for n_t targets against n sources (i-tiles over targets, j-slices over sources).
 int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms, Plan1 *out,
-                 bool allow_sym = false);
+                 bool allow_sym = false, bool atomic_ok = false);
+// Whether the symmetric tiles of tile table `law` can accumulate atomically
+// (gravity and fixed-point gravity).
+bool sym_atomic_law(int law);
 
 // Optional separate targets for launch_forces (subset evaluations).
 struct Targets {
@@ -113,12 +127,25 @@ struct Targets {
 // Bytes of the pair-interleaved source copy that packed tiles read.
 size_t jbuf_bytes(int law, int64_t n);
 
+// Atomic plans (symmetric gravity in fixed point): the accumulators, which the
+// interleave launch before the force kernel zeroes, and the words from which that
+// launch forms the fixed-point scale (see interleave_pairs_blocked_kernel).
+struct AtomicPrep {
+  long long *acc64;  // 4 x n int64 accumulators (x, y, z, w)
+  double *msum;      // one FP64 |m| sum per interleave block: ceil(n / 512) doubles
+  unsigned *ticket;  // zero before the launch (the arena header); zero again after it
+  float eps2;
+  float *scale;      // out: 2^S, read by the force kernel
+  double *inv;       // out: 2^-S, read by the finalize kernel
+};
+
 // jbuf: scratch of jbuf_bytes(law, n) for the pair-interleaved sources of packed tiles.
-// fscale: device word with the fixed-point scale, required exactly for fixed tiles.
+// fscale: device word with the fixed-point scale, required exactly for fixed tiles
+// (atomic plans take theirs from `at`). at: required exactly for atomic plans.
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
                   int *err, bool pot, cudaStream_t s, const Targets *tg = nullptr,
-                  const float *fscale = nullptr);
+                  const float *fscale = nullptr, const AtomicPrep *at = nullptr);
 
 size_t round_up(size_t x, size_t a);
 

@@ -103,5 +103,6 @@ extern "C" int nbody_forces_subset(const void *pos_m, const void *prm, const int
   f.pos = tpos;
   f.acc = static_cast<float4 *>(acc);
   f.mode = kFinWriteAcc;
+  f.plain = (p.flags & NBODY_NO_COMPENSATION) ? 1 : 0;
   return launch_finalize(f, s, nullptr);
 }

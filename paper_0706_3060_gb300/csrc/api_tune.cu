@@ -105,13 +105,15 @@ int nbody_tune(int32_t table, const void *pos_m, const void *prm, int64_t n, flo
     for (int js : kSplits) {
       if (js > 0 && int64_t(js) * tiles[t].jt > n) continue;  // slices shorter than a j-tile
       if (tiles[t].sym) {  // j-split = source parts per block; skip what the plan refuses
-        if (!sym_fits(n, tiles[t].tile_i)) continue;
+        // softened gravity accumulates atomically (no partial-sum cap)
+        const bool atomic = sym_atomic_law(table) && eps2 > 0.0f;
+        if (!atomic && !sym_fits(n, tiles[t].tile_i)) continue;
         if (js > 0 && table == kTableVjpGrav) {  // the VJP plan takes powers of two
           if ((js & (js - 1)) != 0 || js > std::min(8, tiles[t].tile_i / 64)) continue;
         } else if (js > 0) {  // only splits the plan takes as given (not rounded or refused)
           Plan1 probe{};
           if (table >= kTableVjpGrav || table == kTableBatched ||
-              plan_single(table, n, t, js, sms, &probe, true) != NBODY_OK ||
+              plan_single(table, n, t, js, sms, &probe, true, atomic) != NBODY_OK ||
               probe.sym_split != js) {
             clear_error();
             continue;

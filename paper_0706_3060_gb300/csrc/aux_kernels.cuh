@@ -75,6 +75,13 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
       if (f.fx_inv) {
         // 64-bit fixed-point partials: exact integer sum, one rounding at the end
         long long sx = 0, sy = 0, sz = 0, sw = 0;
+        if (f.acc64) {  // already summed by the force kernel's integer atomics
+          const long long st = f.stride;
+          sx = f.acc64[i];
+          sy = f.acc64[st + i];
+          sz = f.acc64[2 * st + i];
+          sw = f.acc64[3 * st + i];
+        }
         auto take = [&](int k) {
           const long long *ph = reinterpret_cast<const long long *>(f.part_hi) +
                                 2 * ((long long)k * f.stride + i);
@@ -85,8 +92,10 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
           sz += pl[0];
           sw += pl[1];
         };
-        for (int kb = 0; kb < own_b; ++kb) take(kb * sp + own_s);
-        for (int k = k_all; k < slices; ++k) take(k);
+        if (!f.acc64) {
+          for (int kb = 0; kb < own_b; ++kb) take(kb * sp + own_s);
+          for (int k = k_all; k < slices; ++k) take(k);
+        }
         const double inv = *f.fx_inv;
         const double dx = double(sx) * inv, dy = double(sy) * inv, dz = double(sz) * inv,
                      dw = double(sw) * inv;
@@ -97,11 +106,19 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
         // part_lo == nullptr: partials without low parts (symmetric tiles)
         const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 hi = zero, lo = zero;
+        const bool plain = f.plain != 0;
         auto add = [&](const float4 &h, const float4 &l) {
-          comp_add(hi.x, lo.x, h.x);
-          comp_add(hi.y, lo.y, h.y);
-          comp_add(hi.z, lo.z, h.z);
-          comp_add(hi.w, lo.w, h.w);
+          if (plain) {
+            hi.x = __fadd_rn(hi.x, h.x);
+            hi.y = __fadd_rn(hi.y, h.y);
+            hi.z = __fadd_rn(hi.z, h.z);
+            hi.w = __fadd_rn(hi.w, h.w);
+          } else {
+            comp_add(hi.x, lo.x, h.x);
+            comp_add(hi.y, lo.y, h.y);
+            comp_add(hi.z, lo.z, h.z);
+            comp_add(hi.w, lo.w, h.w);
+          }
           lo.x = __fadd_rn(lo.x, l.x);
           lo.y = __fadd_rn(lo.y, l.y);
           lo.z = __fadd_rn(lo.z, l.z);
@@ -209,10 +226,8 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
   if (f.mode & kFinDiag) block_sum8(dv, f.diag_part + (size_t)blockIdx.x * kDiagFields);
 }
 
-// Scale of the fixed-point mode: a power of two 2^S such that the largest sum a
-// target can reach, |sum_j m_j d / s^3| <= M 2 / (3 sqrt(3) eps^2) and
-// |sum_j m_j / s| <= M / eps (M = sum |m_j|), stays below 2^62. One block; the
-// mass sum runs in FP64 in a fixed order.
+// Scale of the fixed-point mode (fixed_scale_of) for the one-sided fixed-point
+// tiles: one block; the mass sum runs in FP64 in a fixed order.
 __global__ void __launch_bounds__(256) fixed_scale_kernel(const float4 *pos, int n, float eps2,
                                                           float *scale, double *inv) {
   __shared__ double part[256];
@@ -223,12 +238,7 @@ __global__ void __launch_bounds__(256) fixed_scale_kernel(const float4 *pos, int
   if (threadIdx.x == 0) {
     double M = 0.0;
     for (int k = 0; k < 256; ++k) M += part[k];
-    const double e2 = double(eps2);
-    const double bound = fmax(M * 0.3849001794597505 / e2, M / sqrt(e2)) + 1e-300;
-    int S = int(floor(62.0 - log2(bound)));
-    S = S > 126 ? 126 : (S < -126 ? -126 : S);
-    *scale = ldexpf(1.0f, S);
-    *inv = ldexp(1.0, -S);
+    fixed_scale_of(M, eps2, scale, inv);
   }
 }
 

@@ -37,6 +37,9 @@ struct FinalizeArgs {
   float4 *acc_lo;        // may be null
   float4 *trace_next;    // positions after the drift, or null
   const double *fx_inv;  // fixed-point partials (int64): value = sum * (*fx_inv); else null
+  // fixed-point accumulators of atomic plans (four int64 arrays x, y, z, w of
+  // stride `stride`, one element per particle; with fx_inv), else null
+  const long long *acc64;
   float4 *x_lo;          // compensated state: low parts of x and v, or null
   float4 *v_lo;
   int mode;
@@ -46,6 +49,9 @@ struct FinalizeArgs {
   // i / block or k % split is i's part. sym_split <= 1: every slot counts.
   int sym_block;
   int sym_split;
+  // 1: add the slots in plain FP32 (NBODY_NO_COMPENSATION); 0: compensated
+  // (TwoSum into a high and a low part).
+  int plain;
 };
 
 constexpr int kFinThreads = 256;

@@ -121,4 +121,18 @@ __device__ __forceinline__ void comp_add(float &hi, float &lo, float b) {
   lo = __fadd_rn(lo, e);
 }
 
+// Scale of the 64-bit fixed-point accumulation of softened gravity: the largest
+// power of two 2^S for which every sum a target can reach, |sum_j m_j d / s^3| <=
+// M 2 / (3 sqrt(3) eps^2) and |sum_j m_j / s| <= M / eps (M = sum |m_j|, the
+// maximum of r / (r^2 + eps^2)^(3/2) being 2 / (3 sqrt(3) eps^2)), stays below 2^62.
+// Writes 2^S and 2^-S.
+__device__ __forceinline__ void fixed_scale_of(double M, float eps2, float *scale, double *inv) {
+  const double e2 = double(eps2);
+  const double bound = fmax(M * 0.3849001794597505 / e2, M / sqrt(e2)) + 1e-300;
+  int S = int(floor(62.0 - log2(bound)));
+  S = S > 126 ? 126 : (S < -126 ? -126 : S);
+  *scale = ldexpf(1.0f, S);
+  *inv = ldexp(1.0, -S);
+}
+
 }  // namespace nbody

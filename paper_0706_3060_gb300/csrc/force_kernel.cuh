@@ -75,6 +75,11 @@ struct ForceArgs {
   int *counter;        // null: single-system mode
   int comp;            // 1: compensated (hi, lo) sums per j-tile
   const float *fscale; // fixed-point kernels: device word holding the scale 2^S
+  // Newton-symmetric gravity with atomic accumulation: four int64 arrays
+  // (x, y, z, w) of stride `stride`, zeroed before the launch, into which every
+  // CTA adds its per-block partials rounded onto the fixed-point grid *fscale;
+  // null: per-block partial slots in part_hi / part_lo
+  long long *acc64;
 };
 
 enum : int { kChunkFirst = 1, kChunkLast = 2, kChunkEnd = 4 };

@@ -30,9 +30,14 @@
 // bj * S + s, its source-side partial to slot bi * S + s, so a particle of block
 // b and part s_p receives every slot k with k / S >= b and, below that, those with
 // k % S == s_p; the finalize kernel skips the rest. S = 1 is the plain scheme.
-// FX (NBODY_FIXED_POINT, Sec. 3.2): each partial is rounded onto the 64-bit
-// fixed-point grid 2^S (S from *a.fscale) and stored as four int64, (x, y) in
-// part_hi and (z, w) in part_lo, which the finalize adds as integers.
+// Atomic accumulation (a.acc64 set; gravity with eps > 0, Sec. 3.2's GRAPE-6
+// scheme): each partial is rounded onto the 64-bit fixed-point grid 2^S (S from
+// *a.fscale, chosen from an a-priori bound on every sum) and added with integer
+// atomics into one accumulator per particle; integer addition is associative,
+// so the result does not depend on the order of the CTAs, and the scratch is
+// 32 bytes per particle instead of one partial per particle and block.
+// FX without a.acc64: each partial is stored as four int64 in its slot, (x, y)
+// in part_hi and (z, w) in part_lo, which the finalize adds as integers.
 #pragma once
 
 #include <cmath>
@@ -67,10 +72,25 @@ __device__ __forceinline__ void sym_tile_of(long long t, int nb, int &bi, int &b
   bj = b + int(t - start(b));
 }
 
-// Store one partial of particle `idx` in slot `base` (FP32, or four int64 with FX).
-template <bool FX>
-__device__ __forceinline__ void sym_store(const ForceArgs &a, long long idx, float x, float y,
-                                          float z, float w) {
+// Store one partial of `particle`: with a.acc64, add it, rounded onto the 64-bit
+// fixed-point grid, to the particle's accumulator with integer atomics (exact,
+// so the order in which CTAs arrive does not change the sum); otherwise write it
+// to element `particle` of the slot starting at `slot_base` (FP32, or four int64
+// with FX).
+template <bool FX, bool POT>
+__device__ __forceinline__ void sym_store(const ForceArgs &a, long long slot_base, int particle,
+                                          float x, float y, float z, float w) {
+  if (a.acc64) {
+    const float sc = __ldg(a.fscale);
+    unsigned long long *p = reinterpret_cast<unsigned long long *>(a.acc64) + particle;
+    const long long st = a.stride;
+    atomicAdd(p, static_cast<unsigned long long>(__float2ll_rn(x * sc)));
+    atomicAdd(p + st, static_cast<unsigned long long>(__float2ll_rn(y * sc)));
+    atomicAdd(p + 2 * st, static_cast<unsigned long long>(__float2ll_rn(z * sc)));
+    if (POT) atomicAdd(p + 3 * st, static_cast<unsigned long long>(__float2ll_rn(w * sc)));
+    return;
+  }
+  const long long idx = slot_base + particle;
   if constexpr (FX) {
     const float sc = __ldg(a.fscale);
     long long *ph = reinterpret_cast<long long *>(a.part_hi) + 2 * idx;
@@ -229,12 +249,13 @@ __global__ void __launch_bounds__(NT, MINB) sym_grav_kernel(const ForceArgs a) {
 #pragma unroll
   for (int r = 0; r < I; ++r)
     if (ig[r] >= 0)
-      sym_store<FX>(a, ibase + ig[r], ax[r].x + ax[r].y, ay[r].x + ay[r].y, az[r].x + az[r].y,
-                    aw[r].x + aw[r].y);
+      sym_store<FX, POT>(a, ibase, ig[r], ax[r].x + ax[r].y, ay[r].x + ay[r].y,
+                         az[r].x + az[r].y, aw[r].x + aw[r].y);
   if (diag) return;
   // j side: slot bi (part s) of every source of the part, warps added in index order
   __syncthreads();
-  const long long jbase = (long long)(bi * np_ + s_) * a.stride + j0 + 2 * p0_;
+  const long long jbase = (long long)(bi * np_ + s_) * a.stride;
+  const int jfirst = j0 + 2 * p0_;
   const int nq = min(2 * npairs, nsrc - 2 * p0_);
   for (int q = tid; q < nq; q += NT) {
     const int pp = q >> 1, h = q & 1;
@@ -246,7 +267,7 @@ __global__ void __launch_bounds__(NT, MINB) sym_grav_kernel(const ForceArgs a) {
       vz += Jw[(4 + h) * T::kPairs + pp];
       if (POT) vw += Jw[(6 + h) * T::kPairs + pp];
     }
-    sym_store<FX>(a, jbase + q, vx, vy, vz, vw);
+    sym_store<FX, POT>(a, jbase, jfirst + q, vx, vy, vz, vw);
   }
 }
 
