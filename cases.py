@@ -64,16 +64,17 @@ def _ensemble(nb, torch, dev, nsys=512, seed=3):
     return torch.from_numpy(pos).to(dev).contiguous(), prm, table
 
 
-def build_case(name, nb, torch, dev):
-    """Return a zero-argument callable running one call of the named workload."""
+def build_case(name, nb, torch, dev, tile=-1, jsplit=0):
+    """Return a zero-argument callable running one call of the named workload
+    (force and VJP cases with the given tile and j-split; -1 / 0: tuned)."""
     if name in ("grav65536", "grav262144"):
         pos, _, eps = _grav(nb, torch, dev, int(name[4:]))
         acc = torch.empty_like(pos)
-        return lambda: nb.forces(pos, eps=eps, out=acc)
+        return lambda: nb.forces(pos, eps=eps, out=acc, tile=tile, jsplit=jsplit)
     if name in ("ljc8192", "ljc65536"):
         pos, prm = _ljc(nb, torch, dev, int(name[3:]))
         acc = torch.empty_like(pos)
-        return lambda: nb.forces(pos, prm, out=acc)
+        return lambda: nb.forces(pos, prm, out=acc, tile=tile, jsplit=jsplit)
     if name == "ljcvjp8192":
         pos, prm = _ljc(nb, torch, dev, 8192)
         lam = torch.randn_like(pos)
@@ -86,7 +87,26 @@ def build_case(name, nb, torch, dev):
         lam = torch.randn_like(pos)
         gx = torch.empty_like(pos)
         gm = torch.empty(pos.shape[0], device=dev)
-        return lambda: nb.adjoint(pos, lam, eps=eps, grad_x=gx, grad_m=gm)
+        return lambda: nb.adjoint(pos, lam, eps=eps, grad_x=gx, grad_m=gm, tile=tile,
+                                  jsplit=jsplit)
+    if name == "adjoint16384":  # forward + backward of the adjoint workload (200 steps, k = 20)
+        import numpy as np
+        import workloads
+        from paper_0706_3060_gb300.autograd import leapfrog
+        n = 16384
+        g = workloads.plummer(n, seed=4, eps=workloads.plummer_softening(n))
+        x, v, m = g.f32()
+        tgt = torch.from_numpy(workloads.perturbed_target(x.astype(np.float64), seed=4)
+                               .astype(np.float32)).to(dev)
+        eps = float(np.float32(g.eps))
+
+        def run():
+            x0 = torch.from_numpy(x).to(dev).requires_grad_(True)
+            v0 = torch.from_numpy(v).to(dev).requires_grad_(True)
+            m0 = torch.from_numpy(m).to(dev).requires_grad_(True)
+            xT, _ = leapfrog(x0, v0, m0, dt=1e-4, nsteps=200, k=20, eps=eps)
+            (((xT - tgt) ** 2).sum() / n).backward()
+        return run
     if name in ("jerk65536", "jerk262144"):
         pos, vel, eps = _grav(nb, torch, dev, int(name[4:]))
         return lambda: nb.forces_jerk(pos, vel, eps=eps)
@@ -102,9 +122,11 @@ def build_case(name, nb, torch, dev):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["grav65536", "grav262144", "ljc8192", "ljcvjp8192", "ljc65536", "vjp16384",
-                                     "jerk65536", "jerk262144", "batched512"])
+                                     "jerk65536", "jerk262144", "batched512", "adjoint16384"])
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--iters", type=int, default=2)
+    ap.add_argument("--tile", type=int, default=-1)
+    ap.add_argument("--jsplit", type=int, default=0)
     a = ap.parse_args()
     root = os.path.dirname(os.path.abspath(__file__))
     if root not in sys.path:
@@ -113,7 +135,7 @@ def main():
 
     import paper_0706_3060_gb300 as nb
     dev = torch.device("cuda", 0)
-    fn = build_case(a.case, nb, torch, dev)
+    fn = build_case(a.case, nb, torch, dev, a.tile, a.jsplit)
     for _ in range(a.warmup + a.iters):
         fn()
     torch.cuda.synchronize()

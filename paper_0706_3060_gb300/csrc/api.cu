@@ -152,11 +152,14 @@ int get_scratch(cudaStream_t s, int law, int n, const Plan1 &plan, int diag_rows
 }
 
 // One force evaluation into scratch partials, then one finalize launch.
+// first_eval: the first evaluation of this call (atomic plans form the
+// fixed-point scale there; the masses do not change between the steps of a call).
 int eval_and_finalize(const float4 *pos, const float4 *prm, const nbody_params &p, int n,
                       const Plan1 &plan, const Scratch &sc, int *err, bool pot,
-                      FinalizeArgs f, cudaStream_t s, int *nblk) {
+                      FinalizeArgs f, cudaStream_t s, int *nblk, bool first_eval) {
   const bool fx = (p.flags & NBODY_FIXED_POINT) != 0 || plan.atomic;
-  const AtomicPrep at{sc.acc64, sc.msum, sc.ticket, p.eps2, sc.fscale, sc.finv};
+  const AtomicPrep at{sc.acc64, sc.msum, sc.ticket, p.eps2, sc.fscale, sc.finv,
+                      first_eval ? 1 : 0};
   NB_TRY(launch_forces(pos, prm, p.law, p.flags, p.eps2, n, plan, sc.part_hi, sc.part_lo,
                        sc.jbuf, err, pot, s, nullptr,
                        (fx && !plan.atomic) ? sc.fscale : nullptr,
@@ -203,7 +206,7 @@ int forces_device(const float4 *pos, const float4 *prm, float4 *acc, float4 *acc
   f.acc_lo = acc_lo;
   f.mode = kFinWriteAcc;
   return eval_and_finalize(pos, prm, p, n, plan, sc, err, (p.flags & NBODY_COMPUTE_POT) != 0, f,
-                           s, nullptr);
+                           s, nullptr, true);
 }
 
 int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n, float dt,
@@ -222,6 +225,7 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
   if (trace) NB_CUDA(cudaMemcpyAsync(trace, pos, size_t(n) * sizeof(float4),
                                      cudaMemcpyDeviceToDevice, s));
   int row = 0;
+  bool first_eval = true;  // the fixed-point scale of atomic plans is formed once per call
   FinalizeArgs f{};
   f.pos = pos;
   f.vel = vel;
@@ -236,7 +240,8 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
     f.mode = kFinWriteAcc | (report(0) ? kFinDiag : 0) | (nsteps > 0 ? kFinKickDrift : 0);
     f.trace_next = (trace && nsteps > 0) ? trace + size_t(n) : nullptr;
     NB_TRY(eval_and_finalize(pos, prm, p, n, plan, sc, err,
-                             report(0) || (nsteps == 0 && want_pot), f, s, &nblk));
+                             report(0) || (nsteps == 0 && want_pot), f, s, &nblk, first_eval));
+    first_eval = false;
     if (report(0)) NB_TRY(launch_diag_reduce(sc.diag_part, nblk, sc.diag_rows + kDiagFields * row++, s));
   } else if (nsteps > 0) {
     NB_TRY(launch_kick_drift(pos, vel, acc, n, dt, trace ? trace + size_t(n) : nullptr, nullptr,
@@ -249,7 +254,8 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
     f.mode = kFinWriteAcc | kFinKickSync | (rep ? kFinDiag : 0) | (last ? 0 : kFinKickDrift);
     f.trace_next = (trace && !last) ? trace + size_t(st + 1) * size_t(n) : nullptr;
     NB_TRY(eval_and_finalize(pos, prm, p, n, plan, sc, err, rep || (last && want_pot), f, s,
-                             &nblk));
+                             &nblk, first_eval));
+    first_eval = false;
     if (rep) NB_TRY(launch_diag_reduce(sc.diag_part, nblk, sc.diag_rows + kDiagFields * row++, s));
   }
   if (rows > 0)

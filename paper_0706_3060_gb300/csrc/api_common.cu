@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(256) interleave_pairs_blocked_kernel(const flo
     jp[base + pp] = make_float4(a.x, b.x, a.y, b.y);
     jp[base + B / 2 + pp] = make_float4(a.z, b.z, a.w, b.w);
     if (at.acc64) {
-      am = fabs(double(a.w)) + fabs(double(b.w));
+      if (at.form_scale) am = fabs(double(a.w)) + fabs(double(b.w));
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         at.acc64[(long long)c * n + 2 * p] = 0;
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(256) interleave_pairs_blocked_kernel(const flo
       }
     }
   }
-  if (!at.acc64) return;  // the same for every thread of the launch
+  if (!at.acc64 || !at.form_scale) return;  // the same for every thread of the launch
   __shared__ double red[8];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

@@ -137,6 +137,8 @@ struct AtomicPrep {
   float eps2;
   float *scale;      // out: 2^S, read by the force kernel
   double *inv;       // out: 2^-S, read by the finalize kernel
+  int form_scale;    // 1: form the scale in this launch; 0: an earlier launch of the
+                     // same call did (same masses and eps), *scale and *inv hold it
 };
 
 // jbuf: scratch of jbuf_bytes(law, n) for the pair-interleaved sources of packed tiles.

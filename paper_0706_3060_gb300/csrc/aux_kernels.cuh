@@ -124,20 +124,22 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
           lo.z = __fadd_rn(lo.z, l.z);
           lo.w = __fadd_rn(lo.w, l.w);
         };
-        // `count` slots k0, k0 + step, ...; loads issued four slots ahead of the
-        // adds (the symmetric tiles leave one slot per block: hundreds at large N)
+        // `count` slots k0, k0 + step, ...; loads issued eight slots ahead of the
+        // adds (the symmetric tiles leave one slot per block and source part: a
+        // hundred or more per particle, read by few CTAs at small N)
         auto run = [&](int k0, int count, int step) {
+          constexpr int U = 8;
           int c = 0;
-          for (; c + 3 < count; c += 4) {
-            float4 h[4], l[4];
+          for (; c + U <= count; c += U) {
+            float4 h[U], l[U];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < U; ++u) {
               const long long o = (long long)(k0 + (c + u) * step) * f.stride + i;
               h[u] = f.part_hi[o];
               l[u] = f.part_lo ? f.part_lo[o] : zero;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) add(h[u], l[u]);
+            for (int u = 0; u < U; ++u) add(h[u], l[u]);
           }
           for (; c < count; ++c) {
             const long long o = (long long)(k0 + c * step) * f.stride + i;

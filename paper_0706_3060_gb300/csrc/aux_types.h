@@ -54,7 +54,7 @@ struct FinalizeArgs {
   int plain;
 };
 
-constexpr int kFinThreads = 256;
+constexpr int kFinThreads = 64;  // many CTAs: the finalize is latency-bound at small n
 constexpr int kDiagFields = 8;  // K, U, Px, Py, Pz, Lx, Ly, Lz
 
 }  // namespace nbody

@@ -27,6 +27,10 @@ const TileDesc *ljc_tiles(int *count) {
       SymLjcImpl<kLawLJC, 128, 2>::desc(),     // 15: blocks of 256
       SymLjcImpl<kLawLJC, 64, 4>::desc(),      // 16: blocks of 256, 2-warp CTAs
       SymLjcImpl<kLawLJC, 128, 8, 2>::desc(),  // 17: blocks of 1024
+      // small N: eight targets per thread in narrower CTAs, more CTAs per SM
+      SymLjcImpl<kLawLJC, 64, 8, 4>::desc(),   // 18: blocks of 512, 2-warp CTAs
+      SymLjcImpl<kLawLJC, 32, 8, 8>::desc(),   // 19: blocks of 256, 1-warp CTAs
+      SymLjcImpl<kLawLJC, 64, 4, 8>::desc(),   // 20: blocks of 256, 2-warp CTAs, 8 per SM
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;

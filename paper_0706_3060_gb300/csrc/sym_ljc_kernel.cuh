@@ -171,7 +171,10 @@ __global__ void __launch_bounds__(NT, MINB) sym_ljc_kernel(const ForceArgs a) {
             jg + 1 == ig[r]);
     }
   } else {
-    float *J = jsum + size_t(warp) * NC * P;
+    // this warp's source-side sums: one float2 (both halves of a source pair) per
+    // component and pair, added with one packed read-modify-write per component;
+    // they hold +sum f d (negated when the warps are added) and +sum of energies
+    float2 *J = reinterpret_cast<float2 *>(jsum) + size_t(warp) * (NC / 2) * P;
     for (int g0 = 0; g0 < npairs; g0 += 32) {
 #pragma unroll 1
       for (int st = 0; st < 32; ++st) {
@@ -186,17 +189,10 @@ __global__ void __launch_bounds__(NT, MINB) sym_ljc_kernel(const ForceArgs a) {
           for (int r = 0; r < I; ++r)
             sym_ljc_pair2<POT, PRECISE, LIN>(X, Y, Z, Q, S, E, nx[r], ny[r], nz[r], qi[r], si[r],
                                              ei[r], ax[r], ay[r], az[r], aw[r], jx, jy, jz, jw);
-          // the sources feel -f d; the pair energy counts for both
-          J[0 * P + pp] -= jx.x;
-          J[1 * P + pp] -= jx.y;
-          J[2 * P + pp] -= jy.x;
-          J[3 * P + pp] -= jy.y;
-          J[4 * P + pp] -= jz.x;
-          J[5 * P + pp] -= jz.y;
-          if (POT) {
-            J[6 * P + pp] += jw.x;
-            J[7 * P + pp] += jw.y;
-          }
+          J[0 * P + pp] = __fadd2_rn(J[0 * P + pp], jx);
+          J[1 * P + pp] = __fadd2_rn(J[1 * P + pp], jy);
+          J[2 * P + pp] = __fadd2_rn(J[2 * P + pp], jz);
+          if (POT) J[3 * P + pp] = __fadd2_rn(J[3 * P + pp], jw);
         }
         __syncwarp();  // at the next step lane l - 1 updates the slot lane l just wrote
       }
@@ -218,13 +214,14 @@ __global__ void __launch_bounds__(NT, MINB) sym_ljc_kernel(const ForceArgs a) {
     const int pp = q >> 1, h = q & 1;
     float vx = 0.0f, vy = 0.0f, vz = 0.0f, vw = 0.0f;
     for (int w = 0; w < T::kWarps; ++w) {
-      const float *Jw = jsum + size_t(w) * NC * P;
-      vx += Jw[(0 + h) * P + pp];
-      vy += Jw[(2 + h) * P + pp];
-      vz += Jw[(4 + h) * P + pp];
-      if (POT) vw += Jw[(6 + h) * P + pp];
+      const float *Jw = jsum + size_t(w) * NC * P;  // float view of the float2 sums
+      vx += Jw[2 * (0 * P + pp) + h];
+      vy += Jw[2 * (1 * P + pp) + h];
+      vz += Jw[2 * (2 * P + pp) + h];
+      if (POT) vw += Jw[2 * (3 * P + pp) + h];
     }
-    a.part_hi[jbase + q] = make_float4(vx, vy, vz, vw);
+    // the sources feel -f d; the pair energy counts for both
+    a.part_hi[jbase + q] = make_float4(-vx, -vy, -vz, vw);
   }
 }
 

@@ -49,30 +49,50 @@ __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs
     const int below = own_b;        // slots own_s, own_s + sp, ... below the own block
     const int k_all = own_b * sp;   // every slot from here on
     const int count = below + (f.slices - k_all);
-    for (int c = 0; c < count; ++c) {
+    auto offset = [&](int c) {
       const int k = c < below ? c * sp + own_s : k_all + (c - below);
-      const long long o = (long long)k * f.stride + i;
-      float4 h = f.part_hi[o], l = f.part_lo ? f.part_lo[o] : zero;
-      comp_add(hA.x, oA.x, h.x);
-      comp_add(hA.y, oA.y, h.y);
-      comp_add(hA.z, oA.z, h.z);
-      comp_add(hA.w, oA.w, h.w);
-      oA.x += l.x;
-      oA.y += l.y;
-      oA.z += l.z;
-      oA.w += l.w;
-      if (lj) {
-        h = f.part_hi[f.bstride + o];
-        l = f.part_lo ? f.part_lo[f.bstride + o] : zero;
-        comp_add(hB.x, oB.x, h.x);
-        comp_add(hB.y, oB.y, h.y);
-        comp_add(hB.z, oB.z, h.z);
-        comp_add(hB.w, oB.w, h.w);
-        oB.x += l.x;
-        oB.y += l.y;
-        oB.z += l.z;
-        oB.w += l.w;
+      return (long long)k * f.stride + i;
+    };
+    auto add = [&](float4 &h, float4 &o, const float4 &a, const float4 &l) {
+      comp_add(h.x, o.x, a.x);
+      comp_add(h.y, o.y, a.y);
+      comp_add(h.z, o.z, a.z);
+      comp_add(h.w, o.w, a.w);
+      o.x += l.x;
+      o.y += l.y;
+      o.z += l.z;
+      o.w += l.w;
+    };
+    // slots in the same order as one at a time, with the loads of eight slots
+    // issued before their adds (the symmetric tiles leave dozens per particle)
+    constexpr int U = 8;
+    int c = 0;
+    for (; c + U <= count; c += U) {
+      float4 h[U], l[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long o = offset(c + u);
+        h[u] = f.part_hi[o];
+        l[u] = f.part_lo ? f.part_lo[o] : zero;
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) add(hA, oA, h[u], l[u]);
+      if (lj) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const long long o = f.bstride + offset(c + u);
+          h[u] = f.part_hi[o];
+          l[u] = f.part_lo ? f.part_lo[o] : zero;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) add(hB, oB, h[u], l[u]);
+      }
+    }
+    for (; c < count; ++c) {
+      const long long o = offset(c);
+      add(hA, oA, f.part_hi[o], f.part_lo ? f.part_lo[o] : zero);
+      if (lj)
+        add(hB, oB, f.part_hi[f.bstride + o], f.part_lo ? f.part_lo[f.bstride + o] : zero);
     }
     const float ax = hA.x + oA.x, ay = hA.y + oA.y, az = hA.z + oA.z, aw = hA.w + oA.w;
     float gx, gy, gz, gm;

@@ -166,7 +166,14 @@ def test_ljc_forces(n):
     assert np.sqrt(np.mean(e * e)) <= 1e-5 and e.max() <= 1e-4
 
 
-@pytest.mark.parametrize("tile", range(18))
+LJC_TILES = 21  # rows of the LJC force table (checked below against the library)
+
+
+def test_ljc_tile_count():
+    assert lib().tile_count(lib().LAW_LJC) == LJC_TILES
+
+
+@pytest.mark.parametrize("tile", range(LJC_TILES))
 def test_ljc_every_tile(tile):
     nb = lib()
     s = workloads.ljc_sphere(1500, seed=9)
