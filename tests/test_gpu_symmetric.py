@@ -546,3 +546,28 @@ def test_symmetric_no_compensation_is_honoured():
         assert not torch.equal(a, b), t
         for acc in (a, b):
             assert_forces_close(acc[idx, :3].double().cpu().numpy(), ref, what=f"tile {t}")
+
+
+def test_symmetric_gravity_beyond_the_slot_cap():
+    """Softened gravity at N = 2^21 through the Newton-symmetric tile with blocks of
+    1024: per-block FP32 slots would need nb x N x 16 B = 32 GiB (above the cap), the
+    fixed-point atomic accumulation needs 32 B per particle. 512 sampled targets
+    against the oracle, and the same bits on a second call."""
+    nb = lib()
+    n = 1 << 21
+    t = [k for k in _sym_tiles() if nb.tile_info(nb.LAW_GRAV, k)["j_tile"] == 1024][-1]
+    g = workloads.plummer(n, seed=13, eps=workloads.plummer_softening(n))
+    pos, _ = grav_tensors(g)
+    eps = float(np.float32(g.eps))
+    assert nb.workspace_size(n, eps=eps, tile=t) < 64 * n
+    with pytest.raises(nb.NBodyError):  # the slot path at this size is refused
+        nb.workspace_size(n, eps=eps, tile=t, compensated=False)
+    acc = nb.forces(pos, eps=eps, tile=t, pot=True)
+    again = nb.forces(pos, eps=eps, tile=t, pot=True)
+    assert torch.equal(acc, again)
+    x, _, m = g.f32_as_f64()
+    idx = np.random.default_rng(21).choice(n, 512, replace=False)
+    ref, phi = oracle.grav_accel(x, m, eps=eps, idx=idx, potential=True)
+    got = acc[torch.from_numpy(idx).to(dev())].double().cpu().numpy()
+    assert_forces_close(got[:, :3], ref, what="N = 2^21 symmetric")
+    assert np.all(np.abs(got[:, 3] - phi) <= 1e-5 * np.abs(phi))
