@@ -893,7 +893,7 @@ def adjoint_accuracy(torch, dev, n=16384, steps=200, k=20, dt=1e-4):
                                     "particles vs the stored FP64 oracle gradient "
                                     "(per particle, floor 10% of RMS); directional "
                                     "derivatives vs oracle central differences (h = 1e-4)",
-           "adjoint_loss_rel_err": abs(float(loss) - golden["loss"]) / golden["loss"]}
+           "adjoint_loss_rel_err": abs(float(loss.detach()) - golden["loss"]) / golden["loss"]}
     for key in ("x0", "v0", "m"):
         ref = np.reshape(np.asarray(golden[key]), (len(idx), -1))
         num = np.linalg.norm(np.reshape(got[key][idx], (len(idx), -1)) - ref, axis=1)

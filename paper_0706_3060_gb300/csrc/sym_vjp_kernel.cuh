@@ -175,7 +175,10 @@ __global__ void __launch_bounds__(NT, MINB) sym_gvjp_kernel(const VjpArgs a) {
                                     jg + 1 == ig[r]);
     }
   } else {
-    float *J = jsum + size_t(warp) * 8 * P;
+    // this warp's source-side sums: one float2 (both halves of a source pair) per
+    // component and pair, one packed read-modify-write per component; they hold
+    // the terms before the sources' sign change (negated when the warps are added)
+    float2 *J = reinterpret_cast<float2 *>(jsum) + size_t(warp) * 4 * P;
     for (int g0 = 0; g0 < npairs; g0 += 32) {
 #pragma unroll 1
       for (int st = 0; st < 32; ++st) {
@@ -192,15 +195,10 @@ __global__ void __launch_bounds__(NT, MINB) sym_gvjp_kernel(const VjpArgs a) {
             sym_gvjp_pair2<true, false>(X, Y, Z, nM, LX, LY, LZ, nx[r], ny[r], nz[r], mk[r],
                                         lkx[r], lky[r], lkz[r], e2, ax[r], ay[r], az[r], aw[r],
                                         jx, jy, jz, jw);
-          // the sources receive the negated terms
-          J[0 * P + pp] -= jx.x;
-          J[1 * P + pp] -= jx.y;
-          J[2 * P + pp] -= jy.x;
-          J[3 * P + pp] -= jy.y;
-          J[4 * P + pp] -= jz.x;
-          J[5 * P + pp] -= jz.y;
-          J[6 * P + pp] -= jw.x;
-          J[7 * P + pp] -= jw.y;
+          J[0 * P + pp] = __fadd2_rn(J[0 * P + pp], jx);
+          J[1 * P + pp] = __fadd2_rn(J[1 * P + pp], jy);
+          J[2 * P + pp] = __fadd2_rn(J[2 * P + pp], jz);
+          J[3 * P + pp] = __fadd2_rn(J[3 * P + pp], jw);
         }
         __syncwarp();  // at the next step lane l - 1 updates the slot lane l just wrote
       }
@@ -222,13 +220,14 @@ __global__ void __launch_bounds__(NT, MINB) sym_gvjp_kernel(const VjpArgs a) {
     const int pp = q >> 1, h = q & 1;
     float vx = 0.0f, vy = 0.0f, vz = 0.0f, vw = 0.0f;
     for (int w = 0; w < T::kWarps; ++w) {
-      const float *Jw = jsum + size_t(w) * 8 * P;
-      vx += Jw[(0 + h) * P + pp];
-      vy += Jw[(2 + h) * P + pp];
-      vz += Jw[(4 + h) * P + pp];
-      vw += Jw[(6 + h) * P + pp];
+      const float *Jw = jsum + size_t(w) * 8 * P;  // float view of the float2 sums
+      vx += Jw[2 * (0 * P + pp) + h];
+      vy += Jw[2 * (1 * P + pp) + h];
+      vz += Jw[2 * (2 * P + pp) + h];
+      vw += Jw[2 * (3 * P + pp) + h];
     }
-    a.part_hi[jbase + q] = make_float4(vx, vy, vz, vw);
+    // the sources receive the negated terms
+    a.part_hi[jbase + q] = make_float4(-vx, -vy, -vz, -vw);
   }
 }
 
