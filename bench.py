@@ -69,7 +69,7 @@ def config(n_gpus):
             "eps": 4.0 / N_BENCH ** (1.0 / 3.0) * 0.01, "dt": DT,
             "pairs_per_step": N_BENCH * N_BENCH, "law": "gravity (Eq. 1)",
             "precision": ("FP32 pairs; plain FP32 sums within each block pair, per-block "
-                          "partials added with compensation"),
+                          "partials added as 64-bit fixed point (integer atomics)"),
             "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": f"replicas x{n_gpus}" if n_gpus > 1 else "single GPU"}
 
@@ -405,8 +405,8 @@ def extras(nb, torch, dev, g, eps):
     ex["force_err_max"] = float(e.max())
     ex["force_err_sample"] = "1024 seeded targets vs FP64 oracle"
     ex["default_mode"] = ("hardware rsqrt; Newton-symmetric tile: plain sums per block pair, "
-                          "per-block partials added with compensation (plain with "
-                          "NBODY_NO_COMPENSATION)")
+                          "per-block partials added as 64-bit fixed point with integer atomics "
+                          "(with NBODY_NO_COMPENSATION: stored per block and added plainly)")
     # the other precision modes on the same targets: Newton-refined rsqrt, plain
     # FP32 sums, 64-bit fixed-point sums (error and device time per evaluation)
     out_acc = torch.empty_like(pos)
