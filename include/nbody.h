@@ -367,12 +367,17 @@ enum {
                                   gravity VJP the j-split
                                   cuts each block's sources into 1, 2, 4 or 8 parts
                                   (one CTA each; 0: one part, other values rounded
-                                  down); scratch holds one
-                                  partial per particle and block, so it is refused
-                                  (explicit tile) or replaced by the default tile
-                                  (tuned) when the partials would exceed an eighth of
-                                  the device's memory or 16 GiB, and always for
-                                  subsets and the allocation-free entry point */
+                                  down). Softened gravity (eps2 > 0, without
+                                  NBODY_NO_COMPENSATION) adds each block's partial
+                                  sums as 64-bit fixed point with integer atomics
+                                  into 32 bytes of scratch per particle (Sec. 3.2,
+                                  the GRAPE-6 scheme; bitwise reproducible); the
+                                  other cases keep one partial per particle and
+                                  block, so the tile is refused (explicit tile) or
+                                  replaced by the default tile (tuned) when those
+                                  partials would exceed an eighth of the device's
+                                  memory or 16 GiB. Never used for subsets or by
+                                  the allocation-free entry point */
 };
 /* Describe configuration `tile` of `law`: threads per CTA (consumer warps),
  * i-particles per thread, j-lanes per warp, j-tile length, and its kind
