@@ -243,7 +243,8 @@ int nbody_forces_subset(const void *pos_m, const void *prm, const int32_t *idx,
  * each call rewrites what it reads, but calls whose GPU work overlaps (e.g. on
  * two streams) race on the array: serialize them. A bounded wait that runs out
  * in its kernels is recorded in the library's device error word (no allocation
- * either) and reported by the next nbody_check, like any other call's. */
+ * either) and reported by the next nbody_check, like any other call's. Its
+ * kernels are not bracketed by the kernel timers (which create CUDA events). */
 int nbody_forces_static(const void *pos_m, const void *prm, void *acc, int64_t n,
                         const nbody_params *params, nbody_stream_t stream);
 

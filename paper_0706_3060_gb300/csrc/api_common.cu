@@ -567,7 +567,7 @@ size_t jbuf_bytes(int law, int64_t n) {
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
                   int *err, bool pot, cudaStream_t s, const Targets *tg,
-                  const float *fscale, const AtomicPrep *at) {
+                  const float *fscale, const AtomicPrep *at, bool timed) {
   const bool atomic = at && at->acc64;
   if (p.atomic != atomic || (atomic && (law != NBODY_LAW_GRAV || tg || !at->msum ||
                                         !at->ticket || !at->scale || !at->inv)))
@@ -612,7 +612,7 @@ int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags,
   a.comp = (flags & NBODY_NO_COMPENSATION) ? 0 : 1;
   a.fscale = fscale;
   a.acc64 = atomic ? at->acc64 : nullptr;
-  const TimerMark tm = timer_begin(0, s);
+  const TimerMark tm = timed ? timer_begin(0, s) : TimerMark{};
   cudaError_t e = p.tile->launch(a, p.grid, pot, (flags & NBODY_PRECISE_RSQRT) != 0, s);
   timer_end(tm, s);
   if (e != cudaSuccess)

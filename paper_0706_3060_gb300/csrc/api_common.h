@@ -144,10 +144,13 @@ struct AtomicPrep {
 // jbuf: scratch of jbuf_bytes(law, n) for the pair-interleaved sources of packed tiles.
 // fscale: device word with the fixed-point scale, required exactly for fixed tiles
 // (atomic plans take theirs from `at`). at: required exactly for atomic plans.
+// timed: bracket the force kernel with the kernel timers when they are enabled (they
+// create CUDA events on first use; the allocation-free entry point passes false).
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
                   int *err, bool pot, cudaStream_t s, const Targets *tg = nullptr,
-                  const float *fscale = nullptr, const AtomicPrep *at = nullptr);
+                  const float *fscale = nullptr, const AtomicPrep *at = nullptr,
+                  bool timed = true);
 
 size_t round_up(size_t x, size_t a);
 

@@ -176,7 +176,8 @@ extern "C" int nbody_forces_static(const void *pos_m, const void *prm, void *acc
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   NB_TRY(launch_forces(static_cast<const float4 *>(pos_m), static_cast<const float4 *>(prm),
                        p.law, p.flags, p.eps2, int(n), plan, part_hi, part_lo, jbuf, err,
-                       (p.flags & NBODY_COMPUTE_POT) != 0, s));
+                       (p.flags & NBODY_COMPUTE_POT) != 0, s, nullptr, nullptr, nullptr,
+                       /*timed=*/false));
   FinalizeArgs f{};
   f.part_hi = part_hi;
   f.part_lo = part_lo;

@@ -15,6 +15,10 @@ const TileDesc *ljclin_tiles(int *count) {
       SymLjcImpl<kLawLJCLin, 128, 4>::desc(),  // 5: blocks of 512
       SymLjcImpl<kLawLJCLin, 128, 2>::desc(),  // 6: blocks of 256
       SymLjcImpl<kLawLJCLin, 64, 4>::desc(),   // 7: blocks of 256, 2-warp CTAs
+      // small N: more CTAs per SM (as LJC tiles 18-20)
+      SymLjcImpl<kLawLJCLin, 128, 8, 2>::desc(),  // 8: blocks of 1024
+      SymLjcImpl<kLawLJCLin, 64, 8, 4>::desc(),   // 9: blocks of 512, 2-warp CTAs
+      SymLjcImpl<kLawLJCLin, 64, 4, 8>::desc(),   // 10: blocks of 256, 8 CTAs per SM
   };
   *count = int(sizeof(tiles) / sizeof(tiles[0]));
   return tiles;

@@ -169,8 +169,12 @@ def test_ljc_forces(n):
 LJC_TILES = 21  # rows of the LJC force table (checked below against the library)
 
 
+LJCLIN_TILES = 11  # rows of the LJC(linear) force table
+
+
 def test_ljc_tile_count():
     assert lib().tile_count(lib().LAW_LJC) == LJC_TILES
+    assert lib().tile_count(lib().LAW_LJC_LINEAR) == LJCLIN_TILES
 
 
 @pytest.mark.parametrize("tile", range(LJC_TILES))
@@ -304,7 +308,7 @@ def _ljclin_tensors(s, D=4.0):
     return pos.contiguous(), prm, sysm, x.astype(np.float64)
 
 
-@pytest.mark.parametrize("tile", range(8))
+@pytest.mark.parametrize("tile", range(LJCLIN_TILES))
 @pytest.mark.parametrize("n", [257, 3000, 8192])
 def test_ljc_linear_dielectric(tile, n):
     """Table 1 LJC(linear): dielectric D r with D = 4 (reading C3)."""
