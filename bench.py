@@ -618,6 +618,24 @@ def _device_ms(torch, fn, reps=5):
     return float(np.median(ts))
 
 
+def _back_to_back_ms(torch, fn, calls=20, reps=5):
+    """Device milliseconds per call with `calls` eager calls issued back to back
+    (no synchronization between them: the host's launch work for one call overlaps
+    the GPU's work for the previous ones, as in a simulation loop)."""
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(calls):
+            fn()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b) / calls)
+    return float(np.median(ts))
+
+
 def _graph_ms(torch, fn, calls=10, reps=5):
     """Device milliseconds per call with the calls replayed from a CUDA graph (no
     host launch overhead between them): warm up on the capture stream, capture
@@ -647,8 +665,9 @@ def _graph_ms(torch, fn, calls=10, reps=5):
 
 def secondary_kernel_extras(nb, torch, dev, pos, eps):
     """Throughput of the other force forms on the same GPU (device time per call,
-    and for the 8192-atom cases also per call replayed from a CUDA graph, which
-    removes the host launch overhead that dominates calls this small):
+    and for the 8192-atom cases also per call issued back to back and per call
+    replayed from a CUDA graph, which hide or remove the host launch overhead that
+    dominates a synchronous call this small):
     LJ + Coulomb (constant and linear dielectric) on the 8192-atom sphere;
     acceleration + jerk, a Hermite step, an active subset of 1024 targets and the
     fixed-point mode on the N = 262144 Plummer sphere."""
@@ -664,6 +683,8 @@ def secondary_kernel_extras(nb, torch, dev, pos, eps):
     lacc = torch.empty_like(lpos)
     ms = _device_ms(torch, lambda: nb.forces(lpos, prm))
     out["ljc_8192_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
+    ms = _back_to_back_ms(torch, lambda: nb.forces(lpos, prm, out=lacc))
+    out["ljc_8192_back_to_back_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
     ms = _graph_ms(torch, lambda: nb.forces(lpos, prm, out=lacc))
     out["ljc_8192_graph_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
     n = pos.shape[0]
@@ -680,6 +701,9 @@ def secondary_kernel_extras(nb, torch, dev, pos, eps):
                           torch.from_numpy(s.types).to(dev), kq=332.0637 / 4.0)
     ms = _device_ms(torch, lambda: nb.forces(lpos, prm_lin, law=nb.LAW_LJC_LINEAR))
     out["ljc_linear_8192_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
+    ms = _back_to_back_ms(torch, lambda: nb.forces(lpos, prm_lin, law=nb.LAW_LJC_LINEAR,
+                                                    out=lacc))
+    out["ljc_linear_8192_back_to_back_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
     ms = _graph_ms(torch, lambda: nb.forces(lpos, prm_lin, law=nb.LAW_LJC_LINEAR, out=lacc))
     out["ljc_linear_8192_graph_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
     lam = torch.randn_like(lpos)
@@ -688,6 +712,8 @@ def secondary_kernel_extras(nb, torch, dev, pos, eps):
     vjp = lambda: nb.adjoint(lpos, lam, prm, grad_x=lgx, grad_m=lgm, grad_types=lgt)  # noqa: E731
     ms = _device_ms(torch, vjp)
     out["ljc_vjp_8192_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
+    ms = _back_to_back_ms(torch, vjp)
+    out["ljc_vjp_8192_back_to_back_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
     ms = _graph_ms(torch, vjp)
     out["ljc_vjp_8192_graph_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
     hp, hv = pos.clone(), vel.clone()
