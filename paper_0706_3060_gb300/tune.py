@@ -94,11 +94,13 @@ def _vjp_timer(torch, table):
 
 
 def tune(law: int, sizes, jsplits=(0, 1, 2, 4, 8, 16, 32), reps=5, verbose=True,
-         native=True):
+         native=True, tiles=None):
     """Time every tile x j-split of tile table `law` (0-2 force laws, 4 fixed point,
     5-7 the VJP and jerk tables) at each size and install the fastest per size
     bucket. native=True runs the search inside the library (nbody_tune, the same
-    j-splits); native=False times each configuration from Python and prints it."""
+    j-splits); native=False times each configuration from Python and prints it,
+    optionally only the tiles listed in `tiles` (for sizes where timing every
+    configuration would take hours)."""
     import torch
     if native:
         table = {}
@@ -125,7 +127,7 @@ def tune(law: int, sizes, jsplits=(0, 1, 2, 4, 8, 16, 32), reps=5, verbose=True,
     for n in sizes:
         pos, prm = _inputs(torch, in_law, n)
         results = []
-        for tile in range(api.tile_count(law)):
+        for tile in (range(api.tile_count(law)) if tiles is None else tiles):
             info = api.tile_info(law, tile)
             tile_i = info["threads"] // info["j_lanes"] * info["i_per_thread"]
             for js in jsplits:
@@ -233,6 +235,10 @@ def main():
     ap.add_argument("--python", action="store_true",
                     help="time each configuration from Python and print it (default: the "
                          "library's nbody_tune)")
+    ap.add_argument("--tiles", type=int, nargs="+", default=None,
+                    help="with --python: only these tiles")
+    ap.add_argument("--jsplits", type=int, nargs="+", default=[0, 1, 2, 4, 8, 16, 32],
+                    help="with --python: the j-splits to time")
     a = ap.parse_args()
     if a.law == "batched":
         table = tune_batched(reps=a.reps)
@@ -243,7 +249,10 @@ def main():
     law = {"grav": LAW_GRAV, "ljc": LAW_LJC, "ljclin": LAW_LJC_LINEAR, "fixed": TABLE_GRAV_FIXED,
            "vjp": TABLE_VJP_GRAV, "vjpljc": TABLE_VJP_LJC, "vjpljclin": TABLE_VJP_LJC_LINEAR,
            "jerk": TABLE_JERK}[a.law]
-    table = tune(law, a.n, reps=a.reps, native=not a.python)
+    if (a.tiles is not None or a.jsplits != [0, 1, 2, 4, 8, 16, 32]) and not a.python:
+        ap.error("--tiles and --jsplits need --python")
+    table = tune(law, a.n, jsplits=tuple(a.jsplits), reps=a.reps, native=not a.python,
+                 tiles=a.tiles)
     print(json.dumps(table))
     if a.save:
         save_cache(law, table)
