@@ -370,9 +370,12 @@ enum {
                                   (one CTA each; 0: one part, other values rounded
                                   down). Softened gravity (eps2 > 0, without
                                   NBODY_NO_COMPENSATION) adds each block's partial
-                                  sums as 64-bit fixed point with integer atomics
-                                  into 32 bytes of scratch per particle (Sec. 3.2,
-                                  the GRAPE-6 scheme; bitwise reproducible); the
+                                  sums as fixed point with integer atomics (an
+                                  integer part and a 2^-32 fraction word per
+                                  component: every FP32 partial is added exactly,
+                                  whatever the softening; Sec. 3.2, the GRAPE-6
+                                  scheme; bitwise reproducible) into 64 bytes of
+                                  scratch per particle; the
                                   other cases keep one partial per particle and
                                   block, so the tile is refused (explicit tile) or
                                   replaced by the default tile (tuned) when those

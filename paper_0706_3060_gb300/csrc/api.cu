@@ -97,7 +97,7 @@ struct Scratch {
   float4 *jbuf;
   float4 *part_hi;
   float4 *part_lo;
-  long long *acc64;  // atomic plans: four int64 accumulators per particle
+  long long *acc64;  // atomic plans: eight int64 accumulators per particle
   double *diag_part;
   double *diag_rows;
 };
@@ -116,7 +116,7 @@ ScratchSizes scratch_sizes(int law, int n, const Plan1 &plan, int diag_rows) {
   ScratchSizes z{};
   const bool lo = !plan.atomic && (!plan.tile->sym || plan.tile->fixed);  // FX: int64 (z, w)
   const int64_t jn = plan.tile->sym ? int64_t(plan.slices) * plan.slice_len : n;
-  z.part = plan.atomic ? round_up(size_t(4) * size_t(n) * sizeof(long long), 256)
+  z.part = plan.atomic ? round_up(size_t(8) * size_t(n) * sizeof(long long), 256)
                        : round_up(size_t(plan.slices) * size_t(n) * sizeof(float4), 256);
   z.lopart = lo ? z.part : 0;
   const int nblk = std::max(1, (n + kFinThreads - 1) / kFinThreads);

@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(256) interleave_pairs_blocked_kernel(const flo
     if (at.acc64) {
       if (at.form_scale) am = fabs(double(a.w)) + fabs(double(b.w));
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < 8; ++c) {
         at.acc64[(long long)c * n + 2 * p] = 0;
         if (2 * p + 1 < n) at.acc64[(long long)c * n + 2 * p + 1] = 0;
       }

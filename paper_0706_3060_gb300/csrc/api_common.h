@@ -91,8 +91,8 @@ struct Plan1 {
   int grid;
   int sym_split;   // symmetric tiles: source parts per block (1 otherwise)
   bool atomic;     // symmetric gravity: per-block partials added with integer atomics
-                   // into one 64-bit fixed-point accumulator per particle (scratch
-                   // 32 bytes per particle) instead of one slot per block
+                   // into fixed-point accumulators per particle (scratch 64 bytes
+                   // per particle) instead of one slot per block
 };
 // allow_sym: the Newton-symmetric tiles may be used (targets are the sources
 // and the partials have room for one slot per block); otherwise a tuned
@@ -131,7 +131,7 @@ size_t jbuf_bytes(int law, int64_t n);
 // interleave launch before the force kernel zeroes, and the words from which that
 // launch forms the fixed-point scale (see interleave_pairs_blocked_kernel).
 struct AtomicPrep {
-  long long *acc64;  // 4 x n int64 accumulators (x, y, z, w)
+  long long *acc64;  // 8 x n int64 accumulators (integer parts and fractions of x, y, z, w)
   double *msum;      // one FP64 |m| sum per interleave block: ceil(n / 512) doubles
   unsigned *ticket;  // zero before the launch (the arena header); zero again after it
   float eps2;

@@ -75,12 +75,16 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
       if (f.fx_inv) {
         // 64-bit fixed-point partials: exact integer sum, one rounding at the end
         long long sx = 0, sy = 0, sz = 0, sw = 0;
+        // atomic plans: integer parts in words 0-3, fractions (units of 2^-32) in 4-7
+        long long fr[4] = {0, 0, 0, 0};
         if (f.acc64) {  // already summed by the force kernel's integer atomics
           const long long st = f.stride;
           sx = f.acc64[i];
           sy = f.acc64[st + i];
           sz = f.acc64[2 * st + i];
           sw = f.acc64[3 * st + i];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) fr[c] = f.acc64[(4 + c) * st + i];
         }
         auto take = [&](int k) {
           const long long *ph = reinterpret_cast<const long long *>(f.part_hi) +
@@ -96,9 +100,11 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
           for (int kb = 0; kb < own_b; ++kb) take(kb * sp + own_s);
           for (int k = k_all; k < slices; ++k) take(k);
         }
-        const double inv = *f.fx_inv;
-        const double dx = double(sx) * inv, dy = double(sy) * inv, dz = double(sz) * inv,
-                     dw = double(sw) * inv;
+        const double inv = *f.fx_inv, finv = inv * 0x1p-32;
+        const double dx = fma(double(fr[0]), finv, double(sx) * inv),
+                     dy = fma(double(fr[1]), finv, double(sy) * inv),
+                     dz = fma(double(fr[2]), finv, double(sz) * inv),
+                     dw = fma(double(fr[3]), finv, double(sw) * inv);
         t = make_float4(float(dx), float(dy), float(dz), float(dw));
         r = make_float4(float(dx - double(t.x)), float(dy - double(t.y)),
                         float(dz - double(t.z)), float(dw - double(t.w)));

@@ -37,8 +37,9 @@ struct FinalizeArgs {
   float4 *acc_lo;        // may be null
   float4 *trace_next;    // positions after the drift, or null
   const double *fx_inv;  // fixed-point partials (int64): value = sum * (*fx_inv); else null
-  // fixed-point accumulators of atomic plans (four int64 arrays x, y, z, w of
-  // stride `stride`, one element per particle; with fx_inv), else null
+  // fixed-point accumulators of atomic plans (eight int64 arrays of stride
+  // `stride`, one element per particle: the integer parts of x, y, z, w, then
+  // their fractions in units of 2^-32; with fx_inv), else null
   const long long *acc64;
   float4 *x_lo;          // compensated state: low parts of x and v, or null
   float4 *v_lo;

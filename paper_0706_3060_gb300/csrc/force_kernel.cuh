@@ -75,10 +75,10 @@ struct ForceArgs {
   int *counter;        // null: single-system mode
   int comp;            // 1: compensated (hi, lo) sums per j-tile
   const float *fscale; // fixed-point kernels: device word holding the scale 2^S
-  // Newton-symmetric gravity with atomic accumulation: four int64 arrays
-  // (x, y, z, w) of stride `stride`, zeroed before the launch, into which every
-  // CTA adds its per-block partials rounded onto the fixed-point grid *fscale;
-  // null: per-block partial slots in part_hi / part_lo
+  // Newton-symmetric gravity with atomic accumulation: eight int64 arrays of
+  // stride `stride` (integer parts of x, y, z, w scaled by *fscale, then their
+  // fractions in units of 2^-32), zeroed before the launch, into which every CTA
+  // adds its per-block partials; null: per-block partial slots in part_hi / part_lo
   long long *acc64;
 };
 

@@ -31,11 +31,12 @@
 // b and part s_p receives every slot k with k / S >= b and, below that, those with
 // k % S == s_p; the finalize kernel skips the rest. S = 1 is the plain scheme.
 // Atomic accumulation (a.acc64 set; gravity with eps > 0, Sec. 3.2's GRAPE-6
-// scheme): each partial is rounded onto the 64-bit fixed-point grid 2^S (S from
-// *a.fscale, chosen from an a-priori bound on every sum) and added with integer
-// atomics into one accumulator per particle; integer addition is associative,
-// so the result does not depend on the order of the CTAs, and the scratch is
-// 32 bytes per particle instead of one partial per particle and block.
+// scheme): each partial, scaled by 2^S (S from *a.fscale, chosen from an a-priori
+// bound on every sum), is added with integer atomics as an integer part and a
+// fraction in units of 2^-32 into two int64 words per component and particle;
+// integer addition is associative, so the result does not depend on the order of
+// the CTAs, and the scratch is 64 bytes per particle instead of one partial per
+// particle and block.
 // FX without a.acc64: each partial is stored as four int64 in its slot, (x, y)
 // in part_hi and (z, w) in part_lo, which the finalize adds as integers.
 #pragma once
@@ -84,10 +85,23 @@ __device__ __forceinline__ void sym_store(const ForceArgs &a, long long slot_bas
     const float sc = __ldg(a.fscale);
     unsigned long long *p = reinterpret_cast<unsigned long long *>(a.acc64) + particle;
     const long long st = a.stride;
-    atomicAdd(p, static_cast<unsigned long long>(__float2ll_rn(x * sc)));
-    atomicAdd(p + st, static_cast<unsigned long long>(__float2ll_rn(y * sc)));
-    atomicAdd(p + 2 * st, static_cast<unsigned long long>(__float2ll_rn(z * sc)));
-    if (POT) atomicAdd(p + 3 * st, static_cast<unsigned long long>(__float2ll_rn(w * sc)));
+    // v 2^S split into its integer part (word c) and its fraction in units of 2^-32
+    // (word 4 + c): both exact for an FP32 partial (to 2^-(S+32)), so the integer
+    // sums are exact whatever the softening makes of the grid spacing 2^-S; the
+    // fraction word is touched only when the fraction is nonzero
+    auto add = [&](float v, int c) {
+      const float t = v * sc;      // exact: sc is a power of two
+      const float h = truncf(t);   // integer part, |h| < 2^62
+      atomicAdd(p + c * st, static_cast<unsigned long long>(static_cast<long long>(h)));
+      if (fabsf(t) < 16777216.0f) {  // from 2^24 on an FP32 value has no fraction bits
+        const long long lo = __float2ll_rn((t - h) * 4294967296.0f);  // t - h is exact
+        if (lo != 0) atomicAdd(p + (4 + c) * st, static_cast<unsigned long long>(lo));
+      }
+    };
+    add(x, 0);
+    add(y, 1);
+    add(z, 2);
+    if (POT) add(w, 3);
     return;
   }
   const long long idx = slot_base + particle;
