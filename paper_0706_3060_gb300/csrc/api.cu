@@ -154,16 +154,21 @@ int get_scratch(cudaStream_t s, int law, int n, const Plan1 &plan, int diag_rows
 // One force evaluation into scratch partials, then one finalize launch.
 // first_eval: the first evaluation of this call (atomic plans form the
 // fixed-point scale there; the masses do not change between the steps of a call).
+// sources_ready: the previous finalize of this call wrote the pair-interleaved
+// sources (no interleave launch). prepare_next: this finalize drifts (kFinKickDrift)
+// and writes them for the next evaluation; returns in *prepared whether it did.
 int eval_and_finalize(const float4 *pos, const float4 *prm, const nbody_params &p, int n,
                       const Plan1 &plan, const Scratch &sc, int *err, bool pot,
-                      FinalizeArgs f, cudaStream_t s, int *nblk, bool first_eval) {
+                      FinalizeArgs f, cudaStream_t s, int *nblk, bool first_eval,
+                      bool sources_ready = false, bool prepare_next = false,
+                      bool *prepared = nullptr) {
   const bool fx = (p.flags & NBODY_FIXED_POINT) != 0 || plan.atomic;
   const AtomicPrep at{sc.acc64, sc.msum, sc.ticket, p.eps2, sc.fscale, sc.finv,
                       first_eval ? 1 : 0};
   NB_TRY(launch_forces(pos, prm, p.law, p.flags, p.eps2, n, plan, sc.part_hi, sc.part_lo,
                        sc.jbuf, err, pot, s, nullptr,
                        (fx && !plan.atomic) ? sc.fscale : nullptr,
-                       plan.atomic ? &at : nullptr));
+                       plan.atomic ? &at : nullptr, true, sources_ready));
   f.fx_inv = fx ? sc.finv : nullptr;
   f.acc64 = sc.acc64;
   f.part_hi = sc.part_hi;
@@ -179,6 +184,12 @@ int eval_and_finalize(const float4 *pos, const float4 *prm, const nbody_params &
   f.G = p.G;
   f.diag_part = sc.diag_part;
   f.plain = (p.flags & NBODY_NO_COMPENSATION) ? 1 : 0;
+  const bool prep = prepare_next && plan.tile->packed && (f.mode & kFinKickDrift);
+  f.jnext = prep ? sc.jbuf : nullptr;
+  f.jn_block = plan.tile->sym ? plan.tile->tile_i : 0;
+  f.jn_words = p.law == NBODY_LAW_GRAV ? 2 : 3;
+  f.rezero = (prep && plan.atomic) ? 1 : 0;
+  if (prepared) *prepared = prep;
   return launch_finalize(f, s, nblk);
 }
 
@@ -226,6 +237,7 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
                                      cudaMemcpyDeviceToDevice, s));
   int row = 0;
   bool first_eval = true;  // the fixed-point scale of atomic plans is formed once per call
+  bool ready = false;      // the last finalize wrote the next evaluation's source pairs
   FinalizeArgs f{};
   f.pos = pos;
   f.vel = vel;
@@ -240,7 +252,8 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
     f.mode = kFinWriteAcc | (report(0) ? kFinDiag : 0) | (nsteps > 0 ? kFinKickDrift : 0);
     f.trace_next = (trace && nsteps > 0) ? trace + size_t(n) : nullptr;
     NB_TRY(eval_and_finalize(pos, prm, p, n, plan, sc, err,
-                             report(0) || (nsteps == 0 && want_pot), f, s, &nblk, first_eval));
+                             report(0) || (nsteps == 0 && want_pot), f, s, &nblk, first_eval,
+                             false, nsteps > 0, &ready));
     first_eval = false;
     if (report(0)) NB_TRY(launch_diag_reduce(sc.diag_part, nblk, sc.diag_rows + kDiagFields * row++, s));
   } else if (nsteps > 0) {
@@ -254,7 +267,7 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
     f.mode = kFinWriteAcc | kFinKickSync | (rep ? kFinDiag : 0) | (last ? 0 : kFinKickDrift);
     f.trace_next = (trace && !last) ? trace + size_t(st + 1) * size_t(n) : nullptr;
     NB_TRY(eval_and_finalize(pos, prm, p, n, plan, sc, err, rep || (last && want_pot), f, s,
-                             &nblk, first_eval));
+                             &nblk, first_eval, ready, !last, &ready));
     first_eval = false;
     if (rep) NB_TRY(launch_diag_reduce(sc.diag_part, nblk, sc.diag_rows + kDiagFields * row++, s));
   }

@@ -567,7 +567,8 @@ size_t jbuf_bytes(int law, int64_t n) {
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
                   int *err, bool pot, cudaStream_t s, const Targets *tg,
-                  const float *fscale, const AtomicPrep *at, bool timed) {
+                  const float *fscale, const AtomicPrep *at, bool timed,
+                  bool sources_ready) {
   const bool atomic = at && at->acc64;
   if (p.atomic != atomic || (atomic && (law != NBODY_LAW_GRAV || tg || !at->msum ||
                                         !at->ticket || !at->scale || !at->inv)))
@@ -575,7 +576,10 @@ int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags,
   if (atomic) fscale = at->scale;
   if ((p.tile->fixed || p.atomic) != (fscale != nullptr))
     return set_error_msg(NBODY_EINVAL, "fixed-point tile and scale must come together");
-  if (p.tile->packed) {
+  if (sources_ready && (!p.tile->packed || tg || (atomic && at->form_scale)))
+    return set_error_msg(NBODY_EINVAL, "prepared sources need a packed tile, all targets "
+                                       "and a formed scale");
+  if (p.tile->packed && !sources_ready) {
     if (!jbuf) return set_error_msg(NBODY_EINVAL, "packed tile without pair buffer");
     const int np = (n + 1) / 2;
     if ((law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR) && p.tile->sym)

@@ -146,11 +146,14 @@ struct AtomicPrep {
 // (atomic plans take theirs from `at`). at: required exactly for atomic plans.
 // timed: bracket the force kernel with the kernel timers when they are enabled (they
 // create CUDA events on first use; the allocation-free entry point passes false).
+// sources_ready: jbuf already holds the pair-interleaved sources at `pos` (and an
+// atomic plan's accumulators are zero), written by the previous step's finalize:
+// no interleave launch.
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
                   int *err, bool pot, cudaStream_t s, const Targets *tg = nullptr,
                   const float *fscale = nullptr, const AtomicPrep *at = nullptr,
-                  bool timed = true);
+                  bool timed = true, bool sources_ready = false);
 
 size_t round_up(size_t x, size_t a);
 

@@ -46,6 +46,7 @@ __device__ __forceinline__ void comp_axpy(float4 &hi, float4 &lo, float c, const
 __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArgs f) {
   const int i = blockIdx.x * kFinThreads + threadIdx.x;
   double dv[kDiagFields] = {0, 0, 0, 0, 0, 0, 0, 0};
+  float4 xn = make_float4(1e18f, 1e18f, 1e18f, 0.0f);  // drifted position (pad: far away)
   if (i < f.n) {
     int law = f.law, slices = f.slices;
     float G = f.G, dt = f.dt;
@@ -85,6 +86,10 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
           sw = f.acc64[3 * st + i];
 #pragma unroll
           for (int c = 0; c < 4; ++c) fr[c] = f.acc64[(4 + c) * st + i];
+          if (f.rezero) {  // ready for the next evaluation of this call
+#pragma unroll
+            for (int c = 0; c < 8; ++c) f.acc64[c * st + i] = 0;
+          }
         }
         auto take = [&](int k) {
           const long long *ph = reinterpret_cast<const long long *>(f.part_hi) +
@@ -221,6 +226,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
             x.z = fmaf(dt, v.z, x.z);
           }
           f.pos[i] = x;
+          xn = x;
           if (f.trace_next) f.trace_next[i] = x;
         }
         f.vel[i] = v;
@@ -228,6 +234,32 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
           f.x_lo[i] = xl;
           f.v_lo[i] = vl;
         }
+      }
+    }
+  }
+  if (f.jnext) {  // the same for every thread of the launch
+    // particles 2p and 2p + 1 are neighbouring lanes: exchange positions, then the
+    // even lane writes the pair's (x x y y) word and the odd lane the (z z) half of
+    // its second word (the even lane as well when its partner is the pad past n)
+    const float px = __shfl_xor_sync(0xffffffffu, xn.x, 1);
+    const float py = __shfl_xor_sync(0xffffffffu, xn.y, 1);
+    const float pz = __shfl_xor_sync(0xffffffffu, xn.z, 1);
+    if (i < f.n) {
+      const int p = i >> 1;
+      long long q0, q1;
+      if (f.jn_block > 0) {
+        const int half = f.jn_block / 2, blk = p / half, pp = p - blk * half;
+        q0 = (long long)blk * f.jn_words * half + pp;
+        q1 = q0 + half;
+      } else {
+        q0 = (long long)f.jn_words * p;
+        q1 = q0 + 1;
+      }
+      if ((i & 1) == 0) {
+        f.jnext[q0] = make_float4(xn.x, px, xn.y, py);
+        if (i + 1 >= f.n) *reinterpret_cast<float2 *>(f.jnext + q1) = make_float2(xn.z, pz);
+      } else {
+        *reinterpret_cast<float2 *>(f.jnext + q1) = make_float2(pz, xn.z);
       }
     }
   }

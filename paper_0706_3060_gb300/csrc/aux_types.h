@@ -40,7 +40,7 @@ struct FinalizeArgs {
   // fixed-point accumulators of atomic plans (eight int64 arrays of stride
   // `stride`, one element per particle: the integer parts of x, y, z, w, then
   // their fractions in units of 2^-32; with fx_inv), else null
-  const long long *acc64;
+  long long *acc64;
   float4 *x_lo;          // compensated state: low parts of x and v, or null
   float4 *v_lo;
   int mode;
@@ -53,6 +53,16 @@ struct FinalizeArgs {
   // 1: add the slots in plain FP32 (NBODY_NO_COMPENSATION); 0: compensated
   // (TwoSum into a high and a low part).
   int plain;
+  // Steps of nbody_step: with kFinKickDrift, also write the drifted positions
+  // into the pair-interleaved source copy that the next force evaluation reads
+  // (null: none), so that it needs no interleave launch. jn_block: block size of
+  // the blocked layout of the symmetric tiles (0: one source pair after another);
+  // jn_words: float4 words per source pair (2 gravity, 3 LJC); only each pair's
+  // (x x y y) word and the (z z) half of its second word change.
+  float4 *jnext;
+  int jn_block;
+  int jn_words;
+  int rezero;  // atomic plans: zero the accumulators after reading them
 };
 
 constexpr int kFinThreads = 64;  // many CTAs: the finalize is latency-bound at small n
