@@ -296,8 +296,9 @@ def main():
         if mh and mb and mh.group(1) == kernel_hash():
             roof["traffic"] = int(mb.group(1))
 
-    # kernels per timed step: kick-drift, [pair interleave,] force, finalize(+kick)
-    per_step = 3 + int(tinfo["packed"])
+    # kernels per timed step: kick-drift (fused into the pair interleave of packed
+    # tiles), force, finalize(+kick)
+    per_step = 3
     out = {"metric": metric_name(), "value": value, "unit": "G pair-interactions/s",
            "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": step_ms / K,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -706,6 +707,11 @@ def secondary_kernel_extras(nb, torch, dev, pos, eps):
     out["ljc_linear_8192_back_to_back_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
     ms = _graph_ms(torch, lambda: nb.forces(lpos, prm_lin, law=nb.LAW_LJC_LINEAR, out=lacc))
     out["ljc_linear_8192_graph_gpairs_per_s"] = 8192.0 ** 2 / ms / 1e6
+    # 20 leapfrog steps in one call (one force and one finalize launch per step
+    # after the first), from a copy of the sphere at rest
+    lp, lv = lpos.clone(), torch.zeros_like(lpos)
+    ms = _device_ms(torch, lambda: nb.step(lp, lv, lacc, prm, dt=1e-5, nsteps=20))
+    out["ljc_8192_step20_gpairs_per_s"] = 20 * 8192.0 ** 2 / ms / 1e6
     lam = torch.randn_like(lpos)
     lgx, lgm = torch.empty_like(lpos), torch.empty(lpos.shape[0], device=dev)
     lgt = torch.zeros(8, dtype=torch.float64, device=dev)
@@ -727,8 +733,9 @@ def secondary_kernel_extras(nb, torch, dev, pos, eps):
 
 def size_sweep_extras(nb, torch, dev, sizes=(16384, 65536, 262144, 1048576)):
     """One force evaluation (tuned tile, device time) on seeded Plummer spheres of each
-    size with softening 0.04 N^(-1/3); at the largest size, the error of 256 sampled
-    targets against the FP64 oracle."""
+    size with softening 0.04 N^(-1/3); at the smallest size also 20 leapfrog steps in
+    one call; at the largest size, the error of 256 sampled targets against the FP64
+    oracle."""
     import oracle
     import workloads
     rate, err = {}, {}
@@ -739,6 +746,10 @@ def size_sweep_extras(nb, torch, dev, sizes=(16384, 65536, 262144, 1048576)):
         p = torch.from_numpy(np.concatenate([x, m[:, None]], 1)).to(dev).contiguous()
         ms = _device_ms(torch, lambda: nb.forces(p, eps=e32), reps=3)
         rate[str(n)] = float(n) ** 2 / ms / 1e6
+        if n == sizes[0]:  # 20 leapfrog steps in one call at the smallest size
+            pv, v0, a0 = p.clone(), torch.zeros_like(p), torch.empty_like(p)
+            ms = _device_ms(torch, lambda: nb.step(pv, v0, a0, dt=1e-5, nsteps=20, eps=e32))
+            steps20 = {"n": n, "gpairs_per_s": 20 * float(n) ** 2 / ms / 1e6}
         if n == sizes[-1]:
             a = nb.forces(p, eps=e32).cpu().numpy()
             idx = np.sort(np.random.default_rng(7).choice(n, 256, replace=False))
@@ -747,7 +758,8 @@ def size_sweep_extras(nb, torch, dev, sizes=(16384, 65536, 262144, 1048576)):
             err = {"n": n, "rms": float(np.sqrt(np.mean(e * e))), "max": float(e.max()),
                    "sample": "256 seeded targets vs FP64 oracle"}
         del p
-    return {"forces_gpairs_per_s_by_n": rate, "force_err_largest_n": err}
+    return {"forces_gpairs_per_s_by_n": rate, "force_err_largest_n": err,
+            "step20_smallest_n": steps20}
 
 
 def _ensemble_arrays(nb, torch, dev, ens):

@@ -93,6 +93,7 @@ struct Scratch {
   float *fscale;  // fixed-point scale (device word) and its inverse: arena header
   double *finv;
   unsigned *ticket;  // atomic plans: last-block ticket of the scale's mass sum (header)
+  unsigned *diag_ticket;  // last-block ticket of the finalize's diagnostics sum (header)
   double *msum;      // atomic plans: per-block |m| sums of the interleave launch
   float4 *jbuf;
   float4 *part_hi;
@@ -139,6 +140,7 @@ int get_scratch(cudaStream_t s, int law, int n, const Plan1 &plan, int diag_rows
   out->finv = reinterpret_cast<double *>(hdr);
   out->fscale = reinterpret_cast<float *>(hdr + 8);
   out->ticket = reinterpret_cast<unsigned *>(hdr + 16);
+  out->diag_ticket = reinterpret_cast<unsigned *>(hdr + 20);
   char *b = static_cast<char *>(base);
   out->msum = plan.atomic ? reinterpret_cast<double *>(b + z.body() - z.msum) : nullptr;
   out->jbuf = reinterpret_cast<float4 *>(b);
@@ -157,18 +159,19 @@ int get_scratch(cudaStream_t s, int law, int n, const Plan1 &plan, int diag_rows
 // sources_ready: the previous finalize of this call wrote the pair-interleaved
 // sources (no interleave launch). prepare_next: this finalize drifts (kFinKickDrift)
 // and writes them for the next evaluation; returns in *prepared whether it did.
+// kd: a first half-kick and drift that the interleave launch applies (packed tiles).
 int eval_and_finalize(const float4 *pos, const float4 *prm, const nbody_params &p, int n,
                       const Plan1 &plan, const Scratch &sc, int *err, bool pot,
                       FinalizeArgs f, cudaStream_t s, int *nblk, bool first_eval,
                       bool sources_ready = false, bool prepare_next = false,
-                      bool *prepared = nullptr) {
+                      bool *prepared = nullptr, const KickDrift *kd = nullptr) {
   const bool fx = (p.flags & NBODY_FIXED_POINT) != 0 || plan.atomic;
   const AtomicPrep at{sc.acc64, sc.msum, sc.ticket, p.eps2, sc.fscale, sc.finv,
                       first_eval ? 1 : 0};
   NB_TRY(launch_forces(pos, prm, p.law, p.flags, p.eps2, n, plan, sc.part_hi, sc.part_lo,
                        sc.jbuf, err, pot, s, nullptr,
                        (fx && !plan.atomic) ? sc.fscale : nullptr,
-                       plan.atomic ? &at : nullptr, true, sources_ready));
+                       plan.atomic ? &at : nullptr, true, sources_ready, kd));
   f.fx_inv = fx ? sc.finv : nullptr;
   f.acc64 = sc.acc64;
   f.part_hi = sc.part_hi;
@@ -189,6 +192,7 @@ int eval_and_finalize(const float4 *pos, const float4 *prm, const nbody_params &
   f.jn_block = plan.tile->sym ? plan.tile->tile_i : 0;
   f.jn_words = p.law == NBODY_LAW_GRAV ? 2 : 3;
   f.rezero = (prep && plan.atomic) ? 1 : 0;
+  f.diag_ticket = sc.diag_ticket;
   if (prepared) *prepared = prep;
   return launch_finalize(f, s, nblk);
 }
@@ -246,30 +250,39 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
   f.dt = dt;
   f.x_lo = state_lo;
   f.v_lo = state_lo ? state_lo + n : nullptr;
+  // Launches: one force evaluation and one finalize per step. The finalize also
+  // sums the diagnostics of a report step, and (all but the last step) drifts the
+  // positions and writes them into the next evaluation's source copy; the first
+  // half-kick from a caller's acceleration rides on the interleave launch.
   // Step 0: a(x_0) from the caller or from one evaluation; then kick + drift.
+  KickDrift kd{pos, vel, acc, trace ? trace + size_t(n) : nullptr, f.x_lo, f.v_lo, dt};
+  bool kd_pending = false;  // the first evaluation's interleave launch applies kd
   if (!(p.flags & NBODY_ACC_VALID) || report(0)) {
-    int nblk = 0;
     f.mode = kFinWriteAcc | (report(0) ? kFinDiag : 0) | (nsteps > 0 ? kFinKickDrift : 0);
     f.trace_next = (trace && nsteps > 0) ? trace + size_t(n) : nullptr;
+    f.diag_out = report(0) ? sc.diag_rows + kDiagFields * row++ : nullptr;
     NB_TRY(eval_and_finalize(pos, prm, p, n, plan, sc, err,
-                             report(0) || (nsteps == 0 && want_pot), f, s, &nblk, first_eval,
+                             report(0) || (nsteps == 0 && want_pot), f, s, nullptr, first_eval,
                              false, nsteps > 0, &ready));
     first_eval = false;
-    if (report(0)) NB_TRY(launch_diag_reduce(sc.diag_part, nblk, sc.diag_rows + kDiagFields * row++, s));
   } else if (nsteps > 0) {
-    NB_TRY(launch_kick_drift(pos, vel, acc, n, dt, trace ? trace + size_t(n) : nullptr, nullptr,
-                             nullptr, f.x_lo, f.v_lo, s));
+    if (plan.tile->packed)
+      kd_pending = true;
+    else
+      NB_TRY(launch_kick_drift(pos, vel, acc, n, dt, kd.trace1, nullptr, nullptr, f.x_lo,
+                               f.v_lo, s));
   }
   for (int st = 1; st <= nsteps; ++st) {
     const bool rep = report(st);
     const bool last = (st == nsteps);
-    int nblk = 0;
     f.mode = kFinWriteAcc | kFinKickSync | (rep ? kFinDiag : 0) | (last ? 0 : kFinKickDrift);
     f.trace_next = (trace && !last) ? trace + size_t(st + 1) * size_t(n) : nullptr;
+    f.diag_out = rep ? sc.diag_rows + kDiagFields * row++ : nullptr;
     NB_TRY(eval_and_finalize(pos, prm, p, n, plan, sc, err, rep || (last && want_pot), f, s,
-                             &nblk, first_eval, ready, !last, &ready));
+                             nullptr, first_eval, ready, !last, &ready,
+                             kd_pending ? &kd : nullptr));
     first_eval = false;
-    if (rep) NB_TRY(launch_diag_reduce(sc.diag_part, nblk, sc.diag_rows + kDiagFields * row++, s));
+    kd_pending = false;
   }
   if (rows > 0)
     NB_CUDA(cudaMemcpyAsync(diag_dev, sc.diag_rows, size_t(rows) * kDiagFields * sizeof(double),

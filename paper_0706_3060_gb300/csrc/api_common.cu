@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "api_common.h"
+#include "leapfrog.cuh"
 #include "vjp_tiles.h"
 
 namespace nbody {
@@ -449,14 +450,22 @@ int plan_targets(int law, int64_t n_t, int64_t n, int tile, int jsplit, int sms,
   return NBODY_OK;
 }
 
+// Position of particle i for the interleave kernels: read, or (kd.vel set) first
+// kicked and drifted in place.
+__device__ __forceinline__ float4 source_at(const float4 *pos, const KickDrift &kd, int i) {
+  return kd.vel ? kick_drift_at(kd.pos, kd.vel, kd.acc, kd.dt, kd.trace1, kd.x_lo, kd.v_lo, i)
+                : pos[i];
+}
+
 // Sources in pairs: jp[2p] = (x0, x1, y0, y1), jp[2p+1] = (z0, z1, m0, m1) for
 // particles 2p, 2p+1; an odd count is padded with a massless particle far away
 // (its pair terms are exactly zero).
-__global__ void interleave_pairs_kernel(const float4 *pos, float4 *jp, int n) {
+__global__ void interleave_pairs_kernel(const float4 *pos, float4 *jp, int n, KickDrift kd) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (2 * p >= n) return;
-  const float4 a = pos[2 * p];
-  const float4 b = (2 * p + 1 < n) ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+  const float4 a = source_at(pos, kd, 2 * p);
+  const float4 b =
+      (2 * p + 1 < n) ? source_at(pos, kd, 2 * p + 1) : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
   jp[2 * p] = make_float4(a.x, b.x, a.y, b.y);
   jp[2 * p + 1] = make_float4(a.z, b.z, a.w, b.w);
 }
@@ -472,13 +481,14 @@ __global__ void interleave_pairs_kernel(const float4 *pos, float4 *jp, int n) {
 // in index order and writes the scale -- the same bits whichever block is last.
 __global__ void __launch_bounds__(256) interleave_pairs_blocked_kernel(const float4 *pos,
                                                                        float4 *jp, int n, int B,
-                                                                       AtomicPrep at) {
+                                                                       AtomicPrep at,
+                                                                       KickDrift kd) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   double am = 0.0;
   if (2 * p < n) {
-    const float4 a = pos[2 * p];
-    const float4 b =
-        (2 * p + 1 < n) ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+    const float4 a = source_at(pos, kd, 2 * p);
+    const float4 b = (2 * p + 1 < n) ? source_at(pos, kd, 2 * p + 1)
+                                     : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
     const int blk = (2 * p) / B, pp = p - blk * (B / 2);
     const long long base = (long long)blk * B;
     jp[base + pp] = make_float4(a.x, b.x, a.y, b.y);
@@ -529,12 +539,12 @@ __global__ void __launch_bounds__(256) interleave_pairs_blocked_kernel(const flo
 // per block): the B/2 pairs' (x0 x1 y0 y1), then (z0 z1 q0 q1), then
 // (s0 s1 e0 e1). Pairs past n are not written.
 __global__ void interleave_ljc_pairs_blocked_kernel(const float4 *pos, const float4 *prm,
-                                                    float4 *jp, int n, int B) {
+                                                    float4 *jp, int n, int B, KickDrift kd) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (2 * p >= n) return;
-  const float4 a = pos[2 * p], qa = prm[2 * p];
+  const float4 a = source_at(pos, kd, 2 * p), qa = prm[2 * p];
   const bool two = 2 * p + 1 < n;
-  const float4 b = two ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+  const float4 b = two ? source_at(pos, kd, 2 * p + 1) : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
   const float4 qb = two ? prm[2 * p + 1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const int blk = (2 * p) / B, P = B / 2, pp = p - blk * P;
   const long long q = (long long)blk * 3 * P + pp;
@@ -546,12 +556,12 @@ __global__ void interleave_ljc_pairs_blocked_kernel(const float4 *pos, const flo
 // LJC sources in pairs: (x0, x1, y0, y1), (z0, z1, q0, q1), (s0, s1, e0, e1); the
 // pad of an odd count is far away with no charge and no LJ well.
 __global__ void interleave_ljc_pairs_kernel(const float4 *pos, const float4 *prm, float4 *jp,
-                                            int n) {
+                                            int n, KickDrift kd) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (2 * p >= n) return;
-  const float4 a = pos[2 * p], qa = prm[2 * p];
+  const float4 a = source_at(pos, kd, 2 * p), qa = prm[2 * p];
   const bool two = 2 * p + 1 < n;
-  const float4 b = two ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+  const float4 b = two ? source_at(pos, kd, 2 * p + 1) : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
   const float4 qb = two ? prm[2 * p + 1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const long long q = 3LL * p;  // 64-bit: 3p passes 2^31 for n above ~1.4e9
   jp[q] = make_float4(a.x, b.x, a.y, b.y);
@@ -568,7 +578,7 @@ int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
                   int *err, bool pot, cudaStream_t s, const Targets *tg,
                   const float *fscale, const AtomicPrep *at, bool timed,
-                  bool sources_ready) {
+                  bool sources_ready, const KickDrift *kd) {
   const bool atomic = at && at->acc64;
   if (p.atomic != atomic || (atomic && (law != NBODY_LAW_GRAV || tg || !at->msum ||
                                         !at->ticket || !at->scale || !at->inv)))
@@ -579,19 +589,23 @@ int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags,
   if (sources_ready && (!p.tile->packed || tg || (atomic && at->form_scale)))
     return set_error_msg(NBODY_EINVAL, "prepared sources need a packed tile, all targets "
                                        "and a formed scale");
+  if (kd && (!p.tile->packed || tg || sources_ready || kd->pos != pos || !kd->vel || !kd->acc))
+    return set_error_msg(NBODY_EINVAL, "a fused kick-drift needs a packed tile, all targets "
+                                       "and the evaluation's own positions");
   if (p.tile->packed && !sources_ready) {
     if (!jbuf) return set_error_msg(NBODY_EINVAL, "packed tile without pair buffer");
     const int np = (n + 1) / 2;
+    const KickDrift k = kd ? *kd : KickDrift{};
     if ((law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR) && p.tile->sym)
       interleave_ljc_pairs_blocked_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, prm, jbuf, n,
-                                                                           p.tile->tile_i);
+                                                                           p.tile->tile_i, k);
     else if (law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR)
-      interleave_ljc_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, prm, jbuf, n);
+      interleave_ljc_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, prm, jbuf, n, k);
     else if (p.tile->sym)
       interleave_pairs_blocked_kernel<<<(np + 255) / 256, 256, 0, s>>>(
-          pos, jbuf, n, p.tile->tile_i, atomic ? *at : AtomicPrep{});
+          pos, jbuf, n, p.tile->tile_i, atomic ? *at : AtomicPrep{}, k);
     else
-      interleave_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, jbuf, n);
+      interleave_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, jbuf, n, k);
     NB_CUDA(cudaGetLastError());
   }
   ForceArgs a{};

@@ -141,6 +141,20 @@ struct AtomicPrep {
                      // same call did (same masses and eps), *scale and *inv hold it
 };
 
+// First half-kick and drift that the interleave launch applies before it copies
+// the sources (a leapfrog step from a known acceleration, NBODY_ACC_VALID): pos
+// (the evaluation's positions, drifted in place), vel, acc, the two-float low
+// parts (or null) and the trace row of the drifted positions (or null).
+struct KickDrift {
+  float4 *pos;
+  float4 *vel;
+  const float4 *acc;
+  float4 *trace1;
+  float4 *x_lo;
+  float4 *v_lo;
+  float dt;
+};
+
 // jbuf: scratch of jbuf_bytes(law, n) for the pair-interleaved sources of packed tiles.
 // fscale: device word with the fixed-point scale, required exactly for fixed tiles
 // (atomic plans take theirs from `at`). at: required exactly for atomic plans.
@@ -148,12 +162,15 @@ struct AtomicPrep {
 // create CUDA events on first use; the allocation-free entry point passes false).
 // sources_ready: jbuf already holds the pair-interleaved sources at `pos` (and an
 // atomic plan's accumulators are zero), written by the previous step's finalize:
-// no interleave launch.
+// no interleave launch. kd: the interleave launch first applies this kick-drift to
+// the positions at `pos` (kd->pos == pos; packed tiles, all targets, not with
+// sources_ready).
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
                   int *err, bool pot, cudaStream_t s, const Targets *tg = nullptr,
                   const float *fscale = nullptr, const AtomicPrep *at = nullptr,
-                  bool timed = true, bool sources_ready = false);
+                  bool timed = true, bool sources_ready = false,
+                  const KickDrift *kd = nullptr);
 
 size_t round_up(size_t x, size_t a);
 

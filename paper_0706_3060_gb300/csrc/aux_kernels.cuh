@@ -9,6 +9,7 @@
 
 #include "aux_types.h"
 #include "device_common.cuh"
+#include "leapfrog.cuh"
 
 namespace nbody {
 
@@ -28,19 +29,6 @@ __device__ __forceinline__ void block_sum8(double v[kDiagFields], double *out) {
     for (int w = 0; w < kFinThreads / 32; ++w) s += red[w][threadIdx.x];
     out[threadIdx.x] = s;
   }
-}
-
-// Two-float state update (hi, lo) += c * d on xyz: the increment and the old
-// low part are added first, then TwoSum splits the new value into the nearest
-// float and its exact residual, so rounding does not accumulate over steps.
-__device__ __forceinline__ void comp_axpy(float4 &hi, float4 &lo, float c, const float4 d) {
-  float e;
-  two_sum(hi.x, fmaf(c, d.x, lo.x), hi.x, e);
-  lo.x = e;
-  two_sum(hi.y, fmaf(c, d.y, lo.y), hi.y, e);
-  lo.y = e;
-  two_sum(hi.z, fmaf(c, d.z, lo.z), hi.z, e);
-  lo.z = e;
 }
 
 __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArgs f) {
@@ -263,7 +251,24 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
       }
     }
   }
-  if (f.mode & kFinDiag) block_sum8(dv, f.diag_part + (size_t)blockIdx.x * kDiagFields);
+  if (!(f.mode & kFinDiag)) return;
+  block_sum8(dv, f.diag_part + (size_t)blockIdx.x * kDiagFields);
+  if (!f.diag_out) return;  // the same for every thread of the launch
+  // The block that finishes last (atomicInc ticket, which wraps back to zero) adds
+  // the block rows as diag_reduce_kernel does: the same bits whichever block it is.
+  __shared__ bool last;
+  __threadfence();  // this block's row is visible before its ticket is taken
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicInc(f.diag_ticket, gridDim.x - 1) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v[kDiagFields] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const volatile double *rows = f.diag_part;
+  for (int b = threadIdx.x; b < int(gridDim.x); b += kFinThreads)
+#pragma unroll
+    for (int k = 0; k < kDiagFields; ++k) v[k] += rows[(size_t)b * kDiagFields + k];
+  block_sum8(v, f.diag_out);
 }
 
 // Scale of the fixed-point mode (fixed_scale_of) for the one-sided fixed-point
@@ -305,27 +310,7 @@ __global__ void kick_drift_kernel(float4 *pos, float4 *vel, const float4 *acc, i
     if (s < 0) return;
     dt = sys[s].dt;
   }
-  float4 x = pos[i], v = vel[i];
-  const float4 a = acc[i];
-  const float h = 0.5f * dt;
-  if (x_lo) {
-    float4 xl = x_lo[i], vl = v_lo[i];
-    comp_axpy(v, vl, h, a);
-    const float4 vv = make_float4(v.x + vl.x, v.y + vl.y, v.z + vl.z, 0.f);
-    comp_axpy(x, xl, dt, vv);
-    x_lo[i] = xl;
-    v_lo[i] = vl;
-  } else {
-    v.x = fmaf(h, a.x, v.x);
-    v.y = fmaf(h, a.y, v.y);
-    v.z = fmaf(h, a.z, v.z);
-    x.x = fmaf(dt, v.x, x.x);
-    x.y = fmaf(dt, v.y, x.y);
-    x.z = fmaf(dt, v.z, x.z);
-  }
-  pos[i] = x;
-  vel[i] = v;
-  if (trace1) trace1[i] = x;
+  kick_drift_at(pos, vel, acc, dt, trace1, x_lo, v_lo, i);
 }
 
 __global__ void copy_float4_kernel(const float4 *src, float4 *dst, int n) {

@@ -63,6 +63,11 @@ struct FinalizeArgs {
   int jn_block;
   int jn_words;
   int rezero;  // atomic plans: zero the accumulators after reading them
+  // With kFinDiag: also add the block rows of diag_part into diag_out (8 doubles)
+  // in the last block to finish, which diag_ticket (zero before the launch, zero
+  // again after it) elects; null: diag_reduce_kernel does it in a launch of its own.
+  double *diag_out;
+  unsigned *diag_ticket;
 };
 
 constexpr int kFinThreads = 64;  // many CTAs: the finalize is latency-bound at small n
