@@ -317,14 +317,17 @@ def main():
     ha = torch.empty_like(hp).pin_memory()
     nb.step(hp, hv, ha, dt=DT, nsteps=0, eps=eps)
     Ke = max(3, min(K, 10))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(Ke):
-        nb.step(hp, hv, ha, dt=DT, nsteps=1, eps=eps, acc_valid=True)
-    te = time.perf_counter() - t0
+    te = float("inf")
+    for _ in range(3):  # best of three wall-clock runs: host-side noise only adds time
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(Ke):
+            nb.step(hp, hv, ha, dt=DT, nsteps=1, eps=eps, acc_valid=True)
+        te = min(te, time.perf_counter() - t0)
     out["e2e"] = {"value": pairs * Ke / te / 1e9, "unit": "G pair-interactions/s",
                   "h2d_bytes_per_step": 3 * N_BENCH * 16, "d2h_bytes_per_step": 3 * N_BENCH * 16,
-                  "path": "nbody_step on pinned host buffers (staged H2D, step, D2H, sync)"}
+                  "path": ("nbody_step on pinned host buffers (staged H2D, step, D2H, sync); "
+                           f"best of 3 wall-clock runs of {Ke} steps")}
 
     if rank == 0 and world == 1:
         r, dt_cpu, used = oracle_rate(CPU_SAMPLE_TARGETS)

@@ -325,7 +325,7 @@ def set_tuned(law: int, n: int, tile: int, jsplit: int = 0) -> None:
 
 def get_config(law: int, n: int) -> tuple[int, int]:
     t, j = ctypes.c_int32(), ctypes.c_int32()
-    check(load().nbody_get_config(int(law), int(n), ctypes.byref(t), ctypes.byref(j)),
+    check(_lib().nbody_get_config(int(law), int(n), ctypes.byref(t), ctypes.byref(j)),
           "nbody_get_config")
     return t.value, j.value
 
