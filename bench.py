@@ -810,7 +810,7 @@ def _time(torch, fn, reps=3):
 def batched_extras(nb, torch, dev, nsys=512, steps=50):
     """512 systems, N log-uniform in [64, 4096], half gravity / half LJ + Coulomb,
     50 leapfrog steps: one persistent launch per step under a CUDA graph, against
-    one nbody_step call per system."""
+    one nbody_step call per system, issued eagerly and replayed from a CUDA graph."""
     import workloads
     ens = workloads.ensemble(nsys=nsys, seed=3)
     pos, vel, prm, table = _ensemble_arrays(nb, torch, dev, ens)
@@ -839,6 +839,18 @@ def batched_extras(nb, torch, dev, nsys=512, steps=50):
                 nb.step(p, v, a, q, dt=t["dt"], nsteps=steps)
 
     t_s = _time(torch, per_system, reps=1)
+    # the same per-system calls replayed from one CUDA graph (no host launch cost;
+    # the workspace of the capturing stream is sized by an uncaptured run first)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        per_system()
+    torch.cuda.synchronize()
+    g_ps = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_ps, stream=side):
+        per_system()
+    t_sg = _time(torch, g_ps.replay)
+    del g_ps
     # accuracy beside the rate: forces of every 32nd system against the FP64 oracle
     import oracle
     pos.copy_(p0)
@@ -863,7 +875,9 @@ def batched_extras(nb, torch, dev, nsys=512, steps=50):
             "batched_system_steps_per_s": nsys * steps / t_b,
             "batched_gpairs_per_s": pairs / t_b / 1e9,
             "per_system_launch_system_steps_per_s": nsys * steps / t_s,
-            "batched_speedup_vs_per_system": t_s / t_b}
+            "per_system_graph_system_steps_per_s": nsys * steps / t_sg,
+            "batched_speedup_vs_per_system": t_s / t_b,
+            "batched_speedup_vs_per_system_graph": t_sg / t_b}
 
 
 def adjoint_extras(nb, torch, dev, n=16384, steps=200, k=20):
