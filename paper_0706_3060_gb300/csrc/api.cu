@@ -13,10 +13,9 @@ using namespace nbody;
 
 namespace nbody {
 
-int launch_finalize(const FinalizeArgs &f, cudaStream_t s, int *nblk_out) {
+int launch_finalize(const FinalizeArgs &f, cudaStream_t s, int *nblk_out, bool pdl) {
   const int nblk = std::max(1, (f.n + kFinThreads - 1) / kFinThreads);
-  finalize_kernel<<<nblk, kFinThreads, 0, s>>>(f);
-  NB_CUDA(cudaGetLastError());
+  NB_CUDA(launch_kernel(finalize_kernel, nblk, kFinThreads, 0, s, pdl, f));
   if (nblk_out) *nblk_out = nblk;
   return NBODY_OK;
 }
@@ -164,14 +163,15 @@ int eval_and_finalize(const float4 *pos, const float4 *prm, const nbody_params &
                       const Plan1 &plan, const Scratch &sc, int *err, bool pot,
                       FinalizeArgs f, cudaStream_t s, int *nblk, bool first_eval,
                       bool sources_ready = false, bool prepare_next = false,
-                      bool *prepared = nullptr, const KickDrift *kd = nullptr) {
+                      bool *prepared = nullptr, const KickDrift *kd = nullptr,
+                      bool chained = false) {
   const bool fx = (p.flags & NBODY_FIXED_POINT) != 0 || plan.atomic;
   const AtomicPrep at{sc.acc64, sc.msum, sc.ticket, p.eps2, sc.fscale, sc.finv,
                       first_eval ? 1 : 0};
   NB_TRY(launch_forces(pos, prm, p.law, p.flags, p.eps2, n, plan, sc.part_hi, sc.part_lo,
                        sc.jbuf, err, pot, s, nullptr,
                        (fx && !plan.atomic) ? sc.fscale : nullptr,
-                       plan.atomic ? &at : nullptr, true, sources_ready, kd));
+                       plan.atomic ? &at : nullptr, true, sources_ready, kd, chained));
   f.fx_inv = fx ? sc.finv : nullptr;
   f.acc64 = sc.acc64;
   f.part_hi = sc.part_hi;
@@ -194,7 +194,7 @@ int eval_and_finalize(const float4 *pos, const float4 *prm, const nbody_params &
   f.rezero = (prep && plan.atomic) ? 1 : 0;
   f.diag_ticket = sc.diag_ticket;
   if (prepared) *prepared = prep;
-  return launch_finalize(f, s, nblk);
+  return launch_finalize(f, s, nblk, true);
 }
 
 int prepare_fixed(const float4 *pos, int n, const nbody_params &p, const Plan1 &plan,
@@ -242,6 +242,7 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
   int row = 0;
   bool first_eval = true;  // the fixed-point scale of atomic plans is formed once per call
   bool ready = false;      // the last finalize wrote the next evaluation's source pairs
+  bool launched = false;   // a kernel of this call precedes (programmatic dependent launch)
   FinalizeArgs f{};
   f.pos = pos;
   f.vel = vel;
@@ -265,12 +266,15 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
                              report(0) || (nsteps == 0 && want_pot), f, s, nullptr, first_eval,
                              false, nsteps > 0, &ready));
     first_eval = false;
+    launched = true;
   } else if (nsteps > 0) {
-    if (plan.tile->packed)
+    if (plan.tile->packed) {
       kd_pending = true;
-    else
+    } else {
       NB_TRY(launch_kick_drift(pos, vel, acc, n, dt, kd.trace1, nullptr, nullptr, f.x_lo,
                                f.v_lo, s));
+      launched = true;
+    }
   }
   for (int st = 1; st <= nsteps; ++st) {
     const bool rep = report(st);
@@ -280,9 +284,10 @@ int step_device(float4 *pos, float4 *vel, float4 *acc, const float4 *prm, int n,
     f.diag_out = rep ? sc.diag_rows + kDiagFields * row++ : nullptr;
     NB_TRY(eval_and_finalize(pos, prm, p, n, plan, sc, err, rep || (last && want_pot), f, s,
                              nullptr, first_eval, ready, !last, &ready,
-                             kd_pending ? &kd : nullptr));
+                             kd_pending ? &kd : nullptr, launched));
     first_eval = false;
     kd_pending = false;
+    launched = true;
   }
   if (rows > 0)
     NB_CUDA(cudaMemcpyAsync(diag_dev, sc.diag_rows, size_t(rows) * kDiagFields * sizeof(double),

@@ -143,33 +143,38 @@ int vjp_prepare(int law, int n, int tile, int jsplit, int sms, cudaStream_t s, V
   return NBODY_OK;
 }
 
-// One VJP: all-pairs kernel + finalize (+ type reduction).
+// One VJP: all-pairs kernel + finalize (+ type reduction). chained: the previous
+// operation in `s` is a kernel of this library issued by the same call, so every
+// launch here may be a programmatic dependent launch (otherwise all but the first).
 int vjp_once(const float4 *pos, const float4 *prm, const float4 *lam, float4 *grad_x,
              float *grad_m, double *grad_types, int ntypes, float alpha, int accumulate, int n,
              const nbody_params &p, const VjpScratch &sc, float4 *lam_v, float dt_next,
-             cudaStream_t s) {
+             cudaStream_t s, bool chained) {
   int *err = nullptr;
   NB_TRY(error_word(&err));
   const float4 *src = lam;
   const bool ljc = (p.law == NBODY_LAW_LJC || p.law == NBODY_LAW_LJC_LINEAR);
   if (ljc) {
-    lam_over_m_kernel<<<(n + 255) / 256, 256, 0, s>>>(lam, pos, sc.u, n);
-    NB_CUDA(cudaGetLastError());
+    NB_CUDA(launch_kernel(lam_over_m_kernel, (n + 255) / 256, 256, 0, s, chained, lam, pos,
+                          sc.u, n));
+    chained = true;
     src = sc.u;
   }
   if (sc.d->packed) {
-    const unsigned pblocks = unsigned(((n + 1) / 2 + 255) / 256);
+    const int pblocks = ((n + 1) / 2 + 255) / 256;
     if (sc.d->sym && ljc)
-      interleave_ljc_vjp_pairs_blocked_kernel<<<pblocks, 256, 0, s>>>(pos, src, prm, sc.jp, n,
-                                                                      sc.d->tile_i);
+      NB_CUDA(launch_kernel(interleave_ljc_vjp_pairs_blocked_kernel, pblocks, 256, 0, s, chained,
+                            pos, src, prm, sc.jp, n, sc.d->tile_i));
     else if (sc.d->sym)
-      interleave_vjp_pairs_blocked_kernel<<<pblocks, 256, 0, s>>>(pos, src, sc.jp, n,
-                                                                  sc.d->tile_i);
+      NB_CUDA(launch_kernel(interleave_vjp_pairs_blocked_kernel, pblocks, 256, 0, s, chained,
+                            pos, src, sc.jp, n, sc.d->tile_i));
     else if (ljc)
-      interleave_ljc_vjp_pairs_kernel<<<pblocks, 256, 0, s>>>(pos, src, prm, sc.jp, n);
+      NB_CUDA(launch_kernel(interleave_ljc_vjp_pairs_kernel, pblocks, 256, 0, s, chained, pos,
+                            src, prm, sc.jp, n));
     else
-      interleave_vjp_pairs_kernel<<<pblocks, 256, 0, s>>>(pos, src, sc.jp, n);
-    NB_CUDA(cudaGetLastError());
+      NB_CUDA(launch_kernel(interleave_vjp_pairs_kernel, pblocks, 256, 0, s, chained, pos, src,
+                            sc.jp, n));
+    chained = true;
   }
   VjpArgs a{};
   a.pos = pos;
@@ -186,6 +191,7 @@ int vjp_once(const float4 *pos, const float4 *prm, const float4 *lam, float4 *gr
   a.slice_len = sc.slice_len;
   a.eps2 = p.eps2;
   a.comp = (p.flags & NBODY_NO_COMPENSATION) ? 0 : 1;
+  a.pdl = chained ? 1 : 0;
   const TimerMark tm = timer_begin(1, s);
   cudaError_t e = sc.d->launch(a, sc.grid, s);
   timer_end(tm, s);
@@ -213,12 +219,10 @@ int vjp_once(const float4 *pos, const float4 *prm, const float4 *lam, float4 *gr
   f.type_part = types ? sc.type_part : nullptr;
   f.lam_v = lam_v;
   f.dt_next = dt_next;
-  vjp_finalize_kernel<<<sc.nblk, 256, 0, s>>>(f);
-  NB_CUDA(cudaGetLastError());
-  if (types) {
-    type_reduce_kernel<<<1, 32, 0, s>>>(sc.type_part, sc.nblk, ntypes, grad_types);
-    NB_CUDA(cudaGetLastError());
-  }
+  NB_CUDA(launch_kernel(vjp_finalize_kernel, sc.nblk, 256, 0, s, true, f));
+  if (types)
+    NB_CUDA(launch_kernel(type_reduce_kernel, 1, 32, 0, s, true, sc.type_part, sc.nblk, ntypes,
+                          grad_types));
   return NBODY_OK;
 }
 
@@ -363,13 +367,15 @@ int nbody_adjoint(const void *pos_m, const void *prm, const void *lam, void *gra
   VjpScratch sc{};
   NB_TRY(vjp_prepare(p.law, int(n), p.tile, p.jsplit, sms, s, &sc));
   const int acc = (p.flags & NBODY_ACCUMULATE) ? 1 : 0;
+  bool launched = false;
   if (grad_types && !acc && p.law != NBODY_LAW_GRAV) {
     zero_doubles_kernel<<<1, 32, 0, s>>>(grad_types, 2 * ntypes);
     NB_CUDA(cudaGetLastError());
+    launched = true;
   }
   return vjp_once(static_cast<const float4 *>(pos_m), static_cast<const float4 *>(prm),
                   static_cast<const float4 *>(lam), static_cast<float4 *>(grad_x), grad_m,
-                  grad_types, ntypes, alpha, acc, int(n), p, sc, nullptr, 0.0f, s);
+                  grad_types, ntypes, alpha, acc, int(n), p, sc, nullptr, 0.0f, s, launched);
 }
 
 int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k, float dt,
@@ -404,7 +410,7 @@ int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k
     const float w = (st == 0 && first) ? 0.5f * dt : dt;
     // lam_x += w J(x_st)^T lam_v, then (except after the last) lam_v += dt lam_x.
     NB_TRY(vjp_once(X + size_t(st) * size_t(n), q, lv, lx, grad_m, grad_types, ntypes, w, 1,
-                    int(n), p, sc, st > 0 ? lv : nullptr, dt, s));
+                    int(n), p, sc, st > 0 ? lv : nullptr, dt, s, true));
   }
   return NBODY_OK;
 }

@@ -461,6 +461,7 @@ __device__ __forceinline__ float4 source_at(const float4 *pos, const KickDrift &
 // particles 2p, 2p+1; an odd count is padded with a massless particle far away
 // (its pair terms are exactly zero).
 __global__ void interleave_pairs_kernel(const float4 *pos, float4 *jp, int n, KickDrift kd) {
+  griddep_start();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (2 * p >= n) return;
   const float4 a = source_at(pos, kd, 2 * p);
@@ -483,6 +484,7 @@ __global__ void __launch_bounds__(256) interleave_pairs_blocked_kernel(const flo
                                                                        float4 *jp, int n, int B,
                                                                        AtomicPrep at,
                                                                        KickDrift kd) {
+  griddep_start();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   double am = 0.0;
   if (2 * p < n) {
@@ -540,6 +542,7 @@ __global__ void __launch_bounds__(256) interleave_pairs_blocked_kernel(const flo
 // (s0 s1 e0 e1). Pairs past n are not written.
 __global__ void interleave_ljc_pairs_blocked_kernel(const float4 *pos, const float4 *prm,
                                                     float4 *jp, int n, int B, KickDrift kd) {
+  griddep_start();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (2 * p >= n) return;
   const float4 a = source_at(pos, kd, 2 * p), qa = prm[2 * p];
@@ -557,6 +560,7 @@ __global__ void interleave_ljc_pairs_blocked_kernel(const float4 *pos, const flo
 // pad of an odd count is far away with no charge and no LJ well.
 __global__ void interleave_ljc_pairs_kernel(const float4 *pos, const float4 *prm, float4 *jp,
                                             int n, KickDrift kd) {
+  griddep_start();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (2 * p >= n) return;
   const float4 a = source_at(pos, kd, 2 * p), qa = prm[2 * p];
@@ -578,7 +582,7 @@ int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
                   int *err, bool pot, cudaStream_t s, const Targets *tg,
                   const float *fscale, const AtomicPrep *at, bool timed,
-                  bool sources_ready, const KickDrift *kd) {
+                  bool sources_ready, const KickDrift *kd, bool chained) {
   const bool atomic = at && at->acc64;
   if (p.atomic != atomic || (atomic && (law != NBODY_LAW_GRAV || tg || !at->msum ||
                                         !at->ticket || !at->scale || !at->inv)))
@@ -596,17 +600,20 @@ int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags,
     if (!jbuf) return set_error_msg(NBODY_EINVAL, "packed tile without pair buffer");
     const int np = (n + 1) / 2;
     const KickDrift k = kd ? *kd : KickDrift{};
+    const int g = (np + 255) / 256;
+    const AtomicPrep ap = atomic ? *at : AtomicPrep{};
     if ((law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR) && p.tile->sym)
-      interleave_ljc_pairs_blocked_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, prm, jbuf, n,
-                                                                           p.tile->tile_i, k);
+      NB_CUDA(launch_kernel(interleave_ljc_pairs_blocked_kernel, g, 256, 0, s, chained, pos, prm,
+                            jbuf, n, p.tile->tile_i, k));
     else if (law == NBODY_LAW_LJC || law == NBODY_LAW_LJC_LINEAR)
-      interleave_ljc_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, prm, jbuf, n, k);
+      NB_CUDA(launch_kernel(interleave_ljc_pairs_kernel, g, 256, 0, s, chained, pos, prm, jbuf,
+                            n, k));
     else if (p.tile->sym)
-      interleave_pairs_blocked_kernel<<<(np + 255) / 256, 256, 0, s>>>(
-          pos, jbuf, n, p.tile->tile_i, atomic ? *at : AtomicPrep{}, k);
+      NB_CUDA(launch_kernel(interleave_pairs_blocked_kernel, g, 256, 0, s, chained, pos, jbuf, n,
+                            p.tile->tile_i, ap, k));
     else
-      interleave_pairs_kernel<<<(np + 255) / 256, 256, 0, s>>>(pos, jbuf, n, k);
-    NB_CUDA(cudaGetLastError());
+      NB_CUDA(launch_kernel(interleave_pairs_kernel, g, 256, 0, s, chained, pos, jbuf, n, k));
+    chained = true;
   }
   ForceArgs a{};
   a.jpair = jbuf;
@@ -630,6 +637,7 @@ int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags,
   a.comp = (flags & NBODY_NO_COMPENSATION) ? 0 : 1;
   a.fscale = fscale;
   a.acc64 = atomic ? at->acc64 : nullptr;
+  a.pdl = chained ? 1 : 0;
   const TimerMark tm = timed ? timer_begin(0, s) : TimerMark{};
   cudaError_t e = p.tile->launch(a, p.grid, pot, (flags & NBODY_PRECISE_RSQRT) != 0, s);
   timer_end(tm, s);

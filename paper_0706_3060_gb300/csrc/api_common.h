@@ -164,13 +164,15 @@ struct KickDrift {
 // atomic plan's accumulators are zero), written by the previous step's finalize:
 // no interleave launch. kd: the interleave launch first applies this kick-drift to
 // the positions at `pos` (kd->pos == pos; packed tiles, all targets, not with
-// sources_ready).
+// sources_ready). chained: the previous operation in `s` is a kernel of this
+// library issued by the same call, so the first launch may be a programmatic
+// dependent launch (the later ones always are).
 int launch_forces(const float4 *pos, const float4 *prm, int law, uint32_t flags, float eps2,
                   int n, const Plan1 &p, float4 *part_hi, float4 *part_lo, float4 *jbuf,
                   int *err, bool pot, cudaStream_t s, const Targets *tg = nullptr,
                   const float *fscale = nullptr, const AtomicPrep *at = nullptr,
                   bool timed = true, bool sources_ready = false,
-                  const KickDrift *kd = nullptr);
+                  const KickDrift *kd = nullptr, bool chained = false);
 
 size_t round_up(size_t x, size_t a);
 
@@ -191,7 +193,8 @@ int timing_read(int which, int64_t *launches, double *total_ms);
 
 // O(N) kernel launches (aux_kernels.cuh), used by several entry points.
 struct FinalizeArgs;
-int launch_finalize(const FinalizeArgs &f, cudaStream_t s, int *nblk_out);
+// pdl: a programmatic dependent launch after the force kernel of the same call.
+int launch_finalize(const FinalizeArgs &f, cudaStream_t s, int *nblk_out, bool pdl = false);
 int launch_diag_reduce(const double *part, int nblk, double *out, cudaStream_t s);
 int launch_kick_drift(float4 *pos, float4 *vel, const float4 *acc, int n, float dt,
                       float4 *trace1, const int *sys_of, const void *sys, float4 *x_lo,

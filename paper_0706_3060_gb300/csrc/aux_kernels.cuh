@@ -32,6 +32,7 @@ __device__ __forceinline__ void block_sum8(double v[kDiagFields], double *out) {
 }
 
 __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArgs f) {
+  griddep_start();
   const int i = blockIdx.x * kFinThreads + threadIdx.x;
   double dv[kDiagFields] = {0, 0, 0, 0, 0, 0, 0, 0};
   float4 xn = make_float4(1e18f, 1e18f, 1e18f, 0.0f);  // drifted position (pad: far away)

@@ -106,6 +106,17 @@ __device__ __forceinline__ float rsqrt_newton(float y, float s) {
   return y * fmaf(hs, yy, 1.5f);
 }
 
+// Programmatic dependent launch: returns once the grid this one depends on has
+// completed and its writes are visible (a no-op for a grid launched without the
+// programmatic-serialization attribute). Called first thing by every kernel of
+// the force / step chain, before it touches global memory. No kernel triggers
+// its dependents early: the next grid is launched as this one's last CTAs exit,
+// so its CTAs are placed on an idle GPU (placed while the previous grid still
+// held the SMs, the CTAs of a grid under one wave bunch up on a few SMs).
+__device__ __forceinline__ void griddep_start() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // Knuth's TwoSum: s + e == a + b exactly, s = fl(a + b).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   s = __fadd_rn(a, b);

@@ -80,6 +80,7 @@ struct ForceArgs {
   // fractions in units of 2^-32), zeroed before the launch, into which every CTA
   // adds its per-block partials; null: per-block partial slots in part_hi / part_lo
   long long *acc64;
+  int pdl;  // host side: launch with programmatic dependent launch (griddep_start)
 };
 
 enum : int { kChunkFirst = 1, kChunkLast = 2, kChunkEnd = 4 };
@@ -253,6 +254,7 @@ struct ForceTile {
 template <int LAW, int NT, int I, int SW, int JT, bool POT, bool PRECISE, bool PK = false,
           int PU = 2, int MINB = 1, bool FX = false>
 __global__ void __launch_bounds__(NT + 32, MINB) force_kernel(const ForceArgs a) {
+  griddep_start();
   using T = ForceTile<LAW, NT, I, SW, JT>;
   constexpr bool LIN = (LAW == kLawLJCLin);
   constexpr bool MIX = (LAW == kLawMixed);

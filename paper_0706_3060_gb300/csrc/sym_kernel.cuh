@@ -120,6 +120,7 @@ __device__ __forceinline__ void sym_store(const ForceArgs &a, long long slot_bas
 
 template <int NT, int I, bool POT, bool PRECISE, int MINB = 1, bool FX = false>
 __global__ void __launch_bounds__(NT, MINB) sym_grav_kernel(const ForceArgs a) {
+  griddep_start();
   using T = SymTile<NT, I>;
   constexpr int B = T::kB;
   constexpr int NC = POT ? 8 : 6;  // j-side float components per source pair

@@ -83,6 +83,7 @@ __device__ __forceinline__ void sym_ljc_pair2(float2 X, float2 Y, float2 Z, floa
 
 template <int LAW, int NT, int I, bool POT, bool PRECISE, int MINB = 1>
 __global__ void __launch_bounds__(NT, MINB) sym_ljc_kernel(const ForceArgs a) {
+  griddep_start();
   static_assert(LAW == kLawLJC || LAW == kLawLJCLin, "LJC laws only");
   constexpr bool LIN = (LAW == kLawLJCLin);
   using T = SymLjcTile<NT, I>;

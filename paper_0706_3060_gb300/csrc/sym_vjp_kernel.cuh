@@ -82,6 +82,7 @@ __device__ __forceinline__ void sym_gvjp_pair2(float2 X, float2 Y, float2 Z, flo
 // contribution, before the G scaling of vjp_finalize_kernel.
 template <int NT, int I, int MINB = 1>
 __global__ void __launch_bounds__(NT, MINB) sym_gvjp_kernel(const VjpArgs a) {
+  griddep_start();
   using T = SymVjpTile<NT, I>;
   constexpr int B = T::kB;
   constexpr int P = T::kPairs;
@@ -297,6 +298,7 @@ __device__ __forceinline__ void sym_gaj_pair2(float2 X, float2 Y, float2 Z, floa
 
 template <int NT, int I, int MINB = 1>
 __global__ void __launch_bounds__(NT, MINB) sym_gaj_kernel(const VjpArgs a) {
+  griddep_start();
   using T = SymGajTile<NT, I>;
   constexpr int B = T::kB;
   constexpr int P = T::kPairs;
@@ -519,6 +521,7 @@ __device__ __forceinline__ void sym_ljc_vjp_pair2(const float4 F0, const float4 
 
 template <int NT, int I, bool LIN, int MINB = 1>
 __global__ void __launch_bounds__(NT, MINB) sym_ljc_vjp_kernel(const VjpArgs a) {
+  griddep_start();
   using T = SymLjcVjpTile<NT, I>;
   constexpr int B = T::kB;
   constexpr int P = T::kPairs;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <utility>
 
 #include "force_kernel.cuh"
 #include "sym_kernel.cuh"
@@ -42,6 +43,29 @@ const TileDesc *ljclin_tiles(int *count);
 const TileDesc *grav_fixed_tiles(int *count);
 const TileDesc *mixed_tiles(int *count);
 
+// Launch `k` on `s`; with `pdl` as a programmatic dependent launch, which lets
+// its CTAs be scheduled while the previous kernel in the stream finishes (the
+// kernel waits for that kernel in griddep_start before touching memory).
+template <typename... P, typename... A>
+inline cudaError_t launch_kernel(void (*k)(P...), int grid, int block, size_t smem,
+                                 cudaStream_t s, bool pdl, A &&...args) {
+  if (!pdl) {
+    k<<<grid, block, smem, s>>>(std::forward<A>(args)...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(unsigned(block));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+
 template <int LAW, int NT, int I, int SW, int JT, bool PK = false, int PU = 2, int MINB = 1,
           bool FX = false>
 struct TileImpl {
@@ -61,8 +85,7 @@ struct TileImpl {
         if (known) opted[dev].store(true, std::memory_order_release);
       }
     }
-    k<<<grid, T::kThreads, T::kSmemBytes, s>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(k, grid, T::kThreads, T::kSmemBytes, s, a.pdl != 0, a);
   }
   static cudaError_t launch(const ForceArgs &a, int grid, bool pot, bool precise,
                             cudaStream_t s) {
@@ -121,8 +144,7 @@ struct SymImpl {
         if (known) opted[dev].store(true, std::memory_order_release);
       }
     }
-    k<<<grid, NT, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(k, grid, NT, smem, s, a.pdl != 0, a);
   }
   static cudaError_t launch(const ForceArgs &a, int grid, bool pot, bool precise,
                             cudaStream_t s) {
@@ -179,8 +201,7 @@ struct SymLjcImpl {
         if (known) opted[dev].store(true, std::memory_order_release);
       }
     }
-    k<<<grid, NT, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(k, grid, NT, smem, s, a.pdl != 0, a);
   }
   static cudaError_t launch(const ForceArgs &a, int grid, bool pot, bool precise,
                             cudaStream_t s) {

@@ -36,6 +36,7 @@ struct VjpFinalizeArgs {
 };
 
 __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs f) {
+  griddep_start();
   const int i = blockIdx.x * 256 + threadIdx.x;
   double tv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (i < f.n) {
@@ -190,6 +191,7 @@ __global__ void __launch_bounds__(256) gaj_finalize_kernel(const float4 *part_hi
 
 // Sum per-block type partials in order and add them into out[0..2*ntypes).
 __global__ void type_reduce_kernel(const double *part, int nblk, int ntypes, double *out) {
+  griddep_start();
   const int k = threadIdx.x;
   if (k >= 8) return;
   double s = 0.0;
@@ -204,6 +206,7 @@ __global__ void type_reduce_kernel(const double *part, int nblk, int ntypes, dou
 // (the kernel copies only the block's own pairs).
 __global__ void interleave_vjp_pairs_blocked_kernel(const float4 *pos, const float4 *lam,
                                                     float4 *jp, int n, int B) {
+  griddep_start();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (2 * p >= n) return;
   const bool two = 2 * p + 1 < n;
@@ -222,6 +225,7 @@ __global__ void interleave_vjp_pairs_blocked_kernel(const float4 *pos, const flo
 // (lz0 lz1 0 0); an odd count is padded with a massless particle far away.
 __global__ void interleave_vjp_pairs_kernel(const float4 *pos, const float4 *lam, float4 *jp,
                                             int n) {
+  griddep_start();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (2 * p >= n) return;
   const bool two = 2 * p + 1 < n;
@@ -239,6 +243,7 @@ __global__ void interleave_vjp_pairs_kernel(const float4 *pos, const float4 *lam
 // an odd count ends with an uncharged, motionless pad at 1e18 with zero LJ terms.
 __global__ void interleave_ljc_vjp_pairs_kernel(const float4 *pos, const float4 *u,
                                                 const float4 *prm, float4 *jp, int n) {
+  griddep_start();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (2 * p >= n) return;
   const bool two = 2 * p + 1 < n;
@@ -260,6 +265,7 @@ __global__ void interleave_ljc_vjp_pairs_kernel(const float4 *pos, const float4 
 __global__ void interleave_ljc_vjp_pairs_blocked_kernel(const float4 *pos, const float4 *u,
                                                         const float4 *prm, float4 *jp, int n,
                                                         int B) {
+  griddep_start();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (2 * p >= n) return;
   const bool two = 2 * p + 1 < n;
@@ -278,6 +284,7 @@ __global__ void interleave_ljc_vjp_pairs_blocked_kernel(const float4 *pos, const
 
 // u = lam / m (LJC sources are weighted by 1 / m_j).
 __global__ void lam_over_m_kernel(const float4 *lam, const float4 *pos, float4 *u, int n) {
+  griddep_start();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float4 l = lam[i];

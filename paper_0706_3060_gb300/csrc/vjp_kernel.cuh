@@ -40,6 +40,7 @@ struct VjpArgs {
   int slice_len;
   float eps2;
   int comp;
+  int pdl;  // host side: launch with programmatic dependent launch (griddep_start)
 };
 
 __device__ __forceinline__ float rcp_hw(float x) {
@@ -300,6 +301,7 @@ __device__ __forceinline__ void shfl_combine(float4 &hi, float4 &lo, int off) {
 
 template <int LAW, int NT, int I, int SW, int JT, bool PK = false, int PU = 2>
 __global__ void __launch_bounds__(NT + 32) vjp_kernel(const VjpArgs a) {
+  griddep_start();
   using T = VjpTile<LAW, NT, I, SW, JT, PK>;
   static_assert(!PK || SW == 1, "packed tiles: one j-lane");
   static_assert(JT % 2 == 0, "j-tiles hold whole source pairs");

@@ -29,8 +29,7 @@ struct VjpImpl {
         if (known) opted[dev].store(true, std::memory_order_release);
       }
     }
-    k<<<grid, T::kThreads, T::kSmemBytes, s>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(k, grid, T::kThreads, T::kSmemBytes, s, a.pdl != 0, a);
   }
   static int occupancy() {  // cached per device, as for the force tiles
     static std::atomic<int> cached[kMaxDevicesTile];
@@ -94,8 +93,7 @@ struct SymVjpImplT {
         if (known) opted[dev].store(true, std::memory_order_release);
       }
     }
-    k<<<grid, NT, T::kSmemBytes, s>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(k, grid, NT, T::kSmemBytes, s, a.pdl != 0, a);
   }
   static int occupancy() {
     static std::atomic<int> cached[kMaxDevicesTile];
