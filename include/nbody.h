@@ -272,6 +272,12 @@ int nbody_forces_static(const void *pos_m, const void *prm, void *acc, int64_t n
  *           always evaluated at the FP32 positions pos_m.
  * Host pointers are accepted as in nbody_forces (all of pos_m, vel, acc, prm
  * on the host); then the call synchronizes. A host diag also synchronizes.
+ * Launches on the stream: for a packed tile one pair-interleave launch before
+ * the first evaluation (with NBODY_ACC_VALID it also applies the first
+ * half-kick and drift), then per evaluation the force kernel and one finalize
+ * kernel, which kicks and drifts, adds the diagnostics of a report step and
+ * writes the next evaluation's source copy; every launch after the first is a
+ * programmatic dependent launch.
  * --------------------------------------------------------------------------- */
 int nbody_step(void *pos_m, void *vel, void *acc, const void *prm, int64_t n, float dt,
                int32_t nsteps, int32_t report_every, double *diag, void *trace, void *state_lo,
@@ -360,8 +366,9 @@ int nbody_adjoint_leapfrog(const void *xs, const void *prm, int64_t n, int32_t k
 int nbody_tile_count(int32_t law);
 /* Kind bits of a tile configuration (nbody_tile_info). */
 enum {
-    NBODY_TILE_PACKED = 1,     /* reads pair-interleaved sources: each force
-                                  evaluation is preceded by one interleave launch */
+    NBODY_TILE_PACKED = 1,     /* reads pair-interleaved sources: a force evaluation
+                                  is preceded by one interleave launch (within an
+                                  nbody_step call, only the first) */
     NBODY_TILE_SYMMETRIC = 2,  /* Newton-symmetric block pairs: each unordered pair
                                   evaluated once and applied to both particles; j_tile
                                   is the block size; for the force laws and the
