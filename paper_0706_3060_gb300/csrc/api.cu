@@ -159,6 +159,8 @@ int get_scratch(cudaStream_t s, int law, int n, const Plan1 &plan, int diag_rows
 // sources (no interleave launch). prepare_next: this finalize drifts (kFinKickDrift)
 // and writes them for the next evaluation; returns in *prepared whether it did.
 // kd: a first half-kick and drift that the interleave launch applies (packed tiles).
+// chained: a kernel of this call precedes in the stream, so the first launch here may
+// be a programmatic dependent launch too (the later ones always are).
 int eval_and_finalize(const float4 *pos, const float4 *prm, const nbody_params &p, int n,
                       const Plan1 &plan, const Scratch &sc, int *err, bool pot,
                       FinalizeArgs f, cudaStream_t s, int *nblk, bool first_eval,
