@@ -73,6 +73,7 @@ int ensure_counters(nbody_batch_plan *p, int need) {
 __global__ void interleave_systems_kernel(const float4 *pos, const float4 *prm,
                                           const int *sys_of, const int4 *sysp, int total,
                                           float4 *jgrav, float4 *jljc) {
+  griddep_start();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   const int k = sys_of[i];
@@ -124,6 +125,7 @@ __global__ void interleave_systems_blocked_kernel(const float4 *pos, const float
                                                   const int *sys_of, const int4 *sysp,
                                                   int total, float4 *jgrav, float4 *jljc,
                                                   int B) {
+  griddep_start();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   const int k = sys_of[i];
@@ -185,15 +187,20 @@ int enqueue_run(nbody_batch_plan *p, float4 *pos, float4 *vel, float4 *acc, cons
   // reset between launches of different steps; all are zeroed up front.
   NB_CUDA(cudaMemsetAsync(p->d_counter, 0, sizeof(int) * size_t(evals), s));
   int counter_idx = 0;
+  // Every launch after the first kernel of the run is a programmatic dependent
+  // launch (the memset before it is not a kernel).
+  bool chained = false;
   auto eval = [&](int mode) -> int {
+    const int g = (total + 255) / 256;
     if (p->td->sym) {
-      interleave_systems_blocked_kernel<<<(total + 255) / 256, 256, 0, s>>>(
-          pos, prm, p->d_sys_of, p->d_sysp, total, p->d_jgrav, p->d_jljc, p->td->tile_i);
-      NB_CUDA(cudaGetLastError());
+      NB_CUDA(launch_kernel(interleave_systems_blocked_kernel, g, 256, 0, s, chained, pos, prm,
+                            p->d_sys_of, p->d_sysp, total, p->d_jgrav, p->d_jljc,
+                            p->td->tile_i));
+      chained = true;
     } else if (p->td->packed) {
-      interleave_systems_kernel<<<(total + 255) / 256, 256, 0, s>>>(
-          pos, prm, p->d_sys_of, p->d_sysp, total, p->d_jgrav, p->d_jljc);
-      NB_CUDA(cudaGetLastError());
+      NB_CUDA(launch_kernel(interleave_systems_kernel, g, 256, 0, s, chained, pos, prm,
+                            p->d_sys_of, p->d_sysp, total, p->d_jgrav, p->d_jljc));
+      chained = true;
     }
     ForceArgs a{};
     a.jpair = p->d_jgrav;
@@ -212,6 +219,7 @@ int enqueue_run(nbody_batch_plan *p, float4 *pos, float4 *vel, float4 *acc, cons
     a.n_items = p->n_items;
     a.counter = p->d_counter + counter_idx++;
     a.comp = (p->flags & NBODY_NO_COMPENSATION) ? 0 : 1;
+    a.pdl = chained ? 1 : 0;
     const TimerMark tm = timer_begin(0, s);
     cudaError_t e = p->td->launch(a, p->grid, false, (p->flags & NBODY_PRECISE_RSQRT) != 0, s);
     timer_end(tm, s);
@@ -230,13 +238,15 @@ int enqueue_run(nbody_batch_plan *p, float4 *pos, float4 *vel, float4 *acc, cons
     f.acc = acc;
     f.mode = mode;
     f.plain = (p->flags & NBODY_NO_COMPENSATION) ? 1 : 0;
-    return launch_finalize(f, s, nullptr);
+    chained = true;
+    return launch_finalize(f, s, nullptr, true);
   };
   if (!(flags & NBODY_ACC_VALID) || nsteps == 0) {
     NB_TRY(eval(kFinWriteAcc | (nsteps > 0 ? kFinKickDrift : 0)));
   } else {
     NB_TRY(launch_kick_drift(pos, vel, acc, total, 0.0f, nullptr, p->d_sys_of, p->d_sys,
                              nullptr, nullptr, s));
+    chained = true;
   }
   for (int st = 1; st <= nsteps; ++st)
     NB_TRY(eval(kFinWriteAcc | kFinKickSync | (st == nsteps ? 0 : kFinKickDrift)));

@@ -209,6 +209,7 @@ __device__ __forceinline__ bool sym_batch_item(const ForceArgs &a, const WorkIte
 
 template <int NT, int I, bool PRECISE, int MINB = 1>
 __global__ void __launch_bounds__(NT, MINB) sym_batch_kernel(const ForceArgs a) {
+  griddep_start();
   using T = SymMixedTile<NT, I>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float4 *src = reinterpret_cast<float4 *>(smem_raw);

@@ -258,8 +258,7 @@ struct SymBatchImpl {
         if (known) opted[dev].store(true, std::memory_order_release);
       }
     }
-    k<<<grid, NT, T::kSmemBytes, s>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(k, grid, NT, T::kSmemBytes, s, a.pdl != 0, a);
   }
   static cudaError_t launch(const ForceArgs &a, int grid, bool pot, bool precise,
                             cudaStream_t s) {
