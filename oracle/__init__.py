@@ -83,6 +83,9 @@ def _load():
             lib.oracle_ljc_model.restype = None
             lib.oracle_grav_vjp.argtypes = [i64, d, d, ctypes.c_double, ctypes.c_double,
                                             d, d, d]
+            lib.oracle_grav_vjp_rows.argtypes = [i64, d, d, ctypes.c_double, ctypes.c_double,
+                                                 d, i64, i64p, d, d]
+            lib.oracle_grav_vjp_rows.restype = None
             lib.oracle_ljc_vjp.argtypes = [i64, d, d, d, i32p, ctypes.c_int32, d, d,
                                            ctypes.c_double, d, d, d, d, d]
             lib.oracle_ljc_vjp_model.argtypes = [i64, d, d, d, i32p, ctypes.c_int32, d, d,
@@ -182,13 +185,22 @@ def ljc_force(x, q, sig, eps, kq=COULOMB_K / 80.0, idx=None, potential=False, li
     return (f, phi) if potential else f
 
 
-def grav_vjp(x, m, lam, G=1.0, eps=0.0):
-    """J^T lam for Eq. 1 and the mass derivative: returns (g (n,3), gm (n,))."""
+def grav_vjp(x, m, lam, G=1.0, eps=0.0, idx=None):
+    """J^T lam for Eq. 1 and the mass derivative: returns (g (n,3), gm (n,)), or
+    with ``idx`` only those rows, each gathered on its own (g (len(idx),3), gm)."""
     lib = _load()
     x = _f64(x, (-1, 3))
     m = _f64(m)
     lam = _f64(lam, (-1, 3))
     n = x.shape[0]
+    if idx is not None:
+        idx, idxp = _idx(idx)
+        nk = idx.shape[0]
+        g = np.zeros((nk, 3))
+        gm = np.zeros(nk)
+        lib.oracle_grav_vjp_rows(n, _dp(x), _dp(m), float(G), float(eps) ** 2, _dp(lam), nk,
+                                 idxp, _dp(g), _dp(gm))
+        return g, gm
     g = np.zeros((n, 3))
     gm = np.zeros(n)
     lib.oracle_grav_vjp(n, _dp(x), _dp(m), float(G), float(eps) ** 2, _dp(lam), _dp(g),

@@ -14,6 +14,7 @@
  *   - oracle_grav_jerk  Table 1 "Gravity (accel & jerk)"
  *   - oracle_ljc_model  Table 1 "LJC (linear)" as well (reading C3 below)
  *   - oracle_grav_vjp   transpose of the Jacobian of Eq. 1, block by block
+ *   - oracle_grav_vjp_rows  selected rows of the same product, gathered per row
  *   - oracle_ljc_vjp    transpose of the Jacobian of the LJC law, plus the
  *                       derivatives w.r.t. per-type sigma, epsilon and masses
  *
@@ -245,6 +246,48 @@ void oracle_grav_vjp(int64_t n, const double *x, const double *m, double G,
         memcpy(gm, ml, sizeof(double) * (size_t)n);
     free(gl);
     free(ml);
+}
+
+/* ---------------------------------------------------------------------------
+ * Rows idx[0..nk) of the same product, each gathered on its own instead of
+ * scattered: row k collects the blocks (i, k) and (k, k) of the sum above,
+ *   g_k  = sum_{i != k} G m_k T(x_i - x_k) lam_i - sum_{j != k} G m_j T(x_k - x_j) lam_k,
+ *   gm_k = sum_{i != k} lam_i . (-G (x_i - x_k) / s_ik^3),
+ * with T(r) = I / s^3 - 3 r r^T / s^5 (even in r). Outputs g (nk x 3), gm (nk).
+ * ------------------------------------------------------------------------- */
+void oracle_grav_vjp_rows(int64_t n, const double *x, const double *m, double G,
+                          double eps2, const double *lam, int64_t nk, const int64_t *idx,
+                          double *g, double *gm)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < nk; ++q) {
+        const int64_t k = idx[q];
+        double acc[3] = {0.0, 0.0, 0.0}, dm = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (i == k)
+                continue;
+            double r[3] = {x[3 * i] - x[3 * k], x[3 * i + 1] - x[3 * k + 1],
+                           x[3 * i + 2] - x[3 * k + 2]};
+            double s2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + eps2;
+            double s = sqrt(s2);
+            double s3 = s2 * s, s5 = s3 * s2;
+            for (int a = 0; a < 3; ++a) {
+                double Ti = 0.0, Tk = 0.0;  /* (T lam_i)_a and (T lam_k)_a */
+                for (int b = 0; b < 3; ++b) {
+                    double T = (a == b ? 1.0 / s3 : 0.0) - 3.0 * r[a] * r[b] / s5;
+                    Ti += T * lam[3 * i + b];
+                    Tk += T * lam[3 * k + b];
+                }
+                acc[a] += G * m[k] * Ti - G * m[i] * Tk;
+            }
+            for (int a = 0; a < 3; ++a)
+                dm += lam[3 * i + a] * (-G * r[a] / s3);
+        }
+        for (int a = 0; a < 3; ++a)
+            g[3 * q + a] = acc[a];
+        if (gm)
+            gm[q] = dm;
+    }
 }
 
 /* ---------------------------------------------------------------------------

@@ -37,6 +37,24 @@ def test_grav_vjp_dot_product_identity():
         assert abs(np.sum(lam * Ju) - np.sum(g * u)) <= 1e-7 * np.abs(g * u).sum()
 
 
+def test_grav_vjp_rows_gather_equals_scatter():
+    """The row-subset VJP gathers each row from the blocks (i, k) and (k, k); the
+    full one scatters every ordered pair into the rows it touches. Two loop
+    structures written apart: the same numbers to rounding, duplicate and
+    unsorted indices included, unequal masses and G != 1."""
+    rng = np.random.default_rng(17)
+    n = 257
+    x = rng.standard_normal((n, 3))
+    m = rng.uniform(0.2, 2.0, n)
+    lam = rng.standard_normal((n, 3))
+    g, gm = oracle.grav_vjp(x, m, lam, G=0.7, eps=0.03)
+    idx = np.array([256, 0, 5, 100, 100, 17])
+    gr, gmr = oracle.grav_vjp(x, m, lam, G=0.7, eps=0.03, idx=idx)
+    scale_g = np.abs(g).max()
+    assert np.abs(gr - g[idx]).max() <= 1e-12 * scale_g
+    assert np.abs(gmr - gm[idx]).max() <= 1e-12 * np.abs(gm).max()
+
+
 def test_grav_mass_derivative():
     x, _, m = _grav_case()
     rng = np.random.default_rng(4)
