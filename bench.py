@@ -379,7 +379,7 @@ def kernel_hash() -> str:
     h = hashlib.sha1()
     pkg = os.path.join(ROOT, "paper_0706_3060_gb300")
     for f in ("csrc/force_kernel.cuh", "csrc/sym_kernel.cuh", "csrc/device_common.cuh",
-              "csrc/force_grav.cu"):
+              "csrc/fixed_point.cuh", "csrc/force_grav.cu"):
         with open(os.path.join(pkg, f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)

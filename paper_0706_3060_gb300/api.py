@@ -262,10 +262,12 @@ def forces_batched(systems, pos_m, vel, acc, prm=None, nsteps=0, acc_valid=False
 # ---------------------------------------------------------------------------
 def adjoint(pos_m, lam, prm=None, *, law=None, G=1.0, eps=0.0, alpha=1.0, grad_x=None,
             grad_m=None, grad_types=None, ntypes=4, accumulate=False, tile=-1, jsplit=0,
-            stream=None):
+            compensated=True, fixed=False, stream=None):
     """One force VJP: returns (grad_x (n,4), grad_m (n,), grad_types (2*ntypes,) or None).
     ``tile`` indexes tile table 5 (gravity), 6 (LJC) or 8 (LJC linear); -1:
-    tuned/default."""
+    tuned/default. ``compensated=False`` sets NBODY_NO_COMPENSATION (plain FP32
+    per-tile sums); ``fixed=True`` sets NBODY_FIXED_POINT (gravity, eps > 0: the
+    symmetric tiles add their per-block partials exactly in fixed point)."""
     _check4(pos_m, "pos_m")
     _check4(lam, "lam")
     law = (LAW_LJC if prm is not None else LAW_GRAV) if law is None else law
@@ -276,7 +278,8 @@ def adjoint(pos_m, lam, prm=None, *, law=None, G=1.0, eps=0.0, alpha=1.0, grad_x
     gt = grad_types
     if gt is None and law in (LAW_LJC, LAW_LJC_LINEAR):
         gt = torch.zeros(2 * ntypes, dtype=torch.float64, device=dev)
-    p = params(law, G, eps, accumulate=accumulate, tile=tile, jsplit=jsplit)
+    p = params(law, G, eps, compensated=compensated, accumulate=accumulate, tile=tile,
+               jsplit=jsplit, fixed=fixed)
     check(_lib().nbody_adjoint(_ptr(pos_m), _ptr(prm), _ptr(lam), _ptr(gx), _ptr(gm), _ptr(gt),
                                int(ntypes), float(alpha), n, ctypes.byref(p),
                                _stream(stream, dev)), "nbody_adjoint")

@@ -9,6 +9,7 @@
 
 #include "aux_types.h"
 #include "device_common.cuh"
+#include "fixed_point.cuh"
 #include "leapfrog.cuh"
 
 namespace nbody {
@@ -94,11 +95,9 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
           for (int kb = 0; kb < own_b; ++kb) take(kb * sp + own_s);
           for (int k = k_all; k < slices; ++k) take(k);
         }
-        const double inv = *f.fx_inv, finv = inv * 0x1p-32;
-        const double dx = fma(double(fr[0]), finv, double(sx) * inv),
-                     dy = fma(double(fr[1]), finv, double(sy) * inv),
-                     dz = fma(double(fr[2]), finv, double(sz) * inv),
-                     dw = fma(double(fr[3]), finv, double(sw) * inv);
+        const double inv = *f.fx_inv;
+        const double dx = fixed_value(sx, fr[0], inv), dy = fixed_value(sy, fr[1], inv),
+                     dz = fixed_value(sz, fr[2], inv), dw = fixed_value(sw, fr[3], inv);
         t = make_float4(float(dx), float(dy), float(dz), float(dw));
         r = make_float4(float(dx - double(t.x)), float(dy - double(t.y)),
                         float(dz - double(t.z)), float(dw - double(t.w)));

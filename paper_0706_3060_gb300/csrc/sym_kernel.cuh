@@ -43,6 +43,7 @@
 
 #include <cmath>
 
+#include "fixed_point.cuh"
 #include "force_kernel.cuh"
 
 namespace nbody {
@@ -84,24 +85,10 @@ __device__ __forceinline__ void sym_store(const ForceArgs &a, long long slot_bas
   if (a.acc64) {
     const float sc = __ldg(a.fscale);
     unsigned long long *p = reinterpret_cast<unsigned long long *>(a.acc64) + particle;
-    const long long st = a.stride;
-    // v 2^S split into its integer part (word c) and its fraction in units of 2^-32
-    // (word 4 + c): both exact for an FP32 partial (to 2^-(S+32)), so the integer
-    // sums are exact whatever the softening makes of the grid spacing 2^-S; the
-    // fraction word is touched only when the fraction is nonzero
-    auto add = [&](float v, int c) {
-      const float t = v * sc;      // exact: sc is a power of two
-      const float h = truncf(t);   // integer part, |h| < 2^62
-      atomicAdd(p + c * st, static_cast<unsigned long long>(static_cast<long long>(h)));
-      if (fabsf(t) < 16777216.0f) {  // from 2^24 on an FP32 value has no fraction bits
-        const long long lo = __float2ll_rn((t - h) * 4294967296.0f);  // t - h is exact
-        if (lo != 0) atomicAdd(p + (4 + c) * st, static_cast<unsigned long long>(lo));
-      }
-    };
-    add(x, 0);
-    add(y, 1);
-    add(z, 2);
-    if (POT) add(w, 3);
+    fixed_add(p, a.stride, 0, x, sc);
+    fixed_add(p, a.stride, 1, y, sc);
+    fixed_add(p, a.stride, 2, z, sc);
+    if (POT) fixed_add(p, a.stride, 3, w, sc);
     return;
   }
   const long long idx = slot_base + particle;

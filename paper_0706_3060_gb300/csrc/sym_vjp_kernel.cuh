@@ -16,6 +16,7 @@
 // (x x y y), then (z z m m), (lx lx ly ly) and (lz lz 0 0) words.
 #pragma once
 
+#include "fixed_point.cuh"
 #include "sym_kernel.cuh"
 #include "vjp_kernel.cuh"
 
@@ -78,8 +79,26 @@ __device__ __forceinline__ void sym_gvjp_pair2(float2 X, float2 Y, float2 Z, flo
   }
 }
 
+// One particle's (g.x, g.y, g.z, mass term) partial of one CTA: added exactly in
+// fixed point to the particle's accumulator (a.acc64), or stored to element
+// `particle` of the slot that starts at slot_base.
+__device__ __forceinline__ void vjp_store(const VjpArgs &a, long long slot_base, int particle,
+                                          float x, float y, float z, float w) {
+  if (a.acc64) {
+    const float sc = __ldg(a.fscale);
+    unsigned long long *p = reinterpret_cast<unsigned long long *>(a.acc64) + particle;
+    fixed_add(p, a.stride, 0, x, sc);
+    fixed_add(p, a.stride, 1, y, sc);
+    fixed_add(p, a.stride, 2, z, sc);
+    fixed_add(p, a.stride, 3, w, sc);
+    return;
+  }
+  a.part_hi[slot_base + particle] = make_float4(x, y, z, w);
+}
+
 // Partials: slot ob of part_hi holds (g.x, g.y, g.z, mass term) of block ob's
-// contribution, before the G scaling of vjp_finalize_kernel.
+// contribution, before the G scaling of vjp_finalize_kernel; with a.acc64 every
+// CTA adds its partials to the particles' fixed-point accumulators instead.
 template <int NT, int I, int MINB = 1>
 __global__ void __launch_bounds__(NT, MINB) sym_gvjp_kernel(const VjpArgs a) {
   griddep_start();
@@ -211,11 +230,12 @@ __global__ void __launch_bounds__(NT, MINB) sym_gvjp_kernel(const VjpArgs a) {
 #pragma unroll
   for (int r = 0; r < I; ++r)
     if (ig[r] >= 0)
-      a.part_hi[ibase + ig[r]] = make_float4(ax[r].x + ax[r].y, ay[r].x + ay[r].y,
-                                             az[r].x + az[r].y, aw[r].x + aw[r].y);
+      vjp_store(a, ibase, ig[r], ax[r].x + ax[r].y, ay[r].x + ay[r].y, az[r].x + az[r].y,
+                aw[r].x + aw[r].y);
   if (diag) return;
   __syncthreads();
-  const long long jbase = (long long)(bi * np_ + s_) * a.stride + j0 + 2 * p0_;
+  const long long jbase = (long long)(bi * np_ + s_) * a.stride;
+  const int jfirst = j0 + 2 * p0_;
   const int nq = min(2 * npairs, nsrc - 2 * p0_);
   for (int q = tid; q < nq; q += NT) {
     const int pp = q >> 1, h = q & 1;
@@ -228,7 +248,7 @@ __global__ void __launch_bounds__(NT, MINB) sym_gvjp_kernel(const VjpArgs a) {
       vw += Jw[2 * (3 * P + pp) + h];
     }
     // the sources receive the negated terms
-    a.part_hi[jbase + q] = make_float4(-vx, -vy, -vz, -vw);
+    vjp_store(a, jbase, jfirst + q, -vx, -vy, -vz, -vw);
   }
 }
 

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "nbody.h"
+#include "fixed_point.cuh"
 #include "vjp_kernel.cuh"
 
 namespace nbody {
@@ -33,6 +34,10 @@ struct VjpFinalizeArgs {
   // every slot from its own block on (sym_split <= 1: every slot)
   int sym_block;
   int sym_split;
+  // exact fixed-point accumulators of the symmetric gravity VJP (eight int64
+  // arrays of stride `stride`, see VjpArgs) and the word holding 2^-S; null: slots
+  const long long *acc64;
+  const double *fx_inv;
 };
 
 __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs f) {
@@ -49,7 +54,7 @@ __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs
     const int own_s = sp > 1 ? ((i - own_b * f.sym_block) >> 1) / (f.sym_block / 2 / sp) : 0;
     const int below = own_b;        // slots own_s, own_s + sp, ... below the own block
     const int k_all = own_b * sp;   // every slot from here on
-    const int count = below + (f.slices - k_all);
+    const int count = f.acc64 ? 0 : below + (f.slices - k_all);
     auto offset = [&](int c) {
       const int k = c < below ? c * sp + own_s : k_all + (c - below);
       return (long long)k * f.stride + i;
@@ -95,7 +100,15 @@ __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs
       if (lj)
         add(hB, oB, f.part_hi[f.bstride + o], f.part_lo ? f.part_lo[f.bstride + o] : zero);
     }
-    const float ax = hA.x + oA.x, ay = hA.y + oA.y, az = hA.z + oA.z, aw = hA.w + oA.w;
+    float ax = hA.x + oA.x, ay = hA.y + oA.y, az = hA.z + oA.z, aw = hA.w + oA.w;
+    if (f.acc64) {  // the exact sums, rounded once
+      const long long st = f.stride;
+      const double inv = *f.fx_inv;
+      ax = float(fixed_value(f.acc64[i], f.acc64[4 * st + i], inv));
+      ay = float(fixed_value(f.acc64[st + i], f.acc64[5 * st + i], inv));
+      az = float(fixed_value(f.acc64[2 * st + i], f.acc64[6 * st + i], inv));
+      aw = float(fixed_value(f.acc64[3 * st + i], f.acc64[7 * st + i], inv));
+    }
     float gx, gy, gz, gm;
     if (!lj) {
       gx = f.G * ax;
@@ -200,25 +213,128 @@ __global__ void type_reduce_kernel(const double *part, int nblk, int ntypes, dou
   if (t < ntypes) out[which * ntypes + t] += s;
 }
 
+// Fixed-point accumulation of the symmetric gravity VJP: the accumulators that
+// the interleave launch zeroes, and the words from which it forms the scale.
+struct VjpAtomicPrep {
+  long long *acc64;  // 8 x n accumulators, or null (slots: nothing to prepare)
+  double *part;      // four doubles per interleave block: sum |m|, max |m|, sum |lam|, max |lam|
+  unsigned *ticket;  // zero before the launch; zero again after it
+  float eps2;
+  float *scale;      // out: 2^S, read by the VJP kernel
+  double *inv;       // out: 2^-S, read by vjp_finalize_kernel
+};
+
+// Scale of the VJP's fixed-point sums. With y = 1/s <= 1/eps and the matrix
+// I - 3 y^2 d d^T of norm at most 2 (its eigenvalues are 1 and 1 - 3 r^2 / s^2),
+// a particle's J^T lambda sum obeys |g_k| <= 2 / eps^3 (m_max L + lam_max M), and
+// its mass term |sum lam_j . d y^3| <= 2 / (3 sqrt(3) eps^2) L (the maximum of
+// r / s^3), with M = sum |m| and L = sum |lam_j|. Writes the largest 2^S that keeps
+// both below 2^62, and 2^-S.
+__device__ __forceinline__ void vjp_scale_of(double M, double mmax, double L, double lmax,
+                                             float eps2, float *scale, double *inv) {
+  const double e2 = double(eps2), e = sqrt(e2);
+  const double bound =
+      fmax(2.0 * (mmax * L + lmax * M) / (e2 * e), 0.3849001794597505 * L / e2) + 1e-300;
+  int S = int(floor(62.0 - log2(bound)));
+  S = S > 126 ? 126 : (S < -126 ? -126 : S);
+  *scale = ldexpf(1.0f, S);
+  *inv = ldexp(1.0, -S);
+}
+
 // Gravity VJP sources of the Newton-symmetric tiles, block by block (B
 // particles, 2B float4 per block): the B/2 pairs' (x0 x1 y0 y1), then their
 // (z0 z1 m0 m1), (lx0 lx1 ly0 ly1) and (lz0 lz1 0 0). Pairs past n are not written
-// (the kernel copies only the block's own pairs).
-__global__ void interleave_vjp_pairs_blocked_kernel(const float4 *pos, const float4 *lam,
-                                                    float4 *jp, int n, int B) {
+// (the kernel copies only the block's own pairs). With at.acc64 the launch also
+// zeroes its particles' accumulators and forms the fixed-point scale: every block
+// reduces |m| and |lam| of its particles in FP64 in a fixed order, and the block
+// that finishes last (atomicInc ticket, which wraps back to zero) combines the
+// block results in index order -- the same bits whichever block is last.
+__global__ void __launch_bounds__(256) interleave_vjp_pairs_blocked_kernel(
+    const float4 *pos, const float4 *lam, float4 *jp, int n, int B, VjpAtomicPrep at) {
   griddep_start();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (2 * p >= n) return;
-  const bool two = 2 * p + 1 < n;
-  const float4 a = pos[2 * p], la = lam[2 * p];
-  const float4 b = two ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
-  const float4 lb = two ? lam[2 * p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const int blk = (2 * p) / B, P = B / 2, pp = p - blk * P;
-  const long long q = (long long)blk * 2 * B + pp;
-  jp[q] = make_float4(a.x, b.x, a.y, b.y);
-  jp[q + P] = make_float4(a.z, b.z, a.w, b.w);
-  jp[q + 2 * P] = make_float4(la.x, lb.x, la.y, lb.y);
-  jp[q + 3 * P] = make_float4(la.z, lb.z, 0.f, 0.f);
+  double v[4] = {0.0, 0.0, 0.0, 0.0};  // sum |m|, max |m|, sum |lam|, max |lam|
+  if (2 * p < n) {
+    const bool two = 2 * p + 1 < n;
+    const float4 a = pos[2 * p], la = lam[2 * p];
+    const float4 b = two ? pos[2 * p + 1] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+    const float4 lb = two ? lam[2 * p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int blk = (2 * p) / B, P = B / 2, pp = p - blk * P;
+    const long long q = (long long)blk * 2 * B + pp;
+    jp[q] = make_float4(a.x, b.x, a.y, b.y);
+    jp[q + P] = make_float4(a.z, b.z, a.w, b.w);
+    jp[q + 2 * P] = make_float4(la.x, lb.x, la.y, lb.y);
+    jp[q + 3 * P] = make_float4(la.z, lb.z, 0.f, 0.f);
+    if (at.acc64) {
+      const double ma = fabs(double(a.w)), mb = fabs(double(b.w));
+      const double na = sqrt(double(la.x) * la.x + double(la.y) * la.y + double(la.z) * la.z);
+      const double nb = sqrt(double(lb.x) * lb.x + double(lb.y) * lb.y + double(lb.z) * lb.z);
+      v[0] = ma + mb;
+      v[1] = fmax(ma, mb);
+      v[2] = na + nb;
+      v[3] = fmax(na, nb);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        at.acc64[(long long)c * n + 2 * p] = 0;
+        if (two) at.acc64[(long long)c * n + 2 * p + 1] = 0;
+      }
+    }
+  }
+  if (!at.acc64) return;  // the same for every thread of the launch
+  __shared__ double red[8][4];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  auto warp_reduce = [&](double x[4]) {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      x[0] += __shfl_down_sync(0xffffffffu, x[0], off);
+      x[1] = fmax(x[1], __shfl_down_sync(0xffffffffu, x[1], off));
+      x[2] += __shfl_down_sync(0xffffffffu, x[2], off);
+      x[3] = fmax(x[3], __shfl_down_sync(0xffffffffu, x[3], off));
+    }
+  };
+  warp_reduce(v);
+  if (lane == 0)
+    for (int k = 0; k < 4; ++k) red[warp][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bs[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int w = 0; w < 8; ++w) {
+      bs[0] += red[w][0];
+      bs[1] = fmax(bs[1], red[w][1]);
+      bs[2] += red[w][2];
+      bs[3] = fmax(bs[3], red[w][3]);
+    }
+    for (int k = 0; k < 4; ++k) at.part[4 * blockIdx.x + k] = bs[k];
+    __threadfence();  // the block result is visible before the ticket is taken
+    last = atomicInc(at.ticket, gridDim.x - 1) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  const volatile double *part = at.part;
+  for (int k = threadIdx.x; k < int(gridDim.x); k += 256) {
+    t[0] += part[4 * k];
+    t[1] = fmax(t[1], part[4 * k + 1]);
+    t[2] += part[4 * k + 2];
+    t[3] = fmax(t[3], part[4 * k + 3]);
+  }
+  warp_reduce(t);
+  __syncthreads();
+  if (lane == 0)
+    for (int k = 0; k < 4; ++k) red[warp][k] = t[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double M = 0.0, mmax = 0.0, L = 0.0, lmax = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      M += red[w][0];
+      mmax = fmax(mmax, red[w][1]);
+      L += red[w][2];
+      lmax = fmax(lmax, red[w][3]);
+    }
+    vjp_scale_of(M, mmax, L, lmax, at.eps2, at.scale, at.inv);
+  }
 }
 
 // Packed gravity VJP sources: per pair (x0 x1 y0 y1)(z0 z1 m0 m1)(lx0 lx1 ly0 ly1)

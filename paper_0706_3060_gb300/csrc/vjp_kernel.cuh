@@ -41,6 +41,12 @@ struct VjpArgs {
   float eps2;
   int comp;
   int pdl;  // host side: launch with programmatic dependent launch (griddep_start)
+  // Newton-symmetric gravity VJP with exact fixed-point accumulation: eight int64
+  // arrays of stride `stride` (integer parts of g.x, g.y, g.z and the mass term
+  // scaled by *fscale, then their fractions in units of 2^-32), zeroed before the
+  // launch; null: per-block partial slots in part_hi
+  long long *acc64;
+  const float *fscale;
 };
 
 __device__ __forceinline__ float rcp_hw(float x) {

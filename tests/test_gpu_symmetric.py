@@ -196,6 +196,11 @@ def test_symmetric_vjp_unsoftened_and_repeatable():
 
 
 def test_symmetric_vjp_planning_rules():
+    """One partial slot per block (no softening, or plain sums asked for) is
+    refused where the slots pass the cap; the fixed-point path, which softened
+    gravity takes there, has none (it runs at 2^20 in
+    test_symmetric_vjp_fixed_point_at_two_to_the_twenty); fixed point without
+    softening is refused."""
     nb = lib()
     t = _sym_vjp_tiles()[0]
     B = nb.tile_info(nb.TABLE_VJP_GRAV, t)["j_tile"]
@@ -204,7 +209,61 @@ def test_symmetric_vjp_planning_rules():
     pos = torch.zeros((n_big, 4), device=dev())
     pos[:, 0] = torch.arange(n_big, device=dev(), dtype=torch.float32)
     with pytest.raises(nb.NBodyError):
-        nb.adjoint(pos, torch.zeros_like(pos), eps=0.01, tile=t)
+        nb.adjoint(pos, torch.zeros_like(pos), eps=0.0, tile=t)
+    with pytest.raises(nb.NBodyError):
+        nb.adjoint(pos, torch.zeros_like(pos), eps=0.01, tile=t, compensated=False)
+    small = torch.zeros((8, 4), device=dev())
+    with pytest.raises(nb.NBodyError):
+        nb.adjoint(small, small, eps=0.0, tile=t, fixed=True)
+
+
+@pytest.mark.parametrize("n", [257, 3001])
+def test_symmetric_vjp_fixed_point_and_slots(n):
+    """Softened gravity: the exact fixed-point sums (fixed=True), the per-block
+    slots with compensation (default at this size) and without (compensated=False)
+    of every symmetric VJP tile and source split against the oracle; the
+    fixed-point result is bitwise repeatable."""
+    nb = lib()
+    g = workloads.plummer(n, seed=800 + n, eps=0.01)
+    pos, _ = grav_tensors(g)
+    eps = float(np.float32(g.eps))
+    lam = np.random.default_rng(n).standard_normal((n, 4)).astype(np.float32)
+    lt = torch.from_numpy(lam).to(dev())
+    x, _, m = g.f32_as_f64()
+    rg, rm = oracle.grav_vjp(x, m, lam[:, :3].astype(np.float64), G=1.3, eps=eps)
+    for tile in _sym_vjp_tiles():
+        for jsplit in (0, 2, 4):
+            for mode in ("fixed", "slots", "plain"):
+                kw = dict(fixed=mode == "fixed", compensated=mode != "plain")
+                gx, gm, _ = nb.adjoint(pos, lt, G=1.3, eps=eps, tile=tile, jsplit=jsplit, **kw)
+                assert_vjp_close(gx[:, :3].cpu().numpy(), gm.cpu().numpy(), rg, rm,
+                                 what=str((tile, jsplit, mode)))
+                if mode == "fixed":
+                    gx2, gm2, _ = nb.adjoint(pos, lt, G=1.3, eps=eps, tile=tile,
+                                             jsplit=jsplit, **kw)
+                    assert torch.equal(gx, gx2) and torch.equal(gm, gm2)
+
+
+@pytest.mark.slow
+def test_symmetric_vjp_fixed_point_at_two_to_the_twenty():
+    """N = 2^20, blocks of 512 in 2 parts: one slot per block and part would take
+    32 GiB (above the cap), so the softened VJP takes the fixed-point sums (64 B
+    per particle); 48 seeded particles against the oracle's rows, computed one by
+    one."""
+    nb = lib()
+    n = 1 << 20
+    g = workloads.plummer(n, seed=9, eps=workloads.plummer_softening(n))
+    pos, _ = grav_tensors(g)
+    eps = float(np.float32(g.eps))
+    lam = np.random.default_rng(9).standard_normal((n, 4)).astype(np.float32)
+    tile = [t for t in _sym_vjp_tiles()
+            if nb.tile_info(nb.TABLE_VJP_GRAV, t)["j_tile"] == 512][0]
+    gx, gm, _ = nb.adjoint(pos, torch.from_numpy(lam).to(dev()), eps=eps, tile=tile, jsplit=2)
+    idx = np.sort(np.random.default_rng(10).choice(n, 48, replace=False))
+    x, _, m = g.f32_as_f64()
+    rg, rm = oracle.grav_vjp(x, m, lam[:, :3].astype(np.float64), eps=eps, idx=idx)
+    it = torch.from_numpy(idx).to(dev())
+    assert_vjp_close(gx[it, :3].cpu().numpy(), gm[it].cpu().numpy(), rg, rm, what="2^20")
 
 
 def test_symmetric_forces_and_vjp_in_reverse_leapfrog():
