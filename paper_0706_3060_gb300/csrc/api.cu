@@ -20,12 +20,6 @@ int launch_finalize(const FinalizeArgs &f, cudaStream_t s, int *nblk_out, bool p
   return NBODY_OK;
 }
 
-int launch_diag_reduce(const double *part, int nblk, double *out, cudaStream_t s) {
-  diag_reduce_kernel<<<1, kFinThreads, 0, s>>>(part, nblk, out);
-  NB_CUDA(cudaGetLastError());
-  return NBODY_OK;
-}
-
 int launch_kick_drift(float4 *pos, float4 *vel, const float4 *acc, int n, float dt,
                       float4 *trace1, const int *sys_of, const void *sys, float4 *x_lo,
                       float4 *v_lo, cudaStream_t s) {

@@ -195,7 +195,6 @@ int timing_read(int which, int64_t *launches, double *total_ms);
 struct FinalizeArgs;
 // pdl: a programmatic dependent launch after the force kernel of the same call.
 int launch_finalize(const FinalizeArgs &f, cudaStream_t s, int *nblk_out, bool pdl = false);
-int launch_diag_reduce(const double *part, int nblk, double *out, cudaStream_t s);
 int launch_kick_drift(float4 *pos, float4 *vel, const float4 *acc, int n, float dt,
                       float4 *trace1, const int *sys_of, const void *sys, float4 *x_lo,
                       float4 *v_lo, cudaStream_t s);

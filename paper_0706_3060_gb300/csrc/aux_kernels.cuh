@@ -255,7 +255,8 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const FinalizeArg
   block_sum8(dv, f.diag_part + (size_t)blockIdx.x * kDiagFields);
   if (!f.diag_out) return;  // the same for every thread of the launch
   // The block that finishes last (atomicInc ticket, which wraps back to zero) adds
-  // the block rows as diag_reduce_kernel does: the same bits whichever block it is.
+  // the block rows: thread t the rows t, t + kFinThreads, ... in order, then the
+  // fixed tree of block_sum8 -- the same bits whichever block it is.
   __shared__ bool last;
   __threadfence();  // this block's row is visible before its ticket is taken
   __syncthreads();
@@ -287,17 +288,6 @@ __global__ void __launch_bounds__(256) fixed_scale_kernel(const float4 *pos, int
   }
 }
 
-// Deterministic final sum of the per-block FP64 diagnostics: one block,
-// thread t adds blocks t, t + 256, ... in order, then a fixed tree.
-__global__ void __launch_bounds__(kFinThreads) diag_reduce_kernel(const double *part, int nblk,
-                                                                  double *out) {
-  double v[kDiagFields] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int b = threadIdx.x; b < nblk; b += kFinThreads)
-#pragma unroll
-    for (int k = 0; k < kDiagFields; ++k) v[k] += part[(size_t)b * kDiagFields + k];
-  block_sum8(v, out);
-}
-
 // First half-kick and drift from a caller-supplied acceleration (NBODY_ACC_VALID).
 // Batched runs pass sys_of / sys for the per-system step size.
 __global__ void kick_drift_kernel(float4 *pos, float4 *vel, const float4 *acc, int n, float dt,
@@ -311,11 +301,6 @@ __global__ void kick_drift_kernel(float4 *pos, float4 *vel, const float4 *acc, i
     dt = sys[s].dt;
   }
   kick_drift_at(pos, vel, acc, dt, trace1, x_lo, v_lo, i);
-}
-
-__global__ void copy_float4_kernel(const float4 *src, float4 *dst, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = src[i];
 }
 
 // Packing: caller SoA doubles -> (x, y, z, m) float4.

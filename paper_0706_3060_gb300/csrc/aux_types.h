@@ -65,7 +65,7 @@ struct FinalizeArgs {
   int rezero;  // atomic plans: zero the accumulators after reading them
   // With kFinDiag: also add the block rows of diag_part into diag_out (8 doubles)
   // in the last block to finish, which diag_ticket (zero before the launch, zero
-  // again after it) elects; null: diag_reduce_kernel does it in a launch of its own.
+  // again after it) elects; null: only the block rows are written.
   double *diag_out;
   unsigned *diag_ticket;
 };
