@@ -129,3 +129,35 @@ def test_diagnostics_summed_in_the_finalize(law, n):
     for row, (x_, v_, a_) in zip(d, ((pos, vel, a0), (p, v, a))):
         ref, scale = _diag_ref(x_, v_, a_, law)
         np.testing.assert_array_less(np.abs(row - ref), 1e-11 * scale + 1e-300)
+
+
+@pytest.mark.parametrize("law", [0, 1])
+def test_step_loop_replays_from_a_cuda_graph(law):
+    """A multi-step call (its launches chained as programmatic dependent launches,
+    the finalize preparing each next step's sources) captured in a CUDA graph and
+    replayed gives the bits of the same call issued eagerly, report rows included."""
+    nb = lib()
+    pos, vel, prm, kw = _system(law, N_RAGGED, seed=91 + law)
+    kw.pop("law", None)
+    steps = 4
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    p1, v1 = pos.clone(), vel.clone()
+    a1 = torch.empty_like(p1)
+    d1 = torch.zeros((3, 8), dtype=torch.float64, device=pos.device)
+    with torch.cuda.stream(s):  # eager, and sizes the capturing stream's workspace
+        nb.step(p1, v1, a1, prm, law=law, nsteps=steps, report_every=2, diag=d1, **kw)
+    s.synchronize()
+    p2, v2 = pos.clone(), vel.clone()
+    a2 = torch.empty_like(p2)
+    d2 = torch.zeros_like(d1)
+    p0, v0 = p2.clone(), v2.clone()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        nb.step(p2, v2, a2, prm, law=law, nsteps=steps, report_every=2, diag=d2, **kw)
+    p2.copy_(p0)
+    v2.copy_(v0)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(p1, p2) and torch.equal(v1, v2) and torch.equal(a1[:, :3], a2[:, :3])
+    assert torch.equal(d1, d2)
