@@ -94,10 +94,12 @@ enum {
                                         per-tile sums (Sec. 3.2, GRAPE-6);
                                         results are bitwise independent of the
                                         j-split. params->tile then indexes
-                                        tile table 4. nbody_adjoint(_leapfrog):
-                                        the Newton-symmetric gravity VJP tiles
-                                        add their per-block partials exactly
-                                        in fixed point (64 B of scratch per
+                                        tile table 4. nbody_adjoint(_leapfrog),
+                                        nbody_forces_jerk, nbody_hermite_step:
+                                        the Newton-symmetric gravity VJP and
+                                        acceleration + jerk tiles add their
+                                        per-block partials exactly in fixed
+                                        point (64 / 128 B of scratch per
                                         particle); without the flag they do so
                                         only where one partial per block would
                                         pass the partial-sum cap. Other laws or

@@ -149,14 +149,16 @@ def forces_subset(pos_m, idx, prm=None, *, law=None, G=1.0, eps=0.0, pot=False, 
 
 
 def forces_jerk(pos_m, vel, *, G=1.0, eps=0.0, compensated=True, tile=-1, jsplit=0,
-                stream=None):
+                fixed=False, stream=None):
     """Acceleration and jerk (Table 1 GAJ): returns (acc, jerk), each (n, 4).
-    ``tile`` indexes tile table 7 (-1: tuned/default)."""
+    ``tile`` indexes tile table 7 (-1: tuned/default). ``fixed=True`` (eps > 0):
+    the symmetric tiles add their per-block partials exactly in fixed point."""
     _check4(pos_m, "pos_m")
     _check4(vel, "vel")
     acc = torch.empty_like(pos_m)
     jerk = torch.empty_like(pos_m)
-    p = params(LAW_GRAV, G, eps, compensated=compensated, tile=tile, jsplit=jsplit)
+    p = params(LAW_GRAV, G, eps, compensated=compensated, tile=tile, jsplit=jsplit,
+               fixed=fixed)
     check(_lib().nbody_forces_jerk(_ptr(pos_m), _ptr(vel), _ptr(acc), _ptr(jerk), pos_m.shape[0],
                                    ctypes.byref(p), _stream(stream, pos_m.device)),
           "nbody_forces_jerk")
@@ -164,12 +166,12 @@ def forces_jerk(pos_m, vel, *, G=1.0, eps=0.0, compensated=True, tile=-1, jsplit
 
 
 def hermite_step(pos_m, vel, acc, jerk, *, dt, nsteps=1, G=1.0, eps=0.0, acc_valid=False,
-                 compensated=True, tile=-1, jsplit=0, stream=None):
+                 compensated=True, tile=-1, jsplit=0, fixed=False, stream=None):
     """``nsteps`` fourth-order Hermite steps in place; acc/jerk receive (a, j) at exit."""
     for t, nm in ((pos_m, "pos_m"), (vel, "vel"), (acc, "acc"), (jerk, "jerk")):
         _check4(t, nm)
     p = params(LAW_GRAV, G, eps, compensated=compensated, acc_valid=acc_valid, tile=tile,
-               jsplit=jsplit)
+               jsplit=jsplit, fixed=fixed)
     check(_lib().nbody_hermite_step(_ptr(pos_m), _ptr(vel), _ptr(acc), _ptr(jerk),
                                     pos_m.shape[0], float(dt), int(nsteps), ctypes.byref(p),
                                     _stream(stream, pos_m.device)), "nbody_hermite_step")

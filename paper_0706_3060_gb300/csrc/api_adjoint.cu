@@ -36,8 +36,9 @@ struct VjpScratch {
   double *finv;
 };
 
-// When the symmetric gravity VJP adds its per-block partials in exact fixed point
-// (its scale needs a bound: eps > 0): 2 always (NBODY_FIXED_POINT), 1 only where
+// When the symmetric gravity VJP (and, with the same params, acceleration + jerk)
+// adds its per-block partials in exact fixed point (its scale needs a bound:
+// eps > 0): 2 always (NBODY_FIXED_POINT), 1 only where
 // one partial per particle, block and part would pass the partial-sum cap (at
 // N = 16384 and 65536 the slots measured 2-5% faster: eight integer atomics per
 // particle and CTA cost more than the slot writes and their read-back), 0 never
@@ -72,7 +73,7 @@ int vjp_prepare(int law, int n, int tile, int jsplit, int sms, cudaStream_t s, V
   if (jsplit <= 0) jsplit = tj;
   if (!tiles || tile < 0 || tile >= count)
     return set_error_msg(NBODY_EINVAL, "bad tile %d for table %d", tile, table);
-  const bool atomic = law == NBODY_LAW_GRAV && tiles[tile].sym &&
+  const bool atomic = (law == NBODY_LAW_GRAV || law == kLawGAJ) && tiles[tile].sym &&
                      (atomic_mode == 2 ||
                       (atomic_mode == 1 && !sym_fits(n, tiles[tile].tile_i)));
   if (tiles[tile].sym && !atomic && !sym_fits(n, tiles[tile].tile_i)) {
@@ -96,10 +97,11 @@ int vjp_prepare(int law, int n, int tile, int jsplit, int sms, cudaStream_t s, V
     if (pairs * S > 0x7fffffffLL)
       return set_error_msg(NBODY_EINVAL, "n = %d too large for symmetric tile %d split %d", n,
                            tile, S);
-    // the partials: one float4 slot per particle, block and part, or the eight
-    // int64 fixed-point accumulators per particle
+    // the partials: one float4 slot per particle, block and part, or the int64
+    // fixed-point accumulators per particle (8 for the VJP, 16 for acceleration
+    // and jerk)
     const size_t part =
-        atomic ? round_up(size_t(8) * size_t(n) * sizeof(long long), 256)
+        atomic ? round_up(size_t(8 * nblocks) * size_t(n) * sizeof(long long), 256)
                : round_up(size_t(nblocks) * size_t(nb) * S * size_t(n) * sizeof(float4), 256);
     const size_t ubytes = round_up(size_t(n) * sizeof(float4), 256);
     const int nblk = (n + 255) / 256;
@@ -211,7 +213,7 @@ int vjp_once(const float4 *pos, const float4 *prm, const float4 *lam, float4 *gr
       NB_CUDA(launch_kernel(interleave_vjp_pairs_blocked_kernel, pblocks, 256, 0, s, chained,
                             pos, src, sc.jp, n, sc.d->tile_i,
                             VjpAtomicPrep{sc.acc64, sc.vpart, sc.ticket, p.eps2, sc.fscale,
-                                          sc.finv}));
+                                          sc.finv, 0, 8}));
     else if (ljc)
       NB_CUDA(launch_kernel(interleave_ljc_vjp_pairs_kernel, pblocks, 256, 0, s, chained, pos,
                             src, prm, sc.jp, n));
@@ -348,9 +350,9 @@ int gaj_eval(const float4 *pos, const float4 *vel, float4 *acc, float4 *jerk, in
   if (sc.d->packed) {  // (x, m) and velocities of source pairs, interleaved
     const unsigned pblocks = unsigned(((n + 1) / 2 + 255) / 256);
     if (sc.d->sym)
-      interleave_vjp_pairs_blocked_kernel<<<pblocks, 256, 0, s>>>(pos, vel, sc.jp, n,
-                                                                  sc.d->tile_i,
-                                                                  VjpAtomicPrep{});
+      interleave_vjp_pairs_blocked_kernel<<<pblocks, 256, 0, s>>>(
+          pos, vel, sc.jp, n, sc.d->tile_i,
+          VjpAtomicPrep{sc.acc64, sc.vpart, sc.ticket, p.eps2, sc.fscale, sc.finv, 1, 16});
     else
       interleave_vjp_pairs_kernel<<<pblocks, 256, 0, s>>>(pos, vel, sc.jp, n);
     NB_CUDA(cudaGetLastError());
@@ -369,13 +371,16 @@ int gaj_eval(const float4 *pos, const float4 *vel, float4 *acc, float4 *jerk, in
   a.slice_len = sc.slice_len;
   a.eps2 = p.eps2;
   a.comp = (p.flags & NBODY_NO_COMPENSATION) ? 0 : 1;
+  a.acc64 = sc.acc64;
+  a.fscale = sc.acc64 ? sc.fscale : nullptr;
   const TimerMark tm = timer_begin(0, s);
   cudaError_t e = sc.d->launch(a, sc.grid, s);
   timer_end(tm, s);
   if (e != cudaSuccess)
     return set_error_msg(NBODY_ECUDA, "jerk kernel launch failed: %s", cudaGetErrorString(e));
   gaj_finalize_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(
-      sc.part_hi, sc.part_lo, n, sc.bstride, sc.slices, n, p.G, acc, jerk);
+      sc.part_hi, sc.part_lo, n, sc.bstride, sc.slices, n, p.G, acc, jerk, sc.acc64,
+      sc.acc64 ? sc.finv : nullptr);
   NB_CUDA(cudaGetLastError());
   return NBODY_OK;
 }
@@ -385,10 +390,12 @@ int check_jerk_params(const nbody_params *params, uint32_t extra_flags) {
   const nbody_params &p = *params;
   if (p.law != NBODY_LAW_GRAV)
     return set_error_msg(NBODY_EINVAL, "acceleration + jerk is defined for gravity only");
-  if (p.flags & ~(uint32_t)(NBODY_NO_COMPENSATION | extra_flags))
+  if (p.flags & ~(uint32_t)(NBODY_NO_COMPENSATION | NBODY_FIXED_POINT | extra_flags))
     return set_error_msg(NBODY_EUNSUPPORTED, "unsupported flag bits 0x%x", p.flags);
   if (!(p.eps2 >= 0.0f) || !std::isfinite(p.G))
     return set_error_msg(NBODY_EINVAL, "bad G or eps2");
+  if ((p.flags & NBODY_FIXED_POINT) && !(p.eps2 > 0.0f))
+    return set_error_msg(NBODY_EINVAL, "fixed-point accumulation needs eps2 > 0");
   return NBODY_OK;
 }
 
@@ -482,7 +489,8 @@ int nbody_forces_jerk(const void *pos_m, const void *vel, void *acc, void *jerk,
   NB_TRY(check_dev_ptrs({pos_m, vel, acc, jerk}));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   VjpScratch sc{};
-  NB_TRY(vjp_prepare(kLawGAJ, int(n), params->tile, params->jsplit, sms, s, &sc, 0));
+  NB_TRY(vjp_prepare(kLawGAJ, int(n), params->tile, params->jsplit, sms, s, &sc, 0,
+                     vjp_atomic_mode(*params)));
   return gaj_eval(static_cast<const float4 *>(pos_m), static_cast<const float4 *>(vel),
                   static_cast<float4 *>(acc), static_cast<float4 *>(jerk), int(n), *params, sc, s);
 }
@@ -507,7 +515,8 @@ int nbody_hermite_step(void *pos_m, void *vel, void *acc, void *jerk, int64_t n,
   // scratch: GAJ partials, then predicted (x, v) and the new (a, j)
   VjpScratch sc{};
   const size_t q = round_up(size_t(n) * sizeof(float4), 256);
-  NB_TRY(vjp_prepare(kLawGAJ, int(n), params->tile, params->jsplit, sms, s, &sc, 4 * q));
+  NB_TRY(vjp_prepare(kLawGAJ, int(n), params->tile, params->jsplit, sms, s, &sc, 4 * q,
+                     vjp_atomic_mode(*params)));
   float4 *xp = reinterpret_cast<float4 *>(sc.extra);
   float4 *vp = reinterpret_cast<float4 *>(sc.extra + q);
   float4 *a1 = reinterpret_cast<float4 *>(sc.extra + 2 * q);

@@ -107,7 +107,9 @@ int nbody_tune(int32_t table, const void *pos_m, const void *prm, int64_t n, flo
       if (tiles[t].sym) {  // j-split = source parts per block; skip what the plan refuses
         // softened gravity (forces and the VJP) accumulates in fixed point where
         // the slots would not fit (no partial-sum cap)
-        const bool atomic = (sym_atomic_law(table) || table == kTableVjpGrav) && eps2 > 0.0f;
+        const bool atomic =
+            (sym_atomic_law(table) || table == kTableVjpGrav || table == kTableJerk) &&
+            eps2 > 0.0f;
         if (!atomic && !sym_fits(n, tiles[t].tile_i)) continue;
         if (js > 0 && table == kTableVjpGrav) {  // the VJP plan takes powers of two
           if ((js & (js - 1)) != 0 || js > std::min(8, tiles[t].tile_i / 64)) continue;

@@ -316,6 +316,30 @@ __device__ __forceinline__ void sym_gaj_pair2(float2 X, float2 Y, float2 Z, floa
   }
 }
 
+// One particle's acceleration and jerk partial of one CTA: added exactly in fixed
+// point (a.acc64: eight int64 arrays for the acceleration, eight more for the
+// jerk, each set laid out as in fixed_add), or stored to element `particle` of
+// the slot at slot_base of partial blocks A (acceleration) and B (jerk).
+__device__ __forceinline__ void gaj_store(const VjpArgs &a, long long slot_base, int particle,
+                                          float ax, float ay, float az, float jx, float jy,
+                                          float jz) {
+  if (a.acc64) {
+    const float sc = __ldg(a.fscale);
+    const long long st = a.stride;
+    unsigned long long *pa = reinterpret_cast<unsigned long long *>(a.acc64) + particle;
+    unsigned long long *pj = pa + 8 * st;
+    fixed_add(pa, st, 0, ax, sc);
+    fixed_add(pa, st, 1, ay, sc);
+    fixed_add(pa, st, 2, az, sc);
+    fixed_add(pj, st, 0, jx, sc);
+    fixed_add(pj, st, 1, jy, sc);
+    fixed_add(pj, st, 2, jz, sc);
+    return;
+  }
+  a.part_hi[slot_base + particle] = make_float4(ax, ay, az, 0.0f);
+  a.part_hi[a.bstride + slot_base + particle] = make_float4(jx, jy, jz, 0.0f);
+}
+
 template <int NT, int I, int MINB = 1>
 __global__ void __launch_bounds__(NT, MINB) sym_gaj_kernel(const VjpArgs a) {
   griddep_start();
@@ -435,15 +459,12 @@ __global__ void __launch_bounds__(NT, MINB) sym_gaj_kernel(const VjpArgs a) {
   const long long ibase = (long long)bj * a.stride;
 #pragma unroll
   for (int r = 0; r < I; ++r)
-    if (ig[r] >= 0) {
-      a.part_hi[ibase + ig[r]] =
-          make_float4(ax[r].x + ax[r].y, ay[r].x + ay[r].y, az[r].x + az[r].y, 0.0f);
-      a.part_hi[a.bstride + ibase + ig[r]] =
-          make_float4(bx[r].x + bx[r].y, by[r].x + by[r].y, bz[r].x + bz[r].y, 0.0f);
-    }
+    if (ig[r] >= 0)
+      gaj_store(a, ibase, ig[r], ax[r].x + ax[r].y, ay[r].x + ay[r].y, az[r].x + az[r].y,
+                bx[r].x + bx[r].y, by[r].x + by[r].y, bz[r].x + bz[r].y);
   if (diag) return;
   __syncthreads();
-  const long long jbase = (long long)bi * a.stride + j0;
+  const long long jbase = (long long)bi * a.stride;
   for (int q = tid; q < nsrc; q += NT) {
     const int pp = q >> 1, h = q & 1;
     float v[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -452,8 +473,7 @@ __global__ void __launch_bounds__(NT, MINB) sym_gaj_kernel(const VjpArgs a) {
 #pragma unroll
       for (int c = 0; c < 6; ++c) v[c] += Jw[(2 * c + h) * P + pp];
     }
-    a.part_hi[jbase + q] = make_float4(v[0], v[1], v[2], 0.0f);
-    a.part_hi[a.bstride + jbase + q] = make_float4(v[3], v[4], v[5], 0.0f);
+    gaj_store(a, jbase, j0 + q, v[0], v[1], v[2], v[3], v[4], v[5]);
   }
 }
 

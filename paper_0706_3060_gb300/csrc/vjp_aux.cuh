@@ -170,13 +170,31 @@ __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpFinalizeArgs
 
 // GAJ: fixed-order compensated sum of the per-slice partials of A (acceleration)
 // and B (jerk), scaled by G.
+// acc64 (with inv = 2^-S): the exact fixed-point sums of the Newton-symmetric
+// tiles, sixteen int64 arrays of stride `stride` (acceleration x, y, z, -, their
+// fractions, then the same four and four for the jerk), rounded once; else null.
 __global__ void __launch_bounds__(256) gaj_finalize_kernel(const float4 *part_hi,
                                                            const float4 *part_lo,
                                                            long long stride, long long bstride,
                                                            int slices, int n, float G,
-                                                           float4 *acc, float4 *jerk) {
+                                                           float4 *acc, float4 *jerk,
+                                                           const long long *acc64,
+                                                           const double *inv) {
   const int i = blockIdx.x * 256 + threadIdx.x;
   if (i >= n) return;
+  if (acc64) {
+    const double iv = *inv;
+    auto v = [&](int c) {
+      return G * float(fixed_value(acc64[c * stride + i], acc64[(4 + c) * stride + i], iv));
+    };
+    auto w = [&](int c) {
+      return G * float(fixed_value(acc64[(8 + c) * stride + i], acc64[(12 + c) * stride + i],
+                                   iv));
+    };
+    acc[i] = make_float4(v(0), v(1), v(2), 0.0f);
+    jerk[i] = make_float4(w(0), w(1), w(2), 0.0f);
+    return;
+  }
   // part_lo == nullptr: partials without low parts (Newton-symmetric tiles)
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 hA = part_hi[i], oA = part_lo ? part_lo[i] : zero;
@@ -216,12 +234,14 @@ __global__ void type_reduce_kernel(const double *part, int nblk, int ntypes, dou
 // Fixed-point accumulation of the symmetric gravity VJP: the accumulators that
 // the interleave launch zeroes, and the words from which it forms the scale.
 struct VjpAtomicPrep {
-  long long *acc64;  // 8 x n accumulators, or null (slots: nothing to prepare)
+  long long *acc64;  // nwords x n accumulators, or null (slots: nothing to prepare)
   double *part;      // four doubles per interleave block: sum |m|, max |m|, sum |lam|, max |lam|
   unsigned *ticket;  // zero before the launch; zero again after it
   float eps2;
   float *scale;      // out: 2^S, read by the VJP kernel
   double *inv;       // out: 2^-S, read by vjp_finalize_kernel
+  int kind;          // 0: the VJP's bound (lam); 1: acceleration + jerk (lam = velocities)
+  int nwords;        // int64 arrays to zero: 8 (VJP), 16 (acceleration and jerk)
 };
 
 // Scale of the VJP's fixed-point sums. With y = 1/s <= 1/eps and the matrix
@@ -235,6 +255,21 @@ __device__ __forceinline__ void vjp_scale_of(double M, double mmax, double L, do
   const double e2 = double(eps2), e = sqrt(e2);
   const double bound =
       fmax(2.0 * (mmax * L + lmax * M) / (e2 * e), 0.3849001794597505 * L / e2) + 1e-300;
+  int S = int(floor(62.0 - log2(bound)));
+  S = S > 126 ? 126 : (S < -126 ? -126 : S);
+  *scale = ldexpf(1.0f, S);
+  *inv = ldexp(1.0, -S);
+}
+
+// Scale of the fixed-point sums of acceleration + jerk. With |d| / s^3 at most
+// 2 / (3 sqrt(3) eps^2), u = v_j - v_i of norm at most 2 v_max and
+// |u - 3 y^2 (d.u) d| <= 4 |u|, a particle's acceleration sum obeys |a| <= M 2 /
+// (3 sqrt(3) eps^2) and its jerk sum |j| <= 8 v_max M / eps^3 (M = sum |m|).
+// Writes the largest 2^S that keeps both below 2^62, and 2^-S.
+__device__ __forceinline__ void gaj_scale_of(double M, double vmax, float eps2, float *scale,
+                                             double *inv) {
+  const double e2 = double(eps2), e = sqrt(e2);
+  const double bound = fmax(0.3849001794597505 * M / e2, 8.0 * vmax * M / (e2 * e)) + 1e-300;
   int S = int(floor(62.0 - log2(bound)));
   S = S > 126 ? 126 : (S < -126 ? -126 : S);
   *scale = ldexpf(1.0f, S);
@@ -273,8 +308,7 @@ __global__ void __launch_bounds__(256) interleave_vjp_pairs_blocked_kernel(
       v[1] = fmax(ma, mb);
       v[2] = na + nb;
       v[3] = fmax(na, nb);
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < at.nwords; ++c) {
         at.acc64[(long long)c * n + 2 * p] = 0;
         if (two) at.acc64[(long long)c * n + 2 * p + 1] = 0;
       }
@@ -333,7 +367,10 @@ __global__ void __launch_bounds__(256) interleave_vjp_pairs_blocked_kernel(
       L += red[w][2];
       lmax = fmax(lmax, red[w][3]);
     }
-    vjp_scale_of(M, mmax, L, lmax, at.eps2, at.scale, at.inv);
+    if (at.kind == 1)
+      gaj_scale_of(M, lmax, at.eps2, at.scale, at.inv);
+    else
+      vjp_scale_of(M, mmax, L, lmax, at.eps2, at.scale, at.inv);
   }
 }
 

@@ -351,9 +351,14 @@ def test_symmetric_jerk_ragged_sizes(n):
     tiles = _sym_ljc_tiles(nb.TABLE_JERK)
     assert tiles
     for tile in tiles:
-        acc, jerk = nb.forces_jerk(pos, vel, G=1.3, eps=eps, tile=tile)
-        assert_forces_close(acc[:, :3].cpu().numpy(), ra, what=f"GAJ acc tile {tile} n {n}")
-        assert_forces_close(jerk[:, :3].cpu().numpy(), rj, what=f"GAJ jerk tile {tile} n {n}")
+        for fixed in (False, True):  # per-block slots; exact fixed-point sums
+            acc, jerk = nb.forces_jerk(pos, vel, G=1.3, eps=eps, tile=tile, fixed=fixed)
+            what = f"tile {tile} n {n} fixed {fixed}"
+            assert_forces_close(acc[:, :3].cpu().numpy(), ra, what=f"GAJ acc {what}")
+            assert_forces_close(jerk[:, :3].cpu().numpy(), rj, what=f"GAJ jerk {what}")
+            if fixed:
+                acc2, jerk2 = nb.forces_jerk(pos, vel, G=1.3, eps=eps, tile=tile, fixed=True)
+                assert torch.equal(acc, acc2) and torch.equal(jerk, jerk2)
 
 
 def test_symmetric_jerk_unsoftened_and_hermite():
@@ -371,14 +376,39 @@ def test_symmetric_jerk_unsoftened_and_hermite():
         _, jerk = nb.forces_jerk(pos, vel, eps=0.0, tile=tile)
         np.testing.assert_allclose(jerk[0, :3].cpu().numpy(), [-0.00128, -0.02304, 0.0],
                                    rtol=2e-6, atol=1e-9)
-        p, vv = grav_tensors(g)
-        acc = torch.empty_like(p)
-        jk = torch.empty_like(p)
-        nb.hermite_step(p, vv, acc, jk, dt=1e-3, nsteps=10, eps=eps, tile=tile)
-        ex = traj_errors(p[:, :3].cpu().numpy(), xr)
-        ev = traj_errors(vv[:, :3].cpu().numpy(), vr)
-        assert ex[0] <= 1e-6 and ex[1] <= 1e-5, (tile, ex)
-        assert ev[0] <= 1e-5 and ev[1] <= 1e-4, (tile, ev)
+        for fixed in (False, True):
+            p, vv = grav_tensors(g)
+            acc = torch.empty_like(p)
+            jk = torch.empty_like(p)
+            nb.hermite_step(p, vv, acc, jk, dt=1e-3, nsteps=10, eps=eps, tile=tile,
+                            fixed=fixed)
+            ex = traj_errors(p[:, :3].cpu().numpy(), xr)
+            ev = traj_errors(vv[:, :3].cpu().numpy(), vr)
+            assert ex[0] <= 1e-6 and ex[1] <= 1e-5, (tile, fixed, ex)
+            assert ev[0] <= 1e-5 and ev[1] <= 1e-4, (tile, fixed, ev)
+    with pytest.raises(nb.NBodyError):  # no bound without softening
+        nb.forces_jerk(pos, vel, eps=0.0, fixed=True)
+
+
+@pytest.mark.slow
+def test_symmetric_jerk_fixed_point_at_two_to_the_twenty():
+    """N = 2^20, blocks of 512: the two partial blocks of one slot per particle and
+    block would take 64 GiB (above the cap), so the softened evaluation takes the
+    fixed-point sums (128 B per particle); 48 seeded particles against the oracle."""
+    nb = lib()
+    n = 1 << 20
+    g = workloads.plummer(n, seed=11, eps=workloads.plummer_softening(n))
+    pos, vel = grav_tensors(g)
+    eps = float(np.float32(g.eps))
+    tile = [t for t in _sym_ljc_tiles(nb.TABLE_JERK)
+            if nb.tile_info(nb.TABLE_JERK, t)["j_tile"] == 512][0]
+    acc, jerk = nb.forces_jerk(pos, vel, eps=eps, tile=tile)
+    idx = np.sort(np.random.default_rng(12).choice(n, 48, replace=False))
+    x, v, m = g.f32_as_f64()
+    ra, rj = oracle.grav_jerk(x, v, m, eps=eps, idx=idx)
+    it = torch.from_numpy(idx).to(dev())
+    assert_forces_close(acc[it, :3].cpu().numpy(), ra, what="GAJ acc 2^20")
+    assert_forces_close(jerk[it, :3].cpu().numpy(), rj, what="GAJ jerk 2^20")
 
 
 @pytest.mark.parametrize("linear", [False, True])
