@@ -4,9 +4,11 @@ Forward: ``nsteps`` KDK steps through nbody_step with the compensated two-float
 state, storing (x, v, low parts) every ``k`` steps, and the positions of the
 newest chunk. Backward: for each chunk, newest first, run the reverse sweep
 nbody_adjoint_leapfrog (force VJP kernels + fused adjoint updates) over the
-chunk's positions; those are recomputed from the checkpoint with nbody_step's
-trace on a second stream while the sweep of the next-newer chunk runs, so the
-two fill each other's partial waves (the newest chunk's positions are stored).
+chunk's positions; those are recomputed from the checkpoint (positions,
+velocities, two-float low parts and the acceleration carried in) with
+nbody_step's trace on a second stream while the sweep of the next-newer chunk
+runs, so the two fill each other's partial waves (the newest chunk's positions
+are stored): k - 1 force evaluations per chunk of k steps.
 With merged half-kicks the sweep is
 
     lam_x += dt/2 J(x_T)^T lam_v                      (only if dL/dv_T != 0)
@@ -69,7 +71,10 @@ class NBodyLeapfrog(torch.autograd.Function):
         last_trace = None
         while done < cfg.nsteps:
             steps = min(cfg.k, cfg.nsteps - done)
-            ckpts.append((pos.clone(), vel.clone(), lo.clone()))
+            # the checkpoint keeps a(x) at its positions too (carried in from the
+            # previous chunk), so that its recompute starts without an evaluation
+            ckpts.append((pos.clone(), vel.clone(), lo.clone(),
+                          acc.clone() if done > 0 else None))
             # The newest chunk is the first one the backward pass needs: keep its
             # positions now instead of recomputing them from the checkpoint.
             if done + steps == cfg.nsteps:
@@ -111,16 +116,23 @@ class NBodyLeapfrog(torch.autograd.Function):
         side_acc = []
 
         def recompute(c):
-            """Enqueue chunk c's positions on the side stream; (trace, done event)."""
-            p0, v0, l0 = ctx.ckpts[c]
+            """Enqueue chunk c's positions on the side stream; (trace, done event).
+            The sweep reads x_0 .. x_{steps-1} of the chunk: steps - 1 leapfrog
+            steps from the checkpoint (with its stored a(x_0) where the forward pass
+            carried one in) give exactly those, with the forward's own kernels and
+            bits, and no force evaluation whose result the sweep does not use."""
+            p0, v0, l0, a0 = ctx.ckpts[c]
             steps = min(cfg.k, cfg.nsteps - starts[c])
             with torch.cuda.stream(side):
                 pos, vel, lo = p0.clone(), v0.clone(), l0.clone()
                 if not side_acc:
                     side_acc.append(torch.empty_like(pos))
-                trace = torch.empty(((steps + 1) * n, 4), dtype=torch.float32, device=dev)
-                api.step(pos, vel, side_acc[0], ctx.prm, dt=cfg.dt, nsteps=steps, law=cfg.law,
-                         G=cfg.G, eps=cfg.eps, trace=trace, state_lo=lo, stream=side)
+                if a0 is not None:
+                    side_acc[0].copy_(a0)
+                trace = torch.empty((steps * n, 4), dtype=torch.float32, device=dev)
+                api.step(pos, vel, side_acc[0], ctx.prm, dt=cfg.dt, nsteps=steps - 1,
+                         law=cfg.law, G=cfg.G, eps=cfg.eps, acc_valid=a0 is not None,
+                         trace=trace, state_lo=lo, stream=side)
             done = torch.cuda.Event()
             done.record(side)
             return trace, done
