@@ -106,6 +106,24 @@ def test_bad_arguments_rejected_without_gpu(lib):
                           None) == 1
 
 
+def test_fixed_point_needs_softened_gravity_without_gpu(lib):
+    """NBODY_FIXED_POINT for the VJP and acceleration + jerk: its scale needs a
+    bound, so eps2 == 0 (and, for the VJP, an LJC law) is refused before any
+    device work."""
+    from paper_0706_3060_gb300._lib import FIXED_POINT, NBodyParams
+    ptr = ctypes.c_void_p(16)
+    p = NBodyParams(0, FIXED_POINT, 1.0, 0.0, -1, 0)
+    st = lib.nbody_adjoint(ptr, None, ptr, ptr, None, None, 4, ctypes.c_float(1.0), 8,
+                           ctypes.byref(p), None)
+    assert st == 1 and b"eps2 > 0" in lib.nbody_last_error()
+    q = NBodyParams(1, FIXED_POINT, 1.0, 0.01, -1, 0)
+    st = lib.nbody_adjoint(ptr, ptr, ptr, ptr, None, None, 4, ctypes.c_float(1.0), 8,
+                           ctypes.byref(q), None)
+    assert st == 1 and b"gravity" in lib.nbody_last_error()
+    st = lib.nbody_forces_jerk(ptr, ptr, ptr, ptr, 8, ctypes.byref(p), None)
+    assert st == 1 and b"eps2 > 0" in lib.nbody_last_error()
+
+
 def test_no_device_is_reported(lib):
     import torch
     if torch.cuda.is_available():
